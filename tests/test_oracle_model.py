@@ -1,0 +1,241 @@
+"""Pins of the oracle's model terms: basis, kinetic, Hartree, exchange,
+Coulomb kernel, Hermiticity, energy combination and the gradient (Eq. 8)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import roks as R
+from paper_2605_28637_gb300 import synthetic as syn
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def tiny(**kw):
+    return syn.with_changes(syn.make_config("tiny-16", 0), **kw)
+
+
+def free_electron_cfg(n_closed=7, N=16):
+    cfg = tiny(n_closed=n_closed, mode=0, grid=N)
+    cfg["atoms"] = [dict(a, depth=0.0) for a in cfg["atoms"]]
+    cfg["species"] = [dict(s, D=np.zeros_like(s["D"]), Q=np.zeros_like(s["Q"]))
+                      for s in cfg["species"]]
+    return cfg
+
+
+# ------------------------------------------------------------------ basis
+def test_basis_counts_golden():
+    """Full-sphere counts by brute force in floating point; half-sphere counts
+    against the plane-wave numbers quoted with the workloads."""
+    with open(os.path.join(GOLDEN, "basis_counts.json")) as f:
+        gold = json.load(f)
+    for name, ent in gold["workloads"].items():
+        cfg = syn.make_config(name, 0)
+        L, ecut = cfg["L"], cfg["ecut"]
+        b = 2 * np.pi / L
+        n = int(np.ceil(np.sqrt(2 * ecut) / b)) + 1
+        r = np.arange(-n, n + 1)
+        i, j, k = np.meshgrid(r, r, r, indexing="ij")
+        cnt = int((0.5 * b * b * (i * i + j * j + k * k) <= ecut).sum())
+        assert cnt == ent["npw_full"]
+        assert (cnt + 1) // 2 == ent["npw_half"]
+        if "quoted_approx" in ent:
+            assert abs(ent["npw_half"] - ent["quoted_approx"]) <= 0.1 * ent["quoted_approx"]
+
+
+def test_basis_order_and_map():
+    s = R.System(tiny())
+    m = s.miller
+    assert s.npw == 1045
+    key = [tuple(v) for v in m]
+    assert key == sorted(key)                       # i, then j, then k ascending
+    assert len(set(s.gidx.tolist())) == s.npw       # injective on the grid
+    assert ((m ** 2).sum(1) <= s.M).all()
+    assert s.N >= 2 * s.nmax + 1
+
+
+# ------------------------------------------------------------------ kinetic / free electrons
+def test_free_electron_apply_is_kinetic():
+    s = R.System(free_electron_cfg(), hartree=False, xc=False)
+    pot = s.potentials(np.zeros((3, s.N ** 3)))
+    Psi = np.zeros((s.npw, 5), complex)
+    picks = [0, 17, 300, 522, 1044]
+    for c, g in enumerate(picks):
+        Psi[g, c] = 1.0
+    for cls in (0, 1, 2):
+        F, S = s.apply(Psi, pot, classes=np.full(5, cls))
+        expect = s.w[cls] * 0.5 * s.g2[picks]
+        for c, g in enumerate(picks):
+            col = F[:, c].copy()
+            assert abs(col[g] - expect[c]) < 1e-12
+            col[g] = 0
+            assert np.abs(col).max() < 1e-12
+        assert np.allclose(S, Psi)
+
+
+@pytest.mark.slow
+def test_free_electron_ground_state_eigenvalues():
+    """Closed shell with V=0: the occupied subspace of F^c = 2H holds
+    |G|^2 (= 2 * |G|^2/2) for G = 0 and the six shortest G."""
+    s = R.System(free_electron_cfg(n_closed=7), hartree=False, xc=False)
+    Psi = s.initial_orbitals(syn.orbital_uniforms(s.cfg, s.npw))
+    Psi, hist = R.run(s, Psi, max_iter=200, e_tol=1e-12)
+    pot = s.potentials(s.class_densities(Psi))
+    F, _ = s.apply(Psi, pot)
+    ev = np.sort(np.linalg.eigvalsh(0.5 * (Psi.conj().T @ F + (Psi.conj().T @ F).conj().T)))
+    k1 = (2 * np.pi / s.L) ** 2
+    assert np.allclose(ev, [0.0] + [k1] * 6, atol=1e-7)
+
+
+# ------------------------------------------------------------------ Hartree / exchange / kernel
+def test_hartree_single_cosine():
+    s = R.System(tiny(), xc=False)
+    N, L = s.N, s.L
+    a = np.arange(N) * L / N
+    x, y, z = np.meshgrid(a, a, a, indexing="ij")
+    G0 = 2 * np.pi / L * np.array([2, -1, 3])
+    rho0 = 0.37
+    rho = rho0 * np.cos(G0[0] * x + G0[1] * y + G0[2] * z).reshape(-1)
+    rho_k = np.zeros((3, N ** 3))
+    rho_k[0] = 0.5 * rho                       # total density = 2 rho_closed
+    pot = s.potentials(rho_k)
+    g02 = G0 @ G0
+    assert abs(pot.E["H"] - s.omega * np.pi * rho0 ** 2 / g02) < 1e-12
+    assert np.allclose(pot.VH, 4 * np.pi * rho / g02, atol=1e-12)
+
+
+def test_slater_uniform_and_derivative():
+    s = R.System(tiny(), hartree=False)
+    N = s.N
+    rho_k = np.zeros((3, N ** 3))
+    rho_k[0], rho_k[1], rho_k[2] = 0.02, 0.013, 0.007
+    pot = s.potentials(rho_k)
+    cx = 0.75 * (6 / np.pi) ** (1 / 3)
+    up, dn = 0.02 + 0.013, 0.02 + 0.007
+    assert np.isclose(pot.E["x_M"], -cx * s.omega * (up ** (4 / 3) + dn ** (4 / 3)), rtol=1e-13)
+    assert np.allclose(pot.vx[0], -(6 * up / np.pi) ** (1 / 3), rtol=1e-13)
+    # finite difference of E_x^M with respect to rho_a at one grid point
+    rng = np.random.default_rng(3)
+    rho_k = rng.uniform(0.001, 0.05, (3, N ** 3))
+    p = 1234
+    h = 1e-6
+    rp, rm = rho_k.copy(), rho_k.copy()
+    rp[1, p] += h
+    rm[1, p] -= h
+    fd = (s.potentials(rp).E["x_M"] - s.potentials(rm).E["x_M"]) / (2 * h)
+    v = s.potentials(rho_k).vx[0, p]                 # rho_a enters the up-M channel
+    assert np.isclose(fd, v * s.dvol(), rtol=1e-7)
+
+
+def test_truncated_coulomb_gaussian_self_energy():
+    """A normalised Gaussian charge of width sigma has self-energy
+    1/(2 sigma sqrt(pi)); the truncated kernel reproduces the isolated value."""
+    cfg = tiny(grid=48, L=16.0)
+    s = R.System(cfg, hartree=False, xc=False)
+    N, L = s.N, s.L
+    a = np.arange(N) * L / N - L / 2
+    x, y, z = np.meshgrid(a, a, a, indexing="ij")
+    sig = 0.6
+    rho = ((2 * np.pi * sig ** 2) ** -1.5 * np.exp(-(x * x + y * y + z * z) / (2 * sig ** 2))).reshape(-1)
+    rG = s.grid_fourier(rho)
+    K = s.omega * float((s.coulomb_trunc() * np.abs(rG) ** 2).sum())
+    assert abs(0.5 * K - 1 / (2 * sig * np.sqrt(np.pi))) < 1e-6
+
+
+# ------------------------------------------------------------------ operators
+@pytest.mark.parametrize("alpha", [0.0, 1 / 3])
+def test_hermiticity(alpha):
+    s = R.System(tiny(alpha=alpha))
+    Psi = s.initial_orbitals(syn.orbital_uniforms(s.cfg, s.npw))
+    pot = s.potentials(s.class_densities(Psi))
+    phi = syn.random_vectors(11, s.npw, 3)
+    psi = syn.random_vectors(12, s.npw, 3)
+    for cls in (0, 1, 2):
+        classes = np.full(3, cls)
+        Fpsi, Spsi = s.apply(psi, pot, classes=classes, occ=Psi)
+        Fphi, Sphi = s.apply(phi, pot, classes=classes, occ=Psi)
+        a = phi.conj().T @ Fpsi
+        b = (psi.conj().T @ Fphi).conj().T
+        assert np.abs(a - b).max() < 1e-12 * np.abs(a).max()
+        a = phi.conj().T @ Spsi
+        b = (psi.conj().T @ Sphi).conj().T
+        assert np.abs(a - b).max() < 1e-12 * np.abs(a).max()
+
+
+@pytest.mark.parametrize("mode,alpha", [(1, 0.0), (1, 1 / 3), (2, 0.0), (0, 0.0), (0, 1 / 3)])
+def test_gradient_finite_difference(mode, alpha):
+    """dE/dh along a random direction = 2 Re sum_n <delta_n|F^n psi_n> (Eq. 8)."""
+    s = R.System(tiny(mode=mode, alpha=alpha, n_closed=4 if mode else 5))
+    Psi = s.initial_orbitals(syn.orbital_uniforms(s.cfg, s.npw))
+    pot = s.potentials(s.class_densities(Psi))
+    F, _ = s.apply(Psi, pot)
+    d = 0.1 * syn.random_vectors(5, s.npw, s.nb)
+    an = 2 * np.real(np.vdot(d, F))
+    h = 1e-4
+    fd = (s.energy(Psi + h * d) - s.energy(Psi - h * d)) / (2 * h)
+    assert abs(fd - an) < 1e-8 * abs(an)
+
+
+def test_energy_combination_term_by_term():
+    """E_S = 2 E_M - E_T, and the one-electron and Hartree parts are shared by
+    the two configurations so that E_S - E_T = 2 (E_x^M - E_x^T) + 2 alpha (E_HF^M - E_HF^T)."""
+    s = R.System(tiny(alpha=1 / 3))
+    Psi = s.initial_orbitals(syn.orbital_uniforms(s.cfg, s.npw))
+    E = s.energies(Psi)
+    assert E["total"] == pytest.approx(2 * E["M"] - E["T"], abs=1e-13)
+    lhs = E["total"] - E["T"]
+    rhs = 2 * (E["x_M"] - E["x_T"]) + 2 * s.alpha * (E["hf_M"] - E["hf_T"])
+    assert abs(lhs - rhs) < 1e-12
+    # independent evaluation of E_M from the mixed configuration's spin orbitals
+    up = list(range(s.n_closed)) + [s.n_closed]
+    dn = list(range(s.n_closed)) + [s.n_closed + 1]
+    psis = [s.to_real(Psi[:, n]) for n in range(s.nb)]
+    rup = sum(np.abs(psis[n]) ** 2 for n in up)
+    rdn = sum(np.abs(psis[n]) ** 2 for n in dn)
+    ex = -(1 - s.alpha) * R.slater_prefactor() * s.dvol() * ((rup ** (4 / 3)).sum() + (rdn ** (4 / 3)).sum())
+    assert np.isclose(ex, E["x_M"], rtol=1e-13)
+
+
+def test_orbital_classes_and_weights():
+    """Shell weights from f and c_L: w = (2, 1, 1); the exchange pair table of
+    the singlet; triplet shares the a/b operator."""
+    s = R.System(tiny())
+    assert np.allclose(s.w, [2, 1, 1])
+    assert np.allclose(s.WX, [[2, 1, 1], [1, 1, -1], [1, -1, 1]])
+    assert np.allclose(s.C, [[2, 2, -1, -1], [2, 0, -1, 0], [0, 2, -1, 0]])
+    t = R.System(tiny(mode=2))
+    assert np.allclose(t.C[1], t.C[2]) and np.allclose(t.w, [2, 1, 1])
+    g = R.System(tiny(mode=0, n_closed=5))
+    assert g.nb == 5 and np.allclose(g.w[0], 2) and np.allclose(g.C[0], [1, 1, 0, 0])
+
+
+def test_local_potential_is_periodic_gaussian_sum():
+    """On a fine grid far from the Nyquist planes the band-limited wells match
+    the real-space periodic Gaussian sum."""
+    cfg = tiny(grid=40)
+    s = R.System(cfg)
+    N, L = s.N, s.L
+    a = np.arange(N) * L / N
+    X, Y, Z = np.meshgrid(a, a, a, indexing="ij")
+    V = np.zeros_like(X)
+    for at in cfg["atoms"]:
+        R0 = np.array(at["pos"])
+        for sx in (-1, 0, 1):
+            for sy in (-1, 0, 1):
+                for sz in (-1, 0, 1):
+                    d2 = ((X - R0[0] - sx * L) ** 2 + (Y - R0[1] - sy * L) ** 2
+                          + (Z - R0[2] - sz * L) ** 2)
+                    V -= at["depth"] * np.exp(-d2 / (2 * at["width"] ** 2))
+    assert np.abs(V.reshape(-1) - s.Vloc).max() < 1e-8
+
+
+def test_projector_norm_and_overlap():
+    """Each projector has unit norm in a large cell; S is positive definite."""
+    cfg = tiny(L=14.0, ecut=40.0, grid=48)
+    s = R.System(cfg)
+    norms = np.sum(np.abs(s.P) ** 2, axis=0)
+    assert np.allclose(norms, 1.0, atol=1e-6)
+    Gm = s.P.conj().T @ s.P
+    ev = np.linalg.eigvalsh(np.eye(s.nproj) + 0.5 * (s.Q @ Gm + (s.Q @ Gm).conj().T))
+    assert ev.min() > 0.1
