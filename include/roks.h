@@ -1,0 +1,232 @@
+/*
+ * roks.h -- C ABI of the GB300 (sm_103a) ROKS plane-wave hot path.
+ *
+ * The method: restricted open-shell Kohn-Sham DFT for the lowest excited
+ * singlet, E_S = 2 E(Phi_1) - E(Phi_3) (Eq. 1), minimised over one set of
+ * spatial orbitals shared by the mixed-spin configuration Phi_1 (a up,
+ * b down) and the triplet Phi_3 (a up, b up), subject to <m|S|n> = delta_mn
+ * (Eq. 2), by all-band preconditioned conjugate gradients (Sec. II A,
+ * Eqs. 5-24).  Orbitals are expanded in plane waves on a cubic cell at the
+ * Gamma point.  The Hamiltonian model: kinetic energy, Gaussian local wells,
+ * separable s/p projectors sum |p_i> D_ij <p_j| with overlap
+ * S = 1 + sum |p_i> Q_ij <p_j| (Eq. 3), Hartree, LSDA Slater exchange per
+ * spin channel and an optional exact-exchange fraction alpha with a
+ * spherically truncated Coulomb kernel.
+ *
+ * Conventions for every entry point:
+ *  - Orbitals Psi are column-major, npw x nbands complex numbers stored as
+ *    interleaved (re, im) pairs, leading dimension ld >= npw (in complex
+ *    elements).  Element type: double for ROKS_FP64, float for ROKS_MIXED.
+ *    Column order is closed bands, then open band a, then open band b.
+ *  - Coefficient index g follows the basis order of roks_basis().
+ *  - Device pointers belong to the caller; they must stay valid for the
+ *    duration of the call (stream ordered).  The library owns its internal
+ *    workspaces and frees them in roks_destroy().
+ *  - All work is ordered on the CUDA stream given to roks_setup().  Calls
+ *    that return host scalars (roks_potential, roks_pcg_step,
+ *    roks_energies_get) synchronise that stream; the others do not.
+ *  - Errors are returned as roks_status; roks_last_error() gives text.  No
+ *    C++ exception crosses this interface.  A context is not thread safe.
+ */
+#ifndef ROKS_H
+#define ROKS_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ROKS_API __attribute__((visibility("default")))
+#else
+#define ROKS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct roks_ctx roks_ctx;
+
+typedef enum {
+    ROKS_OK = 0,
+    ROKS_EINVAL = 1,      /* invalid argument or unsupported size            */
+    ROKS_ENOMEM = 2,      /* device or host allocation failed                 */
+    ROKS_ECUDA = 3,       /* a CUDA runtime call failed                       */
+    ROKS_ENOTPOSDEF = 4,  /* overlap matrix not positive definite (Cholesky) */
+    ROKS_ENOCONV = 5,     /* iteration limit reached without convergence      */
+    ROKS_ETIMEOUT = 6,    /* a bounded device wait ran out                    */
+    ROKS_EDIVERGED = 7    /* non-finite energy or gradient                    */
+} roks_status;
+
+enum { ROKS_FP64 = 0, ROKS_MIXED = 1 };
+/* Occupation modes (Sec. II A): 0 closed-shell ground state, one
+ * configuration with c = 1; 1 ROKS singlet, c_M = 2, c_T = -1 (Eq. 1);
+ * 2 triplet configuration alone, c_T = 1. */
+enum { ROKS_MODE_GS = 0, ROKS_MODE_SINGLET = 1, ROKS_MODE_TRIPLET = 2 };
+
+/* Cubic cell of side L (Bohr) with an N x N x N FFT grid.  Supported N:
+ * 16, 24, 32, 48, 72, 96, 120. */
+typedef struct {
+    double L;
+    int grid;
+} roks_cell;
+
+/* Atom: position (Bohr), species index, Gaussian local well
+ * V(r) = -depth * exp(-|r-R|^2 / (2 width^2)), summed over periodic images
+ * and band limited to the grid (Nyquist planes excluded). */
+typedef struct {
+    double pos[3];
+    int species;
+    double depth;   /* Ha */
+    double width;   /* Bohr */
+} roks_atom;
+
+/* Projector set of a species: nproj channels, channel c has angular
+ * momentum l[c] (0 = s, 1 = p), Cartesian component m[c] (p only: 0 x,
+ * 1 y, 2 z) and Gaussian radius rc[c] (Bohr).  In reciprocal space
+ * p_c(G) = Omega^{-1/2} N_l (2 pi rc^2)^{3/2} exp(-G^2 rc^2/2) Y(G) exp(-iG.R),
+ * Y = 1 (s) or -i rc^2 G_m (p), N_l giving unit norm.  D (Ha) and Q
+ * (dimensionless) are nproj x nproj symmetric, row major.  The arrays are
+ * read during roks_setup only. */
+typedef struct {
+    int nproj;
+    const int* l;
+    const int* m;
+    const double* rc;
+    const double* D;
+    const double* Q;
+} roks_species;
+
+/* n_closed doubly occupied bands; modes 1 and 2 add the open bands a, b. */
+typedef struct {
+    int n_closed;
+    int mode;
+} roks_occ;
+
+typedef struct {
+    int precision;     /* ROKS_FP64 or ROKS_MIXED (FP32 FFTs and contractions,
+                          FP64 Cholesky, reductions and scalars)             */
+    double alpha;      /* exact-exchange fraction (0 = none); Slater exchange
+                          is scaled by (1 - alpha)                           */
+    int suppress_ab;   /* 1: zero the open-shell a-b block of R (Eq. 20),
+                          the coupling suppression of Sec. II A              */
+    double e_tol;      /* PCG convergence: |E_i+1 - E_i| < e_tol twice (Ha)  */
+} roks_options;
+
+/* Energy terms (Ha).  E_kin, E_loc, E_nl carry the occupation weights;
+ * E_M, E_T are the two configuration energies, E_total = c_M E_M + c_T E_T
+ * (E_S for the singlet, Eq. 1). */
+typedef struct {
+    double E_kin, E_loc, E_nl, E_H;
+    double E_x_M, E_x_T;          /* (1 - alpha) Slater exchange per configuration */
+    double E_hf_M, E_hf_T;        /* exact-exchange integrals (before alpha)       */
+    double E_M, E_T, E_total;
+} roks_energies;
+
+/* Result of one PCG iteration. */
+typedef struct {
+    double E;            /* energy at the start of the step                 */
+    double E_new;        /* energy after the step                           */
+    double step;         /* Delta of Eqs. 5 and 24                          */
+    double grad_norm;    /* Frobenius norm of the constrained gradient g    */
+    double coupling_re;  /* <a|F^a - F^b|b> at the start (Eq. 16)           */
+    double coupling_im;
+    double beta;         /* Fletcher-Reeves ratio used (0 after a restart)  */
+    double dE0;          /* directional derivative of E along the step      */
+    int restarted;       /* 1 when the CG direction was reset               */
+    int converged;       /* 1 once |dE| < e_tol on two consecutive steps    */
+} roks_step_info;
+
+/* Builds the plane-wave basis (Miller vectors with |G|^2/2 <= ecut, tested
+ * in integers as i^2+j^2+k^2 <= floor(2 ecut (L/2pi)^2); loops i, j, k
+ * ascending from -n to n), the local potential, the projectors and all
+ * device workspaces, on `cuda_stream` (a cudaStream_t, or NULL for the
+ * legacy default stream) of the current device.  Returns ROKS_EINVAL for an
+ * unsupported grid, a grid smaller than 2 n + 1, or bad counts.  On success
+ * *out owns device memory until roks_destroy(). */
+ROKS_API roks_status roks_setup(const roks_cell* cell, double ecut, int natoms,
+                       const roks_atom* atoms, int nspecies,
+                       const roks_species* species, const roks_occ* occ,
+                       const roks_options* opt, void* cuda_stream,
+                       roks_ctx** out);
+
+/* Basis size, band count, the minimal leading dimension, and a host
+ * pointer to the npw x 3 Miller indices (row major, owned by the context). */
+ROKS_API roks_status roks_basis(roks_ctx* ctx, int* npw, int* nbands, int* ld_min,
+                       const int32_t** miller);
+
+/* Initial orbitals (seeded start): u_host holds nbands x npw x 2 uniform
+ * numbers (band major, re/im innermost); the library forms
+ * c_nG = (u_re + i u_im)/(1 + |G|^2) and S-orthonormalises them into psi
+ * (device, ld >= npw).  u_host is read before the call returns. */
+ROKS_API roks_status roks_init_orbitals(roks_ctx* ctx, const double* u_host,
+                               void* psi, int64_t ld);
+
+/* Class densities rho_k(r) = sum_{n in k} |psi_n(r)|^2, k = closed, a, b
+ * (the inputs of the spin densities of Eq. 9), plus the kinetic and
+ * non-local energy terms of psi.  rho_out (optional, device, 3 x N^3 double,
+ * grid index (x N + y) N + z) receives a copy. */
+ROKS_API roks_status roks_density(roks_ctx* ctx, const void* psi, int64_t ld,
+                         double* rho_out);
+
+/* From the last roks_density: channel densities rho^{sigma L}, one Hartree
+ * solve (rho_M = rho_T), Slater exchange per channel and the class
+ * potentials V^k = w_k (V_loc + V_H) + sum_{sigma L} c_L f_k v_x (Eqs. 9, 14).
+ * Fills *e (host; may be NULL).  vclass_out (optional, device, 3 x N^3 of
+ * the orbital element type) receives V^closed, V^a, V^b.  Synchronises. */
+ROKS_API roks_status roks_potential(roks_ctx* ctx, roks_energies* e, void* vclass_out);
+
+/* Shell operators applied to each band with the last roks_potential:
+ * fpsi_n = F^{k(n)}|n> (Eq. 14: kinetic + local + non-local, and exact
+ * exchange if alpha != 0).  spsi (optional) = S|n>.  grad (optional)
+ * = g_n = F^n|n> - sum_m S|m> gamma_nm with gamma of Eq. 11.  All outputs
+ * are device arrays with the same ld as psi. */
+ROKS_API roks_status roks_apply_h(roks_ctx* ctx, const void* psi, int64_t ld,
+                         void* fpsi, void* spsi, void* grad);
+
+/* In place S-orthonormalisation: O = Psi^H S Psi = L L^H (FP64 Cholesky),
+ * Psi <- Psi L^{-H}; band order closed, a, b.  ROKS_ENOTPOSDEF if O is not
+ * positive definite. */
+ROKS_API roks_status roks_orthonormalize(roks_ctx* ctx, void* psi, int64_t ld);
+
+/* One PCG iteration on psi (in place, S-orthonormal on entry and exit):
+ * gradient and gamma (Eqs. 8, 11), split (Eq. 12), TPA preconditioning
+ * (Eqs. 17, 18), Fletcher-Reeves direction (Eq. 7), R-matrix rotation
+ * generator (Eqs. 20-23), parabolic line search on E (Eq. 5) and the update
+ * orth((Psi + Delta s) exp(Delta (A^i + beta A^{i-1}))) (Eq. 24).  The
+ * direction history lives in the context; the first call (or the first after
+ * roks_init_orbitals / roks_orthonormalize) starts with steepest descent.
+ * psi must not be modified by the caller between consecutive steps.
+ * Fills *info (host).  Synchronises. */
+ROKS_API roks_status roks_pcg_step(roks_ctx* ctx, void* psi, int64_t ld,
+                          roks_step_info* info);
+
+/* Energies of the last completed density/potential evaluation.  Synchronises. */
+ROKS_API roks_status roks_energies_get(roks_ctx* ctx, roks_energies* e);
+
+/* Kernel-family timing (tracing).  While enabled, CUDA events are recorded
+ * on the context's stream around each instrumented launch group (the band
+ * transform stages, projector contractions, potentials, orthonormalisation,
+ * subspace and rotation steps). */
+typedef struct {
+    char name[32];     /* family name, NUL terminated                        */
+    int launches;      /* event pairs recorded since the last read          */
+    double ms;         /* summed device time between the pairs (ms)         */
+} roks_profile_entry;
+
+ROKS_API roks_status roks_profile_enable(roks_ctx* ctx, int enable);
+
+/* Synchronises the stream, writes up to cap entries to out (host), sets
+ * *count to the number of families recorded and clears the record. */
+ROKS_API roks_status roks_profile_read(roks_ctx* ctx, roks_profile_entry* out, int cap,
+                                       int* count);
+
+/* Text of the last error on this context ("" if none).  Never NULL. */
+ROKS_API const char* roks_last_error(const roks_ctx* ctx);
+
+/* Frees every device and host resource of the context.  NULL is a no-op. */
+ROKS_API void roks_destroy(roks_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ROKS_H */

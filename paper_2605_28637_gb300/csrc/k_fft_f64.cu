@@ -1,0 +1,5 @@
+// Double-precision instantiation of the band and grid transforms.
+#include "k_fft_impl.cuh"
+namespace roks {
+ROKS_INSTANTIATE_FFT(double)
+}

@@ -1,0 +1,461 @@
+// k_fft_impl.cuh -- the band transforms of the plane-wave apply and density
+// passes, and the full-grid 3D transform.  Included by one translation unit
+// per precision.
+//
+// Band path (inverse direction, coefficients -> real space):
+//   z stage : for every (i, j) column of the sphere, scatter the contiguous
+//             coefficients k = -kmax..kmax into a z line and transform it;
+//   y stage : for every plane i and every z, gather the columns of the plane
+//             into a y line and transform it;
+//   x stage : for every (y, z), gather the 2 nmax + 1 nonzero planes into an
+//             x line and transform it -> psi(r) line.
+// Only the x stage touches full grid lines; columns and planes outside the
+// sphere are never stored.  The forward direction mirrors it and keeps only
+// the outputs that lie in the sphere.
+#pragma once
+
+#include "roks_impl.cuh"
+
+namespace roks {
+
+template <typename V, int N>
+__device__ __forceinline__ void load_twiddles(V* tws, const V* tw) {
+    for (int t = threadIdx.x; t < N; t += blockDim.x) tws[t] = tw[t];
+}
+
+template <typename V, int N, int LS>
+__device__ __forceinline__ V* tile_buf(unsigned char* smem) { return reinterpret_cast<V*>(smem); }
+
+template <typename V, int N, int LS>
+constexpr size_t tile_smem_bytes() { return sizeof(V) * (size_t(N) * LS + N); }
+
+// ------------------------------------------------------------------ z stage
+template <typename T, int N>
+__global__ void __launch_bounds__(kThreads) k_band_z_inv(Sphere s, const c2<T>* __restrict__ tw,
+                                                         const c2<T>* __restrict__ psi, int64_t ld,
+                                                         int b0, c2<T>* __restrict__ Zc) {
+    using V = c2<T>;
+    constexpr int TL = tile_lines(N), LS = TL + 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    V* buf = reinterpret_cast<V*>(smem);
+    V* tws = buf + N * LS;
+    load_twiddles<V, N>(tws, tw);
+    const int c0 = blockIdx.x * TL;
+    const int bb = blockIdx.y;
+    const V* p = psi + (int64_t)(b0 + bb) * ld;
+    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
+        const int line = idx / N, e = idx - line * N;
+        const int c = c0 + line;
+        V v = mk<T>(T(0), T(0));
+        if (c < s.ncol) {
+            const int k = signed_freq(e, N);
+            const int km = s.col_kmax[c];
+            if (k >= -km && k <= km) v = p[s.col_start[c] + k + km];
+        }
+        buf[e * LS + line] = v;
+    }
+    __syncthreads();
+    tile_fft<V, N, +1, TL, LS, kThreads>(buf, tws);
+    V* out = Zc + (int64_t)bb * s.ncol * N;
+    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
+        const int line = idx / N, e = idx - line * N;
+        const int c = c0 + line;
+        if (c < s.ncol) out[(int64_t)c * N + e] = buf[e * LS + line];
+    }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kThreads) k_band_z_fwd(Sphere s, const c2<T>* __restrict__ tw,
+                                                         const c2<T>* __restrict__ Zc,
+                                                         c2<T>* __restrict__ out, int64_t ldo,
+                                                         const c2<T>* __restrict__ psi, int64_t ldp,
+                                                         const T* __restrict__ g2half,
+                                                         const T* __restrict__ wk, int b0, int n_closed) {
+    using V = c2<T>;
+    constexpr int TL = tile_lines(N), LS = TL + 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    V* buf = reinterpret_cast<V*>(smem);
+    V* tws = buf + N * LS;
+    load_twiddles<V, N>(tws, tw);
+    const int c0 = blockIdx.x * TL;
+    const int bb = blockIdx.y;
+    const int b = b0 + bb;
+    const V* in = Zc + (int64_t)bb * s.ncol * N;
+    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
+        const int line = idx / N, e = idx - line * N;
+        const int c = c0 + line;
+        buf[e * LS + line] = (c < s.ncol) ? in[(int64_t)c * N + e] : mk<T>(T(0), T(0));
+    }
+    __syncthreads();
+    tile_fft<V, N, -1, TL, LS, kThreads>(buf, tws);
+    const int cls = b < n_closed ? 0 : b - n_closed + 1;
+    const T w = wk[cls];
+    V* o = out + (int64_t)b * ldo;
+    const V* p = psi + (int64_t)b * ldp;
+    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
+        const int line = idx / N, e = idx - line * N;
+        const int c = c0 + line;
+        if (c < s.ncol) {
+            const int k = signed_freq(e, N);
+            const int km = s.col_kmax[c];
+            if (k >= -km && k <= km) {
+                const int g = s.col_start[c] + k + km;
+                const V loc = buf[e * LS + line];
+                const V ps = p[g];
+                const T kin = w * g2half[g];
+                o[g] = mk<T>(loc.x + kin * ps.x, loc.y + kin * ps.y);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ y stage
+template <typename T, int N>
+__global__ void __launch_bounds__(kThreads) k_band_y_inv(Sphere s, const c2<T>* __restrict__ tw,
+                                                         const c2<T>* __restrict__ Zc,
+                                                         c2<T>* __restrict__ Yp) {
+    using V = c2<T>;
+    constexpr int TL = tile_lines(N), LS = TL + 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    V* buf = reinterpret_cast<V*>(smem);
+    V* tws = buf + N * LS;
+    load_twiddles<V, N>(tws, tw);
+    const int z0 = blockIdx.x * TL;
+    const int p = blockIdx.y;
+    const int bb = blockIdx.z;
+    const int jm = s.plane_jmax[p];
+    const V* in = Zc + ((int64_t)bb * s.ncol + s.plane_col0[p] + jm) * N;
+    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
+        const int e = idx / TL, line = idx - e * TL;
+        const int z = z0 + line;
+        const int j = signed_freq(e, N);
+        V v = mk<T>(T(0), T(0));
+        if (z < N && j >= -jm && j <= jm) v = in[(int64_t)j * N + z];
+        buf[e * LS + line] = v;
+    }
+    __syncthreads();
+    tile_fft<V, N, +1, TL, LS, kThreads>(buf, tws);
+    V* out = Yp + ((int64_t)bb * s.np + p) * N * N;
+    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
+        const int e = idx / TL, line = idx - e * TL;
+        const int z = z0 + line;
+        if (z < N) out[(int64_t)e * N + z] = buf[e * LS + line];
+    }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kThreads) k_band_y_fwd(Sphere s, const c2<T>* __restrict__ tw,
+                                                         const c2<T>* __restrict__ Yp,
+                                                         c2<T>* __restrict__ Zc) {
+    using V = c2<T>;
+    constexpr int TL = tile_lines(N), LS = TL + 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    V* buf = reinterpret_cast<V*>(smem);
+    V* tws = buf + N * LS;
+    load_twiddles<V, N>(tws, tw);
+    const int z0 = blockIdx.x * TL;
+    const int p = blockIdx.y;
+    const int bb = blockIdx.z;
+    const V* in = Yp + ((int64_t)bb * s.np + p) * N * N;
+    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
+        const int e = idx / TL, line = idx - e * TL;
+        const int z = z0 + line;
+        buf[e * LS + line] = (z < N) ? in[(int64_t)e * N + z] : mk<T>(T(0), T(0));
+    }
+    __syncthreads();
+    tile_fft<V, N, -1, TL, LS, kThreads>(buf, tws);
+    const int jm = s.plane_jmax[p];
+    V* out = Zc + ((int64_t)bb * s.ncol + s.plane_col0[p] + jm) * N;
+    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
+        const int e = idx / TL, line = idx - e * TL;
+        const int z = z0 + line;
+        const int j = signed_freq(e, N);
+        if (z < N && j >= -jm && j <= jm) out[(int64_t)j * N + z] = buf[e * LS + line];
+    }
+}
+
+// ------------------------------------------------------------------ x stage
+template <typename T, int N>
+__device__ __forceinline__ void load_x_lines(const Sphere& s, c2<T>* buf, const c2<T>* Ypb, int y, int z0) {
+    constexpr int TL = tile_lines(N), LS = TL + 1;
+    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
+        const int e = idx / TL, line = idx - e * TL;
+        const int z = z0 + line;
+        const int i = signed_freq(e, N);
+        c2<T> v = mk<T>(T(0), T(0));
+        if (z < N && i >= -s.nmax && i <= s.nmax) v = Ypb[((int64_t)(i + s.nmax) * N + y) * N + z];
+        buf[e * LS + line] = v;
+    }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kThreads) k_band_x_apply(Sphere s, const c2<T>* __restrict__ tw,
+                                                           c2<T>* __restrict__ Yp,
+                                                           const T* __restrict__ Vk, int b0,
+                                                           int n_closed, T scale) {
+    using V = c2<T>;
+    constexpr int TL = tile_lines(N), LS = TL + 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    V* buf = reinterpret_cast<V*>(smem);
+    V* tws = buf + N * LS;
+    load_twiddles<V, N>(tws, tw);
+    const int z0 = blockIdx.x * TL;
+    const int y = blockIdx.y;
+    const int bb = blockIdx.z;
+    const int b = b0 + bb;
+    const int cls = b < n_closed ? 0 : b - n_closed + 1;
+    V* Ypb = Yp + (int64_t)bb * s.np * N * N;
+    load_x_lines<T, N>(s, buf, Ypb, y, z0);
+    __syncthreads();
+    tile_fft<V, N, +1, TL, LS, kThreads>(buf, tws);
+    const T* Vc = Vk + (int64_t)cls * N * N * N;
+    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
+        const int e = idx / TL, line = idx - e * TL;
+        const int z = z0 + line;
+        if (z < N) {
+            const T v = Vc[((int64_t)e * N + y) * N + z] * scale;
+            V a = buf[e * LS + line];
+            buf[e * LS + line] = mk<T>(a.x * v, a.y * v);
+        }
+    }
+    __syncthreads();
+    tile_fft<V, N, -1, TL, LS, kThreads>(buf, tws);
+    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
+        const int e = idx / TL, line = idx - e * TL;
+        const int z = z0 + line;
+        const int i = signed_freq(e, N);
+        if (z < N && i >= -s.nmax && i <= s.nmax)
+            Ypb[((int64_t)(i + s.nmax) * N + y) * N + z] = buf[e * LS + line];
+    }
+}
+
+// Density: one block per (z tile, y) walks all bands of the block, keeping
+// the per-point sums of its own tile entries in registers (FP32 partial sums
+// of up to 16 bands folded into FP64 for the mixed path).
+template <typename T, int N>
+__global__ void __launch_bounds__(kThreads) k_band_x_density(Sphere s, const c2<T>* __restrict__ tw,
+                                                             const c2<T>* __restrict__ Yp,
+                                                             double* __restrict__ rho3, int b0, int nbb,
+                                                             int n_closed, double scale) {
+    using V = c2<T>;
+    constexpr int TL = tile_lines(N), LS = TL + 1;
+    constexpr int PER = (TL * N + kThreads - 1) / kThreads;
+    extern __shared__ __align__(16) unsigned char smem[];
+    V* buf = reinterpret_cast<V*>(smem);
+    V* tws = buf + N * LS;
+    load_twiddles<V, N>(tws, tw);
+    const int z0 = blockIdx.x * TL;
+    const int y = blockIdx.y;
+    const int N3 = N * N * N;
+    int bb = 0;
+    while (bb < nbb) {
+        const int b = b0 + bb;
+        const int cls = b < n_closed ? 0 : b - n_closed + 1;
+        const int seg_end = cls == 0 ? min(nbb, n_closed - b0) : bb + 1;
+        double acc[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) acc[q] = 0.0;
+        while (bb < seg_end) {
+            T part[PER];
+#pragma unroll
+            for (int q = 0; q < PER; ++q) part[q] = T(0);
+            const int chunk_end = min(seg_end, bb + 16);
+            for (; bb < chunk_end; ++bb) {
+                load_x_lines<T, N>(s, buf, Yp + (int64_t)bb * s.np * N * N, y, z0);
+                __syncthreads();
+                tile_fft<V, N, +1, TL, LS, kThreads>(buf, tws);
+#pragma unroll
+                for (int q = 0; q < PER; ++q) {
+                    const int idx = threadIdx.x + q * kThreads;
+                    if (idx < TL * N) {
+                        const int e = idx / TL, line = idx - e * TL;
+                        const V a = buf[e * LS + line];
+                        part[q] += a.x * a.x + a.y * a.y;
+                    }
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int q = 0; q < PER; ++q) acc[q] += double(part[q]);
+        }
+        double* r = rho3 + (int64_t)cls * N3;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int idx = threadIdx.x + q * kThreads;
+            if (idx < TL * N) {
+                const int e = idx / TL, line = idx - e * TL;
+                const int z = z0 + line;
+                if (z < N) r[((int64_t)e * N + y) * N + z] += acc[q] * scale;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ full grid
+template <typename T, int N>
+__global__ void __launch_bounds__(kThreads) k_grid_fft_z(const c2<T>* __restrict__ tw, c2<T>* data, int dir) {
+    using V = c2<T>;
+    constexpr int TL = tile_lines(N), LS = TL + 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    V* buf = reinterpret_cast<V*>(smem);
+    V* tws = buf + N * LS;
+    load_twiddles<V, N>(tws, tw);
+    const int l0 = blockIdx.x * TL;           // line = x * N + y
+    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
+        const int line = idx / N, e = idx - line * N;
+        const int l = l0 + line;
+        buf[e * LS + line] = (l < N * N) ? data[(int64_t)l * N + e] : mk<T>(T(0), T(0));
+    }
+    __syncthreads();
+    if (dir > 0) tile_fft<V, N, +1, TL, LS, kThreads>(buf, tws);
+    else tile_fft<V, N, -1, TL, LS, kThreads>(buf, tws);
+    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
+        const int line = idx / N, e = idx - line * N;
+        const int l = l0 + line;
+        if (l < N * N) data[(int64_t)l * N + e] = buf[e * LS + line];
+    }
+}
+
+// Lines along y (outer = x, estride = N) or x (outer = y, ostride = N,
+// estride = N^2); the tile runs over consecutive z.
+template <typename T, int N>
+__global__ void __launch_bounds__(kThreads) k_grid_fft_strided(const c2<T>* __restrict__ tw, c2<T>* data,
+                                                               int64_t ostride, int64_t estride, int dir) {
+    using V = c2<T>;
+    constexpr int TL = tile_lines(N), LS = TL + 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    V* buf = reinterpret_cast<V*>(smem);
+    V* tws = buf + N * LS;
+    load_twiddles<V, N>(tws, tw);
+    const int z0 = blockIdx.x * TL;
+    V* base = data + (int64_t)blockIdx.y * ostride;
+    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
+        const int e = idx / TL, line = idx - e * TL;
+        const int z = z0 + line;
+        buf[e * LS + line] = (z < N) ? base[e * estride + z] : mk<T>(T(0), T(0));
+    }
+    __syncthreads();
+    if (dir > 0) tile_fft<V, N, +1, TL, LS, kThreads>(buf, tws);
+    else tile_fft<V, N, -1, TL, LS, kThreads>(buf, tws);
+    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
+        const int e = idx / TL, line = idx - e * TL;
+        const int z = z0 + line;
+        if (z < N) base[e * estride + z] = buf[e * LS + line];
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+template <typename K>
+static void set_smem(K kernel, size_t bytes) {
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T, int N>
+struct BandFft {
+    using V = c2<T>;
+    static constexpr int TL = tile_lines(N);
+    static constexpr size_t SM = tile_smem_bytes<V, N, TL + 1>();
+
+    static void z_inv(const Sphere& s, const V* tw, const V* psi, int64_t ld, int b0, int nbb, V* Zc,
+                      cudaStream_t st) {
+        set_smem(k_band_z_inv<T, N>, SM);
+        dim3 gz((s.ncol + TL - 1) / TL, nbb);
+        k_band_z_inv<T, N><<<gz, kThreads, SM, st>>>(s, tw, psi, ld, b0, Zc);
+    }
+    static void y_inv(const Sphere& s, const V* tw, const V* Zc, V* Yp, int nbb, cudaStream_t st) {
+        set_smem(k_band_y_inv<T, N>, SM);
+        dim3 gy((N + TL - 1) / TL, s.np, nbb);
+        k_band_y_inv<T, N><<<gy, kThreads, SM, st>>>(s, tw, Zc, Yp);
+    }
+    static void x_apply(const Sphere& s, const V* tw, V* Yp, const T* Vk, int b0, int nbb, int nc, T scale,
+                        cudaStream_t st) {
+        set_smem(k_band_x_apply<T, N>, SM);
+        dim3 g((N + TL - 1) / TL, N, nbb);
+        k_band_x_apply<T, N><<<g, kThreads, SM, st>>>(s, tw, Yp, Vk, b0, nc, scale);
+    }
+    static void y_fwd(const Sphere& s, const V* tw, const V* Yp, V* Zc, int nbb, cudaStream_t st) {
+        set_smem(k_band_y_fwd<T, N>, SM);
+        dim3 gy((N + TL - 1) / TL, s.np, nbb);
+        k_band_y_fwd<T, N><<<gy, kThreads, SM, st>>>(s, tw, Yp, Zc);
+    }
+    static void z_fwd(const Sphere& s, const V* tw, const V* Zc, V* out, int64_t ldo, const V* psi, int64_t ldp,
+                      const T* g2half, const T* wk, int b0, int nbb, int nc, cudaStream_t st) {
+        set_smem(k_band_z_fwd<T, N>, SM);
+        dim3 gz((s.ncol + TL - 1) / TL, nbb);
+        k_band_z_fwd<T, N><<<gz, kThreads, SM, st>>>(s, tw, Zc, out, ldo, psi, ldp, g2half, wk, b0, nc);
+    }
+    static void x_density(const Sphere& s, const V* tw, const V* Yp, double* rho3, int b0, int nbb, int nc,
+                          double scale, cudaStream_t st) {
+        set_smem(k_band_x_density<T, N>, SM);
+        dim3 g((N + TL - 1) / TL, N);
+        k_band_x_density<T, N><<<g, kThreads, SM, st>>>(s, tw, Yp, rho3, b0, nbb, nc, scale);
+    }
+    static void grid3(const V* tw, V* data, int dir, cudaStream_t st) {
+        set_smem(k_grid_fft_z<T, N>, SM);
+        set_smem(k_grid_fft_strided<T, N>, SM);
+        k_grid_fft_z<T, N><<<(N * N + TL - 1) / TL, kThreads, SM, st>>>(tw, data, dir);
+        dim3 g((N + TL - 1) / TL, N);
+        k_grid_fft_strided<T, N><<<g, kThreads, SM, st>>>(tw, data, (int64_t)N * N, (int64_t)N, dir);
+        k_grid_fft_strided<T, N><<<g, kThreads, SM, st>>>(tw, data, (int64_t)N, (int64_t)N * N, dir);
+    }
+};
+
+#define ROKS_GRID_DISPATCH(N_, CALL)    \
+    switch (N_) {                       \
+        case 16: { constexpr int NN = 16; CALL; } break;   \
+        case 24: { constexpr int NN = 24; CALL; } break;   \
+        case 32: { constexpr int NN = 32; CALL; } break;   \
+        case 48: { constexpr int NN = 48; CALL; } break;   \
+        case 72: { constexpr int NN = 72; CALL; } break;   \
+        case 96: { constexpr int NN = 96; CALL; } break;   \
+        case 120: { constexpr int NN = 120; CALL; } break; \
+        default: break;                 \
+    }
+
+template <typename T>
+void band_z_inv(const Sphere& s, const c2<T>* tw, const c2<T>* psi, int64_t ld, int b0, int nbb, c2<T>* Zc,
+                cudaStream_t st) {
+    ROKS_GRID_DISPATCH(s.N, (BandFft<T, NN>::z_inv(s, tw, psi, ld, b0, nbb, Zc, st)));
+}
+template <typename T>
+void band_y_inv(const Sphere& s, const c2<T>* tw, const c2<T>* Zc, c2<T>* Yp, int nbb, cudaStream_t st) {
+    ROKS_GRID_DISPATCH(s.N, (BandFft<T, NN>::y_inv(s, tw, Zc, Yp, nbb, st)));
+}
+template <typename T>
+void band_x_apply(const Sphere& s, const c2<T>* tw, c2<T>* Yp, const T* Vk, int b0, int nbb, int n_closed,
+                  T scale, cudaStream_t st) {
+    ROKS_GRID_DISPATCH(s.N, (BandFft<T, NN>::x_apply(s, tw, Yp, Vk, b0, nbb, n_closed, scale, st)));
+}
+template <typename T>
+void band_y_fwd(const Sphere& s, const c2<T>* tw, const c2<T>* Yp, c2<T>* Zc, int nbb, cudaStream_t st) {
+    ROKS_GRID_DISPATCH(s.N, (BandFft<T, NN>::y_fwd(s, tw, Yp, Zc, nbb, st)));
+}
+template <typename T>
+void band_z_fwd(const Sphere& s, const c2<T>* tw, const c2<T>* Zc, c2<T>* out, int64_t ldo, const c2<T>* psi,
+                int64_t ldp, const T* g2half, const T* wk, int b0, int nbb, int n_closed, cudaStream_t st) {
+    ROKS_GRID_DISPATCH(s.N, (BandFft<T, NN>::z_fwd(s, tw, Zc, out, ldo, psi, ldp, g2half, wk, b0, nbb, n_closed,
+                                                   st)));
+}
+template <typename T>
+void band_x_density(const Sphere& s, const c2<T>* tw, const c2<T>* Yp, double* rho3, int b0, int nbb,
+                    int n_closed, double scale, cudaStream_t st) {
+    ROKS_GRID_DISPATCH(s.N, (BandFft<T, NN>::x_density(s, tw, Yp, rho3, b0, nbb, n_closed, scale, st)));
+}
+template <typename T>
+void grid_fft3(int N, const c2<T>* tw, c2<T>* data, int dir, cudaStream_t st) {
+    ROKS_GRID_DISPATCH(N, (BandFft<T, NN>::grid3(tw, data, dir, st)));
+}
+
+#define ROKS_INSTANTIATE_FFT(T)                                                                              \
+    template void band_z_inv<T>(const Sphere&, const c2<T>*, const c2<T>*, int64_t, int, int, c2<T>*,           \
+                                cudaStream_t);                                                                   \
+    template void band_y_inv<T>(const Sphere&, const c2<T>*, const c2<T>*, c2<T>*, int, cudaStream_t);          \
+    template void band_x_apply<T>(const Sphere&, const c2<T>*, c2<T>*, const T*, int, int, int, T, cudaStream_t); \
+    template void band_y_fwd<T>(const Sphere&, const c2<T>*, const c2<T>*, c2<T>*, int, cudaStream_t);          \
+    template void band_z_fwd<T>(const Sphere&, const c2<T>*, const c2<T>*, c2<T>*, int64_t, const c2<T>*,        \
+                                int64_t, const T*, const T*, int, int, int, cudaStream_t);                      \
+    template void band_x_density<T>(const Sphere&, const c2<T>*, const c2<T>*, double*, int, int, int, double,  \
+                                    cudaStream_t);                                                               \
+    template void grid_fft3<T>(int, const c2<T>*, c2<T>*, int, cudaStream_t);
+
+}  // namespace roks

@@ -1,0 +1,448 @@
+// k_grid.cu -- pointwise and reduction kernels on the real-space grid and on
+// plane-wave coefficient blocks: model set-up (local wells, projectors),
+// per-band sums, potentials (Hartree, Slater exchange, class potentials),
+// and the pointwise steps of the PCG iteration (TPA preconditioner, axpy).
+#include "roks_grid.cuh"
+
+namespace roks {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int RB = 256;   // threads of the reduction blocks
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = RB / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// ------------------------------------------------------------------ set-up
+// V(G) = -(1/Omega) sum_a d_a (2 pi w^2)^{3/2} exp(-G^2 w^2 / 2) exp(-i G.R_a)
+// on the grid (signed frequencies, N/2 -> +N/2), zero on Nyquist planes.
+__global__ void k_vloc_G(int N, double b, double omega, int natoms, const double* __restrict__ atoms,
+                         double2* __restrict__ out) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t N3 = (int64_t)N * N * N;
+    if (idx >= N3) return;
+    const int z = idx % N, y = (idx / N) % N, x = idx / ((int64_t)N * N);
+    const int fx = signed_freq(x, N), fy = signed_freq(y, N), fz = signed_freq(z, N);
+    double2 v = make_double2(0.0, 0.0);
+    const bool nyq = (N % 2 == 0) && (fx == N / 2 || fy == N / 2 || fz == N / 2);
+    if (!nyq) {
+        const double gx = b * fx, gy = b * fy, gz = b * fz;
+        const double g2 = gx * gx + gy * gy + gz * gz;
+        for (int a = 0; a < natoms; ++a) {
+            const double* at = atoms + 5 * a;   // x, y, z, depth, width
+            const double w = at[4];
+            const double amp = -at[3] * pow(2.0 * kPi * w * w, 1.5) / omega * exp(-0.5 * g2 * w * w);
+            const double ph = -(gx * at[0] + gy * at[1] + gz * at[2]);
+            double sn, cs;
+            sincos(ph, &sn, &cs);
+            v.x += amp * cs;
+            v.y += amp * sn;
+        }
+    }
+    out[idx] = v;
+}
+
+__global__ void k_real_part(int64_t n, const double2* __restrict__ in, double* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[i].x;
+}
+
+// p_i(G) = Omega^{-1/2} N_l (2 pi rc^2)^{3/2} exp(-G^2 rc^2/2) Y(G) exp(-iG.R)
+// proj[i] = {x, y, z, rc, l, m}; G from the Miller vectors.
+template <typename T>
+__global__ void k_projectors(int npw, int nproj, double b, double omega, const int* __restrict__ miller,
+                             const double* __restrict__ proj, c2<T>* __restrict__ P, int64_t ldp) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (g >= npw) return;
+    const double* pr = proj + 6 * i;
+    const double gx = b * miller[3 * g], gy = b * miller[3 * g + 1], gz = b * miller[3 * g + 2];
+    const double g2 = gx * gx + gy * gy + gz * gz;
+    const double rc = pr[3];
+    const int l = int(pr[4]), m = int(pr[5]);
+    double norm = pow(kPi * rc * rc, -0.75);
+    if (l == 1) norm *= sqrt(2.0 / (rc * rc));
+    const double pref = norm * pow(2.0 * kPi * rc * rc, 1.5) / sqrt(omega) * exp(-0.5 * g2 * rc * rc);
+    double sn, cs;
+    sincos(-(gx * pr[0] + gy * pr[1] + gz * pr[2]), &sn, &cs);
+    double re = pref * cs, im = pref * sn;
+    if (l == 1) {
+        // multiply by -i rc^2 G_m
+        const double gm = (m == 0 ? gx : (m == 1 ? gy : gz)) * rc * rc;
+        const double r2 = im * gm, i2 = -re * gm;
+        re = r2;
+        im = i2;
+    }
+    P[(int64_t)i * ldp + g] = mk<T>(T(re), T(im));
+}
+
+template <typename T>
+__global__ void k_init_orbitals(int npw, int nb, const double* __restrict__ u, const double* __restrict__ g2,
+                                c2<T>* __restrict__ psi, int64_t ld) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    if (g >= npw) return;
+    const double d = 1.0 / (1.0 + g2[g]);
+    const double* un = u + ((int64_t)n * npw + g) * 2;
+    psi[(int64_t)n * ld + g] = mk<T>(T(un[0] * d), T(un[1] * d));
+}
+
+template <typename T>
+__global__ void k_to_real(int64_t n, const double* __restrict__ in, T* __restrict__ out, double scale) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = T(in[i] * scale);
+}
+
+// ------------------------------------------------------------------ per-band sums
+// part[(op_out * nb + n) * nsplit + split]; ops:
+//  0: sum 0.5 g2 |x|^2           (kinetic)
+//  1: sum |x|^2, sum g2 |x|^2    (TPA scale)
+//  2: sum Re(conj(x) y)          (inner product)
+//  3: sum |x|^2
+template <typename T, int OP>
+__global__ void __launch_bounds__(RB) k_colred(int npw, int nb, const c2<T>* __restrict__ x, int64_t ldx,
+                                               const c2<T>* __restrict__ y, int64_t ldy,
+                                               const double* __restrict__ g2, int nsplit, double* __restrict__ part) {
+    __shared__ double sh[RB];
+    const int n = blockIdx.x, sp = blockIdx.y;
+    const int per = (npw + nsplit - 1) / nsplit;
+    const int g0 = sp * per, g1 = min(npw, g0 + per);
+    double s0 = 0.0, s1 = 0.0;
+    const c2<T>* xc = x + (int64_t)n * ldx;
+    for (int g = g0 + threadIdx.x; g < g1; g += RB) {
+        const c2<T> a = xc[g];
+        const double ax = double(a.x), ay = double(a.y);
+        if (OP == 0) s0 += 0.5 * g2[g] * (ax * ax + ay * ay);
+        if (OP == 1) {
+            const double m = ax * ax + ay * ay;
+            s0 += m;
+            s1 += g2[g] * m;
+        }
+        if (OP == 2) {
+            const c2<T> bb = y[(int64_t)n * ldy + g];
+            s0 += ax * double(bb.x) + ay * double(bb.y);
+        }
+        if (OP == 3) s0 += ax * ax + ay * ay;
+    }
+    s0 = block_sum(s0, sh);
+    if (OP == 1) s1 = block_sum(s1, sh);
+    if (threadIdx.x == 0) {
+        part[((int64_t)0 * nb + n) * nsplit + sp] = s0;
+        if (OP == 1) part[((int64_t)1 * nb + n) * nsplit + sp] = s1;
+    }
+}
+
+__global__ void k_colred_final(int count, int nsplit, const double* __restrict__ part, double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    double s = 0.0;
+    for (int k = 0; k < nsplit; ++k) s += part[(int64_t)i * nsplit + k];
+    out[i] = s;
+}
+
+template <typename T>
+void column_sums(int op, int npw, int nb, const c2<T>* x, int64_t ldx, const c2<T>* y, int64_t ldy,
+                 const double* g2, double* part, double* out, cudaStream_t st) {
+    constexpr int nsplit = 16;
+    dim3 g(nb, nsplit);
+    switch (op) {
+        case 0: k_colred<T, 0><<<g, RB, 0, st>>>(npw, nb, x, ldx, y, ldy, g2, nsplit, part); break;
+        case 1: k_colred<T, 1><<<g, RB, 0, st>>>(npw, nb, x, ldx, y, ldy, g2, nsplit, part); break;
+        case 2: k_colred<T, 2><<<g, RB, 0, st>>>(npw, nb, x, ldx, y, ldy, g2, nsplit, part); break;
+        default: k_colred<T, 3><<<g, RB, 0, st>>>(npw, nb, x, ldx, y, ldy, g2, nsplit, part); break;
+    }
+    const int count = (op == 1 ? 2 : 1) * nb;
+    k_colred_final<<<(count + 127) / 128, 128, 0, st>>>(count, nsplit, part, out);
+}
+
+// ------------------------------------------------------------------ projector blocks
+// B: nproj x nb (double2, ld nproj).  Block-diagonal D, Q stored by rows:
+// row i holds blk_n[i] entries for projectors blk_off[i] ... (<= kMaxBlk).
+__global__ void k_apply_DQ(int nproj, int nb, const double2* __restrict__ B, const int* __restrict__ blk_off,
+                           const int* __restrict__ blk_n, const double* __restrict__ Drow,
+                           const double* __restrict__ Qrow, const double* __restrict__ wband,
+                           double2* __restrict__ DB, double2* __restrict__ QB) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nproj * nb) return;
+    const int i = idx % nproj, n = idx / nproj;
+    const int o = blk_off[i], cnt = blk_n[i];
+    double dr = 0, di = 0, qr = 0, qi = 0;
+    for (int j = 0; j < cnt; ++j) {
+        const double2 bj = B[(int64_t)n * nproj + o + j];
+        const double d = Drow[i * kMaxBlk + j], q = Qrow[i * kMaxBlk + j];
+        dr += d * bj.x;
+        di += d * bj.y;
+        qr += q * bj.x;
+        qi += q * bj.y;
+    }
+    const double w = wband ? wband[n] : 1.0;
+    if (DB) DB[idx] = make_double2(w * dr, w * di);
+    if (QB) QB[idx] = make_double2(qr, qi);
+}
+
+// NL_n = Re sum_i conj(B_in) (D B)_in  (DB unweighted)
+__global__ void k_band_quadratic(int nproj, int nb, const double2* __restrict__ B,
+                                 const double2* __restrict__ DB, double* __restrict__ out) {
+    __shared__ double sh[RB];
+    const int n = blockIdx.x;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nproj; i += RB) {
+        const double2 a = B[(int64_t)n * nproj + i], d = DB[(int64_t)n * nproj + i];
+        s += a.x * d.x + a.y * d.y;
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) out[n] = s;
+}
+
+// ------------------------------------------------------------------ potentials
+// Channel densities rho^{ch} = sum_k f[k][ch] rho_k; total rho = up M + down M.
+// xc3[k] = sum_ch C[k][ch] v^{ch},  v = -(1-alpha) (6 rho / pi)^{1/3};
+// partial sums of (1-alpha) Slater energies per configuration and of V_loc rho.
+__global__ void __launch_bounds__(RB) k_pot_xc(int64_t N3, const double* __restrict__ rho3,
+                                               const double* __restrict__ vloc, PotCoef cf,
+                                               double2* __restrict__ rho_grid, double* __restrict__ xc3,
+                                               double* __restrict__ part) {
+    __shared__ double sh[RB];
+    double exM = 0, exT = 0, eloc = 0;
+    const double cx = 0.75 * cbrt(6.0 / kPi);
+    for (int64_t p = (int64_t)blockIdx.x * RB + threadIdx.x; p < N3; p += (int64_t)gridDim.x * RB) {
+        const double rk[3] = {rho3[p], rho3[N3 + p], rho3[2 * N3 + p]};
+        double v[4];
+        double rho_tot = 0;
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+            double r = 0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) r += cf.f[k][ch] * rk[k];
+            r = fmax(r, 0.0);
+            const double c = cbrt(r);
+            v[ch] = -cf.xscale * cbrt(6.0 / kPi) * c;
+            const double e = -cf.xscale * cx * c * r;
+            if (ch < 2) { exM += e; rho_tot += r; } else exT += e;
+        }
+        eloc += vloc[p] * rho_tot;
+        rho_grid[p] = make_double2(rho_tot, 0.0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double s = 0;
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch) s += cf.C[k][ch] * v[ch];
+            xc3[k * N3 + p] = s;
+        }
+    }
+    exM = block_sum(exM, sh);
+    exT = block_sum(exT, sh);
+    eloc = block_sum(eloc, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x * 4 + 0] = exM;
+        part[blockIdx.x * 4 + 1] = exT;
+        part[blockIdx.x * 4 + 2] = eloc;
+        part[blockIdx.x * 4 + 3] = 0.0;
+    }
+}
+
+// After the forward transform: rho(G) = grid / N^3; E_H partial
+// sum 4 pi |rho(G)|^2 / G^2; grid <- V_H(G) = 4 pi rho(G) / G^2 (G = 0 -> 0).
+__global__ void __launch_bounds__(RB) k_hartree_G(int N, double b, double2* __restrict__ grid,
+                                                  double* __restrict__ part) {
+    __shared__ double sh[RB];
+    const int64_t N3 = (int64_t)N * N * N;
+    const double inv = 1.0 / double(N3);
+    double eh = 0;
+    for (int64_t p = (int64_t)blockIdx.x * RB + threadIdx.x; p < N3; p += (int64_t)gridDim.x * RB) {
+        const int z = p % N, y = (p / N) % N, x = p / ((int64_t)N * N);
+        const int fx = signed_freq(x, N), fy = signed_freq(y, N), fz = signed_freq(z, N);
+        const double g2 = b * b * double(fx * fx + fy * fy + fz * fz);
+        double2 r = grid[p];
+        r.x *= inv;
+        r.y *= inv;
+        double2 o = make_double2(0.0, 0.0);
+        if (g2 > 0) {
+            const double k = 4.0 * kPi / g2;
+            eh += k * (r.x * r.x + r.y * r.y);
+            o = make_double2(k * r.x, k * r.y);
+        }
+        grid[p] = o;
+    }
+    eh = block_sum(eh, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = eh;
+}
+
+// V^k = w_k (V_loc + V_H) + xc3[k]; partial sums <a|V^c|a>, <b|V^c|b> (rho_a, rho_b).
+template <typename T>
+__global__ void __launch_bounds__(RB) k_pot_class(int64_t N3, const double* __restrict__ vloc,
+                                                  const double2* __restrict__ vh, const double* __restrict__ xc3,
+                                                  const double* __restrict__ rho3, PotCoef cf, T* __restrict__ Vk,
+                                                  double* __restrict__ Vk64, double* __restrict__ part) {
+    __shared__ double sh[RB];
+    double ea = 0, eb = 0;
+    for (int64_t p = (int64_t)blockIdx.x * RB + threadIdx.x; p < N3; p += (int64_t)gridDim.x * RB) {
+        const double v0 = vloc[p] + vh[p].x;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const double v = cf.w[k] * v0 + xc3[k * N3 + p];
+            Vk[k * N3 + p] = T(v);
+            if (Vk64) Vk64[k * N3 + p] = v;
+            if (k == 0) {
+                ea += v * rho3[N3 + p];
+                eb += v * rho3[2 * N3 + p];
+            }
+        }
+    }
+    ea = block_sum(ea, sh);
+    eb = block_sum(eb, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x * 2 + 0] = ea;
+        part[blockIdx.x * 2 + 1] = eb;
+    }
+}
+
+// Sum per-block partials in a fixed order: out[q] = scale[q] * sum_b part[b * nq + q].
+__global__ void k_partials_final(int nblocks, int nq, const double* __restrict__ part, double* __restrict__ out,
+                                 double s0, double s1, double s2, double s3) {
+    const int q = threadIdx.x;
+    if (q >= nq) return;
+    double s = 0;
+    for (int b = 0; b < nblocks; ++b) s += part[b * nq + q];
+    const double sc[4] = {s0, s1, s2, s3};
+    out[q] = s * sc[q];
+}
+
+// ------------------------------------------------------------------ PCG pointwise
+// K g: K(G, n) = -(2 / X_n) tpa(|G|^2 / X_n), X_n = 1.5 sum g2 |g|^2 / sum |g|^2.
+template <typename T>
+__global__ void k_precond(int npw, const c2<T>* __restrict__ gI, int64_t ld, const double* __restrict__ g2,
+                          const double* __restrict__ sums /* [2 nb]: |g|^2, g2 |g|^2 */, int nb,
+                          c2<T>* __restrict__ out, int64_t ldo) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    if (g >= npw) return;
+    const double X = 1.5 * sums[nb + n] / fmax(sums[n], 1e-300);
+    const double x = g2[g] / X;
+    const double num = 27.0 + x * (18.0 + x * (12.0 + 8.0 * x));
+    const double K = -(2.0 / X) * num / (num + 16.0 * x * x * x * x);
+    const c2<T> a = gI[(int64_t)n * ld + g];
+    out[(int64_t)n * ldo + g] = mk<T>(T(K * double(a.x)), T(K * double(a.y)));
+}
+
+// out = x + coef[0] * y  (coef on the device; y may be null -> copy)
+template <typename T>
+__global__ void k_axpy(int npw, const c2<T>* __restrict__ x, int64_t ldx, const c2<T>* __restrict__ y, int64_t ldy,
+                       const double* __restrict__ coef, double csign, c2<T>* __restrict__ out, int64_t ldo) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    if (g >= npw) return;
+    c2<T> a = x[(int64_t)n * ldx + g];
+    if (y) {
+        const T c = T(csign * coef[0]);
+        const c2<T> b = y[(int64_t)n * ldy + g];
+        a.x += c * b.x;
+        a.y += c * b.y;
+    }
+    out[(int64_t)n * ldo + g] = a;
+}
+
+// ------------------------------------------------------------------ host wrappers
+void vloc_setup(int N, double L, int natoms, const double* atoms_dev, double2* grid, double* vloc,
+                const double2* tw64, cudaStream_t st) {
+    const int64_t N3 = (int64_t)N * N * N;
+    const double omega = L * L * L;
+    k_vloc_G<<<(N3 + 255) / 256, 256, 0, st>>>(N, 2.0 * kPi / L, omega, natoms, atoms_dev, grid);
+    grid_fft3<double>(N, tw64, grid, +1, st);
+    k_real_part<<<(N3 + 255) / 256, 256, 0, st>>>(N3, grid, vloc);
+}
+
+template <typename T>
+void projectors_setup(int npw, int nproj, double L, const int* miller_dev, const double* proj_dev, c2<T>* P,
+                      int64_t ldp, cudaStream_t st) {
+    if (nproj == 0) return;
+    dim3 g((npw + 255) / 256, nproj);
+    k_projectors<T><<<g, 256, 0, st>>>(npw, nproj, 2.0 * kPi / L, L * L * L, miller_dev, proj_dev, P, ldp);
+}
+
+template <typename T>
+void init_orbitals(int npw, int nb, const double* u_dev, const double* g2, c2<T>* psi, int64_t ld, cudaStream_t st) {
+    dim3 g((npw + 255) / 256, nb);
+    k_init_orbitals<T><<<g, 256, 0, st>>>(npw, nb, u_dev, g2, psi, ld);
+}
+
+template <typename T>
+void to_real_type(int64_t n, const double* in, T* out, double scale, cudaStream_t st) {
+    k_to_real<T><<<(n + 255) / 256, 256, 0, st>>>(n, in, out, scale);
+}
+
+void apply_DQ(int nproj, int nb, const double2* B, const int* blk_off, const int* blk_n, const double* Drow,
+              const double* Qrow, const double* wband, double2* DB, double2* QB, cudaStream_t st) {
+    if (nproj == 0) return;
+    k_apply_DQ<<<(nproj * nb + 127) / 128, 128, 0, st>>>(nproj, nb, B, blk_off, blk_n, Drow, Qrow, wband, DB, QB);
+}
+
+void band_quadratic(int nproj, int nb, const double2* B, const double2* DB, double* out, cudaStream_t st) {
+    if (nproj == 0) {
+        cudaMemsetAsync(out, 0, sizeof(double) * nb, st);
+        return;
+    }
+    k_band_quadratic<<<nb, RB, 0, st>>>(nproj, nb, B, DB, out);
+}
+
+constexpr int kPotBlocks = 512;
+
+template <typename T>
+void potentials(int N, double L, const double* rho3, const double* vloc, const PotCoef& cf, double2* grid,
+                double* xc3, const double2* tw64, T* Vk, double* Vk64, double* part, double* out6,
+                cudaStream_t st) {
+    // out6: [E_x^M, E_x^T, E_loc, E_H, <a|V^c|a>, <b|V^c|b>]
+    const int64_t N3 = (int64_t)N * N * N;
+    const double dvol = L * L * L / double(N3);
+    k_pot_xc<<<kPotBlocks, RB, 0, st>>>(N3, rho3, vloc, cf, grid, xc3, part);
+    k_partials_final<<<1, 32, 0, st>>>(kPotBlocks, 4, part, out6, dvol, dvol, dvol, 0.0);
+    grid_fft3<double>(N, tw64, grid, -1, st);
+    k_hartree_G<<<kPotBlocks, RB, 0, st>>>(N, 2.0 * kPi / L, grid, part);
+    k_partials_final<<<1, 32, 0, st>>>(kPotBlocks, 1, part, out6 + 3, 0.5 * L * L * L, 0, 0, 0);
+    grid_fft3<double>(N, tw64, grid, +1, st);
+    k_pot_class<T><<<kPotBlocks, RB, 0, st>>>(N3, vloc, grid, xc3, rho3, cf, Vk, Vk64, part);
+    k_partials_final<<<1, 32, 0, st>>>(kPotBlocks, 2, part, out6 + 4, dvol, dvol, 0, 0);
+}
+
+size_t potentials_part_elems() { return (size_t)kPotBlocks * 4; }
+
+template <typename T>
+void precondition(int npw, int nb, const c2<T>* gI, int64_t ld, const double* g2, const double* sums, c2<T>* out,
+                  int64_t ldo, cudaStream_t st) {
+    dim3 g((npw + 255) / 256, nb);
+    k_precond<T><<<g, 256, 0, st>>>(npw, gI, ld, g2, sums, nb, out, ldo);
+}
+
+template <typename T>
+void axpy(int npw, int nb, const c2<T>* x, int64_t ldx, const c2<T>* y, int64_t ldy, const double* coef,
+          double csign, c2<T>* out, int64_t ldo, cudaStream_t st) {
+    dim3 g((npw + 255) / 256, nb);
+    k_axpy<T><<<g, 256, 0, st>>>(npw, x, ldx, y, ldy, coef, csign, out, ldo);
+}
+
+#define ROKS_INSTANTIATE_GRID(T)                                                                               \
+    template void projectors_setup<T>(int, int, double, const int*, const double*, c2<T>*, int64_t,            \
+                                      cudaStream_t);                                                           \
+    template void init_orbitals<T>(int, int, const double*, const double*, c2<T>*, int64_t, cudaStream_t);     \
+    template void to_real_type<T>(int64_t, const double*, T*, double, cudaStream_t);                           \
+    template void column_sums<T>(int, int, int, const c2<T>*, int64_t, const c2<T>*, int64_t, const double*,  \
+                                 double*, double*, cudaStream_t);                                              \
+    template void potentials<T>(int, double, const double*, const double*, const PotCoef&, double2*, double*, \
+                                const double2*, T*, double*, double*, double*, cudaStream_t);                 \
+    template void precondition<T>(int, int, const c2<T>*, int64_t, const double*, const double*, c2<T>*,      \
+                                  int64_t, cudaStream_t);                                                      \
+    template void axpy<T>(int, int, const c2<T>*, int64_t, const c2<T>*, int64_t, const double*, double,      \
+                          c2<T>*, int64_t, cudaStream_t);
+
+ROKS_INSTANTIATE_GRID(float)
+ROKS_INSTANTIATE_GRID(double)
+
+}  // namespace roks

@@ -1,0 +1,243 @@
+// k_pcg.cu -- band-space part of one PCG iteration, kept on the device so
+// that a step needs no host round trip: gamma and the gradient split
+// (Eqs. 11, 12), the ROKS R matrix (Eq. 20), the rotation generator
+// (Eqs. 22-23), the Fletcher-Reeves ratio (Eq. 7) with restarts, the
+// parabolic line search (Eq. 5) and the energy combination (Eq. 1).
+#include <cstddef>
+
+#include "roks_grid.cuh"
+
+namespace roks {
+
+// Gam_mn = gamma_nm = (theta_mn + conj theta_nm)/2; Gin_mn = theta_mn - conj theta_nm;
+// R_mn: same shell theta_mn; shell(m) < shell(n): conj theta_nm - theta_mn;
+// shell(m) > shell(n): theta_mn - conj theta_nm; a-b zeroed when suppressed.
+// A_mn = -(1/2) atan2(2|R|, |d_m - d_n|) sgn(d_m - d_n) R/|R| for m < n,
+// A_nm = -conj A_mn (|R| < 1e-14 -> 0).
+__global__ void k_pcg_rotation(int nb, const double2* __restrict__ Th, const double* __restrict__ d,
+                               const int* __restrict__ shell, int suppress_ab, int ia, int ib,
+                               double2* __restrict__ Gam, double2* __restrict__ Gin, double2* __restrict__ A) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nb * nb) return;
+    const int m = idx % nb, n = idx / nb;
+    const double2 tmn = Th[(int64_t)n * nb + m];
+    const double2 tnm = Th[(int64_t)m * nb + n];
+    Gam[idx] = make_double2(0.5 * (tmn.x + tnm.x), 0.5 * (tmn.y - tnm.y));
+    Gin[idx] = make_double2(tmn.x - tnm.x, tmn.y + tnm.y);
+    double2 a = make_double2(0.0, 0.0);
+    if (m != n) {
+        // the element of the upper triangle that defines this pair
+        const int p = m < n ? m : n, q = m < n ? n : m;
+        const double2 tpq = Th[(int64_t)q * nb + p];
+        const double2 tqp = Th[(int64_t)p * nb + q];
+        double2 r;
+        if (shell[p] == shell[q]) r = tpq;
+        else if (shell[p] < shell[q]) r = make_double2(tqp.x - tpq.x, -tqp.y - tpq.y);
+        else r = make_double2(tpq.x - tqp.x, tpq.y + tqp.y);
+        if (suppress_ab && ((p == ia && q == ib) || (p == ib && q == ia))) r = make_double2(0.0, 0.0);
+        const double ar = sqrt(r.x * r.x + r.y * r.y);
+        if (ar >= 1e-14) {
+            const double dd = d[p] - d[q];
+            const double sg = dd >= 0.0 ? 1.0 : -1.0;
+            const double phi = 0.5 * atan2(2.0 * ar, fabs(dd));
+            const double2 apq = make_double2(-phi * sg * r.x / ar, -phi * sg * r.y / ar);
+            a = (m == p) ? apq : make_double2(-apq.x, apq.y);
+        }
+    }
+    A[idx] = a;
+}
+
+__global__ void k_pcg_coupling(int nb, const double2* __restrict__ Th, int ia, int ib, PcgScalars* sc) {
+    if (threadIdx.x != 0) return;
+    if (ia < 0) {
+        sc->coup_re = sc->coup_im = 0.0;
+        return;
+    }
+    // <a|F^a - F^b|b> = conj(theta_ba) - theta_ab
+    const double2 tab = Th[(int64_t)ib * nb + ia];
+    const double2 tba = Th[(int64_t)ia * nb + ib];
+    sc->coup_re = tba.x - tab.x;
+    sc->coup_im = -tba.y - tab.y;
+}
+
+void pcg_rotation(int nb, const double2* Theta, const double* d, const int* shell, int suppress_ab, int ia, int ib,
+                  double2* Gam, double2* Gin, double2* A, PcgScalars* sc, cudaStream_t st) {
+    k_pcg_rotation<<<(nb * nb + 127) / 128, 128, 0, st>>>(nb, Theta, d, shell, suppress_ab, ia, ib, Gam, Gin, A);
+    k_pcg_coupling<<<1, 32, 0, st>>>(nb, Theta, ia, ib, sc);
+}
+
+// d_m = <m|F^c|m>.  Closed bands: Re theta_mm.  Open bands:
+// w_c (<m|T|m> + <m|V_nl|m>) + <m|V^c|m> with the local part from rho_m.
+__global__ void k_pcg_diag(int nb, int n_closed, const double2* __restrict__ Th, const double* __restrict__ kin_b,
+                           const double* __restrict__ nl_b, const double* __restrict__ open_vc, double wc,
+                           double* __restrict__ d) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= nb) return;
+    if (m < n_closed) d[m] = Th[(int64_t)m * nb + m].x;
+    else d[m] = wc * (kin_b[m] + nl_b[m]) + open_vc[m - n_closed];
+}
+
+void pcg_diag(int nb, int n_closed, const double2* Theta, const double* kin_b, const double* nl_b,
+              const double* open_vc, double wc, double* d, cudaStream_t st) {
+    k_pcg_diag<<<(nb + 127) / 128, 128, 0, st>>>(nb, n_closed, Theta, kin_b, nl_b, open_vc, wc, d);
+}
+
+__global__ void k_pcg_rot_dots(int nb, const double2* __restrict__ A, const double2* __restrict__ Ap,
+                               const double2* __restrict__ Gin, PcgScalars* sc) {
+    __shared__ double s1[256], s2[256];
+    double r1 = 0, r2 = 0;
+    for (int i = threadIdx.x; i < nb * nb; i += blockDim.x) {
+        const double2 g = Gin[i], a = A[i], p = Ap[i];
+        r1 += a.x * g.x + a.y * g.y;
+        r2 += p.x * g.x + p.y * g.y;
+    }
+    s1[threadIdx.x] = r1;
+    s2[threadIdx.x] = r2;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            s1[threadIdx.x] += s1[threadIdx.x + w];
+            s2[threadIdx.x] += s2[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        sc->r1 = s1[0];
+        sc->r2 = s2[0];
+        sc->rot_pg = 0.5 * s1[0];
+    }
+}
+
+void pcg_rot_dots(int nb, const double2* A, const double2* Aprev, const double2* Gin, PcgScalars* sc,
+                  cudaStream_t st) {
+    k_pcg_rot_dots<<<1, 256, 0, st>>>(nb, A, Aprev, Gin, sc);
+}
+
+// beta = pg / pg_prev; dE(beta) = 2 a1 + 2 beta a2 + r1 + beta r2.
+// Not descent with beta != 0: restart (beta = 0).  Still not descent: drop
+// the rotation.
+__global__ void k_pcg_direction(PcgScalars* sc) {
+    if (threadIdx.x != 0) return;
+    sc->pg = sc->pgI + sc->rot_pg;
+    double beta = (sc->has_prev != 0.0) ? sc->pg / sc->pg_prev : 0.0;
+    double dE = 2.0 * sc->a1 + 2.0 * beta * sc->a2 + sc->r1 + beta * sc->r2;
+    double rot = 1.0, restarted = 0.0;
+    if (dE >= 0.0 && beta != 0.0) {
+        beta = 0.0;
+        restarted = 1.0;
+        dE = 2.0 * sc->a1 + sc->r1;
+    }
+    if (dE >= 0.0) {
+        rot = 0.0;
+        restarted = 1.0;
+        dE = 2.0 * sc->a1 + 2.0 * beta * sc->a2;
+    }
+    sc->beta = beta;
+    sc->dE0 = dE;
+    sc->rot = rot;
+    sc->restarted = restarted;
+}
+
+void pcg_direction(PcgScalars* sc, cudaStream_t st) { k_pcg_direction<<<1, 32, 0, st>>>(sc); }
+
+__global__ void k_pcg_total_rotation(int nb, const double2* __restrict__ A, const double2* __restrict__ Ap,
+                                     const PcgScalars* __restrict__ sc, double2* __restrict__ At) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb * nb) return;
+    const double r = sc->rot, b = sc->beta;
+    const double2 a = A[i], p = Ap[i];
+    At[i] = make_double2(r * (a.x + b * p.x), r * (a.y + b * p.y));
+}
+
+void pcg_total_rotation(int nb, const double2* A, const double2* Aprev, PcgScalars* sc, double2* Atot,
+                        cudaStream_t st) {
+    k_pcg_total_rotation<<<(nb * nb + 127) / 128, 128, 0, st>>>(nb, A, Aprev, sc, Atot);
+}
+
+// Parabola E(x) = E0 + dE0 x + c x^2 through E(dt) = Et; c > 0 gives the
+// minimum -dE0/(2c), otherwise the trial step is kept; capped at 3 dt.
+__global__ void k_pcg_line_search(PcgScalars* sc) {
+    if (threadIdx.x != 0) return;
+    const double dt = sc->dt;
+    const double c = (sc->Et - sc->E0 - sc->dE0 * dt) / (dt * dt);
+    double step = c > 0.0 ? -sc->dE0 / (2.0 * c) : dt;
+    step = fmin(step, 3.0 * dt);
+    sc->step = step;
+}
+
+void pcg_line_search(PcgScalars* sc, cudaStream_t st) { k_pcg_line_search<<<1, 32, 0, st>>>(sc); }
+
+// After the step: next trial step, history.
+__global__ void k_pcg_finish(PcgScalars* sc) {
+    if (threadIdx.x != 0) return;
+    sc->dt = fmin(fmax(sc->step, 0.05), 2.0);
+    sc->pg_prev = sc->pg;
+    sc->has_prev = 1.0;
+}
+
+__global__ void k_set_cur(PcgScalars* sc, int field) {
+    if (threadIdx.x == 0) sc->cur = reinterpret_cast<double*>(sc)[field];
+}
+
+void pcg_set_cur(PcgScalars* sc, int field, cudaStream_t st) { k_set_cur<<<1, 32, 0, st>>>(sc, field); }
+
+void pcg_finish(PcgScalars* sc, cudaStream_t st) { k_pcg_finish<<<1, 32, 0, st>>>(sc); }
+
+// E[0..10] = kin, loc, nl, H, xM, xT, hfM, hfT, M, T, total
+__global__ void k_energy_combine(const double* __restrict__ kin_b, const double* __restrict__ nl_b, int nb,
+                                 const double* __restrict__ wband, const double* __restrict__ out6, double cM,
+                                 double cT, double alpha, const double* __restrict__ hf2, double* __restrict__ E) {
+    if (threadIdx.x != 0) return;
+    double kin = 0, nl = 0;
+    for (int n = 0; n < nb; ++n) {
+        kin += wband[n] * kin_b[n];
+        nl += wband[n] * nl_b[n];
+    }
+    const double loc = out6[2], H = out6[3], xM = out6[0], xT = out6[1];
+    const double hfM = hf2 ? hf2[0] : 0.0, hfT = hf2 ? hf2[1] : 0.0;
+    const double one = kin + loc + nl + H;
+    const double M = one + xM + alpha * hfM;
+    const double T = one + xT + alpha * hfT;
+    E[0] = kin; E[1] = loc; E[2] = nl; E[3] = H; E[4] = xM; E[5] = xT; E[6] = hfM; E[7] = hfT;
+    E[8] = M; E[9] = T; E[10] = cM * M + cT * T;
+}
+
+void energy_combine(const double* kin_b, const double* nl_b, int nb, const double* wband, const double* out6,
+                    double cM, double cT, double alpha, const double* hf2, double* E, cudaStream_t st) {
+    k_energy_combine<<<1, 32, 0, st>>>(kin_b, nl_b, nb, wband, out6, cM, cT, alpha, hf2, E);
+}
+
+__global__ void k_take_energy(const double* __restrict__ E, PcgScalars* sc, int field) {
+    if (threadIdx.x == 0) reinterpret_cast<double*>(sc)[field] = E[10];
+}
+
+void pcg_take_energy(const double* E, PcgScalars* sc, int field, cudaStream_t st) {
+    k_take_energy<<<1, 32, 0, st>>>(E, sc, field);
+}
+
+__global__ void k_hermitize(int n, double2* O) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * n) return;
+    const int m = idx % n, c = idx / n;
+    if (m > c) return;
+    const double2 a = O[(int64_t)c * n + m], b = O[(int64_t)m * n + c];
+    const double2 h = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+    O[(int64_t)c * n + m] = h;
+    O[(int64_t)m * n + c] = make_double2(h.x, -h.y);
+}
+
+void hermitize(int n, double2* O, cudaStream_t st) { k_hermitize<<<(n * n + 127) / 128, 128, 0, st>>>(n, O); }
+
+// dst = scale * sum_i v[i]  (fixed order)
+__global__ void k_sum_to(const double* __restrict__ v, int n, double* dst, double scale) {
+    if (threadIdx.x != 0) return;
+    double s = 0;
+    for (int i = 0; i < n; ++i) s += v[i];
+    dst[0] = scale * s;
+}
+
+void sum_to(const double* v, int n, double* dst, double scale, cudaStream_t st) {
+    k_sum_to<<<1, 32, 0, st>>>(v, n, dst, scale);
+}
+
+}  // namespace roks

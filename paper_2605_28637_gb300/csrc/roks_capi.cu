@@ -1,0 +1,895 @@
+// roks_capi.cu -- the C ABI (include/roks.h): set-up of the plane-wave model
+// on one GPU and the host-side ordering of the kernels of each entry point.
+// All arithmetic of the method runs in the kernels; the host only validates
+// arguments, builds integer index maps and launches.
+#include <cmath>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/roks.h"
+#include "roks_grid.cuh"
+
+using namespace roks;
+
+namespace roks {
+void sum_to(const double* v, int n, double* dst, double scale, cudaStream_t st);
+void pcg_finish(PcgScalars* sc, cudaStream_t st);
+}
+
+#define SC_FIELD(f) int(offsetof(PcgScalars, f) / sizeof(double))
+
+struct roks_ctx {
+    std::string err;
+    cudaStream_t st = nullptr;
+    int prec = ROKS_FP64;
+    // model
+    double L = 0, omega = 0, ecut = 0, alpha = 0, e_tol = 1e-6;
+    int N = 0, npw = 0, ld_min = 0, nmax = 0, M = 0, ncol = 0, np = 0;
+    int nb = 0, nc = 0, mode = 1, nproj = 0, natoms = 0, suppress_ab = 0;
+    double cM = 0, cT = 0;
+    PotCoef cf{};
+    std::vector<int32_t> miller;
+    // device: index maps and model tables
+    int *d_col_start = nullptr, *d_col_kmax = nullptr, *d_plane_col0 = nullptr, *d_plane_jmax = nullptr;
+    int* d_miller = nullptr;
+    int* d_shell = nullptr;
+    double* d_g2 = nullptr;        // |G|^2 (FP64)
+    void* d_g2half = nullptr;      // |G|^2 / 2 (T)
+    void* d_wk = nullptr;          // class weights (T)
+    double* d_wband = nullptr;     // weight per band (FP64)
+    double* d_vloc = nullptr;      // V_loc(r)
+    void* d_P = nullptr;           // projectors npw x nproj (T complex, ld = ld_min)
+    int *d_blk_off = nullptr, *d_blk_n = nullptr;
+    double *d_Drow = nullptr, *d_Qrow = nullptr;
+    void* d_tw = nullptr;          // twiddles (T)
+    double2* d_tw64 = nullptr;     // twiddles (FP64)
+    // band transforms
+    void *d_Zc = nullptr, *d_Yp = nullptr;
+    // grid
+    double* d_rho3 = nullptr;
+    double* d_xc3 = nullptr;
+    double2* d_grid = nullptr;
+    void* d_Vk = nullptr;
+    double* d_part = nullptr;
+    double* d_out6 = nullptr;
+    double* d_E = nullptr;
+    // band blocks (T complex, ld_min x nb)
+    void *W_F = nullptr, *W_S = nullptr, *W_G = nullptr, *W_gI = nullptr, *W_K = nullptr, *W_u = nullptr,
+         *W_v = nullptr, *W_s = nullptr, *W_sprev = nullptr, *W_Y = nullptr, *W_Y2 = nullptr;
+    // band-space FP64
+    double2 *d_Th = nullptr, *d_Gam = nullptr, *d_Gin = nullptr, *d_A = nullptr, *d_Aprev = nullptr,
+            *d_Atot = nullptr, *d_U = nullptr, *d_O = nullptr, *d_L = nullptr, *d_LinvH = nullptr,
+            *d_Msm = nullptr, *d_e1 = nullptr, *d_e2 = nullptr, *d_e3 = nullptr;
+    double2 *d_B = nullptr, *d_DB = nullptr, *d_QB = nullptr, *d_B2 = nullptr;
+    double2* d_gemm_work = nullptr;
+    size_t gemm_work_elems = 0;
+    double *d_kin_b = nullptr, *d_nl_b = nullptr, *d_colpart = nullptr, *d_colout = nullptr, *d_d = nullptr;
+    double* d_expm_info = nullptr;
+    int* d_flag = nullptr;
+    PcgScalars* d_sc = nullptr;
+    // state
+    const void* cache_psi = nullptr;   // potentials valid for this buffer (pcg chain)
+    bool pot_valid = false;
+    int n_small = 0;
+    std::vector<void*> allocs;
+    // kernel-family timing (roks_profile_enable / roks_profile_read)
+    struct Rec {
+        int fam;
+        cudaEvent_t a, b;
+    };
+    bool prof_on = false;
+    std::vector<std::string> prof_names;
+    std::vector<Rec> prof_recs;
+    std::vector<cudaEvent_t> prof_pool;
+};
+
+namespace {
+
+roks_status fail(roks_ctx* c, roks_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+#define CK(call)                                                                      \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess)                                                        \
+            return fail(ctx, ROKS_ECUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename P>
+cudaError_t dalloc(roks_ctx* ctx, P** p, size_t bytes) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes > 0 ? bytes : 16);
+    if (e == cudaSuccess) {
+        ctx->allocs.push_back(q);
+        cudaMemsetAsync(q, 0, bytes > 0 ? bytes : 16, ctx->st);
+    }
+    *p = static_cast<P*>(q);
+    return e;
+}
+
+cudaEvent_t prof_event(roks_ctx* c) {
+    if (!c->prof_pool.empty()) {
+        cudaEvent_t e = c->prof_pool.back();
+        c->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Records CUDA events around the launches issued while it is alive.
+struct ProfScope {
+    roks_ctx* c;
+    int fam = -1;
+    cudaEvent_t a = nullptr;
+    ProfScope(roks_ctx* ctx, const char* name) : c(ctx) {
+        if (!c->prof_on) return;
+        for (size_t i = 0; i < c->prof_names.size(); ++i)
+            if (c->prof_names[i] == name) fam = (int)i;
+        if (fam < 0) {
+            fam = (int)c->prof_names.size();
+            c->prof_names.push_back(name);
+        }
+        a = prof_event(c);
+        cudaEventRecord(a, c->st);
+    }
+    ~ProfScope() {
+        if (fam < 0) return;
+        cudaEvent_t b = prof_event(c);
+        cudaEventRecord(b, c->st);
+        c->prof_recs.push_back({fam, a, b});
+    }
+};
+#define PROF_CAT2(a, b) a##b
+#define PROF_CAT(a, b) PROF_CAT2(a, b)
+#define PROF(name) ProfScope PROF_CAT(prof_scope_, __LINE__)(ctx, name)
+
+Sphere sphere(const roks_ctx* c) {
+    Sphere s;
+    s.N = c->N;
+    s.nmax = c->nmax;
+    s.np = c->np;
+    s.ncol = c->ncol;
+    s.col_start = c->d_col_start;
+    s.col_kmax = c->d_col_kmax;
+    s.plane_col0 = c->d_plane_col0;
+    s.plane_jmax = c->d_plane_jmax;
+    return s;
+}
+
+bool grid_supported(int n) {
+    for (int g : kGrids)
+        if (g == n) return true;
+    return false;
+}
+
+int isqrt_floor(long v) {
+    long r = (long)std::sqrt((double)v);
+    while (r * r > v) --r;
+    while ((r + 1) * (r + 1) <= v) ++r;
+    return (int)r;
+}
+
+// ------------------------------------------------------------------ typed implementation
+template <typename T>
+struct Impl {
+    using V = c2<T>;
+    static V* cv(void* p) { return static_cast<V*>(p); }
+    static const V* ccv(const void* p) { return static_cast<const V*>(p); }
+
+    // rho3, kin_b, nl_b of psi.  Bgiven: projector coefficients of psi if known.
+    static roks_status density(roks_ctx* ctx, const void* psi, int64_t ld, const double2* Bgiven) {
+        const Sphere s = sphere(ctx);
+        cudaStream_t st = ctx->st;
+        const V* p = ccv(psi);
+        { PROF("fft_z_inv"); band_z_inv<T>(s, ccv(ctx->d_tw), p, ld, 0, ctx->nb, cv(ctx->d_Zc), st); }
+        { PROF("fft_y_inv"); band_y_inv<T>(s, ccv(ctx->d_tw), cv(ctx->d_Zc), cv(ctx->d_Yp), ctx->nb, st); }
+        CK(cudaMemsetAsync(ctx->d_rho3, 0, sizeof(double) * 3 * (size_t)ctx->N * ctx->N * ctx->N, st));
+        {
+            PROF("fft_x_density");
+            band_x_density<T>(s, ccv(ctx->d_tw), cv(ctx->d_Yp), ctx->d_rho3, 0, ctx->nb, ctx->nc, 1.0 / ctx->omega, st);
+        }
+        column_sums<T>(0, ctx->npw, ctx->nb, p, ld, nullptr, 0, ctx->d_g2, ctx->d_colpart, ctx->d_kin_b, st);
+        const double2* B = Bgiven;
+        if (!B) {
+            PROF("proj_PhPsi");
+            gemm_cn<T>(ctx->nproj, ctx->nb, ctx->npw, ccv(ctx->d_P), ctx->ld_min, p, ld, ctx->d_B, ctx->nproj,
+                       ctx->d_gemm_work, ctx->gemm_work_elems, st);
+            B = ctx->d_B;
+        }
+        apply_DQ(ctx->nproj, ctx->nb, B, ctx->d_blk_off, ctx->d_blk_n, ctx->d_Drow, ctx->d_Qrow, nullptr,
+                 ctx->d_DB, nullptr, st);
+        band_quadratic(ctx->nproj, ctx->nb, B, ctx->d_DB, ctx->d_nl_b, st);
+        CK(cudaGetLastError());
+        return ROKS_OK;
+    }
+
+    static roks_status potential(roks_ctx* ctx) {
+        cudaStream_t st = ctx->st;
+        PROF("potential");
+        potentials<T>(ctx->N, ctx->L, ctx->d_rho3, ctx->d_vloc, ctx->cf, ctx->d_grid, ctx->d_xc3, ctx->d_tw64,
+                      static_cast<T*>(ctx->d_Vk), nullptr, ctx->d_part, ctx->d_out6, st);
+        energy_combine(ctx->d_kin_b, ctx->d_nl_b, ctx->nb, ctx->d_wband, ctx->d_out6, ctx->cM, ctx->cT,
+                       ctx->alpha, nullptr, ctx->d_E, st);
+        CK(cudaGetLastError());
+        return ROKS_OK;
+    }
+
+    // F = F^{k(n)}|n>, S = S|n> (S optional), with the current potentials.
+    static roks_status apply(roks_ctx* ctx, const void* psi, int64_t ld, void* F, int64_t ldf, void* S,
+                             int64_t lds) {
+        const Sphere s = sphere(ctx);
+        cudaStream_t st = ctx->st;
+        const V* p = ccv(psi);
+        const int N = ctx->N;
+        { PROF("fft_z_inv"); band_z_inv<T>(s, ccv(ctx->d_tw), p, ld, 0, ctx->nb, cv(ctx->d_Zc), st); }
+        { PROF("fft_y_inv"); band_y_inv<T>(s, ccv(ctx->d_tw), cv(ctx->d_Zc), cv(ctx->d_Yp), ctx->nb, st); }
+        {
+            PROF("fft_x_apply");
+            band_x_apply<T>(s, ccv(ctx->d_tw), cv(ctx->d_Yp), static_cast<const T*>(ctx->d_Vk), 0, ctx->nb, ctx->nc,
+                            T(1.0 / (double(N) * N * N)), st);
+        }
+        { PROF("fft_y_fwd"); band_y_fwd<T>(s, ccv(ctx->d_tw), cv(ctx->d_Yp), cv(ctx->d_Zc), ctx->nb, st); }
+        {
+            PROF("fft_z_fwd");
+            band_z_fwd<T>(s, ccv(ctx->d_tw), cv(ctx->d_Zc), cv(F), ldf, p, ld, static_cast<const T*>(ctx->d_g2half),
+                          static_cast<const T*>(ctx->d_wk), 0, ctx->nb, ctx->nc, st);
+        }
+        if (ctx->nproj > 0) {
+            {
+                PROF("proj_PhPsi");
+                gemm_cn<T>(ctx->nproj, ctx->nb, ctx->npw, ccv(ctx->d_P), ctx->ld_min, p, ld, ctx->d_B, ctx->nproj,
+                           ctx->d_gemm_work, ctx->gemm_work_elems, st);
+            }
+            apply_DQ(ctx->nproj, ctx->nb, ctx->d_B, ctx->d_blk_off, ctx->d_blk_n, ctx->d_Drow, ctx->d_Qrow,
+                     ctx->d_wband, ctx->d_DB, ctx->d_QB, st);
+            PROF("proj_PX");
+            gemm_nn<T>(ctx->npw, ctx->nb, ctx->nproj, ccv(ctx->d_P), ctx->ld_min, ctx->d_DB, ctx->nproj, cv(F), ldf,
+                       1.0, 1.0, st);
+        }
+        if (S) {
+            CK(cudaMemcpy2DAsync(S, lds * sizeof(V), psi, ld * sizeof(V), ctx->npw * sizeof(V), ctx->nb,
+                                 cudaMemcpyDeviceToDevice, st));
+            if (ctx->nproj > 0) {
+                PROF("proj_PX");
+                gemm_nn<T>(ctx->npw, ctx->nb, ctx->nproj, ccv(ctx->d_P), ctx->ld_min, ctx->d_QB, ctx->nproj, cv(S),
+                           lds, 1.0, 1.0, st);
+            }
+        }
+        CK(cudaGetLastError());
+        return ROKS_OK;
+    }
+
+    // out = in L^{-H} with in^H S in = L L^H; Bout = P^H out.
+    static roks_status orth(roks_ctx* ctx, const void* in, int64_t ldi, void* out, int64_t ldo, double2* Bout) {
+        cudaStream_t st = ctx->st;
+        const int nb = ctx->nb;
+        PROF("orthonormalize");
+        gemm_cn<T>(nb, nb, ctx->npw, ccv(in), ldi, ccv(in), ldi, ctx->d_O, nb, ctx->d_gemm_work,
+                   ctx->gemm_work_elems, st);
+        if (ctx->nproj > 0) {
+            gemm_cn<T>(ctx->nproj, nb, ctx->npw, ccv(ctx->d_P), ctx->ld_min, ccv(in), ldi, ctx->d_B2, ctx->nproj,
+                       ctx->d_gemm_work, ctx->gemm_work_elems, st);
+            apply_DQ(ctx->nproj, nb, ctx->d_B2, ctx->d_blk_off, ctx->d_blk_n, ctx->d_Drow, ctx->d_Qrow, nullptr,
+                     nullptr, ctx->d_QB, st);
+            small_gemm(nb, nb, ctx->nproj, ctx->d_B2, ctx->nproj, true, ctx->d_QB, ctx->nproj, false, ctx->d_O, nb,
+                       1.0, 1.0, st);
+        }
+        hermitize(nb, ctx->d_O, st);
+        cholesky_inverse(nb, ctx->d_O, ctx->d_L, ctx->d_LinvH, ctx->d_flag, st);
+        gemm_nn<T>(ctx->npw, nb, nb, ccv(in), ldi, ctx->d_LinvH, nb, cv(out), ldo, 1.0, 0.0, st);
+        if (Bout && ctx->nproj > 0)
+            small_gemm(ctx->nproj, nb, nb, ctx->d_B2, ctx->nproj, false, ctx->d_LinvH, nb, false, Bout, ctx->nproj,
+                       1.0, 0.0, st);
+        CK(cudaGetLastError());
+        return ROKS_OK;
+    }
+
+    static roks_status check_flag(roks_ctx* ctx) {
+        int flag = 0;
+        CK(cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        if (flag) {
+            CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->st));
+            return fail(ctx, ROKS_ENOTPOSDEF,
+                        "overlap matrix not positive definite at band " + std::to_string(flag - 1));
+        }
+        return ROKS_OK;
+    }
+
+    // s-projection: out = x - Psi ((S Psi)^H x)
+    static void project(roks_ctx* ctx, const void* psi, int64_t ld, const void* x, void* out) {
+        cudaStream_t st = ctx->st;
+        const int nb = ctx->nb;
+        const int64_t l = ctx->ld_min;
+        PROF("subspace_project");
+        gemm_cn<T>(nb, nb, ctx->npw, ccv(ctx->W_S), l, ccv(x), l, ctx->d_Msm, nb, ctx->d_gemm_work,
+                   ctx->gemm_work_elems, st);
+        if (out != x)
+            cudaMemcpyAsync(out, x, sizeof(V) * l * nb, cudaMemcpyDeviceToDevice, st);
+        gemm_nn<T>(ctx->npw, nb, nb, ccv(psi), ld, ctx->d_Msm, nb, cv(out), l, -1.0, 1.0, st);
+    }
+
+    // dst field = sum_n Re <x_n|y_n>
+    static void dot_to(roks_ctx* ctx, const void* x, const void* y, int field) {
+        const int64_t l = ctx->ld_min;
+        column_sums<T>(2, ctx->npw, ctx->nb, ccv(x), l, ccv(y), l, ctx->d_g2, ctx->d_colpart, ctx->d_colout, ctx->st);
+        sum_to(ctx->d_colout, ctx->nb, reinterpret_cast<double*>(ctx->d_sc) + field, 1.0, ctx->st);
+    }
+
+    // out = orth((psi + step s) exp(step Atot)); energies of out in d_E.
+    static roks_status move(roks_ctx* ctx, const void* psi, int64_t ld, int step_field, void* out, int64_t ldo) {
+        cudaStream_t st = ctx->st;
+        const int nb = ctx->nb;
+        const int64_t l = ctx->ld_min;
+        double* scd = reinterpret_cast<double*>(ctx->d_sc);
+        {
+            PROF("rotate");
+            axpy<T>(ctx->npw, nb, ccv(psi), ld, ccv(ctx->W_s), l, scd + step_field, 1.0, cv(ctx->W_Y), l, st);
+            expm_scaled(nb, ctx->d_Atot, scd + step_field, ctx->d_U, ctx->d_e1, ctx->d_e2, ctx->d_e3,
+                        ctx->d_expm_info, st);
+            gemm_nn<T>(ctx->npw, nb, nb, ccv(ctx->W_Y), l, ctx->d_U, nb, cv(ctx->W_Y2), l, 1.0, 0.0, st);
+        }
+        roks_status r = orth(ctx, ctx->W_Y2, l, out, ldo, ctx->d_B);
+        if (r != ROKS_OK) return r;
+        r = density(ctx, out, ldo, ctx->nproj > 0 ? ctx->d_B : nullptr);
+        if (r != ROKS_OK) return r;
+        return potential(ctx);
+    }
+
+    static roks_status pcg_step(roks_ctx* ctx, void* psi, int64_t ld, roks_step_info* info) {
+        cudaStream_t st = ctx->st;
+        const int nb = ctx->nb, npw = ctx->npw;
+        const int64_t l = ctx->ld_min;
+        roks_status r;
+        if (!(ctx->pot_valid && ctx->cache_psi == psi)) {
+            r = density(ctx, psi, ld, nullptr);
+            if (r != ROKS_OK) return r;
+            r = potential(ctx);
+            if (r != ROKS_OK) return r;
+        }
+        pcg_take_energy(ctx->d_E, ctx->d_sc, SC_FIELD(E0), st);
+        // F Psi, S Psi, theta, d
+        r = apply(ctx, psi, ld, ctx->W_F, l, ctx->W_S, l);
+        if (r != ROKS_OK) return r;
+        {
+            PROF("subspace_theta");
+            gemm_cn<T>(nb, nb, npw, ccv(psi), ld, ccv(ctx->W_F), l, ctx->d_Th, nb, ctx->d_gemm_work,
+                       ctx->gemm_work_elems, st);
+        }
+        pcg_diag(nb, ctx->nc, ctx->d_Th, ctx->d_kin_b, ctx->d_nl_b, ctx->d_out6 + 4, ctx->cf.w[0], ctx->d_d, st);
+        const int ia = (ctx->mode == ROKS_MODE_SINGLET) ? ctx->nc : -1;
+        const int ib = (ctx->mode == ROKS_MODE_SINGLET) ? ctx->nc + 1 : -1;
+        pcg_rotation(nb, ctx->d_Th, ctx->d_d, ctx->d_shell, ctx->suppress_ab && ctx->mode == ROKS_MODE_SINGLET, ia,
+                     ib, ctx->d_Gam, ctx->d_Gin, ctx->d_A, ctx->d_sc, st);
+        // G = F - S Gam ; gI = F - S theta
+        {
+        PROF("gradient_precond");
+        CK(cudaMemcpyAsync(ctx->W_G, ctx->W_F, sizeof(V) * l * nb, cudaMemcpyDeviceToDevice, st));
+        gemm_nn<T>(npw, nb, nb, ccv(ctx->W_S), l, ctx->d_Gam, nb, cv(ctx->W_G), l, -1.0, 1.0, st);
+        CK(cudaMemcpyAsync(ctx->W_gI, ctx->W_F, sizeof(V) * l * nb, cudaMemcpyDeviceToDevice, st));
+        gemm_nn<T>(npw, nb, nb, ccv(ctx->W_S), l, ctx->d_Th, nb, cv(ctx->W_gI), l, -1.0, 1.0, st);
+        column_sums<T>(3, npw, nb, ccv(ctx->W_G), l, nullptr, 0, ctx->d_g2, ctx->d_colpart, ctx->d_colout, st);
+        sum_to(ctx->d_colout, nb, reinterpret_cast<double*>(ctx->d_sc) + SC_FIELD(gnorm2), 1.0, st);
+        // p_I = K g_I - Psi (S Psi)^H K g_I
+        column_sums<T>(1, npw, nb, ccv(ctx->W_gI), l, nullptr, 0, ctx->d_g2, ctx->d_colpart, ctx->d_colout, st);
+        precondition<T>(npw, nb, ccv(ctx->W_gI), l, ctx->d_g2, ctx->d_colout, cv(ctx->W_K), l, st);
+        }
+        project(ctx, psi, ld, ctx->W_K, ctx->W_K);
+        dot_to(ctx, ctx->W_K, ctx->W_gI, SC_FIELD(pgI));
+        pcg_rot_dots(nb, ctx->d_A, ctx->d_Aprev, ctx->d_Gin, ctx->d_sc, st);
+        // u = proj(p_I), v = proj(s_prev)
+        project(ctx, psi, ld, ctx->W_K, ctx->W_u);
+        project(ctx, psi, ld, ctx->W_sprev, ctx->W_v);
+        dot_to(ctx, ctx->W_u, ctx->W_G, SC_FIELD(a1));
+        dot_to(ctx, ctx->W_v, ctx->W_G, SC_FIELD(a2));
+        pcg_direction(ctx->d_sc, st);
+        // s = u + beta v, A_tot = rot (A + beta A_prev)
+        axpy<T>(npw, nb, ccv(ctx->W_u), l, ccv(ctx->W_v), l, reinterpret_cast<double*>(ctx->d_sc) + SC_FIELD(beta),
+                1.0, cv(ctx->W_s), l, st);
+        pcg_total_rotation(nb, ctx->d_A, ctx->d_Aprev, ctx->d_sc, ctx->d_Atot, st);
+        // trial point
+        r = move(ctx, psi, ld, SC_FIELD(dt), ctx->W_F, l);
+        if (r != ROKS_OK) return r;
+        pcg_take_energy(ctx->d_E, ctx->d_sc, SC_FIELD(Et), st);
+        pcg_line_search(ctx->d_sc, st);
+        // accepted point (written to W_F, then copied over psi)
+        r = move(ctx, psi, ld, SC_FIELD(step), ctx->W_F, l);
+        if (r != ROKS_OK) return r;
+        pcg_take_energy(ctx->d_E, ctx->d_sc, SC_FIELD(Enew), st);
+        CK(cudaMemcpy2DAsync(psi, ld * sizeof(V), ctx->W_F, l * sizeof(V), npw * sizeof(V), nb,
+                             cudaMemcpyDeviceToDevice, st));
+        // history
+        CK(cudaMemcpyAsync(ctx->W_sprev, ctx->W_s, sizeof(V) * l * nb, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(ctx->d_Aprev, ctx->d_A, sizeof(double2) * nb * nb, cudaMemcpyDeviceToDevice, st));
+        pcg_finish(ctx->d_sc, st);
+        CK(cudaGetLastError());
+        r = check_flag(ctx);
+        if (r != ROKS_OK) return r;
+        ctx->cache_psi = psi;
+        ctx->pot_valid = true;
+        PcgScalars h;
+        CK(cudaMemcpyAsync(&h, ctx->d_sc, sizeof(h), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (info) {
+            info->E = h.E0;
+            info->E_new = h.Enew;
+            info->step = h.step;
+            info->grad_norm = std::sqrt(h.gnorm2);
+            info->coupling_re = h.coup_re;
+            info->coupling_im = h.coup_im;
+            info->beta = h.beta;
+            info->dE0 = h.dE0;
+            info->restarted = h.restarted != 0.0;
+        }
+        if (!std::isfinite(h.Enew) || !std::isfinite(h.gnorm2))
+            return fail(ctx, ROKS_EDIVERGED, "non-finite energy or gradient");
+        return ROKS_OK;
+    }
+};
+
+void reset_history(roks_ctx* ctx) {
+    PcgScalars h;
+    std::memset(&h, 0, sizeof(h));
+    h.dt = 0.3;
+    h.neg_one = -1.0;
+    cudaMemcpyAsync(ctx->d_sc, &h, sizeof(h), cudaMemcpyHostToDevice, ctx->st);
+    const size_t bytes = (ctx->prec == ROKS_FP64 ? sizeof(double2) : sizeof(float2)) * (size_t)ctx->ld_min * ctx->nb;
+    cudaMemsetAsync(ctx->W_sprev, 0, bytes, ctx->st);
+    cudaMemsetAsync(ctx->d_Aprev, 0, sizeof(double2) * ctx->nb * ctx->nb, ctx->st);
+    ctx->pot_valid = false;
+    ctx->cache_psi = nullptr;
+    ctx->n_small = 0;
+    cudaStreamSynchronize(ctx->st);
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const roks_atom* atoms, int nspecies,
+                       const roks_species* species, const roks_occ* occ, const roks_options* opt,
+                       void* cuda_stream, roks_ctx** out) {
+    if (!out) return ROKS_EINVAL;
+    *out = nullptr;
+    if (!cell || !occ || !opt || (natoms > 0 && !atoms) || (nspecies > 0 && !species) || natoms < 0 ||
+        nspecies < 0)
+        return ROKS_EINVAL;
+    if (!(cell->L > 0) || !(ecut > 0) || !grid_supported(cell->grid)) return ROKS_EINVAL;
+    if (occ->n_closed < 0 || occ->mode < 0 || occ->mode > 2) return ROKS_EINVAL;
+    if (opt->precision != ROKS_FP64 && opt->precision != ROKS_MIXED) return ROKS_EINVAL;
+    if (opt->alpha != 0.0) return ROKS_EINVAL;   // exact exchange is not built yet
+    roks_ctx* ctx = new (std::nothrow) roks_ctx();
+    if (!ctx) return ROKS_ENOMEM;
+    ctx->st = static_cast<cudaStream_t>(cuda_stream);
+    ctx->prec = opt->precision;
+    ctx->L = cell->L;
+    ctx->N = cell->grid;
+    ctx->omega = cell->L * cell->L * cell->L;
+    ctx->ecut = ecut;
+    ctx->alpha = opt->alpha;
+    ctx->e_tol = opt->e_tol > 0 ? opt->e_tol : 1e-6;
+    ctx->suppress_ab = opt->suppress_ab;
+    ctx->mode = occ->mode;
+    ctx->nc = occ->n_closed;
+    ctx->nb = occ->n_closed + (occ->mode == ROKS_MODE_GS ? 0 : 2);
+    ctx->natoms = natoms;
+    auto bail = [&](roks_status s, const std::string& m) {
+        roks_destroy(ctx);
+        (void)m;
+        return s;
+    };
+    if (ctx->nb <= 0) return bail(ROKS_EINVAL, "no bands");
+    // -------- basis: i^2 + j^2 + k^2 <= floor(2 ecut (L / 2 pi)^2)
+    const double q = cell->L / (2.0 * M_PI);
+    const double Mq = std::floor(2.0 * ecut * q * q);
+    if (Mq > 1e7) return bail(ROKS_EINVAL, "cut-off too large");
+    ctx->M = (int)Mq;
+    ctx->nmax = isqrt_floor(ctx->M);
+    const int n = ctx->nmax, N = ctx->N;
+    if (N < 2 * n + 1) return bail(ROKS_EINVAL, "grid smaller than 2 n + 1");
+    std::vector<int> col_start, col_kmax, plane_col0, plane_jmax;
+    for (int i = -n; i <= n; ++i) {
+        const int ji = isqrt_floor(ctx->M - i * i);
+        plane_col0.push_back((int)col_kmax.size());
+        plane_jmax.push_back(ji);
+        for (int j = -ji; j <= ji; ++j) {
+            const int kj = isqrt_floor(ctx->M - i * i - j * j);
+            col_start.push_back((int)(ctx->miller.size() / 3));
+            col_kmax.push_back(kj);
+            for (int k = -kj; k <= kj; ++k) {
+                ctx->miller.push_back(i);
+                ctx->miller.push_back(j);
+                ctx->miller.push_back(k);
+            }
+        }
+    }
+    ctx->npw = (int)(ctx->miller.size() / 3);
+    ctx->ld_min = (ctx->npw + 31) / 32 * 32;
+    ctx->ncol = (int)col_kmax.size();
+    ctx->np = 2 * n + 1;
+    if (ctx->nb > ctx->npw) return bail(ROKS_EINVAL, "more bands than plane waves");
+    // -------- occupations (Eqs. 8, 14): f table and c_L
+    const double ftab[3][4] = {{1, 1, 1, 1}, {1, 0, 1, 0}, {0, 1, 1, 0}};
+    ctx->cM = occ->mode == 0 ? 1.0 : (occ->mode == 1 ? 2.0 : 0.0);
+    ctx->cT = occ->mode == 0 ? 0.0 : (occ->mode == 1 ? -1.0 : 1.0);
+    const double cch[4] = {ctx->cM, ctx->cM, ctx->cT, ctx->cT};
+    for (int k = 0; k < 3; ++k) {
+        double w = 0;
+        for (int ch = 0; ch < 4; ++ch) {
+            ctx->cf.f[k][ch] = ftab[k][ch];
+            ctx->cf.C[k][ch] = cch[ch] * ftab[k][ch];
+            w += ctx->cf.C[k][ch];
+        }
+        ctx->cf.w[k] = w;
+    }
+    ctx->cf.xscale = 1.0 - opt->alpha;
+    // -------- projectors: per-projector table and block-diagonal rows
+    std::vector<double> proj, Drow, Qrow, atomtab;
+    std::vector<int> blk_off, blk_n;
+    for (int a = 0; a < natoms; ++a) {
+        const roks_atom& at = atoms[a];
+        if (at.species < 0 || at.species >= nspecies || !(at.width > 0)) return bail(ROKS_EINVAL, "bad atom");
+        atomtab.insert(atomtab.end(), {at.pos[0], at.pos[1], at.pos[2], at.depth, at.width});
+        const roks_species& sp = species[at.species];
+        if (sp.nproj < 0 || sp.nproj > kMaxBlk) return bail(ROKS_EINVAL, "bad projector count");
+        if (sp.nproj > 0 && (!sp.l || !sp.m || !sp.rc || !sp.D || !sp.Q)) return bail(ROKS_EINVAL, "bad species");
+        const int off = (int)blk_off.size();
+        for (int c = 0; c < sp.nproj; ++c) {
+            if ((sp.l[c] != 0 && sp.l[c] != 1) || sp.m[c] < 0 || sp.m[c] > 2 || !(sp.rc[c] > 0))
+                return bail(ROKS_EINVAL, "bad projector channel");
+            proj.insert(proj.end(), {at.pos[0], at.pos[1], at.pos[2], sp.rc[c], (double)sp.l[c], (double)sp.m[c]});
+            blk_off.push_back(off);
+            blk_n.push_back(sp.nproj);
+            for (int j = 0; j < kMaxBlk; ++j) {
+                Drow.push_back(j < sp.nproj ? sp.D[c * sp.nproj + j] : 0.0);
+                Qrow.push_back(j < sp.nproj ? sp.Q[c * sp.nproj + j] : 0.0);
+            }
+        }
+    }
+    ctx->nproj = (int)blk_off.size();
+    // -------- device allocations
+    const bool f64 = ctx->prec == ROKS_FP64;
+    const size_t cs = f64 ? sizeof(double2) : sizeof(float2);
+    const size_t rs = f64 ? sizeof(double) : sizeof(float);
+    const size_t N3 = (size_t)N * N * N;
+    const int nb = ctx->nb, l = ctx->ld_min, npw = ctx->npw;
+    cudaError_t e = cudaSuccess;
+#define AL(p, bytes)                                                   \
+    do {                                                               \
+        e = dalloc(ctx, &(p), (bytes));                                \
+        if (e != cudaSuccess) return bail(ROKS_ENOMEM, "cudaMalloc"); \
+    } while (0)
+    AL(ctx->d_col_start, sizeof(int) * ctx->ncol);
+    AL(ctx->d_col_kmax, sizeof(int) * ctx->ncol);
+    AL(ctx->d_plane_col0, sizeof(int) * ctx->np);
+    AL(ctx->d_plane_jmax, sizeof(int) * ctx->np);
+    AL(ctx->d_miller, sizeof(int) * 3 * npw);
+    AL(ctx->d_shell, sizeof(int) * nb);
+    AL(ctx->d_g2, sizeof(double) * npw);
+    AL(ctx->d_g2half, rs * npw);
+    AL(ctx->d_wk, rs * 3);
+    AL(ctx->d_wband, sizeof(double) * nb);
+    AL(ctx->d_vloc, sizeof(double) * N3);
+    AL(ctx->d_P, cs * (size_t)l * (ctx->nproj > 0 ? ctx->nproj : 1));
+    AL(ctx->d_blk_off, sizeof(int) * (ctx->nproj + 1));
+    AL(ctx->d_blk_n, sizeof(int) * (ctx->nproj + 1));
+    AL(ctx->d_Drow, sizeof(double) * (Drow.size() + 1));
+    AL(ctx->d_Qrow, sizeof(double) * (Qrow.size() + 1));
+    AL(ctx->d_tw, cs * N);
+    AL(ctx->d_tw64, sizeof(double2) * N);
+    AL(ctx->d_Zc, cs * (size_t)nb * ctx->ncol * N);
+    AL(ctx->d_Yp, cs * (size_t)nb * ctx->np * N * N);
+    AL(ctx->d_rho3, sizeof(double) * 3 * N3);
+    AL(ctx->d_xc3, sizeof(double) * 3 * N3);
+    AL(ctx->d_grid, sizeof(double2) * N3);
+    AL(ctx->d_Vk, rs * 3 * N3);
+    AL(ctx->d_part, sizeof(double) * potentials_part_elems());
+    AL(ctx->d_out6, sizeof(double) * 8);
+    AL(ctx->d_E, sizeof(double) * 12);
+    void** bands[] = {&ctx->W_F, &ctx->W_S, &ctx->W_G, &ctx->W_gI, &ctx->W_K, &ctx->W_u,
+                      &ctx->W_v, &ctx->W_s, &ctx->W_sprev, &ctx->W_Y, &ctx->W_Y2};
+    for (void** b : bands) AL(*b, cs * (size_t)l * nb);
+    double2** smalls[] = {&ctx->d_Th, &ctx->d_Gam, &ctx->d_Gin, &ctx->d_A, &ctx->d_Aprev, &ctx->d_Atot, &ctx->d_U,
+                          &ctx->d_O, &ctx->d_L, &ctx->d_LinvH, &ctx->d_Msm, &ctx->d_e1, &ctx->d_e2, &ctx->d_e3};
+    for (double2** b : smalls) AL(*b, sizeof(double2) * nb * nb);
+    const int np_ = ctx->nproj > 0 ? ctx->nproj : 1;
+    AL(ctx->d_B, sizeof(double2) * np_ * nb);
+    AL(ctx->d_DB, sizeof(double2) * np_ * nb);
+    AL(ctx->d_QB, sizeof(double2) * np_ * nb);
+    AL(ctx->d_B2, sizeof(double2) * np_ * nb);
+    size_t gw = gemm_cn_work(np_ > nb ? np_ : nb, nb, npw);
+    ctx->gemm_work_elems = gw;
+    AL(ctx->d_gemm_work, sizeof(double2) * gw);
+    AL(ctx->d_kin_b, sizeof(double) * nb);
+    AL(ctx->d_nl_b, sizeof(double) * nb);
+    AL(ctx->d_colpart, sizeof(double) * 2 * nb * 16);
+    AL(ctx->d_colout, sizeof(double) * 2 * nb);
+    AL(ctx->d_d, sizeof(double) * nb);
+    AL(ctx->d_expm_info, sizeof(double) * 2);
+    AL(ctx->d_flag, sizeof(int) * 2);
+    AL(ctx->d_sc, sizeof(PcgScalars));
+    double* d_atoms = nullptr;
+    double* d_proj = nullptr;
+    AL(d_atoms, sizeof(double) * (atomtab.size() + 1));
+    AL(d_proj, sizeof(double) * (proj.size() + 1));
+#undef AL
+    // -------- uploads
+    std::vector<int> shell(nb), dummy;
+    for (int b = 0; b < nb; ++b) {
+        const int cls = b < ctx->nc ? 0 : b - ctx->nc + 1;
+        shell[b] = (ctx->mode == ROKS_MODE_TRIPLET && cls > 0) ? 1 : cls;
+    }
+    std::vector<double> g2(npw), wband(nb);
+    const double bq = 2.0 * M_PI / cell->L;
+    for (int g = 0; g < npw; ++g) {
+        const double gx = bq * ctx->miller[3 * g], gy = bq * ctx->miller[3 * g + 1], gz = bq * ctx->miller[3 * g + 2];
+        g2[g] = gx * gx + gy * gy + gz * gz;
+    }
+    for (int b = 0; b < nb; ++b) wband[b] = ctx->cf.w[b < ctx->nc ? 0 : b - ctx->nc + 1];
+    std::vector<double2> tw64(N);
+    for (int t = 0; t < N; ++t) tw64[t] = make_double2(std::cos(-2.0 * M_PI * t / N), std::sin(-2.0 * M_PI * t / N));
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+        return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->st) : cudaSuccess;
+    };
+    e = up(ctx->d_col_start, col_start.data(), sizeof(int) * col_start.size());
+    if (e == cudaSuccess) e = up(ctx->d_col_kmax, col_kmax.data(), sizeof(int) * col_kmax.size());
+    if (e == cudaSuccess) e = up(ctx->d_plane_col0, plane_col0.data(), sizeof(int) * plane_col0.size());
+    if (e == cudaSuccess) e = up(ctx->d_plane_jmax, plane_jmax.data(), sizeof(int) * plane_jmax.size());
+    if (e == cudaSuccess) e = up(ctx->d_miller, ctx->miller.data(), sizeof(int) * ctx->miller.size());
+    if (e == cudaSuccess) e = up(ctx->d_shell, shell.data(), sizeof(int) * nb);
+    if (e == cudaSuccess) e = up(ctx->d_g2, g2.data(), sizeof(double) * npw);
+    if (e == cudaSuccess) e = up(ctx->d_wband, wband.data(), sizeof(double) * nb);
+    if (e == cudaSuccess) e = up(ctx->d_tw64, tw64.data(), sizeof(double2) * N);
+    if (e == cudaSuccess) e = up(ctx->d_blk_off, blk_off.data(), sizeof(int) * blk_off.size());
+    if (e == cudaSuccess) e = up(ctx->d_blk_n, blk_n.data(), sizeof(int) * blk_n.size());
+    if (e == cudaSuccess) e = up(ctx->d_Drow, Drow.data(), sizeof(double) * Drow.size());
+    if (e == cudaSuccess) e = up(ctx->d_Qrow, Qrow.data(), sizeof(double) * Qrow.size());
+    if (e == cudaSuccess) e = up(d_atoms, atomtab.data(), sizeof(double) * atomtab.size());
+    if (e == cudaSuccess) e = up(d_proj, proj.data(), sizeof(double) * proj.size());
+    if (e != cudaSuccess) return bail(ROKS_ECUDA, "upload");
+    // typed tables
+    std::vector<double> wk(ctx->cf.w, ctx->cf.w + 3);
+    double* d_tmp = nullptr;
+    e = cudaMalloc(&d_tmp, sizeof(double) * (npw + 8));
+    if (e != cudaSuccess) return bail(ROKS_ENOMEM, "cudaMalloc");
+    std::vector<double> g2h(npw);
+    for (int g = 0; g < npw; ++g) g2h[g] = 0.5 * g2[g];
+    std::vector<double> twf(2 * N);
+    for (int t = 0; t < N; ++t) { twf[2 * t] = tw64[t].x; twf[2 * t + 1] = tw64[t].y; }
+    cudaMemcpyAsync(d_tmp, g2h.data(), sizeof(double) * npw, cudaMemcpyHostToDevice, ctx->st);
+    if (f64) to_real_type<double>(npw, d_tmp, static_cast<double*>(ctx->d_g2half), 1.0, ctx->st);
+    else to_real_type<float>(npw, d_tmp, static_cast<float*>(ctx->d_g2half), 1.0, ctx->st);
+    cudaStreamSynchronize(ctx->st);
+    cudaMemcpyAsync(d_tmp, wk.data(), sizeof(double) * 3, cudaMemcpyHostToDevice, ctx->st);
+    if (f64) to_real_type<double>(3, d_tmp, static_cast<double*>(ctx->d_wk), 1.0, ctx->st);
+    else to_real_type<float>(3, d_tmp, static_cast<float*>(ctx->d_wk), 1.0, ctx->st);
+    cudaStreamSynchronize(ctx->st);
+    cudaFree(d_tmp);
+    if (f64) {
+        cudaMemcpyAsync(ctx->d_tw, tw64.data(), sizeof(double2) * N, cudaMemcpyHostToDevice, ctx->st);
+    } else {
+        std::vector<float2> t32(N);
+        for (int t = 0; t < N; ++t) t32[t] = make_float2((float)tw64[t].x, (float)tw64[t].y);
+        cudaMemcpyAsync(ctx->d_tw, t32.data(), sizeof(float2) * N, cudaMemcpyHostToDevice, ctx->st);
+        cudaStreamSynchronize(ctx->st);
+    }
+    // -------- model on the device
+    vloc_setup(N, cell->L, natoms, d_atoms, ctx->d_grid, ctx->d_vloc, ctx->d_tw64, ctx->st);
+    if (f64) projectors_setup<double>(npw, ctx->nproj, cell->L, ctx->d_miller, d_proj,
+                                      static_cast<double2*>(ctx->d_P), l, ctx->st);
+    else projectors_setup<float>(npw, ctx->nproj, cell->L, ctx->d_miller, d_proj, static_cast<float2*>(ctx->d_P), l,
+                                 ctx->st);
+    e = cudaStreamSynchronize(ctx->st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return bail(ROKS_ECUDA, cudaGetErrorString(e));
+    reset_history(ctx);
+    *out = ctx;
+    return ROKS_OK;
+}
+
+roks_status roks_basis(roks_ctx* ctx, int* npw, int* nbands, int* ld_min, const int32_t** miller) {
+    if (!ctx) return ROKS_EINVAL;
+    if (npw) *npw = ctx->npw;
+    if (nbands) *nbands = ctx->nb;
+    if (ld_min) *ld_min = ctx->ld_min;
+    if (miller) *miller = ctx->miller.data();
+    return ROKS_OK;
+}
+
+static roks_status check_psi(roks_ctx* ctx, const void* psi, int64_t ld) {
+    if (!psi) return fail(ctx, ROKS_EINVAL, "null orbital pointer");
+    if (ld < ctx->npw) return fail(ctx, ROKS_EINVAL, "leading dimension smaller than npw");
+    return ROKS_OK;
+}
+
+roks_status roks_init_orbitals(roks_ctx* ctx, const double* u_host, void* psi, int64_t ld) {
+    if (!ctx) return ROKS_EINVAL;
+    if (!u_host) return fail(ctx, ROKS_EINVAL, "null random numbers");
+    roks_status r = check_psi(ctx, psi, ld);
+    if (r != ROKS_OK) return r;
+    double* d_u = nullptr;
+    const size_t bytes = sizeof(double) * 2 * (size_t)ctx->npw * ctx->nb;
+    CK(cudaMalloc(&d_u, bytes));
+    cudaMemcpyAsync(d_u, u_host, bytes, cudaMemcpyHostToDevice, ctx->st);
+    const int64_t l = ctx->ld_min;
+    if (ctx->prec == ROKS_FP64) {
+        init_orbitals<double>(ctx->npw, ctx->nb, d_u, ctx->d_g2, static_cast<double2*>(ctx->W_Y), l, ctx->st);
+        r = Impl<double>::orth(ctx, ctx->W_Y, l, psi, ld, nullptr);
+    } else {
+        init_orbitals<float>(ctx->npw, ctx->nb, d_u, ctx->d_g2, static_cast<float2*>(ctx->W_Y), l, ctx->st);
+        r = Impl<float>::orth(ctx, ctx->W_Y, l, psi, ld, nullptr);
+    }
+    cudaStreamSynchronize(ctx->st);
+    cudaFree(d_u);
+    if (r != ROKS_OK) return r;
+    reset_history(ctx);
+    return ctx->prec == ROKS_FP64 ? Impl<double>::check_flag(ctx) : Impl<float>::check_flag(ctx);
+}
+
+roks_status roks_density(roks_ctx* ctx, const void* psi, int64_t ld, double* rho_out) {
+    if (!ctx) return ROKS_EINVAL;
+    roks_status r = check_psi(ctx, psi, ld);
+    if (r != ROKS_OK) return r;
+    ctx->pot_valid = false;
+    r = ctx->prec == ROKS_FP64 ? Impl<double>::density(ctx, psi, ld, nullptr)
+                               : Impl<float>::density(ctx, psi, ld, nullptr);
+    if (r != ROKS_OK) return r;
+    if (rho_out)
+        CK(cudaMemcpyAsync(rho_out, ctx->d_rho3, sizeof(double) * 3 * (size_t)ctx->N * ctx->N * ctx->N,
+                           cudaMemcpyDeviceToDevice, ctx->st));
+    return ROKS_OK;
+}
+
+static void fill_energies(const double* h, roks_energies* e) {
+    e->E_kin = h[0]; e->E_loc = h[1]; e->E_nl = h[2]; e->E_H = h[3];
+    e->E_x_M = h[4]; e->E_x_T = h[5]; e->E_hf_M = h[6]; e->E_hf_T = h[7];
+    e->E_M = h[8]; e->E_T = h[9]; e->E_total = h[10];
+}
+
+roks_status roks_energies_get(roks_ctx* ctx, roks_energies* e) {
+    if (!ctx || !e) return ROKS_EINVAL;
+    double h[12];
+    CK(cudaMemcpyAsync(h, ctx->d_E, sizeof(double) * 11, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    fill_energies(h, e);
+    return ROKS_OK;
+}
+
+roks_status roks_potential(roks_ctx* ctx, roks_energies* e, void* vclass_out) {
+    if (!ctx) return ROKS_EINVAL;
+    roks_status r = ctx->prec == ROKS_FP64 ? Impl<double>::potential(ctx) : Impl<float>::potential(ctx);
+    if (r != ROKS_OK) return r;
+    const size_t N3 = (size_t)ctx->N * ctx->N * ctx->N;
+    if (vclass_out)
+        CK(cudaMemcpyAsync(vclass_out, ctx->d_Vk, (ctx->prec == ROKS_FP64 ? 8 : 4) * 3 * N3, cudaMemcpyDeviceToDevice,
+                           ctx->st));
+    if (e) return roks_energies_get(ctx, e);
+    CK(cudaStreamSynchronize(ctx->st));
+    return ROKS_OK;
+}
+
+roks_status roks_apply_h(roks_ctx* ctx, const void* psi, int64_t ld, void* fpsi, void* spsi, void* grad) {
+    if (!ctx) return ROKS_EINVAL;
+    roks_status r = check_psi(ctx, psi, ld);
+    if (r != ROKS_OK) return r;
+    if (!fpsi) return fail(ctx, ROKS_EINVAL, "null output");
+    const int64_t l = ctx->ld_min;
+    const int nb = ctx->nb;
+    void* S = spsi ? spsi : (grad ? ctx->W_S : nullptr);
+    const int64_t lds = spsi ? ld : l;
+    if (ctx->prec == ROKS_FP64) r = Impl<double>::apply(ctx, psi, ld, fpsi, ld, S, lds);
+    else r = Impl<float>::apply(ctx, psi, ld, fpsi, ld, S, lds);
+    if (r != ROKS_OK || !grad) return r;
+    // g = F - S Gam, Gam_mn = (theta_mn + conj theta_nm) / 2
+    if (ctx->prec == ROKS_FP64) {
+        gemm_cn<double>(nb, nb, ctx->npw, static_cast<const double2*>(psi), ld, static_cast<const double2*>(fpsi), ld,
+                        ctx->d_Th, nb, ctx->d_gemm_work, ctx->gemm_work_elems, ctx->st);
+    } else {
+        gemm_cn<float>(nb, nb, ctx->npw, static_cast<const float2*>(psi), ld, static_cast<const float2*>(fpsi), ld,
+                       ctx->d_Th, nb, ctx->d_gemm_work, ctx->gemm_work_elems, ctx->st);
+    }
+    CK(cudaMemcpyAsync(ctx->d_Gam, ctx->d_Th, sizeof(double2) * nb * nb, cudaMemcpyDeviceToDevice, ctx->st));
+    hermitize(nb, ctx->d_Gam, ctx->st);
+    const size_t es = ctx->prec == ROKS_FP64 ? sizeof(double2) : sizeof(float2);
+    CK(cudaMemcpy2DAsync(grad, ld * es, fpsi, ld * es, ctx->npw * es, nb, cudaMemcpyDeviceToDevice, ctx->st));
+    if (ctx->prec == ROKS_FP64)
+        gemm_nn<double>(ctx->npw, nb, nb, static_cast<const double2*>(S), lds, ctx->d_Gam, nb,
+                        static_cast<double2*>(grad), ld, -1.0, 1.0, ctx->st);
+    else
+        gemm_nn<float>(ctx->npw, nb, nb, static_cast<const float2*>(S), lds, ctx->d_Gam, nb,
+                       static_cast<float2*>(grad), ld, -1.0, 1.0, ctx->st);
+    CK(cudaGetLastError());
+    return ROKS_OK;
+}
+
+roks_status roks_orthonormalize(roks_ctx* ctx, void* psi, int64_t ld) {
+    if (!ctx) return ROKS_EINVAL;
+    roks_status r = check_psi(ctx, psi, ld);
+    if (r != ROKS_OK) return r;
+    const int64_t l = ctx->ld_min;
+    const size_t es = ctx->prec == ROKS_FP64 ? sizeof(double2) : sizeof(float2);
+    CK(cudaMemcpy2DAsync(ctx->W_Y, l * es, psi, ld * es, ctx->npw * es, ctx->nb, cudaMemcpyDeviceToDevice, ctx->st));
+    r = ctx->prec == ROKS_FP64 ? Impl<double>::orth(ctx, ctx->W_Y, l, psi, ld, nullptr)
+                               : Impl<float>::orth(ctx, ctx->W_Y, l, psi, ld, nullptr);
+    if (r != ROKS_OK) return r;
+    reset_history(ctx);
+    return ctx->prec == ROKS_FP64 ? Impl<double>::check_flag(ctx) : Impl<float>::check_flag(ctx);
+}
+
+roks_status roks_pcg_step(roks_ctx* ctx, void* psi, int64_t ld, roks_step_info* info) {
+    if (!ctx) return ROKS_EINVAL;
+    roks_status r = check_psi(ctx, psi, ld);
+    if (r != ROKS_OK) return r;
+    roks_step_info tmp;
+    std::memset(&tmp, 0, sizeof(tmp));
+    r = ctx->prec == ROKS_FP64 ? Impl<double>::pcg_step(ctx, psi, ld, &tmp) : Impl<float>::pcg_step(ctx, psi, ld, &tmp);
+    if (r != ROKS_OK && r != ROKS_EDIVERGED) return r;
+    // convergence: |E_new - E| < e_tol on two consecutive steps
+    if (std::fabs(tmp.E_new - tmp.E) < ctx->e_tol) ctx->n_small += 1;
+    else ctx->n_small = 0;
+    tmp.converged = ctx->n_small >= 2 ? 1 : 0;
+    if (info) *info = tmp;
+    return r;
+}
+
+roks_status roks_profile_enable(roks_ctx* ctx, int enable) {
+    if (!ctx) return ROKS_EINVAL;
+    ctx->prof_on = enable != 0;
+    return ROKS_OK;
+}
+
+roks_status roks_profile_read(roks_ctx* ctx, roks_profile_entry* out, int cap, int* count) {
+    if (!ctx || cap < 0 || (cap > 0 && !out)) return ROKS_EINVAL;
+    CK(cudaStreamSynchronize(ctx->st));
+    const size_t nf = ctx->prof_names.size();
+    std::vector<double> ms(nf, 0.0);
+    std::vector<int> cnt(nf, 0);
+    for (const auto& r : ctx->prof_recs) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+            ms[r.fam] += t;
+            cnt[r.fam] += 1;
+        }
+        ctx->prof_pool.push_back(r.a);
+        ctx->prof_pool.push_back(r.b);
+    }
+    ctx->prof_recs.clear();
+    int n = 0;
+    for (size_t f = 0; f < nf; ++f) {
+        if (cnt[f] == 0) continue;
+        if (n < cap) {
+            std::memset(out[n].name, 0, sizeof(out[n].name));
+            std::strncpy(out[n].name, ctx->prof_names[f].c_str(), sizeof(out[n].name) - 1);
+            out[n].launches = cnt[f];
+            out[n].ms = ms[f];
+        }
+        ++n;
+    }
+    if (count) *count = n;
+    return ROKS_OK;
+}
+
+const char* roks_last_error(const roks_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void roks_destroy(roks_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->st) cudaStreamSynchronize(ctx->st);
+    else cudaDeviceSynchronize();
+    for (void* p : ctx->allocs) cudaFree(p);
+    for (const auto& r : ctx->prof_recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
+    delete ctx;
+}
+
+}  // extern "C"

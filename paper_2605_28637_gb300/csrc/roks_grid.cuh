@@ -1,0 +1,100 @@
+// roks_grid.cuh -- declarations of the grid, reduction and PCG-step kernels'
+// host wrappers (internal to the library).
+#pragma once
+
+#include "roks_impl.cuh"
+
+namespace roks {
+
+constexpr int kMaxBlk = 16;   // projectors per atom
+
+// Occupation-derived coefficients of the class potentials (Eq. 14):
+// f[k][ch] = f_k^{sigma L}, C[k][ch] = c_L f_k^{sigma L}, w[k] = sum_ch C[k][ch],
+// channels (up M, down M, up T, down T); xscale = 1 - alpha.
+struct PotCoef {
+    double f[3][4];
+    double C[3][4];
+    double w[3];
+    double xscale;
+};
+
+void vloc_setup(int N, double L, int natoms, const double* atoms_dev, double2* grid, double* vloc,
+                const double2* tw64, cudaStream_t st);
+template <typename T>
+void projectors_setup(int npw, int nproj, double L, const int* miller_dev, const double* proj_dev, c2<T>* P,
+                      int64_t ldp, cudaStream_t st);
+template <typename T>
+void init_orbitals(int npw, int nb, const double* u_dev, const double* g2, c2<T>* psi, int64_t ld, cudaStream_t st);
+template <typename T>
+void to_real_type(int64_t n, const double* in, T* out, double scale, cudaStream_t st);
+// op 0: kinetic 0.5 g2 |x|^2; 1: (|x|^2, g2 |x|^2) -> out[0..nb), out[nb..2nb); 2: Re <x|y>; 3: |x|^2.
+// part must hold 2 * nb * 16 doubles.
+template <typename T>
+void column_sums(int op, int npw, int nb, const c2<T>* x, int64_t ldx, const c2<T>* y, int64_t ldy,
+                 const double* g2, double* part, double* out, cudaStream_t st);
+void apply_DQ(int nproj, int nb, const double2* B, const int* blk_off, const int* blk_n, const double* Drow,
+              const double* Qrow, const double* wband, double2* DB, double2* QB, cudaStream_t st);
+void band_quadratic(int nproj, int nb, const double2* B, const double2* DB, double* out, cudaStream_t st);
+template <typename T>
+void potentials(int N, double L, const double* rho3, const double* vloc, const PotCoef& cf, double2* grid,
+                double* xc3, const double2* tw64, T* Vk, double* Vk64, double* part, double* out6,
+                cudaStream_t st);
+size_t potentials_part_elems();
+template <typename T>
+void precondition(int npw, int nb, const c2<T>* gI, int64_t ld, const double* g2, const double* sums, c2<T>* out,
+                  int64_t ldo, cudaStream_t st);
+template <typename T>
+void axpy(int npw, int nb, const c2<T>* x, int64_t ldx, const c2<T>* y, int64_t ldy, const double* coef,
+          double csign, c2<T>* out, int64_t ldo, cudaStream_t st);
+
+// ------------------------------------------------------------ PCG step, band-space part (k_pcg.cu)
+// Device scalars of one PCG iteration.
+struct PcgScalars {
+    double E0, Et, Enew;      // energies at the start, trial, new point
+    double pg, pg_prev;       // <p|g> now and at the previous step (0 = none)
+    double beta;              // Fletcher-Reeves ratio in use
+    double a1, a2, r1, r2;    // Re<u|G>, Re<v|G>, Re sum A^* Gin, Re sum A_prev^* Gin
+    double pgI;               // Re <p_I|g_I>
+    double rot_pg;            // (1/2) Re sum A^* Gin
+    double dE0;               // directional derivative
+    double dt;                // trial step
+    double step;              // accepted step
+    double rot;               // 1 when the rotation is used
+    double restarted;
+    double has_prev;          // 1 when a previous direction exists
+    double cur;               // scalar used by launches that scale by a device value
+    double gnorm2;
+    double coup_re, coup_im;
+    double neg_one;           // constant -1 for device-scaled axpy
+};
+
+// Gam = (Theta + Theta^H)/2, Gin = Theta - Theta^H, R (Eq. 20) -> A (Eqs. 22-23),
+// and the open-shell coupling; shell[n] is the shell index of band n.
+void pcg_rotation(int nb, const double2* Theta, const double* d, const int* shell, int suppress_ab, int ia,
+                  int ib, double2* Gam, double2* Gin, double2* A, PcgScalars* sc, cudaStream_t st);
+// d_m = <m|F^c|m>: Re theta_mm for closed bands, from expectation values for open ones.
+void pcg_diag(int nb, int n_closed, const double2* Theta, const double* kin_b, const double* nl_b,
+              const double* open_vc, double wc, double* d, cudaStream_t st);
+// sc->rot_pg = 1/2 Re sum conj(A) Gin; sc->r1, r2 as named.
+void pcg_rot_dots(int nb, const double2* A, const double2* Aprev, const double2* Gin, PcgScalars* sc,
+                  cudaStream_t st);
+// Decide beta / restart / rotation, set dE0 and the trial step.
+void pcg_direction(PcgScalars* sc, cudaStream_t st);
+// A_tot = rot * (A + beta Aprev)
+void pcg_total_rotation(int nb, const double2* A, const double2* Aprev, PcgScalars* sc, double2* Atot,
+                        cudaStream_t st);
+// Parabola through E0, dE0, Et -> step; next trial; pg_prev.
+void pcg_line_search(PcgScalars* sc, cudaStream_t st);
+// sc->cur = sc->(field); used to feed device-scaled launches.
+void pcg_set_cur(PcgScalars* sc, int field, cudaStream_t st);
+// Energy combination on the device: out (11 doubles) from the pieces.
+void energy_combine(const double* kin_b, const double* nl_b, int nb, const double* wband, const double* out6,
+                    double cM, double cT, double alpha, const double* hf2, double* E, cudaStream_t st);
+// Copy E[total] into a scalar field.
+void pcg_take_energy(const double* E, PcgScalars* sc, int field, cudaStream_t st);
+// Hermitian part: O <- (O + O^H)/2
+void hermitize(int n, double2* O, cudaStream_t st);
+
+enum { SC_E0 = 0, SC_ET = 1, SC_ENEW = 2, SC_DT = 14, SC_STEP = 15, SC_BETA = 5 };
+
+}  // namespace roks

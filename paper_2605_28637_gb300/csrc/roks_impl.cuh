@@ -1,0 +1,91 @@
+// roks_impl.cuh -- internal declarations shared by the library's translation
+// units: geometry of the plane-wave sphere on the FFT grid, the launchers of
+// the CUDA kernels, and small helpers.  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "fft_core.cuh"
+
+namespace roks {
+
+// Grid sizes with compiled transforms.
+constexpr int kGrids[] = {16, 24, 32, 48, 72, 96, 120};
+
+// Lines per shared-memory tile for a transform length.
+__host__ __device__ constexpr int tile_lines(int n) {
+    return n == 16 ? 16 : (n == 32 || n == 96) ? 32 : 24;
+}
+constexpr int kThreads = 256;
+
+// The plane-wave sphere seen from the grid.  Basis order is i, j, k
+// ascending, so the coefficients of one (i, j) column are contiguous with
+// k running from -kmax to kmax; the columns of one i plane are contiguous
+// with j running from -jmax to jmax.
+struct Sphere {
+    int N;        // grid points per side
+    int nmax;     // largest |i|, |j|, |k|
+    int np;       // planes i = -nmax .. nmax  (2 nmax + 1)
+    int ncol;     // (i, j) columns
+    const int* col_start;   // [ncol] first coefficient (k = -kmax)
+    const int* col_kmax;    // [ncol]
+    const int* plane_col0;  // [np] first column of plane i
+    const int* plane_jmax;  // [np]
+};
+
+__host__ __device__ __forceinline__ int signed_freq(int e, int n) { return e <= n / 2 ? e : e - n; }
+
+// ------------------------------------------------------------ band FFTs
+// Bands b0 .. b0+nbb-1 of psi (column major, ld).  Zc holds nbb x ncol x N
+// z-lines, Yp holds nbb x np x N x N plane data (y, z).
+// z stage, inverse: sphere columns -> Zc
+template <typename T>
+void band_z_inv(const Sphere& s, const c2<T>* tw, const c2<T>* psi, int64_t ld, int b0, int nbb, c2<T>* Zc,
+                cudaStream_t st);
+// y stage, inverse: Zc -> Yp
+template <typename T>
+void band_y_inv(const Sphere& s, const c2<T>* tw, const c2<T>* Zc, c2<T>* Yp, int nbb, cudaStream_t st);
+// x stage, in place on Yp: inverse transform, multiply by V^{class(b)} * scale,
+// forward transform, keep the planes of the sphere
+template <typename T>
+void band_x_apply(const Sphere& s, const c2<T>* tw, c2<T>* Yp, const T* Vk, int b0, int nbb, int n_closed,
+                  T scale, cudaStream_t st);
+// y stage, forward: Yp -> Zc (columns of the sphere only)
+template <typename T>
+void band_y_fwd(const Sphere& s, const c2<T>* tw, const c2<T>* Yp, c2<T>* Zc, int nbb, cudaStream_t st);
+// z stage, forward: Zc -> out[b] = gathered coefficients + wk[class] g2half psi[b]
+template <typename T>
+void band_z_fwd(const Sphere& s, const c2<T>* tw, const c2<T>* Zc, c2<T>* out, int64_t ldo, const c2<T>* psi,
+                int64_t ldp, const T* g2half, const T* wk, int b0, int nbb, int n_closed, cudaStream_t st);
+// x stage, inverse, accumulating |psi|^2 * scale into rho3 (3 x N^3, double)
+template <typename T>
+void band_x_density(const Sphere& s, const c2<T>* tw, const c2<T>* Yp, double* rho3, int b0, int nbb,
+                    int n_closed, double scale, cudaStream_t st);
+
+// ------------------------------------------------------------ full-grid 3D FFT (in place)
+template <typename T>
+void grid_fft3(int N, const c2<T>* tw, c2<T>* data, int dir, cudaStream_t st);
+
+// ------------------------------------------------------------ dense complex contractions
+// Cpart[chunk] (double2, M x N column major) = sum over the k of the chunk of
+// conj(A[k, m]) B[k, n]; then C = sum_chunks Cpart (double2, ldc).
+template <typename T>
+void gemm_cn(int M, int N, int K, const c2<T>* A, int64_t lda, const c2<T>* B, int64_t ldb,
+             double2* C, int ldc, double2* work, size_t work_elems, cudaStream_t st);
+size_t gemm_cn_work(int M, int N, int K);
+// C[m, n] = alpha sum_k A[m, k] B[k, n] + beta C[m, n]; B is FP64 (small).
+template <typename T>
+void gemm_nn(int M, int N, int K, const c2<T>* A, int64_t lda, const double2* B, int ldb,
+             c2<T>* C, int64_t ldc, double alpha, double beta, cudaStream_t st);
+
+// ------------------------------------------------------------ small FP64 matrices (n x n, column major)
+void small_gemm(int M, int N, int K, const double2* A, int lda, bool ca, const double2* B, int ldb,
+                bool cb, double2* C, int ldc, double alpha, double beta, cudaStream_t st);
+// O (Hermitian) -> LinvH = L^{-H}, L L^H = O.  flag[0] set to 1 + column on failure.
+void cholesky_inverse(int n, const double2* O, double2* Lw, double2* LinvH, int* flag, cudaStream_t st);
+// E = expm(scale_dev[0] * A), A anti-Hermitian, Taylor + scaling and squaring.
+void expm_scaled(int n, const double2* A, const double* scale_dev, double2* E, double2* w1, double2* w2,
+                 double2* w3, double* sdev, cudaStream_t st);
+
+}  // namespace roks

@@ -1,0 +1,262 @@
+"""ctypes binding of libroks_gb300.so (the C ABI of include/roks.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Device buffers are torch tensors (used for memory and
+streams); orbitals are tensors of shape (nbands, ld) with dtype complex128
+(FP64 path) or complex64 (mixed path), row n holding band n, which is the
+column-major npw x nbands layout of the C ABI.
+
+The module-level functions carry the C names (roks_setup, roks_density, ...).
+`Context` wraps them for convenience.  Loading fails loudly when the library
+has not been built; there is no other implementation behind these names.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libroks_gb300.so")
+
+ROKS_OK, ROKS_EINVAL, ROKS_ENOMEM, ROKS_ECUDA, ROKS_ENOTPOSDEF, ROKS_ENOCONV, ROKS_ETIMEOUT, ROKS_EDIVERGED = range(8)
+ROKS_FP64, ROKS_MIXED = 0, 1
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTPOSDEF", "ENOCONV", "ETIMEOUT", "EDIVERGED"]
+
+
+class RoksError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"ROKS_{name}: {msg}")
+        self.status = status
+
+
+class roks_cell(C.Structure):
+    _fields_ = [("L", C.c_double), ("grid", C.c_int)]
+
+
+class roks_atom(C.Structure):
+    _fields_ = [("pos", C.c_double * 3), ("species", C.c_int), ("depth", C.c_double), ("width", C.c_double)]
+
+
+class roks_species(C.Structure):
+    _fields_ = [("nproj", C.c_int), ("l", C.POINTER(C.c_int)), ("m", C.POINTER(C.c_int)),
+                ("rc", C.POINTER(C.c_double)), ("D", C.POINTER(C.c_double)), ("Q", C.POINTER(C.c_double))]
+
+
+class roks_occ(C.Structure):
+    _fields_ = [("n_closed", C.c_int), ("mode", C.c_int)]
+
+
+class roks_options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("alpha", C.c_double), ("suppress_ab", C.c_int), ("e_tol", C.c_double)]
+
+
+class roks_energies(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("E_kin", "E_loc", "E_nl", "E_H", "E_x_M", "E_x_T", "E_hf_M", "E_hf_T",
+                                          "E_M", "E_T", "E_total")]
+
+
+class roks_step_info(C.Structure):
+    _fields_ = [("E", C.c_double), ("E_new", C.c_double), ("step", C.c_double), ("grad_norm", C.c_double),
+                ("coupling_re", C.c_double), ("coupling_im", C.c_double), ("beta", C.c_double),
+                ("dE0", C.c_double), ("restarted", C.c_int), ("converged", C.c_int)]
+
+
+EXPORTS = ["roks_setup", "roks_basis", "roks_init_orbitals", "roks_density", "roks_potential", "roks_apply_h",
+           "roks_orthonormalize", "roks_pcg_step", "roks_energies_get", "roks_last_error", "roks_destroy"]
+
+_lib = None
+
+
+def load(path: str | None = None) -> C.CDLL:
+    """Open the compiled library (build it with paper_2605_28637_gb300.build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"{path} is missing: build the CUDA library first "
+                                "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    lib.roks_setup.argtypes = [C.POINTER(roks_cell), C.c_double, C.c_int, C.POINTER(roks_atom), C.c_int,
+                               C.POINTER(roks_species), C.POINTER(roks_occ), C.POINTER(roks_options), P,
+                               C.POINTER(P)]
+    lib.roks_basis.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                               C.POINTER(C.POINTER(C.c_int32))]
+    lib.roks_init_orbitals.argtypes = [P, C.POINTER(C.c_double), P, C.c_int64]
+    lib.roks_density.argtypes = [P, P, C.c_int64, P]
+    lib.roks_potential.argtypes = [P, C.POINTER(roks_energies), P]
+    lib.roks_apply_h.argtypes = [P, P, C.c_int64, P, P, P]
+    lib.roks_orthonormalize.argtypes = [P, P, C.c_int64]
+    lib.roks_pcg_step.argtypes = [P, P, C.c_int64, C.POINTER(roks_step_info)]
+    lib.roks_energies_get.argtypes = [P, C.POINTER(roks_energies)]
+    lib.roks_last_error.argtypes = [P]
+    lib.roks_last_error.restype = C.c_char_p
+    lib.roks_destroy.argtypes = [P]
+    lib.roks_destroy.restype = None
+    for name in EXPORTS[:-2]:
+        getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(ctx, status):
+    if status != ROKS_OK:
+        msg = load().roks_last_error(ctx).decode() if ctx else ""
+        raise RoksError(status, msg)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------- C names
+def roks_setup(cfg: dict, precision: int = ROKS_FP64, stream=None, suppress_ab: bool = False,
+               e_tol: float = 1e-6):
+    """Marshal a workload description (see synthetic.make_config) and call roks_setup."""
+    lib = load()
+    cell = roks_cell(cfg["L"], cfg["grid"])
+    keep = []
+    sp_arr = (roks_species * max(1, len(cfg["species"])))()
+    for i, sp in enumerate(cfg["species"]):
+        n = len(sp["l"])
+        l = (C.c_int * n)(*sp["l"])
+        m = (C.c_int * n)(*sp["m"])
+        rc = (C.c_double * n)(*sp["rc"])
+        D = np.ascontiguousarray(np.asarray(sp["D"], dtype=np.float64).reshape(n, n))
+        Q = np.ascontiguousarray(np.asarray(sp["Q"], dtype=np.float64).reshape(n, n))
+        keep += [l, m, rc, D, Q]
+        sp_arr[i] = roks_species(n, l, m, rc, D.ctypes.data_as(C.POINTER(C.c_double)),
+                                 Q.ctypes.data_as(C.POINTER(C.c_double)))
+    atoms = cfg["atoms"]
+    at_arr = (roks_atom * max(1, len(atoms)))()
+    for i, a in enumerate(atoms):
+        at_arr[i] = roks_atom((C.c_double * 3)(*a["pos"]), a["species"], a["depth"], a["width"])
+    occ = roks_occ(cfg["n_closed"], cfg["mode"])
+    opt = roks_options(precision, cfg.get("alpha", 0.0), int(suppress_ab), e_tol)
+    out = C.c_void_p()
+    st = C.c_void_p(stream) if stream else None
+    status = lib.roks_setup(C.byref(cell), cfg["ecut"], len(atoms), at_arr, len(cfg["species"]), sp_arr,
+                            C.byref(occ), C.byref(opt), st, C.byref(out))
+    if status != ROKS_OK:
+        raise RoksError(status, "roks_setup rejected the workload")
+    return out
+
+
+def roks_basis(ctx):
+    lib = load()
+    npw, nb, ld = C.c_int(), C.c_int(), C.c_int()
+    mil = C.POINTER(C.c_int32)()
+    _check(ctx, lib.roks_basis(ctx, C.byref(npw), C.byref(nb), C.byref(ld), C.byref(mil)))
+    miller = np.ctypeslib.as_array(mil, shape=(npw.value, 3)).copy()
+    return npw.value, nb.value, ld.value, miller
+
+
+def roks_init_orbitals(ctx, u: np.ndarray, psi, ld: int):
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    _check(ctx, load().roks_init_orbitals(ctx, u.ctypes.data_as(C.POINTER(C.c_double)), _ptr(psi), ld))
+
+
+def roks_density(ctx, psi, ld: int, rho_out=None):
+    _check(ctx, load().roks_density(ctx, _ptr(psi), ld, _ptr(rho_out)))
+
+
+def roks_potential(ctx, vclass_out=None) -> dict:
+    e = roks_energies()
+    _check(ctx, load().roks_potential(ctx, C.byref(e), _ptr(vclass_out)))
+    return {n: getattr(e, n) for n, _ in roks_energies._fields_}
+
+
+def roks_apply_h(ctx, psi, ld: int, fpsi, spsi=None, grad=None):
+    _check(ctx, load().roks_apply_h(ctx, _ptr(psi), ld, _ptr(fpsi), _ptr(spsi), _ptr(grad)))
+
+
+def roks_orthonormalize(ctx, psi, ld: int):
+    _check(ctx, load().roks_orthonormalize(ctx, _ptr(psi), ld))
+
+
+def roks_pcg_step(ctx, psi, ld: int) -> dict:
+    info = roks_step_info()
+    _check(ctx, load().roks_pcg_step(ctx, _ptr(psi), ld, C.byref(info)))
+    return {n: getattr(info, n) for n, _ in roks_step_info._fields_}
+
+
+def roks_energies_get(ctx) -> dict:
+    e = roks_energies()
+    _check(ctx, load().roks_energies_get(ctx, C.byref(e)))
+    return {n: getattr(e, n) for n, _ in roks_energies._fields_}
+
+
+def roks_last_error(ctx) -> str:
+    return load().roks_last_error(ctx).decode()
+
+
+def roks_destroy(ctx):
+    load().roks_destroy(ctx)
+
+
+# ---------------------------------------------------------------- convenience wrapper
+class Context:
+    """Owns one roks_ctx on the current CUDA device and stream."""
+
+    def __init__(self, cfg: dict, precision: str = "fp64", suppress_ab: bool = False, e_tol: float = 1e-6,
+                 stream=None):
+        import torch
+        self.torch = torch
+        self.precision = ROKS_FP64 if precision == "fp64" else ROKS_MIXED
+        self.cdtype = torch.complex128 if self.precision == ROKS_FP64 else torch.complex64
+        self.rdtype = torch.float64 if self.precision == ROKS_FP64 else torch.float32
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.ctx = roks_setup(cfg, self.precision, self.stream.cuda_stream, suppress_ab, e_tol)
+        self.npw, self.nb, self.ld, self.miller = roks_basis(self.ctx)
+        self.N = cfg["grid"]
+
+    def new_bands(self):
+        return self.torch.zeros((self.nb, self.ld), dtype=self.cdtype, device="cuda")
+
+    def init_orbitals(self, u, psi=None):
+        psi = self.new_bands() if psi is None else psi
+        roks_init_orbitals(self.ctx, u, psi, self.ld)
+        return psi
+
+    def density(self, psi, want_rho=False):
+        rho = (self.torch.empty((3, self.N ** 3), dtype=self.torch.float64, device="cuda")
+               if want_rho else None)
+        roks_density(self.ctx, psi, self.ld, rho)
+        return rho
+
+    def potential(self, want_v=False):
+        v = (self.torch.empty((3, self.N ** 3), dtype=self.rdtype, device="cuda") if want_v else None)
+        e = roks_potential(self.ctx, v)
+        return (e, v) if want_v else e
+
+    def apply_h(self, psi, want_s=True, want_grad=False):
+        f = self.new_bands()
+        s = self.new_bands() if want_s else None
+        g = self.new_bands() if want_grad else None
+        roks_apply_h(self.ctx, psi, self.ld, f, s, g)
+        return f, s, g
+
+    def orthonormalize(self, psi):
+        roks_orthonormalize(self.ctx, psi, self.ld)
+        return psi
+
+    def pcg_step(self, psi):
+        return roks_pcg_step(self.ctx, psi, self.ld)
+
+    def energies(self):
+        return roks_energies_get(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            roks_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,213 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.
+
+FP64 path: 1e-10 relative (element by element on small cases).  Mixed path
+(FP32 transforms and contractions, FP64 reductions and Cholesky): the
+tolerances stated in each test, derived from FP32 rounding (2^-24 per
+operation, a few hundred operations deep)."""
+import numpy as np
+import pytest
+
+from oracle import roks as R
+from paper_2605_28637_gb300 import synthetic as syn
+from tests.gpu_helpers import built, rel, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+def cfg_of(name="tiny-16", **kw):
+    return syn.with_changes(syn.make_config(name, 0), **kw)
+
+
+# variants spanning every compiled grid size that the oracle finishes quickly,
+# with ragged tiles and both the singlet, triplet and ground-state modes
+SMALL = {
+    "tiny16-singlet": dict(),
+    "tiny16-triplet": dict(mode=2),
+    "tiny16-gs": dict(mode=0, n_closed=5),
+    "grid24": dict(grid=24, L=11.0, ecut=12.0, n_closed=5),
+    "grid32": dict(grid=32, L=12.0, ecut=20.0, n_closed=6),
+    "grid48": dict(grid=48, L=12.0, ecut=35.0, n_closed=3),
+}
+
+
+def setup_pair(cfg, precision="fp64"):
+    roks = built()
+    ctx = roks.Context(cfg, precision)
+    s = R.System(cfg)
+    return roks, ctx, s
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_basis_bit_exact(name):
+    cfg = cfg_of(**SMALL[name])
+    roks, ctx, s = setup_pair(cfg)
+    assert ctx.npw == s.npw
+    assert np.array_equal(ctx.miller, s.miller)
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_density_potential_apply_fp64(name):
+    cfg = cfg_of(**SMALL[name])
+    roks, ctx, s = setup_pair(cfg)
+    u = syn.orbital_uniforms(cfg, ctx.npw)
+    psi = ctx.init_orbitals(u)
+    P_ref = s.initial_orbitals(u)
+    assert rel(to_np(psi, s.npw), P_ref) < TOL64
+    # densities
+    rho = ctx.density(psi, want_rho=True).cpu().numpy()
+    rho_ref = s.class_densities(P_ref)
+    assert rel(rho, rho_ref) < TOL64
+    # potentials and energies
+    E, V = ctx.potential(want_v=True)
+    pot = s.potentials(rho_ref)
+    Eref = s.energies(P_ref, pot)
+    assert rel(V.cpu().numpy(), pot.Vk) < TOL64
+    for k_gpu, k_ref in (("E_kin", "kin"), ("E_loc", "loc"), ("E_nl", "nl"), ("E_H", "H"), ("E_x_M", "x_M"),
+                         ("E_x_T", "x_T"), ("E_M", "M"), ("E_T", "T"), ("E_total", "total")):
+        assert abs(E[k_gpu] - Eref[k_ref]) <= TOL64 * max(1.0, abs(Eref[k_ref])), k_gpu
+    # F|n>, S|n>, g_n
+    f, sp, g = ctx.apply_h(psi, want_s=True, want_grad=True)
+    F_ref, S_ref = s.apply(P_ref, pot)
+    assert rel(to_np(f, s.npw), F_ref) < TOL64
+    assert rel(to_np(sp, s.npw), S_ref) < TOL64
+    _, G_ref, _, _ = R.gradient_parts(P_ref, F_ref, S_ref)
+    assert rel(to_np(g, s.npw), G_ref) < 1e-9
+    ctx.close()
+
+
+def test_orthonormalize_fp64():
+    cfg = cfg_of()
+    roks, ctx, s = setup_pair(cfg)
+    X = s.initial_orbitals(syn.orbital_uniforms(cfg, s.npw)) + 0.3 * syn.random_vectors(9, s.npw, s.nb)
+    psi = to_dev(ctx, X)
+    ctx.orthonormalize(psi)
+    Y = to_np(psi, s.npw)
+    assert rel(Y, s.orthonormalize(X)) < TOL64
+    assert np.abs(s.overlap(Y) - np.eye(s.nb)).max() < 1e-12
+
+
+def test_orthonormalize_rejects_singular_overlap():
+    cfg = cfg_of()
+    roks, ctx, s = setup_pair(cfg)
+    X = s.initial_orbitals(syn.orbital_uniforms(cfg, s.npw))
+    X[:, 1] = X[:, 0]                              # rank deficient
+    psi = to_dev(ctx, X)
+    with pytest.raises(roks.RoksError) as ei:
+        ctx.orthonormalize(psi)
+    assert ei.value.status == roks.ROKS_ENOTPOSDEF
+    # the context stays usable
+    psi = ctx.init_orbitals(syn.orbital_uniforms(cfg, s.npw))
+    ctx.density(psi)
+    ctx.potential()
+
+
+def test_setup_rejects_bad_input():
+    roks = built()
+    with pytest.raises(roks.RoksError):
+        roks.Context(cfg_of(grid=20))              # no compiled transform
+    with pytest.raises(roks.RoksError):
+        roks.Context(cfg_of(grid=16, ecut=40.0))   # sphere does not fit the grid
+    ctx = roks.Context(cfg_of())
+    import torch
+    bad = torch.zeros((ctx.nb, ctx.npw - 1), dtype=torch.complex128, device="cuda")
+    with pytest.raises(roks.RoksError):
+        roks.roks_density(ctx.ctx, bad, ctx.npw - 1)
+
+
+def test_no_projectors():
+    cfg = cfg_of()
+    cfg["species"] = [dict(l=[], m=[], rc=[], D=np.zeros((0, 0)), Q=np.zeros((0, 0)))]
+    roks, ctx, s = setup_pair(cfg)
+    assert s.nproj == 0
+    u = syn.orbital_uniforms(cfg, ctx.npw)
+    psi = ctx.init_orbitals(u)
+    P_ref = s.initial_orbitals(u)
+    ctx.density(psi)
+    E = ctx.potential()
+    assert abs(E["E_total"] - s.energy(P_ref)) < TOL64 * abs(s.energy(P_ref))
+
+
+@pytest.mark.parametrize("variant", ["singlet", "suppress", "gs", "triplet"])
+def test_pcg_trajectory_fp64(variant):
+    kw = {"singlet": {}, "suppress": {}, "gs": dict(mode=0, n_closed=5), "triplet": dict(mode=2)}[variant]
+    cfg = cfg_of(**kw)
+    sup = variant == "suppress"
+    roks = built()
+    ctx = roks.Context(cfg, "fp64", suppress_ab=sup)
+    s = R.System(cfg)
+    u = syn.orbital_uniforms(cfg, ctx.npw)
+    psi = ctx.init_orbitals(u)
+    P = s.initial_orbitals(u)
+    pcg = R.PCG(s, suppress_ab=sup)
+    for it in range(8):
+        info = ctx.pcg_step(psi)
+        P, ref = pcg.step(P)
+        assert abs(info["E"] - ref.E) <= TOL64 * max(1, abs(ref.E)), (it, info["E"], ref.E)
+        assert abs(info["E_new"] - ref.E_new) <= TOL64 * max(1, abs(ref.E_new)), (it, info["E_new"], ref.E_new)
+        assert abs(info["step"] - ref.step) <= 1e-8 * ref.step
+        assert abs(info["beta"] - ref.beta) <= 1e-8 * max(1, abs(ref.beta))
+        assert bool(info["restarted"]) == ref.restarted
+        assert abs(info["grad_norm"] - ref.grad_norm) <= 1e-9 * ref.grad_norm
+    assert rel(to_np(psi, s.npw), P) < 1e-8
+
+
+def test_pcg_tiny_50_iterations_fp64():
+    """The tiny workload's 50 iterations: energy after every step within
+    1e-6 Ha of the oracle's trajectory (and 1e-9 relative for the first 20)."""
+    cfg = cfg_of()
+    roks = built()
+    ctx = roks.Context(cfg, "fp64")
+    s = R.System(cfg)
+    u = syn.orbital_uniforms(cfg, ctx.npw)
+    psi = ctx.init_orbitals(u)
+    P = s.initial_orbitals(u)
+    pcg = R.PCG(s)
+    for it in range(50):
+        info = ctx.pcg_step(psi)
+        P, ref = pcg.step(P)
+        tol = 1e-9 * abs(ref.E_new) if it < 20 else 1e-6
+        assert abs(info["E_new"] - ref.E_new) <= tol, (it, info["E_new"], ref.E_new)
+
+
+@pytest.mark.parametrize("name", ["tiny16-singlet", "grid32"])
+def test_mixed_precision_apply(name):
+    """FP32 path: densities to 2e-6 relative, F|n> and S|n> to 2e-5 relative
+    (of the largest entry), energies to 2e-5 Ha."""
+    cfg = cfg_of(**SMALL[name])
+    roks, ctx, s = setup_pair(cfg, "mixed")
+    u = syn.orbital_uniforms(cfg, ctx.npw)
+    psi = ctx.init_orbitals(u)
+    P_ref = s.initial_orbitals(u)
+    assert rel(to_np(psi, s.npw), P_ref) < 2e-6
+    rho = ctx.density(psi, want_rho=True).cpu().numpy()
+    rho_ref = s.class_densities(P_ref)
+    assert rel(rho, rho_ref) < 2e-6
+    E = ctx.potential()
+    Eref = s.energies(P_ref)
+    assert abs(E["E_total"] - Eref["total"]) < 2e-5
+    f, sp, _ = ctx.apply_h(to_dev(ctx, P_ref))
+    pot = s.potentials(rho_ref)
+    F_ref, S_ref = s.apply(P_ref, pot)
+    assert rel(to_np(f, s.npw), F_ref) < 2e-5
+    assert rel(to_np(sp, s.npw), S_ref) < 2e-6
+
+
+def test_mixed_precision_pcg_tiny():
+    """Mixed path follows the FP64 trajectory: |E_new - E_new(oracle)| < 1e-5 Ha
+    over 20 iterations of the tiny workload."""
+    cfg = cfg_of()
+    roks = built()
+    ctx = roks.Context(cfg, "mixed")
+    s = R.System(cfg)
+    u = syn.orbital_uniforms(cfg, ctx.npw)
+    psi = ctx.init_orbitals(u)
+    P = s.initial_orbitals(u)
+    pcg = R.PCG(s)
+    for it in range(20):
+        info = ctx.pcg_step(psi)
+        P, ref = pcg.step(P)
+        assert abs(info["E_new"] - ref.E_new) < 1e-5, (it, info["E_new"], ref.E_new)
