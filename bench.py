@@ -1,0 +1,426 @@
+"""Benchmark of the ROKS plane-wave hot path on GB300.
+
+A step is one PCG iteration (every row of the hot path: density, Hartree and
+Slater potentials, class potentials, F^n|n> and S|n> for all bands,
+subspace matrices, gradient, TPA preconditioner, Fletcher-Reeves direction,
+trial and final rotation + Cholesky orthonormalisation with their density
+and energy passes).  The metric counts the band applications F^n|psi_n>
+per second (one per band per step) and also reports seconds per PCG
+iteration and seconds to converge (|dE| < 1e-6 Ha twice), mixed precision
+against the plain FP64 GPU path.
+
+Default workload: organic-molecule box (20 Bohr cell, 96^3 grid, Ecut 20 Ha,
+34265 plane waves, 30 atoms with 172 projectors, 40 closed + 2 open bands),
+synthetic seeded inputs.  Multi-GPU (torchrun): independent replicas, one
+per rank (seed = rank), no collective on the data path.
+
+--impl reference times the FP64 CPU oracle (the only reference there is) on
+a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ROKS band-H|ψ> applies/s; s/PCG-to-1e-6 Ha, chosen vs plain FP64 on 1 GB300"
+UNIT = "band-applies/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="organic-96")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--converge-iters", type=int, default=400,
+                    help="iteration cap of the time-to-convergence runs (0 skips them)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", FALLBACK_HBM_GBS)), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, gpu_index=None):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                if gpu_index is not None and parts[0] != str(gpu_index):
+                    continue
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- algorithmic bytes per launch
+def algorithmic_bytes(ctx, cfg, family: str, csize: int, rsize: int):
+    """Compulsory DRAM bytes of one launch of a kernel family (all bands)."""
+    N = cfg["grid"]
+    nb, npw = ctx.nb, ctx.npw
+    geo = _geometry(ctx.miller)
+    npl, ncol = geo["np"], geo["ncol"]
+    planes = nb * npl * N * N * csize
+    cols = nb * ncol * N * csize
+    band = nb * npw * csize
+    return {
+        "fft_x_apply": 2 * planes + 3 * N ** 3 * rsize,
+        "fft_x_density": planes + 3 * N ** 3 * 8,
+        "fft_y_inv": cols + planes,
+        "fft_y_fwd": planes + cols,
+        "fft_z_inv": band + cols,
+        "fft_z_fwd": cols + 2 * band,
+    }.get(family)
+
+
+def _geometry(miller):
+    ij = {(int(a), int(b)) for a, b, _ in miller}
+    i = {int(a) for a, _, _ in miller}
+    return {"ncol": len(ij), "np": len(i)}
+
+
+def traffic_record(family):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f)
+    ent = rec.get("kernels", {}).get(family)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, ent["source"])
+    if not os.path.exists(src):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if sha != ent.get("source_sha"):
+        return None
+    return float(ent["bytes_per_launch"])
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+def oracle_sample(cfg, n_bands_timed=4, reps=1):
+    """F^n|n> of a few bands with the oracle (FP64 numpy) at a fixed
+    potential; returns (band-applies/s, seconds, description)."""
+    from oracle import roks as R
+    from paper_2605_28637_gb300 import synthetic as syn
+    s = R.System(cfg)
+    u = syn.orbital_uniforms(cfg, s.npw)
+    c = (u[..., 0] + 1j * u[..., 1]).T / (1.0 + s.g2)[:, None]
+    nt = min(n_bands_timed, s.nb)
+    # the potential of the first two bands stands in for the self-consistent
+    # one (the timing does not depend on its values)
+    rho = np.zeros((3, s.N ** 3))
+    for n in range(min(2, s.nb)):
+        psi = s.to_real(c[:, n])
+        rho[0] += (psi.conj() * psi).real
+    pot = s.potentials(rho)
+    X = c[:, :nt]
+    cls = s.cls[:nt]
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        s.apply(X, pot, classes=cls)
+    dt = time.perf_counter() - t0
+    desc = (f"F^n|n> (kinetic+local+non-local) of {nt} bands x {reps} of {cfg['name']} "
+            f"({cfg['grid']}^3 grid, {s.npw} plane waves, {s.nproj} projectors), FP64 numpy oracle, fixed potential")
+    return nt * reps / dt, dt, desc
+
+
+def cpu_cores():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        blas = max([i.get("num_threads", 1) for i in info] or [1])
+        return int(blas)
+    except Exception:
+        return 1
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2605_28637_gb300 import synthetic as syn
+    cfg = syn.make_config(args.workload, 0)
+    # each step: F^n|n> of 2 bands of the workload (bounded sample)
+    from oracle import roks as R
+    s = R.System(cfg)
+    u = syn.orbital_uniforms(cfg, s.npw)
+    c = (u[..., 0] + 1j * u[..., 1]).T / (1.0 + s.g2)[:, None]
+    rho = np.zeros((3, s.N ** 3))
+    for n in range(min(2, s.nb)):
+        psi = s.to_real(c[:, n])
+        rho[0] += (psi.conj() * psi).real
+    pot = s.potentials(rho)
+    X = c[:, :2]
+    for _ in range(args.warmup):
+        s.apply(X, pot, classes=s.cls[:2])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.apply(X, pot, classes=s.cls[:2])
+    dt = time.perf_counter() - t0
+    value = 2 * args.steps / dt
+    sample = (f"each step: F^n|n> of 2 bands of {cfg['name']} ({cfg['grid']}^3, {s.npw} plane waves), "
+              "FP64 numpy oracle on the host cores, fixed potential")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": cfg["name"], "grid": cfg["grid"], "bands": s.nb, "plane_waves": s.npw},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def time_pcg(ctx, psi, steps, torch, profile=False):
+    from paper_2605_28637_gb300 import roks
+    st = ctx.stream
+    if profile:
+        roks.roks_profile_enable(ctx.ctx, 1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    infos = []
+    for _ in range(steps):
+        infos.append(ctx.pcg_step(psi))
+    e1.record(st)
+    torch.cuda.synchronize()
+    prof = None
+    if profile:
+        prof = roks.roks_profile_read(ctx.ctx)
+        roks.roks_profile_enable(ctx.ctx, 0)
+    return e0.elapsed_time(e1), infos, prof
+
+
+def converge(cfg, precision, cap, torch):
+    """Seconds and iterations of PCG from the seeded start to |dE| < 1e-6 Ha twice."""
+    from paper_2605_28637_gb300 import roks, synthetic as syn
+    ctx = roks.Context(cfg, precision, e_tol=1e-6)
+    psi = ctx.init_orbitals(syn.orbital_uniforms(cfg, ctx.npw))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    it, info = 0, None
+    for it in range(1, cap + 1):
+        info = ctx.pcg_step(psi)
+        if info["converged"]:
+            break
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    out = {"seconds": dt, "iterations": it, "converged": bool(info and info["converged"]),
+           "E_final": info["E_new"] if info else None, "s_per_iter": dt / max(it, 1)}
+    ctx.close()
+    return out
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__ as g
+    if rank == 0:
+        g.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2605_28637_gb300 import roks, synthetic as syn
+    cfg = syn.make_config(args.workload, rank)
+    ctx = roks.Context(cfg, args.precision)
+    u = syn.orbital_uniforms(cfg, ctx.npw)
+    psi = ctx.init_orbitals(u)
+    for _ in range(args.warmup):
+        ctx.pcg_step(psi)
+    # ---- timed region: K PCG steps, inputs resident in HBM
+    clocks = ClockSampler()
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ms, infos, prof = time_pcg(ctx, psi, args.steps, torch, profile=True)
+    if world > 1:
+        torch.distributed.barrier()
+    ck = clocks.stop(gpu_index=None if world == 1 else local)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = ctx.nb * args.steps * world / (ms_max / 1000.0)
+    # ---- apply-only throughput (roks_apply_h over all bands)
+    f = ctx.new_bands()
+    sp = ctx.new_bands()
+    for _ in range(3):
+        roks.roks_apply_h(ctx.ctx, psi, ctx.ld, f, sp, None)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(ctx.stream)
+    n_apply = 20
+    for _ in range(n_apply):
+        roks.roks_apply_h(ctx.ctx, psi, ctx.ld, f, sp, None)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    apply_ms = e0.elapsed_time(e1) / n_apply
+    # ---- end to end: host orbitals in pinned memory, copied in and out each step
+    host = torch.empty_like(psi, device="cpu").pin_memory()
+    host.copy_(psi)
+    e2e_steps = max(3, args.steps // 4)
+    torch.cuda.synchronize()
+    e0.record(ctx.stream)
+    for _ in range(e2e_steps):
+        psi.copy_(host, non_blocking=True)
+        ctx.pcg_step(psi)
+        host.copy_(psi, non_blocking=True)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    t2 = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t2, op=torch.distributed.ReduceOp.MAX)
+    e2e_value = ctx.nb * e2e_steps * world / (float(t2.item()) / 1000.0)
+    bytes_psi = psi.numel() * psi.element_size()
+    # ---- roofline of the dominant kernel family
+    csize = 16 if args.precision == "fp64" else 8
+    rsize = 8 if args.precision == "fp64" else 4
+    kernels = [e for e in prof if e["name"] == "kernel_launches"]
+    prof = [e for e in prof if e["name"] != "kernel_launches"]
+    total_prof = sum(e["ms"] for e in prof) or 1.0
+    hbm, peak_kind = peaks()
+    dom = None
+    for e in sorted(prof, key=lambda e: -e["ms"]):
+        if algorithmic_bytes(ctx, cfg, e["name"], csize, rsize) is not None:
+            dom = e
+            break
+    top = max(prof, key=lambda e: e["ms"]) if prof else None
+    roofline = None
+    if dom is not None:
+        per_launch_ms = dom["ms"] / dom["launches"]
+        alg = algorithmic_bytes(ctx, cfg, dom["name"], csize, rsize)
+        achieved = alg / (per_launch_ms / 1000.0) / 1e9
+        roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm, "peak_kind": f"{peak_kind} (copy bandwidth)",
+                    "traffic": traffic_record(dom["name"]), "algorithmic_bytes_per_launch": alg,
+                    "ms_per_launch": per_launch_ms, "share_of_step": dom["ms"] / total_prof}
+    launches = sum(e["launches"] for e in prof)
+    # ---- time to convergence: chosen (mixed) vs plain FP64
+    pcg = None
+    if args.converge_iters > 0 and rank == 0:
+        mixed = converge(cfg, "mixed", args.converge_iters, torch)
+        fp64 = converge(cfg, "fp64", args.converge_iters, torch)
+        pcg = {"mixed": mixed, "fp64": fp64,
+               "speedup_s_per_iter": fp64["s_per_iter"] / mixed["s_per_iter"],
+               "dE_mixed_vs_fp64_final": (mixed["E_final"] - fp64["E_final"])
+               if mixed["E_final"] is not None and fp64["E_final"] is not None else None}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, desc = oracle_sample(cfg, n_bands_timed=4)
+        cpu = {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": desc,
+               "seconds": dt}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": cfg["name"], "grid": cfg["grid"], "ecut_ha": cfg["ecut"], "bands": ctx.nb,
+                       "plane_waves": ctx.npw, "atoms": len(cfg["atoms"]),
+                       "precision": args.precision, "parallelism": f"replicas{world}",
+                       "l2": "per-step working set above the 129 MB L2 (plane buffers, projectors, band blocks)"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bytes_psi,
+                    "d2h_bytes_per_step": bytes_psi},
+            "gpu_launches": None,
+            "clocks": ck,
+            "apply_only": {"value": ctx.nb / (apply_ms / 1000.0), "unit": UNIT, "ms_per_apply_all_bands": apply_ms},
+            "pcg": pcg,
+            "profile": {e["name"]: {"launches": e["launches"], "ms": e["ms"]} for e in prof},
+            "E_last": infos[-1]["E_new"] if infos else None,
+        }
+        line["gpu_launches"] = kernels[0]["launches"] if kernels else None
+        line["kernel_groups_timed"] = launches
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -215,7 +215,9 @@ typedef struct {
 ROKS_API roks_status roks_profile_enable(roks_ctx* ctx, int enable);
 
 /* Synchronises the stream, writes up to cap entries to out (host), sets
- * *count to the number of families recorded and clears the record. */
+ * *count to the number of entries and clears the record.  The last entry,
+ * "kernel_launches", counts every kernel the library launched (in any
+ * context of the process) since profiling was enabled, with ms = 0. */
 ROKS_API roks_status roks_profile_read(roks_ctx* ctx, roks_profile_entry* out, int cap,
                                        int* count);
 

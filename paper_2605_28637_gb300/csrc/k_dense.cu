@@ -4,146 +4,217 @@
 // (Cholesky inverse, Taylor exponential).
 //
 // The contractions here are SIMT tiled kernels with register blocking.
+#include <atomic>
+
 #include "roks_impl.cuh"
 
 namespace roks {
 
-// ------------------------------------------------------------------ C = A^H B, split over K
-// A: K x M, B: K x N (column major).  Each block: 32 x 32 outputs over one
-// K chunk; 256 threads, 2 x 2 outputs each.  Chunk sums are exact FP64
-// additions of FP32 (or FP64) partial sums.
-constexpr int CN_T = 32, CN_KT = 16, CN_KC = 1024;
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launches_take() { return g_launches.exchange(0); }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_gemm_cn(int M, int N, int K, const c2<T>* __restrict__ A, int64_t lda,
-                                                 const c2<T>* __restrict__ B, int64_t ldb, double2* __restrict__ part) {
+// ------------------------------------------------------------------ C = A^H B, split over K
+// A: K x M, B: K x N (column major).  A block of 16 x 16 threads owns an
+// output tile of (16 RM) x (16 RN) and one K chunk; each thread keeps an
+// RM x RN register tile.  Chunk partials are written in FP64 and summed in a
+// fixed order by k_chunk_sum.
+template <typename T> struct CnTile { static constexpr int KT = sizeof(T) == 4 ? 32 : 16; };
+constexpr int CN_KT = 32;   // chunk granularity (a multiple of every k tile)
+
+template <typename T, int RM, int RN>
+__global__ void __launch_bounds__(256) k_gemm_cn(int M, int N, int K, int kchunk, const c2<T>* __restrict__ A,
+                                                 int64_t lda, const c2<T>* __restrict__ B, int64_t ldb,
+                                                 double2* __restrict__ part) {
     using V = c2<T>;
-    __shared__ V As[CN_KT][CN_T + 1];
-    __shared__ V Bs[CN_KT][CN_T + 1];
+    constexpr int TM = 16 * RM, TN = 16 * RN;
+    constexpr int KT = CnTile<T>::KT;
+    __shared__ V As[KT][TM + 1];
+    __shared__ V Bs[KT][TN + 1];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int m0 = blockIdx.x * CN_T, n0 = blockIdx.y * CN_T;
-    const int kbeg = blockIdx.z * CN_KC, kend = min(K, kbeg + CN_KC);
-    V acc[2][2];
+    const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
+    const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+    V acc[RM][RN];
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+    for (int i = 0; i < RM; ++i)
 #pragma unroll
-        for (int b = 0; b < 2; ++b) acc[a][b] = mk<T>(T(0), T(0));
-    for (int k0 = kbeg; k0 < kend; k0 += CN_KT) {
+        for (int j = 0; j < RN; ++j) acc[i][j] = mk<T>(T(0), T(0));
+    constexpr int RS = 256 / KT;                                    // rows per load pass
+    const int lk = threadIdx.x % KT, lr = threadIdx.x / KT;
+    for (int k0 = kbeg; k0 < kend; k0 += KT) {
+        const int k = k0 + lk;
+        const bool kin = k < kend;
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int t = threadIdx.x + q * 256;
-            const int kk = t & 15, mm = t >> 4;      // 16 x 32
-            const int k = k0 + kk;
-            const int m = m0 + mm, n = n0 + mm;
-            As[kk][mm] = (k < kend && m < M) ? A[(int64_t)m * lda + k] : mk<T>(T(0), T(0));
-            Bs[kk][mm] = (k < kend && n < N) ? B[(int64_t)n * ldb + k] : mk<T>(T(0), T(0));
+        for (int r = lr; r < TM; r += RS) {
+            const int m = m0 + r;
+            As[lk][r] = (kin && m < M) ? A[(int64_t)m * lda + k] : mk<T>(T(0), T(0));
+        }
+#pragma unroll
+        for (int r = lr; r < TN; r += RS) {
+            const int n = n0 + r;
+            Bs[lk][r] = (kin && n < N) ? B[(int64_t)n * ldb + k] : mk<T>(T(0), T(0));
         }
         __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < KT; ++kk) {
+            V a[RM], b[RN];
 #pragma unroll
-        for (int kk = 0; kk < CN_KT; ++kk) {
-            V a0 = As[kk][ty], a1 = As[kk][ty + 16];
-            V b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
-            acc[0][0] = cadd(acc[0][0], cmulc(a0, b0));
-            acc[0][1] = cadd(acc[0][1], cmulc(a0, b1));
-            acc[1][0] = cadd(acc[1][0], cmulc(a1, b0));
-            acc[1][1] = cadd(acc[1][1], cmulc(a1, b1));
+            for (int i = 0; i < RM; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < RN; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < RM; ++i)
+#pragma unroll
+                for (int j = 0; j < RN; ++j) {
+                    acc[i][j].x += a[i].x * b[j].x + a[i].y * b[j].y;
+                    acc[i][j].y += a[i].x * b[j].y - a[i].y * b[j].x;
+                }
         }
         __syncthreads();
     }
     double2* P = part + (int64_t)blockIdx.z * M * N;
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+    for (int i = 0; i < RM; ++i)
 #pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const int m = m0 + ty + 16 * a, n = n0 + tx + 16 * b;
-            if (m < M && n < N) P[(int64_t)n * M + m] = make_double2(double(acc[a][b].x), double(acc[a][b].y));
+        for (int j = 0; j < RN; ++j) {
+            const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+            if (m < M && n < N) P[(int64_t)n * M + m] = make_double2(double(acc[i][j].x), double(acc[i][j].y));
         }
 }
 
+// One warp per output element sums the chunk partials in a fixed order.
 __global__ void k_chunk_sum(int M, int N, int nchunk, const double2* __restrict__ part, double2* __restrict__ C,
                             int ldc) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= M * N) return;
-    const int m = idx % M, n = idx / M;
-    double2 s = make_double2(0.0, 0.0);
-    for (int c = 0; c < nchunk; ++c) {
-        const double2 v = part[(int64_t)c * M * N + idx];
-        s.x += v.x;
-        s.y += v.y;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= M * N) return;
+    double sx = 0.0, sy = 0.0;
+    for (int c = lane; c < nchunk; c += 32) {
+        const double2 v = part[(int64_t)c * M * N + w];
+        sx += v.x;
+        sy += v.y;
     }
-    C[(int64_t)n * ldc + m] = s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    }
+    if (lane == 0) C[(int64_t)(w / M) * ldc + (w % M)] = make_double2(sx, sy);
 }
 
+namespace {
+struct CnPlan {
+    int rm, rn, mt, nt, kchunk, nchunk;
+};
+CnPlan cn_plan(int M, int N, int K) {
+    CnPlan p;
+    p.rm = M <= 16 ? 1 : (M <= 32 ? 2 : 3);
+    p.rn = N <= 16 ? 1 : (N <= 32 ? 2 : 3);
+    p.mt = (M + 16 * p.rm - 1) / (16 * p.rm);
+    p.nt = (N + 16 * p.rn - 1) / (16 * p.rn);
+    const int tiles = p.mt * p.nt;
+    // about four blocks per SM over the whole grid, chunks a multiple of the k tile
+    const int want = tiles >= 608 ? 1 : (608 + tiles - 1) / tiles;
+    int kc = (K + want - 1) / want;
+    kc = ((kc + CN_KT - 1) / CN_KT) * CN_KT;
+    if (kc < CN_KT) kc = CN_KT;
+    p.kchunk = kc;
+    p.nchunk = K > 0 ? (K + kc - 1) / kc : 1;
+    return p;
+}
+}  // namespace
+
 size_t gemm_cn_work(int M, int N, int K) {
-    const int nchunk = (K + CN_KC - 1) / CN_KC;
-    return (size_t)nchunk * M * N;
+    const CnPlan p = cn_plan(M, N, K);
+    return (size_t)p.nchunk * M * N;
 }
 
 template <typename T>
 void gemm_cn(int M, int N, int K, const c2<T>* A, int64_t lda, const c2<T>* B, int64_t ldb, double2* C, int ldc,
              double2* work, size_t work_elems, cudaStream_t st) {
     if (M <= 0 || N <= 0) return;
-    const int nchunk = K > 0 ? (K + CN_KC - 1) / CN_KC : 1;
+    const CnPlan p = cn_plan(M, N, K);
     (void)work_elems;
-    dim3 g((M + CN_T - 1) / CN_T, (N + CN_T - 1) / CN_T, nchunk);
-    if (K > 0) k_gemm_cn<T><<<g, 256, 0, st>>>(M, N, K, A, lda, B, ldb, work);
-    else cudaMemsetAsync(work, 0, sizeof(double2) * M * N, st);
-    k_chunk_sum<<<(M * N + 255) / 256, 256, 0, st>>>(M, N, nchunk, work, C, ldc);
+    dim3 g(p.mt, p.nt, p.nchunk);
+    if (K <= 0) {
+        cudaMemsetAsync(work, 0, sizeof(double2) * M * N, st);
+    } else {
+#define CN_CASE(RM_, RN_)                                                                                   \
+    if (p.rm == RM_ && p.rn == RN_)                                                                       \
+        roks::count_launch(), k_gemm_cn<T, RM_, RN_><<<g, 256, 0, st>>>(M, N, K, p.kchunk, A, lda, B, ldb, work);
+        CN_CASE(1, 1) CN_CASE(1, 2) CN_CASE(1, 3) CN_CASE(2, 1) CN_CASE(2, 2) CN_CASE(2, 3) CN_CASE(3, 1)
+        CN_CASE(3, 2) CN_CASE(3, 3)
+#undef CN_CASE
+    }
+    const long long thr = (long long)M * N * 32;
+    roks::count_launch(), k_chunk_sum<<<(unsigned)((thr + 255) / 256), 256, 0, st>>>(M, N, p.nchunk, work, C, ldc);
 }
 
 // ------------------------------------------------------------------ C = alpha A B + beta C
 // A: M x K (tall, column major, element type T), B: K x N FP64 (small).
-// Block: 64 rows x 32 columns; thread (tx < 64, ty < 4) owns rows m0+tx and
-// columns n0 + ty + 4 c, c < 8.
-constexpr int NN_TM = 64, NN_TN = 32, NN_KT = 16;
+// Block: 32 x 8 threads, tile (32 RM) rows x (8 RN) columns; thread (tx, ty)
+// owns rows m0 + tx + 32 i and columns n0 + ty + 8 j.
+constexpr int NN_KT = 16;
 
-template <typename T>
+template <typename T, int RM, int RN>
 __global__ void __launch_bounds__(256) k_gemm_nn(int M, int N, int K, const c2<T>* __restrict__ A, int64_t lda,
                                                  const double2* __restrict__ B, int ldb, c2<T>* __restrict__ C,
                                                  int64_t ldc, T alpha, T beta) {
     using V = c2<T>;
-    __shared__ V As[NN_KT][NN_TM];
-    __shared__ V Bs[NN_KT][NN_TN];
-    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
-    const int m0 = blockIdx.x * NN_TM, n0 = blockIdx.y * NN_TN;
-    V acc[8];
+    constexpr int TM = 32 * RM, TN = 8 * RN;
+    __shared__ V As[NN_KT][TM];
+    __shared__ V Bs[NN_KT][TN];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
+    V acc[RM][RN];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[c] = mk<T>(T(0), T(0));
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+        for (int j = 0; j < RN; ++j) acc[i][j] = mk<T>(T(0), T(0));
     for (int k0 = 0; k0 < K; k0 += NN_KT) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int t = threadIdx.x + q * 256;       // 16 x 64
-            const int mm = t & 63, kk = t >> 6;
+        for (int t = threadIdx.x; t < NN_KT * TM; t += 256) {
+            const int mm = t % TM, kk = t / TM;
             const int m = m0 + mm, k = k0 + kk;
             As[kk][mm] = (m < M && k < K) ? A[(int64_t)k * lda + m] : mk<T>(T(0), T(0));
         }
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int t = threadIdx.x + q * 256;       // 16 x 32
-            const int kk = t & 15, nn = t >> 4;
+        for (int t = threadIdx.x; t < NN_KT * TN; t += 256) {
+            const int kk = t % NN_KT, nn = t / NN_KT;
             const int k = k0 + kk, n = n0 + nn;
-            double2 b = (k < K && n < N) ? B[(int64_t)n * ldb + k] : make_double2(0.0, 0.0);
+            const double2 b = (k < K && n < N) ? B[(int64_t)n * ldb + k] : make_double2(0.0, 0.0);
             Bs[kk][nn] = mk<T>(T(b.x), T(b.y));
         }
         __syncthreads();
-#pragma unroll
+#pragma unroll 4
         for (int kk = 0; kk < NN_KT; ++kk) {
-            const V a = As[kk][tx];
+            V a[RM], b[RN];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) acc[c] = cadd(acc[c], cmul(a, Bs[kk][ty + 4 * c]));
+            for (int i = 0; i < RM; ++i) a[i] = As[kk][tx + 32 * i];
+#pragma unroll
+            for (int j = 0; j < RN; ++j) b[j] = Bs[kk][ty + 8 * j];
+#pragma unroll
+            for (int i = 0; i < RM; ++i)
+#pragma unroll
+                for (int j = 0; j < RN; ++j) {
+                    acc[i][j].x += a[i].x * b[j].x - a[i].y * b[j].y;
+                    acc[i][j].y += a[i].x * b[j].y + a[i].y * b[j].x;
+                }
         }
         __syncthreads();
     }
-    const int m = m0 + tx;
-    if (m >= M) return;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const int n = n0 + ty + 4 * c;
-        if (n < N) {
-            V* dst = C + (int64_t)n * ldc + m;
-            V r = cscale(acc[c], alpha);
-            if (beta != T(0)) r = cadd(r, cscale(*dst, beta));
-            *dst = r;
+    for (int i = 0; i < RM; ++i) {
+        const int m = m0 + tx + 32 * i;
+        if (m >= M) continue;
+#pragma unroll
+        for (int j = 0; j < RN; ++j) {
+            const int n = n0 + ty + 8 * j;
+            if (n < N) {
+                V* dst = C + (int64_t)n * ldc + m;
+                V r = cscale(acc[i][j], alpha);
+                if (beta != T(0)) r = cadd(r, cscale(*dst, beta));
+                *dst = r;
+            }
         }
     }
 }
@@ -152,8 +223,13 @@ template <typename T>
 void gemm_nn(int M, int N, int K, const c2<T>* A, int64_t lda, const double2* B, int ldb, c2<T>* C, int64_t ldc,
              double alpha, double beta, cudaStream_t st) {
     if (M <= 0 || N <= 0) return;
-    dim3 g((M + NN_TM - 1) / NN_TM, (N + NN_TN - 1) / NN_TN);
-    k_gemm_nn<T><<<g, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, T(alpha), T(beta));
+    const int rn = N <= 8 ? 1 : (N <= 16 ? 2 : (N <= 32 ? 4 : 6));
+    constexpr int RM = 4;
+    dim3 g((M + 32 * RM - 1) / (32 * RM), (N + 8 * rn - 1) / (8 * rn));
+#define NN_CASE(RN_)                                                                                            \
+    if (rn == RN_) roks::count_launch(), k_gemm_nn<T, RM, RN_><<<g, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, T(alpha), T(beta));
+    NN_CASE(1) NN_CASE(2) NN_CASE(4) NN_CASE(6)
+#undef NN_CASE
 }
 
 template void gemm_cn<float>(int, int, int, const float2*, int64_t, const float2*, int64_t, double2*, int,
@@ -166,14 +242,16 @@ template void gemm_nn<double>(int, int, int, const double2*, int64_t, const doub
                               double, double, cudaStream_t);
 
 // ------------------------------------------------------------------ small FP64 matrices
+// One warp per output element; the lanes split K and reduce with shuffles.
 __global__ void k_small_gemm(int M, int N, int K, const double2* __restrict__ A, int lda, int ca,
                              const double2* __restrict__ B, int ldb, int cb, double2* __restrict__ C, int ldc,
                              double alpha, double beta) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= M * N) return;
-    const int m = idx % M, n = idx / M;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= M * N) return;
+    const int m = warp % M, n = warp / M;
     double sr = 0.0, si = 0.0;
-    for (int k = 0; k < K; ++k) {
+    for (int k = lane; k < K; k += 32) {
         double2 a = ca ? A[(int64_t)m * lda + k] : A[(int64_t)k * lda + m];
         double2 b = cb ? B[(int64_t)k * ldb + n] : B[(int64_t)n * ldb + k];
         if (ca) a.y = -a.y;
@@ -181,6 +259,12 @@ __global__ void k_small_gemm(int M, int N, int K, const double2* __restrict__ A,
         sr += a.x * b.x - a.y * b.y;
         si += a.x * b.y + a.y * b.x;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    if (lane != 0) return;
     double2* c = C + (int64_t)n * ldc + m;
     double2 r = make_double2(alpha * sr, alpha * si);
     if (beta != 0.0) { r.x += beta * c->x; r.y += beta * c->y; }
@@ -191,7 +275,92 @@ __global__ void k_small_gemm(int M, int N, int K, const double2* __restrict__ A,
 void small_gemm(int M, int N, int K, const double2* A, int lda, bool ca, const double2* B, int ldb, bool cb,
                 double2* C, int ldc, double alpha, double beta, cudaStream_t st) {
     if (M <= 0 || N <= 0) return;
-    k_small_gemm<<<(M * N + 127) / 128, 128, 0, st>>>(M, N, K, A, lda, ca, B, ldb, cb, C, ldc, alpha, beta);
+    const long long threads = (long long)M * N * 32;
+    roks::count_launch(), k_small_gemm<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(M, N, K, A, lda, ca, B, ldb, cb, C, ldc, alpha, beta);
+}
+
+// Cholesky inverse held in shared memory (n <= kSmallN), FP64: right-looking
+// factorisation O = L L^H (two barriers per column), then X = L^{-1} by
+// forward substitution with one warp per column (lanes split the dot
+// products); LinvH = X^H.
+constexpr int kSmallN = 64;
+
+__global__ void __launch_bounds__(1024) k_cholesky_small(int n, const double2* __restrict__ O,
+                                                         double2* __restrict__ LinvH, int* flag) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2* L = reinterpret_cast<double2*>(smem_raw);          // n x n, column major
+    double2* X = L + n * n;                                      // n x n, column major
+    __shared__ int bad;
+    __shared__ double dinv[kSmallN];                             // 1 / L_jj
+    if (threadIdx.x == 0) bad = 0;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        L[idx] = O[idx];
+        X[idx] = make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    // FP64 throughput is a per-SM resource: the pivot square root and
+    // reciprocal are computed once, by one thread, not by every thread.
+    for (int j = 0; j < n; ++j) {
+        if (threadIdx.x == 0) {
+            double d = L[j * n + j].x;
+            if (!(d > 0.0)) {
+                if (!bad) bad = j + 1;
+                d = 1.0;
+            }
+            const double piv = sqrt(d);
+            L[j * n + j] = make_double2(piv, 0.0);
+            dinv[j] = 1.0 / piv;
+        }
+        __syncthreads();
+        const double inv = dinv[j];
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+            const double2 v = L[j * n + i];
+            L[j * n + i] = make_double2(v.x * inv, v.y * inv);
+        }
+        __syncthreads();
+        // trailing update A_ik -= L_ij conj(L_kj), j < k <= i
+        const int m = n - j - 1;
+        for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+            const int k = t / m;
+            const int i = t - k * m;
+            if (k > i) continue;
+            const double2 a = L[j * n + j + 1 + i], b = L[j * n + j + 1 + k];
+            double2 c = L[(j + 1 + k) * n + j + 1 + i];
+            c.x -= a.x * b.x + a.y * b.y;
+            c.y -= a.y * b.x - a.x * b.y;
+            L[(j + 1 + k) * n + j + 1 + i] = c;
+        }
+        __syncthreads();
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int c = warp; c < n; c += nw) {
+        for (int i = c; i < n; ++i) {
+            double sr = 0.0, si = 0.0;
+            for (int k = c + lane; k < i; k += 32) {
+                const double2 l = L[k * n + i], x = X[c * n + k];
+                sr += l.x * x.x - l.y * x.y;
+                si += l.x * x.y + l.y * x.x;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                si += __shfl_xor_sync(0xffffffffu, si, o);
+            }
+            if (lane == 0) {
+                const double di = dinv[i];
+                X[c * n + i] = make_double2(((i == c) ? 1.0 - sr : -sr) * di, -si * di);
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    // LinvH (row c, column i) = conj X (row i, column c)
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int c = idx % n, i = idx / n;
+        const double2 x = X[c * n + i];
+        LinvH[idx] = make_double2(x.x, -x.y);
+    }
+    if (threadIdx.x == 0 && bad) flag[0] = bad;
 }
 
 // Cholesky O = L L^H (Crout, column by column) and the inverse of L, one
@@ -254,7 +423,13 @@ __global__ void __launch_bounds__(1024) k_cholesky_inverse(int n, const double2*
 }
 
 void cholesky_inverse(int n, const double2* O, double2* Lw, double2* LinvH, int* flag, cudaStream_t st) {
-    k_cholesky_inverse<<<1, 1024, 0, st>>>(n, O, Lw, LinvH, flag);
+    if (n <= kSmallN) {
+        const size_t sm = sizeof(double2) * 2 * n * n;
+        if (sm > 48 * 1024) cudaFuncSetAttribute(k_cholesky_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        roks::count_launch(), k_cholesky_small<<<1, 1024, sm, st>>>(n, O, LinvH, flag);
+        return;
+    }
+    roks::count_launch(), k_cholesky_inverse<<<1, 1024, 0, st>>>(n, O, Lw, LinvH, flag);
 }
 
 // ------------------------------------------------------------------ exp(s A)
@@ -337,21 +512,121 @@ __global__ void k_expm_square(int n, const double2* __restrict__ E, double2* __r
     Eout[idx] = make_double2(sr, si);
 }
 
+// exp(s A) for n <= kSmallN in single precision, one block, all in shared
+// memory: X = s A / 2^q (||s A||_1 / 2^q <= 1/4), Taylor degree 8 by Horner
+// (truncation below 1e-11), q squarings.  Used by the mixed-precision path, whose orbitals are
+// re-orthonormalised after every rotation.
+// C = A B for n x n column-major matrices in shared memory; each thread
+// computes a 2 x 2 block of C (n padded to even by the caller's layout).
+__device__ __forceinline__ void smem_matmul_f(int n, const float2* A, const float2* B, float2* C) {
+    const int h = (n + 1) / 2;
+    for (int t = threadIdx.x; t < h * h; t += blockDim.x) {
+        const int m = 2 * (t % h), c = 2 * (t / h);
+        const bool m1 = m + 1 < n, c1 = c + 1 < n;
+        float2 s00 = make_float2(0.f, 0.f), s01 = s00, s10 = s00, s11 = s00;
+        for (int k = 0; k < n; ++k) {
+            const float2 a0 = A[k * n + m], a1 = m1 ? A[k * n + m + 1] : make_float2(0.f, 0.f);
+            const float2 b0 = B[c * n + k], b1 = c1 ? B[(c + 1) * n + k] : make_float2(0.f, 0.f);
+            s00.x += a0.x * b0.x - a0.y * b0.y; s00.y += a0.x * b0.y + a0.y * b0.x;
+            s01.x += a0.x * b1.x - a0.y * b1.y; s01.y += a0.x * b1.y + a0.y * b1.x;
+            s10.x += a1.x * b0.x - a1.y * b0.y; s10.y += a1.x * b0.y + a1.y * b0.x;
+            s11.x += a1.x * b1.x - a1.y * b1.y; s11.y += a1.x * b1.y + a1.y * b1.x;
+        }
+        C[c * n + m] = s00;
+        if (c1) C[(c + 1) * n + m] = s01;
+        if (m1) C[c * n + m + 1] = s10;
+        if (m1 && c1) C[(c + 1) * n + m + 1] = s11;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_expm_small_f32(int n, const double2* __restrict__ A,
+                                                         const double* __restrict__ s, double2* __restrict__ E) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* X = reinterpret_cast<float2*>(smem_raw);
+    float2* P = X + n * n;
+    float2* Q = P + n * n;
+    __shared__ float colmax[1024];
+    __shared__ int qs;
+    float best = 0.f;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        float sum = 0.f;
+        for (int r = 0; r < n; ++r) {
+            const double2 a = A[c * n + r];
+            const float ax = (float)a.x, ay = (float)a.y;
+            sum += sqrtf(ax * ax + ay * ay);
+        }
+        best = fmaxf(best, sum);
+    }
+    colmax[threadIdx.x] = best;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) colmax[threadIdx.x] = fmaxf(colmax[threadIdx.x], colmax[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        float scaled = fabsf((float)s[0]) * colmax[0];
+        int q = 0;
+        while (scaled > 0.25f && q < 30) {
+            scaled *= 0.5f;
+            ++q;
+        }
+        qs = q;
+    }
+    __syncthreads();
+    const int q = qs;
+    const float f = (float)s[0] * ldexpf(1.f, -q);
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const double2 a = A[idx];
+        const float xr = f * (float)a.x, xi = f * (float)a.y;
+        X[idx] = make_float2(xr, xi);
+        const int m = idx % n, c = idx / n;
+        // P = I + X / 8
+        P[idx] = make_float2((m == c ? 1.f : 0.f) + xr * 0.125f, xi * 0.125f);
+    }
+    __syncthreads();
+    for (int k = 7; k >= 1; --k) {
+        smem_matmul_f(n, X, P, Q);
+        __syncthreads();
+        const float ik = 1.f / (float)k;
+        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+            const int m = idx % n, c = idx / n;
+            const float2 t = Q[idx];
+            P[idx] = make_float2((m == c ? 1.f : 0.f) + t.x * ik, t.y * ik);
+        }
+        __syncthreads();
+    }
+    for (int r = 0; r < q; ++r) {
+        smem_matmul_f(n, P, P, Q);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) P[idx] = Q[idx];
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) E[idx] = make_double2(P[idx].x, P[idx].y);
+}
+
+bool expm_small_f32(int n, const double2* A, const double* scale_dev, double2* E, cudaStream_t st) {
+    if (n > kSmallN) return false;
+    const size_t sm = sizeof(float2) * 3 * n * n;
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_expm_small_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    roks::count_launch(), k_expm_small_f32<<<1, 1024, sm, st>>>(n, A, scale_dev, E);
+    return true;
+}
+
 void expm_scaled(int n, const double2* A, const double* scale_dev, double2* E, double2* w1, double2* w2,
                  double2* w3, double* sdev, cudaStream_t st) {
-    k_expm_scale<<<1, 256, 0, st>>>(n, A, scale_dev, w1, sdev);
+    roks::count_launch(), k_expm_scale<<<1, 256, 0, st>>>(n, A, scale_dev, w1, sdev);
     const int blocks = (n * n + 127) / 128;
     // Horner: E_deg = I + X / deg, ..., E_1 = I + X E_2
     double2* cur = w2;
     double2* nxt = w3;
-    k_expm_horner<<<blocks, 128, 0, st>>>(n, w1, nullptr, cur, 1.0 / kExpmDegree, 1);
+    roks::count_launch(), k_expm_horner<<<blocks, 128, 0, st>>>(n, w1, nullptr, cur, 1.0 / kExpmDegree, 1);
     for (int k = kExpmDegree - 1; k >= 1; --k) {
-        k_expm_horner<<<blocks, 128, 0, st>>>(n, w1, cur, nxt, 1.0 / k, 0);
+        roks::count_launch(), k_expm_horner<<<blocks, 128, 0, st>>>(n, w1, cur, nxt, 1.0 / k, 0);
         double2* t = cur; cur = nxt; nxt = t;
     }
     for (int q = 0; q < kExpmMaxSquare; ++q) {
         double2* dst = (q == kExpmMaxSquare - 1) ? E : nxt;
-        k_expm_square<<<blocks, 128, 0, st>>>(n, cur, dst, q, sdev);
+        roks::count_launch(), k_expm_square<<<blocks, 128, 0, st>>>(n, cur, dst, q, sdev);
         if (q == kExpmMaxSquare - 1) break;
         double2* t = cur; cur = nxt; nxt = t;
     }

@@ -360,43 +360,43 @@ struct BandFft {
                       cudaStream_t st) {
         set_smem(k_band_z_inv<T, N>, SM);
         dim3 gz((s.ncol + TL - 1) / TL, nbb);
-        k_band_z_inv<T, N><<<gz, kThreads, SM, st>>>(s, tw, psi, ld, b0, Zc);
+        roks::count_launch(), k_band_z_inv<T, N><<<gz, kThreads, SM, st>>>(s, tw, psi, ld, b0, Zc);
     }
     static void y_inv(const Sphere& s, const V* tw, const V* Zc, V* Yp, int nbb, cudaStream_t st) {
         set_smem(k_band_y_inv<T, N>, SM);
         dim3 gy((N + TL - 1) / TL, s.np, nbb);
-        k_band_y_inv<T, N><<<gy, kThreads, SM, st>>>(s, tw, Zc, Yp);
+        roks::count_launch(), k_band_y_inv<T, N><<<gy, kThreads, SM, st>>>(s, tw, Zc, Yp);
     }
     static void x_apply(const Sphere& s, const V* tw, V* Yp, const T* Vk, int b0, int nbb, int nc, T scale,
                         cudaStream_t st) {
         set_smem(k_band_x_apply<T, N>, SM);
         dim3 g((N + TL - 1) / TL, N, nbb);
-        k_band_x_apply<T, N><<<g, kThreads, SM, st>>>(s, tw, Yp, Vk, b0, nc, scale);
+        roks::count_launch(), k_band_x_apply<T, N><<<g, kThreads, SM, st>>>(s, tw, Yp, Vk, b0, nc, scale);
     }
     static void y_fwd(const Sphere& s, const V* tw, const V* Yp, V* Zc, int nbb, cudaStream_t st) {
         set_smem(k_band_y_fwd<T, N>, SM);
         dim3 gy((N + TL - 1) / TL, s.np, nbb);
-        k_band_y_fwd<T, N><<<gy, kThreads, SM, st>>>(s, tw, Yp, Zc);
+        roks::count_launch(), k_band_y_fwd<T, N><<<gy, kThreads, SM, st>>>(s, tw, Yp, Zc);
     }
     static void z_fwd(const Sphere& s, const V* tw, const V* Zc, V* out, int64_t ldo, const V* psi, int64_t ldp,
                       const T* g2half, const T* wk, int b0, int nbb, int nc, cudaStream_t st) {
         set_smem(k_band_z_fwd<T, N>, SM);
         dim3 gz((s.ncol + TL - 1) / TL, nbb);
-        k_band_z_fwd<T, N><<<gz, kThreads, SM, st>>>(s, tw, Zc, out, ldo, psi, ldp, g2half, wk, b0, nc);
+        roks::count_launch(), k_band_z_fwd<T, N><<<gz, kThreads, SM, st>>>(s, tw, Zc, out, ldo, psi, ldp, g2half, wk, b0, nc);
     }
     static void x_density(const Sphere& s, const V* tw, const V* Yp, double* rho3, int b0, int nbb, int nc,
                           double scale, cudaStream_t st) {
         set_smem(k_band_x_density<T, N>, SM);
         dim3 g((N + TL - 1) / TL, N);
-        k_band_x_density<T, N><<<g, kThreads, SM, st>>>(s, tw, Yp, rho3, b0, nbb, nc, scale);
+        roks::count_launch(), k_band_x_density<T, N><<<g, kThreads, SM, st>>>(s, tw, Yp, rho3, b0, nbb, nc, scale);
     }
     static void grid3(const V* tw, V* data, int dir, cudaStream_t st) {
         set_smem(k_grid_fft_z<T, N>, SM);
         set_smem(k_grid_fft_strided<T, N>, SM);
-        k_grid_fft_z<T, N><<<(N * N + TL - 1) / TL, kThreads, SM, st>>>(tw, data, dir);
+        roks::count_launch(), k_grid_fft_z<T, N><<<(N * N + TL - 1) / TL, kThreads, SM, st>>>(tw, data, dir);
         dim3 g((N + TL - 1) / TL, N);
-        k_grid_fft_strided<T, N><<<g, kThreads, SM, st>>>(tw, data, (int64_t)N * N, (int64_t)N, dir);
-        k_grid_fft_strided<T, N><<<g, kThreads, SM, st>>>(tw, data, (int64_t)N, (int64_t)N * N, dir);
+        roks::count_launch(), k_grid_fft_strided<T, N><<<g, kThreads, SM, st>>>(tw, data, (int64_t)N * N, (int64_t)N, dir);
+        roks::count_launch(), k_grid_fft_strided<T, N><<<g, kThreads, SM, st>>>(tw, data, (int64_t)N, (int64_t)N * N, dir);
     }
 };
 

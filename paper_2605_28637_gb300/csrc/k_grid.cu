@@ -115,25 +115,26 @@ __global__ void __launch_bounds__(RB) k_colred(int npw, int nb, const c2<T>* __r
     const int n = blockIdx.x, sp = blockIdx.y;
     const int per = (npw + nsplit - 1) / nsplit;
     const int g0 = sp * per, g1 = min(npw, g0 + per);
-    double s0 = 0.0, s1 = 0.0;
+    // per-thread sums in the element type (a handful of terms), block sums in FP64
+    T t0 = T(0), t1 = T(0);
     const c2<T>* xc = x + (int64_t)n * ldx;
     for (int g = g0 + threadIdx.x; g < g1; g += RB) {
         const c2<T> a = xc[g];
-        const double ax = double(a.x), ay = double(a.y);
-        if (OP == 0) s0 += 0.5 * g2[g] * (ax * ax + ay * ay);
+        const T m = a.x * a.x + a.y * a.y;
+        if (OP == 0) t0 += T(0.5) * T(g2[g]) * m;
         if (OP == 1) {
-            const double m = ax * ax + ay * ay;
-            s0 += m;
-            s1 += g2[g] * m;
+            t0 += m;
+            t1 += T(g2[g]) * m;
         }
         if (OP == 2) {
             const c2<T> bb = y[(int64_t)n * ldy + g];
-            s0 += ax * double(bb.x) + ay * double(bb.y);
+            t0 += a.x * bb.x + a.y * bb.y;
         }
-        if (OP == 3) s0 += ax * ax + ay * ay;
+        if (OP == 3) t0 += m;
     }
-    s0 = block_sum(s0, sh);
-    if (OP == 1) s1 = block_sum(s1, sh);
+    double s0 = block_sum(double(t0), sh);
+    double s1 = 0.0;
+    if (OP == 1) s1 = block_sum(double(t1), sh);
     if (threadIdx.x == 0) {
         part[((int64_t)0 * nb + n) * nsplit + sp] = s0;
         if (OP == 1) part[((int64_t)1 * nb + n) * nsplit + sp] = s1;
@@ -154,13 +155,13 @@ void column_sums(int op, int npw, int nb, const c2<T>* x, int64_t ldx, const c2<
     constexpr int nsplit = 16;
     dim3 g(nb, nsplit);
     switch (op) {
-        case 0: k_colred<T, 0><<<g, RB, 0, st>>>(npw, nb, x, ldx, y, ldy, g2, nsplit, part); break;
-        case 1: k_colred<T, 1><<<g, RB, 0, st>>>(npw, nb, x, ldx, y, ldy, g2, nsplit, part); break;
-        case 2: k_colred<T, 2><<<g, RB, 0, st>>>(npw, nb, x, ldx, y, ldy, g2, nsplit, part); break;
-        default: k_colred<T, 3><<<g, RB, 0, st>>>(npw, nb, x, ldx, y, ldy, g2, nsplit, part); break;
+        case 0: roks::count_launch(), k_colred<T, 0><<<g, RB, 0, st>>>(npw, nb, x, ldx, y, ldy, g2, nsplit, part); break;
+        case 1: roks::count_launch(), k_colred<T, 1><<<g, RB, 0, st>>>(npw, nb, x, ldx, y, ldy, g2, nsplit, part); break;
+        case 2: roks::count_launch(), k_colred<T, 2><<<g, RB, 0, st>>>(npw, nb, x, ldx, y, ldy, g2, nsplit, part); break;
+        default: roks::count_launch(), k_colred<T, 3><<<g, RB, 0, st>>>(npw, nb, x, ldx, y, ldy, g2, nsplit, part); break;
     }
     const int count = (op == 1 ? 2 : 1) * nb;
-    k_colred_final<<<(count + 127) / 128, 128, 0, st>>>(count, nsplit, part, out);
+    roks::count_launch(), k_colred_final<<<(count + 127) / 128, 128, 0, st>>>(count, nsplit, part, out);
 }
 
 // ------------------------------------------------------------------ projector blocks
@@ -206,114 +207,123 @@ __global__ void k_band_quadratic(int nproj, int nb, const double2* __restrict__ 
 // Channel densities rho^{ch} = sum_k f[k][ch] rho_k; total rho = up M + down M.
 // xc3[k] = sum_ch C[k][ch] v^{ch},  v = -(1-alpha) (6 rho / pi)^{1/3};
 // partial sums of (1-alpha) Slater energies per configuration and of V_loc rho.
+template <typename T>
 __global__ void __launch_bounds__(RB) k_pot_xc(int64_t N3, const double* __restrict__ rho3,
                                                const double* __restrict__ vloc, PotCoef cf,
-                                               double2* __restrict__ rho_grid, double* __restrict__ xc3,
+                                               c2<T>* __restrict__ rho_grid, double* __restrict__ xc3,
                                                double* __restrict__ part) {
+    // pointwise arithmetic in the element type T; per-thread partial energies
+    // in T over a few points, block and grid sums in FP64
     __shared__ double sh[RB];
-    double exM = 0, exT = 0, eloc = 0;
-    const double cx = 0.75 * cbrt(6.0 / kPi);
+    T exM = 0, exT = 0, eloc = 0;
+    const T c6 = T(cbrt(6.0 / kPi));            // (6 / pi)^{1/3}
+    const T cx = T(0.75) * c6;
+    const T xs = T(cf.xscale);
     for (int64_t p = (int64_t)blockIdx.x * RB + threadIdx.x; p < N3; p += (int64_t)gridDim.x * RB) {
-        const double rk[3] = {rho3[p], rho3[N3 + p], rho3[2 * N3 + p]};
-        double v[4];
-        double rho_tot = 0;
+        const T rk[3] = {T(rho3[p]), T(rho3[N3 + p]), T(rho3[2 * N3 + p])};
+        T v[4];
+        T rho_tot = 0;
 #pragma unroll
         for (int ch = 0; ch < 4; ++ch) {
-            double r = 0;
+            T r = 0;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) r += cf.f[k][ch] * rk[k];
-            r = fmax(r, 0.0);
-            const double c = cbrt(r);
-            v[ch] = -cf.xscale * cbrt(6.0 / kPi) * c;
-            const double e = -cf.xscale * cx * c * r;
+            for (int k = 0; k < 3; ++k) r += T(cf.f[k][ch]) * rk[k];
+            r = r > T(0) ? r : T(0);
+            const T c = cbrt(r);
+            v[ch] = -xs * c6 * c;
+            const T e = -xs * cx * c * r;
             if (ch < 2) { exM += e; rho_tot += r; } else exT += e;
         }
-        eloc += vloc[p] * rho_tot;
-        rho_grid[p] = make_double2(rho_tot, 0.0);
+        eloc += T(vloc[p]) * rho_tot;
+        rho_grid[p] = mk<T>(rho_tot, T(0));
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            double s = 0;
+            T s = 0;
 #pragma unroll
-            for (int ch = 0; ch < 4; ++ch) s += cf.C[k][ch] * v[ch];
-            xc3[k * N3 + p] = s;
+            for (int ch = 0; ch < 4; ++ch) s += T(cf.C[k][ch]) * v[ch];
+            xc3[k * N3 + p] = double(s);
         }
     }
-    exM = block_sum(exM, sh);
-    exT = block_sum(exT, sh);
-    eloc = block_sum(eloc, sh);
+    const double dexM = block_sum(double(exM), sh);
+    const double dexT = block_sum(double(exT), sh);
+    const double deloc = block_sum(double(eloc), sh);
     if (threadIdx.x == 0) {
-        part[blockIdx.x * 4 + 0] = exM;
-        part[blockIdx.x * 4 + 1] = exT;
-        part[blockIdx.x * 4 + 2] = eloc;
+        part[blockIdx.x * 4 + 0] = dexM;
+        part[blockIdx.x * 4 + 1] = dexT;
+        part[blockIdx.x * 4 + 2] = deloc;
         part[blockIdx.x * 4 + 3] = 0.0;
     }
 }
 
 // After the forward transform: rho(G) = grid / N^3; E_H partial
 // sum 4 pi |rho(G)|^2 / G^2; grid <- V_H(G) = 4 pi rho(G) / G^2 (G = 0 -> 0).
-__global__ void __launch_bounds__(RB) k_hartree_G(int N, double b, double2* __restrict__ grid,
+template <typename T>
+__global__ void __launch_bounds__(RB) k_hartree_G(int N, double b, c2<T>* __restrict__ grid,
                                                   double* __restrict__ part) {
     __shared__ double sh[RB];
     const int64_t N3 = (int64_t)N * N * N;
-    const double inv = 1.0 / double(N3);
-    double eh = 0;
+    const T inv = T(1.0 / double(N3));
+    const T fpb = T(4.0 * kPi / (b * b));
+    T eh = 0;
     for (int64_t p = (int64_t)blockIdx.x * RB + threadIdx.x; p < N3; p += (int64_t)gridDim.x * RB) {
         const int z = p % N, y = (p / N) % N, x = p / ((int64_t)N * N);
         const int fx = signed_freq(x, N), fy = signed_freq(y, N), fz = signed_freq(z, N);
-        const double g2 = b * b * double(fx * fx + fy * fy + fz * fz);
-        double2 r = grid[p];
-        r.x *= inv;
-        r.y *= inv;
-        double2 o = make_double2(0.0, 0.0);
-        if (g2 > 0) {
-            const double k = 4.0 * kPi / g2;
-            eh += k * (r.x * r.x + r.y * r.y);
-            o = make_double2(k * r.x, k * r.y);
+        const int m2 = fx * fx + fy * fy + fz * fz;
+        const c2<T> gv = grid[p];
+        const T rx = gv.x * inv, ry = gv.y * inv;
+        c2<T> o = mk<T>(T(0), T(0));
+        if (m2 > 0) {
+            const T k = fpb / T(m2);              // 4 pi / G^2
+            eh += k * (rx * rx + ry * ry);
+            o = mk<T>(k * rx, k * ry);
         }
         grid[p] = o;
     }
-    eh = block_sum(eh, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = eh;
+    const double deh = block_sum(double(eh), sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = deh;
 }
 
 // V^k = w_k (V_loc + V_H) + xc3[k]; partial sums <a|V^c|a>, <b|V^c|b> (rho_a, rho_b).
 template <typename T>
 __global__ void __launch_bounds__(RB) k_pot_class(int64_t N3, const double* __restrict__ vloc,
-                                                  const double2* __restrict__ vh, const double* __restrict__ xc3,
+                                                  const c2<T>* __restrict__ vh, const double* __restrict__ xc3,
                                                   const double* __restrict__ rho3, PotCoef cf, T* __restrict__ Vk,
                                                   double* __restrict__ Vk64, double* __restrict__ part) {
     __shared__ double sh[RB];
-    double ea = 0, eb = 0;
+    T ea = 0, eb = 0;
     for (int64_t p = (int64_t)blockIdx.x * RB + threadIdx.x; p < N3; p += (int64_t)gridDim.x * RB) {
-        const double v0 = vloc[p] + vh[p].x;
+        const T v0 = T(vloc[p]) + vh[p].x;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const double v = cf.w[k] * v0 + xc3[k * N3 + p];
-            Vk[k * N3 + p] = T(v);
-            if (Vk64) Vk64[k * N3 + p] = v;
+            const T v = T(cf.w[k]) * v0 + T(xc3[k * N3 + p]);
+            Vk[k * N3 + p] = v;
+            if (Vk64) Vk64[k * N3 + p] = double(v);
             if (k == 0) {
-                ea += v * rho3[N3 + p];
-                eb += v * rho3[2 * N3 + p];
+                ea += v * T(rho3[N3 + p]);
+                eb += v * T(rho3[2 * N3 + p]);
             }
         }
     }
-    ea = block_sum(ea, sh);
-    eb = block_sum(eb, sh);
+    const double dea = block_sum(double(ea), sh);
+    const double deb = block_sum(double(eb), sh);
     if (threadIdx.x == 0) {
-        part[blockIdx.x * 2 + 0] = ea;
-        part[blockIdx.x * 2 + 1] = eb;
+        part[blockIdx.x * 2 + 0] = dea;
+        part[blockIdx.x * 2 + 1] = deb;
     }
 }
 
-// Sum per-block partials in a fixed order: out[q] = scale[q] * sum_b part[b * nq + q].
-__global__ void k_partials_final(int nblocks, int nq, const double* __restrict__ part, double* __restrict__ out,
-                                 double s0, double s1, double s2, double s3) {
-    const int q = threadIdx.x;
-    if (q >= nq) return;
+// Sum per-block partials in a fixed order: out[q] = scale[q] * sum_b part[b * nq + q];
+// one block per quantity.
+__global__ void __launch_bounds__(RB) k_partials_final(int nblocks, int nq, const double* __restrict__ part,
+                                                       double* __restrict__ out, double s0, double s1, double s2,
+                                                       double s3) {
+    __shared__ double sh[RB];
+    const int q = blockIdx.x;
     double s = 0;
-    for (int b = 0; b < nblocks; ++b) s += part[b * nq + q];
+    for (int b = threadIdx.x; b < nblocks; b += RB) s += part[b * nq + q];
+    s = block_sum(s, sh);
     const double sc[4] = {s0, s1, s2, s3};
-    out[q] = s * sc[q];
+    if (threadIdx.x == 0) out[q] = s * sc[q];
 }
 
 // ------------------------------------------------------------------ PCG pointwise
@@ -322,15 +332,21 @@ template <typename T>
 __global__ void k_precond(int npw, const c2<T>* __restrict__ gI, int64_t ld, const double* __restrict__ g2,
                           const double* __restrict__ sums /* [2 nb]: |g|^2, g2 |g|^2 */, int nb,
                           c2<T>* __restrict__ out, int64_t ldo) {
+    __shared__ T Xs[2];
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = blockIdx.y;
+    if (threadIdx.x == 0) {
+        const double X = 1.5 * sums[nb + n] / fmax(sums[n], 1e-300);
+        Xs[0] = T(1.0 / X);
+        Xs[1] = T(-2.0 / X);
+    }
+    __syncthreads();
     if (g >= npw) return;
-    const double X = 1.5 * sums[nb + n] / fmax(sums[n], 1e-300);
-    const double x = g2[g] / X;
-    const double num = 27.0 + x * (18.0 + x * (12.0 + 8.0 * x));
-    const double K = -(2.0 / X) * num / (num + 16.0 * x * x * x * x);
+    const T x = T(g2[g]) * Xs[0];
+    const T num = T(27) + x * (T(18) + x * (T(12) + T(8) * x));
+    const T K = Xs[1] * num / (num + T(16) * x * x * x * x);
     const c2<T> a = gI[(int64_t)n * ld + g];
-    out[(int64_t)n * ldo + g] = mk<T>(T(K * double(a.x)), T(K * double(a.y)));
+    out[(int64_t)n * ldo + g] = mk<T>(K * a.x, K * a.y);
 }
 
 // out = x + coef[0] * y  (coef on the device; y may be null -> copy)
@@ -355,9 +371,9 @@ void vloc_setup(int N, double L, int natoms, const double* atoms_dev, double2* g
                 const double2* tw64, cudaStream_t st) {
     const int64_t N3 = (int64_t)N * N * N;
     const double omega = L * L * L;
-    k_vloc_G<<<(N3 + 255) / 256, 256, 0, st>>>(N, 2.0 * kPi / L, omega, natoms, atoms_dev, grid);
+    roks::count_launch(), k_vloc_G<<<(N3 + 255) / 256, 256, 0, st>>>(N, 2.0 * kPi / L, omega, natoms, atoms_dev, grid);
     grid_fft3<double>(N, tw64, grid, +1, st);
-    k_real_part<<<(N3 + 255) / 256, 256, 0, st>>>(N3, grid, vloc);
+    roks::count_launch(), k_real_part<<<(N3 + 255) / 256, 256, 0, st>>>(N3, grid, vloc);
 }
 
 template <typename T>
@@ -365,24 +381,24 @@ void projectors_setup(int npw, int nproj, double L, const int* miller_dev, const
                       int64_t ldp, cudaStream_t st) {
     if (nproj == 0) return;
     dim3 g((npw + 255) / 256, nproj);
-    k_projectors<T><<<g, 256, 0, st>>>(npw, nproj, 2.0 * kPi / L, L * L * L, miller_dev, proj_dev, P, ldp);
+    roks::count_launch(), k_projectors<T><<<g, 256, 0, st>>>(npw, nproj, 2.0 * kPi / L, L * L * L, miller_dev, proj_dev, P, ldp);
 }
 
 template <typename T>
 void init_orbitals(int npw, int nb, const double* u_dev, const double* g2, c2<T>* psi, int64_t ld, cudaStream_t st) {
     dim3 g((npw + 255) / 256, nb);
-    k_init_orbitals<T><<<g, 256, 0, st>>>(npw, nb, u_dev, g2, psi, ld);
+    roks::count_launch(), k_init_orbitals<T><<<g, 256, 0, st>>>(npw, nb, u_dev, g2, psi, ld);
 }
 
 template <typename T>
 void to_real_type(int64_t n, const double* in, T* out, double scale, cudaStream_t st) {
-    k_to_real<T><<<(n + 255) / 256, 256, 0, st>>>(n, in, out, scale);
+    roks::count_launch(), k_to_real<T><<<(n + 255) / 256, 256, 0, st>>>(n, in, out, scale);
 }
 
 void apply_DQ(int nproj, int nb, const double2* B, const int* blk_off, const int* blk_n, const double* Drow,
               const double* Qrow, const double* wband, double2* DB, double2* QB, cudaStream_t st) {
     if (nproj == 0) return;
-    k_apply_DQ<<<(nproj * nb + 127) / 128, 128, 0, st>>>(nproj, nb, B, blk_off, blk_n, Drow, Qrow, wband, DB, QB);
+    roks::count_launch(), k_apply_DQ<<<(nproj * nb + 127) / 128, 128, 0, st>>>(nproj, nb, B, blk_off, blk_n, Drow, Qrow, wband, DB, QB);
 }
 
 void band_quadratic(int nproj, int nb, const double2* B, const double2* DB, double* out, cudaStream_t st) {
@@ -390,26 +406,26 @@ void band_quadratic(int nproj, int nb, const double2* B, const double2* DB, doub
         cudaMemsetAsync(out, 0, sizeof(double) * nb, st);
         return;
     }
-    k_band_quadratic<<<nb, RB, 0, st>>>(nproj, nb, B, DB, out);
+    roks::count_launch(), k_band_quadratic<<<nb, RB, 0, st>>>(nproj, nb, B, DB, out);
 }
 
 constexpr int kPotBlocks = 512;
 
 template <typename T>
-void potentials(int N, double L, const double* rho3, const double* vloc, const PotCoef& cf, double2* grid,
-                double* xc3, const double2* tw64, T* Vk, double* Vk64, double* part, double* out6,
+void potentials(int N, double L, const double* rho3, const double* vloc, const PotCoef& cf, c2<T>* grid,
+                double* xc3, const c2<T>* tw, T* Vk, double* Vk64, double* part, double* out6,
                 cudaStream_t st) {
     // out6: [E_x^M, E_x^T, E_loc, E_H, <a|V^c|a>, <b|V^c|b>]
     const int64_t N3 = (int64_t)N * N * N;
     const double dvol = L * L * L / double(N3);
-    k_pot_xc<<<kPotBlocks, RB, 0, st>>>(N3, rho3, vloc, cf, grid, xc3, part);
-    k_partials_final<<<1, 32, 0, st>>>(kPotBlocks, 4, part, out6, dvol, dvol, dvol, 0.0);
-    grid_fft3<double>(N, tw64, grid, -1, st);
-    k_hartree_G<<<kPotBlocks, RB, 0, st>>>(N, 2.0 * kPi / L, grid, part);
-    k_partials_final<<<1, 32, 0, st>>>(kPotBlocks, 1, part, out6 + 3, 0.5 * L * L * L, 0, 0, 0);
-    grid_fft3<double>(N, tw64, grid, +1, st);
-    k_pot_class<T><<<kPotBlocks, RB, 0, st>>>(N3, vloc, grid, xc3, rho3, cf, Vk, Vk64, part);
-    k_partials_final<<<1, 32, 0, st>>>(kPotBlocks, 2, part, out6 + 4, dvol, dvol, 0, 0);
+    roks::count_launch(), k_pot_xc<T><<<kPotBlocks, RB, 0, st>>>(N3, rho3, vloc, cf, grid, xc3, part);
+    roks::count_launch(), k_partials_final<<<4, RB, 0, st>>>(kPotBlocks, 4, part, out6, dvol, dvol, dvol, 0.0);
+    grid_fft3<T>(N, tw, grid, -1, st);
+    roks::count_launch(), k_hartree_G<T><<<kPotBlocks, RB, 0, st>>>(N, 2.0 * kPi / L, grid, part);
+    roks::count_launch(), k_partials_final<<<1, RB, 0, st>>>(kPotBlocks, 1, part, out6 + 3, 0.5 * L * L * L, 0, 0, 0);
+    grid_fft3<T>(N, tw, grid, +1, st);
+    roks::count_launch(), k_pot_class<T><<<kPotBlocks, RB, 0, st>>>(N3, vloc, grid, xc3, rho3, cf, Vk, Vk64, part);
+    roks::count_launch(), k_partials_final<<<2, RB, 0, st>>>(kPotBlocks, 2, part, out6 + 4, dvol, dvol, 0, 0);
 }
 
 size_t potentials_part_elems() { return (size_t)kPotBlocks * 4; }
@@ -418,14 +434,14 @@ template <typename T>
 void precondition(int npw, int nb, const c2<T>* gI, int64_t ld, const double* g2, const double* sums, c2<T>* out,
                   int64_t ldo, cudaStream_t st) {
     dim3 g((npw + 255) / 256, nb);
-    k_precond<T><<<g, 256, 0, st>>>(npw, gI, ld, g2, sums, nb, out, ldo);
+    roks::count_launch(), k_precond<T><<<g, 256, 0, st>>>(npw, gI, ld, g2, sums, nb, out, ldo);
 }
 
 template <typename T>
 void axpy(int npw, int nb, const c2<T>* x, int64_t ldx, const c2<T>* y, int64_t ldy, const double* coef,
           double csign, c2<T>* out, int64_t ldo, cudaStream_t st) {
     dim3 g((npw + 255) / 256, nb);
-    k_axpy<T><<<g, 256, 0, st>>>(npw, x, ldx, y, ldy, coef, csign, out, ldo);
+    roks::count_launch(), k_axpy<T><<<g, 256, 0, st>>>(npw, x, ldx, y, ldy, coef, csign, out, ldo);
 }
 
 #define ROKS_INSTANTIATE_GRID(T)                                                                               \
@@ -435,8 +451,8 @@ void axpy(int npw, int nb, const c2<T>* x, int64_t ldx, const c2<T>* y, int64_t 
     template void to_real_type<T>(int64_t, const double*, T*, double, cudaStream_t);                           \
     template void column_sums<T>(int, int, int, const c2<T>*, int64_t, const c2<T>*, int64_t, const double*,  \
                                  double*, double*, cudaStream_t);                                              \
-    template void potentials<T>(int, double, const double*, const double*, const PotCoef&, double2*, double*, \
-                                const double2*, T*, double*, double*, double*, cudaStream_t);                 \
+    template void potentials<T>(int, double, const double*, const double*, const PotCoef&, c2<T>*, double*,   \
+                                const c2<T>*, T*, double*, double*, double*, cudaStream_t);                   \
     template void precondition<T>(int, int, const c2<T>*, int64_t, const double*, const double*, c2<T>*,      \
                                   int64_t, cudaStream_t);                                                      \
     template void axpy<T>(int, int, const c2<T>*, int64_t, const c2<T>*, int64_t, const double*, double,      \

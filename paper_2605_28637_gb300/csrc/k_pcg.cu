@@ -62,8 +62,8 @@ __global__ void k_pcg_coupling(int nb, const double2* __restrict__ Th, int ia, i
 
 void pcg_rotation(int nb, const double2* Theta, const double* d, const int* shell, int suppress_ab, int ia, int ib,
                   double2* Gam, double2* Gin, double2* A, PcgScalars* sc, cudaStream_t st) {
-    k_pcg_rotation<<<(nb * nb + 127) / 128, 128, 0, st>>>(nb, Theta, d, shell, suppress_ab, ia, ib, Gam, Gin, A);
-    k_pcg_coupling<<<1, 32, 0, st>>>(nb, Theta, ia, ib, sc);
+    roks::count_launch(), k_pcg_rotation<<<(nb * nb + 127) / 128, 128, 0, st>>>(nb, Theta, d, shell, suppress_ab, ia, ib, Gam, Gin, A);
+    roks::count_launch(), k_pcg_coupling<<<1, 32, 0, st>>>(nb, Theta, ia, ib, sc);
 }
 
 // d_m = <m|F^c|m>.  Closed bands: Re theta_mm.  Open bands:
@@ -79,7 +79,7 @@ __global__ void k_pcg_diag(int nb, int n_closed, const double2* __restrict__ Th,
 
 void pcg_diag(int nb, int n_closed, const double2* Theta, const double* kin_b, const double* nl_b,
               const double* open_vc, double wc, double* d, cudaStream_t st) {
-    k_pcg_diag<<<(nb + 127) / 128, 128, 0, st>>>(nb, n_closed, Theta, kin_b, nl_b, open_vc, wc, d);
+    roks::count_launch(), k_pcg_diag<<<(nb + 127) / 128, 128, 0, st>>>(nb, n_closed, Theta, kin_b, nl_b, open_vc, wc, d);
 }
 
 __global__ void k_pcg_rot_dots(int nb, const double2* __restrict__ A, const double2* __restrict__ Ap,
@@ -110,7 +110,7 @@ __global__ void k_pcg_rot_dots(int nb, const double2* __restrict__ A, const doub
 
 void pcg_rot_dots(int nb, const double2* A, const double2* Aprev, const double2* Gin, PcgScalars* sc,
                   cudaStream_t st) {
-    k_pcg_rot_dots<<<1, 256, 0, st>>>(nb, A, Aprev, Gin, sc);
+    roks::count_launch(), k_pcg_rot_dots<<<1, 256, 0, st>>>(nb, A, Aprev, Gin, sc);
 }
 
 // beta = pg / pg_prev; dE(beta) = 2 a1 + 2 beta a2 + r1 + beta r2.
@@ -138,7 +138,7 @@ __global__ void k_pcg_direction(PcgScalars* sc) {
     sc->restarted = restarted;
 }
 
-void pcg_direction(PcgScalars* sc, cudaStream_t st) { k_pcg_direction<<<1, 32, 0, st>>>(sc); }
+void pcg_direction(PcgScalars* sc, cudaStream_t st) { roks::count_launch(), k_pcg_direction<<<1, 32, 0, st>>>(sc); }
 
 __global__ void k_pcg_total_rotation(int nb, const double2* __restrict__ A, const double2* __restrict__ Ap,
                                      const PcgScalars* __restrict__ sc, double2* __restrict__ At) {
@@ -151,7 +151,7 @@ __global__ void k_pcg_total_rotation(int nb, const double2* __restrict__ A, cons
 
 void pcg_total_rotation(int nb, const double2* A, const double2* Aprev, PcgScalars* sc, double2* Atot,
                         cudaStream_t st) {
-    k_pcg_total_rotation<<<(nb * nb + 127) / 128, 128, 0, st>>>(nb, A, Aprev, sc, Atot);
+    roks::count_launch(), k_pcg_total_rotation<<<(nb * nb + 127) / 128, 128, 0, st>>>(nb, A, Aprev, sc, Atot);
 }
 
 // Parabola E(x) = E0 + dE0 x + c x^2 through E(dt) = Et; c > 0 gives the
@@ -165,7 +165,7 @@ __global__ void k_pcg_line_search(PcgScalars* sc) {
     sc->step = step;
 }
 
-void pcg_line_search(PcgScalars* sc, cudaStream_t st) { k_pcg_line_search<<<1, 32, 0, st>>>(sc); }
+void pcg_line_search(PcgScalars* sc, cudaStream_t st) { roks::count_launch(), k_pcg_line_search<<<1, 32, 0, st>>>(sc); }
 
 // After the step: next trial step, history.
 __global__ void k_pcg_finish(PcgScalars* sc) {
@@ -179,9 +179,9 @@ __global__ void k_set_cur(PcgScalars* sc, int field) {
     if (threadIdx.x == 0) sc->cur = reinterpret_cast<double*>(sc)[field];
 }
 
-void pcg_set_cur(PcgScalars* sc, int field, cudaStream_t st) { k_set_cur<<<1, 32, 0, st>>>(sc, field); }
+void pcg_set_cur(PcgScalars* sc, int field, cudaStream_t st) { roks::count_launch(), k_set_cur<<<1, 32, 0, st>>>(sc, field); }
 
-void pcg_finish(PcgScalars* sc, cudaStream_t st) { k_pcg_finish<<<1, 32, 0, st>>>(sc); }
+void pcg_finish(PcgScalars* sc, cudaStream_t st) { roks::count_launch(), k_pcg_finish<<<1, 32, 0, st>>>(sc); }
 
 // E[0..10] = kin, loc, nl, H, xM, xT, hfM, hfT, M, T, total
 __global__ void k_energy_combine(const double* __restrict__ kin_b, const double* __restrict__ nl_b, int nb,
@@ -204,7 +204,7 @@ __global__ void k_energy_combine(const double* __restrict__ kin_b, const double*
 
 void energy_combine(const double* kin_b, const double* nl_b, int nb, const double* wband, const double* out6,
                     double cM, double cT, double alpha, const double* hf2, double* E, cudaStream_t st) {
-    k_energy_combine<<<1, 32, 0, st>>>(kin_b, nl_b, nb, wband, out6, cM, cT, alpha, hf2, E);
+    roks::count_launch(), k_energy_combine<<<1, 32, 0, st>>>(kin_b, nl_b, nb, wband, out6, cM, cT, alpha, hf2, E);
 }
 
 __global__ void k_take_energy(const double* __restrict__ E, PcgScalars* sc, int field) {
@@ -212,7 +212,7 @@ __global__ void k_take_energy(const double* __restrict__ E, PcgScalars* sc, int 
 }
 
 void pcg_take_energy(const double* E, PcgScalars* sc, int field, cudaStream_t st) {
-    k_take_energy<<<1, 32, 0, st>>>(E, sc, field);
+    roks::count_launch(), k_take_energy<<<1, 32, 0, st>>>(E, sc, field);
 }
 
 __global__ void k_hermitize(int n, double2* O) {
@@ -226,7 +226,7 @@ __global__ void k_hermitize(int n, double2* O) {
     O[(int64_t)m * n + c] = make_double2(h.x, -h.y);
 }
 
-void hermitize(int n, double2* O, cudaStream_t st) { k_hermitize<<<(n * n + 127) / 128, 128, 0, st>>>(n, O); }
+void hermitize(int n, double2* O, cudaStream_t st) { roks::count_launch(), k_hermitize<<<(n * n + 127) / 128, 128, 0, st>>>(n, O); }
 
 // dst = scale * sum_i v[i]  (fixed order)
 __global__ void k_sum_to(const double* __restrict__ v, int n, double* dst, double scale) {
@@ -237,7 +237,7 @@ __global__ void k_sum_to(const double* __restrict__ v, int n, double* dst, doubl
 }
 
 void sum_to(const double* v, int n, double* dst, double scale, cudaStream_t st) {
-    k_sum_to<<<1, 32, 0, st>>>(v, n, dst, scale);
+    roks::count_launch(), k_sum_to<<<1, 32, 0, st>>>(v, n, dst, scale);
 }
 
 }  // namespace roks

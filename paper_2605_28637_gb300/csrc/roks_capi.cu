@@ -213,8 +213,8 @@ struct Impl {
     static roks_status potential(roks_ctx* ctx) {
         cudaStream_t st = ctx->st;
         PROF("potential");
-        potentials<T>(ctx->N, ctx->L, ctx->d_rho3, ctx->d_vloc, ctx->cf, ctx->d_grid, ctx->d_xc3, ctx->d_tw64,
-                      static_cast<T*>(ctx->d_Vk), nullptr, ctx->d_part, ctx->d_out6, st);
+        potentials<T>(ctx->N, ctx->L, ctx->d_rho3, ctx->d_vloc, ctx->cf, reinterpret_cast<V*>(ctx->d_grid),
+                      ctx->d_xc3, ccv(ctx->d_tw), static_cast<T*>(ctx->d_Vk), nullptr, ctx->d_part, ctx->d_out6, st);
         energy_combine(ctx->d_kin_b, ctx->d_nl_b, ctx->nb, ctx->d_wband, ctx->d_out6, ctx->cM, ctx->cT,
                        ctx->alpha, nullptr, ctx->d_E, st);
         CK(cudaGetLastError());
@@ -332,8 +332,11 @@ struct Impl {
         {
             PROF("rotate");
             axpy<T>(ctx->npw, nb, ccv(psi), ld, ccv(ctx->W_s), l, scd + step_field, 1.0, cv(ctx->W_Y), l, st);
-            expm_scaled(nb, ctx->d_Atot, scd + step_field, ctx->d_U, ctx->d_e1, ctx->d_e2, ctx->d_e3,
-                        ctx->d_expm_info, st);
+            const bool small32 = (ctx->prec == ROKS_MIXED) && expm_small_f32(nb, ctx->d_Atot, scd + step_field,
+                                                                              ctx->d_U, st);
+            if (!small32)
+                expm_scaled(nb, ctx->d_Atot, scd + step_field, ctx->d_U, ctx->d_e1, ctx->d_e2, ctx->d_e3,
+                            ctx->d_expm_info, st);
             gemm_nn<T>(ctx->npw, nb, nb, ccv(ctx->W_Y), l, ctx->d_U, nb, cv(ctx->W_Y2), l, 1.0, 0.0, st);
         }
         roks_status r = orth(ctx, ctx->W_Y2, l, out, ldo, ctx->d_B);
@@ -843,6 +846,7 @@ roks_status roks_pcg_step(roks_ctx* ctx, void* psi, int64_t ld, roks_step_info* 
 roks_status roks_profile_enable(roks_ctx* ctx, int enable) {
     if (!ctx) return ROKS_EINVAL;
     ctx->prof_on = enable != 0;
+    if (ctx->prof_on) launches_take();
     return ROKS_OK;
 }
 
@@ -862,6 +866,7 @@ roks_status roks_profile_read(roks_ctx* ctx, roks_profile_entry* out, int cap, i
         ctx->prof_pool.push_back(r.b);
     }
     ctx->prof_recs.clear();
+    const long long kernels = launches_take();
     int n = 0;
     for (size_t f = 0; f < nf; ++f) {
         if (cnt[f] == 0) continue;
@@ -873,6 +878,13 @@ roks_status roks_profile_read(roks_ctx* ctx, roks_profile_entry* out, int cap, i
         }
         ++n;
     }
+    if (n < cap) {
+        std::memset(out[n].name, 0, sizeof(out[n].name));
+        std::strncpy(out[n].name, "kernel_launches", sizeof(out[n].name) - 1);
+        out[n].launches = (int)kernels;
+        out[n].ms = 0.0;
+    }
+    ++n;
     if (count) *count = n;
     return ROKS_OK;
 }

@@ -35,9 +35,10 @@ void column_sums(int op, int npw, int nb, const c2<T>* x, int64_t ldx, const c2<
 void apply_DQ(int nproj, int nb, const double2* B, const int* blk_off, const int* blk_n, const double* Drow,
               const double* Qrow, const double* wband, double2* DB, double2* QB, cudaStream_t st);
 void band_quadratic(int nproj, int nb, const double2* B, const double2* DB, double* out, cudaStream_t st);
+// Grid transforms in the element type T (FP32 for the mixed path), energies in FP64.
 template <typename T>
-void potentials(int N, double L, const double* rho3, const double* vloc, const PotCoef& cf, double2* grid,
-                double* xc3, const double2* tw64, T* Vk, double* Vk64, double* part, double* out6,
+void potentials(int N, double L, const double* rho3, const double* vloc, const PotCoef& cf, c2<T>* grid,
+                double* xc3, const c2<T>* tw, T* Vk, double* Vk64, double* part, double* out6,
                 cudaStream_t st);
 size_t potentials_part_elems();
 template <typename T>
@@ -95,6 +96,5 @@ void pcg_take_energy(const double* E, PcgScalars* sc, int field, cudaStream_t st
 // Hermitian part: O <- (O + O^H)/2
 void hermitize(int n, double2* O, cudaStream_t st);
 
-enum { SC_E0 = 0, SC_ET = 1, SC_ENEW = 2, SC_DT = 14, SC_STEP = 15, SC_BETA = 5 };
 
 }  // namespace roks

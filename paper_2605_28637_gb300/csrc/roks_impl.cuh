@@ -36,6 +36,11 @@ struct Sphere {
 
 __host__ __device__ __forceinline__ int signed_freq(int e, int n) { return e <= n / 2 ? e : e - n; }
 
+// Host-side count of the kernel launches issued by the library (every launch
+// site calls count_launch(); read and reset through the profiling API).
+void count_launch();
+long long launches_take();
+
 // ------------------------------------------------------------ band FFTs
 // Bands b0 .. b0+nbb-1 of psi (column major, ld).  Zc holds nbb x ncol x N
 // z-lines, Yp holds nbb x np x N x N plane data (y, z).
@@ -87,5 +92,7 @@ void cholesky_inverse(int n, const double2* O, double2* Lw, double2* LinvH, int*
 // E = expm(scale_dev[0] * A), A anti-Hermitian, Taylor + scaling and squaring.
 void expm_scaled(int n, const double2* A, const double* scale_dev, double2* E, double2* w1, double2* w2,
                  double2* w3, double* sdev, cudaStream_t st);
+// Single-precision, single-block variant for n <= 64; false if n is larger.
+bool expm_small_f32(int n, const double2* A, const double* scale_dev, double2* E, cudaStream_t st);
 
 }  // namespace roks

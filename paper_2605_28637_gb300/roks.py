@@ -64,8 +64,13 @@ class roks_step_info(C.Structure):
                 ("dE0", C.c_double), ("restarted", C.c_int), ("converged", C.c_int)]
 
 
+class roks_profile_entry(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int), ("ms", C.c_double)]
+
+
 EXPORTS = ["roks_setup", "roks_basis", "roks_init_orbitals", "roks_density", "roks_potential", "roks_apply_h",
-           "roks_orthonormalize", "roks_pcg_step", "roks_energies_get", "roks_last_error", "roks_destroy"]
+           "roks_orthonormalize", "roks_pcg_step", "roks_energies_get", "roks_profile_enable", "roks_profile_read",
+           "roks_last_error", "roks_destroy"]
 
 _lib = None
 
@@ -93,6 +98,8 @@ def load(path: str | None = None) -> C.CDLL:
     lib.roks_orthonormalize.argtypes = [P, P, C.c_int64]
     lib.roks_pcg_step.argtypes = [P, P, C.c_int64, C.POINTER(roks_step_info)]
     lib.roks_energies_get.argtypes = [P, C.POINTER(roks_energies)]
+    lib.roks_profile_enable.argtypes = [P, C.c_int]
+    lib.roks_profile_read.argtypes = [P, C.POINTER(roks_profile_entry), C.c_int, C.POINTER(C.c_int)]
     lib.roks_last_error.argtypes = [P]
     lib.roks_last_error.restype = C.c_char_p
     lib.roks_destroy.argtypes = [P]
@@ -188,6 +195,18 @@ def roks_energies_get(ctx) -> dict:
     e = roks_energies()
     _check(ctx, load().roks_energies_get(ctx, C.byref(e)))
     return {n: getattr(e, n) for n, _ in roks_energies._fields_}
+
+
+def roks_profile_enable(ctx, enable: int):
+    _check(ctx, load().roks_profile_enable(ctx, int(enable)))
+
+
+def roks_profile_read(ctx, cap: int = 64) -> list:
+    arr = (roks_profile_entry * cap)()
+    n = C.c_int()
+    _check(ctx, load().roks_profile_read(ctx, arr, cap, C.byref(n)))
+    return [{"name": arr[i].name.decode(), "launches": arr[i].launches, "ms": arr[i].ms}
+            for i in range(min(n.value, cap))]
 
 
 def roks_last_error(ctx) -> str:
