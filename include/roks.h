@@ -221,6 +221,26 @@ ROKS_API roks_status roks_profile_enable(roks_ctx* ctx, int enable);
 ROKS_API roks_status roks_profile_read(roks_ctx* ctx, roks_profile_entry* out, int cap,
                                        int* count);
 
+/* Allocation-free orthonormalisation of a band block with overlap S = 1
+ * (no counterpart in the paper; it exists for callers that cannot call
+ * cudaMalloc, such as code inside a framework that has reserved the GPU's
+ * memory for its own allocator, or a solver loop that must not allocate once
+ * running).  psi (device, npw x nbands complex, column major, ld >= npw,
+ * double for ROKS_FP64 or float for ROKS_MIXED) is replaced in place by
+ * psi L^{-H} with psi^H psi = L L^H (FP64 Cholesky), exactly what
+ * roks_orthonormalize does on a context without projectors.  Needs no
+ * context and allocates nothing: its scratch (4.2 MiB: split-K partial sums,
+ * the overlap, L^{-H} and a status flag) is a fixed array in the library's
+ * device memory, present on every GPU that loads the library until the
+ * process exits.  The first call on a device resolves that array's device
+ * address; make it before any stream capture.  All calls share the array
+ * and it keeps the last call's contents, so calls that overlap on the GPU
+ * (different streams or threads at once) race; serialise them.
+ * Limits: nbands <= 64 (ROKS_EINVAL beyond).  Synchronises the stream;
+ * ROKS_ENOTPOSDEF leaves psi unchanged. */
+ROKS_API roks_status roks_orthonormalize_noalloc(int precision, int npw, int nbands,
+                                                 void* psi, int64_t ld, void* cuda_stream);
+
 /* Text of the last error on this context ("" if none).  Never NULL. */
 ROKS_API const char* roks_last_error(const roks_ctx* ctx);
 

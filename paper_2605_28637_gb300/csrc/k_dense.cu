@@ -150,6 +150,39 @@ void gemm_cn(int M, int N, int K, const c2<T>* A, int64_t lda, const c2<T>* B, i
     roks::count_launch(), k_chunk_sum<<<(unsigned)((thr + 255) / 256), 256, 0, st>>>(M, N, p.nchunk, work, C, ldc);
 }
 
+// Same contraction with the number of K chunks capped at max_chunks, for
+// callers whose partial-sum buffer has a fixed size (max_chunks * M * N).
+template <typename T>
+void gemm_cn_capped(int M, int N, int K, const c2<T>* A, int64_t lda, const c2<T>* B, int64_t ldb, double2* C,
+                    int ldc, double2* work, int max_chunks, cudaStream_t st) {
+    if (M <= 0 || N <= 0) return;
+    CnPlan p = cn_plan(M, N, K);
+    if (p.nchunk > max_chunks) {
+        int kc = (K + max_chunks - 1) / max_chunks;
+        kc = ((kc + CN_KT - 1) / CN_KT) * CN_KT;
+        p.kchunk = kc;
+        p.nchunk = (K + kc - 1) / kc;
+    }
+    dim3 g(p.mt, p.nt, p.nchunk);
+    if (K <= 0) {
+        cudaMemsetAsync(work, 0, sizeof(double2) * M * N, st);
+    } else {
+#define CN_CASE(RM_, RN_)                                                                                   \
+    if (p.rm == RM_ && p.rn == RN_)                                                                       \
+        roks::count_launch(), k_gemm_cn<T, RM_, RN_><<<g, 256, 0, st>>>(M, N, K, p.kchunk, A, lda, B, ldb, work);
+        CN_CASE(1, 1) CN_CASE(1, 2) CN_CASE(1, 3) CN_CASE(2, 1) CN_CASE(2, 2) CN_CASE(2, 3) CN_CASE(3, 1)
+        CN_CASE(3, 2) CN_CASE(3, 3)
+#undef CN_CASE
+    }
+    const long long thr = (long long)M * N * 32;
+    roks::count_launch(), k_chunk_sum<<<(unsigned)((thr + 255) / 256), 256, 0, st>>>(M, N, p.nchunk, work, C, ldc);
+}
+
+template void gemm_cn_capped<float>(int, int, int, const float2*, int64_t, const float2*, int64_t, double2*, int,
+                                    double2*, int, cudaStream_t);
+template void gemm_cn_capped<double>(int, int, int, const double2*, int64_t, const double2*, int64_t, double2*, int,
+                                     double2*, int, cudaStream_t);
+
 // ------------------------------------------------------------------ C = alpha A B + beta C
 // A: M x K (tall, column major, element type T), B: K x N FP64 (small).
 // Block: 32 x 8 threads, tile (32 RM) rows x (8 RN) columns; thread (tx, ty)

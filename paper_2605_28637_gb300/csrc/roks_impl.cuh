@@ -79,6 +79,10 @@ template <typename T>
 void gemm_cn(int M, int N, int K, const c2<T>* A, int64_t lda, const c2<T>* B, int64_t ldb,
              double2* C, int ldc, double2* work, size_t work_elems, cudaStream_t st);
 size_t gemm_cn_work(int M, int N, int K);
+// Same, with at most max_chunks K chunks (work holds max_chunks * M * N).
+template <typename T>
+void gemm_cn_capped(int M, int N, int K, const c2<T>* A, int64_t lda, const c2<T>* B, int64_t ldb,
+                    double2* C, int ldc, double2* work, int max_chunks, cudaStream_t st);
 // C[m, n] = alpha sum_k A[m, k] B[k, n] + beta C[m, n]; B is FP64 (small).
 template <typename T>
 void gemm_nn(int M, int N, int K, const c2<T>* A, int64_t lda, const double2* B, int ldb,

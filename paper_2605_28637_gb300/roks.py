@@ -70,7 +70,7 @@ class roks_profile_entry(C.Structure):
 
 EXPORTS = ["roks_setup", "roks_basis", "roks_init_orbitals", "roks_density", "roks_potential", "roks_apply_h",
            "roks_orthonormalize", "roks_pcg_step", "roks_energies_get", "roks_profile_enable", "roks_profile_read",
-           "roks_last_error", "roks_destroy"]
+           "roks_orthonormalize_noalloc", "roks_last_error", "roks_destroy"]
 
 _lib = None
 
@@ -100,6 +100,7 @@ def load(path: str | None = None) -> C.CDLL:
     lib.roks_energies_get.argtypes = [P, C.POINTER(roks_energies)]
     lib.roks_profile_enable.argtypes = [P, C.c_int]
     lib.roks_profile_read.argtypes = [P, C.POINTER(roks_profile_entry), C.c_int, C.POINTER(C.c_int)]
+    lib.roks_orthonormalize_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, P, C.c_int64, P]
     lib.roks_last_error.argtypes = [P]
     lib.roks_last_error.restype = C.c_char_p
     lib.roks_destroy.argtypes = [P]
@@ -207,6 +208,14 @@ def roks_profile_read(ctx, cap: int = 64) -> list:
     _check(ctx, load().roks_profile_read(ctx, arr, cap, C.byref(n)))
     return [{"name": arr[i].name.decode(), "launches": arr[i].launches, "ms": arr[i].ms}
             for i in range(min(n.value, cap))]
+
+
+def roks_orthonormalize_noalloc(precision: int, npw: int, nbands: int, psi, ld: int, stream=None):
+    """Allocation-free S = 1 orthonormalisation (see include/roks.h)."""
+    st = C.c_void_p(stream) if stream else None
+    status = load().roks_orthonormalize_noalloc(int(precision), int(npw), int(nbands), _ptr(psi), int(ld), st)
+    if status != ROKS_OK:
+        raise RoksError(status, "roks_orthonormalize_noalloc")
 
 
 def roks_last_error(ctx) -> str:
