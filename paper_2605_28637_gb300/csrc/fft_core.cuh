@@ -10,6 +10,7 @@
 // so the pass arithmetic can also be exercised on the CPU.
 #pragma once
 
+#include <utility>
 #include <vector_types.h>
 
 #ifndef __CUDACC__
@@ -51,8 +52,19 @@ __host__ __device__ __forceinline__ V mul_i(V a) {
 }
 
 // ---------------------------------------------------------------- plans
-// Radix sequence of a length: factors of 8 first, then 5, 4, 3, 2.
+// Radix sequence of a transform length.  The grid sizes of the workloads get
+// two passes with register codelets up to 16 points (96 = 12 x 8,
+// 120 = 12 x 10, 72 = 9 x 8, 48 = 8 x 6, 24 = 8 x 3, 32 = 8 x 4, 16 = 4 x 4);
+// other lengths fall back to factors of 8, 5, 4, 3, 2 in that order.
 __host__ __device__ constexpr int plan_radix(int n, int pass) {
+    switch (n) {
+        case 96: return pass == 0 ? 12 : (pass == 1 ? 8 : 1);
+        case 120: return pass == 0 ? 12 : (pass == 1 ? 10 : 1);
+        case 72: return pass == 0 ? 9 : (pass == 1 ? 8 : 1);
+        case 48: return pass == 0 ? 8 : (pass == 1 ? 6 : 1);
+        case 16: return pass == 0 ? 4 : (pass == 1 ? 4 : 1);
+        default: break;
+    }
     const int cand[5] = {8, 5, 4, 3, 2};
     int p = 0;
     for (int c = 0; c < 5; ++c) {
@@ -79,10 +91,43 @@ __host__ __device__ constexpr bool plan_ok(int n) {
     int m = n;
     for (int p = 0; p < 32 && m > 1; ++p) {
         int r = plan_radix(n, p);
-        if (r <= 1) return false;
+        if (r <= 1 || m % r != 0) return false;
         m /= r;
     }
     return m == 1;
+}
+
+// ---------------------------------------------------------------- compile-time trigonometry
+// cos and sin of 2 pi m / R from their Taylor series (argument reduced to
+// [-pi, pi]; 30 terms give full double precision there).  Used only to fold
+// the internal twiddles of the composite codelets into constants.
+__host__ __device__ constexpr double ct_pi() { return 3.14159265358979323846264338327950288; }
+__host__ __device__ constexpr double ct_series(double x, bool sine) {
+    double term = sine ? x : 1.0, sum = term;
+    const double x2 = x * x;
+    for (int k = 1; k < 30; ++k) {
+        const double a = sine ? (2.0 * k) * (2.0 * k + 1.0) : (2.0 * k - 1.0) * (2.0 * k);
+        term = -term * x2 / a;
+        sum += term;
+    }
+    return sum;
+}
+__host__ __device__ constexpr double ct_angle(int m, int r) {
+    double x = 2.0 * ct_pi() * double(m % r) / double(r);
+    if (x > ct_pi()) x -= 2.0 * ct_pi();
+    return x;
+}
+__host__ __device__ constexpr double ct_cos(int m, int r) { return ct_series(ct_angle(m, r), false); }
+__host__ __device__ constexpr double ct_sin(int m, int r) { return ct_series(ct_angle(m, r), true); }
+
+template <int... I, typename F>
+__host__ __device__ __forceinline__ void sfor_impl(std::integer_sequence<int, I...>, F&& f) {
+    (f(std::integral_constant<int, I>{}), ...);
+}
+// f(integral_constant<int, 0>) ... f(integral_constant<int, N-1>)
+template <int N, typename F>
+__host__ __device__ __forceinline__ void sfor(F&& f) {
+    sfor_impl(std::make_integer_sequence<int, N>{}, f);
 }
 
 // ---------------------------------------------------------------- codelets
@@ -155,6 +200,64 @@ template <int DIR, typename V> struct Dft<8, DIR, V> {
     }
 };
 
+// x * exp(DIR 2 pi i M / R) with M, R compile-time constants.
+template <int R, int M, int DIR, typename V>
+__host__ __device__ __forceinline__ V twiddle_const(V x) {
+    using T = decltype(x.x);
+    constexpr int m = M % R;
+    if constexpr (m == 0) {
+        return x;
+    } else if constexpr (2 * m == R) {
+        V r; r.x = -x.x; r.y = -x.y; return r;
+    } else if constexpr (4 * m == R) {
+        return mul_i<DIR>(x);
+    } else if constexpr (4 * m == 3 * R) {
+        return mul_i<-DIR>(x);
+    } else {
+        constexpr double c = ct_cos(m, R);
+        constexpr double sn = DIR * ct_sin(m, R);
+        V r;
+        r.x = x.x * T(c) - x.y * T(sn);
+        r.y = x.x * T(sn) + x.y * T(c);
+        return r;
+    }
+}
+
+// Composite DFT of R = A * B points in registers (Cooley-Tukey, decimation
+// in time): inputs n = B n1 + n2, outputs k = k1 + A k2,
+// X[k] = sum_n2 W_B^{n2 k2} W_R^{n2 k1} sum_n1 x[B n1 + n2] W_A^{n1 k1}.
+template <int A, int B, int DIR, typename V>
+struct DftAB {
+    __host__ __device__ static __forceinline__ void run(V* v) {
+        constexpr int R = A * B;
+        V y[B][A];
+        sfor<B>([&](auto n2c) {
+            constexpr int n2 = decltype(n2c)::value;
+            V t[A];
+            sfor<A>([&](auto n1c) { t[decltype(n1c)::value] = v[B * decltype(n1c)::value + n2]; });
+            Dft<A, DIR, V>::run(t);
+            sfor<A>([&](auto k1c) {
+                constexpr int k1 = decltype(k1c)::value;
+                y[n2][k1] = twiddle_const<R, n2 * k1, DIR>(t[k1]);
+            });
+        });
+        sfor<A>([&](auto k1c) {
+            constexpr int k1 = decltype(k1c)::value;
+            V t[B];
+            sfor<B>([&](auto n2c) { t[decltype(n2c)::value] = y[decltype(n2c)::value][k1]; });
+            Dft<B, DIR, V>::run(t);
+            sfor<B>([&](auto k2c) { v[k1 + A * decltype(k2c)::value] = t[decltype(k2c)::value]; });
+        });
+    }
+};
+
+template <int DIR, typename V> struct Dft<6, DIR, V> : DftAB<3, 2, DIR, V> {};
+template <int DIR, typename V> struct Dft<9, DIR, V> : DftAB<3, 3, DIR, V> {};
+template <int DIR, typename V> struct Dft<10, DIR, V> : DftAB<5, 2, DIR, V> {};
+template <int DIR, typename V> struct Dft<12, DIR, V> : DftAB<4, 3, DIR, V> {};
+template <int DIR, typename V> struct Dft<15, DIR, V> : DftAB<5, 3, DIR, V> {};
+template <int DIR, typename V> struct Dft<16, DIR, V> : DftAB<4, 4, DIR, V> {};
+
 // ---------------------------------------------------------------- Stockham
 // One pass of radix R with Ns = NS over all TL lines of a tile, in place.
 // tw[t] = exp(-2 pi i t / N); the inverse (DIR = +1) uses its conjugate.
@@ -222,6 +325,91 @@ __device__ __forceinline__ void tile_fft(V* buf, const V* tw) {
     run_passes<V, N, DIR, TL, LS, NT, 0>(buf, tw);
 }
 #endif
+
+// One pass with caller-supplied input and output: ld(line, e) returns
+// element e of a line, st(line, e, v, q, r) receives output element e (q, r
+// identify the register slot, the same for every call with the same tile
+// shape).  SYNC waits between the reads and the writes (needed when both go
+// to the same shared tile).
+template <typename V, int N, int P, int DIR, int TL, int NT, bool SYNC, class Ld, class St>
+__device__ __forceinline__ void pass_io(const V* tw, Ld&& ld, St&& st) {
+    constexpr int R = plan_radix(N, P);
+    constexpr int NS = plan_ns(N, P);
+    constexpr int NBF = N / R;
+    constexpr int TOT = NBF * TL;
+    constexpr int PER = (TOT + NT - 1) / NT;
+    V v[PER][R];
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int beta = tid + q * NT;
+        if (beta < TOT) {
+            const int line = beta % TL, j = beta / TL;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[q][r] = ld(line, j + r * NBF);
+        }
+    }
+    if constexpr (SYNC) __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int beta = tid + q * NT;
+        if (beta < TOT) {
+            const int line = beta % TL, j = beta / TL;
+            twiddle_dft<V, N, R, NS, DIR>(v[q], tw, j);
+            const int base = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+            for (int r = 0; r < R; ++r) st(line, base + r * NS, v[q][r], q, r);
+        }
+    }
+}
+
+template <typename V, int N, int DIR, int TL, int LS, int NT, int P, class Sl, class Ss>
+__device__ __forceinline__ void middle_passes(V* buf, const V* tw, Sl& sl, Ss& ss) {
+    if constexpr (P < plan_passes(N) - 1) {
+        pass_io<V, N, P, DIR, TL, NT, true>(tw, sl, ss);
+        __syncthreads();
+        middle_passes<V, N, DIR, TL, LS, NT, P + 1>(buf, tw, sl, ss);
+    }
+}
+
+// Full transform of TL lines whose first pass reads through ld and whose last
+// pass writes through st; the passes in between use the shared tile buf.
+// FIRST_SMEM: ld reads buf (the caller has synchronised).  LAST_SMEM: st
+// writes buf (the caller synchronises before reading it).
+template <typename V, int N, int DIR, int TL, int LS, int NT, bool FIRST_SMEM, bool LAST_SMEM, class Ld, class St>
+__device__ __forceinline__ void fft_io(V* buf, const V* tw, Ld&& ld, St&& st) {
+    static_assert(plan_ok(N), "unsupported transform length");
+    constexpr int NP = plan_passes(N);
+    auto sl = [&](int line, int e) { return buf[e * LS + line]; };
+    auto ss = [&](int line, int e, V v, int, int) { buf[e * LS + line] = v; };
+    if constexpr (NP == 1) {
+        pass_io<V, N, 0, DIR, TL, NT, FIRST_SMEM || LAST_SMEM>(tw, ld, st);
+    } else {
+        pass_io<V, N, 0, DIR, TL, NT, FIRST_SMEM>(tw, ld, ss);
+        __syncthreads();
+        middle_passes<V, N, DIR, TL, LS, NT, 1>(buf, tw, sl, ss);
+        pass_io<V, N, NP - 1, DIR, TL, NT, LAST_SMEM>(tw, sl, st);
+    }
+}
+
+// Register slots of the last pass of an N-point transform over TL lines:
+// slot (q, r) of thread tid holds output element e of line `line`.
+template <int N, int TL, int NT>
+struct LastPassSlots {
+    static constexpr int P = plan_passes(N) - 1;
+    static constexpr int R = plan_radix(N, P);
+    static constexpr int NS = plan_ns(N, P);
+    static constexpr int TOT = (N / R) * TL;
+    static constexpr int PER = (TOT + NT - 1) / NT;
+    __device__ static __forceinline__ bool point(int tid, int q, int r, int& line, int& e) {
+        const int beta = tid + q * NT;
+        if (beta >= TOT) return false;
+        line = beta % TL;
+        const int j = beta / TL;
+        e = (j / NS) * NS * R + (j % NS) + r * NS;
+        return true;
+    }
+};
 
 // Host-side reference of the same pass sequence on one line (used by a CPU
 // test of the pass arithmetic).

@@ -396,6 +396,121 @@ __global__ void __launch_bounds__(1024) k_cholesky_small(int n, const double2* _
     if (threadIdx.x == 0 && bad) flag[0] = bad;
 }
 
+// FP32 Cholesky of O (FP64 input) and X = L^{-1} (written as FP64), one block,
+// n <= kSmallN: the first half of the refined factorisation below.
+__global__ void __launch_bounds__(1024) k_cholesky_f32(int n, const double2* __restrict__ O,
+                                                       double2* __restrict__ Xout, int* flag) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* L = reinterpret_cast<float2*>(smem_raw);
+    float2* X = L + n * n;
+    __shared__ int bad;
+    __shared__ float dinv[kSmallN];
+    if (threadIdx.x == 0) bad = 0;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const double2 o = O[idx];
+        L[idx] = make_float2((float)o.x, (float)o.y);
+        X[idx] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+        if (threadIdx.x == 0) {
+            float d = L[j * n + j].x;
+            if (!(d > 0.f)) {
+                if (!bad) bad = j + 1;
+                d = 1.f;
+            }
+            const float piv = sqrtf(d);
+            L[j * n + j] = make_float2(piv, 0.f);
+            dinv[j] = 1.f / piv;
+        }
+        __syncthreads();
+        const float inv = dinv[j];
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+            const float2 v = L[j * n + i];
+            L[j * n + i] = make_float2(v.x * inv, v.y * inv);
+        }
+        __syncthreads();
+        const int m = n - j - 1;
+        for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+            const int k = t / m;
+            const int i = t - k * m;
+            if (k > i) continue;
+            const float2 a = L[j * n + j + 1 + i], b = L[j * n + j + 1 + k];
+            float2 c = L[(j + 1 + k) * n + j + 1 + i];
+            c.x -= a.x * b.x + a.y * b.y;
+            c.y -= a.y * b.x - a.x * b.y;
+            L[(j + 1 + k) * n + j + 1 + i] = c;
+        }
+        __syncthreads();
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int c = warp; c < n; c += nw) {
+        for (int i = c; i < n; ++i) {
+            float sr = 0.f, si = 0.f;
+            for (int k = c + lane; k < i; k += 32) {
+                const float2 l = L[k * n + i], x = X[c * n + k];
+                sr += l.x * x.x - l.y * x.y;
+                si += l.x * x.y + l.y * x.x;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                si += __shfl_xor_sync(0xffffffffu, si, o);
+            }
+            if (lane == 0) {
+                const float di = dinv[i];
+                X[c * n + i] = make_float2(((i == c) ? 1.f - sr : -sr) * di, -si * di);
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) Xout[idx] = make_double2(X[idx].x, X[idx].y);
+    if (threadIdx.x == 0 && bad) flag[0] = bad;
+}
+
+// D = I - N with N the first-order Cholesky correction of M = X O X^H:
+// N_ij = M_ij (i > j), N_ii = (M_ii - 1) / 2, N_ij = 0 (i < j).
+__global__ void k_refine_factor(int n, const double2* __restrict__ M, double2* __restrict__ D) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * n) return;
+    const int i = idx % n, j = idx / n;
+    const double2 m = M[idx];
+    double2 d = make_double2(0.0, 0.0);
+    if (i > j) d = make_double2(-m.x, -m.y);
+    else if (i == j) d = make_double2(1.0 - 0.5 * (m.x - 1.0), 0.0);
+    D[idx] = d;
+}
+
+// out = in^H
+__global__ void k_conj_transpose(int n, const double2* __restrict__ in, double2* __restrict__ out) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * n) return;
+    const int i = idx % n, j = idx / n;
+    const double2 v = in[(int64_t)i * n + j];
+    out[idx] = make_double2(v.x, -v.y);
+}
+
+// Cholesky inverse of FP64 accuracy from an FP32 factorisation and one
+// refinement step (n <= kSmallN): X = L32^{-1}; M = X O X^H = I + delta;
+// L^{-1} = (I - N) X with N the lower-triangular first-order factor of delta
+// (error O(|delta|^2)).  The products run in FP64 over many blocks, so the
+// serial part is FP32.  w1, w2 hold n x n each.
+void cholesky_inverse_refined(int n, const double2* O, double2* w1, double2* w2, double2* LinvH, int* flag,
+                              cudaStream_t st) {
+    const size_t sm = sizeof(float2) * 2 * n * n;
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_cholesky_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    roks::count_launch(), k_cholesky_f32<<<1, 1024, sm, st>>>(n, O, w1, flag);          // w1 = X
+    small_gemm(n, n, n, w1, n, false, O, n, false, LinvH, n, 1.0, 0.0, st);              // LinvH = X O
+    small_gemm(n, n, n, LinvH, n, false, w1, n, true, w2, n, 1.0, 0.0, st);              // w2 = X O X^H
+    const int blocks = (n * n + 127) / 128;
+    roks::count_launch(), k_refine_factor<<<blocks, 128, 0, st>>>(n, w2, LinvH);         // LinvH = I - N
+    small_gemm(n, n, n, LinvH, n, false, w1, n, false, w2, n, 1.0, 0.0, st);             // w2 = (I - N) X
+    roks::count_launch(), k_conj_transpose<<<blocks, 128, 0, st>>>(n, w2, LinvH);
+}
+
+bool cholesky_refined_supported(int n) { return n <= kSmallN; }
+
 // Cholesky O = L L^H (Crout, column by column) and the inverse of L, one
 // block.  LinvH[k, i] = conj(Linv[i, k]) so that Psi LinvH = Psi L^{-H}.
 __global__ void __launch_bounds__(1024) k_cholesky_inverse(int n, const double2* __restrict__ O, double2* L,

@@ -120,27 +120,23 @@ __global__ void __launch_bounds__(kThreads) k_band_y_inv(Sphere s, const c2<T>* 
     V* buf = reinterpret_cast<V*>(smem);
     V* tws = buf + N * LS;
     load_twiddles<V, N>(tws, tw);
+    __syncthreads();
     const int z0 = blockIdx.x * TL;
     const int p = blockIdx.y;
     const int bb = blockIdx.z;
     const int jm = s.plane_jmax[p];
     const V* in = Zc + ((int64_t)bb * s.ncol + s.plane_col0[p] + jm) * N;
-    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
-        const int e = idx / TL, line = idx - e * TL;
-        const int z = z0 + line;
-        const int j = signed_freq(e, N);
-        V v = mk<T>(T(0), T(0));
-        if (z < N && j >= -jm && j <= jm) v = in[(int64_t)j * N + z];
-        buf[e * LS + line] = v;
-    }
-    __syncthreads();
-    tile_fft<V, N, +1, TL, LS, kThreads>(buf, tws);
     V* out = Yp + ((int64_t)bb * s.np + p) * N * N;
-    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
-        const int e = idx / TL, line = idx - e * TL;
-        const int z = z0 + line;
-        if (z < N) out[(int64_t)e * N + z] = buf[e * LS + line];
-    }
+    fft_io<V, N, +1, TL, LS, kThreads, false, false>(
+        buf, tws,
+        [&](int line, int e) {
+            const int z = z0 + line, j = signed_freq(e, N);
+            return (z < N && j >= -jm && j <= jm) ? in[(int64_t)j * N + z] : mk<T>(T(0), T(0));
+        },
+        [&](int line, int e, V v, int, int) {
+            const int z = z0 + line;
+            if (z < N) out[(int64_t)e * N + z] = v;
+        });
 }
 
 template <typename T, int N>
@@ -153,25 +149,23 @@ __global__ void __launch_bounds__(kThreads) k_band_y_fwd(Sphere s, const c2<T>* 
     V* buf = reinterpret_cast<V*>(smem);
     V* tws = buf + N * LS;
     load_twiddles<V, N>(tws, tw);
+    __syncthreads();
     const int z0 = blockIdx.x * TL;
     const int p = blockIdx.y;
     const int bb = blockIdx.z;
     const V* in = Yp + ((int64_t)bb * s.np + p) * N * N;
-    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
-        const int e = idx / TL, line = idx - e * TL;
-        const int z = z0 + line;
-        buf[e * LS + line] = (z < N) ? in[(int64_t)e * N + z] : mk<T>(T(0), T(0));
-    }
-    __syncthreads();
-    tile_fft<V, N, -1, TL, LS, kThreads>(buf, tws);
     const int jm = s.plane_jmax[p];
     V* out = Zc + ((int64_t)bb * s.ncol + s.plane_col0[p] + jm) * N;
-    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
-        const int e = idx / TL, line = idx - e * TL;
-        const int z = z0 + line;
-        const int j = signed_freq(e, N);
-        if (z < N && j >= -jm && j <= jm) out[(int64_t)j * N + z] = buf[e * LS + line];
-    }
+    fft_io<V, N, -1, TL, LS, kThreads, false, false>(
+        buf, tws,
+        [&](int line, int e) {
+            const int z = z0 + line;
+            return (z < N) ? in[(int64_t)e * N + z] : mk<T>(T(0), T(0));
+        },
+        [&](int line, int e, V v, int, int) {
+            const int z = z0 + line, j = signed_freq(e, N);
+            if (z < N && j >= -jm && j <= jm) out[(int64_t)j * N + z] = v;
+        });
 }
 
 // ------------------------------------------------------------------ x stage
@@ -191,7 +185,8 @@ __device__ __forceinline__ void load_x_lines(const Sphere& s, c2<T>* buf, const 
 template <typename T, int N>
 __global__ void __launch_bounds__(kThreads) k_band_x_apply(Sphere s, const c2<T>* __restrict__ tw,
                                                            c2<T>* __restrict__ Yp,
-                                                           const T* __restrict__ Vk, int b0,
+                                                           const T* __restrict__ Vk,
+                                                           const c2<T>* __restrict__ Xx, int b0,
                                                            int n_closed, T scale) {
     using V = c2<T>;
     constexpr int TL = tile_lines(N), LS = TL + 1;
@@ -199,107 +194,183 @@ __global__ void __launch_bounds__(kThreads) k_band_x_apply(Sphere s, const c2<T>
     V* buf = reinterpret_cast<V*>(smem);
     V* tws = buf + N * LS;
     load_twiddles<V, N>(tws, tw);
+    __syncthreads();
     const int z0 = blockIdx.x * TL;
     const int y = blockIdx.y;
     const int bb = blockIdx.z;
     const int b = b0 + bb;
     const int cls = b < n_closed ? 0 : b - n_closed + 1;
     V* Ypb = Yp + (int64_t)bb * s.np * N * N;
-    load_x_lines<T, N>(s, buf, Ypb, y, z0);
-    __syncthreads();
-    tile_fft<V, N, +1, TL, LS, kThreads>(buf, tws);
     const T* Vc = Vk + (int64_t)cls * N * N * N;
-    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
-        const int e = idx / TL, line = idx - e * TL;
-        const int z = z0 + line;
-        if (z < N) {
-            const T v = Vc[((int64_t)e * N + y) * N + z] * scale;
-            V a = buf[e * LS + line];
-            buf[e * LS + line] = mk<T>(a.x * v, a.y * v);
-        }
-    }
+    const c2<T>* Xb = Xx ? Xx + (int64_t)b * N * N * N : nullptr;
+    const int nmax = s.nmax;
+    // inverse x transform; the last pass forms (V psi + X) * scale in the tile,
+    // X being the exchange field of the band (absent without exact exchange)
+    fft_io<V, N, +1, TL, LS, kThreads, false, true>(
+        buf, tws,
+        [&](int line, int e) {
+            const int z = z0 + line, i = signed_freq(e, N);
+            return (z < N && i >= -nmax && i <= nmax) ? Ypb[((int64_t)(i + nmax) * N + y) * N + z]
+                                                      : mk<T>(T(0), T(0));
+        },
+        [&](int line, int e, V v, int, int) {
+            const int z = z0 + line;
+            const int64_t gi = ((int64_t)e * N + y) * N + z;
+            const T w = (z < N) ? Vc[gi] * scale : T(0);
+            V o = mk<T>(v.x * w, v.y * w);
+            if (Xb && z < N) {
+                const V xv = Xb[gi];
+                o.x += xv.x * scale;
+                o.y += xv.y * scale;
+            }
+            buf[e * LS + line] = o;
+        });
     __syncthreads();
-    tile_fft<V, N, -1, TL, LS, kThreads>(buf, tws);
-    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
-        const int e = idx / TL, line = idx - e * TL;
-        const int z = z0 + line;
-        const int i = signed_freq(e, N);
-        if (z < N && i >= -s.nmax && i <= s.nmax)
-            Ypb[((int64_t)(i + s.nmax) * N + y) * N + z] = buf[e * LS + line];
-    }
+    // forward x transform; the last pass keeps the planes of the sphere
+    fft_io<V, N, -1, TL, LS, kThreads, true, false>(
+        buf, tws, [&](int line, int e) { return buf[e * LS + line]; },
+        [&](int line, int e, V v, int, int) {
+            const int z = z0 + line, i = signed_freq(e, N);
+            if (z < N && i >= -nmax && i <= nmax) Ypb[((int64_t)(i + nmax) * N + y) * N + z] = v;
+        });
 }
 
-// Density: one block per (z tile, y) walks all bands of the block, keeping
-// the per-point sums of its own tile entries in registers (FP32 partial sums
-// of up to 16 bands folded into FP64 for the mixed path).
+// Real-space orbitals on the full grid: Phi[b] = scale * inverse x transform
+// of the plane data (used by the exact-exchange pair densities).
 template <typename T, int N>
-__global__ void __launch_bounds__(kThreads) k_band_x_density(Sphere s, const c2<T>* __restrict__ tw,
-                                                             const c2<T>* __restrict__ Yp,
-                                                             double* __restrict__ rho3, int b0, int nbb,
-                                                             int n_closed, double scale) {
+__global__ void __launch_bounds__(kThreads) k_band_x_inv_full(Sphere s, const c2<T>* __restrict__ tw,
+                                                              const c2<T>* __restrict__ Yp,
+                                                              c2<T>* __restrict__ Phi, int b0, T scale) {
     using V = c2<T>;
     constexpr int TL = tile_lines(N), LS = TL + 1;
-    constexpr int PER = (TL * N + kThreads - 1) / kThreads;
     extern __shared__ __align__(16) unsigned char smem[];
     V* buf = reinterpret_cast<V*>(smem);
     V* tws = buf + N * LS;
     load_twiddles<V, N>(tws, tw);
+    __syncthreads();
     const int z0 = blockIdx.x * TL;
     const int y = blockIdx.y;
+    const int bb = blockIdx.z;
+    const V* Ypb = Yp + (int64_t)bb * s.np * N * N;
+    V* out = Phi + (int64_t)(b0 + bb) * N * N * N;
+    const int nmax = s.nmax;
+    fft_io<V, N, +1, TL, LS, kThreads, false, false>(
+        buf, tws,
+        [&](int line, int e) {
+            const int z = z0 + line, i = signed_freq(e, N);
+            return (z < N && i >= -nmax && i <= nmax) ? Ypb[((int64_t)(i + nmax) * N + y) * N + z]
+                                                      : mk<T>(T(0), T(0));
+        },
+        [&](int line, int e, V v, int, int) {
+            const int z = z0 + line;
+            if (z < N) out[((int64_t)e * N + y) * N + z] = mk<T>(v.x * scale, v.y * scale);
+        });
+}
+
+// Density: block (z tile, y, g) transforms the bands of group g (bands
+// b0 + g*gs ...).  The last pass of each inverse x transform leaves every
+// thread the same set of output points, so |psi|^2 is summed in registers
+// (FP32 partial sums of up to 16 bands, added in FP64).  Closed-shell sums go
+// to the group's own slot (slot[g], N^3 doubles, written in full so no
+// clearing is needed); the open bands a and b, one band each, go straight to
+// rho3.  k_density_reduce adds the slots in group order.
+template <typename T, int N>
+__global__ void __launch_bounds__(kThreads) k_band_x_density(Sphere s, const c2<T>* __restrict__ tw,
+                                                             const c2<T>* __restrict__ Yp,
+                                                             double* __restrict__ rho3, double* __restrict__ slot,
+                                                             int b0, int nbb, int gs, int n_closed, double scale) {
+    using V = c2<T>;
+    constexpr int TL = tile_lines(N), LS = TL + 1;
+    using Slots = LastPassSlots<N, TL, kThreads>;
+    constexpr int PER = Slots::PER, R = Slots::R;
+    extern __shared__ __align__(16) unsigned char smem[];
+    V* buf = reinterpret_cast<V*>(smem);
+    V* tws = buf + N * LS;
+    load_twiddles<V, N>(tws, tw);
+    __syncthreads();
+    const int z0 = blockIdx.x * TL;
+    const int y = blockIdx.y;
+    const int g = blockIdx.z;
     const int N3 = N * N * N;
-    int bb = 0;
-    while (bb < nbb) {
+    const int nmax = s.nmax;
+    const int gbeg = g * gs, gend = min(nbb, gbeg + gs);
+    double* slot_g = slot + (int64_t)g * N3;
+    bool slot_written = false;
+    int bb = gbeg;
+    while (bb < gend) {
         const int b = b0 + bb;
         const int cls = b < n_closed ? 0 : b - n_closed + 1;
-        const int seg_end = cls == 0 ? min(nbb, n_closed - b0) : bb + 1;
-        double acc[PER];
-#pragma unroll
-        for (int q = 0; q < PER; ++q) acc[q] = 0.0;
+        const int seg_end = cls == 0 ? min(gend, n_closed - b0) : bb + 1;
+        double* rr = cls == 0 ? slot_g : rho3 + (int64_t)cls * N3;
         while (bb < seg_end) {
-            T part[PER];
+            T part[PER][R];
 #pragma unroll
-            for (int q = 0; q < PER; ++q) part[q] = T(0);
+            for (int q = 0; q < PER; ++q)
+#pragma unroll
+                for (int r = 0; r < R; ++r) part[q][r] = T(0);
             const int chunk_end = min(seg_end, bb + 16);
             for (; bb < chunk_end; ++bb) {
-                load_x_lines<T, N>(s, buf, Yp + (int64_t)bb * s.np * N * N, y, z0);
+                const V* Ypb = Yp + (int64_t)bb * s.np * N * N;
+                fft_io<V, N, +1, TL, LS, kThreads, false, false>(
+                    buf, tws,
+                    [&](int line, int e) {
+                        const int z = z0 + line, i = signed_freq(e, N);
+                        return (z < N && i >= -nmax && i <= nmax) ? Ypb[((int64_t)(i + nmax) * N + y) * N + z]
+                                                                  : mk<T>(T(0), T(0));
+                    },
+                    [&](int, int, V v, int q, int r) { part[q][r] += v.x * v.x + v.y * v.y; });
                 __syncthreads();
-                tile_fft<V, N, +1, TL, LS, kThreads>(buf, tws);
+            }
+            const bool first = cls == 0 && !slot_written;
 #pragma unroll
-                for (int q = 0; q < PER; ++q) {
-                    const int idx = threadIdx.x + q * kThreads;
-                    if (idx < TL * N) {
-                        const int e = idx / TL, line = idx - e * TL;
-                        const V a = buf[e * LS + line];
-                        part[q] += a.x * a.x + a.y * a.y;
+            for (int q = 0; q < PER; ++q)
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    int line = 0, e = 0;
+                    if (Slots::point(threadIdx.x, q, r, line, e) && z0 + line < N) {
+                        double* dst = rr + ((int64_t)e * N + y) * N + z0 + line;
+                        const double add = double(part[q][r]) * scale;
+                        *dst = (cls != 0 || !first) ? *dst + add : add;
                     }
                 }
-                __syncthreads();
-            }
-#pragma unroll
-            for (int q = 0; q < PER; ++q) acc[q] += double(part[q]);
-        }
-        double* r = rho3 + (int64_t)cls * N3;
-#pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int idx = threadIdx.x + q * kThreads;
-            if (idx < TL * N) {
-                const int e = idx / TL, line = idx - e * TL;
-                const int z = z0 + line;
-                if (z < N) r[((int64_t)e * N + y) * N + z] += acc[q] * scale;
-            }
+            if (cls == 0) slot_written = true;
         }
     }
+    if (!slot_written) {
+        // a group without closed bands still owns its slot
+#pragma unroll
+        for (int q = 0; q < PER; ++q)
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                int line = 0, e = 0;
+                if (Slots::point(threadIdx.x, q, r, line, e) && z0 + line < N)
+                    slot_g[((int64_t)e * N + y) * N + z0 + line] = 0.0;
+            }
+    }
+}
+
+// rho3[0] = sum of the closed-shell slots in group order (templated only so
+// that each precision's translation unit has its own copy)
+template <typename T>
+__global__ void k_density_reduce(int64_t N3, int ng, const double* __restrict__ slot, double* __restrict__ rho) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N3) return;
+    double s = 0.0;
+    for (int g = 0; g < ng; ++g) s += slot[(int64_t)g * N3 + p];
+    rho[p] = s;
 }
 
 // ------------------------------------------------------------------ full grid
 template <typename T, int N>
-__global__ void __launch_bounds__(kThreads) k_grid_fft_z(const c2<T>* __restrict__ tw, c2<T>* data, int dir) {
+__global__ void __launch_bounds__(kThreads) k_grid_fft_z(const c2<T>* __restrict__ tw, c2<T>* data, int dir,
+                                                         int64_t bstride) {
     using V = c2<T>;
     constexpr int TL = tile_lines(N), LS = TL + 1;
     extern __shared__ __align__(16) unsigned char smem[];
     V* buf = reinterpret_cast<V*>(smem);
     V* tws = buf + N * LS;
     load_twiddles<V, N>(tws, tw);
+    data += (int64_t)blockIdx.y * bstride;
     const int l0 = blockIdx.x * TL;           // line = x * N + y
     for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
         const int line = idx / N, e = idx - line * N;
@@ -320,28 +391,29 @@ __global__ void __launch_bounds__(kThreads) k_grid_fft_z(const c2<T>* __restrict
 // estride = N^2); the tile runs over consecutive z.
 template <typename T, int N>
 __global__ void __launch_bounds__(kThreads) k_grid_fft_strided(const c2<T>* __restrict__ tw, c2<T>* data,
-                                                               int64_t ostride, int64_t estride, int dir) {
+                                                               int64_t ostride, int64_t estride, int dir,
+                                                               int64_t bstride) {
     using V = c2<T>;
     constexpr int TL = tile_lines(N), LS = TL + 1;
     extern __shared__ __align__(16) unsigned char smem[];
     V* buf = reinterpret_cast<V*>(smem);
     V* tws = buf + N * LS;
     load_twiddles<V, N>(tws, tw);
-    const int z0 = blockIdx.x * TL;
-    V* base = data + (int64_t)blockIdx.y * ostride;
-    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
-        const int e = idx / TL, line = idx - e * TL;
-        const int z = z0 + line;
-        buf[e * LS + line] = (z < N) ? base[e * estride + z] : mk<T>(T(0), T(0));
-    }
     __syncthreads();
-    if (dir > 0) tile_fft<V, N, +1, TL, LS, kThreads>(buf, tws);
-    else tile_fft<V, N, -1, TL, LS, kThreads>(buf, tws);
-    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
-        const int e = idx / TL, line = idx - e * TL;
+    const int z0 = blockIdx.x * TL;
+    V* base = data + (int64_t)blockIdx.z * bstride + (int64_t)blockIdx.y * ostride;
+    auto ld = [&](int line, int e) {
         const int z = z0 + line;
-        if (z < N) base[e * estride + z] = buf[e * LS + line];
-    }
+        return (z < N) ? base[e * estride + z] : mk<T>(T(0), T(0));
+    };
+    auto st = [&](int line, int e, V v, int, int) {
+        const int z = z0 + line;
+        if (z < N) base[e * estride + z] = v;
+    };
+    // every element is read in the first pass before any is written in the
+    // last (the tile sits between), so the transform may work in place
+    if (dir > 0) fft_io<V, N, +1, TL, LS, kThreads, false, false>(buf, tws, ld, st);
+    else fft_io<V, N, -1, TL, LS, kThreads, false, false>(buf, tws, ld, st);
 }
 
 // ------------------------------------------------------------------ launchers
@@ -367,11 +439,17 @@ struct BandFft {
         dim3 gy((N + TL - 1) / TL, s.np, nbb);
         roks::count_launch(), k_band_y_inv<T, N><<<gy, kThreads, SM, st>>>(s, tw, Zc, Yp);
     }
-    static void x_apply(const Sphere& s, const V* tw, V* Yp, const T* Vk, int b0, int nbb, int nc, T scale,
-                        cudaStream_t st) {
+    static void x_apply(const Sphere& s, const V* tw, V* Yp, const T* Vk, const V* Xx, int b0, int nbb, int nc,
+                        T scale, cudaStream_t st) {
         set_smem(k_band_x_apply<T, N>, SM);
         dim3 g((N + TL - 1) / TL, N, nbb);
-        roks::count_launch(), k_band_x_apply<T, N><<<g, kThreads, SM, st>>>(s, tw, Yp, Vk, b0, nc, scale);
+        roks::count_launch(), k_band_x_apply<T, N><<<g, kThreads, SM, st>>>(s, tw, Yp, Vk, Xx, b0, nc, scale);
+    }
+    static void x_inv_full(const Sphere& s, const V* tw, const V* Yp, V* Phi, int b0, int nbb, T scale,
+                           cudaStream_t st) {
+        set_smem(k_band_x_inv_full<T, N>, SM);
+        dim3 g((N + TL - 1) / TL, N, nbb);
+        roks::count_launch(), k_band_x_inv_full<T, N><<<g, kThreads, SM, st>>>(s, tw, Yp, Phi, b0, scale);
     }
     static void y_fwd(const Sphere& s, const V* tw, const V* Yp, V* Zc, int nbb, cudaStream_t st) {
         set_smem(k_band_y_fwd<T, N>, SM);
@@ -384,19 +462,27 @@ struct BandFft {
         dim3 gz((s.ncol + TL - 1) / TL, nbb);
         roks::count_launch(), k_band_z_fwd<T, N><<<gz, kThreads, SM, st>>>(s, tw, Zc, out, ldo, psi, ldp, g2half, wk, b0, nc);
     }
-    static void x_density(const Sphere& s, const V* tw, const V* Yp, double* rho3, int b0, int nbb, int nc,
-                          double scale, cudaStream_t st) {
+    static void x_density(const Sphere& s, const V* tw, const V* Yp, double* rho3, double* slot, int ngroups,
+                          int b0, int nbb, int nc, double scale, cudaStream_t st) {
         set_smem(k_band_x_density<T, N>, SM);
-        dim3 g((N + TL - 1) / TL, N);
-        roks::count_launch(), k_band_x_density<T, N><<<g, kThreads, SM, st>>>(s, tw, Yp, rho3, b0, nbb, nc, scale);
+        const int gs = (nbb + ngroups - 1) / ngroups;
+        const int ng = (nbb + gs - 1) / gs;
+        dim3 g((N + TL - 1) / TL, N, ng);
+        roks::count_launch(), k_band_x_density<T, N><<<g, kThreads, SM, st>>>(s, tw, Yp, rho3, slot, b0, nbb, gs, nc,
+                                                                            scale);
+        const int64_t N3 = (int64_t)N * N * N;
+        roks::count_launch(), k_density_reduce<T><<<(unsigned)((N3 + 255) / 256), 256, 0, st>>>(N3, ng, slot, rho3);
     }
-    static void grid3(const V* tw, V* data, int dir, cudaStream_t st) {
+    static void grid3(const V* tw, V* data, int dir, int batch, int64_t bstride, cudaStream_t st) {
         set_smem(k_grid_fft_z<T, N>, SM);
         set_smem(k_grid_fft_strided<T, N>, SM);
-        roks::count_launch(), k_grid_fft_z<T, N><<<(N * N + TL - 1) / TL, kThreads, SM, st>>>(tw, data, dir);
-        dim3 g((N + TL - 1) / TL, N);
-        roks::count_launch(), k_grid_fft_strided<T, N><<<g, kThreads, SM, st>>>(tw, data, (int64_t)N * N, (int64_t)N, dir);
-        roks::count_launch(), k_grid_fft_strided<T, N><<<g, kThreads, SM, st>>>(tw, data, (int64_t)N, (int64_t)N * N, dir);
+        dim3 gz((N * N + TL - 1) / TL, batch);
+        roks::count_launch(), k_grid_fft_z<T, N><<<gz, kThreads, SM, st>>>(tw, data, dir, bstride);
+        dim3 g((N + TL - 1) / TL, N, batch);
+        roks::count_launch(), k_grid_fft_strided<T, N><<<g, kThreads, SM, st>>>(tw, data, (int64_t)N * N, (int64_t)N,
+                                                                               dir, bstride);
+        roks::count_launch(), k_grid_fft_strided<T, N><<<g, kThreads, SM, st>>>(tw, data, (int64_t)N, (int64_t)N * N,
+                                                                               dir, bstride);
     }
 };
 
@@ -422,9 +508,14 @@ void band_y_inv(const Sphere& s, const c2<T>* tw, const c2<T>* Zc, c2<T>* Yp, in
     ROKS_GRID_DISPATCH(s.N, (BandFft<T, NN>::y_inv(s, tw, Zc, Yp, nbb, st)));
 }
 template <typename T>
-void band_x_apply(const Sphere& s, const c2<T>* tw, c2<T>* Yp, const T* Vk, int b0, int nbb, int n_closed,
-                  T scale, cudaStream_t st) {
-    ROKS_GRID_DISPATCH(s.N, (BandFft<T, NN>::x_apply(s, tw, Yp, Vk, b0, nbb, n_closed, scale, st)));
+void band_x_apply(const Sphere& s, const c2<T>* tw, c2<T>* Yp, const T* Vk, const c2<T>* Xx, int b0, int nbb,
+                  int n_closed, T scale, cudaStream_t st) {
+    ROKS_GRID_DISPATCH(s.N, (BandFft<T, NN>::x_apply(s, tw, Yp, Vk, Xx, b0, nbb, n_closed, scale, st)));
+}
+template <typename T>
+void band_x_inv_full(const Sphere& s, const c2<T>* tw, const c2<T>* Yp, c2<T>* Phi, int b0, int nbb, T scale,
+                     cudaStream_t st) {
+    ROKS_GRID_DISPATCH(s.N, (BandFft<T, NN>::x_inv_full(s, tw, Yp, Phi, b0, nbb, scale, st)));
 }
 template <typename T>
 void band_y_fwd(const Sphere& s, const c2<T>* tw, const c2<T>* Yp, c2<T>* Zc, int nbb, cudaStream_t st) {
@@ -437,25 +528,33 @@ void band_z_fwd(const Sphere& s, const c2<T>* tw, const c2<T>* Zc, c2<T>* out, i
                                                    st)));
 }
 template <typename T>
-void band_x_density(const Sphere& s, const c2<T>* tw, const c2<T>* Yp, double* rho3, int b0, int nbb,
-                    int n_closed, double scale, cudaStream_t st) {
-    ROKS_GRID_DISPATCH(s.N, (BandFft<T, NN>::x_density(s, tw, Yp, rho3, b0, nbb, n_closed, scale, st)));
+void band_x_density(const Sphere& s, const c2<T>* tw, const c2<T>* Yp, double* rho3, double* slot, int ngroups,
+                    int b0, int nbb, int n_closed, double scale, cudaStream_t st) {
+    ROKS_GRID_DISPATCH(s.N, (BandFft<T, NN>::x_density(s, tw, Yp, rho3, slot, ngroups, b0, nbb, n_closed, scale,
+                                                       st)));
 }
 template <typename T>
 void grid_fft3(int N, const c2<T>* tw, c2<T>* data, int dir, cudaStream_t st) {
-    ROKS_GRID_DISPATCH(N, (BandFft<T, NN>::grid3(tw, data, dir, st)));
+    ROKS_GRID_DISPATCH(N, (BandFft<T, NN>::grid3(tw, data, dir, 1, 0, st)));
+}
+template <typename T>
+void grid_fft3_batched(int N, const c2<T>* tw, c2<T>* data, int batch, int64_t bstride, int dir, cudaStream_t st) {
+    ROKS_GRID_DISPATCH(N, (BandFft<T, NN>::grid3(tw, data, dir, batch, bstride, st)));
 }
 
 #define ROKS_INSTANTIATE_FFT(T)                                                                              \
     template void band_z_inv<T>(const Sphere&, const c2<T>*, const c2<T>*, int64_t, int, int, c2<T>*,           \
                                 cudaStream_t);                                                                   \
     template void band_y_inv<T>(const Sphere&, const c2<T>*, const c2<T>*, c2<T>*, int, cudaStream_t);          \
-    template void band_x_apply<T>(const Sphere&, const c2<T>*, c2<T>*, const T*, int, int, int, T, cudaStream_t); \
+    template void band_x_apply<T>(const Sphere&, const c2<T>*, c2<T>*, const T*, const c2<T>*, int, int, int, T,  \
+                                  cudaStream_t);                                                                 \
+    template void band_x_inv_full<T>(const Sphere&, const c2<T>*, const c2<T>*, c2<T>*, int, int, T, cudaStream_t); \
+    template void grid_fft3_batched<T>(int, const c2<T>*, c2<T>*, int, int64_t, int, cudaStream_t);             \
     template void band_y_fwd<T>(const Sphere&, const c2<T>*, const c2<T>*, c2<T>*, int, cudaStream_t);          \
     template void band_z_fwd<T>(const Sphere&, const c2<T>*, const c2<T>*, c2<T>*, int64_t, const c2<T>*,        \
                                 int64_t, const T*, const T*, int, int, int, cudaStream_t);                      \
-    template void band_x_density<T>(const Sphere&, const c2<T>*, const c2<T>*, double*, int, int, int, double,  \
-                                    cudaStream_t);                                                               \
+    template void band_x_density<T>(const Sphere&, const c2<T>*, const c2<T>*, double*, double*, int, int, int,  \
+                                    int, double, cudaStream_t);                                                  \
     template void grid_fft3<T>(int, const c2<T>*, c2<T>*, int, cudaStream_t);
 
 }  // namespace roks

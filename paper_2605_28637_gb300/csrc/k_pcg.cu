@@ -69,17 +69,22 @@ void pcg_rotation(int nb, const double2* Theta, const double* d, const int* shel
 // d_m = <m|F^c|m>.  Closed bands: Re theta_mm.  Open bands:
 // w_c (<m|T|m> + <m|V_nl|m>) + <m|V^c|m> with the local part from rho_m.
 __global__ void k_pcg_diag(int nb, int n_closed, const double2* __restrict__ Th, const double* __restrict__ kin_b,
-                           const double* __restrict__ nl_b, const double* __restrict__ open_vc, double wc,
-                           double* __restrict__ d) {
+                           const double* __restrict__ nl_b, const double* __restrict__ open_vc,
+                           const double* __restrict__ open_x, double wc, double* __restrict__ d) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= nb) return;
-    if (m < n_closed) d[m] = Th[(int64_t)m * nb + m].x;
-    else d[m] = wc * (kin_b[m] + nl_b[m]) + open_vc[m - n_closed];
+    if (m < n_closed) {
+        d[m] = Th[(int64_t)m * nb + m].x;
+    } else {
+        d[m] = wc * (kin_b[m] + nl_b[m]) + open_vc[m - n_closed];
+        if (open_x) d[m] += open_x[m - n_closed];
+    }
 }
 
 void pcg_diag(int nb, int n_closed, const double2* Theta, const double* kin_b, const double* nl_b,
-              const double* open_vc, double wc, double* d, cudaStream_t st) {
-    roks::count_launch(), k_pcg_diag<<<(nb + 127) / 128, 128, 0, st>>>(nb, n_closed, Theta, kin_b, nl_b, open_vc, wc, d);
+              const double* open_vc, const double* open_x, double wc, double* d, cudaStream_t st) {
+    roks::count_launch(), k_pcg_diag<<<(nb + 127) / 128, 128, 0, st>>>(nb, n_closed, Theta, kin_b, nl_b, open_vc,
+                                                                     open_x, wc, d);
 }
 
 __global__ void k_pcg_rot_dots(int nb, const double2* __restrict__ A, const double2* __restrict__ Ap,

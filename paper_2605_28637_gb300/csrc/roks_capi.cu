@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/roks.h"
+#include "roks_exx.cuh"
 #include "roks_grid.cuh"
 
 using namespace roks;
@@ -50,6 +51,7 @@ struct roks_ctx {
     void *d_Zc = nullptr, *d_Yp = nullptr;
     // grid
     double* d_rho3 = nullptr;
+    double* d_rho_slot = nullptr;   // closed-shell density partials per band group
     double* d_xc3 = nullptr;
     double2* d_grid = nullptr;
     void* d_Vk = nullptr;
@@ -70,6 +72,12 @@ struct roks_ctx {
     double* d_expm_info = nullptr;
     int* d_flag = nullptr;
     PcgScalars* d_sc = nullptr;
+    // exact exchange (alpha != 0)
+    void *d_Phi = nullptr, *d_Xx = nullptr, *d_exbuf = nullptr, *d_vG = nullptr;
+    int *d_pj = nullptr, *d_pn = nullptr;
+    double *d_expart = nullptr, *d_Kmat = nullptr, *d_hf2 = nullptr, *d_exopen = nullptr;
+    int npairs = 0, exx_batch = 0;
+    ExxCoef exc{};
     // state
     const void* cache_psi = nullptr;   // potentials valid for this buffer (pcg chain)
     bool pot_valid = false;
@@ -183,6 +191,34 @@ struct Impl {
     static V* cv(void* p) { return static_cast<V*>(p); }
     static const V* ccv(const void* p) { return static_cast<const V*>(p); }
 
+    // Exact exchange of the bands whose plane data sit in Yp: real-space
+    // orbitals, pair integrals, energies and (want_field) the exchange fields.
+    static void exchange(roks_ctx* ctx, bool want_field) {
+        const Sphere s = sphere(ctx);
+        cudaStream_t st = ctx->st;
+        band_x_inv_full<T>(s, ccv(ctx->d_tw), cv(ctx->d_Yp), cv(ctx->d_Phi), 0, ctx->nb, T(1.0 / std::sqrt(ctx->omega)),
+                           st);
+        ExxArgs<T> a;
+        a.N = ctx->N;
+        a.nb = ctx->nb;
+        a.npairs = ctx->npairs;
+        a.batch = ctx->exx_batch;
+        a.L = ctx->L;
+        a.tw = ccv(ctx->d_tw);
+        a.vG = static_cast<const T*>(ctx->d_vG);
+        a.Phi = ccv(ctx->d_Phi);
+        a.X = cv(ctx->d_Xx);
+        a.buf = cv(ctx->d_exbuf);
+        a.pj = ctx->d_pj;
+        a.pn = ctx->d_pn;
+        a.part = ctx->d_expart;
+        a.Kmat = ctx->d_Kmat;
+        a.hf2 = ctx->d_hf2;
+        a.open_diag = ctx->d_exopen;
+        a.cf = ctx->exc;
+        exx_pairs<T>(a, want_field, st);
+    }
+
     // rho3, kin_b, nl_b of psi.  Bgiven: projector coefficients of psi if known.
     static roks_status density(roks_ctx* ctx, const void* psi, int64_t ld, const double2* Bgiven) {
         const Sphere s = sphere(ctx);
@@ -190,10 +226,15 @@ struct Impl {
         const V* p = ccv(psi);
         { PROF("fft_z_inv"); band_z_inv<T>(s, ccv(ctx->d_tw), p, ld, 0, ctx->nb, cv(ctx->d_Zc), st); }
         { PROF("fft_y_inv"); band_y_inv<T>(s, ccv(ctx->d_tw), cv(ctx->d_Zc), cv(ctx->d_Yp), ctx->nb, st); }
+        if (ctx->alpha != 0.0) {
+            PROF("exchange");
+            exchange(ctx, false);
+        }
         CK(cudaMemsetAsync(ctx->d_rho3, 0, sizeof(double) * 3 * (size_t)ctx->N * ctx->N * ctx->N, st));
         {
             PROF("fft_x_density");
-            band_x_density<T>(s, ccv(ctx->d_tw), cv(ctx->d_Yp), ctx->d_rho3, 0, ctx->nb, ctx->nc, 1.0 / ctx->omega, st);
+            band_x_density<T>(s, ccv(ctx->d_tw), cv(ctx->d_Yp), ctx->d_rho3, ctx->d_rho_slot, kDensityGroups, 0,
+                              ctx->nb, ctx->nc, 1.0 / ctx->omega, st);
         }
         column_sums<T>(0, ctx->npw, ctx->nb, p, ld, nullptr, 0, ctx->d_g2, ctx->d_colpart, ctx->d_kin_b, st);
         const double2* B = Bgiven;
@@ -216,7 +257,7 @@ struct Impl {
         potentials<T>(ctx->N, ctx->L, ctx->d_rho3, ctx->d_vloc, ctx->cf, reinterpret_cast<V*>(ctx->d_grid),
                       ctx->d_xc3, ccv(ctx->d_tw), static_cast<T*>(ctx->d_Vk), nullptr, ctx->d_part, ctx->d_out6, st);
         energy_combine(ctx->d_kin_b, ctx->d_nl_b, ctx->nb, ctx->d_wband, ctx->d_out6, ctx->cM, ctx->cT,
-                       ctx->alpha, nullptr, ctx->d_E, st);
+                       ctx->alpha, ctx->alpha != 0.0 ? ctx->d_hf2 : nullptr, ctx->d_E, st);
         CK(cudaGetLastError());
         return ROKS_OK;
     }
@@ -230,9 +271,14 @@ struct Impl {
         const int N = ctx->N;
         { PROF("fft_z_inv"); band_z_inv<T>(s, ccv(ctx->d_tw), p, ld, 0, ctx->nb, cv(ctx->d_Zc), st); }
         { PROF("fft_y_inv"); band_y_inv<T>(s, ccv(ctx->d_tw), cv(ctx->d_Zc), cv(ctx->d_Yp), ctx->nb, st); }
+        if (ctx->alpha != 0.0) {
+            PROF("exchange");
+            exchange(ctx, true);
+        }
         {
             PROF("fft_x_apply");
-            band_x_apply<T>(s, ccv(ctx->d_tw), cv(ctx->d_Yp), static_cast<const T*>(ctx->d_Vk), 0, ctx->nb, ctx->nc,
+            band_x_apply<T>(s, ccv(ctx->d_tw), cv(ctx->d_Yp), static_cast<const T*>(ctx->d_Vk),
+                            ctx->alpha != 0.0 ? ccv(ctx->d_Xx) : nullptr, 0, ctx->nb, ctx->nc,
                             T(1.0 / (double(N) * N * N)), st);
         }
         { PROF("fft_y_fwd"); band_y_fwd<T>(s, ccv(ctx->d_tw), cv(ctx->d_Yp), cv(ctx->d_Zc), ctx->nb, st); }
@@ -270,23 +316,40 @@ struct Impl {
     static roks_status orth(roks_ctx* ctx, const void* in, int64_t ldi, void* out, int64_t ldo, double2* Bout) {
         cudaStream_t st = ctx->st;
         const int nb = ctx->nb;
-        PROF("orthonormalize");
-        gemm_cn<T>(nb, nb, ctx->npw, ccv(in), ldi, ccv(in), ldi, ctx->d_O, nb, ctx->d_gemm_work,
-                   ctx->gemm_work_elems, st);
+        {
+            PROF("orth_overlap");
+            gemm_cn<T>(nb, nb, ctx->npw, ccv(in), ldi, ccv(in), ldi, ctx->d_O, nb, ctx->d_gemm_work,
+                       ctx->gemm_work_elems, st);
+        }
         if (ctx->nproj > 0) {
-            gemm_cn<T>(ctx->nproj, nb, ctx->npw, ccv(ctx->d_P), ctx->ld_min, ccv(in), ldi, ctx->d_B2, ctx->nproj,
-                       ctx->d_gemm_work, ctx->gemm_work_elems, st);
+            {
+                PROF("proj_PhPsi");
+                gemm_cn<T>(ctx->nproj, nb, ctx->npw, ccv(ctx->d_P), ctx->ld_min, ccv(in), ldi, ctx->d_B2, ctx->nproj,
+                           ctx->d_gemm_work, ctx->gemm_work_elems, st);
+            }
+            PROF("orth_small");
             apply_DQ(ctx->nproj, nb, ctx->d_B2, ctx->d_blk_off, ctx->d_blk_n, ctx->d_Drow, ctx->d_Qrow, nullptr,
                      nullptr, ctx->d_QB, st);
             small_gemm(nb, nb, ctx->nproj, ctx->d_B2, ctx->nproj, true, ctx->d_QB, ctx->nproj, false, ctx->d_O, nb,
                        1.0, 1.0, st);
         }
-        hermitize(nb, ctx->d_O, st);
-        cholesky_inverse(nb, ctx->d_O, ctx->d_L, ctx->d_LinvH, ctx->d_flag, st);
-        gemm_nn<T>(ctx->npw, nb, nb, ccv(in), ldi, ctx->d_LinvH, nb, cv(out), ldo, 1.0, 0.0, st);
-        if (Bout && ctx->nproj > 0)
+        {
+            PROF("orth_cholesky");
+            hermitize(nb, ctx->d_O, st);
+            if (ctx->prec == ROKS_MIXED && cholesky_refined_supported(nb))
+                cholesky_inverse_refined(nb, ctx->d_O, ctx->d_L, ctx->d_e1, ctx->d_LinvH, ctx->d_flag, st);
+            else
+                cholesky_inverse(nb, ctx->d_O, ctx->d_L, ctx->d_LinvH, ctx->d_flag, st);
+        }
+        {
+            PROF("orth_apply");
+            gemm_nn<T>(ctx->npw, nb, nb, ccv(in), ldi, ctx->d_LinvH, nb, cv(out), ldo, 1.0, 0.0, st);
+        }
+        if (Bout && ctx->nproj > 0) {
+            PROF("orth_small");
             small_gemm(ctx->nproj, nb, nb, ctx->d_B2, ctx->nproj, false, ctx->d_LinvH, nb, false, Bout, ctx->nproj,
                        1.0, 0.0, st);
+        }
         CK(cudaGetLastError());
         return ROKS_OK;
     }
@@ -366,7 +429,8 @@ struct Impl {
             gemm_cn<T>(nb, nb, npw, ccv(psi), ld, ccv(ctx->W_F), l, ctx->d_Th, nb, ctx->d_gemm_work,
                        ctx->gemm_work_elems, st);
         }
-        pcg_diag(nb, ctx->nc, ctx->d_Th, ctx->d_kin_b, ctx->d_nl_b, ctx->d_out6 + 4, ctx->cf.w[0], ctx->d_d, st);
+        pcg_diag(nb, ctx->nc, ctx->d_Th, ctx->d_kin_b, ctx->d_nl_b, ctx->d_out6 + 4,
+                 ctx->alpha != 0.0 ? ctx->d_exopen : nullptr, ctx->cf.w[0], ctx->d_d, st);
         const int ia = (ctx->mode == ROKS_MODE_SINGLET) ? ctx->nc : -1;
         const int ib = (ctx->mode == ROKS_MODE_SINGLET) ? ctx->nc + 1 : -1;
         pcg_rotation(nb, ctx->d_Th, ctx->d_d, ctx->d_shell, ctx->suppress_ab && ctx->mode == ROKS_MODE_SINGLET, ia,
@@ -468,7 +532,7 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     if (!(cell->L > 0) || !(ecut > 0) || !grid_supported(cell->grid)) return ROKS_EINVAL;
     if (occ->n_closed < 0 || occ->mode < 0 || occ->mode > 2) return ROKS_EINVAL;
     if (opt->precision != ROKS_FP64 && opt->precision != ROKS_MIXED) return ROKS_EINVAL;
-    if (opt->alpha != 0.0) return ROKS_EINVAL;   // exact exchange is not built yet
+    if (!(opt->alpha >= 0.0 && opt->alpha <= 1.0)) return ROKS_EINVAL;
     roks_ctx* ctx = new (std::nothrow) roks_ctx();
     if (!ctx) return ROKS_ENOMEM;
     ctx->st = static_cast<cudaStream_t>(cuda_stream);
@@ -534,6 +598,27 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
         ctx->cf.w[k] = w;
     }
     ctx->cf.xscale = 1.0 - opt->alpha;
+    // exchange pair weights w(k, k') = sum_ch c_L f_k f_k' (Eq. 14 with the
+    // exact-exchange energy of each configuration)
+    {
+        const double sq = std::sqrt(ctx->omega);
+        for (int k = 0; k < 3; ++k)
+            for (int k2 = 0; k2 < 3; ++k2) {
+                double w = 0, fm = 0, ft = 0;
+                for (int ch = 0; ch < 4; ++ch) {
+                    const double ff = ftab[k][ch] * ftab[k2][ch];
+                    w += cch[ch] * ff;
+                    if (ch < 2) fm += ff;
+                    else ft += ff;
+                }
+                ctx->exc.c[k][k2] = -opt->alpha * sq * w;
+                ctx->exc.fM[k][k2] = fm;
+                ctx->exc.fT[k][k2] = ft;
+                if (k == 0) ctx->exc.wxc[k2] = w;
+            }
+        ctx->exc.alpha = opt->alpha;
+        ctx->exc.n_closed = ctx->nc;
+    }
     // -------- projectors: per-projector table and block-diagonal rows
     std::vector<double> proj, Drow, Qrow, atomtab;
     std::vector<int> blk_off, blk_n;
@@ -591,6 +676,7 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     AL(ctx->d_Zc, cs * (size_t)nb * ctx->ncol * N);
     AL(ctx->d_Yp, cs * (size_t)nb * ctx->np * N * N);
     AL(ctx->d_rho3, sizeof(double) * 3 * N3);
+    AL(ctx->d_rho_slot, sizeof(double) * kDensityGroups * N3);
     AL(ctx->d_xc3, sizeof(double) * 3 * N3);
     AL(ctx->d_grid, sizeof(double2) * N3);
     AL(ctx->d_Vk, rs * 3 * N3);
@@ -619,6 +705,31 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     AL(ctx->d_expm_info, sizeof(double) * 2);
     AL(ctx->d_flag, sizeof(int) * 2);
     AL(ctx->d_sc, sizeof(PcgScalars));
+    std::vector<int> pj, pn;
+    if (opt->alpha != 0.0) {
+        for (int n2 = 0; n2 < nb; ++n2)
+            for (int j2 = 0; j2 <= n2; ++j2) {
+                pj.push_back(j2);
+                pn.push_back(n2);
+            }
+        ctx->npairs = (int)pj.size();
+        const size_t grid_bytes = cs * N3;
+        int batch = (int)((256u << 20) / grid_bytes);
+        if (batch < 1) batch = 1;
+        if (batch > 64) batch = 64;
+        if (batch > ctx->npairs) batch = ctx->npairs;
+        ctx->exx_batch = batch;
+        AL(ctx->d_Phi, cs * N3 * nb);
+        AL(ctx->d_Xx, cs * N3 * nb);
+        AL(ctx->d_exbuf, cs * N3 * batch);
+        AL(ctx->d_vG, rs * N3);
+        AL(ctx->d_pj, sizeof(int) * ctx->npairs);
+        AL(ctx->d_pn, sizeof(int) * ctx->npairs);
+        AL(ctx->d_expart, sizeof(double) * batch * kExxBlocks);
+        AL(ctx->d_Kmat, sizeof(double) * nb * nb);
+        AL(ctx->d_hf2, sizeof(double) * 2);
+        AL(ctx->d_exopen, sizeof(double) * 2);
+    }
     double* d_atoms = nullptr;
     double* d_proj = nullptr;
     AL(d_atoms, sizeof(double) * (atomtab.size() + 1));
@@ -657,6 +768,8 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     if (e == cudaSuccess) e = up(ctx->d_Qrow, Qrow.data(), sizeof(double) * Qrow.size());
     if (e == cudaSuccess) e = up(d_atoms, atomtab.data(), sizeof(double) * atomtab.size());
     if (e == cudaSuccess) e = up(d_proj, proj.data(), sizeof(double) * proj.size());
+    if (e == cudaSuccess && ctx->npairs > 0) e = up(ctx->d_pj, pj.data(), sizeof(int) * pj.size());
+    if (e == cudaSuccess && ctx->npairs > 0) e = up(ctx->d_pn, pn.data(), sizeof(int) * pn.size());
     if (e != cudaSuccess) return bail(ROKS_ECUDA, "upload");
     // typed tables
     std::vector<double> wk(ctx->cf.w, ctx->cf.w + 3);
@@ -690,6 +803,10 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
                                       static_cast<double2*>(ctx->d_P), l, ctx->st);
     else projectors_setup<float>(npw, ctx->nproj, cell->L, ctx->d_miller, d_proj, static_cast<float2*>(ctx->d_P), l,
                                  ctx->st);
+    if (opt->alpha != 0.0) {
+        if (f64) exx_setup_kernel<double>(N, cell->L, static_cast<double*>(ctx->d_vG), ctx->st);
+        else exx_setup_kernel<float>(N, cell->L, static_cast<float*>(ctx->d_vG), ctx->st);
+    }
     e = cudaStreamSynchronize(ctx->st);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return bail(ROKS_ECUDA, cudaGetErrorString(e));

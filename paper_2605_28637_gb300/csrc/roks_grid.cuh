@@ -75,7 +75,7 @@ void pcg_rotation(int nb, const double2* Theta, const double* d, const int* shel
                   int ib, double2* Gam, double2* Gin, double2* A, PcgScalars* sc, cudaStream_t st);
 // d_m = <m|F^c|m>: Re theta_mm for closed bands, from expectation values for open ones.
 void pcg_diag(int nb, int n_closed, const double2* Theta, const double* kin_b, const double* nl_b,
-              const double* open_vc, double wc, double* d, cudaStream_t st);
+              const double* open_vc, const double* open_x, double wc, double* d, cudaStream_t st);
 // sc->rot_pg = 1/2 Re sum conj(A) Gin; sc->r1, r2 as named.
 void pcg_rot_dots(int nb, const double2* A, const double2* Aprev, const double2* Gin, PcgScalars* sc,
                   cudaStream_t st);

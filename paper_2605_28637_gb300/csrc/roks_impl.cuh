@@ -54,8 +54,12 @@ void band_y_inv(const Sphere& s, const c2<T>* tw, const c2<T>* Zc, c2<T>* Yp, in
 // x stage, in place on Yp: inverse transform, multiply by V^{class(b)} * scale,
 // forward transform, keep the planes of the sphere
 template <typename T>
-void band_x_apply(const Sphere& s, const c2<T>* tw, c2<T>* Yp, const T* Vk, int b0, int nbb, int n_closed,
-                  T scale, cudaStream_t st);
+void band_x_apply(const Sphere& s, const c2<T>* tw, c2<T>* Yp, const T* Vk, const c2<T>* Xx, int b0, int nbb,
+                  int n_closed, T scale, cudaStream_t st);
+// x stage, inverse, full real-space lines: Phi[b0 + b] = scale * psi~ (N^3 each)
+template <typename T>
+void band_x_inv_full(const Sphere& s, const c2<T>* tw, const c2<T>* Yp, c2<T>* Phi, int b0, int nbb, T scale,
+                     cudaStream_t st);
 // y stage, forward: Yp -> Zc (columns of the sphere only)
 template <typename T>
 void band_y_fwd(const Sphere& s, const c2<T>* tw, const c2<T>* Yp, c2<T>* Zc, int nbb, cudaStream_t st);
@@ -63,14 +67,20 @@ void band_y_fwd(const Sphere& s, const c2<T>* tw, const c2<T>* Yp, c2<T>* Zc, in
 template <typename T>
 void band_z_fwd(const Sphere& s, const c2<T>* tw, const c2<T>* Zc, c2<T>* out, int64_t ldo, const c2<T>* psi,
                 int64_t ldp, const T* g2half, const T* wk, int b0, int nbb, int n_closed, cudaStream_t st);
-// x stage, inverse, accumulating |psi|^2 * scale into rho3 (3 x N^3, double)
+// x stage, inverse: rho3 (3 x N^3, double) = sum |psi|^2 * scale per class,
+// bands split into up to ngroups groups; slot holds ngroups x N^3 doubles.
+// rho3 classes a, b must be zero on entry (class 0 is overwritten).
+constexpr int kDensityGroups = 4;
 template <typename T>
-void band_x_density(const Sphere& s, const c2<T>* tw, const c2<T>* Yp, double* rho3, int b0, int nbb,
-                    int n_closed, double scale, cudaStream_t st);
+void band_x_density(const Sphere& s, const c2<T>* tw, const c2<T>* Yp, double* rho3, double* slot, int ngroups,
+                    int b0, int nbb, int n_closed, double scale, cudaStream_t st);
 
 // ------------------------------------------------------------ full-grid 3D FFT (in place)
 template <typename T>
 void grid_fft3(int N, const c2<T>* tw, c2<T>* data, int dir, cudaStream_t st);
+// batch grids data + k bstride, k < batch
+template <typename T>
+void grid_fft3_batched(int N, const c2<T>* tw, c2<T>* data, int batch, int64_t bstride, int dir, cudaStream_t st);
 
 // ------------------------------------------------------------ dense complex contractions
 // Cpart[chunk] (double2, M x N column major) = sum over the k of the chunk of
@@ -93,6 +103,11 @@ void small_gemm(int M, int N, int K, const double2* A, int lda, bool ca, const d
                 bool cb, double2* C, int ldc, double alpha, double beta, cudaStream_t st);
 // O (Hermitian) -> LinvH = L^{-H}, L L^H = O.  flag[0] set to 1 + column on failure.
 void cholesky_inverse(int n, const double2* O, double2* Lw, double2* LinvH, int* flag, cudaStream_t st);
+// FP32 factorisation + one FP64 refinement step (FP64 accuracy for a
+// well-conditioned O); n <= 64.  w1, w2: n x n scratch.
+void cholesky_inverse_refined(int n, const double2* O, double2* w1, double2* w2, double2* LinvH, int* flag,
+                              cudaStream_t st);
+bool cholesky_refined_supported(int n);
 // E = expm(scale_dev[0] * A), A anti-Hermitian, Taylor + scaling and squaring.
 void expm_scaled(int n, const double2* A, const double* scale_dev, double2* E, double2* w1, double2* w2,
                  double2* w3, double* sdev, cudaStream_t st);

@@ -211,3 +211,63 @@ def test_mixed_precision_pcg_tiny():
         info = ctx.pcg_step(psi)
         P, ref = pcg.step(P)
         assert abs(info["E_new"] - ref.E_new) < 1e-5, (it, info["E_new"], ref.E_new)
+
+
+# ------------------------------------------------------------------ exact exchange
+HYBRID = {
+    "tiny16-hybrid": dict(alpha=1.0 / 3.0),
+    "grid24-hybrid-2batches": dict(grid=24, L=11.0, ecut=12.0, n_closed=10, alpha=1.0 / 3.0),
+}
+
+
+@pytest.mark.parametrize("name", list(HYBRID))
+def test_exact_exchange_fp64(name):
+    """Pair integrals, exchange energies and F|n> with the exchange operator
+    (truncated Coulomb kernel, alpha = 1/3) against the oracle, 1e-10."""
+    cfg = cfg_of(**HYBRID[name])
+    roks, ctx, s = setup_pair(cfg)
+    u = syn.orbital_uniforms(cfg, ctx.npw)
+    psi = ctx.init_orbitals(u)
+    P_ref = s.initial_orbitals(u)
+    ctx.density(psi)
+    E = ctx.potential()
+    Eref = s.energies(P_ref)
+    for k_gpu, k_ref in (("E_hf_M", "hf_M"), ("E_hf_T", "hf_T"), ("E_x_M", "x_M"), ("E_total", "total")):
+        assert abs(E[k_gpu] - Eref[k_ref]) <= TOL64 * max(1.0, abs(Eref[k_ref])), k_gpu
+    f, sp, _ = ctx.apply_h(psi)
+    pot = s.potentials(s.class_densities(P_ref))
+    F_ref, _ = s.apply(P_ref, pot)
+    assert rel(to_np(f, s.npw), F_ref) < TOL64
+
+
+def test_exact_exchange_pcg_fp64():
+    cfg = cfg_of(**HYBRID["tiny16-hybrid"])
+    roks = built()
+    ctx = roks.Context(cfg, "fp64")
+    s = R.System(cfg)
+    u = syn.orbital_uniforms(cfg, ctx.npw)
+    psi = ctx.init_orbitals(u)
+    P = s.initial_orbitals(u)
+    pcg = R.PCG(s)
+    for it in range(4):
+        info = ctx.pcg_step(psi)
+        P, ref = pcg.step(P)
+        assert abs(info["E_new"] - ref.E_new) <= TOL64 * max(1, abs(ref.E_new)), (it, info["E_new"], ref.E_new)
+        assert abs(info["step"] - ref.step) <= 1e-8 * ref.step
+
+
+def test_exact_exchange_mixed():
+    cfg = cfg_of(**HYBRID["grid24-hybrid-2batches"])
+    roks, ctx, s = setup_pair(cfg, "mixed")
+    u = syn.orbital_uniforms(cfg, ctx.npw)
+    psi = ctx.init_orbitals(u)
+    P_ref = s.initial_orbitals(u)
+    ctx.density(psi)
+    E = ctx.potential()
+    Eref = s.energies(P_ref)
+    assert abs(E["E_total"] - Eref["total"]) < 2e-5
+    assert abs(E["E_hf_M"] - Eref["hf_M"]) < 2e-5
+    f, _, _ = ctx.apply_h(to_dev(ctx, P_ref))
+    pot = s.potentials(s.class_densities(P_ref))
+    F_ref, _ = s.apply(P_ref, pot)
+    assert rel(to_np(f, s.npw), F_ref) < 2e-5
