@@ -70,6 +70,7 @@ struct roks_ctx {
     size_t gemm_work_elems = 0;
     double *d_kin_b = nullptr, *d_nl_b = nullptr, *d_colpart = nullptr, *d_colout = nullptr, *d_d = nullptr;
     double* d_expm_info = nullptr;
+    void* d_bigwork = nullptr;      // blocked Cholesky / exponential for more than 64 bands
     int* d_flag = nullptr;
     PcgScalars* d_sc = nullptr;
     // exact exchange (alpha != 0)
@@ -336,7 +337,10 @@ struct Impl {
         {
             PROF("orth_cholesky");
             hermitize(nb, ctx->d_O, st);
-            if (ctx->prec == ROKS_MIXED && cholesky_refined_supported(nb))
+            if (nb > 64)
+                cholesky_inverse_big(nb, ctx->d_O, ctx->d_bigwork, ctx->prec == ROKS_FP64, ctx->d_LinvH, ctx->d_flag,
+                                     st);
+            else if (ctx->prec == ROKS_MIXED && cholesky_refined_supported(nb))
                 cholesky_inverse_refined(nb, ctx->d_O, ctx->d_L, ctx->d_e1, ctx->d_LinvH, ctx->d_flag, st);
             else
                 cholesky_inverse(nb, ctx->d_O, ctx->d_L, ctx->d_LinvH, ctx->d_flag, st);
@@ -395,11 +399,16 @@ struct Impl {
         {
             PROF("rotate");
             axpy<T>(ctx->npw, nb, ccv(psi), ld, ccv(ctx->W_s), l, scd + step_field, 1.0, cv(ctx->W_Y), l, st);
-            const bool small32 = (ctx->prec == ROKS_MIXED) && expm_small_f32(nb, ctx->d_Atot, scd + step_field,
-                                                                              ctx->d_U, st);
-            if (!small32)
-                expm_scaled(nb, ctx->d_Atot, scd + step_field, ctx->d_U, ctx->d_e1, ctx->d_e2, ctx->d_e3,
-                            ctx->d_expm_info, st);
+            if (nb > 64) {
+                expm_big(nb, ctx->d_Atot, scd + step_field, ctx->d_U, ctx->d_bigwork, ctx->d_expm_info,
+                         ctx->prec == ROKS_FP64, st);
+            } else {
+                const bool small32 = (ctx->prec == ROKS_MIXED) &&
+                                     expm_small_f32(nb, ctx->d_Atot, scd + step_field, ctx->d_U, st);
+                if (!small32)
+                    expm_scaled(nb, ctx->d_Atot, scd + step_field, ctx->d_U, ctx->d_e1, ctx->d_e2, ctx->d_e3,
+                                ctx->d_expm_info, st);
+            }
             gemm_nn<T>(ctx->npw, nb, nb, ccv(ctx->W_Y), l, ctx->d_U, nb, cv(ctx->W_Y2), l, 1.0, 0.0, st);
         }
         roks_status r = orth(ctx, ctx->W_Y2, l, out, ldo, ctx->d_B);
@@ -703,6 +712,10 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     AL(ctx->d_colout, sizeof(double) * 2 * nb);
     AL(ctx->d_d, sizeof(double) * nb);
     AL(ctx->d_expm_info, sizeof(double) * 2);
+    if (nb > 64) {
+        const size_t w1 = cholesky_big_work_bytes(nb, f64), w2 = expm_big_work_bytes(nb, f64);
+        AL(ctx->d_bigwork, w1 > w2 ? w1 : w2);
+    }
     AL(ctx->d_flag, sizeof(int) * 2);
     AL(ctx->d_sc, sizeof(PcgScalars));
     std::vector<int> pj, pn;

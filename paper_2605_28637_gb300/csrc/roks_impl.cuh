@@ -108,6 +108,16 @@ void cholesky_inverse(int n, const double2* O, double2* Lw, double2* LinvH, int*
 void cholesky_inverse_refined(int n, const double2* O, double2* w1, double2* w2, double2* LinvH, int* flag,
                               cudaStream_t st);
 bool cholesky_refined_supported(int n);
+// Blocked multi-block Cholesky inverse for any n (FP32 or FP64 arithmetic);
+// work: cholesky_big_work_bytes(n, fp64).
+size_t cholesky_big_work_bytes(int n, bool fp64);
+void cholesky_inverse_big(int n, const double2* O, void* work, bool fp64, double2* LinvH, int* flag,
+                          cudaStream_t st);
+// exp(scale A) for any n on a tiled square GEMM (FP32 degree 8 or FP64
+// degree 16); work: expm_big_work_bytes(n, fp64); info: 1 double.
+size_t expm_big_work_bytes(int n, bool fp64);
+void expm_big(int n, const double2* A, const double* scale_dev, double2* E, void* work, double* info, bool fp64,
+              cudaStream_t st);
 // E = expm(scale_dev[0] * A), A anti-Hermitian, Taylor + scaling and squaring.
 void expm_scaled(int n, const double2* A, const double* scale_dev, double2* E, double2* w1, double2* w2,
                  double2* w3, double* sdev, cudaStream_t st);

@@ -271,3 +271,40 @@ def test_exact_exchange_mixed():
     pot = s.potentials(s.class_densities(P_ref))
     F_ref, _ = s.apply(P_ref, pot)
     assert rel(to_np(f, s.npw), F_ref) < 2e-5
+
+
+# ------------------------------------------------------------------ more than 64 bands
+def test_many_bands_blocked_paths_fp64():
+    """70 bands (beyond the single-block band-space kernels): the blocked
+    Cholesky inverse and the tiled exponential follow the oracle's PCG."""
+    cfg = cfg_of(grid=32, L=14.0, ecut=16.0, n_closed=68)
+    roks = built()
+    ctx = roks.Context(cfg, "fp64")
+    s = R.System(cfg)
+    assert s.nb == 70
+    u = syn.orbital_uniforms(cfg, ctx.npw)
+    psi = ctx.init_orbitals(u)
+    P = s.initial_orbitals(u)
+    assert rel(to_np(psi, s.npw), P) < TOL64
+    pcg = R.PCG(s)
+    for it in range(2):
+        info = ctx.pcg_step(psi)
+        P, ref = pcg.step(P)
+        assert abs(info["E_new"] - ref.E_new) <= TOL64 * max(1, abs(ref.E_new)), (it, info["E_new"], ref.E_new)
+
+
+def test_many_bands_blocked_paths_mixed():
+    cfg = cfg_of(grid=32, L=14.0, ecut=16.0, n_closed=68)
+    roks = built()
+    ctx = roks.Context(cfg, "mixed")
+    s = R.System(cfg)
+    u = syn.orbital_uniforms(cfg, ctx.npw)
+    psi = ctx.init_orbitals(u)
+    Y = to_np(psi, s.npw)
+    assert np.abs(s.overlap(Y) - np.eye(s.nb)).max() < 5e-6
+    P = s.initial_orbitals(u)
+    pcg = R.PCG(s)
+    for it in range(2):
+        info = ctx.pcg_step(psi)
+        P, ref = pcg.step(P)
+        assert abs(info["E_new"] - ref.E_new) < 5e-5, (it, info["E_new"], ref.E_new)
