@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--converge-iters", type=int, default=400,
                     help="iteration cap of the time-to-convergence runs (0 skips them)")
+    ap.add_argument("--converge-seconds", type=float, default=60.0,
+                    help="wall-clock cap of each time-to-convergence run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -262,8 +264,9 @@ def time_pcg(ctx, psi, steps, torch, profile=False):
     return e0.elapsed_time(e1), infos, prof
 
 
-def converge(cfg, precision, cap, torch):
-    """Seconds and iterations of PCG from the seeded start to |dE| < 1e-6 Ha twice."""
+def converge(cfg, precision, cap, torch, max_seconds):
+    """Seconds and iterations of PCG from the seeded start to |dE| < 1e-6 Ha
+    twice, stopped after cap iterations or max_seconds of wall clock."""
     from paper_2605_28637_gb300 import roks, synthetic as syn
     ctx = roks.Context(cfg, precision, e_tol=1e-6)
     psi = ctx.init_orbitals(syn.orbital_uniforms(cfg, ctx.npw))
@@ -272,7 +275,7 @@ def converge(cfg, precision, cap, torch):
     it, info = 0, None
     for it in range(1, cap + 1):
         info = ctx.pcg_step(psi)
-        if info["converged"]:
+        if info["converged"] or time.perf_counter() - t0 > max_seconds:
             break
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
@@ -374,8 +377,8 @@ def run_gpu(args):
     # ---- time to convergence: chosen (mixed) vs plain FP64
     pcg = None
     if args.converge_iters > 0 and rank == 0:
-        mixed = converge(cfg, "mixed", args.converge_iters, torch)
-        fp64 = converge(cfg, "fp64", args.converge_iters, torch)
+        mixed = converge(cfg, "mixed", args.converge_iters, torch, args.converge_seconds)
+        fp64 = converge(cfg, "fp64", args.converge_iters, torch, args.converge_seconds)
         pcg = {"mixed": mixed, "fp64": fp64,
                "speedup_s_per_iter": fp64["s_per_iter"] / mixed["s_per_iter"],
                "dE_mixed_vs_fp64_final": (mixed["E_final"] - fp64["E_final"])

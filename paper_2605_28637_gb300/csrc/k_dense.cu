@@ -102,6 +102,11 @@ __global__ void k_chunk_sum(int M, int N, int nchunk, const double2* __restrict_
     if (lane == 0) C[(int64_t)(w / M) * ldc + (w % M)] = make_double2(sx, sy);
 }
 
+void chunk_sum(int M, int N, int nchunk, const double2* part, double2* C, int ldc, cudaStream_t st) {
+    const long long thr = (long long)M * N * 32;
+    roks::count_launch(), k_chunk_sum<<<(unsigned)((thr + 255) / 256), 256, 0, st>>>(M, N, nchunk, part, C, ldc);
+}
+
 namespace {
 struct CnPlan {
     int rm, rn, mt, nt, kchunk, nchunk;
@@ -131,10 +136,16 @@ size_t gemm_cn_work(int M, int N, int K) {
 
 template <typename T>
 void gemm_cn(int M, int N, int K, const c2<T>* A, int64_t lda, const c2<T>* B, int64_t ldb, double2* C, int ldc,
-             double2* work, size_t work_elems, cudaStream_t st) {
+             double2* work, size_t work_elems, cudaStream_t st, bool allow_tc) {
     if (M <= 0 || N <= 0) return;
+    if constexpr (sizeof(T) == 4) {
+        // mixed path: tcgen05 tensor cores (split TF32) when the shape allows
+        const int max_chunks = allow_tc ? (int)(work_elems / ((size_t)M * N)) : 0;
+        if (gemm_cn_tc(M, N, K, reinterpret_cast<const float2*>(A), lda, reinterpret_cast<const float2*>(B), ldb,
+                       C, ldc, work, max_chunks, st))
+            return;
+    }
     const CnPlan p = cn_plan(M, N, K);
-    (void)work_elems;
     dim3 g(p.mt, p.nt, p.nchunk);
     if (K <= 0) {
         cudaMemsetAsync(work, 0, sizeof(double2) * M * N, st);
@@ -266,9 +277,9 @@ void gemm_nn(int M, int N, int K, const c2<T>* A, int64_t lda, const double2* B,
 }
 
 template void gemm_cn<float>(int, int, int, const float2*, int64_t, const float2*, int64_t, double2*, int,
-                             double2*, size_t, cudaStream_t);
+                             double2*, size_t, cudaStream_t, bool);
 template void gemm_cn<double>(int, int, int, const double2*, int64_t, const double2*, int64_t, double2*, int,
-                              double2*, size_t, cudaStream_t);
+                              double2*, size_t, cudaStream_t, bool);
 template void gemm_nn<float>(int, int, int, const float2*, int64_t, const double2*, int, float2*, int64_t, double,
                              double, cudaStream_t);
 template void gemm_nn<double>(int, int, int, const double2*, int64_t, const double2*, int, double2*, int64_t,

@@ -320,7 +320,7 @@ struct Impl {
         {
             PROF("orth_overlap");
             gemm_cn<T>(nb, nb, ctx->npw, ccv(in), ldi, ccv(in), ldi, ctx->d_O, nb, ctx->d_gemm_work,
-                       ctx->gemm_work_elems, st);
+                       ctx->gemm_work_elems, st, false);
         }
         if (ctx->nproj > 0) {
             {
@@ -362,6 +362,8 @@ struct Impl {
         int flag = 0;
         CK(cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
         CK(cudaStreamSynchronize(ctx->st));
+        if (tc_timeout_take())
+            return fail(ctx, ROKS_ETIMEOUT, "a tensor-core completion wait ran out (bounded mbarrier wait)");
         if (flag) {
             CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->st));
             return fail(ctx, ROKS_ENOTPOSDEF,

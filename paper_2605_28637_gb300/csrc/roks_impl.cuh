@@ -84,11 +84,22 @@ void grid_fft3_batched(int N, const c2<T>* tw, c2<T>* data, int batch, int64_t b
 
 // ------------------------------------------------------------ dense complex contractions
 // Cpart[chunk] (double2, M x N column major) = sum over the k of the chunk of
-// conj(A[k, m]) B[k, n]; then C = sum_chunks Cpart (double2, ldc).
+// conj(A[k, m]) B[k, n]; then C = sum_chunks Cpart (double2, ldc).  FP32
+// inputs go to the tensor cores when allow_tc; the tensor-core accumulation
+// rounds towards zero, so results that must not carry that bias (the
+// overlap matrix of the orthonormalisation) pass allow_tc = false.
 template <typename T>
 void gemm_cn(int M, int N, int K, const c2<T>* A, int64_t lda, const c2<T>* B, int64_t ldb,
-             double2* C, int ldc, double2* work, size_t work_elems, cudaStream_t st);
+             double2* C, int ldc, double2* work, size_t work_elems, cudaStream_t st, bool allow_tc = true);
 size_t gemm_cn_work(int M, int N, int K);
+// C (ldc) = fixed-order sum of nchunk partials (M x N double2 each)
+void chunk_sum(int M, int N, int nchunk, const double2* part, double2* C, int ldc, cudaStream_t st);
+// tcgen05 path of the FP32 contraction (N <= 128); false when not taken.
+bool gemm_cn_tc(int M, int N, int K, const float2* A, int64_t lda, const float2* B, int64_t ldb, double2* C, int ldc,
+                double2* work, int max_chunks, cudaStream_t st);
+bool tc_enabled();
+// 1 if a tensor-core mbarrier wait gave up since the last call (then cleared)
+int tc_timeout_take();
 // Same, with at most max_chunks K chunks (work holds max_chunks * M * N).
 template <typename T>
 void gemm_cn_capped(int M, int N, int K, const c2<T>* A, int64_t lda, const c2<T>* B, int64_t ldb,
