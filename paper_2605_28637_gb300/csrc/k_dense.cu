@@ -14,179 +14,309 @@ static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long launches_take() { return g_launches.exchange(0); }
 
+// ------------------------------------------------------------------ complex multiply-accumulate
+namespace {
+template <typename T> __device__ __forceinline__ T fmat(T a, T b, T c);
+template <> __device__ __forceinline__ float fmat<float>(float a, float b, float c) { return fmaf(a, b, c); }
+template <> __device__ __forceinline__ double fmat<double>(double a, double b, double c) { return fma(a, b, c); }
+
+// acc += conj(a) b as four fused multiply-adds
+template <typename T>
+__device__ __forceinline__ void mac_cn(c2<T>& acc, const c2<T>& a, const c2<T>& b) {
+    acc.x = fmat(a.x, b.x, acc.x);
+    acc.x = fmat(a.y, b.y, acc.x);
+    acc.y = fmat(a.x, b.y, acc.y);
+    acc.y = fmat(-a.y, b.x, acc.y);
+}
+// acc += a b
+template <typename T>
+__device__ __forceinline__ void mac_nn(c2<T>& acc, const c2<T>& a, const c2<T>& b) {
+    acc.x = fmat(a.x, b.x, acc.x);
+    acc.x = fmat(-a.y, b.y, acc.x);
+    acc.y = fmat(a.x, b.y, acc.y);
+    acc.y = fmat(a.y, b.x, acc.y);
+}
+
+// Asynchronous global -> shared copy of one complex element (8 or 16
+// bytes); the destination is zero-filled when !valid (nothing is read).
+template <typename T>
+__device__ __forceinline__ void cp_elem(c2<T>* dst, const c2<T>* src, bool valid) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    const int n = valid ? (int)sizeof(c2<T>) : 0;
+    if constexpr (sizeof(c2<T>) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int NPEND>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(NPEND) : "memory"); }
+
+// Shared-memory position of tile row r when each thread owns R consecutive
+// rows: one pad element after every R rows for even R, so that the 16
+// threads of a row group read 16 different bank pairs.
+template <int R> __host__ __device__ constexpr int padpos(int r) { return (R % 2 == 0) ? r + r / R : r; }
+template <int R> __host__ __device__ constexpr int padgroup() { return (R % 2 == 0) ? R + 1 : R; }
+// row stride of a k slice: covers 16 row groups and is odd (conflict-free transposed stores)
+template <int R> __host__ __device__ constexpr int padstride() { return (16 * padgroup<R>()) | 1; }
+}  // namespace
+
 // ------------------------------------------------------------------ C = A^H B, split over K
-// A: K x M, B: K x N (column major).  A block of 16 x 16 threads owns an
-// output tile of (16 RM) x (16 RN) and one K chunk; each thread keeps an
-// RM x RN register tile.  Chunk partials are written in FP64 and summed in a
+// A: K x M, B: K x N (column major, K contiguous).  A block of TY x TX
+// threads (runtime, at most 16 x 16) owns an output tile of (TY RM) x (TX RN)
+// and one K chunk; thread (tx, ty) keeps the RM x RN register tile of rows
+// ty RM + i and columns tx RN + j.  K slices of KT are double-buffered in
+// shared memory by cp.async.  Chunk partials (element type T) are summed in a
 // fixed order by k_chunk_sum.
 template <typename T> struct CnTile { static constexpr int KT = sizeof(T) == 4 ? 32 : 16; };
-constexpr int CN_KT = 32;   // chunk granularity (a multiple of every k tile)
 
 template <typename T, int RM, int RN>
-__global__ void __launch_bounds__(256) k_gemm_cn(int M, int N, int K, int kchunk, const c2<T>* __restrict__ A,
-                                                 int64_t lda, const c2<T>* __restrict__ B, int64_t ldb,
-                                                 double2* __restrict__ part) {
+__global__ void __launch_bounds__(256) k_gemm_cn(int M, int N, int K, int kchunk, int TY, int TX,
+                                                 const c2<T>* __restrict__ A, int64_t lda,
+                                                 const c2<T>* __restrict__ B, int64_t ldb, c2<T>* __restrict__ part) {
     using V = c2<T>;
-    constexpr int TM = 16 * RM, TN = 16 * RN;
     constexpr int KT = CnTile<T>::KT;
-    __shared__ V As[KT][TM + 1];
-    __shared__ V Bs[KT][TN + 1];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    constexpr int SA = padstride<RM>(), SB = padstride<RN>();
+    extern __shared__ __align__(16) unsigned char cn_smem[];
+    V* As = reinterpret_cast<V*>(cn_smem);   // [2][KT][SA]
+    V* Bs = As + 2 * KT * SA;                // [2][KT][SB]
+    const int nthr = TX * TY, tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const int TM = TY * RM, TN = TX * RN;
     const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
     const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+    const int nk = kend > kbeg ? (kend - kbeg + KT - 1) / KT : 0;
+
+    auto stage_in = [&](int s, int k0) {
+        V* as = As + s * KT * SA;
+        V* bs = Bs + s * KT * SB;
+        for (int e = tid; e < TM * KT; e += nthr) {
+            const int r = e / KT, kk = e % KT;
+            const int m = m0 + r, k = k0 + kk;
+            const bool ok = m < M && k < kend;
+            cp_elem<T>(as + kk * SA + padpos<RM>(r), ok ? A + (int64_t)m * lda + k : A, ok);
+        }
+        for (int e = tid; e < TN * KT; e += nthr) {
+            const int c = e / KT, kk = e % KT;
+            const int n = n0 + c, k = k0 + kk;
+            const bool ok = n < N && k < kend;
+            cp_elem<T>(bs + kk * SB + padpos<RN>(c), ok ? B + (int64_t)n * ldb + k : B, ok);
+        }
+        cp_commit();
+    };
+
     V acc[RM][RN];
 #pragma unroll
     for (int i = 0; i < RM; ++i)
 #pragma unroll
         for (int j = 0; j < RN; ++j) acc[i][j] = mk<T>(T(0), T(0));
-    constexpr int RS = 256 / KT;                                    // rows per load pass
-    const int lk = threadIdx.x % KT, lr = threadIdx.x / KT;
-    for (int k0 = kbeg; k0 < kend; k0 += KT) {
-        const int k = k0 + lk;
-        const bool kin = k < kend;
-#pragma unroll
-        for (int r = lr; r < TM; r += RS) {
-            const int m = m0 + r;
-            As[lk][r] = (kin && m < M) ? A[(int64_t)m * lda + k] : mk<T>(T(0), T(0));
-        }
-#pragma unroll
-        for (int r = lr; r < TN; r += RS) {
-            const int n = n0 + r;
-            Bs[lk][r] = (kin && n < N) ? B[(int64_t)n * ldb + k] : mk<T>(T(0), T(0));
+    if (nk > 0) stage_in(0, kbeg);
+    for (int t = 0; t < nk; ++t) {
+        if (t + 1 < nk) {
+            stage_in((t + 1) & 1, kbeg + (t + 1) * KT);
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
         }
         __syncthreads();
+        const V* as = As + (t & 1) * KT * SA + ty * padgroup<RM>();
+        const V* bs = Bs + (t & 1) * KT * SB + tx * padgroup<RN>();
 #pragma unroll 8
         for (int kk = 0; kk < KT; ++kk) {
             V a[RM], b[RN];
 #pragma unroll
-            for (int i = 0; i < RM; ++i) a[i] = As[kk][ty + 16 * i];
+            for (int i = 0; i < RM; ++i) a[i] = as[kk * SA + i];
 #pragma unroll
-            for (int j = 0; j < RN; ++j) b[j] = Bs[kk][tx + 16 * j];
+            for (int j = 0; j < RN; ++j) b[j] = bs[kk * SB + j];
 #pragma unroll
             for (int i = 0; i < RM; ++i)
 #pragma unroll
-                for (int j = 0; j < RN; ++j) {
-                    acc[i][j].x += a[i].x * b[j].x + a[i].y * b[j].y;
-                    acc[i][j].y += a[i].x * b[j].y - a[i].y * b[j].x;
-                }
+                for (int j = 0; j < RN; ++j) mac_cn<T>(acc[i][j], a[i], b[j]);
         }
         __syncthreads();
     }
-    double2* P = part + (int64_t)blockIdx.z * M * N;
+    // stage the tile (column n at Cs[n TM + r]) and write it out along m
+    V* Cs = As;
 #pragma unroll
     for (int i = 0; i < RM; ++i)
 #pragma unroll
-        for (int j = 0; j < RN; ++j) {
-            const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
-            if (m < M && n < N) P[(int64_t)n * M + m] = make_double2(double(acc[i][j].x), double(acc[i][j].y));
-        }
+        for (int j = 0; j < RN; ++j) Cs[(tx * RN + j) * TM + ty * RM + i] = acc[i][j];
+    __syncthreads();
+    V* P = part + (int64_t)blockIdx.z * M * N;
+    for (int e = tid; e < TM * TN; e += nthr) {
+        const int c = e / TM, r = e - c * TM;
+        const int m = m0 + r, n = n0 + c;
+        if (m < M && n < N) P[(int64_t)n * M + m] = Cs[e];
+    }
 }
 
-// One warp per output element sums the chunk partials in a fixed order.
-__global__ void k_chunk_sum(int M, int N, int nchunk, const double2* __restrict__ part, double2* __restrict__ C,
-                            int ldc) {
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w >= M * N) return;
-    double sx = 0.0, sy = 0.0;
-    for (int c = lane; c < nchunk; c += 32) {
-        const double2 v = part[(int64_t)c * M * N + w];
-        sx += v.x;
-        sy += v.y;
+namespace {
+// s + v with its rounding error accumulated in c (Knuth's two-sum)
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float v) {
+    const float t = s + v;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (v - bp);
+    s = t;
+}
+}  // namespace
+
+// C[n ldc + m] = sum over the chunks of part[c][n][m] in a fixed order.  A
+// block covers 32 consecutive outputs (lanes) and its 8 warps take every
+// 8th chunk; FP32 partials are summed with compensation (two-sum), FP64 ones
+// directly, and the 8 group sums are combined in FP64 in warp order.
+constexpr int kSumGroups = 8;
+template <typename P>
+__global__ void __launch_bounds__(32 * kSumGroups) k_chunk_sum(int M, int MN, int nchunk, const P* __restrict__ part,
+                                                               double2* __restrict__ C, int ldc) {
+    __shared__ double2 red[kSumGroups][32];
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int w = blockIdx.x * 32 + lane;
+    double2 r = make_double2(0.0, 0.0);
+    if (w < MN) {
+        if constexpr (sizeof(P) == 8) {
+            float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+#pragma unroll 4
+            for (int c = g; c < nchunk; c += kSumGroups) {
+                const P v = part[(int64_t)c * MN + w];
+                two_sum_acc(sx, cx, v.x);
+                two_sum_acc(sy, cy, v.y);
+            }
+            r = make_double2((double)sx + (double)cx, (double)sy + (double)cy);
+        } else {
+#pragma unroll 4
+            for (int c = g; c < nchunk; c += kSumGroups) {
+                const P v = part[(int64_t)c * MN + w];
+                r.x += v.x;
+                r.y += v.y;
+            }
+        }
     }
+    red[g][lane] = r;
+    __syncthreads();
+    if (g == 0 && w < MN) {
+        double sx = 0.0, sy = 0.0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        sx += __shfl_xor_sync(0xffffffffu, sx, o);
-        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        for (int q = 0; q < kSumGroups; ++q) {
+            sx += red[q][lane].x;
+            sy += red[q][lane].y;
+        }
+        C[(int64_t)(w / M) * ldc + (w % M)] = make_double2(sx, sy);
     }
-    if (lane == 0) C[(int64_t)(w / M) * ldc + (w % M)] = make_double2(sx, sy);
+}
+
+template <typename P>
+static void chunk_sum_t(int M, int N, int nchunk, const P* part, double2* C, int ldc, cudaStream_t st) {
+    const int MN = M * N;
+    roks::count_launch(), k_chunk_sum<P><<<(MN + 31) / 32, 32 * kSumGroups, 0, st>>>(M, MN, nchunk, part, C, ldc);
 }
 
 void chunk_sum(int M, int N, int nchunk, const double2* part, double2* C, int ldc, cudaStream_t st) {
-    const long long thr = (long long)M * N * 32;
-    roks::count_launch(), k_chunk_sum<<<(unsigned)((thr + 255) / 256), 256, 0, st>>>(M, N, nchunk, part, C, ldc);
+    chunk_sum_t<double2>(M, N, nchunk, part, C, ldc, st);
 }
 
 namespace {
 struct CnPlan {
-    int rm, rn, mt, nt, kchunk, nchunk;
+    int rm, rn, ty, tx, mt, nt, kchunk, nchunk;
 };
-CnPlan cn_plan(int M, int N, int K) {
-    CnPlan p;
-    p.rm = M <= 16 ? 1 : (M <= 32 ? 2 : 3);
-    p.rn = N <= 16 ? 1 : (N <= 32 ? 2 : 3);
-    p.mt = (M + 16 * p.rm - 1) / (16 * p.rm);
-    p.nt = (N + 16 * p.rn - 1) / (16 * p.rn);
-    const int tiles = p.mt * p.nt;
-    // about four blocks per SM over the whole grid, chunks a multiple of the k tile
-    const int want = tiles >= 608 ? 1 : (608 + tiles - 1) / tiles;
+
+// Register tile and thread grid with the least padded work (plus the
+// shared-memory loads per multiply-add), then K chunks for about two blocks
+// per SM, each at least two K slices long.
+template <typename T>
+CnPlan cn_plan(int M, int N, int K, int max_chunks) {
+    constexpr int KT = CnTile<T>::KT;
+    CnPlan best{};
+    double best_cost = 1e300;
+    for (int rm = 1; rm <= 4; ++rm)
+        for (int rn = 1; rn <= 4; ++rn) {
+            const int mt = (M + 16 * rm - 1) / (16 * rm), nt = (N + 16 * rn - 1) / (16 * rn);
+            const int ty = (M + mt * rm - 1) / (mt * rm), tx = (N + nt * rn - 1) / (nt * rn);
+            const double covered = (double)mt * ty * rm * nt * tx * rn;
+            double cost = covered * (1.0 + (rm + rn) / (4.0 * rm * rn));
+            if (ty * tx < 64) cost *= 1.5;   // too few threads per block to hide latency
+            if (cost < best_cost) {
+                best_cost = cost;
+                best = CnPlan{rm, rn, ty, tx, mt, nt, 0, 0};
+            }
+        }
+    const int tiles = best.mt * best.nt;
+    int want = (2 * 152 + tiles - 1) / tiles;
+    const int by_len = (K + 2 * KT - 1) / (2 * KT);
+    if (want > by_len) want = by_len;
+    if (max_chunks > 0 && want > max_chunks) want = max_chunks;
+    if (want < 1) want = 1;
     int kc = (K + want - 1) / want;
-    kc = ((kc + CN_KT - 1) / CN_KT) * CN_KT;
-    if (kc < CN_KT) kc = CN_KT;
-    p.kchunk = kc;
-    p.nchunk = K > 0 ? (K + kc - 1) / kc : 1;
-    return p;
+    kc = ((kc + KT - 1) / KT) * KT;
+    if (kc < KT) kc = KT;
+    best.kchunk = kc;
+    best.nchunk = K > 0 ? (K + kc - 1) / kc : 1;
+    return best;
+}
+
+template <typename T, int RM, int RN>
+void launch_cn(const CnPlan& p, int M, int N, int K, const c2<T>* A, int64_t lda, const c2<T>* B, int64_t ldb,
+               c2<T>* part, cudaStream_t st) {
+    constexpr int KT = CnTile<T>::KT;
+    const size_t smem = sizeof(c2<T>) * 2 * KT * (padstride<RM>() + padstride<RN>());
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_gemm_cn<T, RM, RN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    dim3 g(p.mt, p.nt, p.nchunk);
+    roks::count_launch();
+    k_gemm_cn<T, RM, RN><<<g, p.ty * p.tx, smem, st>>>(M, N, K, p.kchunk, p.ty, p.tx, A, lda, B, ldb, part);
+}
+
+template <typename T>
+void run_cn(const CnPlan& p, int M, int N, int K, const c2<T>* A, int64_t lda, const c2<T>* B, int64_t ldb,
+            double2* C, int ldc, double2* work, cudaStream_t st) {
+    c2<T>* part = reinterpret_cast<c2<T>*>(work);
+    if (K <= 0) {
+        cudaMemsetAsync(part, 0, sizeof(c2<T>) * M * N, st);
+    } else {
+#define CN_CASE(RM_, RN_) \
+    if (p.rm == RM_ && p.rn == RN_) launch_cn<T, RM_, RN_>(p, M, N, K, A, lda, B, ldb, part, st);
+        CN_CASE(1, 1) CN_CASE(1, 2) CN_CASE(1, 3) CN_CASE(1, 4)
+        CN_CASE(2, 1) CN_CASE(2, 2) CN_CASE(2, 3) CN_CASE(2, 4)
+        CN_CASE(3, 1) CN_CASE(3, 2) CN_CASE(3, 3) CN_CASE(3, 4)
+        CN_CASE(4, 1) CN_CASE(4, 2) CN_CASE(4, 3) CN_CASE(4, 4)
+#undef CN_CASE
+    }
+    chunk_sum_t<c2<T>>(M, N, K > 0 ? p.nchunk : 1, part, C, ldc, st);
 }
 }  // namespace
 
+// Partial-sum buffer of a contraction, in double2 elements (enough for
+// either precision).
 size_t gemm_cn_work(int M, int N, int K) {
-    const CnPlan p = cn_plan(M, N, K);
-    return (size_t)p.nchunk * M * N;
+    const CnPlan a = cn_plan<float>(M, N, K, 0), b = cn_plan<double>(M, N, K, 0);
+    const int nc = a.nchunk > b.nchunk ? a.nchunk : b.nchunk;
+    return (size_t)nc * M * N;
 }
 
 template <typename T>
 void gemm_cn(int M, int N, int K, const c2<T>* A, int64_t lda, const c2<T>* B, int64_t ldb, double2* C, int ldc,
              double2* work, size_t work_elems, cudaStream_t st, bool allow_tc) {
     if (M <= 0 || N <= 0) return;
+    const int max_chunks = (int)(work_elems / ((size_t)M * N));
     if constexpr (sizeof(T) == 4) {
-        // mixed path: tcgen05 tensor cores (split TF32) when the shape allows
-        const int max_chunks = allow_tc ? (int)(work_elems / ((size_t)M * N)) : 0;
-        if (gemm_cn_tc(M, N, K, reinterpret_cast<const float2*>(A), lda, reinterpret_cast<const float2*>(B), ldb,
-                       C, ldc, work, max_chunks, st))
+        // mixed path: tcgen05 tensor cores (split TF32) when enabled and the shape allows
+        if (allow_tc && gemm_cn_tc(M, N, K, reinterpret_cast<const float2*>(A), lda,
+                                   reinterpret_cast<const float2*>(B), ldb, C, ldc, work, max_chunks, st))
             return;
     }
-    const CnPlan p = cn_plan(M, N, K);
-    dim3 g(p.mt, p.nt, p.nchunk);
-    if (K <= 0) {
-        cudaMemsetAsync(work, 0, sizeof(double2) * M * N, st);
-    } else {
-#define CN_CASE(RM_, RN_)                                                                                   \
-    if (p.rm == RM_ && p.rn == RN_)                                                                       \
-        roks::count_launch(), k_gemm_cn<T, RM_, RN_><<<g, 256, 0, st>>>(M, N, K, p.kchunk, A, lda, B, ldb, work);
-        CN_CASE(1, 1) CN_CASE(1, 2) CN_CASE(1, 3) CN_CASE(2, 1) CN_CASE(2, 2) CN_CASE(2, 3) CN_CASE(3, 1)
-        CN_CASE(3, 2) CN_CASE(3, 3)
-#undef CN_CASE
-    }
-    const long long thr = (long long)M * N * 32;
-    roks::count_launch(), k_chunk_sum<<<(unsigned)((thr + 255) / 256), 256, 0, st>>>(M, N, p.nchunk, work, C, ldc);
+    run_cn<T>(cn_plan<T>(M, N, K, max_chunks), M, N, K, A, lda, B, ldb, C, ldc, work, st);
 }
 
 // Same contraction with the number of K chunks capped at max_chunks, for
-// callers whose partial-sum buffer has a fixed size (max_chunks * M * N).
+// callers whose partial-sum buffer has a fixed size (max_chunks * M * N
+// double2).
 template <typename T>
 void gemm_cn_capped(int M, int N, int K, const c2<T>* A, int64_t lda, const c2<T>* B, int64_t ldb, double2* C,
                     int ldc, double2* work, int max_chunks, cudaStream_t st) {
     if (M <= 0 || N <= 0) return;
-    CnPlan p = cn_plan(M, N, K);
-    if (p.nchunk > max_chunks) {
-        int kc = (K + max_chunks - 1) / max_chunks;
-        kc = ((kc + CN_KT - 1) / CN_KT) * CN_KT;
-        p.kchunk = kc;
-        p.nchunk = (K + kc - 1) / kc;
-    }
-    dim3 g(p.mt, p.nt, p.nchunk);
-    if (K <= 0) {
-        cudaMemsetAsync(work, 0, sizeof(double2) * M * N, st);
-    } else {
-#define CN_CASE(RM_, RN_)                                                                                   \
-    if (p.rm == RM_ && p.rn == RN_)                                                                       \
-        roks::count_launch(), k_gemm_cn<T, RM_, RN_><<<g, 256, 0, st>>>(M, N, K, p.kchunk, A, lda, B, ldb, work);
-        CN_CASE(1, 1) CN_CASE(1, 2) CN_CASE(1, 3) CN_CASE(2, 1) CN_CASE(2, 2) CN_CASE(2, 3) CN_CASE(3, 1)
-        CN_CASE(3, 2) CN_CASE(3, 3)
-#undef CN_CASE
-    }
-    const long long thr = (long long)M * N * 32;
-    roks::count_launch(), k_chunk_sum<<<(unsigned)((thr + 255) / 256), 256, 0, st>>>(M, N, p.nchunk, work, C, ldc);
+    run_cn<T>(cn_plan<T>(M, N, K, max_chunks), M, N, K, A, lda, B, ldb, C, ldc, work, st);
 }
 
 template void gemm_cn_capped<float>(int, int, int, const float2*, int64_t, const float2*, int64_t, double2*, int,
@@ -195,54 +325,72 @@ template void gemm_cn_capped<double>(int, int, int, const double2*, int64_t, con
                                      double2*, int, cudaStream_t);
 
 // ------------------------------------------------------------------ C = alpha A B + beta C
-// A: M x K (tall, column major, element type T), B: K x N FP64 (small).
-// Block: 32 x 8 threads, tile (32 RM) rows x (8 RN) columns; thread (tx, ty)
-// owns rows m0 + tx + 32 i and columns n0 + ty + 8 j.
+// A: M x K (tall, column major), B: K x N (small, element type T).  A block
+// of 32 x TY threads owns (32 RM) rows x (TY RN) columns; thread (tx, ty)
+// keeps rows m0 + tx + 32 i and columns n0 + ty RN + j.  K slices of 16 are
+// double-buffered in shared memory by cp.async.
 constexpr int NN_KT = 16;
 
 template <typename T, int RM, int RN>
-__global__ void __launch_bounds__(256) k_gemm_nn(int M, int N, int K, const c2<T>* __restrict__ A, int64_t lda,
-                                                 const double2* __restrict__ B, int ldb, c2<T>* __restrict__ C,
-                                                 int64_t ldc, T alpha, T beta) {
+__global__ void __launch_bounds__(256) k_gemm_nn(int M, int N, int K, int TY, const c2<T>* __restrict__ A,
+                                                 int64_t lda, const c2<T>* __restrict__ B, int ldb,
+                                                 c2<T>* __restrict__ C, int64_t ldc, T alpha, T beta) {
     using V = c2<T>;
-    constexpr int TM = 32 * RM, TN = 8 * RN;
-    __shared__ V As[NN_KT][TM];
-    __shared__ V Bs[NN_KT][TN];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    constexpr int TM = 32 * RM, SBN = 8 * RN;
+    extern __shared__ __align__(16) unsigned char nn_smem[];
+    V* As = reinterpret_cast<V*>(nn_smem);   // [2][NN_KT][TM]
+    V* Bs = As + 2 * NN_KT * TM;             // [2][NN_KT][SBN]
+    const int nthr = 32 * TY, tid = threadIdx.x;
+    const int tx = tid & 31, ty = tid >> 5;
+    const int TN = TY * RN;
     const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
+    const int nk = (K + NN_KT - 1) / NN_KT;
+
+    auto stage_in = [&](int s, int k0) {
+        V* as = As + s * NN_KT * TM;
+        V* bs = Bs + s * NN_KT * SBN;
+        for (int e = tid; e < NN_KT * TM; e += nthr) {
+            const int kk = e / TM, r = e - kk * TM;
+            const int m = m0 + r, k = k0 + kk;
+            const bool ok = m < M && k < K;
+            cp_elem<T>(as + e, ok ? A + (int64_t)k * lda + m : A, ok);
+        }
+        for (int e = tid; e < NN_KT * TN; e += nthr) {
+            const int c = e / NN_KT, kk = e % NN_KT;
+            const int n = n0 + c, k = k0 + kk;
+            const bool ok = n < N && k < K;
+            cp_elem<T>(bs + kk * SBN + c, ok ? B + (int64_t)n * ldb + k : B, ok);
+        }
+        cp_commit();
+    };
+
     V acc[RM][RN];
 #pragma unroll
     for (int i = 0; i < RM; ++i)
 #pragma unroll
         for (int j = 0; j < RN; ++j) acc[i][j] = mk<T>(T(0), T(0));
-    for (int k0 = 0; k0 < K; k0 += NN_KT) {
-#pragma unroll
-        for (int t = threadIdx.x; t < NN_KT * TM; t += 256) {
-            const int mm = t % TM, kk = t / TM;
-            const int m = m0 + mm, k = k0 + kk;
-            As[kk][mm] = (m < M && k < K) ? A[(int64_t)k * lda + m] : mk<T>(T(0), T(0));
-        }
-        for (int t = threadIdx.x; t < NN_KT * TN; t += 256) {
-            const int kk = t % NN_KT, nn = t / NN_KT;
-            const int k = k0 + kk, n = n0 + nn;
-            const double2 b = (k < K && n < N) ? B[(int64_t)n * ldb + k] : make_double2(0.0, 0.0);
-            Bs[kk][nn] = mk<T>(T(b.x), T(b.y));
+    if (nk > 0) stage_in(0, 0);
+    for (int t = 0; t < nk; ++t) {
+        if (t + 1 < nk) {
+            stage_in((t + 1) & 1, (t + 1) * NN_KT);
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
         }
         __syncthreads();
+        const V* as = As + (t & 1) * NN_KT * TM + tx;
+        const V* bs = Bs + (t & 1) * NN_KT * SBN + ty * RN;
 #pragma unroll 4
         for (int kk = 0; kk < NN_KT; ++kk) {
             V a[RM], b[RN];
 #pragma unroll
-            for (int i = 0; i < RM; ++i) a[i] = As[kk][tx + 32 * i];
+            for (int i = 0; i < RM; ++i) a[i] = as[kk * TM + 32 * i];
 #pragma unroll
-            for (int j = 0; j < RN; ++j) b[j] = Bs[kk][ty + 8 * j];
+            for (int j = 0; j < RN; ++j) b[j] = bs[kk * SBN + j];
 #pragma unroll
             for (int i = 0; i < RM; ++i)
 #pragma unroll
-                for (int j = 0; j < RN; ++j) {
-                    acc[i][j].x += a[i].x * b[j].x - a[i].y * b[j].y;
-                    acc[i][j].y += a[i].x * b[j].y + a[i].y * b[j].x;
-                }
+                for (int j = 0; j < RN; ++j) mac_nn<T>(acc[i][j], a[i], b[j]);
         }
         __syncthreads();
     }
@@ -252,7 +400,7 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int M, int N, int K, const c2<T
         if (m >= M) continue;
 #pragma unroll
         for (int j = 0; j < RN; ++j) {
-            const int n = n0 + ty + 8 * j;
+            const int n = n0 + ty * RN + j;
             if (n < N) {
                 V* dst = C + (int64_t)n * ldc + m;
                 V r = cscale(acc[i][j], alpha);
@@ -263,16 +411,58 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int M, int N, int K, const c2<T
     }
 }
 
+// FP64 small matrix (K x N, ldb) -> contiguous FP32 copy (K x N, ld K)
+__global__ void k_b_to_f32(int K, int N, const double2* __restrict__ B, int ldb, float2* __restrict__ Bf) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K * N) return;
+    const int n = i / K, k = i - n * K;
+    const double2 v = B[(int64_t)n * ldb + k];
+    Bf[i] = make_float2((float)v.x, (float)v.y);
+}
+
+namespace {
+template <typename T, int RN>
+void launch_nn(int M, int N, int K, int ty, int nt, const c2<T>* A, int64_t lda, const c2<T>* B, int ldb, c2<T>* C,
+               int64_t ldc, T alpha, T beta, cudaStream_t st) {
+    constexpr int RM = 4;
+    const size_t smem = sizeof(c2<T>) * 2 * NN_KT * (32 * RM + 8 * RN);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_gemm_nn<T, RM, RN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    dim3 g((M + 32 * RM - 1) / (32 * RM), nt);
+    roks::count_launch();
+    k_gemm_nn<T, RM, RN><<<g, 32 * ty, smem, st>>>(M, N, K, ty, A, lda, B, ldb, C, ldc, alpha, beta);
+}
+}  // namespace
+
 template <typename T>
 void gemm_nn(int M, int N, int K, const c2<T>* A, int64_t lda, const double2* B, int ldb, c2<T>* C, int64_t ldc,
-             double alpha, double beta, cudaStream_t st) {
+             double alpha, double beta, void* bwork, cudaStream_t st) {
     if (M <= 0 || N <= 0) return;
-    const int rn = N <= 8 ? 1 : (N <= 16 ? 2 : (N <= 32 ? 4 : 6));
-    constexpr int RM = 4;
-    dim3 g((M + 32 * RM - 1) / (32 * RM), (N + 8 * rn - 1) / (8 * rn));
-#define NN_CASE(RN_)                                                                                            \
-    if (rn == RN_) roks::count_launch(), k_gemm_nn<T, RM, RN_><<<g, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, T(alpha), T(beta));
-    NN_CASE(1) NN_CASE(2) NN_CASE(4) NN_CASE(6)
+    // column tiles of at most 64: RN = ceil(tile / 8) columns per thread, TY <= 8 warps
+    const int nt = (N + 63) / 64;
+    const int tn = (N + nt - 1) / nt;
+    const int rn = (tn + 7) / 8;
+    const int ty = (tn + rn - 1) / rn;
+    const c2<T>* Bt;
+    int ldbt;
+    if constexpr (sizeof(T) == 4) {
+        float2* Bf = static_cast<float2*>(bwork);
+        if (K > 0) {
+            roks::count_launch();
+            k_b_to_f32<<<(K * N + 255) / 256, 256, 0, st>>>(K, N, B, ldb, Bf);
+        }
+        Bt = Bf;
+        ldbt = K;
+    } else {
+        Bt = B;
+        ldbt = ldb;
+    }
+#define NN_CASE(RN_) \
+    if (rn == RN_) launch_nn<T, RN_>(M, N, K, ty, nt, A, lda, Bt, ldbt, C, ldc, T(alpha), T(beta), st);
+    NN_CASE(1) NN_CASE(2) NN_CASE(3) NN_CASE(4) NN_CASE(5) NN_CASE(6) NN_CASE(7) NN_CASE(8)
 #undef NN_CASE
 }
 
@@ -281,9 +471,9 @@ template void gemm_cn<float>(int, int, int, const float2*, int64_t, const float2
 template void gemm_cn<double>(int, int, int, const double2*, int64_t, const double2*, int64_t, double2*, int,
                               double2*, size_t, cudaStream_t, bool);
 template void gemm_nn<float>(int, int, int, const float2*, int64_t, const double2*, int, float2*, int64_t, double,
-                             double, cudaStream_t);
+                             double, void*, cudaStream_t);
 template void gemm_nn<double>(int, int, int, const double2*, int64_t, const double2*, int, double2*, int64_t,
-                              double, double, cudaStream_t);
+                              double, double, void*, cudaStream_t);
 
 // ------------------------------------------------------------------ small FP64 matrices
 // One warp per output element; the lanes split K and reduce with shuffles.

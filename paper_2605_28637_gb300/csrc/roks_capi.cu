@@ -298,7 +298,7 @@ struct Impl {
                      ctx->d_wband, ctx->d_DB, ctx->d_QB, st);
             PROF("proj_PX");
             gemm_nn<T>(ctx->npw, ctx->nb, ctx->nproj, ccv(ctx->d_P), ctx->ld_min, ctx->d_DB, ctx->nproj, cv(F), ldf,
-                       1.0, 1.0, st);
+                       1.0, 1.0, ctx->d_gemm_work, st);
         }
         if (S) {
             CK(cudaMemcpy2DAsync(S, lds * sizeof(V), psi, ld * sizeof(V), ctx->npw * sizeof(V), ctx->nb,
@@ -306,7 +306,7 @@ struct Impl {
             if (ctx->nproj > 0) {
                 PROF("proj_PX");
                 gemm_nn<T>(ctx->npw, ctx->nb, ctx->nproj, ccv(ctx->d_P), ctx->ld_min, ctx->d_QB, ctx->nproj, cv(S),
-                           lds, 1.0, 1.0, st);
+                           lds, 1.0, 1.0, ctx->d_gemm_work, st);
             }
         }
         CK(cudaGetLastError());
@@ -347,7 +347,7 @@ struct Impl {
         }
         {
             PROF("orth_apply");
-            gemm_nn<T>(ctx->npw, nb, nb, ccv(in), ldi, ctx->d_LinvH, nb, cv(out), ldo, 1.0, 0.0, st);
+            gemm_nn<T>(ctx->npw, nb, nb, ccv(in), ldi, ctx->d_LinvH, nb, cv(out), ldo, 1.0, 0.0, ctx->d_gemm_work, st);
         }
         if (Bout && ctx->nproj > 0) {
             PROF("orth_small");
@@ -382,7 +382,7 @@ struct Impl {
                    ctx->gemm_work_elems, st);
         if (out != x)
             cudaMemcpyAsync(out, x, sizeof(V) * l * nb, cudaMemcpyDeviceToDevice, st);
-        gemm_nn<T>(ctx->npw, nb, nb, ccv(psi), ld, ctx->d_Msm, nb, cv(out), l, -1.0, 1.0, st);
+        gemm_nn<T>(ctx->npw, nb, nb, ccv(psi), ld, ctx->d_Msm, nb, cv(out), l, -1.0, 1.0, ctx->d_gemm_work, st);
     }
 
     // dst field = sum_n Re <x_n|y_n>
@@ -411,7 +411,7 @@ struct Impl {
                     expm_scaled(nb, ctx->d_Atot, scd + step_field, ctx->d_U, ctx->d_e1, ctx->d_e2, ctx->d_e3,
                                 ctx->d_expm_info, st);
             }
-            gemm_nn<T>(ctx->npw, nb, nb, ccv(ctx->W_Y), l, ctx->d_U, nb, cv(ctx->W_Y2), l, 1.0, 0.0, st);
+            gemm_nn<T>(ctx->npw, nb, nb, ccv(ctx->W_Y), l, ctx->d_U, nb, cv(ctx->W_Y2), l, 1.0, 0.0, ctx->d_gemm_work, st);
         }
         roks_status r = orth(ctx, ctx->W_Y2, l, out, ldo, ctx->d_B);
         if (r != ROKS_OK) return r;
@@ -450,9 +450,9 @@ struct Impl {
         {
         PROF("gradient_precond");
         CK(cudaMemcpyAsync(ctx->W_G, ctx->W_F, sizeof(V) * l * nb, cudaMemcpyDeviceToDevice, st));
-        gemm_nn<T>(npw, nb, nb, ccv(ctx->W_S), l, ctx->d_Gam, nb, cv(ctx->W_G), l, -1.0, 1.0, st);
+        gemm_nn<T>(npw, nb, nb, ccv(ctx->W_S), l, ctx->d_Gam, nb, cv(ctx->W_G), l, -1.0, 1.0, ctx->d_gemm_work, st);
         CK(cudaMemcpyAsync(ctx->W_gI, ctx->W_F, sizeof(V) * l * nb, cudaMemcpyDeviceToDevice, st));
-        gemm_nn<T>(npw, nb, nb, ccv(ctx->W_S), l, ctx->d_Th, nb, cv(ctx->W_gI), l, -1.0, 1.0, st);
+        gemm_nn<T>(npw, nb, nb, ccv(ctx->W_S), l, ctx->d_Th, nb, cv(ctx->W_gI), l, -1.0, 1.0, ctx->d_gemm_work, st);
         column_sums<T>(3, npw, nb, ccv(ctx->W_G), l, nullptr, 0, ctx->d_g2, ctx->d_colpart, ctx->d_colout, st);
         sum_to(ctx->d_colout, nb, reinterpret_cast<double*>(ctx->d_sc) + SC_FIELD(gnorm2), 1.0, st);
         // p_I = K g_I - Psi (S Psi)^H K g_I
@@ -937,10 +937,10 @@ roks_status roks_apply_h(roks_ctx* ctx, const void* psi, int64_t ld, void* fpsi,
     CK(cudaMemcpy2DAsync(grad, ld * es, fpsi, ld * es, ctx->npw * es, nb, cudaMemcpyDeviceToDevice, ctx->st));
     if (ctx->prec == ROKS_FP64)
         gemm_nn<double>(ctx->npw, nb, nb, static_cast<const double2*>(S), lds, ctx->d_Gam, nb,
-                        static_cast<double2*>(grad), ld, -1.0, 1.0, ctx->st);
+                        static_cast<double2*>(grad), ld, -1.0, 1.0, ctx->d_gemm_work, ctx->st);
     else
         gemm_nn<float>(ctx->npw, nb, nb, static_cast<const float2*>(S), lds, ctx->d_Gam, nb,
-                       static_cast<float2*>(grad), ld, -1.0, 1.0, ctx->st);
+                       static_cast<float2*>(grad), ld, -1.0, 1.0, ctx->d_gemm_work, ctx->st);
     CK(cudaGetLastError());
     return ROKS_OK;
 }

@@ -83,8 +83,9 @@ template <typename T>
 void grid_fft3_batched(int N, const c2<T>* tw, c2<T>* data, int batch, int64_t bstride, int dir, cudaStream_t st);
 
 // ------------------------------------------------------------ dense complex contractions
-// Cpart[chunk] (double2, M x N column major) = sum over the k of the chunk of
-// conj(A[k, m]) B[k, n]; then C = sum_chunks Cpart (double2, ldc).  FP32
+// Cpart[chunk] (element type T, M x N column major) = sum over the k of the
+// chunk of conj(A[k, m]) B[k, n]; then C = sum_chunks Cpart (double2, ldc)
+// in a fixed order.  work holds work_elems double2.  FP32
 // inputs go to the tensor cores when allow_tc; the tensor-core accumulation
 // rounds towards zero, so results that must not carry that bias (the
 // overlap matrix of the orthonormalisation) pass allow_tc = false.
@@ -105,9 +106,11 @@ template <typename T>
 void gemm_cn_capped(int M, int N, int K, const c2<T>* A, int64_t lda, const c2<T>* B, int64_t ldb,
                     double2* C, int ldc, double2* work, int max_chunks, cudaStream_t st);
 // C[m, n] = alpha sum_k A[m, k] B[k, n] + beta C[m, n]; B is FP64 (small).
+// For T = float, bwork receives an FP32 copy of B (K x N float2); it may be
+// the partial-sum buffer of gemm_cn (not in use across calls).
 template <typename T>
 void gemm_nn(int M, int N, int K, const c2<T>* A, int64_t lda, const double2* B, int ldb,
-             c2<T>* C, int64_t ldc, double alpha, double beta, cudaStream_t st);
+             c2<T>* C, int64_t ldc, double alpha, double beta, void* bwork, cudaStream_t st);
 
 // ------------------------------------------------------------ small FP64 matrices (n x n, column major)
 void small_gemm(int M, int N, int K, const double2* A, int lda, bool ca, const double2* B, int ldb,
