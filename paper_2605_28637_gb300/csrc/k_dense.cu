@@ -12,6 +12,8 @@ namespace roks {
 
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches_now() { return g_launches.load(std::memory_order_relaxed); }
 long long launches_take() { return g_launches.exchange(0); }
 
 // ------------------------------------------------------------------ complex multiply-accumulate

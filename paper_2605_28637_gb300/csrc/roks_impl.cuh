@@ -39,6 +39,8 @@ __host__ __device__ __forceinline__ int signed_freq(int e, int n) { return e <= 
 // Host-side count of the kernel launches issued by the library (every launch
 // site calls count_launch(); read and reset through the profiling API).
 void count_launch();
+void count_launches(long long n);   // n launches at once (a graph replay)
+long long launches_now();
 long long launches_take();
 
 // ------------------------------------------------------------ band FFTs
