@@ -127,7 +127,7 @@ typedef struct {
     double E_new;        /* energy after the step                           */
     double step;         /* Delta of Eqs. 5 and 24                          */
     double grad_norm;    /* Frobenius norm of the constrained gradient g    */
-    double coupling_re;  /* <a|F^a - F^b|b> at the start (Eq. 16)           */
+    double coupling_re;  /* <a|F^a - F^b|b> at the start (Eq. 15)           */
     double coupling_im;
     double beta;         /* Fletcher-Reeves ratio used (0 after a restart)  */
     double dE0;          /* directional derivative of E along the step      */
@@ -161,7 +161,7 @@ ROKS_API roks_status roks_init_orbitals(roks_ctx* ctx, const double* u_host,
                                void* psi, int64_t ld);
 
 /* Class densities rho_k(r) = sum_{n in k} |psi_n(r)|^2, k = closed, a, b
- * (the inputs of the spin densities of Eq. 9), plus the kinetic and
+ * (the inputs of the spin densities of Eq. 8), plus the kinetic and
  * non-local energy terms of psi.  rho_out (optional, device, 3 x N^3 double,
  * grid index (x N + y) N + z) receives a copy. */
 ROKS_API roks_status roks_density(roks_ctx* ctx, const void* psi, int64_t ld,
@@ -169,13 +169,13 @@ ROKS_API roks_status roks_density(roks_ctx* ctx, const void* psi, int64_t ld,
 
 /* From the last roks_density: channel densities rho^{sigma L}, one Hartree
  * solve (rho_M = rho_T), Slater exchange per channel and the class
- * potentials V^k = w_k (V_loc + V_H) + sum_{sigma L} c_L f_k v_x (Eqs. 9, 14).
+ * potentials V^k = w_k (V_loc + V_H) + sum_{sigma L} c_L f_k v_x (Eqs. 8, 13).
  * Fills *e (host; may be NULL).  vclass_out (optional, device, 3 x N^3 of
  * the orbital element type) receives V^closed, V^a, V^b.  Synchronises. */
 ROKS_API roks_status roks_potential(roks_ctx* ctx, roks_energies* e, void* vclass_out);
 
 /* Shell operators applied to each band with the last roks_potential:
- * fpsi_n = F^{k(n)}|n> (Eq. 14: kinetic + local + non-local, and exact
+ * fpsi_n = F^{k(n)}|n> (Eq. 13: kinetic + local + non-local, and exact
  * exchange if alpha != 0).  spsi (optional) = S|n>.  grad (optional)
  * = g_n = F^n|n> - sum_m S|m> gamma_nm with gamma of Eq. 11.  All outputs
  * are device arrays with the same ld as psi. */
@@ -188,8 +188,8 @@ ROKS_API roks_status roks_apply_h(roks_ctx* ctx, const void* psi, int64_t ld,
 ROKS_API roks_status roks_orthonormalize(roks_ctx* ctx, void* psi, int64_t ld);
 
 /* One PCG iteration on psi (in place, S-orthonormal on entry and exit):
- * gradient and gamma (Eqs. 8, 11), split (Eq. 12), TPA preconditioning
- * (Eqs. 17, 18), Fletcher-Reeves direction (Eq. 7), R-matrix rotation
+ * gradient and gamma (Eqs. 7, 11), split (Eq. 12), TPA preconditioning
+ * (Eqs. 17, 18), Fletcher-Reeves direction (Eq. 6), R-matrix rotation
  * generator (Eqs. 20-23), parabolic line search on E (Eq. 5) and the update
  * orth((Psi + Delta s) exp(Delta (A^i + beta A^{i-1}))) (Eq. 24).  The
  * direction history lives in the context; the first call (or the first after

@@ -11,13 +11,13 @@ What it computes, in the paper's order and notation:
   minimised over one set of spatial orbitals shared by the mixed-spin (M)
   and triplet (T) configurations, c_M = 2, c_T = -1                (Sec. II A)
 * overlap S = 1 + sum |beta> q <beta|                             (Eq. 3)
-* configuration/spin Hamiltonians H^{sigma L}                      (Eq. 9)
-* shell operators F^n = sum_{sigma L} c_L f_n^{sigma L} H^{sigma L} (Eq. 14)
+* configuration/spin Hamiltonians H^{sigma L}                      (Eq. 8)
+* shell operators F^n = sum_{sigma L} c_L f_n^{sigma L} H^{sigma L} (Eq. 13)
 * Lagrange multipliers gamma                                       (Eq. 11, SI S1)
-* gradient, split into out-of-subspace (I) and in-subspace (II)    (Eqs. 8, 12)
+* gradient, split into out-of-subspace (I) and in-subspace (II)    (Eqs. 7, 12)
 * preconditioned gradient with the TPA kinetic preconditioner      (Eqs. 17, 18)
 * ROKS R matrix and the Jacobi-like in-subspace rotation           (Eqs. 20-23)
-* Fletcher-Reeves CG with the two-step update                      (Eqs. 5, 7, 24)
+* Fletcher-Reeves CG with the two-step update                      (Eqs. 5, 6, 24)
 
 The model behind the Hamiltonian (not given by the paper, whose PAW data
 sets are not available): Gaussian local wells, Gaussian s/p projectors with
@@ -56,7 +56,7 @@ TWO_PI = 2.0 * np.pi
 # Occupation table f_k^{sigma L} of the three orbital classes (rows: closed,
 # open a, open b) in the four channels (up M, down M, up T, down T).  The
 # mixed configuration Phi_1 has a-up, b-down; the triplet Phi_3 has a-up,
-# b-up (Fig. 1A; Eq. 8 uses f in {0, 1}).
+# b-up (Fig. 1A; Eq. 7 uses f in {0, 1}).
 F_TABLE = np.array([[1.0, 1.0, 1.0, 1.0],
                     [1.0, 0.0, 1.0, 0.0],
                     [0.0, 1.0, 1.0, 0.0]])
@@ -109,7 +109,7 @@ class System:
 
     # ----------------------------------------------------------- a1: occupations
     def _occupations(self):
-        """Weights that follow from f_n^{sigma L} and c_L (Eqs. 8, 14)."""
+        """Weights that follow from f_n^{sigma L} and c_L (Eqs. 7, 13)."""
         self.cL = config_coefficients(self.mode)
         c_ch = np.repeat(self.cL, 2)                 # c_L per channel
         self.C = F_TABLE * c_ch[None, :]              # c_L f_k^{sigma L}
@@ -242,7 +242,7 @@ class System:
     # ----------------------------------------------------------- a4-a6: potentials
     def potentials(self, rho_k: np.ndarray) -> Potentials:
         """Channel densities rho^{sigma L} = sum_k f_k^{sigma L} rho_k; one
-        Hartree solve (rho_M = rho_T, Eq. 9); Slater exchange per channel;
+        Hartree solve (rho_M = rho_T, Eq. 8); Slater exchange per channel;
         class potentials V^k = w_k (V_loc + V_H) + sum c_L f_k v_x^{sigma L}."""
         rho_ch = F_TABLE.T @ rho_k                    # (4, N^3)
         rho = rho_ch[0] + rho_ch[1]
@@ -315,7 +315,7 @@ class System:
         """F^{k}|n> for each column (k = class of band n unless `classes` is
         given) and S|n>.  F^k = w_k (T + V_loc + V_nl + V_H) + sum c_L f v_x
         (+ exact exchange built from the occupied orbitals `occ`, default the
-        columns themselves), Eq. 14 with Eq. 9."""
+        columns themselves), Eq. 13 with Eq. 8."""
         if classes is None:
             classes = self.cls
         if occ is None:
@@ -392,7 +392,7 @@ class System:
 # =========================================================== a12-a16: PCG pieces
 def gradient_parts(Psi, FPsi, SPsi):
     """theta_mn = <m|F^n|n>; gamma (Eq. 11) as Gam_mn = gamma_nm =
-    (theta_mn + theta_nm^*)/2; full gradient g = F Psi - S Psi Gam (Eq. 8);
+    (theta_mn + theta_nm^*)/2; full gradient g = F Psi - S Psi Gam (Eq. 7);
     out-of-subspace part g_I = F Psi - S Psi theta and in-subspace matrix
     Gin_mn = theta_mn - theta_nm^* = 2 <m|g_n> (Eq. 12)."""
     Theta = Psi.conj().T @ FPsi
@@ -404,13 +404,13 @@ def gradient_parts(Psi, FPsi, SPsi):
 
 
 def tpa_factor(x: np.ndarray) -> np.ndarray:
-    """(27 + 18x + 12x^2 + 8x^3) / (27 + 18x + 12x^2 + 8x^3 + 16x^4) (Eq. 18)."""
+    """(27 + 18x + 12x^2 + 8x^3) / (27 + 18x + 12x^2 + 8x^3 + 16x^4) (Eq. 17)."""
     num = 27.0 + 18.0 * x + 12.0 * x * x + 8.0 * x ** 3
     return num / (num + 16.0 * x ** 4)
 
 
 def precondition(sys_: System, Psi, SPsi, gI):
-    """p_I = K g_I - sum_m |m><m|S K|g_I> (Eq. 17), K = -(2/X) tpa(x),
+    """p_I = K g_I - sum_m |m><m|S K|g_I> (Eq. 16), K = -(2/X) tpa(x),
     x = E_kin(G)/X with E_kin(G) = |G|^2 in Rydberg, X_n = 1.5 E_kin(g_nI) (R1)."""
     g2ry = sys_.g2
     w = np.abs(gI) ** 2
@@ -491,7 +491,7 @@ class StepInfo:
 
 
 class PCG:
-    """All-band preconditioned Fletcher-Reeves CG (Eqs. 5-7) with the ROKS
+    """All-band preconditioned Fletcher-Reeves CG (Eqs. 5, 6) with the ROKS
     two-step update: out-of-subspace step, then U = exp(step (A^i + beta A^{i-1}))
     (Eq. 24)."""
 

@@ -1,7 +1,7 @@
 // k_pcg.cu -- band-space part of one PCG iteration, kept on the device so
 // that a step needs no host round trip: gamma and the gradient split
 // (Eqs. 11, 12), the ROKS R matrix (Eq. 20), the rotation generator
-// (Eqs. 22-23), the Fletcher-Reeves ratio (Eq. 7) with restarts, the
+// (Eqs. 22-23), the Fletcher-Reeves ratio (Eq. 6) with restarts, the
 // parabolic line search (Eq. 5) and the energy combination (Eq. 1).
 #include <cstddef>
 

@@ -666,7 +666,7 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     ctx->ncol = (int)col_kmax.size();
     ctx->np = 2 * n + 1;
     if (ctx->nb > ctx->npw) return bail(ROKS_EINVAL, "more bands than plane waves");
-    // -------- occupations (Eqs. 8, 14): f table and c_L
+    // -------- occupations (Eqs. 7, 13): f table and c_L
     const double ftab[3][4] = {{1, 1, 1, 1}, {1, 0, 1, 0}, {0, 1, 1, 0}};
     ctx->cM = occ->mode == 0 ? 1.0 : (occ->mode == 1 ? 2.0 : 0.0);
     ctx->cT = occ->mode == 0 ? 0.0 : (occ->mode == 1 ? -1.0 : 1.0);
@@ -681,7 +681,7 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
         ctx->cf.w[k] = w;
     }
     ctx->cf.xscale = 1.0 - opt->alpha;
-    // exchange pair weights w(k, k') = sum_ch c_L f_k f_k' (Eq. 14 with the
+    // exchange pair weights w(k, k') = sum_ch c_L f_k f_k' (Eq. 13 with the
     // exact-exchange energy of each configuration)
     {
         const double sq = std::sqrt(ctx->omega);

@@ -8,7 +8,7 @@ namespace roks {
 
 constexpr int kMaxBlk = 16;   // projectors per atom
 
-// Occupation-derived coefficients of the class potentials (Eq. 14):
+// Occupation-derived coefficients of the class potentials (Eq. 13):
 // f[k][ch] = f_k^{sigma L}, C[k][ch] = c_L f_k^{sigma L}, w[k] = sum_ch C[k][ch],
 // channels (up M, down M, up T, down T); xscale = 1 - alpha.
 struct PotCoef {

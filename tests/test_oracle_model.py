@@ -1,5 +1,5 @@
 """Pins of the oracle's model terms: basis, kinetic, Hartree, exchange,
-Coulomb kernel, Hermiticity, energy combination and the gradient (Eq. 8)."""
+Coulomb kernel, Hermiticity, energy combination and the gradient (Eq. 7)."""
 import json
 import os
 
@@ -165,7 +165,7 @@ def test_hermiticity(alpha):
 
 @pytest.mark.parametrize("mode,alpha", [(1, 0.0), (1, 1 / 3), (2, 0.0), (0, 0.0), (0, 1 / 3)])
 def test_gradient_finite_difference(mode, alpha):
-    """dE/dh along a random direction = 2 Re sum_n <delta_n|F^n psi_n> (Eq. 8)."""
+    """dE/dh along a random direction = 2 Re sum_n <delta_n|F^n psi_n> (Eq. 7)."""
     s = R.System(tiny(mode=mode, alpha=alpha, n_closed=4 if mode else 5))
     Psi = s.initial_orbitals(syn.orbital_uniforms(s.cfg, s.npw))
     pot = s.potentials(s.class_densities(Psi))

@@ -1,5 +1,5 @@
-"""Pins of the oracle's PCG pieces: gamma/gradient split (Eqs. 8, 11, 12),
-TPA (Eq. 18), the R-matrix rotation (Eqs. 20-23), orthonormalisation, the
+"""Pins of the oracle's PCG pieces: gamma/gradient split (Eqs. 7, 11, 12),
+TPA (Eqs. 17, 18), the R-matrix rotation (Eqs. 20-23), orthonormalisation, the
 line search and the converged solutions (stationarity, closed-shell limit)."""
 import json
 import os
@@ -50,7 +50,7 @@ def test_preconditioned_gradient_is_s_orthogonal_and_descent():
     F, S = s.apply(Psi, pot)
     Th, G, gI, Gin = R.gradient_parts(Psi, F, S)
     pI, X = R.precondition(s, Psi, S, gI)
-    assert np.abs(S.conj().T @ pI).max() < 1e-11     # Psi^H S p_I = 0 (Eq. 17)
+    assert np.abs(S.conj().T @ pI).max() < 1e-11     # Psi^H S p_I = 0 (Eq. 16)
     assert np.real(np.vdot(pI, gI)) < 0
 
 
@@ -152,7 +152,7 @@ def test_closed_shell_reduction():
 @pytest.mark.slow
 def test_singlet_stationarity():
     """Converged singlet: |g| small and the inter-shell conditions
-    <m|F^n - F^m|n> = 0 (Eq. 16, SI S1) hold."""
+    <m|F^n - F^m|n> = 0 (Eq. 15, SI S1) hold."""
     s, Psi = start(tiny())
     Psi, hist = R.run(s, Psi, max_iter=400, e_tol=1e-9)
     pot = s.potentials(s.class_densities(Psi))
