@@ -41,6 +41,18 @@ CUDA path, which implements them independently):
       before the step; orbitals are S-orthonormalised by Cholesky in the
       order closed, a, b after each step.
   R7  convergence: |E_i+1 - E_i| < e_tol on two consecutive iterations.
+
+What pins each part (tests/test_oracle_*.py; none compares the oracle with
+itself): the transforms against the DFT sum and brute force; the basis
+against brute-force counts; kinetic, Hartree, Slater exchange, truncated
+Coulomb kernel, wells and projectors against closed forms; H against
+Hermiticity and the gradient against finite differences of E; E_S = 2 E_M -
+E_T term by term; gamma, the gradient split, p_I and the R-matrix rotation
+against their defining identities; the line-search slope against finite
+differences along the path taken; the converged result against the dense
+generalised eigenproblem (closed shell) and the stationarity conditions
+(singlet).  Parity unpinned: the exact sequence of step lengths (R5) and of
+Fletcher-Reeves ratios (R4) beyond monotone descent and the fixed point.
 """
 from __future__ import annotations
 

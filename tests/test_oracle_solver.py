@@ -164,3 +164,32 @@ def test_singlet_stationarity():
     assert abs(Gin[a, b]) < 1e-4
     E = s.energies(Psi)
     assert E["total"] == pytest.approx(2 * E["M"] - E["T"], abs=1e-12)
+
+
+def test_line_search_slope_matches_finite_difference():
+    """E'(0) used by the line search (R5) is the derivative of E along the
+    path actually taken, orth((Psi + h s) exp(h A_tot)) (Eqs. 5, 24), with
+    and without the Fletcher-Reeves history: central differences of the
+    energy agree, so a wrong sign, a dropped in-subspace term or a missing
+    factor 2 in 2 Re<s|g> would show."""
+    s, Psi = start(tiny())
+    pcg = R.PCG(s)
+    seen = []
+    trial = pcg.trial
+
+    def spy(P, d, A, h):
+        if len(seen) == 0 or seen[-1][0] is not P:
+            seen.append((P, d, A))
+        return trial(P, d, A, h)
+
+    pcg.trial = spy
+    checked = 0
+    for it in range(3):
+        P0 = Psi
+        Psi, info = pcg.step(Psi)
+        P, d, A = [x for x in seen if x[0] is P0][0]
+        h = 1e-4
+        fd = (s.energy(trial(P, d, A, h)) - s.energy(trial(P, d, A, -h))) / (2 * h)
+        assert abs(fd - info.dE0) < 1e-6 * max(1.0, abs(info.dE0)), (it, fd, info.dE0)
+        checked += info.beta != 0.0
+    assert checked >= 1          # at least one step used the Fletcher-Reeves history
