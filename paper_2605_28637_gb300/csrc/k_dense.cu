@@ -5,6 +5,8 @@
 //
 // The contractions here are SIMT tiled kernels with register blocking.
 #include <atomic>
+#include <mutex>
+#include <vector>
 
 #include "roks_impl.cuh"
 
@@ -163,10 +165,11 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& c, float v) {
 }  // namespace
 
 // C[n ldc + m] = sum over the chunks of part[c][n][m] in a fixed order.  A
-// block covers 32 consecutive outputs (lanes) and its 8 warps take every
-// 8th chunk; FP32 partials are summed with compensation (two-sum), FP64 ones
-// directly, and the 8 group sums are combined in FP64 in warp order.
-constexpr int kSumGroups = 8;
+// block covers 32 consecutive outputs (lanes) and its 32 warps take every
+// 32nd chunk (many loads in flight: the reduction is latency-bound); FP32
+// partials are summed with compensation (two-sum), FP64 ones directly, and
+// the 32 group sums are combined in FP64 in warp order.
+constexpr int kSumGroups = 32;
 template <typename P>
 __global__ void __launch_bounds__(32 * kSumGroups) k_chunk_sum(int M, int MN, int nchunk, const P* __restrict__ part,
                                                                double2* __restrict__ C, int ldc) {
@@ -177,7 +180,7 @@ __global__ void __launch_bounds__(32 * kSumGroups) k_chunk_sum(int M, int MN, in
     if (w < MN) {
         if constexpr (sizeof(P) == 8) {
             float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
-#pragma unroll 4
+#pragma unroll 8
             for (int c = g; c < nchunk; c += kSumGroups) {
                 const P v = part[(int64_t)c * MN + w];
                 two_sum_acc(sx, cx, v.x);
@@ -221,6 +224,57 @@ struct CnPlan {
     int rm, rn, ty, tx, mt, nt, kchunk, nchunk;
 };
 
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+            n = 152;
+    }
+    return n;
+}
+
+template <typename T, int RM, int RN>
+size_t cn_smem() {
+    return sizeof(c2<T>) * 2 * CnTile<T>::KT * (padstride<RM>() + padstride<RN>());
+}
+
+// Blocks of the chosen contraction kernel resident on one SM (occupancy API),
+// so that the split-K grid fills whole waves of the GPU.
+template <typename T>
+int cn_resident_blocks(int rm, int rn, int threads) {
+    // cached per (tile, block size): the first call of each shape queries
+    struct Ent {
+        int rm, rn, threads, nb;
+    };
+    static std::vector<Ent> cache;
+    static std::mutex mu;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        for (const Ent& c : cache)
+            if (c.rm == rm && c.rn == rn && c.threads == threads) return c.nb;
+    }
+    int nb = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+#define CN_OCC(RM_, RN_)                                                                                        \
+    if (rm == RM_ && rn == RN_) {                                                                             \
+        const size_t sm = cn_smem<T, RM_, RN_>();                                                             \
+        cudaFuncSetAttribute(k_gemm_cn<T, RM_, RN_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);    \
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gemm_cn<T, RM_, RN_>, threads, sm);          \
+    }
+    CN_OCC(1, 1) CN_OCC(1, 2) CN_OCC(1, 3) CN_OCC(1, 4) CN_OCC(2, 1) CN_OCC(2, 2) CN_OCC(2, 3) CN_OCC(2, 4)
+    CN_OCC(3, 1) CN_OCC(3, 2) CN_OCC(3, 3) CN_OCC(3, 4) CN_OCC(4, 1) CN_OCC(4, 2) CN_OCC(4, 3) CN_OCC(4, 4)
+#undef CN_OCC
+    if (e != cudaSuccess || nb < 1) {
+        cudaGetLastError();
+        nb = 2;
+    }
+    std::lock_guard<std::mutex> g(mu);
+    cache.push_back(Ent{rm, rn, threads, nb});
+    return nb;
+}
+
 // Register tile and thread grid with the least padded work (plus the
 // shared-memory loads per multiply-add), then K chunks for about two blocks
 // per SM, each at least two K slices long.
@@ -242,7 +296,7 @@ CnPlan cn_plan(int M, int N, int K, int max_chunks) {
             }
         }
     const int tiles = best.mt * best.nt;
-    int want = (2 * 152 + tiles - 1) / tiles;
+    int want = (cn_resident_blocks<T>(best.rm, best.rn, best.ty * best.tx) * sm_count() + tiles - 1) / tiles;
     const int by_len = (K + 2 * KT - 1) / (2 * KT);
     if (want > by_len) want = by_len;
     if (max_chunks > 0 && want > max_chunks) want = max_chunks;
@@ -258,8 +312,7 @@ CnPlan cn_plan(int M, int N, int K, int max_chunks) {
 template <typename T, int RM, int RN>
 void launch_cn(const CnPlan& p, int M, int N, int K, const c2<T>* A, int64_t lda, const c2<T>* B, int64_t ldb,
                c2<T>* part, cudaStream_t st) {
-    constexpr int KT = CnTile<T>::KT;
-    const size_t smem = sizeof(c2<T>) * 2 * KT * (padstride<RM>() + padstride<RN>());
+    const size_t smem = cn_smem<T, RM, RN>();
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_gemm_cn<T, RM, RN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -342,6 +395,7 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int M, int N, int K, int TY, co
     extern __shared__ __align__(16) unsigned char nn_smem[];
     V* As = reinterpret_cast<V*>(nn_smem);   // [2][NN_KT][TM]
     V* Bs = As + 2 * NN_KT * TM;             // [2][NN_KT][SBN]
+    V* Cs = Bs + 2 * NN_KT * SBN;            // [SBN][TM]: beta C, staged before the main loop
     const int nthr = 32 * TY, tid = threadIdx.x;
     const int tx = tid & 31, ty = tid >> 5;
     const int TN = TY * RN;
@@ -371,6 +425,18 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int M, int N, int K, int TY, co
     for (int i = 0; i < RM; ++i)
 #pragma unroll
         for (int j = 0; j < RN; ++j) acc[i][j] = mk<T>(T(0), T(0));
+    // beta C is copied to shared memory asynchronously before the main loop,
+    // so its loads overlap the contraction instead of waiting one by one
+    // behind the stores of C in the epilogue
+    if (beta != T(0)) {
+        for (int e = tid; e < TN * TM; e += nthr) {
+            const int c = e / TM, r = e - c * TM;
+            const int m = m0 + r, n = n0 + c;
+            const bool ok = m < M && n < N;
+            cp_elem<T>(Cs + e, ok ? C + (int64_t)n * ldc + m : C, ok);
+        }
+    }
+    cp_commit();
     if (nk > 0) stage_in(0, 0);
     for (int t = 0; t < nk; ++t) {
         if (t + 1 < nk) {
@@ -396,6 +462,8 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int M, int N, int K, int TY, co
         }
         __syncthreads();
     }
+    cp_wait<0>();
+    __syncthreads();
 #pragma unroll
     for (int i = 0; i < RM; ++i) {
         const int m = m0 + tx + 32 * i;
@@ -404,10 +472,9 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int M, int N, int K, int TY, co
         for (int j = 0; j < RN; ++j) {
             const int n = n0 + ty * RN + j;
             if (n < N) {
-                V* dst = C + (int64_t)n * ldc + m;
                 V r = cscale(acc[i][j], alpha);
-                if (beta != T(0)) r = cadd(r, cscale(*dst, beta));
-                *dst = r;
+                if (beta != T(0)) r = cadd(r, cscale(Cs[(ty * RN + j) * TM + tx + 32 * i], beta));
+                C[(int64_t)n * ldc + m] = r;
             }
         }
     }
@@ -427,7 +494,7 @@ template <typename T, int RN>
 void launch_nn(int M, int N, int K, int ty, int nt, const c2<T>* A, int64_t lda, const c2<T>* B, int ldb, c2<T>* C,
                int64_t ldc, T alpha, T beta, cudaStream_t st) {
     constexpr int RM = 4;
-    const size_t smem = sizeof(c2<T>) * 2 * NN_KT * (32 * RM + 8 * RN);
+    const size_t smem = sizeof(c2<T>) * (2 * NN_KT * (32 * RM + 8 * RN) + (size_t)(8 * RN) * (32 * RM));
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_gemm_nn<T, RM, RN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -603,69 +670,76 @@ __global__ void __launch_bounds__(1024) k_cholesky_small(int n, const double2* _
 // n <= kSmallN: the first half of the refined factorisation below.
 __global__ void __launch_bounds__(1024) k_cholesky_f32(int n, const double2* __restrict__ O,
                                                        double2* __restrict__ Xout, int* flag) {
+    // W: working copy of the lower triangle of O; L: the factor; X = L^{-1}
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* L = reinterpret_cast<float2*>(smem_raw);
+    float2* W = reinterpret_cast<float2*>(smem_raw);
+    float2* L = W + n * n;
     float2* X = L + n * n;
-    __shared__ int bad;
     __shared__ float dinv[kSmallN];
-    if (threadIdx.x == 0) bad = 0;
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
         const double2 o = O[idx];
-        L[idx] = make_float2((float)o.x, (float)o.y);
-        X[idx] = make_float2(0.f, 0.f);
+        W[idx] = make_float2((float)o.x, (float)o.y);
     }
     __syncthreads();
+    int bad = 0;
+    // right-looking factorisation, one barrier per column: every thread
+    // derives the pivot itself, column j of L and the trailing update both
+    // read the unscaled column j of W, and the update writes only columns > j
     for (int j = 0; j < n; ++j) {
-        if (threadIdx.x == 0) {
-            float d = L[j * n + j].x;
-            if (!(d > 0.f)) {
-                if (!bad) bad = j + 1;
-                d = 1.f;
-            }
-            const float piv = sqrtf(d);
-            L[j * n + j] = make_float2(piv, 0.f);
-            dinv[j] = 1.f / piv;
+        float d = W[j * n + j].x;
+        if (!(d > 0.f)) {
+            if (!bad) bad = j + 1;
+            d = 1.f;
         }
-        __syncthreads();
-        const float inv = dinv[j];
-        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
-            const float2 v = L[j * n + i];
-            L[j * n + i] = make_float2(v.x * inv, v.y * inv);
+        const float piv = sqrtf(d), inv = 1.f / piv, invd = inv * inv;
+        if (threadIdx.x == 0) dinv[j] = inv;
+        for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
+            const float2 v = W[j * n + i];
+            L[j * n + i] = (i == j) ? make_float2(piv, 0.f) : make_float2(v.x * inv, v.y * inv);
         }
-        __syncthreads();
         const int m = n - j - 1;
         for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-            const int k = t / m;
-            const int i = t - k * m;
-            if (k > i) continue;
-            const float2 a = L[j * n + j + 1 + i], b = L[j * n + j + 1 + k];
-            float2 c = L[(j + 1 + k) * n + j + 1 + i];
-            c.x -= a.x * b.x + a.y * b.y;
-            c.y -= a.y * b.x - a.x * b.y;
-            L[(j + 1 + k) * n + j + 1 + i] = c;
+            const int k = j + 1 + t / m, i = j + 1 + t % m;
+            if (i < k) continue;
+            const float2 a = W[j * n + i], b = W[j * n + k];
+            // W(i, k) -= W(i, j) conj(W(k, j)) / d
+            float2 c = W[k * n + i];
+            c.x = fmaf(-(a.x * b.x + a.y * b.y), invd, c.x);
+            c.y = fmaf(-(a.y * b.x - a.x * b.y), invd, c.y);
+            W[k * n + i] = c;
         }
         __syncthreads();
     }
+    // X = L^{-1} by columns: warp c solves L x = e_c with a right-looking
+    // sweep (lane l holds rows l and l + 32); x_k reaches every lane by one
+    // shuffle per step
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int c = warp; c < n; c += nw) {
-        for (int i = c; i < n; ++i) {
-            float sr = 0.f, si = 0.f;
-            for (int k = c + lane; k < i; k += 32) {
-                const float2 l = L[k * n + i], x = X[c * n + k];
-                sr += l.x * x.x - l.y * x.y;
-                si += l.x * x.y + l.y * x.x;
+        float2 r0 = make_float2(lane == c ? 1.f : 0.f, 0.f);
+        float2 r1 = make_float2(lane + 32 == c ? 1.f : 0.f, 0.f);
+        for (int k = c; k < n; ++k) {
+            const float2 own = k < 32 ? r0 : r1;
+            const float sx = __shfl_sync(0xffffffffu, own.x, k & 31);
+            const float sy = __shfl_sync(0xffffffffu, own.y, k & 31);
+            const float di = dinv[k];
+            const float2 xk = make_float2(sx * di, sy * di);
+            if (lane == (k & 31)) {
+                if (k < 32) r0 = xk;
+                else r1 = xk;
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                sr += __shfl_xor_sync(0xffffffffu, sr, o);
-                si += __shfl_xor_sync(0xffffffffu, si, o);
+            if (lane > k && lane < n) {
+                const float2 l = L[k * n + lane];
+                r0.x -= l.x * xk.x - l.y * xk.y;
+                r0.y -= l.x * xk.y + l.y * xk.x;
             }
-            if (lane == 0) {
-                const float di = dinv[i];
-                X[c * n + i] = make_float2(((i == c) ? 1.f - sr : -sr) * di, -si * di);
+            if (lane + 32 > k && lane + 32 < n) {
+                const float2 l = L[k * n + lane + 32];
+                r1.x -= l.x * xk.x - l.y * xk.y;
+                r1.y -= l.x * xk.y + l.y * xk.x;
             }
-            __syncwarp();
         }
+        if (lane < n) X[c * n + lane] = lane >= c ? r0 : make_float2(0.f, 0.f);
+        if (lane + 32 < n) X[c * n + lane + 32] = lane + 32 >= c ? r1 : make_float2(0.f, 0.f);
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) Xout[idx] = make_double2(X[idx].x, X[idx].y);
@@ -701,7 +775,7 @@ __global__ void k_conj_transpose(int n, const double2* __restrict__ in, double2*
 // serial part is FP32.  w1, w2 hold n x n each.
 void cholesky_inverse_refined(int n, const double2* O, double2* w1, double2* w2, double2* LinvH, int* flag,
                               cudaStream_t st) {
-    const size_t sm = sizeof(float2) * 2 * n * n;
+    const size_t sm = sizeof(float2) * 3 * n * n;
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_cholesky_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     roks::count_launch(), k_cholesky_f32<<<1, 1024, sm, st>>>(n, O, w1, flag);          // w1 = X
     small_gemm(n, n, n, w1, n, false, O, n, false, LinvH, n, 1.0, 0.0, st);              // LinvH = X O
@@ -867,55 +941,90 @@ __global__ void k_expm_square(int n, const double2* __restrict__ E, double2* __r
 // memory: X = s A / 2^q (||s A||_1 / 2^q <= 1/4), Taylor degree 8 by Horner
 // (truncation below 1e-11), q squarings.  Used by the mixed-precision path, whose orbitals are
 // re-orthonormalised after every rotation.
-// C = A B for n x n column-major matrices in shared memory; each thread
-// computes a 2 x 2 block of C (n padded to even by the caller's layout).
-__device__ __forceinline__ void smem_matmul_f(int n, const float2* A, const float2* B, float2* C) {
+// C = A B + a0 I + a1 X + a2 X2 for n x n column-major matrices in shared
+// memory (A, B may be null: no product); each thread computes a 2 x 2 block
+// of C with fused multiply-adds.
+__device__ __forceinline__ void smem_mm_poly(int n, const float2* A, const float2* B, const float2* X,
+                                             const float2* X2, float a0, float a1, float a2, float2* C) {
     const int h = (n + 1) / 2;
     for (int t = threadIdx.x; t < h * h; t += blockDim.x) {
         const int m = 2 * (t % h), c = 2 * (t / h);
         const bool m1 = m + 1 < n, c1 = c + 1 < n;
-        float2 s00 = make_float2(0.f, 0.f), s01 = s00, s10 = s00, s11 = s00;
-        for (int k = 0; k < n; ++k) {
-            const float2 a0 = A[k * n + m], a1 = m1 ? A[k * n + m + 1] : make_float2(0.f, 0.f);
-            const float2 b0 = B[c * n + k], b1 = c1 ? B[(c + 1) * n + k] : make_float2(0.f, 0.f);
-            s00.x += a0.x * b0.x - a0.y * b0.y; s00.y += a0.x * b0.y + a0.y * b0.x;
-            s01.x += a0.x * b1.x - a0.y * b1.y; s01.y += a0.x * b1.y + a0.y * b1.x;
-            s10.x += a1.x * b0.x - a1.y * b0.y; s10.y += a1.x * b0.y + a1.y * b0.x;
-            s11.x += a1.x * b1.x - a1.y * b1.y; s11.y += a1.x * b1.y + a1.y * b1.x;
+        float2 s[2][2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+                const int mm = m + u, cc = c + v;
+                if (mm < n && cc < n) {
+                    const float2 x = X[cc * n + mm], x2 = X2[cc * n + mm];
+                    s[u][v] = make_float2((mm == cc ? a0 : 0.f) + a1 * x.x + a2 * x2.x, a1 * x.y + a2 * x2.y);
+                } else {
+                    s[u][v] = make_float2(0.f, 0.f);
+                }
+            }
+        if (A) {
+            for (int k = 0; k < n; ++k) {
+                const float2 a[2] = {A[k * n + m], m1 ? A[k * n + m + 1] : make_float2(0.f, 0.f)};
+                const float2 b[2] = {B[c * n + k], c1 ? B[(c + 1) * n + k] : make_float2(0.f, 0.f)};
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+#pragma unroll
+                    for (int v = 0; v < 2; ++v) {
+                        s[u][v].x = fmaf(a[u].x, b[v].x, s[u][v].x);
+                        s[u][v].x = fmaf(-a[u].y, b[v].y, s[u][v].x);
+                        s[u][v].y = fmaf(a[u].x, b[v].y, s[u][v].y);
+                        s[u][v].y = fmaf(a[u].y, b[v].x, s[u][v].y);
+                    }
+            }
         }
-        C[c * n + m] = s00;
-        if (c1) C[(c + 1) * n + m] = s01;
-        if (m1) C[c * n + m + 1] = s10;
-        if (m1 && c1) C[(c + 1) * n + m + 1] = s11;
+        C[c * n + m] = s[0][0];
+        if (c1) C[(c + 1) * n + m] = s[0][1];
+        if (m1) C[c * n + m + 1] = s[1][0];
+        if (m1 && c1) C[(c + 1) * n + m + 1] = s[1][1];
     }
 }
 
+// E = exp(s A) in FP32 (n <= kSmallN): scaling by 2^-q until ||s A||_1 <=
+// 1/4, the degree-8 Taylor polynomial in Paterson-Stockmeyer form
+// T8 = B0 + X^3 (B1 + X^3 B2) with B0 = I + X + X^2/2, B1 = I/3! + X/4! +
+// X^2/5!, B2 = I/6! + X/7! + X^2/8! (four products instead of seven), then q
+// squarings.  Truncation error <= (1/4)^9 / 9! < 1e-11.
 __global__ void __launch_bounds__(1024) k_expm_small_f32(int n, const double2* __restrict__ A,
                                                          const double* __restrict__ s, double2* __restrict__ E) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nn = n * n;
     float2* X = reinterpret_cast<float2*>(smem_raw);
-    float2* P = X + n * n;
-    float2* Q = P + n * n;
-    __shared__ float colmax[1024];
+    float2* X2 = X + nn;
+    float2* X3 = X2 + nn;
+    float2* T1 = X3 + nn;
+    float2* T2 = T1 + nn;
+    __shared__ float wmax[32];
     __shared__ int qs;
+    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+        const double2 a = A[idx];
+        X[idx] = make_float2((float)a.x, (float)a.y);
+    }
+    __syncthreads();
+    // 1-norm: one warp per column, lanes over rows
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     float best = 0.f;
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    for (int c = warp; c < n; c += nw) {
         float sum = 0.f;
-        for (int r = 0; r < n; ++r) {
-            const double2 a = A[c * n + r];
-            const float ax = (float)a.x, ay = (float)a.y;
-            sum += sqrtf(ax * ax + ay * ay);
+        for (int r = lane; r < n; r += 32) {
+            const float2 a = X[c * n + r];
+            sum += sqrtf(a.x * a.x + a.y * a.y);
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
         best = fmaxf(best, sum);
     }
-    colmax[threadIdx.x] = best;
+    if (lane == 0) wmax[warp] = best;
     __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) colmax[threadIdx.x] = fmaxf(colmax[threadIdx.x], colmax[threadIdx.x + w]);
-        __syncthreads();
-    }
     if (threadIdx.x == 0) {
-        float scaled = fabsf((float)s[0]) * colmax[0];
+        float m = 0.f;
+        for (int w = 0; w < nw; ++w) m = fmaxf(m, wmax[w]);
+        float scaled = fabsf((float)s[0]) * m;
         int q = 0;
         while (scaled > 0.25f && q < 30) {
             scaled *= 0.5f;
@@ -926,40 +1035,41 @@ __global__ void __launch_bounds__(1024) k_expm_small_f32(int n, const double2* _
     __syncthreads();
     const int q = qs;
     const float f = (float)s[0] * ldexpf(1.f, -q);
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-        const double2 a = A[idx];
-        const float xr = f * (float)a.x, xi = f * (float)a.y;
-        X[idx] = make_float2(xr, xi);
-        const int m = idx % n, c = idx / n;
-        // P = I + X / 8
-        P[idx] = make_float2((m == c ? 1.f : 0.f) + xr * 0.125f, xi * 0.125f);
-    }
+    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) X[idx] = make_float2(f * X[idx].x, f * X[idx].y);
     __syncthreads();
-    for (int k = 7; k >= 1; --k) {
-        smem_matmul_f(n, X, P, Q);
-        __syncthreads();
-        const float ik = 1.f / (float)k;
-        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-            const int m = idx % n, c = idx / n;
-            const float2 t = Q[idx];
-            P[idx] = make_float2((m == c ? 1.f : 0.f) + t.x * ik, t.y * ik);
-        }
-        __syncthreads();
-    }
+    constexpr float c3 = 1.f / 6.f, c4 = 1.f / 24.f, c5 = 1.f / 120.f, c6 = 1.f / 720.f, c7 = 1.f / 5040.f,
+                    c8 = 1.f / 40320.f;
+    smem_mm_poly(n, X, X, X, X, 0.f, 0.f, 0.f, X2);                  // X^2
+    __syncthreads();
+    smem_mm_poly(n, X2, X, X, X2, 0.f, 0.f, 0.f, X3);                // X^3
+    smem_mm_poly(n, nullptr, nullptr, X, X2, c6, c7, c8, T1);        // B2 (independent of X^3)
+    __syncthreads();
+    smem_mm_poly(n, X3, T1, X, X2, c3, c4, c5, T2);                  // B1 + X^3 B2
+    __syncthreads();
+    smem_mm_poly(n, X3, T2, X, X2, 1.f, 1.f, 0.5f, T1);              // B0 + X^3 (...)
+    __syncthreads();
+    float2* P = T1;
+    float2* Q = T2;
     for (int r = 0; r < q; ++r) {
-        smem_matmul_f(n, P, P, Q);
+        smem_mm_poly(n, P, P, X, X2, 0.f, 0.f, 0.f, Q);
         __syncthreads();
-        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) P[idx] = Q[idx];
-        __syncthreads();
+        float2* t = P;
+        P = Q;
+        Q = t;
     }
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) E[idx] = make_double2(P[idx].x, P[idx].y);
+    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) E[idx] = make_double2(P[idx].x, P[idx].y);
 }
 
 bool expm_small_f32(int n, const double2* A, const double* scale_dev, double2* E, cudaStream_t st) {
     if (n > kSmallN) return false;
-    const size_t sm = sizeof(float2) * 3 * n * n;
+    const size_t sm = sizeof(float2) * 5 * n * n;
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_expm_small_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    roks::count_launch(), k_expm_small_f32<<<1, 1024, sm, st>>>(n, A, scale_dev, E);
+    // one thread per 2 x 2 output block, whole warps, at least two warps
+    const int h = (n + 1) / 2;
+    int threads = ((h * h + 31) / 32) * 32;
+    if (threads < 64) threads = 64;
+    if (threads > 1024) threads = 1024;
+    roks::count_launch(), k_expm_small_f32<<<1, threads, sm, st>>>(n, A, scale_dev, E);
     return true;
 }
 

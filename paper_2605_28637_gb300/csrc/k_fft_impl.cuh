@@ -277,9 +277,12 @@ __global__ void __launch_bounds__(kThreads) k_band_x_inv_full(Sphere s, const c2
 template <typename T, int N>
 __global__ void __launch_bounds__(kThreads) k_band_x_density(Sphere s, const c2<T>* __restrict__ tw,
                                                              const c2<T>* __restrict__ Yp,
-                                                             double* __restrict__ rho3, double* __restrict__ slot,
-                                                             int b0, int nbb, int gs, int n_closed, double scale) {
+                                                             typename DensAcc<T>::S* __restrict__ rho3,
+                                                             typename DensAcc<T>::S* __restrict__ slot,
+                                                             int b0, int nbb, int gs, int n_closed, T scale) {
     using V = c2<T>;
+    using DA = DensAcc<T>;
+    using DS = typename DA::S;
     constexpr int TL = tile_lines(N), LS = TL + 1;
     using Slots = LastPassSlots<N, TL, kThreads>;
     constexpr int PER = Slots::PER, R = Slots::R;
@@ -294,14 +297,14 @@ __global__ void __launch_bounds__(kThreads) k_band_x_density(Sphere s, const c2<
     const int N3 = N * N * N;
     const int nmax = s.nmax;
     const int gbeg = g * gs, gend = min(nbb, gbeg + gs);
-    double* slot_g = slot + (int64_t)g * N3;
+    DS* slot_g = slot + (int64_t)g * N3;
     bool slot_written = false;
     int bb = gbeg;
     while (bb < gend) {
         const int b = b0 + bb;
         const int cls = b < n_closed ? 0 : b - n_closed + 1;
         const int seg_end = cls == 0 ? min(gend, n_closed - b0) : bb + 1;
-        double* rr = cls == 0 ? slot_g : rho3 + (int64_t)cls * N3;
+        DS* rr = cls == 0 ? slot_g : rho3 + (int64_t)cls * N3;
         while (bb < seg_end) {
             T part[PER][R];
 #pragma unroll
@@ -328,9 +331,9 @@ __global__ void __launch_bounds__(kThreads) k_band_x_density(Sphere s, const c2<
                 for (int r = 0; r < R; ++r) {
                     int line = 0, e = 0;
                     if (Slots::point(threadIdx.x, q, r, line, e) && z0 + line < N) {
-                        double* dst = rr + ((int64_t)e * N + y) * N + z0 + line;
-                        const double add = double(part[q][r]) * scale;
-                        *dst = (cls != 0 || !first) ? *dst + add : add;
+                        DS* dst = rr + ((int64_t)e * N + y) * N + z0 + line;
+                        const T add = part[q][r] * scale;
+                        *dst = (cls != 0 || !first) ? DA::add(*dst, add) : DA::make(add);
                     }
                 }
             if (cls == 0) slot_written = true;
@@ -344,19 +347,20 @@ __global__ void __launch_bounds__(kThreads) k_band_x_density(Sphere s, const c2<
             for (int r = 0; r < R; ++r) {
                 int line = 0, e = 0;
                 if (Slots::point(threadIdx.x, q, r, line, e) && z0 + line < N)
-                    slot_g[((int64_t)e * N + y) * N + z0 + line] = 0.0;
+                    slot_g[((int64_t)e * N + y) * N + z0 + line] = DA::make(T(0));
             }
     }
 }
 
-// rho3[0] = sum of the closed-shell slots in group order (templated only so
-// that each precision's translation unit has its own copy)
+// rho3[0] = sum of the closed-shell slots in group order
 template <typename T>
-__global__ void k_density_reduce(int64_t N3, int ng, const double* __restrict__ slot, double* __restrict__ rho) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_density_reduce(int N3, int ng, const typename DensAcc<T>::S* __restrict__ slot,
+                                 typename DensAcc<T>::S* __restrict__ rho) {
+    using DA = DensAcc<T>;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= N3) return;
-    double s = 0.0;
-    for (int g = 0; g < ng; ++g) s += slot[(int64_t)g * N3 + p];
+    typename DA::S s = slot[p];
+    for (int g = 1; g < ng; ++g) s = DA::add2(s, slot[(int64_t)g * N3 + p]);
     rho[p] = s;
 }
 
@@ -468,10 +472,13 @@ struct BandFft {
         const int gs = (nbb + ngroups - 1) / ngroups;
         const int ng = (nbb + gs - 1) / gs;
         dim3 g((N + TL - 1) / TL, N, ng);
-        roks::count_launch(), k_band_x_density<T, N><<<g, kThreads, SM, st>>>(s, tw, Yp, rho3, slot, b0, nbb, gs, nc,
-                                                                            scale);
-        const int64_t N3 = (int64_t)N * N * N;
-        roks::count_launch(), k_density_reduce<T><<<(unsigned)((N3 + 255) / 256), 256, 0, st>>>(N3, ng, slot, rho3);
+        using DS = typename DensAcc<T>::S;
+        DS* r3 = reinterpret_cast<DS*>(rho3);
+        DS* sl = reinterpret_cast<DS*>(slot);
+        roks::count_launch(), k_band_x_density<T, N><<<g, kThreads, SM, st>>>(s, tw, Yp, r3, sl, b0, nbb, gs, nc,
+                                                                            T(scale));
+        const int N3 = N * N * N;
+        roks::count_launch(), k_density_reduce<T><<<(unsigned)((N3 + 255) / 256), 256, 0, st>>>(N3, ng, sl, r3);
     }
     static void grid3(const V* tw, V* data, int dir, int batch, int64_t bstride, cudaStream_t st) {
         set_smem(k_grid_fft_z<T, N>, SM);

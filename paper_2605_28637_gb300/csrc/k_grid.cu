@@ -21,6 +21,37 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return r;
 }
 
+// Block sum of per-thread values of the element type, in FP64, valid in
+// thread 0.  FP32: each warp reduces (sum, error) pairs with Knuth's
+// two-sum and only the warp results are widened, so no per-thread FP64
+// arithmetic or conversion runs (both are slow on this part) while the sum
+// keeps about FP64 accuracy.  FP64: the plain tree.
+template <typename T>
+__device__ __forceinline__ double block_sum_t(T v, double* sh) {
+    if constexpr (sizeof(T) == 8) {
+        return block_sum(v, sh);
+    } else {
+        float s = v, c = 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float so = __shfl_xor_sync(0xffffffffu, s, o);
+            const float co = __shfl_xor_sync(0xffffffffu, c, o);
+            const float t = s + so;
+            const float bp = t - s;
+            c = c + co + ((s - (t - bp)) + (so - bp));
+            s = t;
+        }
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (lane == 0) sh[warp] = double(s) + double(c);
+        __syncthreads();
+        double r = 0.0;
+        if (threadIdx.x == 0)
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sh[w];
+        __syncthreads();
+        return r;
+    }
+}
+
 // ------------------------------------------------------------------ set-up
 // V(G) = -(1/Omega) sum_a d_a (2 pi w^2)^{3/2} exp(-G^2 w^2 / 2) exp(-i G.R_a)
 // on the grid (signed frequencies, N/2 -> +N/2), zero on Nyquist planes.
@@ -110,7 +141,7 @@ __global__ void k_to_real(int64_t n, const double* __restrict__ in, T* __restric
 template <typename T, int OP>
 __global__ void __launch_bounds__(RB) k_colred(int npw, int nb, const c2<T>* __restrict__ x, int64_t ldx,
                                                const c2<T>* __restrict__ y, int64_t ldy,
-                                               const double* __restrict__ g2, int nsplit, double* __restrict__ part) {
+                                               const T* __restrict__ g2h, int nsplit, double* __restrict__ part) {
     __shared__ double sh[RB];
     const int n = blockIdx.x, sp = blockIdx.y;
     const int per = (npw + nsplit - 1) / nsplit;
@@ -121,10 +152,10 @@ __global__ void __launch_bounds__(RB) k_colred(int npw, int nb, const c2<T>* __r
     for (int g = g0 + threadIdx.x; g < g1; g += RB) {
         const c2<T> a = xc[g];
         const T m = a.x * a.x + a.y * a.y;
-        if (OP == 0) t0 += T(0.5) * T(g2[g]) * m;
+        if (OP == 0) t0 += g2h[g] * m;
         if (OP == 1) {
             t0 += m;
-            t1 += T(g2[g]) * m;
+            t1 += T(2) * g2h[g] * m;
         }
         if (OP == 2) {
             const c2<T> bb = y[(int64_t)n * ldy + g];
@@ -132,9 +163,9 @@ __global__ void __launch_bounds__(RB) k_colred(int npw, int nb, const c2<T>* __r
         }
         if (OP == 3) t0 += m;
     }
-    double s0 = block_sum(double(t0), sh);
+    double s0 = block_sum_t<T>(t0, sh);
     double s1 = 0.0;
-    if (OP == 1) s1 = block_sum(double(t1), sh);
+    if (OP == 1) s1 = block_sum_t<T>(t1, sh);
     if (threadIdx.x == 0) {
         part[((int64_t)0 * nb + n) * nsplit + sp] = s0;
         if (OP == 1) part[((int64_t)1 * nb + n) * nsplit + sp] = s1;
@@ -151,7 +182,7 @@ __global__ void k_colred_final(int count, int nsplit, const double* __restrict__
 
 template <typename T>
 void column_sums(int op, int npw, int nb, const c2<T>* x, int64_t ldx, const c2<T>* y, int64_t ldy,
-                 const double* g2, double* part, double* out, cudaStream_t st) {
+                 const T* g2, double* part, double* out, cudaStream_t st) {
     constexpr int nsplit = 16;
     dim3 g(nb, nsplit);
     switch (op) {
@@ -208,45 +239,45 @@ __global__ void k_band_quadratic(int nproj, int nb, const double2* __restrict__ 
 // xc3[k] = sum_ch C[k][ch] v^{ch},  v = -(1-alpha) (6 rho / pi)^{1/3};
 // partial sums of (1-alpha) Slater energies per configuration and of V_loc rho.
 template <typename T>
-__global__ void __launch_bounds__(RB) k_pot_xc(int64_t N3, const double* __restrict__ rho3,
-                                               const double* __restrict__ vloc, PotCoef cf,
-                                               c2<T>* __restrict__ rho_grid, double* __restrict__ xc3,
+__global__ void __launch_bounds__(RB) k_pot_xc(int N3, const typename DensAcc<T>::S* __restrict__ rho3,
+                                               const T* __restrict__ vloc, PotCoefT<T> cf, T c6, T cx,
+                                               c2<T>* __restrict__ rho_grid, T* __restrict__ xc3,
                                                double* __restrict__ part) {
-    // pointwise arithmetic in the element type T; per-thread partial energies
-    // in T over a few points, block and grid sums in FP64
+    // pointwise arithmetic in the element type T (constants come from the
+    // host: FP64 arithmetic per thread is slow on this part); per-thread
+    // partial energies in T over a few points, block and grid sums in FP64
     __shared__ double sh[RB];
     T exM = 0, exT = 0, eloc = 0;
-    const T c6 = T(cbrt(6.0 / kPi));            // (6 / pi)^{1/3}
-    const T cx = T(0.75) * c6;
-    const T xs = T(cf.xscale);
-    for (int64_t p = (int64_t)blockIdx.x * RB + threadIdx.x; p < N3; p += (int64_t)gridDim.x * RB) {
-        const T rk[3] = {T(rho3[p]), T(rho3[N3 + p]), T(rho3[2 * N3 + p])};
+    const T xs = cf.xscale;
+    for (int p = blockIdx.x * RB + threadIdx.x; p < N3; p += gridDim.x * RB) {
+        using DA = DensAcc<T>;
+        const T rk[3] = {T(DA::value(rho3[p])), T(DA::value(rho3[N3 + p])), T(DA::value(rho3[2 * N3 + p]))};
         T v[4];
         T rho_tot = 0;
 #pragma unroll
         for (int ch = 0; ch < 4; ++ch) {
             T r = 0;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) r += T(cf.f[k][ch]) * rk[k];
+            for (int k = 0; k < 3; ++k) r += cf.f[k][ch] * rk[k];
             r = r > T(0) ? r : T(0);
             const T c = cbrt(r);
             v[ch] = -xs * c6 * c;
             const T e = -xs * cx * c * r;
             if (ch < 2) { exM += e; rho_tot += r; } else exT += e;
         }
-        eloc += T(vloc[p]) * rho_tot;
+        eloc += vloc[p] * rho_tot;
         rho_grid[p] = mk<T>(rho_tot, T(0));
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             T s = 0;
 #pragma unroll
-            for (int ch = 0; ch < 4; ++ch) s += T(cf.C[k][ch]) * v[ch];
-            xc3[k * N3 + p] = double(s);
+            for (int ch = 0; ch < 4; ++ch) s += cf.C[k][ch] * v[ch];
+            xc3[k * N3 + p] = s;
         }
     }
-    const double dexM = block_sum(double(exM), sh);
-    const double dexT = block_sum(double(exT), sh);
-    const double deloc = block_sum(double(eloc), sh);
+    const double dexM = block_sum_t<T>(exM, sh);
+    const double dexT = block_sum_t<T>(exT, sh);
+    const double deloc = block_sum_t<T>(eloc, sh);
     if (threadIdx.x == 0) {
         part[blockIdx.x * 4 + 0] = dexM;
         part[blockIdx.x * 4 + 1] = dexT;
@@ -258,15 +289,14 @@ __global__ void __launch_bounds__(RB) k_pot_xc(int64_t N3, const double* __restr
 // After the forward transform: rho(G) = grid / N^3; E_H partial
 // sum 4 pi |rho(G)|^2 / G^2; grid <- V_H(G) = 4 pi rho(G) / G^2 (G = 0 -> 0).
 template <typename T>
-__global__ void __launch_bounds__(RB) k_hartree_G(int N, double b, c2<T>* __restrict__ grid,
+__global__ void __launch_bounds__(RB) k_hartree_G(int N, T inv, T fpb, c2<T>* __restrict__ grid,
                                                   double* __restrict__ part) {
+    // inv = 1 / N^3, fpb = 4 pi / b^2 with b = 2 pi / L (from the host)
     __shared__ double sh[RB];
-    const int64_t N3 = (int64_t)N * N * N;
-    const T inv = T(1.0 / double(N3));
-    const T fpb = T(4.0 * kPi / (b * b));
+    const int N3 = N * N * N;
     T eh = 0;
-    for (int64_t p = (int64_t)blockIdx.x * RB + threadIdx.x; p < N3; p += (int64_t)gridDim.x * RB) {
-        const int z = p % N, y = (p / N) % N, x = p / ((int64_t)N * N);
+    for (int p = blockIdx.x * RB + threadIdx.x; p < N3; p += gridDim.x * RB) {
+        const int z = p % N, y = (p / N) % N, x = p / (N * N);
         const int fx = signed_freq(x, N), fy = signed_freq(y, N), fz = signed_freq(z, N);
         const int m2 = fx * fx + fy * fy + fz * fz;
         const c2<T> gv = grid[p];
@@ -279,33 +309,38 @@ __global__ void __launch_bounds__(RB) k_hartree_G(int N, double b, c2<T>* __rest
         }
         grid[p] = o;
     }
-    const double deh = block_sum(double(eh), sh);
+    const double deh = block_sum_t<T>(eh, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = deh;
 }
 
 // V^k = w_k (V_loc + V_H) + xc3[k]; partial sums <a|V^c|a>, <b|V^c|b> (rho_a, rho_b).
 template <typename T>
-__global__ void __launch_bounds__(RB) k_pot_class(int64_t N3, const double* __restrict__ vloc,
-                                                  const c2<T>* __restrict__ vh, const double* __restrict__ xc3,
-                                                  const double* __restrict__ rho3, PotCoef cf, T* __restrict__ Vk,
+__global__ void __launch_bounds__(RB) k_pot_class(int N3, const T* __restrict__ vloc,
+                                                  const c2<T>* __restrict__ vh, const T* __restrict__ xc3,
+                                                  const typename DensAcc<T>::S* __restrict__ rho3, PotCoef cf,
+                                                  T* __restrict__ Vk,
                                                   double* __restrict__ Vk64, double* __restrict__ part) {
     __shared__ double sh[RB];
     T ea = 0, eb = 0;
-    for (int64_t p = (int64_t)blockIdx.x * RB + threadIdx.x; p < N3; p += (int64_t)gridDim.x * RB) {
-        const T v0 = T(vloc[p]) + vh[p].x;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const T v = T(cf.w[k]) * v0 + T(xc3[k * N3 + p]);
-            Vk[k * N3 + p] = v;
-            if (Vk64) Vk64[k * N3 + p] = double(v);
-            if (k == 0) {
-                ea += v * T(rho3[N3 + p]);
-                eb += v * T(rho3[2 * N3 + p]);
-            }
+    const T w0 = T(cf.w[0]), w1 = T(cf.w[1]), w2 = T(cf.w[2]);
+    for (int p = blockIdx.x * RB + threadIdx.x; p < N3; p += gridDim.x * RB) {
+        const T v0 = vloc[p] + vh[p].x;
+        const T vc = w0 * v0 + xc3[p];
+        const T va = w1 * v0 + xc3[N3 + p];
+        const T vb = w2 * v0 + xc3[2 * N3 + p];
+        Vk[p] = vc;
+        Vk[N3 + p] = va;
+        Vk[2 * N3 + p] = vb;
+        if (Vk64) {
+            Vk64[p] = double(vc);
+            Vk64[N3 + p] = double(va);
+            Vk64[2 * N3 + p] = double(vb);
         }
+        ea += vc * T(DensAcc<T>::value(rho3[N3 + p]));
+        eb += vc * T(DensAcc<T>::value(rho3[2 * N3 + p]));
     }
-    const double dea = block_sum(double(ea), sh);
-    const double deb = block_sum(double(eb), sh);
+    const double dea = block_sum_t<T>(ea, sh);
+    const double deb = block_sum_t<T>(eb, sh);
     if (threadIdx.x == 0) {
         part[blockIdx.x * 2 + 0] = dea;
         part[blockIdx.x * 2 + 1] = deb;
@@ -329,7 +364,7 @@ __global__ void __launch_bounds__(RB) k_partials_final(int nblocks, int nq, cons
 // ------------------------------------------------------------------ PCG pointwise
 // K g: K(G, n) = -(2 / X_n) tpa(|G|^2 / X_n), X_n = 1.5 sum g2 |g|^2 / sum |g|^2.
 template <typename T>
-__global__ void k_precond(int npw, const c2<T>* __restrict__ gI, int64_t ld, const double* __restrict__ g2,
+__global__ void k_precond(int npw, const c2<T>* __restrict__ gI, int64_t ld, const T* __restrict__ g2h,
                           const double* __restrict__ sums /* [2 nb]: |g|^2, g2 |g|^2 */, int nb,
                           c2<T>* __restrict__ out, int64_t ldo) {
     __shared__ T Xs[2];
@@ -342,7 +377,7 @@ __global__ void k_precond(int npw, const c2<T>* __restrict__ gI, int64_t ld, con
     }
     __syncthreads();
     if (g >= npw) return;
-    const T x = T(g2[g]) * Xs[0];
+    const T x = T(2) * g2h[g] * Xs[0];
     const T num = T(27) + x * (T(18) + x * (T(12) + T(8) * x));
     const T K = Xs[1] * num / (num + T(16) * x * x * x * x);
     const c2<T> a = gI[(int64_t)n * ld + g];
@@ -353,12 +388,16 @@ __global__ void k_precond(int npw, const c2<T>* __restrict__ gI, int64_t ld, con
 template <typename T>
 __global__ void k_axpy(int npw, const c2<T>* __restrict__ x, int64_t ldx, const c2<T>* __restrict__ y, int64_t ldy,
                        const double* __restrict__ coef, double csign, c2<T>* __restrict__ out, int64_t ldo) {
+    // the coefficient is formed once per block (FP64 arithmetic per element is slow on this part)
+    __shared__ T cs;
+    if (threadIdx.x == 0 && y) cs = T(csign * coef[0]);
+    __syncthreads();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = blockIdx.y;
     if (g >= npw) return;
     c2<T> a = x[(int64_t)n * ldx + g];
     if (y) {
-        const T c = T(csign * coef[0]);
+        const T c = cs;
         const c2<T> b = y[(int64_t)n * ldy + g];
         a.x += c * b.x;
         a.y += c * b.y;
@@ -409,32 +448,63 @@ void band_quadratic(int nproj, int nb, const double2* B, const double2* DB, doub
     roks::count_launch(), k_band_quadratic<<<nb, RB, 0, st>>>(nproj, nb, B, DB, out);
 }
 
+// Grid densities of the element type's storage -> FP64 (API output)
+template <typename T>
+__global__ void k_density_to_f64(int64_t n, const typename DensAcc<T>::S* __restrict__ in, double* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if constexpr (sizeof(T) == 4) out[i] = double(in[i].x) + double(in[i].y);
+    else out[i] = in[i];
+}
+
+template <typename T>
+void density_to_f64(int64_t n, const double* rho3, double* out, cudaStream_t st) {
+    using DS = typename DensAcc<T>::S;
+    roks::count_launch(), k_density_to_f64<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        n, reinterpret_cast<const DS*>(rho3), out);
+}
+template void density_to_f64<float>(int64_t, const double*, double*, cudaStream_t);
+template void density_to_f64<double>(int64_t, const double*, double*, cudaStream_t);
+
 constexpr int kPotBlocks = 512;
 
 template <typename T>
-void potentials(int N, double L, const double* rho3, const double* vloc, const PotCoef& cf, c2<T>* grid,
-                double* xc3, const c2<T>* tw, T* Vk, double* Vk64, double* part, double* out6,
+void potentials(int N, double L, const double* rho3, const T* vloc, const PotCoef& cf, c2<T>* grid,
+                T* xc3, const c2<T>* tw, T* Vk, double* Vk64, double* part, double* out6,
                 cudaStream_t st) {
     // out6: [E_x^M, E_x^T, E_loc, E_H, <a|V^c|a>, <b|V^c|b>]
-    const int64_t N3 = (int64_t)N * N * N;
+    const int N3 = N * N * N;
     const double dvol = L * L * L / double(N3);
-    roks::count_launch(), k_pot_xc<T><<<kPotBlocks, RB, 0, st>>>(N3, rho3, vloc, cf, grid, xc3, part);
+    const double c6 = std::cbrt(6.0 / kPi);                 // (6 / pi)^{1/3}
+    const double b = 2.0 * kPi / L;
+    using DS = typename DensAcc<T>::S;
+    const DS* r3 = reinterpret_cast<const DS*>(rho3);
+    PotCoefT<T> ct;
+    for (int k = 0; k < 3; ++k)
+        for (int ch = 0; ch < 4; ++ch) {
+            ct.f[k][ch] = T(cf.f[k][ch]);
+            ct.C[k][ch] = T(cf.C[k][ch]);
+        }
+    ct.xscale = T(cf.xscale);
+    roks::count_launch(), k_pot_xc<T><<<kPotBlocks, RB, 0, st>>>(N3, r3, vloc, ct, T(c6), T(0.75 * c6), grid, xc3,
+                                                                  part);
     roks::count_launch(), k_partials_final<<<4, RB, 0, st>>>(kPotBlocks, 4, part, out6, dvol, dvol, dvol, 0.0);
     grid_fft3<T>(N, tw, grid, -1, st);
-    roks::count_launch(), k_hartree_G<T><<<kPotBlocks, RB, 0, st>>>(N, 2.0 * kPi / L, grid, part);
+    roks::count_launch(), k_hartree_G<T><<<kPotBlocks, RB, 0, st>>>(N, T(1.0 / double(N3)), T(4.0 * kPi / (b * b)),
+                                                                     grid, part);
     roks::count_launch(), k_partials_final<<<1, RB, 0, st>>>(kPotBlocks, 1, part, out6 + 3, 0.5 * L * L * L, 0, 0, 0);
     grid_fft3<T>(N, tw, grid, +1, st);
-    roks::count_launch(), k_pot_class<T><<<kPotBlocks, RB, 0, st>>>(N3, vloc, grid, xc3, rho3, cf, Vk, Vk64, part);
+    roks::count_launch(), k_pot_class<T><<<kPotBlocks, RB, 0, st>>>(N3, vloc, grid, xc3, r3, cf, Vk, Vk64, part);
     roks::count_launch(), k_partials_final<<<2, RB, 0, st>>>(kPotBlocks, 2, part, out6 + 4, dvol, dvol, 0, 0);
 }
 
 size_t potentials_part_elems() { return (size_t)kPotBlocks * 4; }
 
 template <typename T>
-void precondition(int npw, int nb, const c2<T>* gI, int64_t ld, const double* g2, const double* sums, c2<T>* out,
+void precondition(int npw, int nb, const c2<T>* gI, int64_t ld, const T* g2h, const double* sums, c2<T>* out,
                   int64_t ldo, cudaStream_t st) {
     dim3 g((npw + 255) / 256, nb);
-    roks::count_launch(), k_precond<T><<<g, 256, 0, st>>>(npw, gI, ld, g2, sums, nb, out, ldo);
+    roks::count_launch(), k_precond<T><<<g, 256, 0, st>>>(npw, gI, ld, g2h, sums, nb, out, ldo);
 }
 
 template <typename T>
@@ -449,11 +519,11 @@ void axpy(int npw, int nb, const c2<T>* x, int64_t ldx, const c2<T>* y, int64_t 
                                       cudaStream_t);                                                           \
     template void init_orbitals<T>(int, int, const double*, const double*, c2<T>*, int64_t, cudaStream_t);     \
     template void to_real_type<T>(int64_t, const double*, T*, double, cudaStream_t);                           \
-    template void column_sums<T>(int, int, int, const c2<T>*, int64_t, const c2<T>*, int64_t, const double*,  \
+    template void column_sums<T>(int, int, int, const c2<T>*, int64_t, const c2<T>*, int64_t, const T*,       \
                                  double*, double*, cudaStream_t);                                              \
-    template void potentials<T>(int, double, const double*, const double*, const PotCoef&, c2<T>*, double*,   \
+    template void potentials<T>(int, double, const double*, const T*, const PotCoef&, c2<T>*, T*,             \
                                 const c2<T>*, T*, double*, double*, double*, cudaStream_t);                   \
-    template void precondition<T>(int, int, const c2<T>*, int64_t, const double*, const double*, c2<T>*,      \
+    template void precondition<T>(int, int, const c2<T>*, int64_t, const T*, const double*, c2<T>*,           \
                                   int64_t, cudaStream_t);                                                      \
     template void axpy<T>(int, int, const c2<T>*, int64_t, const c2<T>*, int64_t, const double*, double,      \
                           c2<T>*, int64_t, cudaStream_t);

@@ -43,6 +43,7 @@ struct roks_ctx {
     void* d_wk = nullptr;          // class weights (T)
     double* d_wband = nullptr;     // weight per band (FP64)
     double* d_vloc = nullptr;      // V_loc(r)
+    void* d_vloc_t = nullptr;      // V_loc(r) in the element type (the FP64 path aliases d_vloc)
     void* d_P = nullptr;           // projectors npw x nproj (T complex, ld = ld_min)
     int *d_blk_off = nullptr, *d_blk_n = nullptr;
     double *d_Drow = nullptr, *d_Qrow = nullptr;
@@ -247,7 +248,7 @@ struct Impl {
             band_x_density<T>(s, ccv(ctx->d_tw), cv(ctx->d_Yp), ctx->d_rho3, ctx->d_rho_slot, kDensityGroups, 0,
                               ctx->nb, ctx->nc, 1.0 / ctx->omega, st);
         }
-        column_sums<T>(0, ctx->npw, ctx->nb, p, ld, nullptr, 0, ctx->d_g2, ctx->d_colpart, ctx->d_kin_b, st);
+        column_sums<T>(0, ctx->npw, ctx->nb, p, ld, nullptr, 0, static_cast<const T*>(ctx->d_g2half), ctx->d_colpart, ctx->d_kin_b, st);
         const double2* B = Bgiven;
         if (!B) {
             PROF("proj_PhPsi");
@@ -265,8 +266,9 @@ struct Impl {
     static roks_status potential(roks_ctx* ctx) {
         cudaStream_t st = ctx->st;
         PROF("potential");
-        potentials<T>(ctx->N, ctx->L, ctx->d_rho3, ctx->d_vloc, ctx->cf, reinterpret_cast<V*>(ctx->d_grid),
-                      ctx->d_xc3, ccv(ctx->d_tw), static_cast<T*>(ctx->d_Vk), nullptr, ctx->d_part, ctx->d_out6, st);
+        potentials<T>(ctx->N, ctx->L, ctx->d_rho3, static_cast<const T*>(ctx->d_vloc_t), ctx->cf,
+                      reinterpret_cast<V*>(ctx->d_grid), reinterpret_cast<T*>(ctx->d_xc3), ccv(ctx->d_tw),
+                      static_cast<T*>(ctx->d_Vk), nullptr, ctx->d_part, ctx->d_out6, st);
         energy_combine(ctx->d_kin_b, ctx->d_nl_b, ctx->nb, ctx->d_wband, ctx->d_out6, ctx->cM, ctx->cT,
                        ctx->alpha, ctx->alpha != 0.0 ? ctx->d_hf2 : nullptr, ctx->d_E, st);
         CK(cudaGetLastError());
@@ -398,7 +400,7 @@ struct Impl {
     // dst field = sum_n Re <x_n|y_n>
     static void dot_to(roks_ctx* ctx, const void* x, const void* y, int field) {
         const int64_t l = ctx->ld_min;
-        column_sums<T>(2, ctx->npw, ctx->nb, ccv(x), l, ccv(y), l, ctx->d_g2, ctx->d_colpart, ctx->d_colout, ctx->st);
+        column_sums<T>(2, ctx->npw, ctx->nb, ccv(x), l, ccv(y), l, static_cast<const T*>(ctx->d_g2half), ctx->d_colpart, ctx->d_colout, ctx->st);
         sum_to(ctx->d_colout, ctx->nb, reinterpret_cast<double*>(ctx->d_sc) + field, 1.0, ctx->st);
     }
 
@@ -459,11 +461,11 @@ struct Impl {
         gemm_nn<T>(npw, nb, nb, ccv(ctx->W_S), l, ctx->d_Gam, nb, cv(ctx->W_G), l, -1.0, 1.0, ctx->d_gemm_work, st);
         CK(cudaMemcpyAsync(ctx->W_gI, ctx->W_F, sizeof(V) * l * nb, cudaMemcpyDeviceToDevice, st));
         gemm_nn<T>(npw, nb, nb, ccv(ctx->W_S), l, ctx->d_Th, nb, cv(ctx->W_gI), l, -1.0, 1.0, ctx->d_gemm_work, st);
-        column_sums<T>(3, npw, nb, ccv(ctx->W_G), l, nullptr, 0, ctx->d_g2, ctx->d_colpart, ctx->d_colout, st);
+        column_sums<T>(3, npw, nb, ccv(ctx->W_G), l, nullptr, 0, static_cast<const T*>(ctx->d_g2half), ctx->d_colpart, ctx->d_colout, st);
         sum_to(ctx->d_colout, nb, reinterpret_cast<double*>(ctx->d_sc) + SC_FIELD(gnorm2), 1.0, st);
         // p_I = K g_I - Psi (S Psi)^H K g_I
-        column_sums<T>(1, npw, nb, ccv(ctx->W_gI), l, nullptr, 0, ctx->d_g2, ctx->d_colpart, ctx->d_colout, st);
-        precondition<T>(npw, nb, ccv(ctx->W_gI), l, ctx->d_g2, ctx->d_colout, cv(ctx->W_K), l, st);
+        column_sums<T>(1, npw, nb, ccv(ctx->W_gI), l, nullptr, 0, static_cast<const T*>(ctx->d_g2half), ctx->d_colpart, ctx->d_colout, st);
+        precondition<T>(npw, nb, ccv(ctx->W_gI), l, static_cast<const T*>(ctx->d_g2half), ctx->d_colout, cv(ctx->W_K), l, st);
         }
         project(ctx, psi, ld, ctx->W_K, ctx->W_K);
         dot_to(ctx, ctx->W_K, ctx->W_gI, SC_FIELD(pgI));
@@ -749,6 +751,7 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     AL(ctx->d_wk, rs * 3);
     AL(ctx->d_wband, sizeof(double) * nb);
     AL(ctx->d_vloc, sizeof(double) * N3);
+    if (ctx->prec != ROKS_FP64) AL(ctx->d_vloc_t, sizeof(float) * N3);
     AL(ctx->d_P, cs * (size_t)l * (ctx->nproj > 0 ? ctx->nproj : 1));
     AL(ctx->d_blk_off, sizeof(int) * (ctx->nproj + 1));
     AL(ctx->d_blk_n, sizeof(int) * (ctx->nproj + 1));
@@ -886,6 +889,8 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     }
     // -------- model on the device
     vloc_setup(N, cell->L, natoms, d_atoms, ctx->d_grid, ctx->d_vloc, ctx->d_tw64, ctx->st);
+    if (ctx->prec == ROKS_FP64) ctx->d_vloc_t = ctx->d_vloc;
+    else to_real_type<float>(N3, ctx->d_vloc, static_cast<float*>(ctx->d_vloc_t), 1.0, ctx->st);
     if (f64) projectors_setup<double>(npw, ctx->nproj, cell->L, ctx->d_miller, d_proj,
                                       static_cast<double2*>(ctx->d_P), l, ctx->st);
     else projectors_setup<float>(npw, ctx->nproj, cell->L, ctx->d_miller, d_proj, static_cast<float2*>(ctx->d_P), l,
@@ -949,9 +954,12 @@ roks_status roks_density(roks_ctx* ctx, const void* psi, int64_t ld, double* rho
     r = ctx->prec == ROKS_FP64 ? Impl<double>::density(ctx, psi, ld, nullptr)
                                : Impl<float>::density(ctx, psi, ld, nullptr);
     if (r != ROKS_OK) return r;
-    if (rho_out)
-        CK(cudaMemcpyAsync(rho_out, ctx->d_rho3, sizeof(double) * 3 * (size_t)ctx->N * ctx->N * ctx->N,
-                           cudaMemcpyDeviceToDevice, ctx->st));
+    if (rho_out) {
+        const int64_t n3 = 3 * (int64_t)ctx->N * ctx->N * ctx->N;
+        if (ctx->prec == ROKS_FP64) density_to_f64<double>(n3, ctx->d_rho3, static_cast<double*>(rho_out), ctx->st);
+        else density_to_f64<float>(n3, ctx->d_rho3, static_cast<double*>(rho_out), ctx->st);
+        CK(cudaGetLastError());
+    }
     return ROKS_OK;
 }
 

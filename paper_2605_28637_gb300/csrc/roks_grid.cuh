@@ -17,6 +17,13 @@ struct PotCoef {
     double w[3];
     double xscale;
 };
+// The same coefficients in the element type, converted once on the host.
+template <typename T>
+struct PotCoefT {
+    T f[3][4];
+    T C[3][4];
+    T xscale;
+};
 
 void vloc_setup(int N, double L, int natoms, const double* atoms_dev, double2* grid, double* vloc,
                 const double2* tw64, cudaStream_t st);
@@ -28,21 +35,26 @@ void init_orbitals(int npw, int nb, const double* u_dev, const double* g2, c2<T>
 template <typename T>
 void to_real_type(int64_t n, const double* in, T* out, double scale, cudaStream_t st);
 // op 0: kinetic 0.5 g2 |x|^2; 1: (|x|^2, g2 |x|^2) -> out[0..nb), out[nb..2nb); 2: Re <x|y>; 3: |x|^2.
-// part must hold 2 * nb * 16 doubles.
+// g2h = |G|^2 / 2 in the element type.  part must hold 2 * nb * 16 doubles.
 template <typename T>
 void column_sums(int op, int npw, int nb, const c2<T>* x, int64_t ldx, const c2<T>* y, int64_t ldy,
-                 const double* g2, double* part, double* out, cudaStream_t st);
+                 const T* g2h, double* part, double* out, cudaStream_t st);
 void apply_DQ(int nproj, int nb, const double2* B, const int* blk_off, const int* blk_n, const double* Drow,
               const double* Qrow, const double* wband, double2* DB, double2* QB, cudaStream_t st);
 void band_quadratic(int nproj, int nb, const double2* B, const double2* DB, double* out, cudaStream_t st);
-// Grid transforms in the element type T (FP32 for the mixed path), energies in FP64.
+// rho3 (3 x N^3) in DensAcc<T> storage -> FP64 values (out may not alias rho3)
 template <typename T>
-void potentials(int N, double L, const double* rho3, const double* vloc, const PotCoef& cf, c2<T>* grid,
-                double* xc3, const c2<T>* tw, T* Vk, double* Vk64, double* part, double* out6,
+void density_to_f64(int64_t n, const double* rho3, double* out, cudaStream_t st);
+// Grid transforms in the element type T (FP32 for the mixed path), energies
+// in FP64.  rho3 in DensAcc<T> storage; vloc and the exchange-correlation
+// fields xc3 (3 x N^3) in the element type T.
+template <typename T>
+void potentials(int N, double L, const double* rho3, const T* vloc, const PotCoef& cf, c2<T>* grid,
+                T* xc3, const c2<T>* tw, T* Vk, double* Vk64, double* part, double* out6,
                 cudaStream_t st);
 size_t potentials_part_elems();
 template <typename T>
-void precondition(int npw, int nb, const c2<T>* gI, int64_t ld, const double* g2, const double* sums, c2<T>* out,
+void precondition(int npw, int nb, const c2<T>* gI, int64_t ld, const T* g2h, const double* sums, c2<T>* out,
                   int64_t ldo, cudaStream_t st);
 template <typename T>
 void axpy(int npw, int nb, const c2<T>* x, int64_t ldx, const c2<T>* y, int64_t ldy, const double* coef,

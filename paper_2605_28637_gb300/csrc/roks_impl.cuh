@@ -69,9 +69,39 @@ void band_y_fwd(const Sphere& s, const c2<T>* tw, const c2<T>* Yp, c2<T>* Zc, in
 template <typename T>
 void band_z_fwd(const Sphere& s, const c2<T>* tw, const c2<T>* Zc, c2<T>* out, int64_t ldo, const c2<T>* psi,
                 int64_t ldp, const T* g2half, const T* wk, int b0, int nbb, int n_closed, cudaStream_t st);
-// x stage, inverse: rho3 (3 x N^3, double) = sum |psi|^2 * scale per class,
-// bands split into up to ngroups groups; slot holds ngroups x N^3 doubles.
-// rho3 classes a, b must be zero on entry (class 0 is overwritten).
+// Grid densities: FP64 in the FP64 path; in the mixed path a compensated FP32
+// pair (hi, lo) in the same 8 bytes per point, summed with Knuth's two-sum,
+// so that no per-point FP64 arithmetic or conversion runs (both are slow on
+// this part) while the sums keep about FP64 accuracy.
+template <typename T> struct DensAcc;
+template <> struct DensAcc<double> {
+    using S = double;
+    __host__ __device__ static S make(double v) { return v; }
+    __host__ __device__ static S add(S a, double v) { return a + v; }
+    __host__ __device__ static S add2(S a, S b) { return a + b; }
+    __host__ __device__ static double value(S a) { return a; }
+};
+template <> struct DensAcc<float> {
+    using S = float2;
+    __host__ __device__ static S make(float v) { return make_float2(v, 0.f); }
+    __host__ __device__ static S add(S a, float v) {
+        const float t = a.x + v;
+        const float bp = t - a.x;
+        const float err = (a.x - (t - bp)) + (v - bp);
+        return make_float2(t, a.y + err);
+    }
+    __host__ __device__ static S add2(S a, S b) {
+        S r = add(a, b.x);
+        r.y += b.y;
+        return r;
+    }
+    __host__ __device__ static float value(S a) { return a.x + a.y; }
+};
+
+// x stage, inverse: rho3 (3 x N^3 DensAcc<T>::S, in a buffer of doubles) =
+// sum |psi|^2 * scale per class, bands split into up to ngroups groups; slot
+// holds ngroups x N^3 values.  rho3 classes a, b must be zero on entry (class
+// 0 is overwritten).
 constexpr int kDensityGroups = 4;
 template <typename T>
 void band_x_density(const Sphere& s, const c2<T>* tw, const c2<T>* Yp, double* rho3, double* slot, int ngroups,
