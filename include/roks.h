@@ -241,6 +241,49 @@ ROKS_API roks_status roks_profile_read(roks_ctx* ctx, roks_profile_entry* out, i
 ROKS_API roks_status roks_orthonormalize_noalloc(int precision, int npw, int nbands,
                                                  void* psi, int64_t ld, void* cuda_stream);
 
+/* ------------------------------------------------------------------
+ * Learned correction of the TPA preconditioner.  The paper preconditions
+ * the out-of-subspace gradient with the TPA kinetic factor K alone (Eqs.
+ * 16-18); this part multiplies K, per plane wave G and band n, by
+ * m = exp(clip(s, -3, 3)), s the output of a network 3 -> 64 -> 64 -> 1
+ * (tanh) of the features
+ *   u0 = log(1 + (|G|^2/2) / T_n), T_n = sum (|G|^2/2)|g_nG|^2 / sum |g_nG|^2,
+ *   u1 = log(1 + |g_nG| / rms_n),   rms_n = (sum |g_nG|^2 / N_pw)^(1/2),
+ *   u2 = eps_n = Theta_nn / w_n     (band energy, Ha).
+ * Parameters: ROKS_MLP_PARAMS floats, W1 (64 x 3, row major), b1 (64), W2
+ * (64 x 64, row major), b2 (64), w3 (64), b3.  The network is trained with
+ * the three calls below (all device pointers, FP32, stream-ordered, no
+ * synchronisation; ROKS_EINVAL on bad sizes or null pointers). */
+#define ROKS_MLP_PARAMS 4481
+#define ROKS_PRECOND_TPA 0
+#define ROKS_PRECOND_TPA_MLP 1
+
+/* s[i] = network output for the feature rows feats (n x 3, row major);
+ * bf16 != 0 rounds the weights to BF16 first (as the preconditioner does). */
+ROKS_API roks_status roks_mlp_forward(int n, const float* feats, const float* params, int bf16, float* s,
+                                      void* cuda_stream);
+/* Floats of the work buffer roks_mlp_grad needs for n samples. */
+ROKS_API size_t roks_mlp_grad_work(int n);
+/* loss[0] = sum_i w_i (s_i - t_i)^2 / sum_i w_i and grad = d loss / d params
+ * (ROKS_MLP_PARAMS floats), summed in a fixed order (deterministic). */
+ROKS_API roks_status roks_mlp_grad(int n, const float* feats, const float* target, const float* weight,
+                                   const float* params, float* work, float* grad, float* loss, void* cuda_stream);
+/* One Adam step (step counts from 1) on params, with moment buffers m, v
+ * (ROKS_MLP_PARAMS floats each, zero before the first step). */
+ROKS_API roks_status roks_mlp_adam(float* params, float* m, float* v, const float* grad, int step, float lr,
+                                   float beta1, float beta2, float eps, void* cuda_stream);
+/* Selects the preconditioner of roks_pcg_step: ROKS_PRECOND_TPA, or
+ * ROKS_PRECOND_TPA_MLP with params (device, ROKS_MLP_PARAMS floats, copied).
+ * With the correction on, an accepted step that raises the energy or a CG
+ * restart suspends it for three iterations (TPA is the fallback). */
+ROKS_API roks_status roks_set_preconditioner(roks_ctx* ctx, int kind, const float* params);
+/* out = K m grad (the preconditioner in use, before the S-projection of Eq.
+ * 16) for a gradient block (device, npw x nbands, ld), and, when feats is
+ * not NULL, the features of every coefficient (device, npw * nbands rows of
+ * 3, band by band).  eps_n comes from Theta of the last roks_apply_h call
+ * that returned a gradient. */
+ROKS_API roks_status roks_precondition(roks_ctx* ctx, const void* grad, int64_t ld, void* out, float* feats);
+
 /* Text of the last error on this context ("" if none).  Never NULL. */
 ROKS_API const char* roks_last_error(const roks_ctx* ctx);
 

@@ -421,15 +421,21 @@ def tpa_factor(x: np.ndarray) -> np.ndarray:
     return num / (num + 16.0 * x ** 4)
 
 
-def precondition(sys_: System, Psi, SPsi, gI):
-    """p_I = K g_I - sum_m |m><m|S K|g_I> (Eq. 16), K = -(2/X) tpa(x),
-    x = E_kin(G)/X with E_kin(G) = |G|^2 in Rydberg, X_n = 1.5 E_kin(g_nI) (R1)."""
+def tpa_step(sys_: System, gI):
+    """K g_I with K = -(2/X) tpa(x) (Eq. 17), x = E_kin(G)/X with E_kin(G) =
+    |G|^2 in Rydberg and X_n = 1.5 E_kin(g_nI) (Eq. 18 with R1); returns
+    (K g_I, X)."""
     g2ry = sys_.g2
     w = np.abs(gI) ** 2
     X = 1.5 * (g2ry[:, None] * w).sum(axis=0) / np.maximum(w.sum(axis=0), 1e-300)
     x = g2ry[:, None] / X[None, :]
     K = -(2.0 / X)[None, :] * tpa_factor(x)
-    KgI = K * gI
+    return K * gI, X
+
+
+def precondition(sys_: System, Psi, SPsi, gI):
+    """p_I = K g_I - sum_m |m><m|S K|g_I> (Eq. 16) with the TPA step of tpa_step."""
+    KgI, X = tpa_step(sys_, gI)
     pI = KgI - Psi @ (SPsi.conj().T @ KgI)
     return pI, X
 

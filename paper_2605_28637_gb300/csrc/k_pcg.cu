@@ -178,6 +178,10 @@ __global__ void k_pcg_finish(PcgScalars* sc) {
     sc->dt = fmin(fmax(sc->step, 0.05), 2.0);
     sc->pg_prev = sc->pg;
     sc->has_prev = 1.0;
+    // TPA stays the fallback of the learned correction: an accepted step that
+    // raised the energy, or a CG restart, suspends it for three iterations
+    if (sc->Enew > sc->E0 || sc->restarted != 0.0) sc->mlp_off = 3.0;
+    else sc->mlp_off = fmax(sc->mlp_off - 1.0, 0.0);
 }
 
 __global__ void k_set_cur(PcgScalars* sc, int field) {

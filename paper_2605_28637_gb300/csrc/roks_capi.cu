@@ -13,6 +13,7 @@
 #include "../../include/roks.h"
 #include "roks_exx.cuh"
 #include "roks_grid.cuh"
+#include "roks_mlp.cuh"
 
 using namespace roks;
 
@@ -85,6 +86,11 @@ struct roks_ctx {
     const void* cache_psi = nullptr;   // potentials valid for this buffer (pcg chain)
     bool pot_valid = false;
     int n_small = 0;
+    // learned correction of the preconditioner; once its run meets the
+    // convergence criterion, TPA alone continues and must meet it again
+    float* d_mlp = nullptr;
+    int mlp_kind = ROKS_PRECOND_TPA;
+    bool mlp_judging = false;
     // one PCG iteration as a CUDA graph, captured on a private stream the
     // second time in a row the same orbital buffer is stepped, replayed on st
     bool graphs = true;
@@ -465,7 +471,11 @@ struct Impl {
         sum_to(ctx->d_colout, nb, reinterpret_cast<double*>(ctx->d_sc) + SC_FIELD(gnorm2), 1.0, st);
         // p_I = K g_I - Psi (S Psi)^H K g_I
         column_sums<T>(1, npw, nb, ccv(ctx->W_gI), l, nullptr, 0, static_cast<const T*>(ctx->d_g2half), ctx->d_colpart, ctx->d_colout, st);
-        precondition<T>(npw, nb, ccv(ctx->W_gI), l, static_cast<const T*>(ctx->d_g2half), ctx->d_colout, cv(ctx->W_K), l, st);
+        if (ctx->mlp_kind == ROKS_PRECOND_TPA_MLP)
+            precondition_mlp<T>(npw, nb, ccv(ctx->W_gI), l, static_cast<const T*>(ctx->d_g2half), ctx->d_colout,
+                                ctx->d_Th, ctx->d_wband, ctx->d_mlp, ctx->d_sc, cv(ctx->W_K), l, st);
+        else
+            precondition<T>(npw, nb, ccv(ctx->W_gI), l, static_cast<const T*>(ctx->d_g2half), ctx->d_colout, cv(ctx->W_K), l, st);
         }
         project(ctx, psi, ld, ctx->W_K, ctx->W_K);
         dot_to(ctx, ctx->W_K, ctx->W_gI, SC_FIELD(pgI));
@@ -593,6 +603,7 @@ void reset_history(roks_ctx* ctx) {
     ctx->pot_valid = false;
     ctx->cache_psi = nullptr;
     ctx->n_small = 0;
+    ctx->mlp_judging = false;
     cudaStreamSynchronize(ctx->st);
 }
 
@@ -751,6 +762,7 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     AL(ctx->d_wk, rs * 3);
     AL(ctx->d_wband, sizeof(double) * nb);
     AL(ctx->d_vloc, sizeof(double) * N3);
+    AL(ctx->d_mlp, sizeof(float) * ROKS_MLP_PARAMS);
     if (ctx->prec != ROKS_FP64) AL(ctx->d_vloc_t, sizeof(float) * N3);
     AL(ctx->d_P, cs * (size_t)l * (ctx->nproj > 0 ? ctx->nproj : 1));
     AL(ctx->d_blk_off, sizeof(int) * (ctx->nproj + 1));
@@ -1051,6 +1063,19 @@ roks_status roks_pcg_step(roks_ctx* ctx, void* psi, int64_t ld, roks_step_info* 
     if (std::fabs(tmp.E_new - tmp.E) < ctx->e_tol) ctx->n_small += 1;
     else ctx->n_small = 0;
     tmp.converged = ctx->n_small >= 2 ? 1 : 0;
+    if (tmp.converged && ctx->mlp_kind == ROKS_PRECOND_TPA_MLP && !ctx->mlp_judging) {
+        // TPA judges the convergence of the corrected run: switch the
+        // correction off for good (a device flag the captured step reads) and
+        // require the criterion again with TPA steps
+        const double off = 1e30;
+        const size_t at = offsetof(PcgScalars, mlp_off);
+        CK(cudaMemcpyAsync(reinterpret_cast<char*>(ctx->d_sc) + at, &off, sizeof(double), cudaMemcpyHostToDevice,
+                           ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        ctx->mlp_judging = true;
+        ctx->n_small = 0;
+        tmp.converged = 0;
+    }
     if (info) *info = tmp;
     return r;
 }
@@ -1098,6 +1123,84 @@ roks_status roks_profile_read(roks_ctx* ctx, roks_profile_entry* out, int cap, i
     }
     ++n;
     if (count) *count = n;
+    return ROKS_OK;
+}
+
+roks_status roks_mlp_forward(int n, const float* feats, const float* params, int bf16, float* s, void* stream) {
+    if (n < 0 || (n > 0 && (!feats || !params || !s))) return ROKS_EINVAL;
+    mlp_forward(n, feats, params, bf16 != 0, s, static_cast<cudaStream_t>(stream));
+    return cudaGetLastError() == cudaSuccess ? ROKS_OK : ROKS_ECUDA;
+}
+
+size_t roks_mlp_grad_work(int n) { return n > 0 ? mlp_grad_work_floats(n) : 0; }
+
+roks_status roks_mlp_grad(int n, const float* feats, const float* target, const float* weight, const float* params,
+                          float* work, float* grad, float* loss, void* stream) {
+    if (n <= 0 || !feats || !target || !weight || !params || !work || !grad) return ROKS_EINVAL;
+    mlp_grad(n, feats, target, weight, params, work, grad, loss, static_cast<cudaStream_t>(stream));
+    return cudaGetLastError() == cudaSuccess ? ROKS_OK : ROKS_ECUDA;
+}
+
+roks_status roks_mlp_adam(float* params, float* m, float* v, const float* grad, int step, float lr, float beta1,
+                          float beta2, float eps, void* stream) {
+    if (!params || !m || !v || !grad || step < 1 || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f))
+        return ROKS_EINVAL;
+    mlp_adam(params, m, v, grad, step, lr, beta1, beta2, eps, static_cast<cudaStream_t>(stream));
+    return cudaGetLastError() == cudaSuccess ? ROKS_OK : ROKS_ECUDA;
+}
+
+roks_status roks_set_preconditioner(roks_ctx* ctx, int kind, const float* params) {
+    if (!ctx) return ROKS_EINVAL;
+    if (kind != ROKS_PRECOND_TPA && kind != ROKS_PRECOND_TPA_MLP)
+        return fail(ctx, ROKS_EINVAL, "unknown preconditioner kind");
+    if (kind == ROKS_PRECOND_TPA_MLP) {
+        if (!params) return fail(ctx, ROKS_EINVAL, "null network parameters");
+        CK(cudaMemcpyAsync(ctx->d_mlp, params, sizeof(float) * ROKS_MLP_PARAMS, cudaMemcpyDeviceToDevice, ctx->st));
+    }
+    if (kind != ctx->mlp_kind && ctx->pcg_exec) {
+        // the captured iteration launches the other preconditioner: capture again
+        CK(cudaStreamSynchronize(ctx->st));
+        cudaGraphExecDestroy(ctx->pcg_exec);
+        ctx->pcg_exec = nullptr;
+        ctx->graph_psi = nullptr;
+    }
+    ctx->mlp_kind = kind;
+    return ROKS_OK;
+}
+
+roks_status roks_precondition(roks_ctx* ctx, const void* grad, int64_t ld, void* out, float* feats) {
+    if (!ctx) return ROKS_EINVAL;
+    if (!grad || !out || ld < ctx->npw) return fail(ctx, ROKS_EINVAL, "bad gradient or output");
+    const int npw = ctx->npw, nb = ctx->nb;
+    cudaStream_t st = ctx->st;
+    if (ctx->prec == ROKS_FP64) {
+        using T = double;
+        const auto* g = static_cast<const double2*>(grad);
+        column_sums<T>(1, npw, nb, g, ld, nullptr, 0, static_cast<const T*>(ctx->d_g2half), ctx->d_colpart,
+                       ctx->d_colout, st);
+        if (feats) mlp_features<T>(npw, nb, g, ld, static_cast<const T*>(ctx->d_g2half), ctx->d_colout, ctx->d_Th,
+                                   ctx->d_wband, feats, st);
+        if (ctx->mlp_kind == ROKS_PRECOND_TPA_MLP)
+            precondition_mlp<T>(npw, nb, g, ld, static_cast<const T*>(ctx->d_g2half), ctx->d_colout, ctx->d_Th,
+                                ctx->d_wband, ctx->d_mlp, nullptr, static_cast<double2*>(out), ld, st);
+        else
+            precondition<T>(npw, nb, g, ld, static_cast<const T*>(ctx->d_g2half), ctx->d_colout,
+                            static_cast<double2*>(out), ld, st);
+    } else {
+        using T = float;
+        const auto* g = static_cast<const float2*>(grad);
+        column_sums<T>(1, npw, nb, g, ld, nullptr, 0, static_cast<const T*>(ctx->d_g2half), ctx->d_colpart,
+                       ctx->d_colout, st);
+        if (feats) mlp_features<T>(npw, nb, g, ld, static_cast<const T*>(ctx->d_g2half), ctx->d_colout, ctx->d_Th,
+                                   ctx->d_wband, feats, st);
+        if (ctx->mlp_kind == ROKS_PRECOND_TPA_MLP)
+            precondition_mlp<T>(npw, nb, g, ld, static_cast<const T*>(ctx->d_g2half), ctx->d_colout, ctx->d_Th,
+                                ctx->d_wband, ctx->d_mlp, nullptr, static_cast<float2*>(out), ld, st);
+        else
+            precondition<T>(npw, nb, g, ld, static_cast<const T*>(ctx->d_g2half), ctx->d_colout,
+                            static_cast<float2*>(out), ld, st);
+    }
+    CK(cudaGetLastError());
     return ROKS_OK;
 }
 

@@ -79,6 +79,7 @@ struct PcgScalars {
     double gnorm2;
     double coup_re, coup_im;
     double neg_one;           // constant -1 for device-scaled axpy
+    double mlp_off;           // iterations left with the learned correction suspended
 };
 
 // Gam = (Theta + Theta^H)/2, Gin = Theta - Theta^H, R (Eq. 20) -> A (Eqs. 22-23),

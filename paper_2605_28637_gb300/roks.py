@@ -70,7 +70,12 @@ class roks_profile_entry(C.Structure):
 
 EXPORTS = ["roks_setup", "roks_basis", "roks_init_orbitals", "roks_density", "roks_potential", "roks_apply_h",
            "roks_orthonormalize", "roks_pcg_step", "roks_energies_get", "roks_profile_enable", "roks_profile_read",
-           "roks_orthonormalize_noalloc", "roks_last_error", "roks_destroy"]
+           "roks_orthonormalize_noalloc", "roks_mlp_forward", "roks_mlp_grad", "roks_mlp_adam",
+           "roks_set_preconditioner", "roks_precondition", "roks_mlp_grad_work", "roks_last_error", "roks_destroy"]
+
+ROKS_MLP_PARAMS = 4481
+ROKS_PRECOND_TPA = 0
+ROKS_PRECOND_TPA_MLP = 1
 
 _lib = None
 
@@ -101,11 +106,18 @@ def load(path: str | None = None) -> C.CDLL:
     lib.roks_profile_enable.argtypes = [P, C.c_int]
     lib.roks_profile_read.argtypes = [P, C.POINTER(roks_profile_entry), C.c_int, C.POINTER(C.c_int)]
     lib.roks_orthonormalize_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, P, C.c_int64, P]
+    lib.roks_mlp_forward.argtypes = [C.c_int, P, P, C.c_int, P, P]
+    lib.roks_mlp_grad.argtypes = [C.c_int, P, P, P, P, P, P, P, P]
+    lib.roks_mlp_adam.argtypes = [P, P, P, P, C.c_int, C.c_float, C.c_float, C.c_float, C.c_float, P]
+    lib.roks_set_preconditioner.argtypes = [P, C.c_int, P]
+    lib.roks_precondition.argtypes = [P, P, C.c_int64, P, P]
+    lib.roks_mlp_grad_work.argtypes = [C.c_int]
+    lib.roks_mlp_grad_work.restype = C.c_size_t
     lib.roks_last_error.argtypes = [P]
     lib.roks_last_error.restype = C.c_char_p
     lib.roks_destroy.argtypes = [P]
     lib.roks_destroy.restype = None
-    for name in EXPORTS[:-2]:
+    for name in EXPORTS[:-3]:
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -218,6 +230,44 @@ def roks_orthonormalize_noalloc(precision: int, npw: int, nbands: int, psi, ld: 
         raise RoksError(status, "roks_orthonormalize_noalloc")
 
 
+def _st(stream):
+    return C.c_void_p(stream) if stream else None
+
+
+def roks_mlp_forward(n: int, feats, params, bf16: bool, s, stream=None):
+    """Network outputs for n feature rows (device float32 tensors)."""
+    status = load().roks_mlp_forward(int(n), _ptr(feats), _ptr(params), int(bool(bf16)), _ptr(s), _st(stream))
+    if status != ROKS_OK:
+        raise RoksError(status, "roks_mlp_forward")
+
+
+def roks_mlp_grad_work(n: int) -> int:
+    return int(load().roks_mlp_grad_work(int(n)))
+
+
+def roks_mlp_grad(n: int, feats, target, weight, params, work, grad, loss, stream=None):
+    status = load().roks_mlp_grad(int(n), _ptr(feats), _ptr(target), _ptr(weight), _ptr(params), _ptr(work),
+                                  _ptr(grad), _ptr(loss), _st(stream))
+    if status != ROKS_OK:
+        raise RoksError(status, "roks_mlp_grad")
+
+
+def roks_mlp_adam(params, m, v, grad, step: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+                  eps: float = 1e-8, stream=None):
+    status = load().roks_mlp_adam(_ptr(params), _ptr(m), _ptr(v), _ptr(grad), int(step), float(lr), float(beta1),
+                                  float(beta2), float(eps), _st(stream))
+    if status != ROKS_OK:
+        raise RoksError(status, "roks_mlp_adam")
+
+
+def roks_set_preconditioner(ctx, kind: int, params=None):
+    _check(ctx, load().roks_set_preconditioner(ctx, int(kind), _ptr(params)))
+
+
+def roks_precondition(ctx, grad, ld: int, out, feats=None):
+    _check(ctx, load().roks_precondition(ctx, _ptr(grad), int(ld), _ptr(out), _ptr(feats)))
+
+
 def roks_last_error(ctx) -> str:
     return load().roks_last_error(ctx).decode()
 
@@ -277,6 +327,21 @@ class Context:
 
     def energies(self):
         return roks_energies_get(self.ctx)
+
+    def set_preconditioner(self, params=None):
+        """TPA (params None) or TPA times the network (device float32 params)."""
+        if params is None:
+            roks_set_preconditioner(self.ctx, ROKS_PRECOND_TPA, None)
+        else:
+            roks_set_preconditioner(self.ctx, ROKS_PRECOND_TPA_MLP, params)
+
+    def precondition(self, grad, want_feats=False):
+        """K m grad and optionally the features (npw * nb, 3)."""
+        out = self.new_bands()
+        feats = (self.torch.empty((self.nb * self.npw, 3), dtype=self.torch.float32, device="cuda")
+                 if want_feats else None)
+        roks_precondition(self.ctx, grad, self.ld, out, feats)
+        return out, feats
 
     def close(self):
         if self.ctx:

@@ -194,3 +194,21 @@ def random_vectors(seed: int, npw: int, nb: int) -> np.ndarray:
     """Complex Uniform(-1,1)+iUniform(-1,1) block (npw, nb) for test probes."""
     u = uniform(seed * 0x2545F491 + 0x77, 0, npw * nb * 2, -1.0, 1.0).reshape(nb, npw, 2)
     return (u[..., 0] + 1j * u[..., 1]).T.copy()
+
+
+MLP_HIDDEN = 64
+MLP_NPARAM = MLP_HIDDEN * 3 + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN + 1
+
+
+def mlp_initial_params(seed: int) -> np.ndarray:
+    """Initial weights of the preconditioner network (flat, float32): W1 and
+    W2 uniform(-1, 1) scaled by 1/sqrt(fan-in), zero biases, zero output
+    layer (so the untrained correction is the identity).  Layout: W1 (64 x 3,
+    row major), b1, W2 (64 x 64, row major), b2, w3, b3."""
+    st = _Stream(seed * 0x100000001 + 0x4D4C50)
+    H = MLP_HIDDEN
+    W1 = st.take(H * 3, -1.0, 1.0) / np.sqrt(3.0)
+    W2 = st.take(H * H, -1.0, 1.0) / np.sqrt(float(H))
+    p = np.concatenate([W1, np.zeros(H), W2, np.zeros(H), np.zeros(H), [0.0]])
+    return p.astype(np.float32)
+
