@@ -183,11 +183,12 @@ __device__ __forceinline__ void load_x_lines(const Sphere& s, c2<T>* buf, const 
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(kThreads) k_band_x_apply(Sphere s, const c2<T>* __restrict__ tw,
-                                                           c2<T>* __restrict__ Yp,
-                                                           const T* __restrict__ Vk,
-                                                           const c2<T>* __restrict__ Xx, int b0,
-                                                           int n_closed, T scale) {
+__global__ void __launch_bounds__(x_threads(N)) k_band_x_apply(Sphere s, const c2<T>* __restrict__ tw,
+                                                               c2<T>* __restrict__ Yp,
+                                                               const T* __restrict__ Vk,
+                                                               const c2<T>* __restrict__ Xx, int b0,
+                                                               int n_closed, T scale) {
+    constexpr int NT = x_threads(N);
     using V = c2<T>;
     constexpr int TL = tile_lines(N), LS = TL + 1;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -200,25 +201,26 @@ __global__ void __launch_bounds__(kThreads) k_band_x_apply(Sphere s, const c2<T>
     const int bb = blockIdx.z;
     const int b = b0 + bb;
     const int cls = b < n_closed ? 0 : b - n_closed + 1;
-    V* Ypb = Yp + (int64_t)bb * s.np * N * N;
-    const T* Vc = Vk + (int64_t)cls * N * N * N;
-    const c2<T>* Xb = Xx ? Xx + (int64_t)b * N * N * N : nullptr;
+    // offsets within one band's planes and within one N^3 grid fit in 32 bits
+    V* Ypb = Yp + (int64_t)bb * s.np * N * N + y * N + z0;
+    const T* Vc = Vk + (int64_t)cls * N * N * N + y * N + z0;
+    const c2<T>* Xb = Xx ? Xx + (int64_t)b * N * N * N + y * N + z0 : nullptr;
     const int nmax = s.nmax;
+    constexpr int NN = N * N;
     // inverse x transform; the last pass forms (V psi + X) * scale in the tile,
     // X being the exchange field of the band (absent without exact exchange)
-    fft_io<V, N, +1, TL, LS, kThreads, false, true>(
+    fft_io<V, N, +1, TL, LS, NT, false, true>(
         buf, tws,
         [&](int line, int e) {
-            const int z = z0 + line, i = signed_freq(e, N);
-            return (z < N && i >= -nmax && i <= nmax) ? Ypb[((int64_t)(i + nmax) * N + y) * N + z]
-                                                      : mk<T>(T(0), T(0));
+            const int i = signed_freq(e, N);
+            return (z0 + line < N && i >= -nmax && i <= nmax) ? Ypb[(i + nmax) * NN + line] : mk<T>(T(0), T(0));
         },
         [&](int line, int e, V v, int, int) {
-            const int z = z0 + line;
-            const int64_t gi = ((int64_t)e * N + y) * N + z;
-            const T w = (z < N) ? Vc[gi] * scale : T(0);
+            const bool in = z0 + line < N;
+            const int gi = e * NN + line;
+            const T w = in ? Vc[gi] * scale : T(0);
             V o = mk<T>(v.x * w, v.y * w);
-            if (Xb && z < N) {
+            if (Xb && in) {
                 const V xv = Xb[gi];
                 o.x += xv.x * scale;
                 o.y += xv.y * scale;
@@ -227,11 +229,11 @@ __global__ void __launch_bounds__(kThreads) k_band_x_apply(Sphere s, const c2<T>
         });
     __syncthreads();
     // forward x transform; the last pass keeps the planes of the sphere
-    fft_io<V, N, -1, TL, LS, kThreads, true, false>(
+    fft_io<V, N, -1, TL, LS, NT, true, false>(
         buf, tws, [&](int line, int e) { return buf[e * LS + line]; },
         [&](int line, int e, V v, int, int) {
-            const int z = z0 + line, i = signed_freq(e, N);
-            if (z < N && i >= -nmax && i <= nmax) Ypb[((int64_t)(i + nmax) * N + y) * N + z] = v;
+            const int i = signed_freq(e, N);
+            if (z0 + line < N && i >= -nmax && i <= nmax) Ypb[(i + nmax) * NN + line] = v;
         });
 }
 
@@ -313,13 +315,14 @@ __global__ void __launch_bounds__(kThreads) k_band_x_density(Sphere s, const c2<
                 for (int r = 0; r < R; ++r) part[q][r] = T(0);
             const int chunk_end = min(seg_end, bb + 16);
             for (; bb < chunk_end; ++bb) {
-                const V* Ypb = Yp + (int64_t)bb * s.np * N * N;
+                // offsets within one band's planes fit in 32 bits
+                const V* Ypb = Yp + (int64_t)bb * s.np * N * N + y * N + z0;
                 fft_io<V, N, +1, TL, LS, kThreads, false, false>(
                     buf, tws,
                     [&](int line, int e) {
-                        const int z = z0 + line, i = signed_freq(e, N);
-                        return (z < N && i >= -nmax && i <= nmax) ? Ypb[((int64_t)(i + nmax) * N + y) * N + z]
-                                                                  : mk<T>(T(0), T(0));
+                        const int i = signed_freq(e, N);
+                        return (z0 + line < N && i >= -nmax && i <= nmax) ? Ypb[(i + nmax) * (N * N) + line]
+                                                                          : mk<T>(T(0), T(0));
                     },
                     [&](int, int, V v, int q, int r) { part[q][r] += v.x * v.x + v.y * v.y; });
                 __syncthreads();
@@ -331,7 +334,7 @@ __global__ void __launch_bounds__(kThreads) k_band_x_density(Sphere s, const c2<
                 for (int r = 0; r < R; ++r) {
                     int line = 0, e = 0;
                     if (Slots::point(threadIdx.x, q, r, line, e) && z0 + line < N) {
-                        DS* dst = rr + ((int64_t)e * N + y) * N + z0 + line;
+                        DS* dst = rr + (e * N + y) * N + z0 + line;
                         const T add = part[q][r] * scale;
                         *dst = (cls != 0 || !first) ? DA::add(*dst, add) : DA::make(add);
                     }
@@ -347,7 +350,7 @@ __global__ void __launch_bounds__(kThreads) k_band_x_density(Sphere s, const c2<
             for (int r = 0; r < R; ++r) {
                 int line = 0, e = 0;
                 if (Slots::point(threadIdx.x, q, r, line, e) && z0 + line < N)
-                    slot_g[((int64_t)e * N + y) * N + z0 + line] = DA::make(T(0));
+                    slot_g[(e * N + y) * N + z0 + line] = DA::make(T(0));
             }
     }
 }
@@ -447,7 +450,7 @@ struct BandFft {
                         T scale, cudaStream_t st) {
         set_smem(k_band_x_apply<T, N>, SM);
         dim3 g((N + TL - 1) / TL, N, nbb);
-        roks::count_launch(), k_band_x_apply<T, N><<<g, kThreads, SM, st>>>(s, tw, Yp, Vk, Xx, b0, nc, scale);
+        roks::count_launch(), k_band_x_apply<T, N><<<g, x_threads(N), SM, st>>>(s, tw, Yp, Vk, Xx, b0, nc, scale);
     }
     static void x_inv_full(const Sphere& s, const V* tw, const V* Yp, V* Phi, int b0, int nbb, T scale,
                            cudaStream_t st) {

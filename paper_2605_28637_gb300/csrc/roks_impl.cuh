@@ -18,6 +18,10 @@ __host__ __device__ constexpr int tile_lines(int n) {
     return n == 16 ? 16 : (n == 32 || n == 96) ? 32 : 24;
 }
 constexpr int kThreads = 256;
+// Threads of the x-stage apply: for N = 96 (radix 12 then 8 over 32 lines:
+// 256 and 384 butterflies) 128 threads take 2 and 3 butterflies each with
+// none idle; other lengths keep kThreads.
+__host__ __device__ constexpr int x_threads(int n) { return n == 96 ? 128 : kThreads; }
 
 // The plane-wave sphere seen from the grid.  Basis order is i, j, k
 // ascending, so the coefficients of one (i, j) column are contiguous with
