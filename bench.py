@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="organic-96")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--converge-iters", type=int, default=400,
+    ap.add_argument("--converge-iters", type=int, default=2000,
                     help="iteration cap of the time-to-convergence runs (0 skips them)")
     ap.add_argument("--converge-seconds", type=float, default=60.0,
                     help="wall-clock cap of each time-to-convergence run")
@@ -264,11 +264,15 @@ def time_pcg(ctx, psi, steps, torch, profile=False):
     return e0.elapsed_time(e1), infos, prof
 
 
-def converge(cfg, precision, cap, torch, max_seconds):
+def converge(cfg, precision, cap, torch, max_seconds, params=None):
     """Seconds and iterations of PCG from the seeded start to |dE| < 1e-6 Ha
-    twice, stopped after cap iterations or max_seconds of wall clock."""
+    twice, stopped after cap iterations or max_seconds of wall clock; with
+    params, the TPA step is corrected by the trained network (TPA judges the
+    last steps)."""
     from paper_2605_28637_gb300 import roks, synthetic as syn
     ctx = roks.Context(cfg, precision, e_tol=1e-6)
+    if params is not None:
+        ctx.set_preconditioner(params)
     psi = ctx.init_orbitals(syn.orbital_uniforms(cfg, ctx.npw))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -280,9 +284,27 @@ def converge(cfg, precision, cap, torch, max_seconds):
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     out = {"seconds": dt, "iterations": it, "converged": bool(info and info["converged"]),
-           "E_final": info["E_new"] if info else None, "s_per_iter": dt / max(it, 1)}
+           "E_final": info["E_new"] if info else None, "grad_norm_final": info["grad_norm"] if info else None,
+           "s_per_iter": dt / max(it, 1)}
     ctx.close()
     return out
+
+
+def train_network(torch):
+    """The preconditioner network trained on seeded tiny systems (singlet and
+    closed shell, seeds 1-8), on the GPU; returns (device params, seconds, losses)."""
+    import numpy as np
+    from paper_2605_28637_gb300 import learned, synthetic as syn
+    t0 = time.perf_counter()
+    Us, ts, ws = [], [], []
+    for seed in range(1, 9):
+        c = syn.make_config("tiny-16", seed)
+        for cfg in (c, syn.with_changes(c, mode=0, n_closed=5)):
+            U, t, w = learned.make_pairs(cfg)
+            Us.append(U); ts.append(t); ws.append(w)
+    params, losses = learned.train(np.concatenate(Us), np.concatenate(ts), np.concatenate(ws), steps=1500, lr=2e-3)
+    torch.cuda.synchronize()
+    return params, time.perf_counter() - t0, losses
 
 
 def run_gpu(args):
@@ -382,12 +404,20 @@ def run_gpu(args):
     # ---- time to convergence: chosen (mixed) vs plain FP64
     pcg = None
     if args.converge_iters > 0 and rank == 0:
+        params, t_train, losses = train_network(torch)
         mixed = converge(cfg, "mixed", args.converge_iters, torch, args.converge_seconds)
+        mixed_mlp = converge(cfg, "mixed", args.converge_iters, torch, args.converge_seconds, params)
         fp64 = converge(cfg, "fp64", args.converge_iters, torch, args.converge_seconds)
-        pcg = {"mixed": mixed, "fp64": fp64,
-               "speedup_s_per_iter": fp64["s_per_iter"] / mixed["s_per_iter"],
-               "dE_mixed_vs_fp64_final": (mixed["E_final"] - fp64["E_final"])
-               if mixed["E_final"] is not None and fp64["E_final"] is not None else None}
+        for leg in (mixed, mixed_mlp):
+            leg["dE_vs_fp64_final"] = (leg["E_final"] - fp64["E_final"]
+                                       if leg["E_final"] is not None and fp64["E_final"] is not None else None)
+            leg["same_state_as_fp64"] = leg["dE_vs_fp64_final"] is not None and abs(leg["dE_vs_fp64_final"]) < 1e-5
+        pcg = {"criterion": "|E_i+1 - E_i| < 1e-6 Ha on two consecutive iterations",
+               "mixed_tpa": mixed, "mixed_tpa_network": mixed_mlp, "fp64_tpa": fp64,
+               "network": {"trained_on": "tiny-16 seeds 1-8, singlet and closed shell", "train_seconds": t_train,
+                           "loss_first": losses[0], "loss_last": losses[-1]},
+               "speedup_s_per_iter_mixed_vs_fp64": fp64["s_per_iter"] / mixed["s_per_iter"],
+               "note": "seconds to convergence compare only between legs with same_state_as_fp64"}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, dt, desc = oracle_sample(cfg, n_bands_timed=4)

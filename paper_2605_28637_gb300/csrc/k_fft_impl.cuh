@@ -291,14 +291,30 @@ __global__ void __launch_bounds__(kThreads) k_band_x_density(Sphere s, const c2<
     extern __shared__ __align__(16) unsigned char smem[];
     V* buf = reinterpret_cast<V*>(smem);
     V* tws = buf + N * LS;
+    V* stg = tws + N;   // two staging buffers of np x TL (planes x lines) for the next band
     load_twiddles<V, N>(tws, tw);
-    __syncthreads();
     const int z0 = blockIdx.x * TL;
     const int y = blockIdx.y;
     const int g = blockIdx.z;
     const int N3 = N * N * N;
-    const int nmax = s.nmax;
+    const int nmax = s.nmax, np = s.np;
     const int gbeg = g * gs, gend = min(nbb, gbeg + gs);
+    // rows of TL lines are 16-byte aligned in both memories (N even, TL a
+    // multiple of 16): copy them with 16-byte cp.async
+    constexpr int CH = TL * (int)sizeof(V) / 16;   // 16-byte chunks per row
+    auto stage = [&](int band, int which) {
+        const char* src = reinterpret_cast<const char*>(Yp + (int64_t)band * np * N * N + y * N + z0);
+        char* dst = reinterpret_cast<char*>(stg + which * np * TL);
+        for (int c = threadIdx.x; c < np * CH; c += blockDim.x) {
+            const int row = c / CH, k = c - row * CH;
+            const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst + row * TL * sizeof(V) + 16 * k));
+            const char* sp = src + (int64_t)row * N * N * sizeof(V) + 16 * k;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(sp) : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if (gbeg < gend) stage(gbeg, 0);
+    __syncthreads();
     DS* slot_g = slot + (int64_t)g * N3;
     bool slot_written = false;
     int bb = gbeg;
@@ -315,14 +331,20 @@ __global__ void __launch_bounds__(kThreads) k_band_x_density(Sphere s, const c2<
                 for (int r = 0; r < R; ++r) part[q][r] = T(0);
             const int chunk_end = min(seg_end, bb + 16);
             for (; bb < chunk_end; ++bb) {
-                // offsets within one band's planes fit in 32 bits
-                const V* Ypb = Yp + (int64_t)bb * s.np * N * N + y * N + z0;
+                // the next band's planes stream in while this one is transformed
+                if (bb + 1 < gend) {
+                    stage(bb + 1, (bb + 1 - gbeg) & 1);
+                    asm volatile("cp.async.wait_group 1;" ::: "memory");
+                } else {
+                    asm volatile("cp.async.wait_group 0;" ::: "memory");
+                }
+                __syncthreads();
+                const V* sb = stg + ((bb - gbeg) & 1) * np * TL;
                 fft_io<V, N, +1, TL, LS, kThreads, false, false>(
                     buf, tws,
                     [&](int line, int e) {
                         const int i = signed_freq(e, N);
-                        return (z0 + line < N && i >= -nmax && i <= nmax) ? Ypb[(i + nmax) * (N * N) + line]
-                                                                          : mk<T>(T(0), T(0));
+                        return (i >= -nmax && i <= nmax) ? sb[(i + nmax) * TL + line] : mk<T>(T(0), T(0));
                     },
                     [&](int, int, V v, int q, int r) { part[q][r] += v.x * v.x + v.y * v.y; });
                 __syncthreads();
@@ -471,14 +493,16 @@ struct BandFft {
     }
     static void x_density(const Sphere& s, const V* tw, const V* Yp, double* rho3, double* slot, int ngroups,
                           int b0, int nbb, int nc, double scale, cudaStream_t st) {
-        set_smem(k_band_x_density<T, N>, SM);
+        // tile, twiddles and two staging buffers of np x TL
+        const size_t sm = SM + 2 * sizeof(V) * (size_t)s.np * TL;
+        set_smem(k_band_x_density<T, N>, sm);
         const int gs = (nbb + ngroups - 1) / ngroups;
         const int ng = (nbb + gs - 1) / gs;
         dim3 g((N + TL - 1) / TL, N, ng);
         using DS = typename DensAcc<T>::S;
         DS* r3 = reinterpret_cast<DS*>(rho3);
         DS* sl = reinterpret_cast<DS*>(slot);
-        roks::count_launch(), k_band_x_density<T, N><<<g, kThreads, SM, st>>>(s, tw, Yp, r3, sl, b0, nbb, gs, nc,
+        roks::count_launch(), k_band_x_density<T, N><<<g, kThreads, sm, st>>>(s, tw, Yp, r3, sl, b0, nbb, gs, nc,
                                                                             T(scale));
         const int N3 = N * N * N;
         roks::count_launch(), k_density_reduce<T><<<(unsigned)((N3 + 255) / 256), 256, 0, st>>>(N3, ng, sl, r3);
