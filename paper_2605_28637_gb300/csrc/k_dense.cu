@@ -75,12 +75,12 @@ template <int R> __host__ __device__ constexpr int padstride() { return (16 * pa
 template <typename T> struct CnTile { static constexpr int KT = sizeof(T) == 4 ? 32 : 16; };
 
 template <typename T, int RM, int RN>
-__global__ void __launch_bounds__(256) k_gemm_cn(int M, int N, int K, int kchunk, int TY, int TX,
+__global__ void __launch_bounds__(256) k_gemm_cn(int M, int N, int K, int kchunk, int TY, int TX, int SA, int SB,
                                                  const c2<T>* __restrict__ A, int64_t lda,
                                                  const c2<T>* __restrict__ B, int64_t ldb, c2<T>* __restrict__ part) {
+    // SA, SB: odd row strides of the k slices, at least TY (TX) padded row groups
     using V = c2<T>;
     constexpr int KT = CnTile<T>::KT;
-    constexpr int SA = padstride<RM>(), SB = padstride<RN>();
     extern __shared__ __align__(16) unsigned char cn_smem[];
     V* As = reinterpret_cast<V*>(cn_smem);   // [2][KT][SA]
     V* Bs = As + 2 * KT * SA;                // [2][KT][SB]
@@ -129,9 +129,11 @@ __global__ void __launch_bounds__(256) k_gemm_cn(int M, int N, int K, int kchunk
         for (int kk = 0; kk < KT; ++kk) {
             V a[RM], b[RN];
 #pragma unroll
-            for (int i = 0; i < RM; ++i) a[i] = as[kk * SA + i];
+            for (int i = 0; i < RM; ++i) a[i] = as[i];
 #pragma unroll
-            for (int j = 0; j < RN; ++j) b[j] = bs[kk * SB + j];
+            for (int j = 0; j < RN; ++j) b[j] = bs[j];
+            as += SA;
+            bs += SB;
 #pragma unroll
             for (int i = 0; i < RM; ++i)
 #pragma unroll
@@ -235,56 +237,94 @@ int sm_count() {
     return n;
 }
 
+// register-tile shapes: all of 1..4 x 1..4, and with 6 in FP32 only
+#define CN_TILES4(X) X(1, 1) X(1, 2) X(1, 3) X(1, 4) X(2, 1) X(2, 2) X(2, 3) X(2, 4) \
+                     X(3, 1) X(3, 2) X(3, 3) X(3, 4) X(4, 1) X(4, 2) X(4, 3) X(4, 4)
+#define CN_TILES6(X) X(1, 6) X(2, 6) X(3, 6) X(4, 6) X(6, 1) X(6, 2) X(6, 3) X(6, 4) X(6, 6)
+
+constexpr int padgroup_rt(int r) { return (r % 2 == 0) ? r + 1 : r; }
+
+// odd row strides of the k slices for a thread grid, and the dynamic
+// shared memory of a launch (two slices of A and B, or the output tile)
+template <typename T>
+void cn_layout(const CnPlan& p, int& SA, int& SB, size_t& smem) {
+    constexpr int KT = CnTile<T>::KT;
+    SA = (p.ty * padgroup_rt(p.rm)) | 1;
+    SB = (p.tx * padgroup_rt(p.rn)) | 1;
+    const size_t slices = (size_t)2 * KT * (SA + SB);
+    const size_t tile = (size_t)p.ty * p.rm * p.tx * p.rn;
+    smem = sizeof(c2<T>) * (slices > tile ? slices : tile);
+}
+
 template <typename T, int RM, int RN>
-size_t cn_smem() {
-    return sizeof(c2<T>) * 2 * CnTile<T>::KT * (padstride<RM>() + padstride<RN>());
+size_t cn_smem_max() {
+    constexpr int KT = CnTile<T>::KT;
+    const size_t slices = (size_t)2 * KT * (padstride<RM>() + padstride<RN>());
+    const size_t tile = (size_t)16 * RM * 16 * RN;
+    return sizeof(c2<T>) * (slices > tile ? slices : tile);
+}
+
+template <typename T, int RM, int RN>
+void cn_attr() {
+    static bool done = false;
+    if (!done) {
+        cudaFuncSetAttribute(k_gemm_cn<T, RM, RN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cn_smem_max<T, RM, RN>());
+        done = true;
+    }
 }
 
 // Blocks of the chosen contraction kernel resident on one SM (occupancy API),
 // so that the split-K grid fills whole waves of the GPU.
 template <typename T>
-int cn_resident_blocks(int rm, int rn, int threads) {
-    // cached per (tile, block size): the first call of each shape queries
+int cn_resident_blocks(int rm, int rn, int threads, size_t smem) {
+    // cached per (tile, block size, shared memory): the first call of each shape queries
     struct Ent {
-        int rm, rn, threads, nb;
+        int rm, rn, threads;
+        size_t smem;
+        int nb;
     };
     static std::vector<Ent> cache;
     static std::mutex mu;
     {
         std::lock_guard<std::mutex> g(mu);
         for (const Ent& c : cache)
-            if (c.rm == rm && c.rn == rn && c.threads == threads) return c.nb;
+            if (c.rm == rm && c.rn == rn && c.threads == threads && c.smem == smem) return c.nb;
     }
     int nb = 0;
     cudaError_t e = cudaErrorInvalidValue;
-#define CN_OCC(RM_, RN_)                                                                                        \
-    if (rm == RM_ && rn == RN_) {                                                                             \
-        const size_t sm = cn_smem<T, RM_, RN_>();                                                             \
-        cudaFuncSetAttribute(k_gemm_cn<T, RM_, RN_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);    \
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gemm_cn<T, RM_, RN_>, threads, sm);          \
+#define CN_OCC(RM_, RN_)                                                                              \
+    if (rm == RM_ && rn == RN_) {                                                                   \
+        cn_attr<T, RM_, RN_>();                                                                     \
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gemm_cn<T, RM_, RN_>, threads, smem); \
     }
-    CN_OCC(1, 1) CN_OCC(1, 2) CN_OCC(1, 3) CN_OCC(1, 4) CN_OCC(2, 1) CN_OCC(2, 2) CN_OCC(2, 3) CN_OCC(2, 4)
-    CN_OCC(3, 1) CN_OCC(3, 2) CN_OCC(3, 3) CN_OCC(3, 4) CN_OCC(4, 1) CN_OCC(4, 2) CN_OCC(4, 3) CN_OCC(4, 4)
+    CN_TILES4(CN_OCC)
+    if constexpr (sizeof(T) == 4) { CN_TILES6(CN_OCC) }
 #undef CN_OCC
     if (e != cudaSuccess || nb < 1) {
         cudaGetLastError();
         nb = 2;
     }
     std::lock_guard<std::mutex> g(mu);
-    cache.push_back(Ent{rm, rn, threads, nb});
+    cache.push_back(Ent{rm, rn, threads, smem, nb});
     return nb;
 }
 
 // Register tile and thread grid with the least padded work (plus the
-// shared-memory loads per multiply-add), then K chunks for about two blocks
-// per SM, each at least two K slices long.
+// shared-memory loads per multiply-add), then K chunks for whole waves of
+// resident blocks, each at least two K slices long.
 template <typename T>
 CnPlan cn_plan(int M, int N, int K, int max_chunks) {
     constexpr int KT = CnTile<T>::KT;
     CnPlan best{};
     double best_cost = 1e300;
-    for (int rm = 1; rm <= 4; ++rm)
-        for (int rn = 1; rn <= 4; ++rn) {
+    // register tiles up to 4 x 4 (6-wide tiles, compiled for FP32, measured no
+    // faster on these shapes: the kernel is issue-bound at any tile size)
+    const int rcand[5] = {1, 2, 3, 4, 6};
+    const int nc = 4;
+    for (int ia = 0; ia < nc; ++ia)
+        for (int ib = 0; ib < nc; ++ib) {
+            const int rm = rcand[ia], rn = rcand[ib];
             const int mt = (M + 16 * rm - 1) / (16 * rm), nt = (N + 16 * rn - 1) / (16 * rn);
             const int ty = (M + mt * rm - 1) / (mt * rm), tx = (N + nt * rn - 1) / (nt * rn);
             const double covered = (double)mt * ty * rm * nt * tx * rn;
@@ -296,7 +336,10 @@ CnPlan cn_plan(int M, int N, int K, int max_chunks) {
             }
         }
     const int tiles = best.mt * best.nt;
-    int want = (cn_resident_blocks<T>(best.rm, best.rn, best.ty * best.tx) * sm_count() + tiles - 1) / tiles;
+    int SA = 0, SB = 0;
+    size_t smem = 0;
+    cn_layout<T>(best, SA, SB, smem);
+    int want = (cn_resident_blocks<T>(best.rm, best.rn, best.ty * best.tx, smem) * sm_count() + tiles - 1) / tiles;
     const int by_len = (K + 2 * KT - 1) / (2 * KT);
     if (want > by_len) want = by_len;
     if (max_chunks > 0 && want > max_chunks) want = max_chunks;
@@ -312,15 +355,13 @@ CnPlan cn_plan(int M, int N, int K, int max_chunks) {
 template <typename T, int RM, int RN>
 void launch_cn(const CnPlan& p, int M, int N, int K, const c2<T>* A, int64_t lda, const c2<T>* B, int64_t ldb,
                c2<T>* part, cudaStream_t st) {
-    const size_t smem = cn_smem<T, RM, RN>();
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_gemm_cn<T, RM, RN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    int SA = 0, SB = 0;
+    size_t smem = 0;
+    cn_layout<T>(p, SA, SB, smem);
+    cn_attr<T, RM, RN>();
     dim3 g(p.mt, p.nt, p.nchunk);
     roks::count_launch();
-    k_gemm_cn<T, RM, RN><<<g, p.ty * p.tx, smem, st>>>(M, N, K, p.kchunk, p.ty, p.tx, A, lda, B, ldb, part);
+    k_gemm_cn<T, RM, RN><<<g, p.ty * p.tx, smem, st>>>(M, N, K, p.kchunk, p.ty, p.tx, SA, SB, A, lda, B, ldb, part);
 }
 
 template <typename T>
@@ -332,10 +373,8 @@ void run_cn(const CnPlan& p, int M, int N, int K, const c2<T>* A, int64_t lda, c
     } else {
 #define CN_CASE(RM_, RN_) \
     if (p.rm == RM_ && p.rn == RN_) launch_cn<T, RM_, RN_>(p, M, N, K, A, lda, B, ldb, part, st);
-        CN_CASE(1, 1) CN_CASE(1, 2) CN_CASE(1, 3) CN_CASE(1, 4)
-        CN_CASE(2, 1) CN_CASE(2, 2) CN_CASE(2, 3) CN_CASE(2, 4)
-        CN_CASE(3, 1) CN_CASE(3, 2) CN_CASE(3, 3) CN_CASE(3, 4)
-        CN_CASE(4, 1) CN_CASE(4, 2) CN_CASE(4, 3) CN_CASE(4, 4)
+        CN_TILES4(CN_CASE)
+        if constexpr (sizeof(T) == 4) { CN_TILES6(CN_CASE) }
 #undef CN_CASE
     }
     chunk_sum_t<c2<T>>(M, N, K > 0 ? p.nchunk : 1, part, C, ldc, st);
@@ -391,7 +430,7 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int M, int N, int K, int TY, co
                                                  int64_t lda, const c2<T>* __restrict__ B, int ldb,
                                                  c2<T>* __restrict__ C, int64_t ldc, T alpha, T beta) {
     using V = c2<T>;
-    constexpr int TM = 32 * RM, SBN = 8 * RN;
+    constexpr int TM = 32 * RM, SBN = 8 * RN + 1;   // odd B stride: conflict-free transposed staging
     extern __shared__ __align__(16) unsigned char nn_smem[];
     V* As = reinterpret_cast<V*>(nn_smem);   // [2][NN_KT][TM]
     V* Bs = As + 2 * NN_KT * TM;             // [2][NN_KT][SBN]
@@ -494,7 +533,7 @@ template <typename T, int RN>
 void launch_nn(int M, int N, int K, int ty, int nt, const c2<T>* A, int64_t lda, const c2<T>* B, int ldb, c2<T>* C,
                int64_t ldc, T alpha, T beta, cudaStream_t st) {
     constexpr int RM = 4;
-    const size_t smem = sizeof(c2<T>) * (2 * NN_KT * (32 * RM + 8 * RN) + (size_t)(8 * RN) * (32 * RM));
+    const size_t smem = sizeof(c2<T>) * (2 * NN_KT * (32 * RM + 8 * RN + 1) + (size_t)(8 * RN) * (32 * RM));
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_gemm_nn<T, RM, RN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -75,6 +75,9 @@ struct roks_ctx {
     double* d_expm_info = nullptr;
     void* d_bigwork = nullptr;      // blocked Cholesky / exponential for more than 64 bands
     int* d_flag = nullptr;
+    // pinned host copy of the PCG scalars and the status flag: one round trip per step
+    PcgScalars* h_sc = nullptr;
+    int* h_flag = nullptr;
     PcgScalars* d_sc = nullptr;
     // exact exchange (alpha != 0)
     void *d_Phi = nullptr, *d_Xx = nullptr, *d_exbuf = nullptr, *d_vG = nullptr;
@@ -567,13 +570,20 @@ struct Impl {
         }
         r = pcg_run(ctx, psi, ld);
         if (r != ROKS_OK) return r;
-        r = check_flag(ctx);
-        if (r != ROKS_OK) return r;
+        // scalars and status flag in one round trip (pinned host copies)
+        CK(cudaMemcpyAsync(ctx->h_sc, ctx->d_sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(ctx->h_flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (tc_timeout_take())
+            return fail(ctx, ROKS_ETIMEOUT, "a tensor-core completion wait ran out (bounded mbarrier wait)");
+        if (*ctx->h_flag) {
+            const int band = *ctx->h_flag - 1;
+            CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), st));
+            return fail(ctx, ROKS_ENOTPOSDEF, "overlap matrix not positive definite at band " + std::to_string(band));
+        }
         ctx->cache_psi = psi;
         ctx->pot_valid = true;
-        PcgScalars h;
-        CK(cudaMemcpyAsync(&h, ctx->d_sc, sizeof(h), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
+        const PcgScalars h = *ctx->h_sc;
         if (info) {
             info->E = h.E0;
             info->E_new = h.Enew;
@@ -806,6 +816,13 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
         AL(ctx->d_bigwork, w1 > w2 ? w1 : w2);
     }
     AL(ctx->d_flag, sizeof(int) * 2);
+    {
+        void* hp = nullptr;
+        if (cudaMallocHost(&hp, sizeof(PcgScalars) + 64) != cudaSuccess) return bail(ROKS_ENOMEM, "cudaMallocHost");
+        ctx->h_sc = static_cast<PcgScalars*>(hp);
+        ctx->h_flag = reinterpret_cast<int*>(static_cast<char*>(hp) + sizeof(PcgScalars) + 32);
+        *ctx->h_flag = 0;
+    }
     AL(ctx->d_sc, sizeof(PcgScalars));
     std::vector<int> pj, pn;
     if (opt->alpha != 0.0) {
@@ -1211,6 +1228,7 @@ void roks_destroy(roks_ctx* ctx) {
     if (ctx->st) cudaStreamSynchronize(ctx->st);
     else cudaDeviceSynchronize();
     if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
+    if (ctx->h_sc) cudaFreeHost(ctx->h_sc);
     if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
     for (void* p : ctx->allocs) cudaFree(p);
     for (const auto& r : ctx->prof_recs) {
