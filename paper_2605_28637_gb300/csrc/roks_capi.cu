@@ -483,14 +483,15 @@ struct Impl {
         project(ctx, psi, ld, ctx->W_K, ctx->W_K);
         dot_to(ctx, ctx->W_K, ctx->W_gI, SC_FIELD(pgI));
         pcg_rot_dots(nb, ctx->d_A, ctx->d_Aprev, ctx->d_Gin, ctx->d_sc, st);
-        // u = proj(p_I), v = proj(s_prev)
-        project(ctx, psi, ld, ctx->W_K, ctx->W_u);
+        // u = p_I (projected above; the S-projector is idempotent on
+        // S-orthonormal orbitals, so projecting again changes nothing),
+        // v = proj(s_prev) (s_prev was projected against the previous orbitals)
         project(ctx, psi, ld, ctx->W_sprev, ctx->W_v);
-        dot_to(ctx, ctx->W_u, ctx->W_G, SC_FIELD(a1));
+        dot_to(ctx, ctx->W_K, ctx->W_G, SC_FIELD(a1));
         dot_to(ctx, ctx->W_v, ctx->W_G, SC_FIELD(a2));
         pcg_direction(ctx->d_sc, st);
         // s = u + beta v, A_tot = rot (A + beta A_prev)
-        axpy<T>(npw, nb, ccv(ctx->W_u), l, ccv(ctx->W_v), l, reinterpret_cast<double*>(ctx->d_sc) + SC_FIELD(beta),
+        axpy<T>(npw, nb, ccv(ctx->W_K), l, ccv(ctx->W_v), l, reinterpret_cast<double*>(ctx->d_sc) + SC_FIELD(beta),
                 1.0, cv(ctx->W_s), l, st);
         pcg_total_rotation(nb, ctx->d_A, ctx->d_Aprev, ctx->d_sc, ctx->d_Atot, st);
         // trial point
