@@ -87,6 +87,7 @@ struct roks_ctx {
     ExxCoef exc{};
     // state
     const void* cache_psi = nullptr;   // potentials valid for this buffer (pcg chain)
+    const void* b_psi = nullptr;       // d_B holds P^H psi for this buffer
     bool pot_valid = false;
     int n_small = 0;
     // learned correction of the preconditioner; once its run meets the
@@ -265,6 +266,7 @@ struct Impl {
                        ctx->d_gemm_work, ctx->gemm_work_elems, st);
             B = ctx->d_B;
         }
+        if (B == ctx->d_B) ctx->b_psi = psi;
         apply_DQ(ctx->nproj, ctx->nb, B, ctx->d_blk_off, ctx->d_blk_n, ctx->d_Drow, ctx->d_Qrow, nullptr,
                  ctx->d_DB, nullptr, st);
         band_quadratic(ctx->nproj, ctx->nb, B, ctx->d_DB, ctx->d_nl_b, st);
@@ -285,8 +287,10 @@ struct Impl {
     }
 
     // F = F^{k(n)}|n>, S = S|n> (S optional), with the current potentials.
+    // reuse_B: d_B already holds P^H psi (the PCG chain keeps it from the
+    // orthonormalisation of the accepted point)
     static roks_status apply(roks_ctx* ctx, const void* psi, int64_t ld, void* F, int64_t ldf, void* S,
-                             int64_t lds) {
+                             int64_t lds, bool reuse_B = false) {
         const Sphere s = sphere(ctx);
         cudaStream_t st = ctx->st;
         const V* p = ccv(psi);
@@ -310,10 +314,11 @@ struct Impl {
                           static_cast<const T*>(ctx->d_wk), 0, ctx->nb, ctx->nc, st);
         }
         if (ctx->nproj > 0) {
-            {
+            if (!reuse_B) {
                 PROF("proj_PhPsi");
                 gemm_cn<T>(ctx->nproj, ctx->nb, ctx->npw, ccv(ctx->d_P), ctx->ld_min, p, ld, ctx->d_B, ctx->nproj,
                            ctx->d_gemm_work, ctx->gemm_work_elems, st);
+                ctx->b_psi = psi;
             }
             apply_DQ(ctx->nproj, ctx->nb, ctx->d_B, ctx->d_blk_off, ctx->d_blk_n, ctx->d_Drow, ctx->d_Qrow,
                      ctx->d_wband, ctx->d_DB, ctx->d_QB, st);
@@ -450,7 +455,7 @@ struct Impl {
         roks_status r;
         pcg_take_energy(ctx->d_E, ctx->d_sc, SC_FIELD(E0), st);
         // F Psi, S Psi, theta, d
-        r = apply(ctx, psi, ld, ctx->W_F, l, ctx->W_S, l);
+        r = apply(ctx, psi, ld, ctx->W_F, l, ctx->W_S, l, true);
         if (r != ROKS_OK) return r;
         {
             PROF("subspace_theta");
@@ -569,8 +574,16 @@ struct Impl {
             r = potential(ctx);
             if (r != ROKS_OK) return r;
         }
+        if (ctx->nproj > 0 && ctx->b_psi != psi) {
+            // the iteration reuses P^H psi from d_B: form it if another call replaced it
+            PROF("proj_PhPsi");
+            gemm_cn<T>(ctx->nproj, ctx->nb, ctx->npw, ccv(ctx->d_P), ctx->ld_min, ccv(psi), ld, ctx->d_B, ctx->nproj,
+                       ctx->d_gemm_work, ctx->gemm_work_elems, st);
+            ctx->b_psi = psi;
+        }
         r = pcg_run(ctx, psi, ld);
         if (r != ROKS_OK) return r;
+        ctx->b_psi = psi;   // d_B: projector coefficients of the accepted point, now in psi
         // scalars and status flag in one round trip (pinned host copies)
         CK(cudaMemcpyAsync(ctx->h_sc, ctx->d_sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(ctx->h_flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -613,6 +626,7 @@ void reset_history(roks_ctx* ctx) {
     cudaMemsetAsync(ctx->d_Aprev, 0, sizeof(double2) * ctx->nb * ctx->nb, ctx->st);
     ctx->pot_valid = false;
     ctx->cache_psi = nullptr;
+    ctx->b_psi = nullptr;
     ctx->n_small = 0;
     ctx->mlp_judging = false;
     cudaStreamSynchronize(ctx->st);
