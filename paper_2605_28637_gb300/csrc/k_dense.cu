@@ -221,6 +221,10 @@ void chunk_sum(int M, int N, int nchunk, const double2* part, double2* C, int ld
     chunk_sum_t<double2>(M, N, nchunk, part, C, ldc, st);
 }
 
+void chunk_sum_f32(int M, int N, int nchunk, const float2* part, double2* C, int ldc, cudaStream_t st) {
+    chunk_sum_t<float2>(M, N, nchunk, part, C, ldc, st);
+}
+
 namespace {
 struct CnPlan {
     int rm, rn, ty, tx, mt, nt, kchunk, nchunk;
@@ -396,6 +400,10 @@ void gemm_cn(int M, int N, int K, const c2<T>* A, int64_t lda, const c2<T>* B, i
     const int max_chunks = (int)(work_elems / ((size_t)M * N));
     if constexpr (sizeof(T) == 4) {
         // mixed path: tcgen05 tensor cores (split TF32) when enabled and the shape allows
+        if (!(allow_tc && tc_enabled()) &&
+            gemm_cn_stream(M, N, K, reinterpret_cast<const float2*>(A), lda, reinterpret_cast<const float2*>(B), ldb,
+                           C, ldc, work, work_elems, st))
+            return;
         if (allow_tc && gemm_cn_tc(M, N, K, reinterpret_cast<const float2*>(A), lda,
                                    reinterpret_cast<const float2*>(B), ldb, C, ldc, work, max_chunks, st))
             return;
@@ -557,6 +565,10 @@ void gemm_nn(int M, int N, int K, const c2<T>* A, int64_t lda, const double2* B,
     const c2<T>* Bt;
     int ldbt;
     if constexpr (sizeof(T) == 4) {
+        if (gemm_nn_stream(M, N, K, reinterpret_cast<const float2*>(A), lda, B, ldb, bwork,
+                           reinterpret_cast<const float2*>(C), reinterpret_cast<float2*>(C), ldc, (float)alpha,
+                           (float)beta, st))
+            return;
         float2* Bf = static_cast<float2*>(bwork);
         if (K > 0) {
             roks::count_launch();

@@ -390,6 +390,8 @@ struct Impl {
         CK(cudaStreamSynchronize(ctx->st));
         if (tc_timeout_take())
             return fail(ctx, ROKS_ETIMEOUT, "a tensor-core completion wait ran out (bounded mbarrier wait)");
+        if (stream_timeout_take())
+            return fail(ctx, ROKS_ETIMEOUT, "a bulk-copy wait of a streamed contraction ran out (bounded mbarrier wait)");
         if (flag) {
             CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->st));
             return fail(ctx, ROKS_ENOTPOSDEF,
@@ -587,9 +589,16 @@ struct Impl {
         // scalars and status flag in one round trip (pinned host copies)
         CK(cudaMemcpyAsync(ctx->h_sc, ctx->d_sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(ctx->h_flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        int* sflag = stream_timeout_flag();
+        ctx->h_flag[1] = 0;
+        if (sflag) CK(cudaMemcpyAsync(ctx->h_flag + 1, sflag, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         if (tc_timeout_take())
             return fail(ctx, ROKS_ETIMEOUT, "a tensor-core completion wait ran out (bounded mbarrier wait)");
+        if (ctx->h_flag[1]) {
+            stream_timeout_take();
+            return fail(ctx, ROKS_ETIMEOUT, "a bulk-copy wait of a streamed contraction ran out (bounded mbarrier wait)");
+        }
         if (*ctx->h_flag) {
             const int band = *ctx->h_flag - 1;
             CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), st));

@@ -137,6 +137,21 @@ bool gemm_cn_tc(int M, int N, int K, const float2* A, int64_t lda, const float2*
 bool tc_enabled();
 // 1 if a tensor-core mbarrier wait gave up since the last call (then cleared)
 int tc_timeout_take();
+// FP32 partials (nchunk x M x N float2) summed like chunk_sum, with compensation.
+void chunk_sum_f32(int M, int N, int nchunk, const float2* part, double2* C, int ldc, cudaStream_t st);
+// Streamed FP32 contractions (bulk copies into a shared-memory ring, one CTA
+// per SM); false when the shape, the alignment (16-byte bases, even leading
+// dimensions) or the buffers do not allow them, and the caller falls back.
+// ROKS_STREAM=0 switches them off.
+bool stream_enabled();
+bool gemm_cn_stream(int M, int N, int K, const float2* A, int64_t lda, const float2* B, int64_t ldb, double2* C,
+                    int ldc, double2* work, size_t work_elems, cudaStream_t st);
+bool gemm_nn_stream(int M, int N, int K, const float2* A, int64_t lda, const double2* B, int ldb, void* bwork,
+                    const float2* Cin, float2* Cout, int64_t ldc, float alpha, float beta, cudaStream_t st);
+// 1 if a streamed-contraction wait gave up since the last call (then cleared);
+// the flag's device address, for asynchronous reads.
+int stream_timeout_take();
+int* stream_timeout_flag();
 // Same, with at most max_chunks K chunks (work holds max_chunks * M * N).
 template <typename T>
 void gemm_cn_capped(int M, int N, int K, const c2<T>* A, int64_t lda, const c2<T>* B, int64_t ldb,
