@@ -169,27 +169,57 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& c, float v) {
 // C[n ldc + m] = sum over the chunks of part[c][n][m] in a fixed order.  A
 // block covers 32 consecutive outputs (lanes) and its 32 warps take every
 // 32nd chunk (many loads in flight: the reduction is latency-bound); FP32
-// partials are summed with compensation (two-sum), FP64 ones directly, and
-// the 32 group sums are combined in FP64 in warp order.
+// partials are summed with compensation (two-sum) and the 32 group sums
+// combined by a fixed pairwise tree of compensated FP32 additions; FP64
+// partials are summed directly, by the same tree.
 constexpr int kSumGroups = 32;
+// (s1, c1) += (s2, c2) for compensated sums: the rounding error of s1 + s2
+// joins the compensations
+__device__ __forceinline__ void comp_add(float& s1, float& c1, float s2, float c2) {
+    const float t = s1 + s2;
+    const float bp = t - s1;
+    c1 += c2 + ((s1 - (t - bp)) + (s2 - bp));
+    s1 = t;
+}
 template <typename P>
 __global__ void __launch_bounds__(32 * kSumGroups) k_chunk_sum(int M, int MN, int nchunk, const P* __restrict__ part,
                                                                double2* __restrict__ C, int ldc) {
-    __shared__ double2 red[kSumGroups][32];
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
     const int w = blockIdx.x * 32 + lane;
-    double2 r = make_double2(0.0, 0.0);
-    if (w < MN) {
-        if constexpr (sizeof(P) == 8) {
-            float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+    if constexpr (sizeof(P) == 8) {
+        // FP32 partials: compensated FP32 throughout (FP64 arithmetic is slow
+        // on this part), one conversion per output at the end
+        __shared__ float4 red[kSumGroups][32];
+        float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+        if (w < MN) {
 #pragma unroll 8
             for (int c = g; c < nchunk; c += kSumGroups) {
                 const P v = part[(int64_t)c * MN + w];
                 two_sum_acc(sx, cx, v.x);
                 two_sum_acc(sy, cy, v.y);
             }
-            r = make_double2((double)sx + (double)cx, (double)sy + (double)cy);
-        } else {
+        }
+        red[g][lane] = make_float4(sx, cx, sy, cy);
+        __syncthreads();
+#pragma unroll
+        for (int h = kSumGroups / 2; h > 0; h >>= 1) {
+            if (g < h) {
+                float4 a = red[g][lane];
+                const float4 b = red[g + h][lane];
+                comp_add(a.x, a.y, b.x, b.y);
+                comp_add(a.z, a.w, b.z, b.w);
+                red[g][lane] = a;
+            }
+            __syncthreads();
+        }
+        if (g == 0 && w < MN) {
+            const float4 r = red[0][lane];
+            C[(int64_t)(w / M) * ldc + (w % M)] = make_double2((double)r.x + (double)r.y, (double)r.z + (double)r.w);
+        }
+    } else {
+        __shared__ double2 red[kSumGroups][32];
+        double2 r = make_double2(0.0, 0.0);
+        if (w < MN) {
 #pragma unroll 4
             for (int c = g; c < nchunk; c += kSumGroups) {
                 const P v = part[(int64_t)c * MN + w];
@@ -197,17 +227,18 @@ __global__ void __launch_bounds__(32 * kSumGroups) k_chunk_sum(int M, int MN, in
                 r.y += v.y;
             }
         }
-    }
-    red[g][lane] = r;
-    __syncthreads();
-    if (g == 0 && w < MN) {
-        double sx = 0.0, sy = 0.0;
+        red[g][lane] = r;
+        __syncthreads();
+        // pairwise, in a fixed tree (five dependent levels instead of 32)
 #pragma unroll
-        for (int q = 0; q < kSumGroups; ++q) {
-            sx += red[q][lane].x;
-            sy += red[q][lane].y;
+        for (int h = kSumGroups / 2; h > 0; h >>= 1) {
+            if (g < h) {
+                red[g][lane].x += red[g + h][lane].x;
+                red[g][lane].y += red[g + h][lane].y;
+            }
+            __syncthreads();
         }
-        C[(int64_t)(w / M) * ldc + (w % M)] = make_double2(sx, sy);
+        if (g == 0 && w < MN) C[(int64_t)(w / M) * ldc + (w % M)] = red[0][lane];
     }
 }
 
@@ -566,7 +597,7 @@ void gemm_nn(int M, int N, int K, const c2<T>* A, int64_t lda, const double2* B,
     int ldbt;
     if constexpr (sizeof(T) == 4) {
         if (gemm_nn_stream(M, N, K, reinterpret_cast<const float2*>(A), lda, B, ldb, bwork,
-                           reinterpret_cast<const float2*>(C), reinterpret_cast<float2*>(C), ldc, (float)alpha,
+                           reinterpret_cast<const float2*>(C), ldc, reinterpret_cast<float2*>(C), ldc, (float)alpha,
                            (float)beta, st))
             return;
         float2* Bf = static_cast<float2*>(bwork);
@@ -585,6 +616,27 @@ void gemm_nn(int M, int N, int K, const c2<T>* A, int64_t lda, const double2* B,
     NN_CASE(1) NN_CASE(2) NN_CASE(3) NN_CASE(4) NN_CASE(5) NN_CASE(6) NN_CASE(7) NN_CASE(8)
 #undef NN_CASE
 }
+
+template <typename T>
+void gemm_nn_io(int M, int N, int K, const c2<T>* A, int64_t lda, const double2* B, int ldb, const c2<T>* Cin,
+                int64_t ldcin, c2<T>* Cout, int64_t ldc, double alpha, double beta, void* bwork, cudaStream_t st) {
+    if (M <= 0 || N <= 0) return;
+    if constexpr (sizeof(T) == 4) {
+        if (gemm_nn_stream(M, N, K, reinterpret_cast<const float2*>(A), lda, B, ldb, bwork,
+                           reinterpret_cast<const float2*>(Cin), ldcin, reinterpret_cast<float2*>(Cout), ldc,
+                           (float)alpha, (float)beta, st))
+            return;
+    }
+    if (beta != 0.0 && (Cin != Cout || ldcin != ldc))
+        cudaMemcpy2DAsync(Cout, ldc * sizeof(c2<T>), Cin, ldcin * sizeof(c2<T>), M * sizeof(c2<T>), N,
+                          cudaMemcpyDeviceToDevice, st);
+    gemm_nn<T>(M, N, K, A, lda, B, ldb, Cout, ldc, alpha, beta, bwork, st);
+}
+
+template void gemm_nn_io<float>(int, int, int, const float2*, int64_t, const double2*, int, const float2*, int64_t,
+                                float2*, int64_t, double, double, void*, cudaStream_t);
+template void gemm_nn_io<double>(int, int, int, const double2*, int64_t, const double2*, int, const double2*,
+                                 int64_t, double2*, int64_t, double, double, void*, cudaStream_t);
 
 template void gemm_cn<float>(int, int, int, const float2*, int64_t, const float2*, int64_t, double2*, int,
                              double2*, size_t, cudaStream_t, bool);
@@ -717,43 +769,48 @@ __global__ void __launch_bounds__(1024) k_cholesky_small(int n, const double2* _
     if (threadIdx.x == 0 && bad) flag[0] = bad;
 }
 
-// FP32 Cholesky of O (FP64 input) and X = L^{-1} (written as FP64), one block,
-// n <= kSmallN: the first half of the refined factorisation below.
-__global__ void __launch_bounds__(1024) k_cholesky_f32(int n, const double2* __restrict__ O,
-                                                       double2* __restrict__ Xout, int* flag) {
-    // W: working copy of the lower triangle of O; L: the factor; X = L^{-1}
+bool cholesky_small_supported(int n) { return n <= kSmallN; }
+
+// Deviation form of the Cholesky inverse for O = I + Delta (FP32, one block,
+// n <= kSmallN).  W holds the working lower triangle of Delta (its diagonal
+// real), L = I + Lambda is built column by column with the pivot deviation
+// lambda_jj = w / (1 + sqrt(1 + w)) (no cancellation), and the columns of
+// Xi = L^{-1} - I solve (I + Lambda) xi_c = -Lambda e_c by a right-looking
+// sweep, one warp per column.
+__global__ void __launch_bounds__(1024) k_cholesky_dev_f32(int n, const double2* __restrict__ O,
+                                                           double2* __restrict__ XiH, int* flag) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* W = reinterpret_cast<float2*>(smem_raw);
-    float2* L = W + n * n;
-    float2* X = L + n * n;
+    float2* W = reinterpret_cast<float2*>(smem_raw);   // Delta (lower), updated in place
+    float2* Lm = W + n * n;                             // Lambda (lower, diagonal deviation in .x)
     __shared__ float dinv[kSmallN];
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-        const double2 o = O[idx];
-        W[idx] = make_float2((float)o.x, (float)o.y);
+        const int i = idx % n, j = idx / n;
+        if (i < j) continue;
+        // average of the two triangles, minus the identity, before rounding to FP32
+        const double2 a = O[(int64_t)j * n + i], b = O[(int64_t)i * n + j];
+        const double re = 0.5 * (a.x + b.x) - (i == j ? 1.0 : 0.0);
+        const double im = i == j ? 0.0 : 0.5 * (a.y - b.y);
+        W[idx] = make_float2((float)re, (float)im);
     }
     __syncthreads();
     int bad = 0;
-    // right-looking factorisation, one barrier per column: every thread
-    // derives the pivot itself, column j of L and the trailing update both
-    // read the unscaled column j of W, and the update writes only columns > j
     for (int j = 0; j < n; ++j) {
-        float d = W[j * n + j].x;
-        if (!(d > 0.f)) {
+        float w = W[j * n + j].x;
+        if (!(1.f + w > 0.f)) {
             if (!bad) bad = j + 1;
-            d = 1.f;
+            w = 0.f;
         }
-        const float piv = sqrtf(d), inv = 1.f / piv, invd = inv * inv;
+        const float piv = sqrtf(1.f + w), inv = 1.f / piv, invd = inv * inv;
         if (threadIdx.x == 0) dinv[j] = inv;
         for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
             const float2 v = W[j * n + i];
-            L[j * n + i] = (i == j) ? make_float2(piv, 0.f) : make_float2(v.x * inv, v.y * inv);
+            Lm[j * n + i] = (i == j) ? make_float2(w / (1.f + piv), 0.f) : make_float2(v.x * inv, v.y * inv);
         }
         const int m = n - j - 1;
         for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
             const int k = j + 1 + t / m, i = j + 1 + t % m;
             if (i < k) continue;
             const float2 a = W[j * n + i], b = W[j * n + k];
-            // W(i, k) -= W(i, j) conj(W(k, j)) / d
             float2 c = W[k * n + i];
             c.x = fmaf(-(a.x * b.x + a.y * b.y), invd, c.x);
             c.y = fmaf(-(a.y * b.x - a.x * b.y), invd, c.y);
@@ -761,13 +818,12 @@ __global__ void __launch_bounds__(1024) k_cholesky_f32(int n, const double2* __r
         }
         __syncthreads();
     }
-    // X = L^{-1} by columns: warp c solves L x = e_c with a right-looking
-    // sweep (lane l holds rows l and l + 32); x_k reaches every lane by one
-    // shuffle per step
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int c = warp; c < n; c += nw) {
-        float2 r0 = make_float2(lane == c ? 1.f : 0.f, 0.f);
-        float2 r1 = make_float2(lane + 32 == c ? 1.f : 0.f, 0.f);
+        // right-hand side -Lambda e_c: rows lane and lane + 32
+        float2 r0 = make_float2(0.f, 0.f), r1 = make_float2(0.f, 0.f);
+        if (lane >= c && lane < n) r0 = make_float2(-Lm[c * n + lane].x, -Lm[c * n + lane].y);
+        if (lane + 32 >= c && lane + 32 < n) r1 = make_float2(-Lm[c * n + lane + 32].x, -Lm[c * n + lane + 32].y);
         for (int k = c; k < n; ++k) {
             const float2 own = k < 32 ? r0 : r1;
             const float sx = __shfl_sync(0xffffffffu, own.x, k & 31);
@@ -779,65 +835,34 @@ __global__ void __launch_bounds__(1024) k_cholesky_f32(int n, const double2* __r
                 else r1 = xk;
             }
             if (lane > k && lane < n) {
-                const float2 l = L[k * n + lane];
+                const float2 l = Lm[k * n + lane];
                 r0.x -= l.x * xk.x - l.y * xk.y;
                 r0.y -= l.x * xk.y + l.y * xk.x;
             }
             if (lane + 32 > k && lane + 32 < n) {
-                const float2 l = L[k * n + lane + 32];
+                const float2 l = Lm[k * n + lane + 32];
                 r1.x -= l.x * xk.x - l.y * xk.y;
                 r1.y -= l.x * xk.y + l.y * xk.x;
             }
         }
-        if (lane < n) X[c * n + lane] = lane >= c ? r0 : make_float2(0.f, 0.f);
-        if (lane + 32 < n) X[c * n + lane + 32] = lane + 32 >= c ? r1 : make_float2(0.f, 0.f);
+        // XiH (row c, column i) = conj Xi (row i, column c); zero above the diagonal of Xi
+        if (lane < n) {
+            const float2 x = lane >= c ? r0 : make_float2(0.f, 0.f);
+            XiH[(int64_t)lane * n + c] = make_double2((double)x.x, -(double)x.y);
+        }
+        if (lane + 32 < n) {
+            const float2 x = lane + 32 >= c ? r1 : make_float2(0.f, 0.f);
+            XiH[(int64_t)(lane + 32) * n + c] = make_double2((double)x.x, -(double)x.y);
+        }
     }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) Xout[idx] = make_double2(X[idx].x, X[idx].y);
     if (threadIdx.x == 0 && bad) flag[0] = bad;
 }
 
-// D = I - N with N the first-order Cholesky correction of M = X O X^H:
-// N_ij = M_ij (i > j), N_ii = (M_ii - 1) / 2, N_ij = 0 (i < j).
-__global__ void k_refine_factor(int n, const double2* __restrict__ M, double2* __restrict__ D) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n * n) return;
-    const int i = idx % n, j = idx / n;
-    const double2 m = M[idx];
-    double2 d = make_double2(0.0, 0.0);
-    if (i > j) d = make_double2(-m.x, -m.y);
-    else if (i == j) d = make_double2(1.0 - 0.5 * (m.x - 1.0), 0.0);
-    D[idx] = d;
+void cholesky_dev_f32(int n, const double2* O, double2* XiH, int* flag, cudaStream_t st) {
+    const size_t sm = sizeof(float2) * 2 * n * n;
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_cholesky_dev_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    roks::count_launch(), k_cholesky_dev_f32<<<1, 1024, sm, st>>>(n, O, XiH, flag);
 }
-
-// out = in^H
-__global__ void k_conj_transpose(int n, const double2* __restrict__ in, double2* __restrict__ out) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n * n) return;
-    const int i = idx % n, j = idx / n;
-    const double2 v = in[(int64_t)i * n + j];
-    out[idx] = make_double2(v.x, -v.y);
-}
-
-// Cholesky inverse of FP64 accuracy from an FP32 factorisation and one
-// refinement step (n <= kSmallN): X = L32^{-1}; M = X O X^H = I + delta;
-// L^{-1} = (I - N) X with N the lower-triangular first-order factor of delta
-// (error O(|delta|^2)).  The products run in FP64 over many blocks, so the
-// serial part is FP32.  w1, w2 hold n x n each.
-void cholesky_inverse_refined(int n, const double2* O, double2* w1, double2* w2, double2* LinvH, int* flag,
-                              cudaStream_t st) {
-    const size_t sm = sizeof(float2) * 3 * n * n;
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_cholesky_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    roks::count_launch(), k_cholesky_f32<<<1, 1024, sm, st>>>(n, O, w1, flag);          // w1 = X
-    small_gemm(n, n, n, w1, n, false, O, n, false, LinvH, n, 1.0, 0.0, st);              // LinvH = X O
-    small_gemm(n, n, n, LinvH, n, false, w1, n, true, w2, n, 1.0, 0.0, st);              // w2 = X O X^H
-    const int blocks = (n * n + 127) / 128;
-    roks::count_launch(), k_refine_factor<<<blocks, 128, 0, st>>>(n, w2, LinvH);         // LinvH = I - N
-    small_gemm(n, n, n, LinvH, n, false, w1, n, false, w2, n, 1.0, 0.0, st);             // w2 = (I - N) X
-    roks::count_launch(), k_conj_transpose<<<blocks, 128, 0, st>>>(n, w2, LinvH);
-}
-
-bool cholesky_refined_supported(int n) { return n <= kSmallN; }
 
 // Cholesky O = L L^H (Crout, column by column) and the inverse of L, one
 // block.  LinvH[k, i] = conj(Linv[i, k]) so that Psi LinvH = Psi L^{-H}.

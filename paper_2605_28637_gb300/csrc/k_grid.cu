@@ -172,12 +172,20 @@ __global__ void __launch_bounds__(RB) k_colred(int npw, int nb, const c2<T>* __r
     }
 }
 
+// out[i] = sum of the nsplit partials of column i (nsplit a multiple of 4):
+// four interleaved FP64 chains, combined pairwise (fixed order)
 __global__ void k_colred_final(int count, int nsplit, const double* __restrict__ part, double* __restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
-    double s = 0.0;
-    for (int k = 0; k < nsplit; ++k) s += part[(int64_t)i * nsplit + k];
-    out[i] = s;
+    const double* p = part + (int64_t)i * nsplit;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (int k = 0; k < nsplit; k += 4) {
+        s0 += p[k];
+        s1 += p[k + 1];
+        s2 += p[k + 2];
+        s3 += p[k + 3];
+    }
+    out[i] = (s0 + s1) + (s2 + s3);
 }
 
 template <typename T>

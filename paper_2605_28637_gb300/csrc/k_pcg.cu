@@ -237,12 +237,15 @@ __global__ void k_hermitize(int n, double2* O) {
 
 void hermitize(int n, double2* O, cudaStream_t st) { roks::count_launch(), k_hermitize<<<(n * n + 127) / 128, 128, 0, st>>>(n, O); }
 
-// dst = scale * sum_i v[i]  (fixed order)
+// dst = scale * sum_i v[i]: lane l sums v[l], v[l + 32], ..., then a fixed
+// shuffle tree (FP64 adds are long-latency: few dependent levels)
 __global__ void k_sum_to(const double* __restrict__ v, int n, double* dst, double scale) {
-    if (threadIdx.x != 0) return;
+    const int lane = threadIdx.x;
     double s = 0;
-    for (int i = 0; i < n; ++i) s += v[i];
-    dst[0] = scale * s;
+    for (int i = lane; i < n; i += 32) s += v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) dst[0] = scale * s;
 }
 
 void sum_to(const double* v, int n, double* dst, double scale, cudaStream_t st) {

@@ -238,11 +238,13 @@ __global__ void __launch_bounds__(cn_maxt(RM, RN)) k_cn_stream(int M, int N, int
 // ------------------------------------------------------------------ Cout = alpha A B + beta Cin
 // Row tiles of TR = 32 RR WS rows: consumer warp (h, w), h < WS, w < W, owns
 // rows 32 RR h + RR l .. + RR - 1 (lane l) and the column pairs 2 (w + W j),
-// j < RN / 2.  Shared memory: B (K x N row major, N even), then NS stages of
-// [A box: K columns x TR rows | Cin box: N columns x TR rows].
+// j < RN / 2.  K is taken in nkc chunks of KC columns: a work item is (tile,
+// chunk), and its stage holds the A box of the chunk (KC columns x TR rows)
+// and, for the tile's last chunk, the Cin box (N columns x TR rows).  B
+// (K x N row major, N even) is resident in shared memory.
 template <int RR, int RN, int WS>
-__global__ void __launch_bounds__(768) k_nn_stream(int M, int N, int K, int rows_per_cta, int W, int NS, int load_c,
-                                                   const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(768) k_nn_stream(int M, int N, int K, int KC, int nkc, int rows_per_cta, int W,
+                                                   int NS, int load_c, const __grid_constant__ CUtensorMap tmA,
                                                    const __grid_constant__ CUtensorMap tmC,
                                                    const float2* __restrict__ Bf, float2* Cout, int64_t ldc,
                                                    float alpha, float beta) {
@@ -254,14 +256,16 @@ __global__ void __launch_bounds__(768) k_nn_stream(int M, int N, int K, int rows
     float2* Bs = reinterpret_cast<float2*>(base);
     const uint32_t b_bytes = (uint32_t)K * (uint32_t)N * 8u;
     unsigned char* ring = base + align_up(b_bytes, 128);
-    const uint32_t a_bytes = (uint32_t)K * TR * 8u;
+    const uint32_t a_bytes = (uint32_t)KC * TR * 8u;
+    const uint32_t a_span = (uint32_t)align_up(a_bytes, 128);
     const uint32_t c_bytes = load_c ? (uint32_t)N * TR * 8u : 0u;
-    const uint32_t stage_bytes = (uint32_t)align_up(a_bytes + c_bytes, 128);
+    const uint32_t stage_bytes = (uint32_t)align_up(a_span + c_bytes, 128);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarps = blockDim.x >> 5;
     const int rb = blockIdx.x * rows_per_cta;
     const int re = min(M, rb + rows_per_cta);
     const int nt = re > rb ? (re - rb + TR - 1) / TR : 0;
+    const int items = nt * nkc;
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
             tc::mbar_init(&full[s], 1);
@@ -273,24 +277,26 @@ __global__ void __launch_bounds__(768) k_nn_stream(int M, int N, int K, int rows
     __syncthreads();
 
     if (warp == nwarps - 1) {
-        // producer (one thread): B once, then the row tiles
+        // producer (one thread): B once, then the (tile, chunk) items
         if (lane == 0 && nt > 0) {
             mb_arrive_expect(&bbar, b_bytes);
             bulk_g2s(Bs, Bf, b_bytes, &bbar);
             int issued = 0;
-            for (int s = 0; s < nt; ++s) {
-                const int sg = s % NS;
-                if (s >= NS && !wait_or_flag(&empty[sg], (uint32_t)((s / NS - 1) & 1))) break;
+            for (int it = 0; it < items; ++it) {
+                const int sg = it % NS;
+                if (it >= NS && !wait_or_flag(&empty[sg], (uint32_t)((it / NS - 1) & 1))) break;
                 unsigned char* st = ring + (size_t)sg * stage_bytes;
-                const int r0 = rb + s * TR;
-                mb_arrive_expect(&full[sg], a_bytes + c_bytes);
-                tma_2d(st, &tmA, r0, 0, &full[sg]);
-                if (load_c) tma_2d(st + a_bytes, &tmC, r0, 0, &full[sg]);
-                issued = s + 1;
+                const int kc = it % nkc;
+                const int r0 = rb + (it / nkc) * TR;
+                const bool last = kc == nkc - 1;
+                mb_arrive_expect(&full[sg], a_bytes + (last ? c_bytes : 0u));
+                tma_2d(st, &tmA, r0, kc * KC, &full[sg]);
+                if (last && load_c) tma_2d(st + a_span, &tmC, r0, 0, &full[sg]);
+                issued = it + 1;
             }
             wait_or_flag(&bbar, 0u);
-            for (int s = (issued > NS ? issued - NS : 0); s < issued; ++s)
-                wait_or_flag(&full[s % NS], (uint32_t)((s / NS) & 1));
+            for (int it = (issued > NS ? issued - NS : 0); it < issued; ++it)
+                wait_or_flag(&full[it % NS], (uint32_t)((it / NS) & 1));
         }
         __syncwarp();
     } else if (warp < W * WS && nt > 0) {
@@ -299,17 +305,22 @@ __global__ void __launch_bounds__(768) k_nn_stream(int M, int N, int K, int rows
         int ncp[RP];
 #pragma unroll
         for (int j = 0; j < RP; ++j) ncp[j] = min(2 * (w + W * j), N - 2);
-        for (int s = 0; s < nt && ok; ++s) {
-            const int sg = s % NS;
-            if (!wait_or_flag(&full[sg], (uint32_t)((s / NS) & 1))) break;
-            const int r0 = rb + s * TR;
+        float2 acc[RR][RN];
+        for (int it = 0; it < items && ok; ++it) {
+            const int sg = it % NS;
+            if (!wait_or_flag(&full[sg], (uint32_t)((it / NS) & 1))) break;
+            const int kc = it % nkc;
+            const int r0 = rb + (it / nkc) * TR;
             const int rows = min(TR, re - r0);
+            const int k0 = kc * KC, kn = min(KC, K - k0);
             const float2* As = reinterpret_cast<const float2*>(ring + (size_t)sg * stage_bytes);
-            float2 acc[RR][RN];
+            const float2* Bk = Bs + (size_t)k0 * N;
+            if (kc == 0) {
 #pragma unroll
-            for (int r = 0; r < RR; ++r)
+                for (int r = 0; r < RR; ++r)
 #pragma unroll
-                for (int j = 0; j < RN; ++j) acc[r][j] = make_float2(0.f, 0.f);
+                    for (int j = 0; j < RN; ++j) acc[r][j] = make_float2(0.f, 0.f);
+            }
             // four k at a time: all shared-memory loads first, then the multiply-adds
             auto kstep = [&](const float4 (&av)[4], const float4 (&bv)[4][RP], int u) {
                 float a[2 * RR];
@@ -348,51 +359,53 @@ __global__ void __launch_bounds__(768) k_nn_stream(int M, int N, int K, int rows
                 return make_float4(v.x, v.y, 0.f, 0.f);
             };
             int k = 0;
-            for (; k + 4 <= K; k += 4) {
+            for (; k + 4 <= kn; k += 4) {
                 float4 av[4], bv[4][RP];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     av[u] = load_a(k + u);
 #pragma unroll
                     for (int j = 0; j < RP; ++j)
-                        bv[u][j] = *reinterpret_cast<const float4*>(Bs + (size_t)(k + u) * N + ncp[j]);
+                        bv[u][j] = *reinterpret_cast<const float4*>(Bk + (size_t)(k + u) * N + ncp[j]);
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) kstep(av, bv, u);
             }
-            for (; k < K; ++k) {
+            for (; k < kn; ++k) {
                 float4 av[4], bv[4][RP];
                 av[0] = load_a(k);
 #pragma unroll
-                for (int j = 0; j < RP; ++j) bv[0][j] = *reinterpret_cast<const float4*>(Bs + (size_t)k * N + ncp[j]);
+                for (int j = 0; j < RP; ++j) bv[0][j] = *reinterpret_cast<const float4*>(Bk + (size_t)k * N + ncp[j]);
                 kstep(av, bv, 0);
             }
-            // epilogue: rows RR lane + r of the tile, columns ncp[j], ncp[j] + 1
-            const float2* Cs = As + (size_t)K * TR;
-            const int lr = hb + RR * lane;
+            if (kc == nkc - 1) {
+                // epilogue: rows RR lane + r of the tile, columns ncp[j], ncp[j] + 1
+                const float2* Cs = reinterpret_cast<const float2*>(ring + (size_t)sg * stage_bytes + a_span);
+                const int lr = hb + RR * lane;
 #pragma unroll
-            for (int j = 0; j < RP; ++j) {
-                if (2 * (w + W * j) >= N) continue;
+                for (int j = 0; j < RP; ++j) {
+                    if (2 * (w + W * j) >= N) continue;
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int n = ncp[j] + h;
-                    float2 v[RR];
+                    for (int h = 0; h < 2; ++h) {
+                        const int n = ncp[j] + h;
+                        float2 v[RR];
 #pragma unroll
-                    for (int r = 0; r < RR; ++r) {
-                        v[r] = make_float2(alpha * acc[r][2 * j + h].x, alpha * acc[r][2 * j + h].y);
-                        if (load_c) {
-                            const float2 c = Cs[(size_t)n * TR + lr + r];
-                            v[r].x = fmaf(beta, c.x, v[r].x);
-                            v[r].y = fmaf(beta, c.y, v[r].y);
+                        for (int r = 0; r < RR; ++r) {
+                            v[r] = make_float2(alpha * acc[r][2 * j + h].x, alpha * acc[r][2 * j + h].y);
+                            if (load_c) {
+                                const float2 c = Cs[(size_t)n * TR + lr + r];
+                                v[r].x = fmaf(beta, c.x, v[r].x);
+                                v[r].y = fmaf(beta, c.y, v[r].y);
+                            }
                         }
-                    }
-                    float2* out = Cout + (int64_t)n * ldc + r0 + lr;
-                    if (RR == 2 && lr + 1 < rows) {
-                        *reinterpret_cast<float4*>(out) = make_float4(v[0].x, v[0].y, v[RR - 1].x, v[RR - 1].y);
-                    } else {
+                        float2* out = Cout + (int64_t)n * ldc + r0 + lr;
+                        if (RR == 2 && lr + 1 < rows) {
+                            *reinterpret_cast<float4*>(out) = make_float4(v[0].x, v[0].y, v[RR - 1].x, v[RR - 1].y);
+                        } else {
 #pragma unroll
-                        for (int r = 0; r < RR; ++r)
-                            if (lr + r < rows) out[r] = v[r];
+                            for (int r = 0; r < RR; ++r)
+                                if (lr + r < rows) out[r] = v[r];
+                        }
                     }
                 }
             }
@@ -576,15 +589,16 @@ bool gemm_cn_stream(int M, int N, int K, const float2* A, int64_t lda, const flo
     return true;
 }
 
-// Cout = alpha A B + beta Cin streamed (B: K x N FP64 small, converted into
-// bwork as K x N FP32 row major); false when the shape or the alignment
-// does not allow it.
+// Cout (ldc) = alpha A B + beta Cin (ldcin) streamed (B: K x N FP64 small,
+// converted into bwork as K x N FP32 row major); false when the shape or the
+// alignment does not allow it.
 bool gemm_nn_stream(int M, int N, int K, const float2* A, int64_t lda, const double2* B, int ldb, void* bwork,
-                    const float2* Cin, float2* Cout, int64_t ldc, float alpha, float beta, cudaStream_t st) {
+                    const float2* Cin, int64_t ldcin, float2* Cout, int64_t ldc, float alpha, float beta,
+                    cudaStream_t st) {
     if (!stream_enabled() || M <= 0 || N <= 0 || K <= 0 || (N & 1) || N > 96 || K > 256) return false;
     const bool load_c = beta != 0.f;
     if ((lda & 1) || (ldc & 1) || !aligned16(A) || !aligned16(bwork) || !aligned16(Cout) ||
-        (load_c && !aligned16(Cin)))
+        (load_c && (!aligned16(Cin) || (ldcin & 1))))
         return false;
     // columns per thread (even) so that at most 11 warps cover N
     const int pairs = N / 2;
@@ -593,19 +607,26 @@ bool gemm_nn_stream(int M, int N, int K, const float2* A, int64_t lda, const dou
     if (RN > 12) return false;
     const int W = (pairs + rp - 1) / rp;
     const size_t bbytes = align_up((size_t)K * N * sizeof(float2), 128);
-    const int ncol = K + (load_c ? N : 0);
-    // rows per lane RR and warp sets WS: the largest row tile with two stages
-    int RR = 0, WS = 0, NS = 0;
+    // rows per lane RR, warp sets WS and K chunks: the largest row tile, then
+    // the fewest chunks, with two stages beside the resident B
+    int RR = 0, WS = 0, NS = 0, KC = 0, nkc = 0;
     size_t stage = 0;
     const int shapes[3][2] = {{2, 2}, {2, 1}, {1, 1}};
     for (int c = 0; c < 3 && !RR; ++c) {
-        const int rr = shapes[c][0], ws = shapes[c][1];
-        stage = align_up((size_t)ncol * 32 * rr * ws * sizeof(float2), 128);
-        if (ST_ALIGN + bbytes + 2 * stage > ST_SMEM) continue;
-        RR = rr;
-        WS = ws;
-        NS = (int)((ST_SMEM - ST_ALIGN - bbytes) / stage);
-        if (NS > 4) NS = 4;
+        const int rr = shapes[c][0], ws = shapes[c][1], tr = 32 * rr * ws;
+        for (int q = 1; q <= 8 && !RR; ++q) {
+            const int kc = (K + q - 1) / q;
+            stage = align_up(align_up((size_t)kc * tr * sizeof(float2), 128) +
+                                 (load_c ? (size_t)N * tr * sizeof(float2) : 0),
+                             128);
+            if (ST_ALIGN + bbytes + 2 * stage > ST_SMEM) continue;
+            RR = rr;
+            WS = ws;
+            KC = kc;
+            nkc = (K + kc - 1) / kc;
+            NS = (int)((ST_SMEM - ST_ALIGN - bbytes) / stage);
+            if (NS > 4) NS = 4;
+        }
     }
     if (!RR) return false;
     const int TR = 32 * RR * WS;
@@ -616,9 +637,9 @@ bool gemm_nn_stream(int M, int N, int K, const float2* A, int64_t lda, const dou
     rows = (rows + 1) & ~1;
     G = (M + rows - 1) / rows;
     CUtensorMap tmA, tmC;
-    if (!encode_block(&tmA, A, M, K, lda, TR, K, false)) return false;
+    if (!encode_block(&tmA, A, M, K, lda, TR, KC, false)) return false;
     if (load_c) {
-        if (!encode_block(&tmC, Cin, M, N, ldc, TR, N, false)) return false;
+        if (!encode_block(&tmC, Cin, M, N, ldcin, TR, N, false)) return false;
     } else {
         tmC = tmA;   // not read
     }
@@ -635,8 +656,8 @@ bool gemm_nn_stream(int M, int N, int K, const float2* A, int64_t lda, const dou
             attr = true;                                                                                    \
         }                                                                                                   \
         roks::count_launch();                                                                               \
-        k_nn_stream<RR_, RN_, WS_><<<G, threads, smem, st>>>(M, N, K, rows, W, NS, load_c ? 1 : 0, tmA, tmC, \
-                                                             Bf, Cout, ldc, alpha, beta);                   \
+        k_nn_stream<RR_, RN_, WS_><<<G, threads, smem, st>>>(M, N, K, KC, nkc, rows, W, NS, load_c ? 1 : 0,  \
+                                                             tmA, tmC, Bf, Cout, ldc, alpha, beta);         \
         return true;                                                                                        \
     }
 #define NNS_RN(RR_, WS_) NNS_CASE(RR_, 2, WS_) NNS_CASE(RR_, 4, WS_) NNS_CASE(RR_, 6, WS_) NNS_CASE(RR_, 8, WS_) \

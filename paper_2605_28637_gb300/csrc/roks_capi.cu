@@ -360,25 +360,37 @@ struct Impl {
             small_gemm(nb, nb, ctx->nproj, ctx->d_B2, ctx->nproj, true, ctx->d_QB, ctx->nproj, false, ctx->d_O, nb,
                        1.0, 1.0, st);
         }
+        // mixed path, small n: L^{-H} = I + Xi^H in deviation form (FP32 errors
+        // relative to |O - I|); out = in + in Xi^H keeps the identity exact
+        const bool dev = ctx->prec == ROKS_MIXED && cholesky_small_supported(nb);
         {
             PROF("orth_cholesky");
-            hermitize(nb, ctx->d_O, st);
-            if (nb > 64)
-                cholesky_inverse_big(nb, ctx->d_O, ctx->d_bigwork, ctx->prec == ROKS_FP64, ctx->d_LinvH, ctx->d_flag,
-                                     st);
-            else if (ctx->prec == ROKS_MIXED && cholesky_refined_supported(nb))
-                cholesky_inverse_refined(nb, ctx->d_O, ctx->d_L, ctx->d_e1, ctx->d_LinvH, ctx->d_flag, st);
-            else
-                cholesky_inverse(nb, ctx->d_O, ctx->d_L, ctx->d_LinvH, ctx->d_flag, st);
+            if (dev) {
+                cholesky_dev_f32(nb, ctx->d_O, ctx->d_LinvH, ctx->d_flag, st);
+            } else {
+                hermitize(nb, ctx->d_O, st);
+                if (nb > 64)
+                    cholesky_inverse_big(nb, ctx->d_O, ctx->d_bigwork, ctx->prec == ROKS_FP64, ctx->d_LinvH,
+                                         ctx->d_flag, st);
+                else
+                    cholesky_inverse(nb, ctx->d_O, ctx->d_L, ctx->d_LinvH, ctx->d_flag, st);
+            }
         }
         {
             PROF("orth_apply");
-            gemm_nn<T>(ctx->npw, nb, nb, ccv(in), ldi, ctx->d_LinvH, nb, cv(out), ldo, 1.0, 0.0, ctx->d_gemm_work, st);
+            if (dev)
+                gemm_nn_io<T>(ctx->npw, nb, nb, ccv(in), ldi, ctx->d_LinvH, nb, ccv(in), ldi, cv(out), ldo, 1.0, 1.0,
+                              ctx->d_gemm_work, st);
+            else
+                gemm_nn<T>(ctx->npw, nb, nb, ccv(in), ldi, ctx->d_LinvH, nb, cv(out), ldo, 1.0, 0.0,
+                           ctx->d_gemm_work, st);
         }
         if (Bout && ctx->nproj > 0) {
             PROF("orth_small");
+            if (dev)
+                CK(cudaMemcpyAsync(Bout, ctx->d_B2, sizeof(double2) * ctx->nproj * nb, cudaMemcpyDeviceToDevice, st));
             small_gemm(ctx->nproj, nb, nb, ctx->d_B2, ctx->nproj, false, ctx->d_LinvH, nb, false, Bout, ctx->nproj,
-                       1.0, 0.0, st);
+                       1.0, dev ? 1.0 : 0.0, st);
         }
         CK(cudaGetLastError());
         return ROKS_OK;

@@ -147,7 +147,8 @@ bool stream_enabled();
 bool gemm_cn_stream(int M, int N, int K, const float2* A, int64_t lda, const float2* B, int64_t ldb, double2* C,
                     int ldc, double2* work, size_t work_elems, cudaStream_t st);
 bool gemm_nn_stream(int M, int N, int K, const float2* A, int64_t lda, const double2* B, int ldb, void* bwork,
-                    const float2* Cin, float2* Cout, int64_t ldc, float alpha, float beta, cudaStream_t st);
+                    const float2* Cin, int64_t ldcin, float2* Cout, int64_t ldc, float alpha, float beta,
+                    cudaStream_t st);
 // 1 if a streamed-contraction wait gave up since the last call (then cleared);
 // the flag's device address, for asynchronous reads.
 int stream_timeout_take();
@@ -163,16 +164,24 @@ template <typename T>
 void gemm_nn(int M, int N, int K, const c2<T>* A, int64_t lda, const double2* B, int ldb,
              c2<T>* C, int64_t ldc, double alpha, double beta, void* bwork, cudaStream_t st);
 
+// Cout (ldc) = alpha A B + beta Cin (ldcin); Cin may differ from Cout (when
+// beta != 0 and it does, Cin is not modified).
+template <typename T>
+void gemm_nn_io(int M, int N, int K, const c2<T>* A, int64_t lda, const double2* B, int ldb, const c2<T>* Cin,
+                int64_t ldcin, c2<T>* Cout, int64_t ldc, double alpha, double beta, void* bwork, cudaStream_t st);
+
 // ------------------------------------------------------------ small FP64 matrices (n x n, column major)
 void small_gemm(int M, int N, int K, const double2* A, int lda, bool ca, const double2* B, int ldb,
                 bool cb, double2* C, int ldc, double alpha, double beta, cudaStream_t st);
 // O (Hermitian) -> LinvH = L^{-H}, L L^H = O.  flag[0] set to 1 + column on failure.
 void cholesky_inverse(int n, const double2* O, double2* Lw, double2* LinvH, int* flag, cudaStream_t st);
-// FP32 factorisation + one FP64 refinement step (FP64 accuracy for a
-// well-conditioned O); n <= 64.  w1, w2: n x n scratch.
-void cholesky_inverse_refined(int n, const double2* O, double2* w1, double2* w2, double2* LinvH, int* flag,
-                              cudaStream_t st);
-bool cholesky_refined_supported(int n);
+// n within the single-block factorisations
+bool cholesky_small_supported(int n);
+// Cholesky inverse of a near-identity Hermitian O in deviation form, FP32,
+// one block (n <= 64): L = I + Lambda, L^{-1} = I + Xi; writes XiH = Xi^H
+// (so that L^{-H} = I + XiH).  The rounding errors scale with |O - I|, not
+// with 1.  O's two triangles are averaged.  flag[0] = 1 + column on failure.
+void cholesky_dev_f32(int n, const double2* O, double2* XiH, int* flag, cudaStream_t st);
 // Blocked multi-block Cholesky inverse for any n (FP32 or FP64 arithmetic);
 // work: cholesky_big_work_bytes(n, fp64).
 size_t cholesky_big_work_bytes(int n, bool fp64);
