@@ -1013,51 +1013,65 @@ __global__ void k_expm_square(int n, const double2* __restrict__ E, double2* __r
     Eout[idx] = make_double2(sr, si);
 }
 
+
 // exp(s A) for n <= kSmallN in single precision, one block, all in shared
-// memory: X = s A / 2^q (||s A||_1 / 2^q <= 1/4), Taylor degree 8 by Horner
-// (truncation below 1e-11), q squarings.  Used by the mixed-precision path, whose orbitals are
-// re-orthonormalised after every rotation.
+// memory: X = s A / 2^q (||s A||_1 / 2^q <= 1/4), Taylor degree 8
+// (truncation below 1e-11, so that the squarings amplify FP32 rounding
+// alone), q squarings.  Used by the mixed-precision path, whose orbitals
+// are re-orthonormalised after every rotation.
 // C = A B + a0 I + a1 X + a2 X2 for n x n column-major matrices in shared
-// memory (A, B may be null: no product); each thread computes a 2 x 2 block
-// of C with fused multiply-adds.
-__device__ __forceinline__ void smem_mm_poly(int n, const float2* A, const float2* B, const float2* X,
+// memory with an even leading dimension ldm (A, B may be null: no product).
+// Thread t < ceil(n/2) ceil(n/4) keeps a 2 x 4 block of C (rows 2 r, 2 r + 1
+// read as one 16-byte load, four columns) in registers.
+__device__ __forceinline__ void smem_mm_poly(int n, int ldm, const float2* A, const float2* B, const float2* X,
                                              const float2* X2, float a0, float a1, float a2, float2* C) {
-    const int h = (n + 1) / 2;
-    for (int t = threadIdx.x; t < h * h; t += blockDim.x) {
-        const int m = 2 * (t % h), c = 2 * (t / h);
-        const bool m1 = m + 1 < n, c1 = c + 1 < n;
-        float2 s[2][2];
+    const int h = (n + 1) / 2, qn = (n + 3) / 4;
+    for (int t = threadIdx.x; t < h * qn; t += blockDim.x) {
+        const int m = 2 * (t % h), c0 = 4 * (t / h);
+        float2 s[2][4];
+        int cl[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) cl[v] = min(c0 + v, n - 1);
 #pragma unroll
         for (int u = 0; u < 2; ++u)
 #pragma unroll
-            for (int v = 0; v < 2; ++v) {
-                const int mm = m + u, cc = c + v;
+            for (int v = 0; v < 4; ++v) {
+                const int mm = m + u, cc = c0 + v;
                 if (mm < n && cc < n) {
-                    const float2 x = X[cc * n + mm], x2 = X2[cc * n + mm];
+                    const float2 x = X[cc * ldm + mm], x2 = X2[cc * ldm + mm];
                     s[u][v] = make_float2((mm == cc ? a0 : 0.f) + a1 * x.x + a2 * x2.x, a1 * x.y + a2 * x2.y);
                 } else {
                     s[u][v] = make_float2(0.f, 0.f);
                 }
             }
         if (A) {
+#pragma unroll 2
             for (int k = 0; k < n; ++k) {
-                const float2 a[2] = {A[k * n + m], m1 ? A[k * n + m + 1] : make_float2(0.f, 0.f)};
-                const float2 b[2] = {B[c * n + k], c1 ? B[(c + 1) * n + k] : make_float2(0.f, 0.f)};
+                const float4 a = *reinterpret_cast<const float4*>(A + k * ldm + m);
+                float2 b[4];
 #pragma unroll
-                for (int u = 0; u < 2; ++u)
+                for (int v = 0; v < 4; ++v) b[v] = B[cl[v] * ldm + k];
 #pragma unroll
-                    for (int v = 0; v < 2; ++v) {
-                        s[u][v].x = fmaf(a[u].x, b[v].x, s[u][v].x);
-                        s[u][v].x = fmaf(-a[u].y, b[v].y, s[u][v].x);
-                        s[u][v].y = fmaf(a[u].x, b[v].y, s[u][v].y);
-                        s[u][v].y = fmaf(a[u].y, b[v].x, s[u][v].y);
-                    }
+                for (int v = 0; v < 4; ++v) {
+                    s[0][v].x = fmaf(a.x, b[v].x, s[0][v].x);
+                    s[1][v].x = fmaf(a.z, b[v].x, s[1][v].x);
+                    s[0][v].y = fmaf(a.x, b[v].y, s[0][v].y);
+                    s[1][v].y = fmaf(a.z, b[v].y, s[1][v].y);
+                }
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    s[0][v].x = fmaf(-a.y, b[v].y, s[0][v].x);
+                    s[1][v].x = fmaf(-a.w, b[v].y, s[1][v].x);
+                    s[0][v].y = fmaf(a.y, b[v].x, s[0][v].y);
+                    s[1][v].y = fmaf(a.w, b[v].x, s[1][v].y);
+                }
             }
         }
-        C[c * n + m] = s[0][0];
-        if (c1) C[(c + 1) * n + m] = s[0][1];
-        if (m1) C[c * n + m + 1] = s[1][0];
-        if (m1 && c1) C[(c + 1) * n + m + 1] = s[1][1];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+                if (m + u < n && c0 + v < n) C[(c0 + v) * ldm + m + u] = s[u][v];
     }
 }
 
@@ -1065,21 +1079,27 @@ __device__ __forceinline__ void smem_mm_poly(int n, const float2* A, const float
 // 1/4, the degree-8 Taylor polynomial in Paterson-Stockmeyer form
 // T8 = B0 + X^3 (B1 + X^3 B2) with B0 = I + X + X^2/2, B1 = I/3! + X/4! +
 // X^2/5!, B2 = I/6! + X/7! + X^2/8! (four products instead of seven), then q
-// squarings.  Truncation error <= (1/4)^9 / 9! < 1e-11.
-__global__ void __launch_bounds__(1024) k_expm_small_f32(int n, const double2* __restrict__ A,
-                                                         const double* __restrict__ s, double2* __restrict__ E) {
+// squarings.
+constexpr int kExpmThreads = 256;
+__global__ void __launch_bounds__(kExpmThreads) k_expm_small_f32(int n, const double2* __restrict__ A,
+                                                                 const double* __restrict__ s,
+                                                                 double2* __restrict__ E) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nn = n * n;
+    const int ldm = (n + 1) & ~1;
+    const int nn = ldm * ldm;
     float2* X = reinterpret_cast<float2*>(smem_raw);
     float2* X2 = X + nn;
     float2* X3 = X2 + nn;
     float2* T1 = X3 + nn;
     float2* T2 = T1 + nn;
-    __shared__ float wmax[32];
+    __shared__ float wmax[kExpmThreads / 32];
     __shared__ int qs;
-    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < 5 * nn; idx += blockDim.x) X[idx] = make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int r = idx % n, c = idx / n;
         const double2 a = A[idx];
-        X[idx] = make_float2((float)a.x, (float)a.y);
+        X[c * ldm + r] = make_float2((float)a.x, (float)a.y);
     }
     __syncthreads();
     // 1-norm: one warp per column, lanes over rows
@@ -1088,7 +1108,7 @@ __global__ void __launch_bounds__(1024) k_expm_small_f32(int n, const double2* _
     for (int c = warp; c < n; c += nw) {
         float sum = 0.f;
         for (int r = lane; r < n; r += 32) {
-            const float2 a = X[c * n + r];
+            const float2 a = X[c * ldm + r];
             sum += sqrtf(a.x * a.x + a.y * a.y);
         }
 #pragma unroll
@@ -1115,37 +1135,37 @@ __global__ void __launch_bounds__(1024) k_expm_small_f32(int n, const double2* _
     __syncthreads();
     constexpr float c3 = 1.f / 6.f, c4 = 1.f / 24.f, c5 = 1.f / 120.f, c6 = 1.f / 720.f, c7 = 1.f / 5040.f,
                     c8 = 1.f / 40320.f;
-    smem_mm_poly(n, X, X, X, X, 0.f, 0.f, 0.f, X2);                  // X^2
+    smem_mm_poly(n, ldm, X, X, X, X, 0.f, 0.f, 0.f, X2);                  // X^2
     __syncthreads();
-    smem_mm_poly(n, X2, X, X, X2, 0.f, 0.f, 0.f, X3);                // X^3
-    smem_mm_poly(n, nullptr, nullptr, X, X2, c6, c7, c8, T1);        // B2 (independent of X^3)
+    smem_mm_poly(n, ldm, X2, X, X, X2, 0.f, 0.f, 0.f, X3);                // X^3
+    smem_mm_poly(n, ldm, nullptr, nullptr, X, X2, c6, c7, c8, T1);        // B2 (independent of X^3)
     __syncthreads();
-    smem_mm_poly(n, X3, T1, X, X2, c3, c4, c5, T2);                  // B1 + X^3 B2
+    smem_mm_poly(n, ldm, X3, T1, X, X2, c3, c4, c5, T2);                  // B1 + X^3 B2
     __syncthreads();
-    smem_mm_poly(n, X3, T2, X, X2, 1.f, 1.f, 0.5f, T1);              // B0 + X^3 (...)
+    smem_mm_poly(n, ldm, X3, T2, X, X2, 1.f, 1.f, 0.5f, T1);              // B0 + X^3 (...)
     __syncthreads();
     float2* P = T1;
     float2* Q = T2;
     for (int r = 0; r < q; ++r) {
-        smem_mm_poly(n, P, P, X, X2, 0.f, 0.f, 0.f, Q);
+        smem_mm_poly(n, ldm, P, P, X, X2, 0.f, 0.f, 0.f, Q);
         __syncthreads();
         float2* t = P;
         P = Q;
         Q = t;
     }
-    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) E[idx] = make_double2(P[idx].x, P[idx].y);
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int r = idx % n, c = idx / n;
+        const float2 v = P[c * ldm + r];
+        E[idx] = make_double2(v.x, v.y);
+    }
 }
 
 bool expm_small_f32(int n, const double2* A, const double* scale_dev, double2* E, cudaStream_t st) {
     if (n > kSmallN) return false;
-    const size_t sm = sizeof(float2) * 5 * n * n;
+    const int ldm = (n + 1) & ~1;
+    const size_t sm = sizeof(float2) * 5 * ldm * ldm;
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_expm_small_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    // one thread per 2 x 2 output block, whole warps, at least two warps
-    const int h = (n + 1) / 2;
-    int threads = ((h * h + 31) / 32) * 32;
-    if (threads < 64) threads = 64;
-    if (threads > 1024) threads = 1024;
-    roks::count_launch(), k_expm_small_f32<<<1, threads, sm, st>>>(n, A, scale_dev, E);
+    roks::count_launch(), k_expm_small_f32<<<1, kExpmThreads, sm, st>>>(n, A, scale_dev, E);
     return true;
 }
 

@@ -99,6 +99,10 @@ struct roks_ctx {
     // second time in a row the same orbital buffer is stepped, replayed on st
     bool graphs = true;
     cudaStream_t cap_st = nullptr;
+    // the rotation exponential (one SM) runs on a side stream beside the
+    // band-block updates that do not need it
+    cudaStream_t side_st = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     cudaGraphExec_t pcg_exec = nullptr;
     const void* graph_psi = nullptr;
     const void* last_psi = nullptr;
@@ -432,7 +436,40 @@ struct Impl {
         sum_to(ctx->d_colout, ctx->nb, reinterpret_cast<double*>(ctx->d_sc) + field, 1.0, ctx->st);
     }
 
-    // out = orth((psi + step s) exp(step Atot)); energies of out in d_E.
+    // U = exp(step A_tot) on the side stream, after everything already
+    // enqueued on st; join_U makes st wait for it.
+    static roks_status fork_U(roks_ctx* ctx, int step_field) {
+        const int nb = ctx->nb;
+        double* scd = reinterpret_cast<double*>(ctx->d_sc);
+        if (!ctx->side_st) {
+            CK(cudaStreamCreateWithFlags(&ctx->side_st, cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming));
+        }
+        CK(cudaEventRecord(ctx->fork_ev, ctx->st));
+        CK(cudaStreamWaitEvent(ctx->side_st, ctx->fork_ev, 0));
+        cudaStream_t ss = ctx->side_st;
+        if (nb > 64) {
+            expm_big(nb, ctx->d_Atot, scd + step_field, ctx->d_U, ctx->d_bigwork, ctx->d_expm_info,
+                     ctx->prec == ROKS_FP64, ss);
+        } else {
+            const bool small32 =
+                (ctx->prec == ROKS_MIXED) && expm_small_f32(nb, ctx->d_Atot, scd + step_field, ctx->d_U, ss);
+            if (!small32)
+                expm_scaled(nb, ctx->d_Atot, scd + step_field, ctx->d_U, ctx->d_e1, ctx->d_e2, ctx->d_e3,
+                            ctx->d_expm_info, ss);
+        }
+        CK(cudaGetLastError());
+        CK(cudaEventRecord(ctx->join_ev, ss));
+        return ROKS_OK;
+    }
+    static roks_status join_U(roks_ctx* ctx) {
+        CK(cudaStreamWaitEvent(ctx->st, ctx->join_ev, 0));
+        return ROKS_OK;
+    }
+
+    // out = orth((psi + step s) exp(step Atot)), U forked before (fork_U);
+    // energies of out in d_E.
     static roks_status move(roks_ctx* ctx, const void* psi, int64_t ld, int step_field, void* out, int64_t ldo) {
         cudaStream_t st = ctx->st;
         const int nb = ctx->nb;
@@ -441,16 +478,8 @@ struct Impl {
         {
             PROF("rotate");
             axpy<T>(ctx->npw, nb, ccv(psi), ld, ccv(ctx->W_s), l, scd + step_field, 1.0, cv(ctx->W_Y), l, st);
-            if (nb > 64) {
-                expm_big(nb, ctx->d_Atot, scd + step_field, ctx->d_U, ctx->d_bigwork, ctx->d_expm_info,
-                         ctx->prec == ROKS_FP64, st);
-            } else {
-                const bool small32 = (ctx->prec == ROKS_MIXED) &&
-                                     expm_small_f32(nb, ctx->d_Atot, scd + step_field, ctx->d_U, st);
-                if (!small32)
-                    expm_scaled(nb, ctx->d_Atot, scd + step_field, ctx->d_U, ctx->d_e1, ctx->d_e2, ctx->d_e3,
-                                ctx->d_expm_info, st);
-            }
+            roks_status r = join_U(ctx);
+            if (r != ROKS_OK) return r;
             gemm_nn<T>(ctx->npw, nb, nb, ccv(ctx->W_Y), l, ctx->d_U, nb, cv(ctx->W_Y2), l, 1.0, 0.0, ctx->d_gemm_work, st);
         }
         roks_status r = orth(ctx, ctx->W_Y2, l, out, ldo, ctx->d_B);
@@ -509,16 +538,20 @@ struct Impl {
         dot_to(ctx, ctx->W_K, ctx->W_G, SC_FIELD(a1));
         dot_to(ctx, ctx->W_v, ctx->W_G, SC_FIELD(a2));
         pcg_direction(ctx->d_sc, st);
-        // s = u + beta v, A_tot = rot (A + beta A_prev)
+        // A_tot = rot (A + beta A_prev) and its exponential beside s = u + beta v
+        pcg_total_rotation(nb, ctx->d_A, ctx->d_Aprev, ctx->d_sc, ctx->d_Atot, st);
+        r = fork_U(ctx, SC_FIELD(dt));
+        if (r != ROKS_OK) return r;
         axpy<T>(npw, nb, ccv(ctx->W_K), l, ccv(ctx->W_v), l, reinterpret_cast<double*>(ctx->d_sc) + SC_FIELD(beta),
                 1.0, cv(ctx->W_s), l, st);
-        pcg_total_rotation(nb, ctx->d_A, ctx->d_Aprev, ctx->d_sc, ctx->d_Atot, st);
         // trial point
         r = move(ctx, psi, ld, SC_FIELD(dt), ctx->W_F, l);
         if (r != ROKS_OK) return r;
         pcg_take_energy(ctx->d_E, ctx->d_sc, SC_FIELD(Et), st);
         pcg_line_search(ctx->d_sc, st);
         // accepted point (written to W_F, then copied over psi)
+        r = fork_U(ctx, SC_FIELD(step));
+        if (r != ROKS_OK) return r;
         r = move(ctx, psi, ld, SC_FIELD(step), ctx->W_F, l);
         if (r != ROKS_OK) return r;
         pcg_take_energy(ctx->d_E, ctx->d_sc, SC_FIELD(Enew), st);
@@ -1266,6 +1299,9 @@ void roks_destroy(roks_ctx* ctx) {
     if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
     if (ctx->h_sc) cudaFreeHost(ctx->h_sc);
     if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
+    if (ctx->side_st) cudaStreamDestroy(ctx->side_st);
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+    if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
     for (void* p : ctx->allocs) cudaFree(p);
     for (const auto& r : ctx->prof_recs) {
         cudaEventDestroy(r.a);
