@@ -685,6 +685,50 @@ void small_gemm(int M, int N, int K, const double2* A, int lda, bool ca, const d
     roks::count_launch(), k_small_gemm<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(M, N, K, A, lda, ca, B, ldb, cb, C, ldc, alpha, beta);
 }
 
+// Same product with FP32 arithmetic on FP64 storage (the mixed-precision
+// path): the conversions are once per loaded element, the dot products and
+// the shuffle reduction in FP32, alpha and beta applied in FP64.
+__global__ void k_small_gemm_f32(int M, int N, int K, const double2* __restrict__ A, int lda, int ca,
+                                 const double2* __restrict__ B, int ldb, int cb, double2* __restrict__ C, int ldc,
+                                 double alpha, double beta) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= M * N) return;
+    const int m = warp % M, n = warp / M;
+    float sr = 0.f, si = 0.f;
+    for (int k = lane; k < K; k += 32) {
+        const double2 ad = ca ? A[(int64_t)m * lda + k] : A[(int64_t)k * lda + m];
+        const double2 bd = cb ? B[(int64_t)k * ldb + n] : B[(int64_t)n * ldb + k];
+        const float ax = (float)ad.x, ay = ca ? -(float)ad.y : (float)ad.y;
+        const float bx = (float)bd.x, by = cb ? -(float)bd.y : (float)bd.y;
+        sr = fmaf(ax, bx, sr);
+        sr = fmaf(-ay, by, sr);
+        si = fmaf(ax, by, si);
+        si = fmaf(ay, bx, si);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    if (lane != 0) return;
+    double2* c = C + (int64_t)n * ldc + m;
+    double2 r = make_double2(alpha * (double)sr, alpha * (double)si);
+    if (beta != 0.0) {
+        r.x += beta * c->x;
+        r.y += beta * c->y;
+    }
+    *c = r;
+}
+
+void small_gemm_f32(int M, int N, int K, const double2* A, int lda, bool ca, const double2* B, int ldb, bool cb,
+                    double2* C, int ldc, double alpha, double beta, cudaStream_t st) {
+    if (M <= 0 || N <= 0) return;
+    const long long threads = (long long)M * N * 32;
+    roks::count_launch(), k_small_gemm_f32<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+                              M, N, K, A, lda, ca, B, ldb, cb, C, ldc, alpha, beta);
+}
+
 // Cholesky inverse held in shared memory (n <= kSmallN), FP64: right-looking
 // factorisation O = L L^H (two barriers per column), then X = L^{-1} by
 // forward substitution with one warp per column (lanes split the dot

@@ -173,6 +173,9 @@ void gemm_nn_io(int M, int N, int K, const c2<T>* A, int64_t lda, const double2*
 // ------------------------------------------------------------ small FP64 matrices (n x n, column major)
 void small_gemm(int M, int N, int K, const double2* A, int lda, bool ca, const double2* B, int ldb,
                 bool cb, double2* C, int ldc, double alpha, double beta, cudaStream_t st);
+// Same with FP32 arithmetic (FP64 storage, alpha and beta applied in FP64).
+void small_gemm_f32(int M, int N, int K, const double2* A, int lda, bool ca, const double2* B, int ldb, bool cb,
+                    double2* C, int ldc, double alpha, double beta, cudaStream_t st);
 // O (Hermitian) -> LinvH = L^{-H}, L L^H = O.  flag[0] set to 1 + column on failure.
 void cholesky_inverse(int n, const double2* O, double2* Lw, double2* LinvH, int* flag, cudaStream_t st);
 // n within the single-block factorisations
