@@ -479,8 +479,9 @@ constexpr int kPotBlocks = 512;
 template <typename T>
 void potentials(int N, double L, const double* rho3, const T* vloc, const PotCoef& cf, c2<T>* grid,
                 T* xc3, const c2<T>* tw, T* Vk, double* Vk64, double* part, double* out6,
-                cudaStream_t st) {
-    // out6: [E_x^M, E_x^T, E_loc, E_H, <a|V^c|a>, <b|V^c|b>]
+                cudaStream_t st, bool energies_only) {
+    // out6: [E_x^M, E_x^T, E_loc, E_H, <a|V^c|a>, <b|V^c|b>]; energies_only
+    // stops after E_H (out6[4..5] and Vk are left as they were)
     const int N3 = N * N * N;
     const double dvol = L * L * L / double(N3);
     const double c6 = std::cbrt(6.0 / kPi);                 // (6 / pi)^{1/3}
@@ -501,6 +502,7 @@ void potentials(int N, double L, const double* rho3, const T* vloc, const PotCoe
     roks::count_launch(), k_hartree_G<T><<<kPotBlocks, RB, 0, st>>>(N, T(1.0 / double(N3)), T(4.0 * kPi / (b * b)),
                                                                      grid, part);
     roks::count_launch(), k_partials_final<<<1, RB, 0, st>>>(kPotBlocks, 1, part, out6 + 3, 0.5 * L * L * L, 0, 0, 0);
+    if (energies_only) return;
     grid_fft3<T>(N, tw, grid, +1, st);
     roks::count_launch(), k_pot_class<T><<<kPotBlocks, RB, 0, st>>>(N3, vloc, grid, xc3, r3, cf, Vk, Vk64, part);
     roks::count_launch(), k_partials_final<<<2, RB, 0, st>>>(kPotBlocks, 2, part, out6 + 4, dvol, dvol, 0, 0);
@@ -530,7 +532,7 @@ void axpy(int npw, int nb, const c2<T>* x, int64_t ldx, const c2<T>* y, int64_t 
     template void column_sums<T>(int, int, int, const c2<T>*, int64_t, const c2<T>*, int64_t, const T*,       \
                                  double*, double*, cudaStream_t);                                              \
     template void potentials<T>(int, double, const double*, const T*, const PotCoef&, c2<T>*, T*,             \
-                                const c2<T>*, T*, double*, double*, double*, cudaStream_t);                   \
+                                const c2<T>*, T*, double*, double*, double*, cudaStream_t, bool);             \
     template void precondition<T>(int, int, const c2<T>*, int64_t, const T*, const double*, c2<T>*,           \
                                   int64_t, cudaStream_t);                                                      \
     template void axpy<T>(int, int, const c2<T>*, int64_t, const c2<T>*, int64_t, const double*, double,      \

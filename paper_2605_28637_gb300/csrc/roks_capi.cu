@@ -278,12 +278,14 @@ struct Impl {
         return ROKS_OK;
     }
 
-    static roks_status potential(roks_ctx* ctx) {
+    // energies_only: the energy of the density (out6[0..3], d_E) without the
+    // class potentials, for points whose potentials no apply will use
+    static roks_status potential(roks_ctx* ctx, bool energies_only = false) {
         cudaStream_t st = ctx->st;
         PROF("potential");
         potentials<T>(ctx->N, ctx->L, ctx->d_rho3, static_cast<const T*>(ctx->d_vloc_t), ctx->cf,
                       reinterpret_cast<V*>(ctx->d_grid), reinterpret_cast<T*>(ctx->d_xc3), ccv(ctx->d_tw),
-                      static_cast<T*>(ctx->d_Vk), nullptr, ctx->d_part, ctx->d_out6, st);
+                      static_cast<T*>(ctx->d_Vk), nullptr, ctx->d_part, ctx->d_out6, st, energies_only);
         energy_combine(ctx->d_kin_b, ctx->d_nl_b, ctx->nb, ctx->d_wband, ctx->d_out6, ctx->cM, ctx->cT,
                        ctx->alpha, ctx->alpha != 0.0 ? ctx->d_hf2 : nullptr, ctx->d_E, st);
         CK(cudaGetLastError());
@@ -470,8 +472,9 @@ struct Impl {
     }
 
     // out = orth((psi + step s) exp(step Atot)), U forked before (fork_U);
-    // energies of out in d_E.
-    static roks_status move(roks_ctx* ctx, const void* psi, int64_t ld, int step_field, void* out, int64_t ldo) {
+    // energies of out in d_E (and its potentials unless energies_only).
+    static roks_status move(roks_ctx* ctx, const void* psi, int64_t ld, int step_field, void* out, int64_t ldo,
+                            bool energies_only = false) {
         cudaStream_t st = ctx->st;
         const int nb = ctx->nb;
         const int64_t l = ctx->ld_min;
@@ -487,7 +490,7 @@ struct Impl {
         if (r != ROKS_OK) return r;
         r = density(ctx, out, ldo, ctx->nproj > 0 ? ctx->d_B : nullptr);
         if (r != ROKS_OK) return r;
-        return potential(ctx);
+        return potential(ctx, energies_only);
     }
 
     // The device work of one PCG iteration from a valid potential: no host
@@ -545,8 +548,8 @@ struct Impl {
         if (r != ROKS_OK) return r;
         axpy<T>(npw, nb, ccv(ctx->W_K), l, ccv(ctx->W_v), l, reinterpret_cast<double*>(ctx->d_sc) + SC_FIELD(beta),
                 1.0, cv(ctx->W_s), l, st);
-        // trial point
-        r = move(ctx, psi, ld, SC_FIELD(dt), ctx->W_F, l);
+        // trial point: its energy alone (the accepted point's potentials replace it)
+        r = move(ctx, psi, ld, SC_FIELD(dt), ctx->W_F, l, true);
         if (r != ROKS_OK) return r;
         pcg_take_energy(ctx->d_E, ctx->d_sc, SC_FIELD(Et), st);
         pcg_line_search(ctx->d_sc, st);

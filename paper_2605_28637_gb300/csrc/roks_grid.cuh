@@ -47,11 +47,12 @@ template <typename T>
 void density_to_f64(int64_t n, const double* rho3, double* out, cudaStream_t st);
 // Grid transforms in the element type T (FP32 for the mixed path), energies
 // in FP64.  rho3 in DensAcc<T> storage; vloc and the exchange-correlation
-// fields xc3 (3 x N^3) in the element type T.
+// fields xc3 (3 x N^3) in the element type T.  energies_only: out6[0..3]
+// alone (no inverse transform, no class potentials Vk).
 template <typename T>
 void potentials(int N, double L, const double* rho3, const T* vloc, const PotCoef& cf, c2<T>* grid,
                 T* xc3, const c2<T>* tw, T* Vk, double* Vk64, double* part, double* out6,
-                cudaStream_t st);
+                cudaStream_t st, bool energies_only = false);
 size_t potentials_part_elems();
 template <typename T>
 void precondition(int npw, int nb, const c2<T>* gI, int64_t ld, const T* g2h, const double* sums, c2<T>* out,
