@@ -286,6 +286,18 @@ def converge(cfg, precision, cap, torch, max_seconds, params=None):
     out = {"seconds": dt, "iterations": it, "converged": bool(info and info["converged"]),
            "E_final": info["E_new"] if info else None, "grad_norm_final": info["grad_norm"] if info else None,
            "s_per_iter": dt / max(it, 1)}
+    if precision == "mixed" and info is not None:
+        # the final orbitals re-evaluated in FP64 (orthonormalised there first):
+        # a mixed leg's energy must be that of its own state, not an FP32 artefact
+        c64 = roks.Context(cfg, "fp64")
+        p64 = c64.new_bands()
+        p64[:, :ctx.npw] = psi[:, :ctx.npw].to(p64.dtype)
+        torch.cuda.synchronize()
+        roks.roks_orthonormalize(c64.ctx, p64, c64.ld)
+        c64.density(p64)
+        out["E_final_fp64_eval"] = c64.potential()["E_total"]
+        out["dE_mixed_vs_fp64_eval"] = out["E_final"] - out["E_final_fp64_eval"]
+        c64.close()
     ctx.close()
     return out
 
