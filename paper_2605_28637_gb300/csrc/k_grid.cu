@@ -188,6 +188,28 @@ __global__ void k_colred_final(int count, int nsplit, const double* __restrict__
     out[i] = (s0 + s1) + (s2 + s3);
 }
 
+// dst = scale * sum over the columns of their nsplit partials (nsplit a
+// multiple of 4), in the order of k_colred_final then k_sum_to: lane l sums
+// columns l, l + 32, ..., each as four interleaved chains, then a shuffle tree.
+__global__ void k_colred_total(int count, int nsplit, const double* __restrict__ part, double* dst, double scale) {
+    const int lane = threadIdx.x;
+    double s = 0;
+    for (int i = lane; i < count; i += 32) {
+        const double* p = part + (int64_t)i * nsplit;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        for (int k = 0; k < nsplit; k += 4) {
+            s0 += p[k];
+            s1 += p[k + 1];
+            s2 += p[k + 2];
+            s3 += p[k + 3];
+        }
+        s += (s0 + s1) + (s2 + s3);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) dst[0] = scale * s;
+}
+
 template <typename T>
 void column_sums(int op, int npw, int nb, const c2<T>* x, int64_t ldx, const c2<T>* y, int64_t ldy,
                  const T* g2, double* part, double* out, cudaStream_t st) {
@@ -201,6 +223,16 @@ void column_sums(int op, int npw, int nb, const c2<T>* x, int64_t ldx, const c2<
     }
     const int count = (op == 1 ? 2 : 1) * nb;
     roks::count_launch(), k_colred_final<<<(count + 127) / 128, 128, 0, st>>>(count, nsplit, part, out);
+}
+
+template <typename T>
+void column_total(int op, int npw, int nb, const c2<T>* x, int64_t ldx, const c2<T>* y, int64_t ldy, const T* g2,
+                  double* part, double* dst, double scale, cudaStream_t st) {
+    constexpr int nsplit = 16;
+    dim3 g(nb, nsplit);
+    if (op == 2) roks::count_launch(), k_colred<T, 2><<<g, RB, 0, st>>>(npw, nb, x, ldx, y, ldy, g2, nsplit, part);
+    else roks::count_launch(), k_colred<T, 3><<<g, RB, 0, st>>>(npw, nb, x, ldx, y, ldy, g2, nsplit, part);
+    roks::count_launch(), k_colred_total<<<1, 32, 0, st>>>(nb, nsplit, part, dst, scale);
 }
 
 // ------------------------------------------------------------------ projector blocks
@@ -531,6 +563,8 @@ void axpy(int npw, int nb, const c2<T>* x, int64_t ldx, const c2<T>* y, int64_t 
     template void to_real_type<T>(int64_t, const double*, T*, double, cudaStream_t);                           \
     template void column_sums<T>(int, int, int, const c2<T>*, int64_t, const c2<T>*, int64_t, const T*,       \
                                  double*, double*, cudaStream_t);                                              \
+    template void column_total<T>(int, int, int, const c2<T>*, int64_t, const c2<T>*, int64_t, const T*,      \
+                                  double*, double*, double, cudaStream_t);                                     \
     template void potentials<T>(int, double, const double*, const T*, const PotCoef&, c2<T>*, T*,             \
                                 const c2<T>*, T*, double*, double*, double*, cudaStream_t, bool);             \
     template void precondition<T>(int, int, const c2<T>*, int64_t, const T*, const double*, c2<T>*,           \

@@ -427,16 +427,15 @@ struct Impl {
         PROF("subspace_project");
         gemm_cn<T>(nb, nb, ctx->npw, ccv(ctx->W_S), l, ccv(x), l, ctx->d_Msm, nb, ctx->d_gemm_work,
                    ctx->gemm_work_elems, st);
-        if (out != x)
-            cudaMemcpyAsync(out, x, sizeof(V) * l * nb, cudaMemcpyDeviceToDevice, st);
-        gemm_nn<T>(ctx->npw, nb, nb, ccv(psi), ld, ctx->d_Msm, nb, cv(out), l, -1.0, 1.0, ctx->d_gemm_work, st);
+        gemm_nn_io<T>(ctx->npw, nb, nb, ccv(psi), ld, ctx->d_Msm, nb, ccv(x), l, cv(out), l, -1.0, 1.0,
+                      ctx->d_gemm_work, st);
     }
 
     // dst field = sum_n Re <x_n|y_n>
     static void dot_to(roks_ctx* ctx, const void* x, const void* y, int field) {
         const int64_t l = ctx->ld_min;
-        column_sums<T>(2, ctx->npw, ctx->nb, ccv(x), l, ccv(y), l, static_cast<const T*>(ctx->d_g2half), ctx->d_colpart, ctx->d_colout, ctx->st);
-        sum_to(ctx->d_colout, ctx->nb, reinterpret_cast<double*>(ctx->d_sc) + field, 1.0, ctx->st);
+        column_total<T>(2, ctx->npw, ctx->nb, ccv(x), l, ccv(y), l, static_cast<const T*>(ctx->d_g2half),
+                        ctx->d_colpart, reinterpret_cast<double*>(ctx->d_sc) + field, 1.0, ctx->st);
     }
 
     // U = exp(step A_tot) on the side stream, after everything already
@@ -518,12 +517,12 @@ struct Impl {
         // G = F - S Gam ; gI = F - S theta
         {
         PROF("gradient_precond");
-        CK(cudaMemcpyAsync(ctx->W_G, ctx->W_F, sizeof(V) * l * nb, cudaMemcpyDeviceToDevice, st));
-        gemm_nn<T>(npw, nb, nb, ccv(ctx->W_S), l, ctx->d_Gam, nb, cv(ctx->W_G), l, -1.0, 1.0, ctx->d_gemm_work, st);
-        CK(cudaMemcpyAsync(ctx->W_gI, ctx->W_F, sizeof(V) * l * nb, cudaMemcpyDeviceToDevice, st));
-        gemm_nn<T>(npw, nb, nb, ccv(ctx->W_S), l, ctx->d_Th, nb, cv(ctx->W_gI), l, -1.0, 1.0, ctx->d_gemm_work, st);
-        column_sums<T>(3, npw, nb, ccv(ctx->W_G), l, nullptr, 0, static_cast<const T*>(ctx->d_g2half), ctx->d_colpart, ctx->d_colout, st);
-        sum_to(ctx->d_colout, nb, reinterpret_cast<double*>(ctx->d_sc) + SC_FIELD(gnorm2), 1.0, st);
+        gemm_nn_io<T>(npw, nb, nb, ccv(ctx->W_S), l, ctx->d_Gam, nb, ccv(ctx->W_F), l, cv(ctx->W_G), l, -1.0, 1.0,
+                      ctx->d_gemm_work, st);
+        gemm_nn_io<T>(npw, nb, nb, ccv(ctx->W_S), l, ctx->d_Th, nb, ccv(ctx->W_F), l, cv(ctx->W_gI), l, -1.0, 1.0,
+                      ctx->d_gemm_work, st);
+        column_total<T>(3, npw, nb, ccv(ctx->W_G), l, nullptr, 0, static_cast<const T*>(ctx->d_g2half), ctx->d_colpart,
+                        reinterpret_cast<double*>(ctx->d_sc) + SC_FIELD(gnorm2), 1.0, st);
         // p_I = K g_I - Psi (S Psi)^H K g_I
         column_sums<T>(1, npw, nb, ccv(ctx->W_gI), l, nullptr, 0, static_cast<const T*>(ctx->d_g2half), ctx->d_colpart, ctx->d_colout, st);
         if (ctx->mlp_kind == ROKS_PRECOND_TPA_MLP)

@@ -39,6 +39,11 @@ void to_real_type(int64_t n, const double* in, T* out, double scale, cudaStream_
 template <typename T>
 void column_sums(int op, int npw, int nb, const c2<T>* x, int64_t ldx, const c2<T>* y, int64_t ldy,
                  const T* g2h, double* part, double* out, cudaStream_t st);
+// dst = scale * sum over the columns of column_sums' op 2 or 3 (out unused),
+// summed in the same order as column_sums followed by sum_to.
+template <typename T>
+void column_total(int op, int npw, int nb, const c2<T>* x, int64_t ldx, const c2<T>* y, int64_t ldy,
+                  const T* g2h, double* part, double* dst, double scale, cudaStream_t st);
 void apply_DQ(int nproj, int nb, const double2* B, const int* blk_off, const int* blk_n, const double* Drow,
               const double* Qrow, const double* wband, double2* DB, double2* QB, cudaStream_t st);
 void band_quadratic(int nproj, int nb, const double2* B, const double2* DB, double* out, cudaStream_t st);
