@@ -39,20 +39,30 @@ __global__ void __launch_bounds__(kThreads) k_band_z_inv(Sphere s, const c2<T>* 
     extern __shared__ __align__(16) unsigned char smem[];
     V* buf = reinterpret_cast<V*>(smem);
     V* tws = buf + N * LS;
+    __shared__ int cstart[TL], ckmax[TL];
     load_twiddles<V, N>(tws, tw);
     const int c0 = blockIdx.x * TL;
     const int bb = blockIdx.y;
     const V* p = psi + (int64_t)(b0 + bb) * ld;
-    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
-        const int line = idx / N, e = idx - line * N;
-        const int c = c0 + line;
-        V v = mk<T>(T(0), T(0));
-        if (c < s.ncol) {
+    // the lines' column descriptors once per block; then every coefficient
+    // load of a thread is independent of the others (all in flight at once)
+    if (threadIdx.x < TL) {
+        const int c = c0 + threadIdx.x;
+        cstart[threadIdx.x] = c < s.ncol ? s.col_start[c] : 0;
+        ckmax[threadIdx.x] = c < s.ncol ? s.col_kmax[c] : -1;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < (TL * N + kThreads - 1) / kThreads; ++r) {
+        const int idx = threadIdx.x + r * kThreads;
+        if (idx < TL * N) {
+            const int line = idx / N, e = idx - line * N;
             const int k = signed_freq(e, N);
-            const int km = s.col_kmax[c];
-            if (k >= -km && k <= km) v = p[s.col_start[c] + k + km];
+            const int km = ckmax[line];
+            V v = mk<T>(T(0), T(0));
+            if (k >= -km && k <= km) v = p[cstart[line] + k + km];
+            buf[e * LS + line] = v;
         }
-        buf[e * LS + line] = v;
     }
     __syncthreads();
     tile_fft<V, N, +1, TL, LS, kThreads>(buf, tws);
@@ -76,15 +86,25 @@ __global__ void __launch_bounds__(kThreads) k_band_z_fwd(Sphere s, const c2<T>* 
     extern __shared__ __align__(16) unsigned char smem[];
     V* buf = reinterpret_cast<V*>(smem);
     V* tws = buf + N * LS;
+    __shared__ int cstart[TL], ckmax[TL];
     load_twiddles<V, N>(tws, tw);
     const int c0 = blockIdx.x * TL;
     const int bb = blockIdx.y;
     const int b = b0 + bb;
     const V* in = Zc + (int64_t)bb * s.ncol * N;
-    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
-        const int line = idx / N, e = idx - line * N;
-        const int c = c0 + line;
-        buf[e * LS + line] = (c < s.ncol) ? in[(int64_t)c * N + e] : mk<T>(T(0), T(0));
+    if (threadIdx.x < TL) {
+        const int c = c0 + threadIdx.x;
+        cstart[threadIdx.x] = c < s.ncol ? s.col_start[c] : 0;
+        ckmax[threadIdx.x] = c < s.ncol ? s.col_kmax[c] : -1;
+    }
+#pragma unroll
+    for (int r = 0; r < (TL * N + kThreads - 1) / kThreads; ++r) {
+        const int idx = threadIdx.x + r * kThreads;
+        if (idx < TL * N) {
+            const int line = idx / N, e = idx - line * N;
+            const int c = c0 + line;
+            buf[e * LS + line] = (c < s.ncol) ? in[(int64_t)c * N + e] : mk<T>(T(0), T(0));
+        }
     }
     __syncthreads();
     tile_fft<V, N, -1, TL, LS, kThreads>(buf, tws);
@@ -92,14 +112,15 @@ __global__ void __launch_bounds__(kThreads) k_band_z_fwd(Sphere s, const c2<T>* 
     const T w = wk[cls];
     V* o = out + (int64_t)b * ldo;
     const V* p = psi + (int64_t)b * ldp;
-    for (int idx = threadIdx.x; idx < TL * N; idx += kThreads) {
-        const int line = idx / N, e = idx - line * N;
-        const int c = c0 + line;
-        if (c < s.ncol) {
+#pragma unroll
+    for (int r = 0; r < (TL * N + kThreads - 1) / kThreads; ++r) {
+        const int idx = threadIdx.x + r * kThreads;
+        if (idx < TL * N) {
+            const int line = idx / N, e = idx - line * N;
             const int k = signed_freq(e, N);
-            const int km = s.col_kmax[c];
+            const int km = ckmax[line];
             if (k >= -km && k <= km) {
-                const int g = s.col_start[c] + k + km;
+                const int g = cstart[line] + k + km;
                 const V loc = buf[e * LS + line];
                 const V ps = p[g];
                 const T kin = w * g2half[g];
