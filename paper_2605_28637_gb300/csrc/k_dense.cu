@@ -8,6 +8,8 @@
 #include <mutex>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "roks_impl.cuh"
 
 namespace roks {
@@ -1058,77 +1060,54 @@ __global__ void k_expm_square(int n, const double2* __restrict__ E, double2* __r
 }
 
 
-// exp(s A) for n <= kSmallN in single precision, one block, all in shared
-// memory: X = s A / 2^q (||s A||_1 / 2^q <= 1/4), Taylor degree 8
-// (truncation below 1e-11, so that the squarings amplify FP32 rounding
-// alone), q squarings.  Used by the mixed-precision path, whose orbitals
-// are re-orthonormalised after every rotation.
-// C = A B + a0 I + a1 X + a2 X2 for n x n column-major matrices in shared
-// memory with an even leading dimension ldm (A, B may be null: no product).
-// Thread t < ceil(n/2) ceil(n/4) keeps a 2 x 4 block of C (rows 2 r, 2 r + 1
-// read as one 16-byte load, four columns) in registers.
-__device__ __forceinline__ void smem_mm_poly(int n, int ldm, const float2* A, const float2* B, const float2* X,
-                                             const float2* X2, float a0, float a1, float a2, float2* C) {
-    const int h = (n + 1) / 2, qn = (n + 3) / 4;
-    for (int t = threadIdx.x; t < h * qn; t += blockDim.x) {
-        const int m = 2 * (t % h), c0 = 4 * (t / h);
-        float2 s[2][4];
-        int cl[4];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) cl[v] = min(c0 + v, n - 1);
-#pragma unroll
-        for (int u = 0; u < 2; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const int mm = m + u, cc = c0 + v;
-                if (mm < n && cc < n) {
-                    const float2 x = X[cc * ldm + mm], x2 = X2[cc * ldm + mm];
-                    s[u][v] = make_float2((mm == cc ? a0 : 0.f) + a1 * x.x + a2 * x2.x, a1 * x.y + a2 * x2.y);
-                } else {
-                    s[u][v] = make_float2(0.f, 0.f);
-                }
-            }
+// exp(s A) for n <= kSmallN in single precision on one thread-block cluster:
+// X = s A / 2^q (||s A||_1 / 2^q <= 1/4), Taylor degree 8 (truncation below
+// 1e-11, so that the squarings amplify FP32 rounding alone), q squarings.
+// Used by the mixed-precision path, whose orbitals are re-orthonormalised
+// after every rotation.
+//
+// Every CTA of the cluster keeps all the n x n matrices (column major,
+// leading dimension ldm) in its shared memory.  A product is split by
+// columns: CTA r computes its slice, one output element per thread, and
+// stores it into the shared memory of every CTA of the cluster; a cluster
+// barrier then publishes the product.  Each output element is accumulated
+// in the same order as by a single block, so the result does not depend on
+// the cluster size.
+constexpr int kExpmCluster = 8;
+constexpr int kExpmThreads = 256;
+namespace cg = cooperative_groups;
+
+// C[:, c0:c1) = A B + a0 I + a1 X + a2 X2 (A, B may be null: no product),
+// written to the C of every CTA in the cluster
+__device__ __forceinline__ void cluster_mm_poly(cg::cluster_group& cluster, int n, int ldm, int c0, int c1,
+                                                const float2* A, const float2* B, const float2* X,
+                                                const float2* X2, float a0, float a1, float a2, float2* C) {
+    const int cols = c1 - c0;
+    for (int t = threadIdx.x; t < n * cols; t += blockDim.x) {
+        const int m = t % n, c = c0 + t / n;
+        const float2 x = X[c * ldm + m], x2 = X2[c * ldm + m];
+        float2 v = make_float2((m == c ? a0 : 0.f) + a1 * x.x + a2 * x2.x, a1 * x.y + a2 * x2.y);
         if (A) {
-#pragma unroll 2
+#pragma unroll 6
             for (int k = 0; k < n; ++k) {
-                const float4 a = *reinterpret_cast<const float4*>(A + k * ldm + m);
-                float2 b[4];
-#pragma unroll
-                for (int v = 0; v < 4; ++v) b[v] = B[cl[v] * ldm + k];
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    s[0][v].x = fmaf(a.x, b[v].x, s[0][v].x);
-                    s[1][v].x = fmaf(a.z, b[v].x, s[1][v].x);
-                    s[0][v].y = fmaf(a.x, b[v].y, s[0][v].y);
-                    s[1][v].y = fmaf(a.z, b[v].y, s[1][v].y);
-                }
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    s[0][v].x = fmaf(-a.y, b[v].y, s[0][v].x);
-                    s[1][v].x = fmaf(-a.w, b[v].y, s[1][v].x);
-                    s[0][v].y = fmaf(a.y, b[v].x, s[0][v].y);
-                    s[1][v].y = fmaf(a.w, b[v].x, s[1][v].y);
-                }
+                const float2 a = A[k * ldm + m], b = B[c * ldm + k];
+                v.x = fmaf(a.x, b.x, v.x);
+                v.y = fmaf(a.x, b.y, v.y);
+                v.x = fmaf(-a.y, b.y, v.x);
+                v.y = fmaf(a.y, b.x, v.y);
             }
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v)
-                if (m + u < n && c0 + v < n) C[(c0 + v) * ldm + m + u] = s[u][v];
+        for (int r = 0; r < kExpmCluster; ++r) cluster.map_shared_rank(C, r)[c * ldm + m] = v;
     }
+    cluster.sync();
 }
 
-// E = exp(s A) in FP32 (n <= kSmallN): scaling by 2^-q until ||s A||_1 <=
-// 1/4, the degree-8 Taylor polynomial in Paterson-Stockmeyer form
-// T8 = B0 + X^3 (B1 + X^3 B2) with B0 = I + X + X^2/2, B1 = I/3! + X/4! +
-// X^2/5!, B2 = I/6! + X/7! + X^2/8! (four products instead of seven), then q
-// squarings.
-constexpr int kExpmThreads = 256;
-__global__ void __launch_bounds__(kExpmThreads) k_expm_small_f32(int n, const double2* __restrict__ A,
-                                                                 const double* __restrict__ s,
-                                                                 double2* __restrict__ E) {
+__global__ void __cluster_dims__(kExpmCluster, 1, 1) __launch_bounds__(kExpmThreads)
+    k_expm_small_f32(int n, const double2* __restrict__ A, const double* __restrict__ s, double2* __restrict__ E) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
     const int ldm = (n + 1) & ~1;
     const int nn = ldm * ldm;
     float2* X = reinterpret_cast<float2*>(smem_raw);
@@ -1138,6 +1117,8 @@ __global__ void __launch_bounds__(kExpmThreads) k_expm_small_f32(int n, const do
     float2* T2 = T1 + nn;
     __shared__ float wmax[kExpmThreads / 32];
     __shared__ int qs;
+    const int cp = (n + kExpmCluster - 1) / kExpmCluster;
+    const int c0 = min(n, rank * cp), c1 = min(n, c0 + cp);
     for (int idx = threadIdx.x; idx < 5 * nn; idx += blockDim.x) X[idx] = make_float2(0.f, 0.f);
     __syncthreads();
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
@@ -1146,7 +1127,7 @@ __global__ void __launch_bounds__(kExpmThreads) k_expm_small_f32(int n, const do
         X[c * ldm + r] = make_float2((float)a.x, (float)a.y);
     }
     __syncthreads();
-    // 1-norm: one warp per column, lanes over rows
+    // 1-norm (every CTA the same way): one warp per column, lanes over rows
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     float best = 0.f;
     for (int c = warp; c < n; c += nw) {
@@ -1176,31 +1157,27 @@ __global__ void __launch_bounds__(kExpmThreads) k_expm_small_f32(int n, const do
     const int q = qs;
     const float f = (float)s[0] * ldexpf(1.f, -q);
     for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) X[idx] = make_float2(f * X[idx].x, f * X[idx].y);
-    __syncthreads();
+    // the peers write into this CTA's matrices from here on
+    cluster.sync();
     constexpr float c3 = 1.f / 6.f, c4 = 1.f / 24.f, c5 = 1.f / 120.f, c6 = 1.f / 720.f, c7 = 1.f / 5040.f,
                     c8 = 1.f / 40320.f;
-    smem_mm_poly(n, ldm, X, X, X, X, 0.f, 0.f, 0.f, X2);                  // X^2
-    __syncthreads();
-    smem_mm_poly(n, ldm, X2, X, X, X2, 0.f, 0.f, 0.f, X3);                // X^3
-    smem_mm_poly(n, ldm, nullptr, nullptr, X, X2, c6, c7, c8, T1);        // B2 (independent of X^3)
-    __syncthreads();
-    smem_mm_poly(n, ldm, X3, T1, X, X2, c3, c4, c5, T2);                  // B1 + X^3 B2
-    __syncthreads();
-    smem_mm_poly(n, ldm, X3, T2, X, X2, 1.f, 1.f, 0.5f, T1);              // B0 + X^3 (...)
-    __syncthreads();
+    cluster_mm_poly(cluster, n, ldm, c0, c1, X, X, X, X, 0.f, 0.f, 0.f, X2);                  // X^2
+    cluster_mm_poly(cluster, n, ldm, c0, c1, X2, X, X, X2, 0.f, 0.f, 0.f, X3);                // X^3
+    cluster_mm_poly(cluster, n, ldm, c0, c1, nullptr, nullptr, X, X2, c6, c7, c8, T1);        // B2
+    cluster_mm_poly(cluster, n, ldm, c0, c1, X3, T1, X, X2, c3, c4, c5, T2);                  // B1 + X^3 B2
+    cluster_mm_poly(cluster, n, ldm, c0, c1, X3, T2, X, X2, 1.f, 1.f, 0.5f, T1);              // B0 + X^3 (...)
     float2* P = T1;
     float2* Q = T2;
     for (int r = 0; r < q; ++r) {
-        smem_mm_poly(n, ldm, P, P, X, X2, 0.f, 0.f, 0.f, Q);
-        __syncthreads();
+        cluster_mm_poly(cluster, n, ldm, c0, c1, P, P, X, X2, 0.f, 0.f, 0.f, Q);
         float2* t = P;
         P = Q;
         Q = t;
     }
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-        const int r = idx % n, c = idx / n;
+    for (int idx = threadIdx.x; idx < n * (c1 - c0); idx += blockDim.x) {
+        const int r = idx % n, c = c0 + idx / n;
         const float2 v = P[c * ldm + r];
-        E[idx] = make_double2(v.x, v.y);
+        E[(int64_t)c * n + r] = make_double2(v.x, v.y);
     }
 }
 
@@ -1208,8 +1185,13 @@ bool expm_small_f32(int n, const double2* A, const double* scale_dev, double2* E
     if (n > kSmallN) return false;
     const int ldm = (n + 1) & ~1;
     const size_t sm = sizeof(float2) * 5 * ldm * ldm;
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_expm_small_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    roks::count_launch(), k_expm_small_f32<<<1, kExpmThreads, sm, st>>>(n, A, scale_dev, E);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_expm_small_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(float2) * 5 * kSmallN * kSmallN));
+        attr = true;
+    }
+    roks::count_launch(), k_expm_small_f32<<<kExpmCluster, kExpmThreads, sm, st>>>(n, A, scale_dev, E);
     return true;
 }
 

@@ -196,12 +196,20 @@ void pcg_finish(PcgScalars* sc, cudaStream_t st) { roks::count_launch(), k_pcg_f
 __global__ void k_energy_combine(const double* __restrict__ kin_b, const double* __restrict__ nl_b, int nb,
                                  const double* __restrict__ wband, const double* __restrict__ out6, double cM,
                                  double cT, double alpha, const double* __restrict__ hf2, double* __restrict__ E) {
-    if (threadIdx.x != 0) return;
+    // band sums: lane l takes bands l, l + 32, ..., then a fixed shuffle tree
+    // (FP64 adds are long-latency: few dependent levels)
+    const int lane = threadIdx.x;
     double kin = 0, nl = 0;
-    for (int n = 0; n < nb; ++n) {
+    for (int n = lane; n < nb; n += 32) {
         kin += wband[n] * kin_b[n];
         nl += wband[n] * nl_b[n];
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        kin += __shfl_xor_sync(0xffffffffu, kin, o);
+        nl += __shfl_xor_sync(0xffffffffu, nl, o);
+    }
+    if (lane != 0) return;
     const double loc = out6[2], H = out6[3], xM = out6[0], xT = out6[1];
     const double hfM = hf2 ? hf2[0] : 0.0, hfT = hf2 ? hf2[1] : 0.0;
     const double one = kin + loc + nl + H;
