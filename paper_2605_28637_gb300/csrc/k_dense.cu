@@ -823,11 +823,18 @@ bool cholesky_small_supported(int n) { return n <= kSmallN; }
 // lambda_jj = w / (1 + sqrt(1 + w)) (no cancellation), and the columns of
 // Xi = L^{-1} - I solve (I + Lambda) xi_c = -Lambda e_c by a right-looking
 // sweep, one warp per column.
+constexpr int kCholFactorThreads = 256;   // threads of the factorisation steps
+// NP: trailing-update pairs per factorisation thread, >= n (n - 1) / 2 / 256
+template <int NP>
 __global__ void __launch_bounds__(1024) k_cholesky_dev_f32(int n, const double2* __restrict__ O,
                                                            double2* __restrict__ XiH, int* flag) {
+    constexpr int kCholPairs = NP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* W = reinterpret_cast<float2*>(smem_raw);   // Delta (lower), updated in place
     float2* Lm = W + n * n;                             // Lambda (lower, diagonal deviation in .x)
+    // trailing-update pairs (i, k), i >= k >= 1, by k descending: the pairs of
+    // step j (k > j) are the first (n - 1 - j)(n - j) / 2
+    int* pk = reinterpret_cast<int*>(Lm + n * n);
     __shared__ float dinv[kSmallN];
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
         const int i = idx % n, j = idx / n;
@@ -837,33 +844,57 @@ __global__ void __launch_bounds__(1024) k_cholesky_dev_f32(int n, const double2*
         const double re = 0.5 * (a.x + b.x) - (i == j ? 1.0 : 0.0);
         const double im = i == j ? 0.0 : 0.5 * (a.y - b.y);
         W[idx] = make_float2((float)re, (float)im);
+        if (j >= 1) {
+            const int d = n - 1 - j;
+            pk[d * (d + 1) / 2 + (i - j)] = (i << 8) | j;
+        }
     }
     __syncthreads();
     int bad = 0;
     for (int j = 0; j < n; ++j) {
-        float w = W[j * n + j].x;
-        if (!(1.f + w > 0.f)) {
-            if (!bad) bad = j + 1;
-            w = 0.f;
-        }
-        const float piv = sqrtf(1.f + w), inv = 1.f / piv, invd = inv * inv;
-        if (threadIdx.x == 0) dinv[j] = inv;
-        for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
-            const float2 v = W[j * n + i];
-            Lm[j * n + i] = (i == j) ? make_float2(w / (1.f + piv), 0.f) : make_float2(v.x * inv, v.y * inv);
-        }
-        const int m = n - j - 1;
-        for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-            const int k = j + 1 + t / m, i = j + 1 + t % m;
-            if (i < k) continue;
-            const float2 a = W[j * n + i], b = W[j * n + k];
-            float2 c = W[k * n + i];
-            c.x = fmaf(-(a.x * b.x + a.y * b.y), invd, c.x);
-            c.y = fmaf(-(a.y * b.x - a.x * b.y), invd, c.y);
-            W[k * n + i] = c;
+        if (threadIdx.x < kCholFactorThreads) {
+            float w = W[j * n + j].x;
+            if (!(1.f + w > 0.f)) {
+                if (!bad) bad = j + 1;
+                w = 0.f;
+            }
+            const float piv = sqrtf(1.f + w), inv = 1.f / piv, invd = inv * inv;
+            if (threadIdx.x == 0) dinv[j] = inv;
+            for (int i = j + threadIdx.x; i < n; i += kCholFactorThreads) {
+                const float2 v = W[j * n + i];
+                Lm[j * n + i] = (i == j) ? make_float2(w / (1.f + piv), 0.f) : make_float2(v.x * inv, v.y * inv);
+            }
+            // trailing update W(i, k) -= W(i, j) conj(W(k, j)) / (1 + w_jj), k > j, i >= k:
+            // all loads of a thread first, then its stores (they never alias)
+            const int npair = (n - 1 - j) * (n - j) / 2;
+            int ii[kCholPairs], kk[kCholPairs];
+            float2 a[kCholPairs], b[kCholPairs], c[kCholPairs];
+#pragma unroll
+            for (int q = 0; q < kCholPairs; ++q) {
+                const int e = threadIdx.x + q * kCholFactorThreads;
+                const int code = e < npair ? pk[e] : 0;
+                ii[q] = code >> 8;
+                kk[q] = code & 255;
+                if (e < npair) {
+                    a[q] = W[j * n + ii[q]];
+                    b[q] = W[j * n + kk[q]];
+                    c[q] = W[kk[q] * n + ii[q]];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kCholPairs; ++q) {
+                const int e = threadIdx.x + q * kCholFactorThreads;
+                if (e < npair) {
+                    float2 t = c[q];
+                    t.x = fmaf(-(a[q].x * b[q].x + a[q].y * b[q].y), invd, t.x);
+                    t.y = fmaf(-(a[q].y * b[q].x - a[q].x * b[q].y), invd, t.y);
+                    W[kk[q] * n + ii[q]] = t;
+                }
+            }
         }
         __syncthreads();
     }
+    if (threadIdx.x == 0 && bad) flag[0] = bad;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int c = warp; c < n; c += nw) {
         // right-hand side -Lambda e_c: rows lane and lane + 32
@@ -901,13 +932,20 @@ __global__ void __launch_bounds__(1024) k_cholesky_dev_f32(int n, const double2*
             XiH[(int64_t)(lane + 32) * n + c] = make_double2((double)x.x, -(double)x.y);
         }
     }
-    if (threadIdx.x == 0 && bad) flag[0] = bad;
 }
 
 void cholesky_dev_f32(int n, const double2* O, double2* XiH, int* flag, cudaStream_t st) {
-    const size_t sm = sizeof(float2) * 2 * n * n;
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_cholesky_dev_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    roks::count_launch(), k_cholesky_dev_f32<<<1, 1024, sm, st>>>(n, O, XiH, flag);
+    const size_t sm = sizeof(float2) * 2 * n * n + sizeof(int) * n * (n - 1) / 2;
+    roks::count_launch();
+    if (n * (n - 1) / 2 <= 4 * kCholFactorThreads) {
+        if (sm > 48 * 1024)
+            cudaFuncSetAttribute(k_cholesky_dev_f32<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_cholesky_dev_f32<4><<<1, 1024, sm, st>>>(n, O, XiH, flag);
+    } else {
+        if (sm > 48 * 1024)
+            cudaFuncSetAttribute(k_cholesky_dev_f32<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_cholesky_dev_f32<8><<<1, 1024, sm, st>>>(n, O, XiH, flag);
+    }
 }
 
 // Cholesky O = L L^H (Crout, column by column) and the inverse of L, one

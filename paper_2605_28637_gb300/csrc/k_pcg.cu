@@ -14,10 +14,37 @@ namespace roks {
 // shell(m) > shell(n): theta_mn - conj theta_nm; a-b zeroed when suppressed.
 // A_mn = -(1/2) atan2(2|R|, |d_m - d_n|) sgn(d_m - d_n) R/|R| for m < n,
 // A_nm = -conj A_mn (|R| < 1e-14 -> 0).
-__global__ void k_pcg_rotation(int nb, const double2* __restrict__ Th, const double* __restrict__ d,
-                               const int* __restrict__ shell, int suppress_ab, int ia, int ib,
-                               double2* __restrict__ Gam, double2* __restrict__ Gin, double2* __restrict__ A) {
+// d_m = <m|F^c|m>.  Closed bands: Re theta_mm.  Open bands:
+// w_c (<m|T|m> + <m|V_nl|m>) + <m|V^c|m> with the local part from rho_m.
+__device__ __forceinline__ double band_diag(int m, int nb, int n_closed, const double2* __restrict__ Th,
+                                            const double* __restrict__ kin_b, const double* __restrict__ nl_b,
+                                            const double* __restrict__ open_vc, const double* __restrict__ open_x,
+                                            double wc) {
+    if (m < n_closed) return Th[(int64_t)m * nb + m].x;
+    double v = wc * (kin_b[m] + nl_b[m]) + open_vc[m - n_closed];
+    if (open_x) v += open_x[m - n_closed];
+    return v;
+}
+
+// Gamma, the rotation gradient and A (Eqs. 11, 20-23) with the diagonal d
+// formed per pair; block 0 also forms the a-b coupling of the open shells.
+__global__ void k_pcg_rotation(int nb, int n_closed, const double2* __restrict__ Th, const double* __restrict__ kin_b,
+                               const double* __restrict__ nl_b, const double* __restrict__ open_vc,
+                               const double* __restrict__ open_x, double wc, const int* __restrict__ shell,
+                               int suppress_ab, int ia, int ib, double2* __restrict__ Gam, double2* __restrict__ Gin,
+                               double2* __restrict__ A, PcgScalars* sc) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx == 0) {
+        if (ia < 0) {
+            sc->coup_re = sc->coup_im = 0.0;
+        } else {
+            // <a|F^a - F^b|b> = conj(theta_ba) - theta_ab
+            const double2 tab = Th[(int64_t)ib * nb + ia];
+            const double2 tba = Th[(int64_t)ia * nb + ib];
+            sc->coup_re = tba.x - tab.x;
+            sc->coup_im = -tba.y - tab.y;
+        }
+    }
     if (idx >= nb * nb) return;
     const int m = idx % nb, n = idx / nb;
     const double2 tmn = Th[(int64_t)n * nb + m];
@@ -37,7 +64,8 @@ __global__ void k_pcg_rotation(int nb, const double2* __restrict__ Th, const dou
         if (suppress_ab && ((p == ia && q == ib) || (p == ib && q == ia))) r = make_double2(0.0, 0.0);
         const double ar = sqrt(r.x * r.x + r.y * r.y);
         if (ar >= 1e-14) {
-            const double dd = d[p] - d[q];
+            const double dd = band_diag(p, nb, n_closed, Th, kin_b, nl_b, open_vc, open_x, wc) -
+                              band_diag(q, nb, n_closed, Th, kin_b, nl_b, open_vc, open_x, wc);
             const double sg = dd >= 0.0 ? 1.0 : -1.0;
             const double phi = 0.5 * atan2(2.0 * ar, fabs(dd));
             const double2 apq = make_double2(-phi * sg * r.x / ar, -phi * sg * r.y / ar);
@@ -47,44 +75,12 @@ __global__ void k_pcg_rotation(int nb, const double2* __restrict__ Th, const dou
     A[idx] = a;
 }
 
-__global__ void k_pcg_coupling(int nb, const double2* __restrict__ Th, int ia, int ib, PcgScalars* sc) {
-    if (threadIdx.x != 0) return;
-    if (ia < 0) {
-        sc->coup_re = sc->coup_im = 0.0;
-        return;
-    }
-    // <a|F^a - F^b|b> = conj(theta_ba) - theta_ab
-    const double2 tab = Th[(int64_t)ib * nb + ia];
-    const double2 tba = Th[(int64_t)ia * nb + ib];
-    sc->coup_re = tba.x - tab.x;
-    sc->coup_im = -tba.y - tab.y;
-}
-
-void pcg_rotation(int nb, const double2* Theta, const double* d, const int* shell, int suppress_ab, int ia, int ib,
-                  double2* Gam, double2* Gin, double2* A, PcgScalars* sc, cudaStream_t st) {
-    roks::count_launch(), k_pcg_rotation<<<(nb * nb + 127) / 128, 128, 0, st>>>(nb, Theta, d, shell, suppress_ab, ia, ib, Gam, Gin, A);
-    roks::count_launch(), k_pcg_coupling<<<1, 32, 0, st>>>(nb, Theta, ia, ib, sc);
-}
-
-// d_m = <m|F^c|m>.  Closed bands: Re theta_mm.  Open bands:
-// w_c (<m|T|m> + <m|V_nl|m>) + <m|V^c|m> with the local part from rho_m.
-__global__ void k_pcg_diag(int nb, int n_closed, const double2* __restrict__ Th, const double* __restrict__ kin_b,
-                           const double* __restrict__ nl_b, const double* __restrict__ open_vc,
-                           const double* __restrict__ open_x, double wc, double* __restrict__ d) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= nb) return;
-    if (m < n_closed) {
-        d[m] = Th[(int64_t)m * nb + m].x;
-    } else {
-        d[m] = wc * (kin_b[m] + nl_b[m]) + open_vc[m - n_closed];
-        if (open_x) d[m] += open_x[m - n_closed];
-    }
-}
-
-void pcg_diag(int nb, int n_closed, const double2* Theta, const double* kin_b, const double* nl_b,
-              const double* open_vc, const double* open_x, double wc, double* d, cudaStream_t st) {
-    roks::count_launch(), k_pcg_diag<<<(nb + 127) / 128, 128, 0, st>>>(nb, n_closed, Theta, kin_b, nl_b, open_vc,
-                                                                     open_x, wc, d);
+void pcg_rotation(int nb, int n_closed, const double2* Theta, const double* kin_b, const double* nl_b,
+                  const double* open_vc, const double* open_x, double wc, const int* shell, int suppress_ab, int ia,
+                  int ib, double2* Gam, double2* Gin, double2* A, PcgScalars* sc, cudaStream_t st) {
+    roks::count_launch(), k_pcg_rotation<<<(nb * nb + 127) / 128, 128, 0, st>>>(
+                              nb, n_closed, Theta, kin_b, nl_b, open_vc, open_x, wc, shell, suppress_ab, ia, ib, Gam,
+                              Gin, A, sc);
 }
 
 __global__ void k_pcg_rot_dots(int nb, const double2* __restrict__ A, const double2* __restrict__ Ap,

@@ -19,8 +19,9 @@
 //    hit different banks; the per-CTA partials are summed in a fixed order,
 //    with compensation, by the chunk-sum kernel.
 //  * k_nn_stream: Cout = alpha A B + beta Cin (A: M x K tall, B: K x N
-//    small, loaded once into shared memory by a bulk copy), one row tile of
-//    A (and of Cin) per stage.
+//    small, loaded once into shared memory, by a bulk copy of an FP32 copy
+//    or, when small, converted from FP64 by the consumer warps), one row
+//    tile of A (and of Cin) per stage.
 //
 // Every wait is bounded: a wait that gives up sets a device flag (read and
 // cleared by stream_timeout_take), the kernel then waits (again bounded)
@@ -246,8 +247,8 @@ template <int RR, int RN, int WS>
 __global__ void __launch_bounds__(768) k_nn_stream(int M, int N, int K, int KC, int nkc, int rows_per_cta, int W,
                                                    int NS, int load_c, const __grid_constant__ CUtensorMap tmA,
                                                    const __grid_constant__ CUtensorMap tmC,
-                                                   const float2* __restrict__ Bf, float2* Cout, int64_t ldc,
-                                                   float alpha, float beta) {
+                                                   const float2* __restrict__ Bf, const double2* __restrict__ Bd,
+                                                   int ldb, float2* Cout, int64_t ldc, float alpha, float beta) {
     constexpr int TR = 32 * RR * WS;
     constexpr int RP = RN / 2;
     extern __shared__ __align__(1024) unsigned char st_smem[];
@@ -277,10 +278,12 @@ __global__ void __launch_bounds__(768) k_nn_stream(int M, int N, int K, int KC, 
     __syncthreads();
 
     if (warp == nwarps - 1) {
-        // producer (one thread): B once, then the (tile, chunk) items
+        // producer (one thread): B once (unless the consumers convert it), then the (tile, chunk) items
         if (lane == 0 && nt > 0) {
-            mb_arrive_expect(&bbar, b_bytes);
-            bulk_g2s(Bs, Bf, b_bytes, &bbar);
+            if (!Bd) {
+                mb_arrive_expect(&bbar, b_bytes);
+                bulk_g2s(Bs, Bf, b_bytes, &bbar);
+            }
             int issued = 0;
             for (int it = 0; it < items; ++it) {
                 const int sg = it % NS;
@@ -294,13 +297,24 @@ __global__ void __launch_bounds__(768) k_nn_stream(int M, int N, int K, int KC, 
                 if (last && load_c) tma_2d(st + a_span, &tmC, r0, 0, &full[sg]);
                 issued = it + 1;
             }
-            wait_or_flag(&bbar, 0u);
+            if (!Bd) wait_or_flag(&bbar, 0u);
             for (int it = (issued > NS ? issued - NS : 0); it < issued; ++it)
                 wait_or_flag(&full[it % NS], (uint32_t)((it / NS) & 1));
         }
         __syncwarp();
     } else if (warp < W * WS && nt > 0) {
-        bool ok = wait_or_flag(&bbar, 0u);
+        bool ok = true;
+        if (Bd) {
+            // small FP64 B: the consumers convert it (row major) while the first tiles are in flight
+            for (int i = tid; i < K * N; i += 32 * W * WS) {
+                const int k = i / N, n = i - k * N;
+                const double2 v = Bd[(int64_t)n * ldb + k];
+                Bs[i] = make_float2((float)v.x, (float)v.y);
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(32 * W * WS) : "memory");
+        } else {
+            ok = wait_or_flag(&bbar, 0u);
+        }
         const int w = warp % W, hb = (warp / W) * 32 * RR;
         int ncp[RP];
 #pragma unroll
@@ -644,8 +658,12 @@ bool gemm_nn_stream(int M, int N, int K, const float2* A, int64_t lda, const dou
         tmC = tmA;   // not read
     }
     float2* Bf = static_cast<float2*>(bwork);
-    roks::count_launch();
-    k_b_rowmajor_f32<<<(K * N + 255) / 256, 256, 0, st>>>(K, N, B, ldb, Bf);
+    // a small B is converted by the kernel's consumers; a large one by a kernel of its own
+    const bool convert_in = K * N <= 2048;
+    if (!convert_in) {
+        roks::count_launch();
+        k_b_rowmajor_f32<<<(K * N + 255) / 256, 256, 0, st>>>(K, N, B, ldb, Bf);
+    }
     const size_t smem = ST_ALIGN + bbytes + (size_t)NS * stage;
     const int threads = 32 * (W * WS + 1);
 #define NNS_CASE(RR_, RN_, WS_)                                                                              \
@@ -657,7 +675,8 @@ bool gemm_nn_stream(int M, int N, int K, const float2* A, int64_t lda, const dou
         }                                                                                                   \
         roks::count_launch();                                                                               \
         k_nn_stream<RR_, RN_, WS_><<<G, threads, smem, st>>>(M, N, K, KC, nkc, rows, W, NS, load_c ? 1 : 0,  \
-                                                             tmA, tmC, Bf, Cout, ldc, alpha, beta);         \
+                                                             tmA, tmC, Bf, convert_in ? B : nullptr, ldb,   \
+                                                             Cout, ldc, alpha, beta);                       \
         return true;                                                                                        \
     }
 #define NNS_RN(RR_, WS_) NNS_CASE(RR_, 2, WS_) NNS_CASE(RR_, 4, WS_) NNS_CASE(RR_, 6, WS_) NNS_CASE(RR_, 8, WS_) \

@@ -71,7 +71,7 @@ struct roks_ctx {
     double2 *d_B = nullptr, *d_DB = nullptr, *d_QB = nullptr, *d_B2 = nullptr;
     double2* d_gemm_work = nullptr;
     size_t gemm_work_elems = 0;
-    double *d_kin_b = nullptr, *d_nl_b = nullptr, *d_colpart = nullptr, *d_colout = nullptr, *d_d = nullptr;
+    double *d_kin_b = nullptr, *d_nl_b = nullptr, *d_colpart = nullptr, *d_colout = nullptr;
     double* d_expm_info = nullptr;
     void* d_bigwork = nullptr;      // blocked Cholesky / exponential for more than 64 bands
     int* d_flag = nullptr;
@@ -508,12 +508,12 @@ struct Impl {
             gemm_cn<T>(nb, nb, npw, ccv(psi), ld, ccv(ctx->W_F), l, ctx->d_Th, nb, ctx->d_gemm_work,
                        ctx->gemm_work_elems, st);
         }
-        pcg_diag(nb, ctx->nc, ctx->d_Th, ctx->d_kin_b, ctx->d_nl_b, ctx->d_out6 + 4,
-                 ctx->alpha != 0.0 ? ctx->d_exopen : nullptr, ctx->cf.w[0], ctx->d_d, st);
         const int ia = (ctx->mode == ROKS_MODE_SINGLET) ? ctx->nc : -1;
         const int ib = (ctx->mode == ROKS_MODE_SINGLET) ? ctx->nc + 1 : -1;
-        pcg_rotation(nb, ctx->d_Th, ctx->d_d, ctx->d_shell, ctx->suppress_ab && ctx->mode == ROKS_MODE_SINGLET, ia,
-                     ib, ctx->d_Gam, ctx->d_Gin, ctx->d_A, ctx->d_sc, st);
+        pcg_rotation(nb, ctx->nc, ctx->d_Th, ctx->d_kin_b, ctx->d_nl_b, ctx->d_out6 + 4,
+                     ctx->alpha != 0.0 ? ctx->d_exopen : nullptr, ctx->cf.w[0], ctx->d_shell,
+                     ctx->suppress_ab && ctx->mode == ROKS_MODE_SINGLET, ia, ib, ctx->d_Gam, ctx->d_Gin, ctx->d_A,
+                     ctx->d_sc, st);
         // G = F - S Gam ; gI = F - S theta
         {
         PROF("gradient_precond");
@@ -881,7 +881,6 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     AL(ctx->d_nl_b, sizeof(double) * nb);
     AL(ctx->d_colpart, sizeof(double) * 2 * nb * 16);
     AL(ctx->d_colout, sizeof(double) * 2 * nb);
-    AL(ctx->d_d, sizeof(double) * nb);
     AL(ctx->d_expm_info, sizeof(double) * 2);
     if (nb > 64) {
         const size_t w1 = cholesky_big_work_bytes(nb, f64), w2 = expm_big_work_bytes(nb, f64);

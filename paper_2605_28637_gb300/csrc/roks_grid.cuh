@@ -89,12 +89,13 @@ struct PcgScalars {
 };
 
 // Gam = (Theta + Theta^H)/2, Gin = Theta - Theta^H, R (Eq. 20) -> A (Eqs. 22-23),
-// and the open-shell coupling; shell[n] is the shell index of band n.
-void pcg_rotation(int nb, const double2* Theta, const double* d, const int* shell, int suppress_ab, int ia,
+// and the open-shell coupling; shell[n] is the shell index of band n.  The
+// diagonal d_m = <m|F^c|m> is Re theta_mm for closed bands and is formed from
+// expectation values for open ones (w_c (<m|T|m> + <m|V_nl|m>) + <m|V^c|m>,
+// plus the exchange term when open_x is given).
+void pcg_rotation(int nb, int n_closed, const double2* Theta, const double* kin_b, const double* nl_b,
+                  const double* open_vc, const double* open_x, double wc, const int* shell, int suppress_ab, int ia,
                   int ib, double2* Gam, double2* Gin, double2* A, PcgScalars* sc, cudaStream_t st);
-// d_m = <m|F^c|m>: Re theta_mm for closed bands, from expectation values for open ones.
-void pcg_diag(int nb, int n_closed, const double2* Theta, const double* kin_b, const double* nl_b,
-              const double* open_vc, const double* open_x, double wc, double* d, cudaStream_t st);
 // sc->rot_pg = 1/2 Re sum conj(A) Gin; sc->r1, r2 as named.
 void pcg_rot_dots(int nb, const double2* A, const double2* Aprev, const double2* Gin, PcgScalars* sc,
                   cudaStream_t st);
