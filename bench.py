@@ -62,6 +62,11 @@ def dist_env():
     return rank, world, local
 
 
+# FP32 FMA rate from the unit counts and the maximum SM clock (no measured
+# FP32 peak is provided): 152 SMs x 128 lanes x 2 flops x 2.07 GHz
+FP32_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -412,6 +417,19 @@ def run_gpu(args):
                     "frac": achieved / hbm, "peak_kind": f"{peak_kind} (copy bandwidth)",
                     "traffic": traffic_record(dom["name"]), "algorithmic_bytes_per_launch": alg,
                     "ms_per_launch": per_launch_ms, "share_of_step": dom["ms"] / total_prof}
+    # FP32-FMA roofline of the projector products F += P (D B), S = Psi + P (Q B)
+    # (streamed tall products, K = N_proj): the largest contraction family
+    roofline_fp32 = None
+    px = next((e for e in prof if e["name"] == "proj_PX"), None)
+    if px is not None and args.precision == "mixed" and ctx.nproj > 0:
+        per_launch_ms = px["ms"] / px["launches"]
+        flops = 8.0 * ctx.npw * ctx.nb * ctx.nproj
+        achieved = flops / (per_launch_ms / 1000.0) / 1e12
+        roofline_fp32 = {"bound": "alu", "kernel": "proj_PX (k_nn_stream, FP32 FMA)", "achieved": achieved,
+                         "peak": FP32_TFLOPS_NOMINAL, "unit": "TFLOP/s", "frac": achieved / FP32_TFLOPS_NOMINAL,
+                         "peak_kind": "nominal: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
+                         "flops_per_launch": flops, "ms_per_launch": per_launch_ms,
+                         "share_of_step": px["ms"] / total_prof}
     launches = sum(e["launches"] for e in prof)
     # ---- time to convergence: chosen (mixed) vs plain FP64
     pcg = None
@@ -446,6 +464,7 @@ def run_gpu(args):
                        "precision": args.precision, "parallelism": f"replicas{world}",
                        "l2": "per-step working set above the 129 MB L2 (plane buffers, projectors, band blocks)"},
             "roofline": roofline,
+            "roofline_fp32": roofline_fp32,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bytes_psi,
                     "d2h_bytes_per_step": bytes_psi},

@@ -291,6 +291,7 @@ class Context:
         self.ctx = roks_setup(cfg, self.precision, self.stream.cuda_stream, suppress_ab, e_tol)
         self.npw, self.nb, self.ld, self.miller = roks_basis(self.ctx)
         self.N = cfg["grid"]
+        self.nproj = sum(len(cfg["species"][a["species"]]["l"]) for a in cfg["atoms"])
 
     def new_bands(self):
         return self.torch.zeros((self.nb, self.ld), dtype=self.cdtype, device="cuda")
