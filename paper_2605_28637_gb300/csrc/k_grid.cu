@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(RB) k_colred(int npw, int nb, const c2<T>* __r
     // per-thread sums in the element type (a handful of terms), block sums in FP64
     T t0 = T(0), t1 = T(0);
     const c2<T>* xc = x + (int64_t)n * ldx;
+#pragma unroll 4
     for (int g = g0 + threadIdx.x; g < g1; g += RB) {
         const c2<T> a = xc[g];
         const T m = a.x * a.x + a.y * a.y;
@@ -170,6 +171,32 @@ __global__ void __launch_bounds__(RB) k_colred(int npw, int nb, const c2<T>* __r
         part[((int64_t)0 * nb + n) * nsplit + sp] = s0;
         if (OP == 1) part[((int64_t)1 * nb + n) * nsplit + sp] = s1;
     }
+}
+
+// Op 1 (TPA sums): out[n] = |g_n|^2, out[nb + n] = sum g2 |g_n|^2 (as
+// k_colred_final sums them), then out[2 nb + 2 n] = 1/X_n and
+// out[2 nb + 2 n + 1] = -2/X_n with X_n = 1.5 out[nb + n] / out[n] (Eqs. 17, 18,
+// reading R1).
+__global__ void k_colred_final_tpa(int nb, int nsplit, const double* __restrict__ part, double* __restrict__ out) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nb) return;
+    double v[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const double* p = part + (int64_t)(h * nb + n) * nsplit;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        for (int k = 0; k < nsplit; k += 4) {
+            s0 += p[k];
+            s1 += p[k + 1];
+            s2 += p[k + 2];
+            s3 += p[k + 3];
+        }
+        v[h] = (s0 + s1) + (s2 + s3);
+        out[h * nb + n] = v[h];
+    }
+    const double X = 1.5 * v[1] / fmax(v[0], 1e-300);
+    out[2 * nb + 2 * n] = 1.0 / X;
+    out[2 * nb + 2 * n + 1] = -2.0 / X;
 }
 
 // out[i] = sum of the nsplit partials of column i (nsplit a multiple of 4):
@@ -221,8 +248,11 @@ void column_sums(int op, int npw, int nb, const c2<T>* x, int64_t ldx, const c2<
         case 2: roks::count_launch(), k_colred<T, 2><<<g, RB, 0, st>>>(npw, nb, x, ldx, y, ldy, g2, nsplit, part); break;
         default: roks::count_launch(), k_colred<T, 3><<<g, RB, 0, st>>>(npw, nb, x, ldx, y, ldy, g2, nsplit, part); break;
     }
-    const int count = (op == 1 ? 2 : 1) * nb;
-    roks::count_launch(), k_colred_final<<<(count + 127) / 128, 128, 0, st>>>(count, nsplit, part, out);
+    if (op == 1) {
+        roks::count_launch(), k_colred_final_tpa<<<(nb + 127) / 128, 128, 0, st>>>(nb, nsplit, part, out);
+        return;
+    }
+    roks::count_launch(), k_colred_final<<<(nb + 127) / 128, 128, 0, st>>>(nb, nsplit, part, out);
 }
 
 template <typename T>
@@ -405,21 +435,17 @@ __global__ void __launch_bounds__(RB) k_partials_final(int nblocks, int nq, cons
 // K g: K(G, n) = -(2 / X_n) tpa(|G|^2 / X_n), X_n = 1.5 sum g2 |g|^2 / sum |g|^2.
 template <typename T>
 __global__ void k_precond(int npw, const c2<T>* __restrict__ gI, int64_t ld, const T* __restrict__ g2h,
-                          const double* __restrict__ sums /* [2 nb]: |g|^2, g2 |g|^2 */, int nb,
-                          c2<T>* __restrict__ out, int64_t ldo) {
-    __shared__ T Xs[2];
+                          const double* __restrict__ sums /* [4 nb]: |g|^2, g2 |g|^2, then 1/X, -2/X */,
+                          int nb, c2<T>* __restrict__ out, int64_t ldo) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = blockIdx.y;
-    if (threadIdx.x == 0) {
-        const double X = 1.5 * sums[nb + n] / fmax(sums[n], 1e-300);
-        Xs[0] = T(1.0 / X);
-        Xs[1] = T(-2.0 / X);
-    }
-    __syncthreads();
     if (g >= npw) return;
-    const T x = T(2) * g2h[g] * Xs[0];
+    // the band's coefficients come from the column-sum kernel (FP64 divisions
+    // once per band, not once per block)
+    const T X0 = T(sums[2 * nb + 2 * n]), X1 = T(sums[2 * nb + 2 * n + 1]);
+    const T x = T(2) * g2h[g] * X0;
     const T num = T(27) + x * (T(18) + x * (T(12) + T(8) * x));
-    const T K = Xs[1] * num / (num + T(16) * x * x * x * x);
+    const T K = X1 * num / (num + T(16) * x * x * x * x);
     const c2<T> a = gI[(int64_t)n * ld + g];
     out[(int64_t)n * ldo + g] = mk<T>(K * a.x, K * a.y);
 }

@@ -880,7 +880,7 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     AL(ctx->d_kin_b, sizeof(double) * nb);
     AL(ctx->d_nl_b, sizeof(double) * nb);
     AL(ctx->d_colpart, sizeof(double) * 2 * nb * 16);
-    AL(ctx->d_colout, sizeof(double) * 2 * nb);
+    AL(ctx->d_colout, sizeof(double) * 4 * nb);   // op-1 sums (2 nb), then the TPA coefficients (2 nb)
     AL(ctx->d_expm_info, sizeof(double) * 2);
     if (nb > 64) {
         const size_t w1 = cholesky_big_work_bytes(nb, f64), w2 = expm_big_work_bytes(nb, f64);

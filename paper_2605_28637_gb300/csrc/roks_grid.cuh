@@ -34,7 +34,8 @@ template <typename T>
 void init_orbitals(int npw, int nb, const double* u_dev, const double* g2, c2<T>* psi, int64_t ld, cudaStream_t st);
 template <typename T>
 void to_real_type(int64_t n, const double* in, T* out, double scale, cudaStream_t st);
-// op 0: kinetic 0.5 g2 |x|^2; 1: (|x|^2, g2 |x|^2) -> out[0..nb), out[nb..2nb); 2: Re <x|y>; 3: |x|^2.
+// op 0: kinetic 0.5 g2 |x|^2; 1: (|x|^2, g2 |x|^2) -> out[0..nb), out[nb..2nb), and the TPA
+// coefficients (1/X_n, -2/X_n) -> out[2nb..4nb) (out holds 4 nb for op 1); 2: Re <x|y>; 3: |x|^2.
 // g2h = |G|^2 / 2 in the element type.  part must hold 2 * nb * 16 doubles.
 template <typename T>
 void column_sums(int op, int npw, int nb, const c2<T>* x, int64_t ldx, const c2<T>* y, int64_t ldy,
