@@ -199,6 +199,57 @@ ROKS_API roks_status roks_orthonormalize(roks_ctx* ctx, void* psi, int64_t ld);
 ROKS_API roks_status roks_pcg_step(roks_ctx* ctx, void* psi, int64_t ld,
                           roks_step_info* info);
 
+/* ------------------------------------------------------------------
+ * DIIS on the ROKS residual (Sec. II A): the paper minimises E_S also with
+ * a DIIS solver (Pulay extrapolation as in Hutter, Luthi and Parrinello
+ * 1994) on the residual of Frank et al.,
+ *   R_n = F^n|n> - sum_m S|m> Lambda_mn,
+ *   Lambda_mn = theta_mn - lambda_mn (theta_mn - theta_nm^*),
+ *   theta_mn = <m|F^n|n>,
+ * lambda_mn = 1/2 for every pair (then R is the gradient g of Eq. 7) except
+ * the open pair: lambda_ab (component along |a> of the residual of b) and
+ * lambda_ba (component along |b> of the residual of a); the paper's choice
+ * for excited singlets of the same symmetry as the ground state is
+ * lambda_ab = 1/2, lambda_ba = -1/2.  One step:
+ *   e = tau K R with the TPA preconditioner K (Eqs. 17, 18), no S-projection;
+ *   the pair (Psi, e) joins the last `history` pairs;
+ *   B_jk = sum_n Re <e_jn|e_kn>; the window is the largest set of the most
+ *   recent pairs whose normalised Gram matrix D^-1/2 B D^-1/2 (D = diag B)
+ *   has every Cholesky pivot L_kk^2 >= 1e-7;
+ *   d = B^-1 1 / (1^T B^-1 1) over the window (real, sum d = 1: the
+ *   minimiser of |sum d_j e_j|^2);
+ *   psi <- orth(sum_j d_j (Psi_j + e_j)) (Cholesky S-orthonormalisation).
+ * The history lives in the context.  It starts afresh on the first call, on
+ * a change of psi, ld or any option, after a PCG step, roks_init_orbitals
+ * or roks_orthonormalize; a DIIS step likewise makes the next PCG step start
+ * with steepest descent.  DIIS uses the TPA preconditioner alone (the learned
+ * correction, if set, applies to PCG only). */
+#define ROKS_DIIS_MAX 8
+typedef struct {
+    int history;       /* pairs kept, 1 .. ROKS_DIIS_MAX (1: preconditioned
+                          steepest descent with step tau)                   */
+    double tau;        /* step scale of the error vector, > 0               */
+    double lambda_ab;  /* coupling coefficients of the open pair (singlet   */
+    double lambda_ba;  /*   mode only; other modes ignore them)             */
+} roks_diis_options;
+
+typedef struct {
+    double E;          /* energy at the start of the step                   */
+    double E_new;      /* energy of the extrapolated, orthonormal orbitals  */
+    double res_norm;   /* Frobenius norm of the residual R at the start     */
+    int window;        /* pairs the extrapolation used                      */
+    double coef[ROKS_DIIS_MAX];   /* their coefficients, oldest first        */
+    int converged;     /* 1 once |E_new - E| < e_tol on two consecutive steps */
+} roks_diis_info;
+
+/* One DIIS step on psi (in place, S-orthonormal on entry and exit).  opt
+ * NULL takes history 6, tau 1/2, lambda_ab = lambda_ba = 1/2.  ROKS_EINVAL
+ * for options out of range; ROKS_EDIVERGED for a non-finite residual or
+ * energy; ROKS_ENOTPOSDEF if the extrapolated orbitals are linearly
+ * dependent.  Fills *info (host).  Synchronises. */
+ROKS_API roks_status roks_diis_step(roks_ctx* ctx, void* psi, int64_t ld, const roks_diis_options* opt,
+                                    roks_diis_info* info);
+
 /* Energies of the last completed density/potential evaluation.  Synchronises. */
 ROKS_API roks_status roks_energies_get(roks_ctx* ctx, roks_energies* e);
 

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/roks.h"
+#include "roks_diis.cuh"
 #include "roks_exx.cuh"
 #include "roks_grid.cuh"
 #include "roks_mlp.cuh"
@@ -90,6 +91,20 @@ struct roks_ctx {
     const void* b_psi = nullptr;       // d_B holds P^H psi for this buffer
     bool pot_valid = false;
     int n_small = 0;
+    // DIIS history: ring of (Psi_j, e_j) pairs, the device state of B and
+    // the window, and the host bookkeeping of the ring (pushes so far, the
+    // options and buffer it belongs to).  pcg_fresh: the next PCG step starts
+    // with steepest descent (a DIIS step has moved the orbitals).
+    void* diis_ring = nullptr;
+    int diis_slots = 0;
+    DiisState* d_diis = nullptr;
+    DiisState* h_diis = nullptr;
+    long long diis_count = 0;
+    int diis_small = 0;
+    roks_diis_options diis_opt{};
+    const void* diis_psi = nullptr;
+    int64_t diis_ld = 0;
+    bool pcg_fresh = false;
     // learned correction of the preconditioner; once its run meets the
     // convergence criterion, TPA alone continues and must meet it again
     float* d_mlp = nullptr;
@@ -670,6 +685,118 @@ struct Impl {
             return fail(ctx, ROKS_EDIVERGED, "non-finite energy or gradient");
         return ROKS_OK;
     }
+
+    // One DIIS step (roks_diis_step): residual with the coupling
+    // coefficients, e = K R into the ring, the new row of B, the window and
+    // its coefficients on the device, the extrapolated orbitals, their
+    // orthonormalisation and energy.  Launched eagerly: the ring slots change
+    // from step to step.
+    static roks_status diis_step(roks_ctx* ctx, void* psi, int64_t ld, const roks_diis_options& o,
+                                 roks_diis_info* info) {
+        cudaStream_t st = ctx->st;
+        const int nb = ctx->nb, npw = ctx->npw;
+        const int64_t l = ctx->ld_min;
+        const int64_t blk = l * nb;
+        roks_status r;
+        if (!(ctx->pot_valid && ctx->cache_psi == psi)) {
+            r = density(ctx, psi, ld, nullptr);
+            if (r != ROKS_OK) return r;
+            r = potential(ctx);
+            if (r != ROKS_OK) return r;
+        }
+        if (ctx->nproj > 0 && ctx->b_psi != psi) {
+            PROF("proj_PhPsi");
+            gemm_cn<T>(ctx->nproj, nb, npw, ccv(ctx->d_P), ctx->ld_min, ccv(psi), ld, ctx->d_B, ctx->nproj,
+                       ctx->d_gemm_work, ctx->gemm_work_elems, st);
+            ctx->b_psi = psi;
+        }
+        CK(cudaMemcpyAsync(&ctx->d_diis->E0, ctx->d_E + 10, sizeof(double), cudaMemcpyDeviceToDevice, st));
+        r = apply(ctx, psi, ld, ctx->W_F, l, ctx->W_S, l, ctx->nproj > 0);
+        if (r != ROKS_OK) return r;
+        {
+            PROF("subspace_theta");
+            gemm_cn<T>(nb, nb, npw, ccv(psi), ld, ccv(ctx->W_F), l, ctx->d_Th, nb, ctx->d_gemm_work,
+                       ctx->gemm_work_elems, st);
+        }
+        const int slot = int(ctx->diis_count % o.history);
+        V* Pj = cv(ctx->diis_ring) + slot * blk;
+        V* Ej = cv(ctx->diis_ring) + (int64_t)(o.history + slot) * blk;
+        {
+            PROF("diis_residual");
+            const bool singlet = ctx->mode == ROKS_MODE_SINGLET;
+            diis_multipliers(nb, ctx->d_Th, singlet ? ctx->nc : -1, singlet ? ctx->nc + 1 : -1, o.lambda_ab,
+                             o.lambda_ba, ctx->d_Gam, st);
+            // R = F - S Lambda
+            gemm_nn_io<T>(npw, nb, nb, ccv(ctx->W_S), l, ctx->d_Gam, nb, ccv(ctx->W_F), l, cv(ctx->W_G), l, -1.0,
+                          1.0, ctx->d_gemm_work, st);
+            column_total<T>(3, npw, nb, ccv(ctx->W_G), l, nullptr, 0, static_cast<const T*>(ctx->d_g2half),
+                            ctx->d_colpart, &ctx->d_diis->rnorm2, 1.0, st);
+            // e = K R (tau enters the extrapolation; d does not depend on a common scale of e)
+            column_sums<T>(1, npw, nb, ccv(ctx->W_G), l, nullptr, 0, static_cast<const T*>(ctx->d_g2half),
+                           ctx->d_colpart, ctx->d_colout, st);
+            precondition<T>(npw, nb, ccv(ctx->W_G), l, static_cast<const T*>(ctx->d_g2half), ctx->d_colout, Ej, l,
+                            st);
+            CK(cudaMemcpy2DAsync(Pj, l * sizeof(V), psi, ld * sizeof(V), npw * sizeof(V), nb,
+                                 cudaMemcpyDeviceToDevice, st));
+        }
+        DiisOrder ord{};
+        ord.n = int(std::min<long long>(ctx->diis_count + 1, o.history));
+        for (int k = 0; k < ord.n; ++k) ord.slot[k] = int((ctx->diis_count + 1 - ord.n + k) % o.history);
+        {
+            PROF("diis_gram");
+            for (int k = 0; k < ord.n; ++k)
+                column_total<T>(2, npw, nb, Ej, l, cv(ctx->diis_ring) + (int64_t)(o.history + ord.slot[k]) * blk, l,
+                                static_cast<const T*>(ctx->d_g2half), ctx->d_colpart,
+                                &ctx->d_diis->B[slot * kDiisMax + ord.slot[k]], 1.0, st);
+            diis_solve(ctx->d_diis, ord, 1e-7, st);
+        }
+        {
+            PROF("diis_combine");
+            diis_combine<T>(npw, nb, ctx->d_diis, cv(ctx->diis_ring), cv(ctx->diis_ring) + (int64_t)o.history * blk,
+                            blk, l, o.tau, cv(ctx->W_Y), l, st);
+        }
+        ctx->diis_count += 1;
+        r = orth(ctx, ctx->W_Y, l, psi, ld, ctx->nproj > 0 ? ctx->d_B : nullptr);
+        if (r != ROKS_OK) return r;
+        ctx->b_psi = ctx->nproj > 0 ? psi : nullptr;
+        r = density(ctx, psi, ld, ctx->nproj > 0 ? ctx->d_B : nullptr);
+        if (r != ROKS_OK) return r;
+        r = potential(ctx);
+        if (r != ROKS_OK) return r;
+        CK(cudaMemcpyAsync(&ctx->d_diis->Enew, ctx->d_E + 10, sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(ctx->h_diis, ctx->d_diis, sizeof(DiisState), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(ctx->h_flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        int* sflag = stream_timeout_flag();
+        ctx->h_flag[1] = 0;
+        if (sflag) CK(cudaMemcpyAsync(ctx->h_flag + 1, sflag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        ctx->cache_psi = psi;
+        ctx->pot_valid = true;
+        if (tc_timeout_take())
+            return fail(ctx, ROKS_ETIMEOUT, "a tensor-core completion wait ran out (bounded mbarrier wait)");
+        if (ctx->h_flag[1]) {
+            stream_timeout_take();
+            return fail(ctx, ROKS_ETIMEOUT, "a bulk-copy wait of a streamed contraction ran out (bounded mbarrier wait)");
+        }
+        const DiisState& h = *ctx->h_diis;
+        if (*ctx->h_flag) {
+            const int band = *ctx->h_flag - 1;
+            CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), st));
+            ctx->pot_valid = false;
+            if (h.h == 0) return fail(ctx, ROKS_EDIVERGED, "non-finite residual");
+            return fail(ctx, ROKS_ENOTPOSDEF, "extrapolated orbitals linearly dependent at band " + std::to_string(band));
+        }
+        if (info) {
+            info->E = h.E0;
+            info->E_new = h.Enew;
+            info->res_norm = std::sqrt(h.rnorm2);
+            info->window = h.h;
+            for (int k = 0; k < ROKS_DIIS_MAX; ++k) info->coef[k] = k < h.h ? h.d[k] : 0.0;
+        }
+        if (h.h == 0 || !std::isfinite(h.Enew) || !std::isfinite(h.rnorm2))
+            return fail(ctx, ROKS_EDIVERGED, "non-finite residual or energy");
+        return ROKS_OK;
+    }
 };
 
 void reset_history(roks_ctx* ctx) {
@@ -686,6 +813,9 @@ void reset_history(roks_ctx* ctx) {
     ctx->b_psi = nullptr;
     ctx->n_small = 0;
     ctx->mlp_judging = false;
+    ctx->diis_count = 0;
+    ctx->diis_small = 0;
+    ctx->pcg_fresh = false;
     cudaStreamSynchronize(ctx->st);
 }
 
@@ -1143,6 +1273,9 @@ roks_status roks_pcg_step(roks_ctx* ctx, void* psi, int64_t ld, roks_step_info* 
     if (!ctx) return ROKS_EINVAL;
     roks_status r = check_psi(ctx, psi, ld);
     if (r != ROKS_OK) return r;
+    // after DIIS steps the direction history belongs to other orbitals
+    if (ctx->pcg_fresh) reset_history(ctx);
+    ctx->diis_count = 0;
     roks_step_info tmp;
     std::memset(&tmp, 0, sizeof(tmp));
     r = ctx->prec == ROKS_FP64 ? Impl<double>::pcg_step(ctx, psi, ld, &tmp) : Impl<float>::pcg_step(ctx, psi, ld, &tmp);
@@ -1164,6 +1297,67 @@ roks_status roks_pcg_step(roks_ctx* ctx, void* psi, int64_t ld, roks_step_info* 
         ctx->n_small = 0;
         tmp.converged = 0;
     }
+    if (info) *info = tmp;
+    return r;
+}
+
+roks_status roks_diis_step(roks_ctx* ctx, void* psi, int64_t ld, const roks_diis_options* opt,
+                           roks_diis_info* info) {
+    if (!ctx) return ROKS_EINVAL;
+    roks_status r = check_psi(ctx, psi, ld);
+    if (r != ROKS_OK) return r;
+    roks_diis_options o;
+    if (opt) {
+        o = *opt;
+    } else {
+        o.history = 6;
+        o.tau = 0.5;
+        o.lambda_ab = 0.5;
+        o.lambda_ba = 0.5;
+    }
+    if (o.history < 1 || o.history > ROKS_DIIS_MAX || !(o.tau > 0.0) || !std::isfinite(o.tau) ||
+        !std::isfinite(o.lambda_ab) || !std::isfinite(o.lambda_ba))
+        return fail(ctx, ROKS_EINVAL, "DIIS options out of range (history 1..8, tau > 0, finite lambdas)");
+    const roks_diis_options& p = ctx->diis_opt;
+    const bool same = ctx->diis_count > 0 && ctx->diis_psi == psi && ctx->diis_ld == ld &&
+                      o.history == p.history && o.tau == p.tau && o.lambda_ab == p.lambda_ab &&
+                      o.lambda_ba == p.lambda_ba;
+    if (!same) {
+        ctx->diis_count = 0;
+        ctx->diis_small = 0;
+    }
+    ctx->diis_opt = o;
+    ctx->diis_psi = psi;
+    ctx->diis_ld = ld;
+    if (!ctx->d_diis) {
+        CK(dalloc(ctx, &ctx->d_diis, sizeof(DiisState)));
+        void* hp = nullptr;
+        CK(cudaMallocHost(&hp, sizeof(DiisState)));
+        ctx->h_diis = static_cast<DiisState*>(hp);
+    }
+    if (ctx->diis_slots < o.history) {
+        if (ctx->diis_ring) {
+            CK(cudaStreamSynchronize(ctx->st));
+            for (auto& q : ctx->allocs)
+                if (q == ctx->diis_ring) q = nullptr;
+            cudaFree(ctx->diis_ring);
+            ctx->diis_ring = nullptr;
+            ctx->diis_slots = 0;
+        }
+        const size_t es = ctx->prec == ROKS_FP64 ? sizeof(double2) : sizeof(float2);
+        if (dalloc(ctx, &ctx->diis_ring, es * (size_t)ctx->ld_min * ctx->nb * 2 * o.history) != cudaSuccess)
+            return fail(ctx, ROKS_ENOMEM, "DIIS history ring");
+        ctx->diis_slots = o.history;
+    }
+    roks_diis_info tmp;
+    std::memset(&tmp, 0, sizeof(tmp));
+    r = ctx->prec == ROKS_FP64 ? Impl<double>::diis_step(ctx, psi, ld, o, &tmp)
+                               : Impl<float>::diis_step(ctx, psi, ld, o, &tmp);
+    ctx->pcg_fresh = true;
+    if (r != ROKS_OK && r != ROKS_EDIVERGED) return r;
+    if (std::fabs(tmp.E_new - tmp.E) < ctx->e_tol) ctx->diis_small += 1;
+    else ctx->diis_small = 0;
+    tmp.converged = ctx->diis_small >= 2 ? 1 : 0;
     if (info) *info = tmp;
     return r;
 }
@@ -1300,6 +1494,7 @@ void roks_destroy(roks_ctx* ctx) {
     else cudaDeviceSynchronize();
     if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
     if (ctx->h_sc) cudaFreeHost(ctx->h_sc);
+    if (ctx->h_diis) cudaFreeHost(ctx->h_diis);
     if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
     if (ctx->side_st) cudaStreamDestroy(ctx->side_st);
     if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);

@@ -64,13 +64,25 @@ class roks_step_info(C.Structure):
                 ("dE0", C.c_double), ("restarted", C.c_int), ("converged", C.c_int)]
 
 
+ROKS_DIIS_MAX = 8
+
+
+class roks_diis_options(C.Structure):
+    _fields_ = [("history", C.c_int), ("tau", C.c_double), ("lambda_ab", C.c_double), ("lambda_ba", C.c_double)]
+
+
+class roks_diis_info(C.Structure):
+    _fields_ = [("E", C.c_double), ("E_new", C.c_double), ("res_norm", C.c_double), ("window", C.c_int),
+                ("coef", C.c_double * ROKS_DIIS_MAX), ("converged", C.c_int)]
+
+
 class roks_profile_entry(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int), ("ms", C.c_double)]
 
 
 EXPORTS = ["roks_setup", "roks_basis", "roks_init_orbitals", "roks_density", "roks_potential", "roks_apply_h",
-           "roks_orthonormalize", "roks_pcg_step", "roks_energies_get", "roks_profile_enable", "roks_profile_read",
-           "roks_orthonormalize_noalloc", "roks_mlp_forward", "roks_mlp_grad", "roks_mlp_adam",
+           "roks_orthonormalize", "roks_pcg_step", "roks_diis_step", "roks_energies_get", "roks_profile_enable",
+           "roks_profile_read", "roks_orthonormalize_noalloc", "roks_mlp_forward", "roks_mlp_grad", "roks_mlp_adam",
            "roks_set_preconditioner", "roks_precondition", "roks_mlp_grad_work", "roks_last_error", "roks_destroy"]
 
 ROKS_MLP_PARAMS = 4481
@@ -102,6 +114,7 @@ def load(path: str | None = None) -> C.CDLL:
     lib.roks_apply_h.argtypes = [P, P, C.c_int64, P, P, P]
     lib.roks_orthonormalize.argtypes = [P, P, C.c_int64]
     lib.roks_pcg_step.argtypes = [P, P, C.c_int64, C.POINTER(roks_step_info)]
+    lib.roks_diis_step.argtypes = [P, P, C.c_int64, C.POINTER(roks_diis_options), C.POINTER(roks_diis_info)]
     lib.roks_energies_get.argtypes = [P, C.POINTER(roks_energies)]
     lib.roks_profile_enable.argtypes = [P, C.c_int]
     lib.roks_profile_read.argtypes = [P, C.POINTER(roks_profile_entry), C.c_int, C.POINTER(C.c_int)]
@@ -202,6 +215,16 @@ def roks_pcg_step(ctx, psi, ld: int) -> dict:
     info = roks_step_info()
     _check(ctx, load().roks_pcg_step(ctx, _ptr(psi), ld, C.byref(info)))
     return {n: getattr(info, n) for n, _ in roks_step_info._fields_}
+
+
+def roks_diis_step(ctx, psi, ld: int, history: int = 6, tau: float = 0.5, lambda_ab: float = 0.5,
+                   lambda_ba: float = 0.5) -> dict:
+    opt = roks_diis_options(history, tau, lambda_ab, lambda_ba)
+    info = roks_diis_info()
+    _check(ctx, load().roks_diis_step(ctx, _ptr(psi), ld, C.byref(opt), C.byref(info)))
+    out = {n: getattr(info, n) for n, _ in roks_diis_info._fields_ if n != "coef"}
+    out["coef"] = [info.coef[k] for k in range(info.window)]
+    return out
 
 
 def roks_energies_get(ctx) -> dict:
@@ -325,6 +348,9 @@ class Context:
 
     def pcg_step(self, psi):
         return roks_pcg_step(self.ctx, psi, self.ld)
+
+    def diis_step(self, psi, history: int = 6, tau: float = 0.5, lambda_ab: float = 0.5, lambda_ba: float = 0.5):
+        return roks_diis_step(self.ctx, psi, self.ld, history, tau, lambda_ab, lambda_ba)
 
     def energies(self):
         return roks_energies_get(self.ctx)

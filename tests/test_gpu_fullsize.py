@@ -1,0 +1,100 @@
+"""Parity at full size: the organic-96 workload (96^3 grid, 34,265 plane
+waves, 42 bands, 172 projectors) on the mixed path, in the launch
+configuration the benchmark times (the PCG iteration captured as a CUDA
+graph and replayed), against the FP64 oracle.
+
+The oracle evaluates the whole state once per check (class densities of all
+42 bands, potentials, energies) and applies F and S to sampled bands only.
+Every comparison takes the GPU's own orbitals as the oracle's input, so it
+measures the evaluation error of one step and not the divergence of two
+trajectories.  Tolerances (FP32 rounding, 2^-24 per operation):
+  orbitals, densities, S|n>: 2e-6 relative;  F|n>: 2e-5 relative;
+  energies: 2e-7 of the sum of the magnitudes of the energy terms (the
+  kinetic, local, non-local, Hartree and exchange terms, some hundred Ha,
+  each summed with compensation from FP32 products);
+  S-orthonormality after a step: 5e-6.
+Properties that hold at any size: the first PCG steps descend, the DIIS
+coefficients sum to one, and the graph replay gives the same energy as the
+oracle's evaluation of the orbitals it produced."""
+import numpy as np
+import pytest
+
+from oracle import roks as R
+from paper_2605_28637_gb300 import synthetic as syn
+from tests.gpu_helpers import built, rel, to_np
+
+pytestmark = pytest.mark.gpu
+
+TERMS = ("kin", "loc", "nl", "H", "x_M", "x_T")
+
+
+@pytest.fixture(scope="module")
+def pair():
+    cfg = syn.make_config("organic-96", 0)
+    roks = built()
+    ctx = roks.Context(cfg, "mixed")
+    s = R.System(cfg)
+    u = syn.orbital_uniforms(cfg, ctx.npw)
+    yield roks, ctx, s, u
+    ctx.close()
+
+
+def oracle_energy(s, P):
+    E = s.energies(P)
+    return E["total"], sum(abs(E[k]) for k in TERMS)
+
+
+def check_orthonormal(s, P):
+    B = s.P.conj().T @ P
+    O = P.conj().T @ P + B.conj().T @ s.Q @ B
+    assert np.abs(O - np.eye(P.shape[1])).max() < 5e-6
+
+
+def test_organic96_state_and_apply(pair):
+    roks, ctx, s, u = pair
+    psi = ctx.init_orbitals(u)
+    P = to_np(psi, s.npw)
+    assert rel(P, s.initial_orbitals(u)) < 2e-6
+    rho = ctx.density(psi, want_rho=True).cpu().numpy()
+    rho_ref = s.class_densities(P)
+    assert rel(rho, rho_ref) < 2e-6
+    E = ctx.potential()
+    pot = s.potentials(rho_ref)
+    Eref = s.energies(P, pot)
+    scale = sum(abs(Eref[k]) for k in TERMS)
+    assert abs(E["E_total"] - Eref["total"]) < 2e-7 * scale, (E["E_total"], Eref["total"], scale)
+    f, sp, _ = ctx.apply_h(psi)
+    idx = [0, 17, s.n_closed - 1, s.n_closed, s.n_closed + 1]   # closed bands and both open bands
+    F_ref, S_ref = s.apply(P[:, idx], pot, classes=s.cls[idx])
+    assert rel(to_np(f, s.npw)[:, idx], F_ref) < 2e-5
+    assert rel(to_np(sp, s.npw)[:, idx], S_ref) < 2e-6
+
+
+def test_organic96_pcg_graph_replay(pair):
+    roks, ctx, s, u = pair
+    psi = ctx.init_orbitals(u)
+    E_prev = None
+    for it in range(3):   # eager, captured, replayed
+        info = ctx.pcg_step(psi)
+        assert info["E_new"] < info["E"], (it, info)
+        if E_prev is not None:
+            assert info["E"] == E_prev
+        E_prev = info["E_new"]
+    P = to_np(psi, s.npw)
+    check_orthonormal(s, P)
+    E_ref, scale = oracle_energy(s, P)
+    assert abs(E_prev - E_ref) < 2e-7 * scale, (E_prev, E_ref, scale)
+
+
+def test_organic96_diis(pair):
+    roks, ctx, s, u = pair
+    psi = ctx.init_orbitals(u)
+    for it in range(3):
+        info = ctx.diis_step(psi, history=4)
+        assert 1 <= info["window"] <= it + 1
+        assert abs(sum(info["coef"]) - 1.0) < 1e-12
+        assert np.isfinite(info["E_new"]) and info["res_norm"] > 0
+    P = to_np(psi, s.npw)
+    check_orthonormal(s, P)
+    E_ref, scale = oracle_energy(s, P)
+    assert abs(info["E_new"] - E_ref) < 2e-7 * scale, (info["E_new"], E_ref, scale)
