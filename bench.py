@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--converge-seconds", type=float, default=60.0,
                     help="wall-clock cap of each time-to-convergence run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--diis-steps", type=int, default=50,
+                    help="timed DIIS steps (roks_diis_step) after the PCG legs; 0 skips them")
     return ap.parse_args()
 
 
@@ -307,6 +309,33 @@ def converge(cfg, precision, cap, torch, max_seconds, params=None):
     return out
 
 
+def converge_diis(cfg, precision, cap, torch, max_seconds, history=6):
+    """DIIS (roks_diis_step, lambda = 1/2) from the seeded start to |dE| < 1e-6 Ha
+    twice, capped like converge()."""
+    from paper_2605_28637_gb300 import roks, synthetic as syn
+    ctx = roks.Context(cfg, precision, e_tol=1e-6)
+    psi = ctx.init_orbitals(syn.orbital_uniforms(cfg, ctx.npw))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    it, info = 0, None
+    for it in range(1, cap + 1):
+        info = ctx.diis_step(psi, history=history)
+        if info["converged"] or time.perf_counter() - t0 > max_seconds:
+            break
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    out = {"seconds": dt, "iterations": it, "converged": bool(info and info["converged"]),
+           "E_final": info["E_new"] if info else None, "res_norm_final": info["res_norm"] if info else None,
+           "s_per_iter": dt / max(it, 1), "history": history}
+    ctx.close()
+    return out
+
+
+def csize_of(precision):
+    """Bytes of one complex coefficient on the path."""
+    return 16 if precision == "fp64" else 8
+
+
 def train_network(torch):
     """The preconditioner network trained on seeded tiny systems (singlet and
     closed shell, seeds 1-8), on the GPU; returns (device params, seconds, losses)."""
@@ -396,6 +425,50 @@ def run_gpu(args):
         torch.distributed.all_reduce(t2, op=torch.distributed.ReduceOp.MAX)
     e2e_value = ctx.nb * e2e_steps * world / (float(t2.item()) / 1000.0)
     bytes_psi = psi.numel() * psi.element_size()
+    # ---- DIIS steps (roks_diis_step: eager launches, one host read per step)
+    # on a copy of the orbitals; its history builds during the warm-up
+    diis = None
+    if args.diis_steps > 0:
+        pd = psi.clone()
+        for _ in range(max(3, args.warmup)):
+            ctx.diis_step(pd)
+        roks.roks_profile_read(ctx.ctx)
+        torch.cuda.synchronize()
+        e0.record(ctx.stream)
+        dinfo = [ctx.diis_step(pd) for _ in range(args.diis_steps)]
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        d_ms = e0.elapsed_time(e1)
+        d_launch = [e for e in roks.roks_profile_read(ctx.ctx) if e["name"] == "kernel_launches"]
+        t3 = torch.tensor([d_ms], dtype=torch.float64, device="cuda")
+        if world > 1:
+            torch.distributed.all_reduce(t3, op=torch.distributed.ReduceOp.MAX)
+        d_ms = float(t3.item())
+        # per-family device times of the same steps (eager, CUDA events per family)
+        # and the HBM roofline of the extrapolation kernel: it reads 2h band
+        # blocks (h pairs of the window) and writes one
+        roks.roks_profile_enable(ctx.ctx, 1)
+        pinfo = [ctx.diis_step(pd) for _ in range(10)]
+        dprof = [e for e in roks.roks_profile_read(ctx.ctx) if e["name"] != "kernel_launches"]
+        roks.roks_profile_enable(ctx.ctx, 0)
+        comb = next((e for e in dprof if e["name"] == "diis_combine"), None)
+        comb_roof = None
+        if comb is not None:
+            blk = ctx.nb * ctx.npw * csize_of(args.precision)
+            alg = sum((2 * i["window"] + 1) * blk for i in pinfo)
+            achieved = alg / (comb["ms"] / 1000.0) / 1e9
+            hbm, peak_kind = peaks()
+            comb_roof = {"bound": "hbm", "kernel": "k_diis_combine", "achieved": achieved, "peak": hbm,
+                         "unit": "GB/s", "frac": achieved / hbm, "peak_kind": f"{peak_kind} (copy bandwidth)",
+                         "algorithmic_bytes_per_launch": alg / len(pinfo),
+                         "ms_per_launch": comb["ms"] / comb["launches"]}
+        diis = {"value": ctx.nb * args.diis_steps * world / (d_ms / 1000.0), "unit": UNIT,
+                "roofline_combine": comb_roof,
+                "profile": {e["name"]: {"launches": e["launches"], "ms": e["ms"]} for e in dprof},
+                "ms_per_step": d_ms / args.diis_steps, "steps": args.diis_steps, "history": 6, "tau": 0.5,
+                "launches_per_step": d_launch[0]["launches"] / args.diis_steps if d_launch else None,
+                "launch": "eager (the ring slot changes every step), host read of the step's scalars",
+                "E_last": dinfo[-1]["E_new"], "window_last": dinfo[-1]["window"]}
     # ---- roofline of the dominant kernel family
     csize = 16 if args.precision == "fp64" else 8
     rsize = 8 if args.precision == "fp64" else 4
@@ -447,6 +520,8 @@ def run_gpu(args):
                "network": {"trained_on": "tiny-16 seeds 1-8, singlet and closed shell", "train_seconds": t_train,
                            "loss_first": losses[0], "loss_last": losses[-1]},
                "speedup_s_per_iter_mixed_vs_fp64": fp64["s_per_iter"] / mixed["s_per_iter"],
+               "mixed_diis": converge_diis(cfg, "mixed", args.converge_iters, torch,
+                                           min(args.converge_seconds, 20.0)),
                "note": "seconds to convergence compare only between legs with same_state_as_fp64"}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -472,6 +547,7 @@ def run_gpu(args):
             "clocks": ck,
             "apply_only": {"value": ctx.nb / (apply_ms / 1000.0), "unit": UNIT, "ms_per_apply_all_bands": apply_ms},
             "pcg": pcg,
+            "diis": diis,
             "profile": {e["name"]: {"launches": e["launches"], "ms": e["ms"]} for e in prof},
             "launch": "one CUDA graph per PCG iteration",
             "E_last": infos[-1]["E_new"] if infos else None,

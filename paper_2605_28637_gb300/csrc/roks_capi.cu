@@ -89,6 +89,11 @@ struct roks_ctx {
     // state
     const void* cache_psi = nullptr;   // potentials valid for this buffer (pcg chain)
     const void* b_psi = nullptr;       // d_B holds P^H psi for this buffer
+    // Yp holds the y-stage planes of every band of this buffer (leading
+    // dimension yp_ld): the density's x stage only reads them, so the next
+    // apply of the same orbitals starts at the x stage
+    const void* yp_psi = nullptr;
+    int64_t yp_ld = 0;
     bool pot_valid = false;
     int n_small = 0;
     // DIIS history: ring of (Psi_j, e_j) pairs, the device state of B and
@@ -267,6 +272,8 @@ struct Impl {
         const V* p = ccv(psi);
         { PROF("fft_z_inv"); band_z_inv<T>(s, ccv(ctx->d_tw), p, ld, 0, ctx->nb, cv(ctx->d_Zc), st); }
         { PROF("fft_y_inv"); band_y_inv<T>(s, ccv(ctx->d_tw), cv(ctx->d_Zc), cv(ctx->d_Yp), ctx->nb, st); }
+        ctx->yp_psi = psi;
+        ctx->yp_ld = ld;
         if (ctx->alpha != 0.0) {
             PROF("exchange");
             exchange(ctx, false);
@@ -310,14 +317,25 @@ struct Impl {
     // F = F^{k(n)}|n>, S = S|n> (S optional), with the current potentials.
     // reuse_B: d_B already holds P^H psi (the PCG chain keeps it from the
     // orthonormalisation of the accepted point)
+    // Yp <- y-stage planes of psi
+    static void planes(roks_ctx* ctx, const void* psi, int64_t ld) {
+        const Sphere s = sphere(ctx);
+        cudaStream_t st = ctx->st;
+        { PROF("fft_z_inv"); band_z_inv<T>(s, ccv(ctx->d_tw), ccv(psi), ld, 0, ctx->nb, cv(ctx->d_Zc), st); }
+        { PROF("fft_y_inv"); band_y_inv<T>(s, ccv(ctx->d_tw), cv(ctx->d_Zc), cv(ctx->d_Yp), ctx->nb, st); }
+        ctx->yp_psi = psi;
+        ctx->yp_ld = ld;
+    }
+
+    // planes_ready: Yp already holds the planes of psi (yp_psi), so the
+    // transform starts at the x stage
     static roks_status apply(roks_ctx* ctx, const void* psi, int64_t ld, void* F, int64_t ldf, void* S,
-                             int64_t lds, bool reuse_B = false) {
+                             int64_t lds, bool reuse_B = false, bool planes_ready = false) {
         const Sphere s = sphere(ctx);
         cudaStream_t st = ctx->st;
         const V* p = ccv(psi);
         const int N = ctx->N;
-        { PROF("fft_z_inv"); band_z_inv<T>(s, ccv(ctx->d_tw), p, ld, 0, ctx->nb, cv(ctx->d_Zc), st); }
-        { PROF("fft_y_inv"); band_y_inv<T>(s, ccv(ctx->d_tw), cv(ctx->d_Zc), cv(ctx->d_Yp), ctx->nb, st); }
+        if (!planes_ready) planes(ctx, psi, ld);
         if (ctx->alpha != 0.0) {
             PROF("exchange");
             exchange(ctx, true);
@@ -328,6 +346,7 @@ struct Impl {
                             ctx->alpha != 0.0 ? ccv(ctx->d_Xx) : nullptr, 0, ctx->nb, ctx->nc,
                             T(1.0 / (double(N) * N * N)), st);
         }
+        ctx->yp_psi = nullptr;   // the x stage works in place
         { PROF("fft_y_fwd"); band_y_fwd<T>(s, ccv(ctx->d_tw), cv(ctx->d_Yp), cv(ctx->d_Zc), ctx->nb, st); }
         {
             PROF("fft_z_fwd");
@@ -516,7 +535,7 @@ struct Impl {
         roks_status r;
         pcg_take_energy(ctx->d_E, ctx->d_sc, SC_FIELD(E0), st);
         // F Psi, S Psi, theta, d
-        r = apply(ctx, psi, ld, ctx->W_F, l, ctx->W_S, l, true);
+        r = apply(ctx, psi, ld, ctx->W_F, l, ctx->W_S, l, true, true);
         if (r != ROKS_OK) return r;
         {
             PROF("subspace_theta");
@@ -579,6 +598,9 @@ struct Impl {
         CK(cudaMemcpyAsync(ctx->W_sprev, ctx->W_s, sizeof(V) * l * nb, cudaMemcpyDeviceToDevice, st));
         CK(cudaMemcpyAsync(ctx->d_Aprev, ctx->d_A, sizeof(double2) * nb * nb, cudaMemcpyDeviceToDevice, st));
         pcg_finish(ctx->d_sc, st);
+        // the accepted point's density left its planes in Yp; psi now holds it
+        ctx->yp_psi = psi;
+        ctx->yp_ld = ld;
         CK(cudaGetLastError());
         return ROKS_OK;
     }
@@ -646,9 +668,14 @@ struct Impl {
                        ctx->d_gemm_work, ctx->gemm_work_elems, st);
             ctx->b_psi = psi;
         }
+        // the iteration's apply starts from the planes in Yp (a captured
+        // iteration leaves those of its accepted point there)
+        if (!(ctx->yp_psi == psi && ctx->yp_ld == ld)) planes(ctx, psi, ld);
         r = pcg_run(ctx, psi, ld);
         if (r != ROKS_OK) return r;
         ctx->b_psi = psi;   // d_B: projector coefficients of the accepted point, now in psi
+        ctx->yp_psi = psi;
+        ctx->yp_ld = ld;
         // scalars and status flag in one round trip (pinned host copies)
         CK(cudaMemcpyAsync(ctx->h_sc, ctx->d_sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(ctx->h_flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -711,7 +738,7 @@ struct Impl {
             ctx->b_psi = psi;
         }
         CK(cudaMemcpyAsync(&ctx->d_diis->E0, ctx->d_E + 10, sizeof(double), cudaMemcpyDeviceToDevice, st));
-        r = apply(ctx, psi, ld, ctx->W_F, l, ctx->W_S, l, ctx->nproj > 0);
+        r = apply(ctx, psi, ld, ctx->W_F, l, ctx->W_S, l, ctx->nproj > 0, ctx->yp_psi == psi && ctx->yp_ld == ld);
         if (r != ROKS_OK) return r;
         {
             PROF("subspace_theta");
@@ -816,6 +843,7 @@ void reset_history(roks_ctx* ctx) {
     ctx->diis_count = 0;
     ctx->diis_small = 0;
     ctx->pcg_fresh = false;
+    ctx->yp_psi = nullptr;
     cudaStreamSynchronize(ctx->st);
 }
 
