@@ -103,6 +103,7 @@ struct roks_ctx {
     void* diis_ring = nullptr;
     int diis_slots = 0;
     DiisState* d_diis = nullptr;
+    double* d_diis_part = nullptr;   // block partials of the Gram row
     DiisState* h_diis = nullptr;
     long long diis_count = 0;
     int diis_small = 0;
@@ -756,9 +757,8 @@ struct Impl {
             // R = F - S Lambda
             gemm_nn_io<T>(npw, nb, nb, ccv(ctx->W_S), l, ctx->d_Gam, nb, ccv(ctx->W_F), l, cv(ctx->W_G), l, -1.0,
                           1.0, ctx->d_gemm_work, st);
-            column_total<T>(3, npw, nb, ccv(ctx->W_G), l, nullptr, 0, static_cast<const T*>(ctx->d_g2half),
-                            ctx->d_colpart, &ctx->d_diis->rnorm2, 1.0, st);
-            // e = K R (tau enters the extrapolation; d does not depend on a common scale of e)
+            // e = K R (tau enters the extrapolation; d does not depend on a common
+            // scale of e); the band norms |R_n|^2 stay in d_colout[0, nb) for rnorm2
             column_sums<T>(1, npw, nb, ccv(ctx->W_G), l, nullptr, 0, static_cast<const T*>(ctx->d_g2half),
                            ctx->d_colpart, ctx->d_colout, st);
             precondition<T>(npw, nb, ccv(ctx->W_G), l, static_cast<const T*>(ctx->d_g2half), ctx->d_colout, Ej, l,
@@ -771,11 +771,9 @@ struct Impl {
         for (int k = 0; k < ord.n; ++k) ord.slot[k] = int((ctx->diis_count + 1 - ord.n + k) % o.history);
         {
             PROF("diis_gram");
-            for (int k = 0; k < ord.n; ++k)
-                column_total<T>(2, npw, nb, Ej, l, cv(ctx->diis_ring) + (int64_t)(o.history + ord.slot[k]) * blk, l,
-                                static_cast<const T*>(ctx->d_g2half), ctx->d_colpart,
-                                &ctx->d_diis->B[slot * kDiisMax + ord.slot[k]], 1.0, st);
-            diis_solve(ctx->d_diis, ord, 1e-7, st);
+            diis_gram<T>(npw, nb, Ej, cv(ctx->diis_ring) + (int64_t)o.history * blk, blk, l, ord, ctx->d_diis_part,
+                         ctx->d_diis, st);
+            diis_solve(ctx->d_diis, ord, 1e-7, ctx->d_colout, nb, st);
         }
         {
             PROF("diis_combine");
@@ -1359,6 +1357,7 @@ roks_status roks_diis_step(roks_ctx* ctx, void* psi, int64_t ld, const roks_diis
     ctx->diis_ld = ld;
     if (!ctx->d_diis) {
         CK(dalloc(ctx, &ctx->d_diis, sizeof(DiisState)));
+        CK(dalloc(ctx, &ctx->d_diis_part, sizeof(double) * kDiisMax * (size_t)diis_gram_blocks(ctx->npw, ctx->nb)));
         void* hp = nullptr;
         CK(cudaMallocHost(&hp, sizeof(DiisState)));
         ctx->h_diis = static_cast<DiisState*>(hp);
