@@ -94,12 +94,19 @@ def energy_gradient(sys_: R.System, Psi, gamma=None) -> np.ndarray:
             dE[a, nu] = loc.real
             if len(cols) == 0:
                 continue
-            dP = np.zeros_like(sys_.P)
-            dP[:, cols] = -1j * sys_.G[:, nu][:, None] * sys_.P[:, cols]
-            dVnl = dP @ sys_.D @ sys_.P.conj().T + sys_.P @ sys_.D @ dP.conj().T
-            dS = dP @ sys_.Q @ sys_.P.conj().T + sys_.P @ sys_.Q @ dP.conj().T
-            nl = sum(wn[n] * np.vdot(Psi[:, n], dVnl @ Psi[:, n]) for n in range(sys_.nb))
-            C = Psi.conj().T @ dS @ Psi
+            # <p_i|n> and <dp_i|n> for the projectors of atom a (the others do
+            # not move); D and Q are block diagonal, so their block suffices
+            Pa = sys_.P[:, cols]
+            dPa = -1j * sys_.G[:, nu][:, None] * Pa
+            Ba = Pa.conj().T @ Psi
+            dBa = dPa.conj().T @ Psi
+            Da = sys_.D[np.ix_(cols, cols)]
+            Qa = sys_.Q[np.ix_(cols, cols)]
+            # <n|dV_nl|n> = <n|dP D P^H + P D dP^H|n>
+            nl = sum(wn[n] * (np.vdot(dBa[:, n], Da @ Ba[:, n]) + np.vdot(Ba[:, n], Da @ dBa[:, n]))
+                     for n in range(sys_.nb))
+            # C_mn = <m|dP Q P^H + P Q dP^H|n>
+            C = dBa.conj().T @ Qa @ Ba + Ba.conj().T @ Qa @ dBa
             ov = np.sum(gamma * C)
             dE[a, nu] += nl.real - ov.real
     return dE
