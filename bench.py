@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--converge-seconds", type=float, default=60.0,
                     help="wall-clock cap of each time-to-convergence run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--force-calls", type=int, default=10,
+                    help="timed roks_forces calls on the final orbitals; 0 skips them")
     ap.add_argument("--diis-steps", type=int, default=50,
                     help="timed DIIS steps (roks_diis_step) after the PCG legs; 0 skips them")
     return ap.parse_args()
@@ -469,6 +471,25 @@ def run_gpu(args):
                 "launches_per_step": d_launch[0]["launches"] / args.diis_steps if d_launch else None,
                 "launch": "eager (the ring slot changes every step), host read of the step's scalars",
                 "E_last": dinfo[-1]["E_new"], "window_last": dinfo[-1]["window"]}
+    # ---- forces on the atoms (roks_forces: density, potentials, apply, the
+    # projector derivatives and the local term; one host read per call)
+    forces_leg = None
+    if args.force_calls > 0:
+        for _ in range(2):
+            ctx.forces(psi)
+        roks.roks_profile_read(ctx.ctx)
+        torch.cuda.synchronize()
+        e0.record(ctx.stream)
+        for _ in range(args.force_calls):
+            Fa = ctx.forces(psi)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        f_ms = e0.elapsed_time(e1) / args.force_calls
+        f_launch = [e for e in roks.roks_profile_read(ctx.ctx) if e["name"] == "kernel_launches"]
+        forces_leg = {"ms_per_call": f_ms, "calls": args.force_calls, "natoms": ctx.natoms,
+                      "launches_per_call": f_launch[0]["launches"] / args.force_calls if f_launch else None,
+                      "max_abs_force_ha_per_bohr": float(abs(Fa).max()),
+                      "launch": "eager, one host read per call"}
     # ---- roofline of the dominant kernel family
     csize = 16 if args.precision == "fp64" else 8
     rsize = 8 if args.precision == "fp64" else 4
@@ -548,6 +569,7 @@ def run_gpu(args):
             "apply_only": {"value": ctx.nb / (apply_ms / 1000.0), "unit": UNIT, "ms_per_apply_all_bands": apply_ms},
             "pcg": pcg,
             "diis": diis,
+            "forces": forces_leg,
             "profile": {e["name"]: {"launches": e["launches"], "ms": e["ms"]} for e in prof},
             "launch": "one CUDA graph per PCG iteration",
             "E_last": infos[-1]["E_new"] if infos else None,

@@ -250,6 +250,26 @@ typedef struct {
 ROKS_API roks_status roks_diis_step(roks_ctx* ctx, void* psi, int64_t ld, const roks_diis_options* opt,
                                     roks_diis_info* info);
 
+/* Forces on the atoms (Sec. II B, generalised Hellmann-Feynman theorem):
+ *   F_Inu = -dE/dR_Inu,
+ *   dE/dR_Inu = sum_{L sigma n} c_L f_n^{sigma L} <n|dH^{sigma L}/dR_Inu|n>
+ *             - sum_mn gamma_mn <m|dS/dR_Inu|n>,
+ * with gamma of Eq. 11 formed from psi.  In this model the wells and the
+ * projectors carry the dependence on the atoms:
+ *   local:     Omega sum_G (-i G_nu) v_I(G) e^{-iG.R_I} conj(rho_w(G)),
+ *              rho_w = sum_n w_n |psi_n|^2, grid G without the Nyquist planes;
+ *   projector: 2 Re sum_{i in I} sum_n conj(<dp_i|n>) [w_n (D B)_in - (Q B Gam)_in],
+ *              B = P^H psi, dp_i/dR_nu = -i G_nu p_i, Gam_mn = gamma_nm.
+ * The paper sums the overlap term in the basis that diagonalises gamma; the
+ * double sum used here has the same value.  At stationary orbitals this is
+ * the total derivative of the minimised E_S; at other orbitals it is the
+ * derivative at fixed orbitals and multipliers of E - sum gamma (S - 1).
+ * forces_host: natoms x 3 doubles (Ha/Bohr, atom order of roks_setup, x y z
+ * innermost), written before the call returns.  Recomputes the density and
+ * potentials of psi (they become those the next PCG or DIIS step uses).
+ * ROKS_EDIVERGED for a non-finite force.  Synchronises. */
+ROKS_API roks_status roks_forces(roks_ctx* ctx, const void* psi, int64_t ld, double* forces_host);
+
 /* Energies of the last completed density/potential evaluation.  Synchronises. */
 ROKS_API roks_status roks_energies_get(roks_ctx* ctx, roks_energies* e);
 

@@ -13,6 +13,7 @@
 #include "../../include/roks.h"
 #include "roks_diis.cuh"
 #include "roks_exx.cuh"
+#include "roks_force.cuh"
 #include "roks_grid.cuh"
 #include "roks_mlp.cuh"
 
@@ -111,6 +112,15 @@ struct roks_ctx {
     const void* diis_psi = nullptr;
     int64_t diis_ld = 0;
     bool pcg_fresh = false;
+    // forces (roks_forces): atom table (x, y, z, depth, width), owner atom of
+    // every projector, and scratch allocated on the first call
+    std::vector<double> atoms_h;
+    std::vector<int> proj_atom_h;
+    double* d_atoms = nullptr;
+    int* d_proj_atom = nullptr;
+    void *d_fdP = nullptr, *d_ftab = nullptr, *d_famp = nullptr, *d_fw2h = nullptr;
+    double2 *d_fdB = nullptr, *d_fY = nullptr;
+    double *d_fc = nullptr, *d_fpart = nullptr, *d_forces = nullptr;
     // learned correction of the preconditioner; once its run meets the
     // convergence criterion, TPA alone continues and must meet it again
     float* d_mlp = nullptr;
@@ -714,6 +724,58 @@ struct Impl {
         return ROKS_OK;
     }
 
+    // Forces (roks_forces): potentials, F Psi and gamma of psi, the
+    // projector derivatives dB_nu = (dP_nu)^H Psi, the projector terms per
+    // projector and the local term per atom (k_force.cu), summed per atom.
+    static roks_status forces(roks_ctx* ctx, const void* psi, int64_t ld, double* out_host) {
+        cudaStream_t st = ctx->st;
+        const int nb = ctx->nb, npw = ctx->npw, np_ = ctx->nproj;
+        const int64_t l = ctx->ld_min;
+        roks_status r = density(ctx, psi, ld, nullptr);
+        if (r != ROKS_OK) return r;
+        r = potential(ctx);
+        if (r != ROKS_OK) return r;
+        ctx->cache_psi = psi;
+        ctx->pot_valid = true;
+        r = apply(ctx, psi, ld, ctx->W_F, l, nullptr, 0, np_ > 0 && ctx->b_psi == psi,
+                  ctx->yp_psi == psi && ctx->yp_ld == ld);
+        if (r != ROKS_OK) return r;
+        const double b = 2.0 * M_PI / ctx->L;
+        {
+            PROF("force");
+            gemm_cn<T>(nb, nb, npw, ccv(psi), ld, ccv(ctx->W_F), l, ctx->d_Th, nb, ctx->d_gemm_work,
+                       ctx->gemm_work_elems, st);
+            diis_multipliers(nb, ctx->d_Th, -1, -1, 0.5, 0.5, ctx->d_Gam, st);   // Gam = (theta + theta^H)/2
+            if (np_ > 0) {
+                for (int nu = 0; nu < 3; ++nu) {
+                    force_dP<T>(npw, np_, ccv(ctx->d_P), l, ctx->d_miller, b, nu, cv(ctx->d_fdP), st);
+                    gemm_cn<T>(np_, nb, npw, ccv(ctx->d_fdP), l, ccv(psi), ld, ctx->d_fdB + (int64_t)nu * np_ * nb,
+                               np_, ctx->d_gemm_work, ctx->gemm_work_elems, st);
+                }
+                apply_DQ(np_, nb, ctx->d_B, ctx->d_blk_off, ctx->d_blk_n, ctx->d_Drow, ctx->d_Qrow, ctx->d_wband,
+                         ctx->d_DB, ctx->d_QB, st);
+                small_gemm(np_, nb, nb, ctx->d_QB, np_, false, ctx->d_Gam, nb, false, ctx->d_fY, np_, 1.0, 0.0, st);
+                force_nl(np_, nb, ctx->d_fdB, ctx->d_DB, ctx->d_fY, ctx->d_fc, st);
+            }
+            force_local<T>(ctx->N, ctx->L, ctx->natoms, ctx->d_atoms, ctx->d_rho3, ctx->cf.w,
+                           static_cast<const T*>(ctx->d_famp), static_cast<const T*>(ctx->d_fw2h), cv(ctx->d_ftab),
+                           reinterpret_cast<V*>(ctx->d_grid), ccv(ctx->d_tw), ctx->d_fpart, st);
+            const double N3 = double(ctx->N) * ctx->N * ctx->N;
+            force_collect(ctx->natoms, np_, ctx->d_proj_atom, ctx->d_fc, ctx->d_fpart, ctx->omega * b / N3,
+                          ctx->d_forces, st);
+        }
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(out_host, ctx->d_forces, sizeof(double) * 3 * ctx->natoms, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (tc_timeout_take())
+            return fail(ctx, ROKS_ETIMEOUT, "a tensor-core completion wait ran out (bounded mbarrier wait)");
+        if (stream_timeout_take())
+            return fail(ctx, ROKS_ETIMEOUT, "a bulk-copy wait of a streamed contraction ran out (bounded mbarrier wait)");
+        for (int i = 0; i < 3 * ctx->natoms; ++i)
+            if (!std::isfinite(out_host[i])) return fail(ctx, ROKS_EDIVERGED, "non-finite force");
+        return ROKS_OK;
+    }
+
     // One DIIS step (roks_diis_step): residual with the coupling
     // coefficients, e = K R into the ring, the new row of B, the window and
     // its coefficients on the device, the extrapolated orbitals, their
@@ -964,6 +1026,7 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
         if (sp.nproj < 0 || sp.nproj > kMaxBlk) return bail(ROKS_EINVAL, "bad projector count");
         if (sp.nproj > 0 && (!sp.l || !sp.m || !sp.rc || !sp.D || !sp.Q)) return bail(ROKS_EINVAL, "bad species");
         const int off = (int)blk_off.size();
+        for (int c = 0; c < sp.nproj; ++c) ctx->proj_atom_h.push_back(a);
         for (int c = 0; c < sp.nproj; ++c) {
             if ((sp.l[c] != 0 && sp.l[c] != 1) || sp.m[c] < 0 || sp.m[c] > 2 || !(sp.rc[c] > 0))
                 return bail(ROKS_EINVAL, "bad projector channel");
@@ -977,6 +1040,7 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
         }
     }
     ctx->nproj = (int)blk_off.size();
+    ctx->atoms_h = atomtab;
     // -------- device allocations
     const bool f64 = ctx->prec == ROKS_FP64;
     const size_t cs = f64 ? sizeof(double2) : sizeof(float2);
@@ -1080,6 +1144,7 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     double* d_proj = nullptr;
     AL(d_atoms, sizeof(double) * (atomtab.size() + 1));
     AL(d_proj, sizeof(double) * (proj.size() + 1));
+    ctx->d_atoms = d_atoms;
 #undef AL
     // -------- uploads
     std::vector<int> shell(nb), dummy;
@@ -1387,6 +1452,55 @@ roks_status roks_diis_step(roks_ctx* ctx, void* psi, int64_t ld, const roks_diis
     tmp.converged = ctx->diis_small >= 2 ? 1 : 0;
     if (info) *info = tmp;
     return r;
+}
+
+roks_status roks_forces(roks_ctx* ctx, const void* psi, int64_t ld, double* forces_host) {
+    if (!ctx) return ROKS_EINVAL;
+    roks_status r = check_psi(ctx, psi, ld);
+    if (r != ROKS_OK) return r;
+    if (!forces_host) return fail(ctx, ROKS_EINVAL, "null force array");
+    if (ctx->natoms == 0) return ROKS_OK;
+    const bool f64 = ctx->prec == ROKS_FP64;
+    if (!ctx->d_forces) {
+        const size_t cs = f64 ? sizeof(double2) : sizeof(float2);
+        const size_t rs = f64 ? sizeof(double) : sizeof(float);
+        const int na = ctx->natoms, np_ = ctx->nproj, nb = ctx->nb;
+        cudaError_t e = cudaSuccess;
+        auto al = [&](auto** p, size_t bytes) {
+            if (e == cudaSuccess) e = dalloc(ctx, p, bytes);
+        };
+        al(&ctx->d_proj_atom, sizeof(int) * (np_ + 1));
+        al(&ctx->d_fdP, cs * (size_t)ctx->ld_min * (np_ > 0 ? np_ : 1));
+        al(&ctx->d_fdB, sizeof(double2) * 3 * (size_t)(np_ > 0 ? np_ : 1) * nb);
+        al(&ctx->d_fY, sizeof(double2) * (size_t)(np_ > 0 ? np_ : 1) * nb);
+        al(&ctx->d_fc, sizeof(double) * 3 * (np_ + 1));
+        al(&ctx->d_ftab, cs * (size_t)na * 3 * ctx->N);
+        al(&ctx->d_famp, rs * na);
+        al(&ctx->d_fw2h, rs * na);
+        al(&ctx->d_fpart, sizeof(double) * (size_t)na * 3 * kForceLocBlocks);
+        al(&ctx->d_forces, sizeof(double) * 3 * na);
+        if (e != cudaSuccess) return fail(ctx, ROKS_ENOMEM, "force workspaces");
+        // per atom: amplitude -d (2 pi w^2)^{3/2} / Omega and w^2 / 2 of the well
+        std::vector<double> amp(na), w2h(na);
+        for (int a = 0; a < na; ++a) {
+            const double d = ctx->atoms_h[5 * a + 3], w = ctx->atoms_h[5 * a + 4];
+            amp[a] = -d * std::pow(2.0 * M_PI * w * w, 1.5) / ctx->omega;
+            w2h[a] = 0.5 * w * w;
+        }
+        if (f64) {
+            CK(cudaMemcpyAsync(ctx->d_famp, amp.data(), sizeof(double) * na, cudaMemcpyHostToDevice, ctx->st));
+            CK(cudaMemcpyAsync(ctx->d_fw2h, w2h.data(), sizeof(double) * na, cudaMemcpyHostToDevice, ctx->st));
+        } else {
+            std::vector<float> a32(amp.begin(), amp.end()), w32(w2h.begin(), w2h.end());
+            CK(cudaMemcpyAsync(ctx->d_famp, a32.data(), sizeof(float) * na, cudaMemcpyHostToDevice, ctx->st));
+            CK(cudaMemcpyAsync(ctx->d_fw2h, w32.data(), sizeof(float) * na, cudaMemcpyHostToDevice, ctx->st));
+        }
+        if (np_ > 0)
+            CK(cudaMemcpyAsync(ctx->d_proj_atom, ctx->proj_atom_h.data(), sizeof(int) * np_, cudaMemcpyHostToDevice,
+                               ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+    }
+    return f64 ? Impl<double>::forces(ctx, psi, ld, forces_host) : Impl<float>::forces(ctx, psi, ld, forces_host);
 }
 
 roks_status roks_profile_enable(roks_ctx* ctx, int enable) {

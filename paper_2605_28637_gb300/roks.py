@@ -81,9 +81,10 @@ class roks_profile_entry(C.Structure):
 
 
 EXPORTS = ["roks_setup", "roks_basis", "roks_init_orbitals", "roks_density", "roks_potential", "roks_apply_h",
-           "roks_orthonormalize", "roks_pcg_step", "roks_diis_step", "roks_energies_get", "roks_profile_enable",
-           "roks_profile_read", "roks_orthonormalize_noalloc", "roks_mlp_forward", "roks_mlp_grad", "roks_mlp_adam",
-           "roks_set_preconditioner", "roks_precondition", "roks_mlp_grad_work", "roks_last_error", "roks_destroy"]
+           "roks_orthonormalize", "roks_pcg_step", "roks_diis_step", "roks_forces", "roks_energies_get",
+           "roks_profile_enable", "roks_profile_read", "roks_orthonormalize_noalloc", "roks_mlp_forward",
+           "roks_mlp_grad", "roks_mlp_adam", "roks_set_preconditioner", "roks_precondition", "roks_mlp_grad_work",
+           "roks_last_error", "roks_destroy"]
 
 ROKS_MLP_PARAMS = 4481
 ROKS_PRECOND_TPA = 0
@@ -115,6 +116,7 @@ def load(path: str | None = None) -> C.CDLL:
     lib.roks_orthonormalize.argtypes = [P, P, C.c_int64]
     lib.roks_pcg_step.argtypes = [P, P, C.c_int64, C.POINTER(roks_step_info)]
     lib.roks_diis_step.argtypes = [P, P, C.c_int64, C.POINTER(roks_diis_options), C.POINTER(roks_diis_info)]
+    lib.roks_forces.argtypes = [P, P, C.c_int64, C.POINTER(C.c_double)]
     lib.roks_energies_get.argtypes = [P, C.POINTER(roks_energies)]
     lib.roks_profile_enable.argtypes = [P, C.c_int]
     lib.roks_profile_read.argtypes = [P, C.POINTER(roks_profile_entry), C.c_int, C.POINTER(C.c_int)]
@@ -227,6 +229,13 @@ def roks_diis_step(ctx, psi, ld: int, history: int = 6, tau: float = 0.5, lambda
     return out
 
 
+def roks_forces(ctx, psi, ld: int, natoms: int) -> np.ndarray:
+    """F_Inu = -dE/dR_Inu (natoms x 3, Ha/Bohr)."""
+    out = np.zeros((natoms, 3), dtype=np.float64)
+    _check(ctx, load().roks_forces(ctx, _ptr(psi), ld, out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
+
+
 def roks_energies_get(ctx) -> dict:
     e = roks_energies()
     _check(ctx, load().roks_energies_get(ctx, C.byref(e)))
@@ -315,6 +324,7 @@ class Context:
         self.npw, self.nb, self.ld, self.miller = roks_basis(self.ctx)
         self.N = cfg["grid"]
         self.nproj = sum(len(cfg["species"][a["species"]]["l"]) for a in cfg["atoms"])
+        self.natoms = len(cfg["atoms"])
 
     def new_bands(self):
         return self.torch.zeros((self.nb, self.ld), dtype=self.cdtype, device="cuda")
@@ -351,6 +361,9 @@ class Context:
 
     def diis_step(self, psi, history: int = 6, tau: float = 0.5, lambda_ab: float = 0.5, lambda_ba: float = 0.5):
         return roks_diis_step(self.ctx, psi, self.ld, history, tau, lambda_ab, lambda_ba)
+
+    def forces(self, psi):
+        return roks_forces(self.ctx, psi, self.ld, self.natoms)
 
     def energies(self):
         return roks_energies_get(self.ctx)
