@@ -66,6 +66,30 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """Largest value of x over the ranks (all-reduce MAX on `device`); x itself
+    when one process runs.  Timings are reported as the slowest rank's."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_config(workload: str, rank: int) -> dict:
+    """Each replica steps its own seeded system (seed = rank): the path does not
+    shard, so N GPUs run N independent problems (weak scaling)."""
+    from paper_2605_28637_gb300 import synthetic as syn
+    return syn.make_config(workload, rank)
+
+
+def aggregate_value(nb: int, steps: int, world: int, ms_max: float) -> float:
+    """Band-applies per second of the whole job: all ranks' bands over the slowest rank's time."""
+    return nb * steps * world / (ms_max / 1000.0)
+
+
 # FP32 FMA rate from the unit counts and the maximum SM clock (no measured
 # FP32 peak is provided): 152 SMs x 128 lanes x 2 flops x 2.07 GHz
 FP32_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -368,7 +392,7 @@ def run_gpu(args):
     if world > 1:
         torch.distributed.barrier()
     from paper_2605_28637_gb300 import roks, synthetic as syn
-    cfg = syn.make_config(args.workload, rank)
+    cfg = replica_config(args.workload, rank)
     ctx = roks.Context(cfg, args.precision)
     u = syn.orbital_uniforms(cfg, ctx.npw)
     psi = ctx.init_orbitals(u)
@@ -390,11 +414,8 @@ def run_gpu(args):
     # the launching stream, over a profiled pass of the same steps (eager launches)
     prof_steps = min(args.steps, 20)
     prof_ms, _, prof = time_pcg(ctx, psi, prof_steps, torch, profile=True)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = ctx.nb * args.steps * world / (ms_max / 1000.0)
+    ms_max = max_over_ranks(ms, world)
+    value = aggregate_value(ctx.nb, args.steps, world, ms_max)
     # ---- apply-only throughput (roks_apply_h over all bands)
     f = ctx.new_bands()
     sp = ctx.new_bands()
@@ -422,10 +443,7 @@ def run_gpu(args):
     e1.record(ctx.stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    t2 = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t2, op=torch.distributed.ReduceOp.MAX)
-    e2e_value = ctx.nb * e2e_steps * world / (float(t2.item()) / 1000.0)
+    e2e_value = aggregate_value(ctx.nb, e2e_steps, world, max_over_ranks(e2e_ms, world))
     bytes_psi = psi.numel() * psi.element_size()
     # ---- DIIS steps (roks_diis_step: eager launches, one host read per step)
     # on a copy of the orbitals; its history builds during the warm-up
@@ -442,10 +460,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         d_ms = e0.elapsed_time(e1)
         d_launch = [e for e in roks.roks_profile_read(ctx.ctx) if e["name"] == "kernel_launches"]
-        t3 = torch.tensor([d_ms], dtype=torch.float64, device="cuda")
-        if world > 1:
-            torch.distributed.all_reduce(t3, op=torch.distributed.ReduceOp.MAX)
-        d_ms = float(t3.item())
+        d_ms = max_over_ranks(d_ms, world)
         # per-family device times of the same steps (eager, CUDA events per family)
         # and the HBM roofline of the extrapolation kernel: it reads 2h band
         # blocks (h pairs of the window) and writes one
@@ -464,7 +479,7 @@ def run_gpu(args):
                          "unit": "GB/s", "frac": achieved / hbm, "peak_kind": f"{peak_kind} (copy bandwidth)",
                          "algorithmic_bytes_per_launch": alg / len(pinfo),
                          "ms_per_launch": comb["ms"] / comb["launches"]}
-        diis = {"value": ctx.nb * args.diis_steps * world / (d_ms / 1000.0), "unit": UNIT,
+        diis = {"value": aggregate_value(ctx.nb, args.diis_steps, world, d_ms), "unit": UNIT,
                 "roofline_combine": comb_roof,
                 "profile": {e["name"]: {"launches": e["launches"], "ms": e["ms"]} for e in dprof},
                 "ms_per_step": d_ms / args.diis_steps, "steps": args.diis_steps, "history": 6, "tau": 0.5,
