@@ -23,8 +23,9 @@
  *    duration of the call (stream ordered).  The library owns its internal
  *    workspaces and frees them in roks_destroy().
  *  - All work is ordered on the CUDA stream given to roks_setup().  Calls
- *    that return host scalars (roks_potential, roks_pcg_step,
- *    roks_energies_get) synchronise that stream; the others do not.
+ *    that return host values (roks_potential, roks_pcg_step, roks_diis_step,
+ *    roks_forces, roks_energies_get) synchronise that stream; the others do
+ *    not.
  *  - Errors are returned as roks_status; roks_last_error() gives text.  No
  *    C++ exception crosses this interface.  A context is not thread safe.
  */
