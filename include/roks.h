@@ -266,8 +266,9 @@ ROKS_API roks_status roks_diis_step(roks_ctx* ctx, void* psi, int64_t ld, const 
  * the total derivative of the minimised E_S; at other orbitals it is the
  * derivative at fixed orbitals and multipliers of E - sum gamma (S - 1).
  * forces_host: natoms x 3 doubles (Ha/Bohr, atom order of roks_setup, x y z
- * innermost), written before the call returns.  Recomputes the density and
- * potentials of psi (they become those the next PCG or DIIS step uses).
+ * innermost), written before the call returns.  Uses the density and
+ * potentials of psi when a PCG or DIIS step (or a force call) on the same
+ * buffer left them current, and forms them otherwise.
  * ROKS_EDIVERGED for a non-finite force.  Synchronises. */
 ROKS_API roks_status roks_forces(roks_ctx* ctx, const void* psi, int64_t ld, double* forces_host);
 

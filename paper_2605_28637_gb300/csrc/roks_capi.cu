@@ -731,12 +731,17 @@ struct Impl {
         cudaStream_t st = ctx->st;
         const int nb = ctx->nb, npw = ctx->npw, np_ = ctx->nproj;
         const int64_t l = ctx->ld_min;
-        roks_status r = density(ctx, psi, ld, nullptr);
-        if (r != ROKS_OK) return r;
-        r = potential(ctx);
-        if (r != ROKS_OK) return r;
-        ctx->cache_psi = psi;
-        ctx->pot_valid = true;
+        roks_status r = ROKS_OK;
+        // the density and potentials of psi are current after a PCG or DIIS
+        // step on it (or a previous force call); otherwise form them
+        if (!(ctx->pot_valid && ctx->cache_psi == psi)) {
+            r = density(ctx, psi, ld, nullptr);
+            if (r != ROKS_OK) return r;
+            r = potential(ctx);
+            if (r != ROKS_OK) return r;
+            ctx->cache_psi = psi;
+            ctx->pot_valid = true;
+        }
         r = apply(ctx, psi, ld, ctx->W_F, l, nullptr, 0, np_ > 0 && ctx->b_psi == psi,
                   ctx->yp_psi == psi && ctx->yp_ld == ld);
         if (r != ROKS_OK) return r;
