@@ -411,8 +411,8 @@ struct LastPassSlots {
     }
 };
 
-// Host-side reference of the same pass sequence on one line (used by a CPU
-// test of the pass arithmetic).
+// The same pass sequence on one line, on the host: tests/cpp/fft_passes.cu
+// runs it for every compiled length against the DFT sum.
 template <typename V, int N, int DIR, int P>
 __host__ void host_passes(V* line, const V* tw) {
     if constexpr (P < plan_passes(N)) {
