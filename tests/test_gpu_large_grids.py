@@ -1,0 +1,50 @@
+"""GPU parity on the 72^3 and 120^3 grids (the transform lengths of the
+hybrid-72 and mgo-120 workloads) at small band counts, against the FP64
+oracle: densities, potentials, energies, F|n> and S|n> on the FP64 path
+(1e-10 relative) and on the mixed path (the bars of test_gpu_parity.py:
+densities 2e-6, F|n> 2e-5, S|n> 2e-6 relative, energies 2e-5 Ha), and, on
+the 72^3 grid, one FP64 PCG step."""
+import pytest
+
+from oracle import roks as R
+from paper_2605_28637_gb300 import synthetic as syn
+from tests.gpu_helpers import built, rel, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+GRIDS = {
+    "grid72": dict(grid=72, L=14.0, ecut=6.0, n_closed=2),
+    "grid120": dict(grid=120, L=16.0, ecut=6.0, n_closed=2),
+}
+
+
+@pytest.mark.parametrize("name", list(GRIDS))
+def test_large_grid(name):
+    cfg = syn.with_changes(syn.make_config("tiny-16", 0), **GRIDS[name])
+    roks = built()
+    s = R.System(cfg)
+    u = syn.orbital_uniforms(cfg, s.npw)
+    P = s.initial_orbitals(u)
+    rho_ref = s.class_densities(P)
+    pot = s.potentials(rho_ref)
+    E_ref = s.energies(P, pot)["total"]
+    F_ref, S_ref = s.apply(P, pot)
+    for prec, tr, tf, ts, te in (("fp64", 1e-10, 1e-10, 1e-10, 1e-10 * max(1.0, abs(E_ref))),
+                                 ("mixed", 2e-6, 2e-5, 2e-6, 2e-5)):
+        ctx = roks.Context(cfg, prec)
+        psi = ctx.init_orbitals(u)
+        assert rel(to_np(psi, s.npw), P) < (1e-10 if prec == "fp64" else 2e-6)
+        psi = to_dev(ctx, P)
+        rho = ctx.density(psi, want_rho=True).cpu().numpy()
+        assert rel(rho, rho_ref) < tr, prec
+        E = ctx.potential()
+        assert abs(E["E_total"] - E_ref) < te, prec
+        f, sp, _ = ctx.apply_h(psi)
+        assert rel(to_np(f, s.npw), F_ref) < tf, prec
+        assert rel(to_np(sp, s.npw), S_ref) < ts, prec
+        if prec == "fp64" and name == "grid72":
+            psi = ctx.init_orbitals(u)
+            info = ctx.pcg_step(psi)
+            _, ref = R.PCG(s).step(P)
+            assert abs(info["E_new"] - ref.E_new) <= 1e-9 * max(1.0, abs(ref.E_new))
+        ctx.close()
