@@ -107,62 +107,7 @@ __global__ void k_diis_solve(DiisState* __restrict__ s, DiisOrder ord, double to
         Bs[ord.slot[k] * kDiisMax + ns] = v;
         s->B[ord.slot[k] * kDiisMax + ns] = v;
     }
-    for (int h = n; h >= 2; --h) {
-        const int o = n - h;
-        double q[kDiisMax], L[kDiisMax][kDiisMax];
-        bool ok = true;
-        for (int j = 0; j < h && ok; ++j) {
-            const double bjj = Bs[ord.slot[o + j] * kDiisMax + ord.slot[o + j]];
-            ok = bjj > 0.0 && isfinite(bjj);
-            q[j] = ok ? 1.0 / sqrt(bjj) : 0.0;
-        }
-        // Cholesky of Bn = D^-1/2 B D^-1/2, pivots L_jj^2 >= tol
-        for (int j = 0; j < h && ok; ++j) {
-            for (int i = j; i < h; ++i) {
-                double v = Bs[ord.slot[o + i] * kDiisMax + ord.slot[o + j]] * q[i] * q[j];
-                for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
-                if (i == j) {
-                    if (!(v >= tol)) {
-                        ok = false;
-                        break;
-                    }
-                    L[j][j] = sqrt(v);
-                } else {
-                    L[i][j] = v / L[j][j];
-                }
-            }
-        }
-        if (!ok) continue;
-        // Bn z = D^-1/2 1, y = D^-1/2 z = B^-1 1, d = y / sum y
-        double w[kDiisMax];
-        for (int i = 0; i < h; ++i) {
-            double v = q[i];
-            for (int k = 0; k < i; ++k) v -= L[i][k] * w[k];
-            w[i] = v / L[i][i];
-        }
-        for (int i = h - 1; i >= 0; --i) {
-            double v = w[i];
-            for (int k = i + 1; k < h; ++k) v -= L[k][i] * w[k];
-            w[i] = v / L[i][i];
-        }
-        double sum = 0.0;
-        for (int i = 0; i < h; ++i) {
-            w[i] *= q[i];
-            sum += w[i];
-        }
-        if (!(sum != 0.0 && isfinite(sum))) continue;
-        for (int i = 0; i < h; ++i) {
-            s->d[i] = w[i] / sum;
-            s->slot[i] = ord.slot[o + i];
-        }
-        s->h = h;
-        return;
-    }
-    // the newest pair alone: d = 1 (unless its residual is not finite)
-    const double bnn = Bs[ns * kDiisMax + ns];
-    s->d[0] = 1.0;
-    s->slot[0] = ns;
-    s->h = isfinite(bnn) ? 1 : 0;
+    s->h = diis_window_coefficients(Bs, ord, tol, s->d, s->slot);
 }
 
 template <typename T>

@@ -3,6 +3,8 @@
 // Hutter, Luthi and Parrinello 1994).  Internal to the library.
 #pragma once
 
+#include <cmath>
+
 #include "roks_impl.cuh"
 
 namespace roks {
@@ -27,6 +29,72 @@ struct DiisOrder {
     int n;
     int slot[kDiisMax];
 };
+
+// The window test and the coefficients (host and device): B by ring slot
+// (B[j * kDiisMax + k], symmetric over the slots of ord).  For h from ord.n
+// down to 2, the h most recent pairs pass when every Cholesky pivot of the
+// normalised Gram matrix D^-1/2 B D^-1/2 (D = diag B) satisfies L_kk^2 >= tol;
+// their coefficients are d = B^-1 1 / (1^T B^-1 1), solved through that
+// factor.  Otherwise the newest pair alone (d = 1).  Writes d and the ring
+// slots of the window (oldest first); returns h, or 0 when the newest
+// diagonal entry is not finite.
+__host__ __device__ inline int diis_window_coefficients(const double* B, const DiisOrder& ord, double tol,
+                                                        double* d, int* slot_out) {
+    const int n = ord.n;
+    const int ns = ord.slot[n - 1];
+    for (int h = n; h >= 2; --h) {
+        const int o = n - h;
+        double q[kDiisMax], L[kDiisMax][kDiisMax];
+        bool ok = true;
+        for (int j = 0; j < h && ok; ++j) {
+            const double bjj = B[ord.slot[o + j] * kDiisMax + ord.slot[o + j]];
+            ok = bjj > 0.0 && isfinite(bjj);
+            q[j] = ok ? 1.0 / sqrt(bjj) : 0.0;
+        }
+        for (int j = 0; j < h && ok; ++j) {
+            for (int i = j; i < h; ++i) {
+                double v = B[ord.slot[o + i] * kDiisMax + ord.slot[o + j]] * q[i] * q[j];
+                for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+                if (i == j) {
+                    if (!(v >= tol)) {
+                        ok = false;
+                        break;
+                    }
+                    L[j][j] = sqrt(v);
+                } else {
+                    L[i][j] = v / L[j][j];
+                }
+            }
+        }
+        if (!ok) continue;
+        // Bn z = D^-1/2 1, y = D^-1/2 z = B^-1 1, d = y / sum y
+        double w[kDiisMax];
+        for (int i = 0; i < h; ++i) {
+            double v = q[i];
+            for (int k = 0; k < i; ++k) v -= L[i][k] * w[k];
+            w[i] = v / L[i][i];
+        }
+        for (int i = h - 1; i >= 0; --i) {
+            double v = w[i];
+            for (int k = i + 1; k < h; ++k) v -= L[k][i] * w[k];
+            w[i] = v / L[i][i];
+        }
+        double sum = 0.0;
+        for (int i = 0; i < h; ++i) {
+            w[i] *= q[i];
+            sum += w[i];
+        }
+        if (!(sum != 0.0 && isfinite(sum))) continue;
+        for (int i = 0; i < h; ++i) {
+            d[i] = w[i] / sum;
+            slot_out[i] = ord.slot[o + i];
+        }
+        return h;
+    }
+    d[0] = 1.0;
+    slot_out[0] = ns;
+    return isfinite(B[ns * kDiisMax + ns]) ? 1 : 0;
+}
 
 // Lambda_mn = theta_mn - lambda_mn (theta_mn - conj theta_nm), lambda_mn = 1/2
 // except lambda[ia, ib] = lab and lambda[ib, ia] = lba (ia < 0: none).
