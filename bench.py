@@ -200,9 +200,10 @@ def traffic_record(family):
 
 
 # ---------------------------------------------------------------- CPU oracle sample
-def oracle_sample(cfg, n_bands_timed=4, reps=1):
+def oracle_sample(cfg, n_bands_timed=4, target_seconds=10.0, max_reps=60):
     """F^n|n> of a few bands with the oracle (FP64 numpy) at a fixed
-    potential; returns (band-applies/s, seconds, description)."""
+    potential, repeated until about target_seconds of CPU work (a bounded
+    sample of the workload); returns (band-applies/s, seconds, description)."""
     from oracle import roks as R
     from paper_2605_28637_gb300 import synthetic as syn
     s = R.System(cfg)
@@ -219,9 +220,11 @@ def oracle_sample(cfg, n_bands_timed=4, reps=1):
     X = c[:, :nt]
     cls = s.cls[:nt]
     t0 = time.perf_counter()
-    for _ in range(reps):
+    reps, dt = 0, 0.0
+    while reps < max_reps and (reps == 0 or dt < target_seconds):
         s.apply(X, pot, classes=cls)
-    dt = time.perf_counter() - t0
+        reps += 1
+        dt = time.perf_counter() - t0
     desc = (f"F^n|n> (kinetic+local+non-local) of {nt} bands x {reps} of {cfg['name']} "
             f"({cfg['grid']}^3 grid, {s.npw} plane waves, {s.nproj} projectors), FP64 numpy oracle, fixed potential")
     return nt * reps / dt, dt, desc
