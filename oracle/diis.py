@@ -34,7 +34,9 @@ path, which implements them independently):
        Bn = D^-1/2 B D^-1/2, the window is accepted when every Cholesky
        pivot of Bn satisfies L_kk^2 >= tol (1e-7); otherwise the oldest
        pair is dropped and the test repeated (h = 1 always passes).
-  R12  convergence as R7: |E_i+1 - E_i| < e_tol on two consecutive steps.
+  R12  convergence as R7: |E_i+1 - E_i| < e_tol on two consecutive steps,
+       and the residual norm |R| < g_tol at the start of the last step when
+       g_tol > 0.
 
 Pins (tests/test_oracle_diis.py): lambda = 1/2 reproduces the gradient of
 Eq. 7 (itself pinned by finite differences of E); the in-subspace part of R
@@ -129,11 +131,13 @@ class DIIS:
     the order of the module docstring."""
 
     def __init__(self, sys_: R.System, history: int = HISTORY, tau: float = TAU,
-                 lambda_ab: float = 0.5, lambda_ba: float = 0.5, e_tol: float = 1e-6, tol: float = COND_TOL):
+                 lambda_ab: float = 0.5, lambda_ba: float = 0.5, e_tol: float = 1e-6, tol: float = COND_TOL,
+                 g_tol: float = 0.0):
         self.sys = sys_
         self.tau = tau
         self.tol = tol
         self.e_tol = e_tol
+        self.g_tol = g_tol
         self.lam = coupling_table(sys_, lambda_ab, lambda_ba)
         self.hist = deque(maxlen=history)
         self.n_small = 0
@@ -164,7 +168,7 @@ class DIIS:
             self.n_small += 1
         else:
             self.n_small = 0
-        self.converged = self.n_small >= 2
+        self.converged = self.n_small >= 2 and (self.g_tol <= 0.0 or float(np.linalg.norm(Rres)) < self.g_tol)
         return Psi_new, DiisInfo(E=E0, E_new=E_new, res_norm=float(np.linalg.norm(Rres)),
                                  grad_norm=float(np.linalg.norm(G)), window=h, coef=d)
 

@@ -40,7 +40,10 @@ CUDA path, which implements them independently):
   R6  the search direction is projected S-orthogonal to the current orbitals
       before the step; orbitals are S-orthonormalised by Cholesky in the
       order closed, a, b after each step.
-  R7  convergence: |E_i+1 - E_i| < e_tol on two consecutive iterations.
+  R7  convergence: |E_i+1 - E_i| < e_tol on two consecutive iterations and,
+      when a gradient tolerance g_tol > 0 is given, |g| < g_tol at the start
+      of the last step (the stationarity the energy criterion stands for,
+      Eq. 15 and SI S1, made explicit).
 
 What pins each part (tests/test_oracle_*.py; none compares the oracle with
 itself): the transforms against the DFT sum and brute force; the basis
@@ -282,15 +285,21 @@ class System:
 
     # ----------------------------------------------------------- a11: exact exchange
     def coulomb_trunc(self) -> np.ndarray:
-        """Spherically truncated Coulomb kernel v(G) = 4 pi (1 - cos(|G| Rc))/G^2,
-        v(0) = 2 pi Rc^2, Rc = (3 Omega / 4 pi)^{1/3}."""
+        """Exchange kernel on the grid.  Default (cfg exx_kernel 0): the
+        spherically truncated Coulomb kernel v(G) = 4 pi (1 - cos(|G| Rc))/G^2,
+        v(0) = 2 pi Rc^2, Rc = (3 Omega / 4 pi)^{1/3}.  exx_kernel 1: the bare
+        Coulomb kernel 4 pi / G^2 with the G = 0 term left out."""
         Rc = (3.0 * self.omega / (4.0 * np.pi)) ** (1.0 / 3.0)
         g2 = self.G2grid
         v = np.empty_like(g2)
         nz = g2 > 0
         g = np.sqrt(g2[nz])
-        v[nz] = 4.0 * np.pi * (1.0 - np.cos(g * Rc)) / g2[nz]
-        v[~nz] = 2.0 * np.pi * Rc * Rc
+        if int(self.cfg.get("exx_kernel", 0)) == 1:
+            v[nz] = 4.0 * np.pi / g2[nz]
+            v[~nz] = 0.0
+        else:
+            v[nz] = 4.0 * np.pi * (1.0 - np.cos(g * Rc)) / g2[nz]
+            v[~nz] = 2.0 * np.pi * Rc * Rc
         return v
 
     def exchange(self, Occ: np.ndarray, X: np.ndarray | None = None, classes=None):
@@ -514,9 +523,10 @@ class PCG:
     (Eq. 24)."""
 
     def __init__(self, sys_: System, e_tol: float = 1e-6, suppress_ab: bool = False,
-                 dt0: float = 0.3):
+                 dt0: float = 0.3, g_tol: float = 0.0):
         self.sys = sys_
         self.e_tol = e_tol
+        self.g_tol = g_tol
         self.suppress_ab = suppress_ab
         self.dt = dt0
         self.s_prev = None
@@ -572,20 +582,21 @@ class PCG:
             self.n_small += 1
         else:
             self.n_small = 0
-        self.converged = self.n_small >= 2
+        grad_norm = float(np.linalg.norm(G))
+        self.converged = self.n_small >= 2 and (self.g_tol <= 0.0 or grad_norm < self.g_tol)
         coupling = 0.0
         if sy.mode == 1:
             ia, ib = sy.n_closed, sy.n_closed + 1
             coupling = np.conj(Theta[ib, ia]) - Theta[ia, ib]
         info = StepInfo(E=E0, E_new=E_new, step=step,
-                        grad_norm=float(np.linalg.norm(G)), coupling=coupling,
+                        grad_norm=grad_norm, coupling=coupling,
                         beta=beta, dE0=dE0, restarted=restarted)
         return Psi_new, info
 
 
-def run(sys_: System, Psi, max_iter=50, e_tol=1e-6, suppress_ab=False, callback=None):
+def run(sys_: System, Psi, max_iter=50, e_tol=1e-6, suppress_ab=False, callback=None, g_tol=0.0):
     """PCG to convergence (R7) or max_iter; returns (Psi, list of StepInfo)."""
-    pcg = PCG(sys_, e_tol=e_tol, suppress_ab=suppress_ab)
+    pcg = PCG(sys_, e_tol=e_tol, suppress_ab=suppress_ab, g_tol=g_tol)
     hist = []
     for _ in range(max_iter):
         Psi, info = pcg.step(Psi)

@@ -239,3 +239,49 @@ def test_projector_norm_and_overlap():
     Gm = s.P.conj().T @ s.P
     ev = np.linalg.eigvalsh(np.eye(s.nproj) + 0.5 * (s.Q @ Gm + (s.Q @ Gm).conj().T))
     assert ev.min() > 0.1
+
+
+def test_projector_real_space_shape():
+    """The projectors synthesised on a real-space grid are the functions the
+    model defines (Eq. 3 with Gaussian s/p channels): N_s exp(-u^2/(2 rc^2))
+    and N_p u_m exp(-u^2/(2 rc^2)), u = r - R summed over periodic images.
+    Pins the sign and the Cartesian index of the p channels (a sign slip in
+    -i rc^2 G_m would flip the p functions; the norm pin does not see it)."""
+    cfg = tiny(L=6.0, ecut=80.0, grid=40)
+    s = R.System(cfg, hartree=False, xc=False)
+    N, L = s.N, s.L
+    a = np.arange(N) * L / N
+    x, y, z = np.meshgrid(a, a, a, indexing="ij")
+    r = np.stack([x.reshape(-1), y.reshape(-1), z.reshape(-1)], axis=1)
+    col = 0
+    for at in cfg["atoms"]:
+        sp = cfg["species"][at["species"]]
+        R0 = np.asarray(at["pos"])
+        for l, m, rc in zip(sp["l"], sp["m"], sp["rc"]):
+            want = np.zeros(N ** 3)
+            for n in np.ndindex(5, 5, 5):
+                u = r - R0 - L * (np.asarray(n) - 2)
+                g = np.exp(-(u * u).sum(1) / (2 * rc * rc))
+                want += g if l == 0 else u[:, m] * g
+            norm = (np.pi * rc * rc) ** -0.75 * (1.0 if l == 0 else np.sqrt(2.0) / rc)
+            got = s.to_real(s.P[:, col])
+            assert np.abs(got.imag).max() < 1e-10
+            assert np.abs(got.real - norm * want).max() < 1e-8 * norm
+            col += 1
+    assert col == s.nproj
+
+
+def test_bare_coulomb_kernel_single_cosine():
+    """The bare exchange kernel (exx_kernel 1) on a single-cosine pair density
+    rho0 cos(G0.r) gives Omega sum_G v |rho(G)|^2 = 2 pi Omega rho0^2 / |G0|^2,
+    and a constant density gives zero (no G = 0 term)."""
+    s = R.System(tiny(exx_kernel=1), hartree=False, xc=False)
+    N, L = s.N, s.L
+    a = np.arange(N) * L / N
+    x, y, z = np.meshgrid(a, a, a, indexing="ij")
+    G0 = 2 * np.pi / L * np.array([1, 2, -2])
+    rho0 = 0.21
+    rho = rho0 * np.cos(G0[0] * x + G0[1] * y + G0[2] * z).reshape(-1) + 0.05
+    rG = s.grid_fourier(rho)
+    K = s.omega * float((s.coulomb_trunc() * np.abs(rG) ** 2).sum())
+    assert abs(K - 2 * np.pi * s.omega * rho0 ** 2 / (G0 @ G0)) < 1e-12
