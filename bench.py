@@ -9,13 +9,17 @@ per second (one per band per step) and also reports seconds per PCG
 iteration and seconds to converge (|dE| < 1e-6 Ha twice), mixed precision
 against the plain FP64 GPU path.
 
-Default workload: organic-molecule box (20 Bohr cell, 96^3 grid, Ecut 20 Ha,
-34265 plane waves, 30 atoms with 172 projectors, 40 closed + 2 open bands),
-synthetic seeded inputs.  Multi-GPU (torchrun): independent replicas, one
-per rank (seed = rank), no collective on the data path.
+Default workload: the MgO-vacancy-shaped supercell (3x3x3 rocksalt cell,
+a = 7.96 Bohr, one O removed: 215 atoms, 1288 projectors; 120^3 grid, Ecut
+15 Ha, 37705 plane waves; 428 closed + 2 open bands), synthetic seeded
+inputs, mixed precision.  The time-to-convergence legs (mixed vs plain FP64,
+TPA with and without the learned correction, DIIS) run on the organic-molecule
+box (20 Bohr, 96^3, 34265 plane waves, 172 projectors, 40 + 2 bands), where
+the FP64 leg converges within a minute.  Multi-GPU (torchrun): independent
+replicas, one per rank (seed = rank), no collective on the data path.
 
 --impl reference times the FP64 CPU oracle (the only reference there is) on
-a bounded sample of the same workload on the host cores.
+a bounded sample of the same workload on all host cores.
 """
 from __future__ import annotations
 
@@ -42,15 +46,23 @@ FALLBACK_HBM_GBS = 6800.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="organic-96")
+    ap.add_argument("--workload", default="mgo-120")
+    ap.add_argument("--converge-workload", default="organic-96",
+                    help="workload of the time-to-convergence legs")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--converge-iters", type=int, default=2000,
                     help="iteration cap of the time-to-convergence runs (0 skips them)")
     ap.add_argument("--converge-seconds", type=float, default=60.0,
                     help="wall-clock cap of each time-to-convergence run")
+    ap.add_argument("--g-tol", type=float, default=2e-4,
+                    help="gradient-norm criterion of the convergence legs (beside |dE| < 1e-6 Ha twice)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="CPU work per host core of the oracle sample")
+    ap.add_argument("--hybrid-applies", type=int, default=3,
+                    help="timed roks_apply_h calls on the hybrid-exchange workload (hybrid-72); 0 skips them")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--force-calls", type=int, default=10,
                     help="timed roks_forces calls on the final orbitals; 0 skips them")
@@ -85,6 +97,11 @@ def replica_config(workload: str, rank: int) -> dict:
     return syn.make_config(workload, rank)
 
 
+def syn_with(cfg: dict, **kw) -> dict:
+    from paper_2605_28637_gb300 import synthetic as syn
+    return syn.with_changes(cfg, **kw)
+
+
 def aggregate_value(nb: int, steps: int, world: int, ms_max: float) -> float:
     """Band-applies per second of the whole job: all ranks' bands over the slowest rank's time."""
     return nb * steps * world / (ms_max / 1000.0)
@@ -93,6 +110,7 @@ def aggregate_value(nb: int, steps: int, world: int, ms_max: float) -> float:
 # FP32 FMA rate from the unit counts and the maximum SM clock (no measured
 # FP32 peak is provided): 152 SMs x 128 lanes x 2 flops x 2.07 GHz
 FP32_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_TFLOPS_NOMINAL = 1.25
 
 
 def peaks():
@@ -173,6 +191,79 @@ def algorithmic_bytes(ctx, cfg, family: str, csize: int, rsize: int):
     }.get(family)
 
 
+def family_work(ctx, cfg, family: str, csize: int, rsize: int, precision: str, tensor=frozenset()):
+    """(bound, algorithmic work per launch) of a kernel family: compulsory
+    DRAM bytes for the band-transform stages, flops (8 per complex
+    multiply-add) for the contractions; None for other families."""
+    b = algorithmic_bytes(ctx, cfg, family, csize, rsize)
+    if b is not None:
+        return "hbm", float(b)
+    npw, nb, npj = float(ctx.npw), float(ctx.nb), float(ctx.nproj)
+    flops = {
+        "proj_PhPsi": 8 * npw * npj * nb,          # B = P^H Psi
+        "proj_PX": 8 * npw * npj * nb,             # F += P (D B) or S = Psi + P (Q B)
+        "orth_overlap": 8 * npw * nb * nb,         # O = Psi^H Psi
+        "orth_apply": 8 * npw * nb * nb,           # Psi L^{-H}
+        "subspace_theta": 8 * npw * nb * nb,       # Theta = Psi^H F Psi
+        "subspace_project": 16 * npw * nb * nb,    # (S Psi)^H x, then x - Psi M
+        "gradient_precond": 16 * npw * nb * nb,    # F - S Gam, F - S Theta
+    }.get(family)
+    if flops is None or flops == 0:
+        return None
+    return ("tensor" if family in tensor else "alu"), flops
+
+
+def tensor_families(ctx, precision: str, tc_launches: int):
+    """Kernel families whose products the library puts on the tcgen05 tensor
+    cores at this workload (the shape rule of k_tcgemm.cu: A^H B with
+    M >= 128, N >= 64, K >= 1024; tall products with M >= 4096, N >= 64,
+    K >= 64), provided tensor-core launches were counted."""
+    if precision != "mixed" or not tc_launches:
+        return frozenset()
+    nb, npj, npw = ctx.nb, ctx.nproj, ctx.npw
+
+    def cn(M, N, K):
+        return M >= 128 and N >= 64 and K >= 1024
+
+    def nn(M, N, K):
+        return M >= 4096 and N >= 64 and K >= 64
+    fams = set()
+    if cn(npj, nb, npw):
+        fams.add("proj_PhPsi")
+    if nn(npw, nb, npj):
+        fams.add("proj_PX")
+    if cn(nb, nb, npw):
+        fams |= {"orth_overlap", "subspace_theta"}
+    if nn(npw, nb, nb):
+        fams |= {"orth_apply", "gradient_precond"}
+    if cn(nb, nb, npw) and nn(npw, nb, nb):
+        fams.add("subspace_project")
+    return frozenset(fams)
+
+
+def bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        if "bf16_tflops" in d:
+            return float(d["bf16_tflops"]), "measured"
+    return 1900.0, "fallback"
+
+
+def alu_peak(precision: str, bound: str = "alu"):
+    """Peak of a contraction family.  Tensor cores: the TF32 rate (measured
+    bf16 peak x the nominal TF32/BF16 ratio 1.1/2.25) over the three TF32
+    products each FP32 product takes.  SIMT: FP32 FMA from the unit counts
+    and clock (no measured FP32 peak is provided), or the FP64 rate."""
+    if bound == "tensor":
+        b, kind = bf16_peak()
+        return b * (1.1 / 2.25) / 3.0, (f"{kind} bf16 peak x 1.1/2.25 (TF32) / 3 TF32 products per FP32 product")
+    if precision == "fp64":
+        return FP64_TFLOPS_NOMINAL, "nominal FP64: 1.25 TFLOP/s (GB300 dense FP64)"
+    return FP32_TFLOPS_NOMINAL, "nominal FP32: 152 SMs x 128 lanes x 2 flops x 2.07 GHz"
+
+
 def _geometry(miller):
     ij = {(int(a), int(b)) for a, b, _ in miller}
     i = {int(a) for a, _, _ in miller}
@@ -200,44 +291,117 @@ def traffic_record(family):
 
 
 # ---------------------------------------------------------------- CPU oracle sample
-def oracle_sample(cfg, n_bands_timed=4, target_seconds=10.0, max_reps=60):
-    """F^n|n> of a few bands with the oracle (FP64 numpy) at a fixed
-    potential, repeated until about target_seconds of CPU work (a bounded
-    sample of the workload); returns (band-applies/s, seconds, description)."""
-    from oracle import roks as R
-    from paper_2605_28637_gb300 import synthetic as syn
-    s = R.System(cfg)
-    u = syn.orbital_uniforms(cfg, s.npw)
-    c = (u[..., 0] + 1j * u[..., 1]).T / (1.0 + s.g2)[:, None]
-    nt = min(n_bands_timed, s.nb)
-    # the potential of the first two bands stands in for the self-consistent
-    # one (the timing does not depend on its values)
-    rho = np.zeros((3, s.N ** 3))
-    for n in range(min(2, s.nb)):
-        psi = s.to_real(c[:, n])
-        rho[0] += (psi.conj() * psi).real
-    pot = s.potentials(rho)
-    X = c[:, :nt]
-    cls = s.cls[:nt]
-    t0 = time.perf_counter()
-    reps, dt = 0, 0.0
-    while reps < max_reps and (reps == 0 or dt < target_seconds):
-        s.apply(X, pot, classes=cls)
-        reps += 1
-        dt = time.perf_counter() - t0
-    desc = (f"F^n|n> (kinetic+local+non-local) of {nt} bands x {reps} of {cfg['name']} "
-            f"({cfg['grid']}^3 grid, {s.npw} plane waves, {s.nproj} projectors), FP64 numpy oracle, fixed potential")
-    return nt * reps / dt, dt, desc
-
-
-def cpu_cores():
+def host_cores() -> int:
+    """Host cores this process may run on (the affinity mask; os.cpu_count()
+    where the mask is not available)."""
     try:
-        import threadpoolctl
-        info = threadpoolctl.threadpool_info()
-        blas = max([i.get("num_threads", 1) for i in info] or [1])
-        return int(blas)
+        return len(os.sched_getaffinity(0))
     except Exception:
-        return 1
+        return os.cpu_count() or 1
+
+
+def _mem_available_bytes() -> float:
+    """Memory the oracle workers may use: MemAvailable, capped by a cgroup limit."""
+    avail = float("inf")
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    avail = float(line.split()[1]) * 1024
+    except Exception:
+        pass
+    for path in ("/sys/fs/cgroup/memory.max", "/sys/fs/cgroup/memory/memory.limit_in_bytes"):
+        try:
+            with open(path) as f:
+                v = f.read().strip()
+            if v.isdigit():
+                avail = min(avail, float(v))
+        except Exception:
+            pass
+    return avail
+
+
+def _oracle_worker(name, seed, band, mode, amount, warmup, barrier, out):
+    """One host core: the oracle's F^n|n> (kinetic + local + non-local, FP64)
+    of one band of the seeded start, at the potential of the start's first
+    two bands, repeated `amount` times (mode "steps", after `warmup` untimed
+    repeats) or for `amount` seconds (mode "seconds").  The timed loops of all
+    workers start together (barrier)."""
+    try:
+        from oracle import roks as R
+        from paper_2605_28637_gb300 import synthetic as syn
+        cfg = syn.make_config(name, seed)
+        s = R.System(cfg)
+
+        def band_coeffs(b0, nb):
+            u = syn.orbital_uniforms(cfg, s.npw, b0, nb)
+            return (u[..., 0] + 1j * u[..., 1]).T / (1.0 + s.g2)[:, None]
+
+        rho = np.zeros((3, s.N ** 3))
+        c2 = band_coeffs(0, min(2, s.nb))
+        for n in range(c2.shape[1]):
+            psi = s.to_real(c2[:, n])
+            rho[0] += (psi.conj() * psi).real
+        pot = s.potentials(rho)
+        b = band % s.nb
+        X = band_coeffs(b, 1)
+        cls = s.cls[b:b + 1]
+        for _ in range(warmup):
+            s.apply(X, pot, classes=cls)
+        barrier.wait(timeout=600)
+        t0 = time.perf_counter()
+        reps = 0
+        while (mode == "steps" and reps < amount) or (mode == "seconds" and (reps == 0 or
+                                                                              time.perf_counter() - t0 < amount)):
+            s.apply(X, pot, classes=cls)
+            reps += 1
+        out.put((reps, time.perf_counter() - t0, s.npw, s.nproj))
+    except Exception as e:   # reported by the parent
+        try:
+            barrier.abort()
+        except Exception:
+            pass
+        out.put(("error", repr(e)))
+
+
+def oracle_parallel(name: str, seed: int, mode: str, amount: float, warmup: int = 0, per_worker_gb: float = 2.5):
+    """The oracle's band applies on all host cores at once: one spawned
+    process per core (each with single-threaded BLAS), each applying F to its
+    own band of the workload.  Returns band-applies/s over the slowest
+    worker's timed loop, the cores used and the seconds."""
+    import multiprocessing as mp
+    cores = host_cores()
+    mem_cap = int(0.6 * _mem_available_bytes() / (per_worker_gb * 2 ** 30))
+    workers = max(1, min(cores, mem_cap))
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(workers)
+    out = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(name, seed, w, mode, amount, warmup, barrier, out))
+             for w in range(workers)]
+    for p in procs:
+        p.start()
+    res = [out.get(timeout=1800) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+    errs = [r[1] for r in res if r[0] == "error"]
+    if errs:
+        raise RuntimeError(f"oracle worker failed: {errs[0]}")
+    applies = sum(r[0] for r in res)
+    dt = max(r[1] for r in res)
+    return {"value": applies / dt, "cores": workers, "seconds": dt, "applies": applies,
+            "npw": res[0][2], "nproj": res[0][3], "host_cores": cores}
+
+
+def cpu_baseline_leg(name: str, seconds: float):
+    r = oracle_parallel(name, 0, "seconds", seconds)
+    desc = (f"F^n|n> (kinetic + local + non-local, FP64 numpy oracle) of one band per core of {name} "
+            f"({r['npw']} plane waves, {r['nproj']} projectors) at the potential of the seeded start's first two "
+            f"bands, repeated for about {seconds:.0f} s on {r['cores']} host cores at once "
+            f"({r['applies']} band applies); scaled to band-applies/s")
+    return {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle", "sample": desc,
+            "seconds": r["seconds"], "host_cores": r["host_cores"]}
 
 
 # ---------------------------------------------------------------- reference arm
@@ -247,32 +411,19 @@ def run_reference(args):
         return 0
     from paper_2605_28637_gb300 import synthetic as syn
     cfg = syn.make_config(args.workload, 0)
-    # each step: F^n|n> of 2 bands of the workload (bounded sample)
-    from oracle import roks as R
-    s = R.System(cfg)
-    u = syn.orbital_uniforms(cfg, s.npw)
-    c = (u[..., 0] + 1j * u[..., 1]).T / (1.0 + s.g2)[:, None]
-    rho = np.zeros((3, s.N ** 3))
-    for n in range(min(2, s.nb)):
-        psi = s.to_real(c[:, n])
-        rho[0] += (psi.conj() * psi).real
-    pot = s.potentials(rho)
-    X = c[:, :2]
-    for _ in range(args.warmup):
-        s.apply(X, pot, classes=s.cls[:2])
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        s.apply(X, pot, classes=s.cls[:2])
-    dt = time.perf_counter() - t0
-    value = 2 * args.steps / dt
-    sample = (f"each step: F^n|n> of 2 bands of {cfg['name']} ({cfg['grid']}^3, {s.npw} plane waves), "
-              "FP64 numpy oracle on the host cores, fixed potential")
+    # each step: every host core applies F to one band of the workload
+    r = oracle_parallel(args.workload, 0, "steps", args.steps, warmup=args.warmup)
+    value = r["value"]
+    sample = (f"each step: F^n|n> (kinetic + local + non-local) of one band per host core of {cfg['name']} "
+              f"({cfg['grid']}^3, {r['npw']} plane waves, {r['nproj']} projectors), FP64 numpy oracle, "
+              f"{r['cores']} cores at once, fixed potential")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": 1000 * r["seconds"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": cfg["name"], "grid": cfg["grid"], "bands": s.nb, "plane_waves": s.npw},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+            "config": {"workload": cfg["name"], "grid": cfg["grid"], "bands": syn.n_bands(cfg),
+                       "plane_waves": r["npw"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -300,13 +451,13 @@ def time_pcg(ctx, psi, steps, torch, profile=False):
     return e0.elapsed_time(e1), infos, prof
 
 
-def converge(cfg, precision, cap, torch, max_seconds, params=None):
+def converge(cfg, precision, cap, torch, max_seconds, g_tol, params=None, keep=False):
     """Seconds and iterations of PCG from the seeded start to |dE| < 1e-6 Ha
-    twice, stopped after cap iterations or max_seconds of wall clock; with
-    params, the TPA step is corrected by the trained network (TPA judges the
-    last steps)."""
+    twice with |g| < g_tol, stopped after cap iterations or max_seconds of
+    wall clock; with params, the TPA step is corrected by the trained network
+    (TPA judges the last steps).  keep: also return the final orbitals."""
     from paper_2605_28637_gb300 import roks, synthetic as syn
-    ctx = roks.Context(cfg, precision, e_tol=1e-6)
+    ctx = roks.Context(cfg, precision, e_tol=1e-6, g_tol=g_tol)
     if params is not None:
         ctx.set_preconditioner(params)
     psi = ctx.init_orbitals(syn.orbital_uniforms(cfg, ctx.npw))
@@ -322,27 +473,46 @@ def converge(cfg, precision, cap, torch, max_seconds, params=None):
     out = {"seconds": dt, "iterations": it, "converged": bool(info and info["converged"]),
            "E_final": info["E_new"] if info else None, "grad_norm_final": info["grad_norm"] if info else None,
            "s_per_iter": dt / max(it, 1)}
-    if precision == "mixed" and info is not None:
+    psi64 = None
+    if info is not None:
         # the final orbitals re-evaluated in FP64 (orthonormalised there first):
         # a mixed leg's energy must be that of its own state, not an FP32 artefact
         c64 = roks.Context(cfg, "fp64")
-        p64 = c64.new_bands()
-        p64[:, :ctx.npw] = psi[:, :ctx.npw].to(p64.dtype)
+        psi64 = c64.new_bands()
+        psi64[:, :ctx.npw] = psi[:, :ctx.npw].to(psi64.dtype)
         torch.cuda.synchronize()
-        roks.roks_orthonormalize(c64.ctx, p64, c64.ld)
-        c64.density(p64)
+        roks.roks_orthonormalize(c64.ctx, psi64, c64.ld)
+        c64.density(psi64)
         out["E_final_fp64_eval"] = c64.potential()["E_total"]
-        out["dE_mixed_vs_fp64_eval"] = out["E_final"] - out["E_final_fp64_eval"]
+        out["dE_vs_fp64_eval"] = out["E_final"] - out["E_final_fp64_eval"]
         c64.close()
     ctx.close()
-    return out
+    return (out, psi64) if keep else out
 
 
-def converge_diis(cfg, precision, cap, torch, max_seconds, history=6):
+def open_overlap(cfg, psi_a, psi_b, torch):
+    """min over the open orbitals x = a, b of |<x_A|S|x_B>| (FP64 orbitals of
+    two legs; S applied by the library): the same-state test of two runs."""
+    from paper_2605_28637_gb300 import roks
+    c64 = roks.Context(cfg, "fp64")
+    sb = c64.new_bands()
+    fb = c64.new_bands()
+    c64.density(psi_b)
+    c64.potential()
+    roks.roks_apply_h(c64.ctx, psi_b, c64.ld, fb, sb, None)
+    nb = c64.nb
+    vals = []
+    for col in (nb - 2, nb - 1):
+        vals.append(float(torch.abs(torch.vdot(psi_a[col, :c64.npw], sb[col, :c64.npw])).item()))
+    c64.close()
+    return min(vals)
+
+
+def converge_diis(cfg, precision, cap, torch, max_seconds, g_tol, history=6):
     """DIIS (roks_diis_step, lambda = 1/2) from the seeded start to |dE| < 1e-6 Ha
-    twice, capped like converge()."""
+    twice with residual norm below g_tol, capped like converge()."""
     from paper_2605_28637_gb300 import roks, synthetic as syn
-    ctx = roks.Context(cfg, precision, e_tol=1e-6)
+    ctx = roks.Context(cfg, precision, e_tol=1e-6, g_tol=g_tol)
     psi = ctx.init_orbitals(syn.orbital_uniforms(cfg, ctx.npw))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -356,6 +526,52 @@ def converge_diis(cfg, precision, cap, torch, max_seconds, history=6):
     out = {"seconds": dt, "iterations": it, "converged": bool(info and info["converged"]),
            "E_final": info["E_new"] if info else None, "res_norm_final": info["res_norm"] if info else None,
            "s_per_iter": dt / max(it, 1), "history": history}
+    ctx.close()
+    return out
+
+
+def hybrid_leg(args, torch):
+    """roks_apply_h on the hybrid-exchange workload (2x2x2 rocksalt cell minus
+    one O, 72^3, 128 bands, exact-exchange fraction 1/3): the exchange apply
+    makes 8256 pair transforms (both directions) per call.  Its HBM roofline
+    counts 12.1 MB per pair (read psi_j, psi_n, one grid round trip of the
+    pair density, the field update: 4 x 8 N^3 + the pair's sphere data)."""
+    from paper_2605_28637_gb300 import roks, synthetic as syn
+    cfg = syn.make_config("hybrid-72", 0)
+    ctx = roks.Context(cfg, "mixed")
+    psi = ctx.init_orbitals(syn.orbital_uniforms(cfg, ctx.npw))
+    ctx.density(psi)
+    e = ctx.potential()
+    f = ctx.new_bands()
+    sp = ctx.new_bands()
+    roks.roks_apply_h(ctx.ctx, psi, ctx.ld, f, sp, None)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(ctx.stream)
+    for _ in range(args.hybrid_applies):
+        roks.roks_apply_h(ctx.ctx, psi, ctx.ld, f, sp, None)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.hybrid_applies
+    roks.roks_profile_enable(ctx.ctx, 1)
+    roks.roks_apply_h(ctx.ctx, psi, ctx.ld, f, sp, None)
+    prof = {x["name"]: x for x in roks.roks_profile_read(ctx.ctx)}
+    roks.roks_profile_enable(ctx.ctx, 0)
+    N = cfg["grid"]
+    npairs = ctx.nb * (ctx.nb + 1) // 2
+    alg = npairs * (4 * 8 * N ** 3 + 16 * ctx.npw)
+    ex = prof.get("exchange")
+    roof = None
+    if ex:
+        hbm, kind = peaks()
+        ach = alg / (ex["ms"] / ex["launches"] / 1000.0) / 1e9
+        roof = {"bound": "hbm", "kernel": "exchange (pair densities, batched grid transforms, kernel multiply, "
+                                          "field accumulation)", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "peak_kind": f"{kind} (copy bandwidth)", "algorithmic_bytes_per_call": alg,
+                "ms_per_call": ex["ms"] / ex["launches"]}
+    out = {"workload": cfg["name"], "bands": ctx.nb, "pairs": npairs, "ms_per_apply": ms,
+           "value": ctx.nb / (ms / 1000.0), "unit": UNIT, "E_total": e["E_total"], "E_hf_M": e["E_hf_M"],
+           "roofline_exchange": roof}
     ctx.close()
     return out
 
@@ -469,7 +685,7 @@ def run_gpu(args):
         # blocks (h pairs of the window) and writes one
         roks.roks_profile_enable(ctx.ctx, 1)
         pinfo = [ctx.diis_step(pd) for _ in range(10)]
-        dprof = [e for e in roks.roks_profile_read(ctx.ctx) if e["name"] != "kernel_launches"]
+        dprof = [e for e in roks.roks_profile_read(ctx.ctx) if e["name"] not in ("kernel_launches", "tensor_core_launches")]
         roks.roks_profile_enable(ctx.ctx, 0)
         comb = next((e for e in dprof if e["name"] == "diis_combine"), None)
         comb_roof = None
@@ -508,65 +724,85 @@ def run_gpu(args):
                       "launches_per_call": f_launch[0]["launches"] / args.force_calls if f_launch else None,
                       "max_abs_force_ha_per_bohr": float(abs(Fa).max()),
                       "launch": "eager, one host read per call"}
-    # ---- roofline of the dominant kernel family
+    # ---- rooflines of the kernel families with known algorithmic work; the
+    # family with the most device time is the line's "roofline"
     csize = 16 if args.precision == "fp64" else 8
     rsize = 8 if args.precision == "fp64" else 4
-    prof = [e for e in prof if e["name"] != "kernel_launches"]
+    tc_launches = next((e["launches"] for e in prof if e["name"] == "tensor_core_launches"), 0)
+    tensor = tensor_families(ctx, args.precision, tc_launches)
+    prof = [e for e in prof if e["name"] not in ("kernel_launches", "tensor_core_launches")]
     total_prof = sum(e["ms"] for e in prof) or 1.0
     hbm, peak_kind = peaks()
-    dom = None
+    rooflines = []
     for e in sorted(prof, key=lambda e: -e["ms"]):
-        if algorithmic_bytes(ctx, cfg, e["name"], csize, rsize) is not None:
-            dom = e
-            break
-    top = max(prof, key=lambda e: e["ms"]) if prof else None
-    roofline = None
-    if dom is not None:
-        per_launch_ms = dom["ms"] / dom["launches"]
-        alg = algorithmic_bytes(ctx, cfg, dom["name"], csize, rsize)
-        achieved = alg / (per_launch_ms / 1000.0) / 1e9
-        roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved / hbm, "peak_kind": f"{peak_kind} (copy bandwidth)",
-                    "traffic": traffic_record(dom["name"]), "algorithmic_bytes_per_launch": alg,
-                    "ms_per_launch": per_launch_ms, "share_of_step": dom["ms"] / total_prof}
-    # FP32-FMA roofline of the projector products F += P (D B), S = Psi + P (Q B)
-    # (streamed tall products, K = N_proj): the largest contraction family
-    roofline_fp32 = None
-    px = next((e for e in prof if e["name"] == "proj_PX"), None)
-    if px is not None and args.precision == "mixed" and ctx.nproj > 0:
-        per_launch_ms = px["ms"] / px["launches"]
-        flops = 8.0 * ctx.npw * ctx.nb * ctx.nproj
-        achieved = flops / (per_launch_ms / 1000.0) / 1e12
-        roofline_fp32 = {"bound": "alu", "kernel": "proj_PX (k_nn_stream, FP32 FMA)", "achieved": achieved,
-                         "peak": FP32_TFLOPS_NOMINAL, "unit": "TFLOP/s", "frac": achieved / FP32_TFLOPS_NOMINAL,
-                         "peak_kind": "nominal: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
-                         "flops_per_launch": flops, "ms_per_launch": per_launch_ms,
-                         "share_of_step": px["ms"] / total_prof}
+        work = family_work(ctx, cfg, e["name"], csize, rsize, args.precision, tensor)
+        if work is None:
+            continue
+        bound, amount = work
+        per_launch_ms = e["ms"] / e["launches"]
+        if bound == "hbm":
+            achieved = amount / (per_launch_ms / 1000.0) / 1e9
+            ent = {"bound": "hbm", "kernel": e["name"], "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                   "frac": achieved / hbm, "peak_kind": f"{peak_kind} (copy bandwidth)",
+                   "traffic": traffic_record(e["name"]), "algorithmic_bytes_per_launch": amount}
+        else:
+            peak, pk = alu_peak(args.precision, bound)
+            achieved = amount / (per_launch_ms / 1000.0) / 1e12
+            ent = {"bound": bound, "kernel": e["name"], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                   "frac": achieved / peak, "peak_kind": pk, "traffic": None, "flops_per_launch": amount}
+        ent["ms_per_launch"] = per_launch_ms
+        ent["share_of_step"] = e["ms"] / total_prof
+        rooflines.append(ent)
+    roofline = rooflines[0] if rooflines else None
+    roofline_hbm = next((r for r in rooflines if r["bound"] == "hbm"), None)
     launches = sum(e["launches"] for e in prof)
-    # ---- time to convergence: chosen (mixed) vs plain FP64
+    # ---- time to convergence: chosen (mixed) vs plain FP64, on the
+    # convergence workload, judged in the same state.  The closed-shell
+    # ground state (one minimum) carries the time-to-solution comparison;
+    # the singlet, whose minimisation has several stationary states, is
+    # reported with the state each leg reached.
     pcg = None
     if args.converge_iters > 0 and rank == 0:
+        base = replica_config(args.converge_workload, 0)
         params, t_train, losses = train_network(torch)
-        mixed = converge(cfg, "mixed", args.converge_iters, torch, args.converge_seconds)
-        mixed_mlp = converge(cfg, "mixed", args.converge_iters, torch, args.converge_seconds, params)
-        fp64 = converge(cfg, "fp64", args.converge_iters, torch, args.converge_seconds)
-        for leg in (mixed, mixed_mlp):
-            leg["dE_vs_fp64_final"] = (leg["E_final"] - fp64["E_final"]
-                                       if leg["E_final"] is not None and fp64["E_final"] is not None else None)
-            leg["same_state_as_fp64"] = leg["dE_vs_fp64_final"] is not None and abs(leg["dE_vs_fp64_final"]) < 1e-5
-        pcg = {"criterion": "|E_i+1 - E_i| < 1e-6 Ha on two consecutive iterations",
-               "mixed_tpa": mixed, "mixed_tpa_network": mixed_mlp, "fp64_tpa": fp64,
+        ground = syn_with(base, mode=0, n_closed=base["n_closed"] + 1)
+        g64 = converge(ground, "fp64", args.converge_iters, torch, args.converge_seconds, args.g_tol)
+        gl = {}
+        for key, prm in (("mixed_tpa", None), ("mixed_tpa_network", params)):
+            leg = converge(ground, "mixed", args.converge_iters, torch, args.converge_seconds, args.g_tol, params=prm)
+            leg["dE_vs_fp64_final"] = leg["E_final"] - g64["E_final"]
+            leg["dE_fp64_eval_vs_fp64_final"] = leg["E_final_fp64_eval"] - g64["E_final"]
+            leg["same_state_as_fp64"] = abs(leg["dE_fp64_eval_vs_fp64_final"]) < 1e-5
+            ok = leg["converged"] and g64["converged"] and leg["same_state_as_fp64"]
+            leg["time_to_solution_speedup_vs_fp64"] = g64["seconds"] / leg["seconds"] if ok else None
+            gl[key] = leg
+        singlet = {}
+        s64, p64 = converge(base, "fp64", args.converge_iters, torch, min(args.converge_seconds, 20.0), args.g_tol,
+                            keep=True)
+        sm, pm = converge(base, "mixed", args.converge_iters, torch, min(args.converge_seconds, 20.0), args.g_tol,
+                          keep=True)
+        sm["open_overlap_with_fp64"] = open_overlap(base, pm, p64, torch)
+        sm["same_state_as_fp64"] = sm["open_overlap_with_fp64"] > 0.99
+        sm["dE_vs_fp64_final"] = sm["E_final"] - s64["E_final"]
+        singlet = {"fp64_tpa": s64, "mixed_tpa": sm}
+        del p64, pm
+        pcg = {"workload": base["name"],
+               "criterion": f"|E_i+1 - E_i| < 1e-6 Ha on two consecutive iterations and |g| < {args.g_tol:g}",
+               "ground_state": {"fp64_tpa": g64, **gl,
+                                "same_state": "energies of the final orbitals, re-evaluated in FP64, within 1e-5 Ha"},
+               "singlet": {**singlet, "same_state": "open orbitals a, b: |<x|S|x_fp64>| > 0.99"},
                "network": {"trained_on": "tiny-16 seeds 1-8, singlet and closed shell", "train_seconds": t_train,
                            "loss_first": losses[0], "loss_last": losses[-1]},
-               "speedup_s_per_iter_mixed_vs_fp64": fp64["s_per_iter"] / mixed["s_per_iter"],
-               "mixed_diis": converge_diis(cfg, "mixed", args.converge_iters, torch,
-                                           min(args.converge_seconds, 20.0)),
-               "note": "seconds to convergence compare only between legs with same_state_as_fp64"}
+               "speedup_s_per_iter_mixed_vs_fp64": g64["s_per_iter"] / gl["mixed_tpa"]["s_per_iter"],
+               "mixed_diis_singlet": converge_diis(base, "mixed", args.converge_iters, torch,
+                                                   min(args.converge_seconds, 20.0), args.g_tol),
+               "note": "time-to-solution ratios only between converged legs in the FP64 leg's state"}
+    hybrid = None
+    if args.hybrid_applies > 0 and rank == 0:
+        hybrid = hybrid_leg(args, torch)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, dt, desc = oracle_sample(cfg, n_bands_timed=4)
-        cpu = {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": desc,
-               "seconds": dt}
+        cpu = cpu_baseline_leg(cfg["name"], args.cpu_seconds)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -578,7 +814,8 @@ def run_gpu(args):
                        "precision": args.precision, "parallelism": f"replicas{world}",
                        "l2": "per-step working set above the 129 MB L2 (plane buffers, projectors, band blocks)"},
             "roofline": roofline,
-            "roofline_fp32": roofline_fp32,
+            "roofline_hbm": roofline_hbm,
+            "rooflines": rooflines,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bytes_psi,
                     "d2h_bytes_per_step": bytes_psi},
@@ -588,6 +825,7 @@ def run_gpu(args):
             "pcg": pcg,
             "diis": diis,
             "forces": forces_leg,
+            "hybrid": hybrid,
             "profile": {e["name"]: {"launches": e["launches"], "ms": e["ms"]} for e in prof},
             "launch": "one CUDA graph per PCG iteration",
             "E_last": infos[-1]["E_new"] if infos else None,

@@ -96,20 +96,57 @@ typedef struct {
     const double* Q;
 } roks_species;
 
-/* n_closed doubly occupied bands; modes 1 and 2 add the open bands a, b. */
+/* n_closed doubly occupied bands; modes 1 and 2 add the two singly
+ * occupied bands a, b (Fig. 1A).  n_open states the open-shell size and must
+ * be 0 for ROKS_MODE_GS and 2 for the other modes (ROKS_EINVAL otherwise). */
 typedef struct {
     int n_closed;
+    int n_open;
     int mode;
 } roks_occ;
 
+/* Exact-exchange kernels v(G) of the pair potentials (Sec. III hybrid). */
+enum {
+    ROKS_EXX_TRUNCATED = 0,   /* spherical truncation, v = 4 pi (1 - cos(|G| R_c)) / G^2,
+                                 v(0) = 2 pi R_c^2, R_c = (3 Omega / 4 pi)^(1/3) */
+    ROKS_EXX_BARE = 1         /* bare Coulomb 4 pi / G^2 without the G = 0 term  */
+};
+
+/* Options.  Every field after e_tol takes its default when zero. */
 typedef struct {
-    int precision;     /* ROKS_FP64 or ROKS_MIXED (FP32 FFTs and contractions,
-                          FP64 Cholesky, reductions and scalars)             */
+    int precision;     /* ROKS_FP64, or ROKS_MIXED: FP32 transforms and
+                          contractions, band-space work in FP32 on FP64
+                          storage (the overlap Cholesky in deviation form
+                          O = I + Delta up to 64 bands, so that its rounding
+                          scales with |Delta|), FP64 energy combination and
+                          PCG scalars, compensated FP32 block sums           */
     double alpha;      /* exact-exchange fraction (0 = none); Slater exchange
                           is scaled by (1 - alpha)                           */
     int suppress_ab;   /* 1: zero the open-shell a-b block of R (Eq. 20),
                           the coupling suppression of Sec. II A              */
-    double e_tol;      /* PCG convergence: |E_i+1 - E_i| < e_tol twice (Ha)  */
+    double e_tol;      /* convergence: |E_i+1 - E_i| < e_tol (Ha) on two
+                          consecutive steps (0: 1e-6)                        */
+    double g_tol;      /* and, when > 0, the gradient norm |g| (PCG) or the
+                          residual norm |R| (DIIS) of the last step < g_tol  */
+    int max_iter;      /* > 0: a step that is the max_iter-th since the last
+                          roks_init_orbitals, roks_orthonormalize or
+                          roks_invalidate without having converged returns
+                          ROKS_ENOCONV (its update is kept)                  */
+    uint64_t seed;     /* SplitMix64 seed of roks_init_orbitals when it is
+                          given no host random numbers                       */
+    int precond;       /* ROKS_PRECOND_TPA (0) or ROKS_PRECOND_TPA_MLP: the
+                          learned correction with all-zero weights (m = 1,
+                          TPA itself) until roks_set_preconditioner loads
+                          trained ones                                       */
+    int autotune;      /* 1: roks_setup times the candidate launch shapes of
+                          the band transforms and keeps the fastest          */
+    int exx_kernel;    /* ROKS_EXX_TRUNCATED (0) or ROKS_EXX_BARE            */
+    int wait_cap;      /* polls of every bounded device wait (mbarrier waits
+                          of the streamed and tensor-core contractions) before
+                          it gives up with ROKS_ETIMEOUT; 0: 2^26; < 0: no
+                          poll at all, so every such wait gives up (a test of
+                          the timeout path).  Copies already in flight are
+                          still waited for with the default cap.             */
 } roks_options;
 
 /* Energy terms (Ha).  E_kin, E_loc, E_nl carry the occupation weights;
@@ -133,7 +170,8 @@ typedef struct {
     double beta;         /* Fletcher-Reeves ratio used (0 after a restart)  */
     double dE0;          /* directional derivative of E along the step      */
     int restarted;       /* 1 when the CG direction was reset               */
-    int converged;       /* 1 once |dE| < e_tol on two consecutive steps    */
+    int converged;       /* 1 once |dE| < e_tol on two consecutive steps
+                            (and grad_norm < g_tol when g_tol > 0)           */
 } roks_step_info;
 
 /* Builds the plane-wave basis (Miller vectors with |G|^2/2 <= ecut, tested
@@ -155,11 +193,24 @@ ROKS_API roks_status roks_basis(roks_ctx* ctx, int* npw, int* nbands, int* ld_mi
                        const int32_t** miller);
 
 /* Initial orbitals (seeded start): u_host holds nbands x npw x 2 uniform
- * numbers (band major, re/im innermost); the library forms
+ * numbers in [-1, 1) (band major, re/im innermost); the library forms
  * c_nG = (u_re + i u_im)/(1 + |G|^2) and S-orthonormalises them into psi
- * (device, ld >= npw).  u_host is read before the call returns. */
+ * (device, ld >= npw).  u_host is read before the call returns.  With
+ * u_host NULL the numbers are drawn on the device: number i (same order) is
+ * -1 + 2 (z_i >> 11) 2^-53, z_i output i of SplitMix64 seeded with
+ * roks_options.seed (z_i = mix(seed + (i + 1) 0x9E3779B97F4A7C15) with
+ * Vigna's mixing function).  Allocates nothing (host numbers are staged in
+ * the context's workspaces).  Resets the direction and DIIS histories. */
 ROKS_API roks_status roks_init_orbitals(roks_ctx* ctx, const double* u_host,
                                void* psi, int64_t ld);
+
+/* Forgets everything the context derived from orbital buffers: the density
+ * and potentials, the projector coefficients P^H psi, the transform planes,
+ * the PCG direction and DIIS histories.  Steps and force calls key these on
+ * the buffer address and leading dimension alone, so a caller that writes
+ * new values into a buffer a step or force call has used (a copy from the
+ * host, an in-place edit) calls this before the next call on it. */
+ROKS_API roks_status roks_invalidate(roks_ctx* ctx);
 
 /* Class densities rho_k(r) = sum_{n in k} |psi_n(r)|^2, k = closed, a, b
  * (the inputs of the spin densities of Eq. 8), plus the kinetic and
@@ -183,9 +234,10 @@ ROKS_API roks_status roks_potential(roks_ctx* ctx, roks_energies* e, void* vclas
 ROKS_API roks_status roks_apply_h(roks_ctx* ctx, const void* psi, int64_t ld,
                          void* fpsi, void* spsi, void* grad);
 
-/* In place S-orthonormalisation: O = Psi^H S Psi = L L^H (FP64 Cholesky),
- * Psi <- Psi L^{-H}; band order closed, a, b.  ROKS_ENOTPOSDEF if O is not
- * positive definite. */
+/* In place S-orthonormalisation: O = Psi^H S Psi = L L^H (Cholesky: FP64
+ * on the FP64 path; on the mixed path FP32 in deviation form up to 64 bands
+ * and blocked FP32 beyond), Psi <- Psi L^{-H}; band order closed, a, b.
+ * ROKS_ENOTPOSDEF if O is not positive definite. */
 ROKS_API roks_status roks_orthonormalize(roks_ctx* ctx, void* psi, int64_t ld);
 
 /* One PCG iteration on psi (in place, S-orthonormal on entry and exit):
@@ -195,8 +247,11 @@ ROKS_API roks_status roks_orthonormalize(roks_ctx* ctx, void* psi, int64_t ld);
  * orth((Psi + Delta s) exp(Delta (A^i + beta A^{i-1}))) (Eq. 24).  The
  * direction history lives in the context; the first call (or the first after
  * roks_init_orbitals / roks_orthonormalize) starts with steepest descent.
- * psi must not be modified by the caller between consecutive steps.
- * Fills *info (host).  Synchronises. */
+ * psi must not be modified by the caller between consecutive steps (or
+ * roks_invalidate must be called after such a change).  ROKS_EDIVERGED for
+ * a non-finite energy or gradient (checked before any other status);
+ * ROKS_ENOCONV past roks_options.max_iter.  Fills *info (host).
+ * Synchronises. */
 ROKS_API roks_status roks_pcg_step(roks_ctx* ctx, void* psi, int64_t ld,
                           roks_step_info* info);
 
@@ -240,10 +295,12 @@ typedef struct {
     double res_norm;   /* Frobenius norm of the residual R at the start     */
     int window;        /* pairs the extrapolation used                      */
     double coef[ROKS_DIIS_MAX];   /* their coefficients, oldest first        */
-    int converged;     /* 1 once |E_new - E| < e_tol on two consecutive steps */
+    int converged;     /* 1 once |E_new - E| < e_tol on two consecutive steps
+                          (and res_norm < g_tol when g_tol > 0)             */
 } roks_diis_info;
 
-/* One DIIS step on psi (in place, S-orthonormal on entry and exit).  opt
+/* One DIIS step on psi (in place, S-orthonormal on entry and exit; psi
+ * unmodified by the caller between steps, as for roks_pcg_step).  opt
  * NULL takes history 6, tau 1/2, lambda_ab = lambda_ba = 1/2.  ROKS_EINVAL
  * for options out of range; ROKS_EDIVERGED for a non-finite residual or
  * energy; ROKS_ENOTPOSDEF if the extrapolated orbitals are linearly
@@ -268,9 +325,25 @@ ROKS_API roks_status roks_diis_step(roks_ctx* ctx, void* psi, int64_t ld, const 
  * forces_host: natoms x 3 doubles (Ha/Bohr, atom order of roks_setup, x y z
  * innermost), written before the call returns.  Uses the density and
  * potentials of psi when a PCG or DIIS step (or a force call) on the same
- * buffer left them current, and forms them otherwise.
+ * buffer and leading dimension left them current, and forms them otherwise;
+ * after writing new orbitals into such a buffer, call roks_invalidate first.
+ * The call leaves the step's own state (potentials, projector coefficients,
+ * direction history) as it was: the next step on psi proceeds unchanged.
  * ROKS_EDIVERGED for a non-finite force.  Synchronises. */
 ROKS_API roks_status roks_forces(roks_ctx* ctx, const void* psi, int64_t ld, double* forces_host);
+
+/* Launch shapes in use (the autotuner's choices when roks_options.autotune
+ * was set, else the defaults): the number of band groups of the density's
+ * x-stage transform (2, 4 or 8; default 4) and the K-split depth of the
+ * tensor-core A^H B products in waves of one CTA per SM, times two (3, 5 or
+ * 8; default 5).  candidate_ms: the timed candidates in that order (ms per
+ * launch; 0 when not timed).  Host struct, filled before the call returns. */
+typedef struct {
+    int density_groups;
+    int tc_split_waves_x2;
+    double candidate_ms[6];
+} roks_tuning;
+ROKS_API roks_status roks_tuning_get(const roks_ctx* ctx, roks_tuning* t);
 
 /* Energies of the last completed density/potential evaluation.  Synchronises. */
 ROKS_API roks_status roks_energies_get(roks_ctx* ctx, roks_energies* e);
@@ -288,9 +361,10 @@ typedef struct {
 ROKS_API roks_status roks_profile_enable(roks_ctx* ctx, int enable);
 
 /* Synchronises the stream, writes up to cap entries to out (host), sets
- * *count to the number of entries and clears the record.  The last entry,
- * "kernel_launches", counts every kernel the library launched (in any
- * context of the process) since profiling was enabled, with ms = 0. */
+ * *count to the number of entries and clears the record.  The last two
+ * entries, with ms = 0, count the kernels the library launched (in any
+ * context of the process) since the last read: "kernel_launches" all of
+ * them, "tensor_core_launches" the tcgen05 contractions among them. */
 ROKS_API roks_status roks_profile_read(roks_ctx* ctx, roks_profile_entry* out, int cap,
                                        int* count);
 
@@ -305,8 +379,10 @@ ROKS_API roks_status roks_profile_read(roks_ctx* ctx, roks_profile_entry* out, i
  * context and allocates nothing: its scratch (4.2 MiB: split-K partial sums,
  * the overlap, L^{-H} and a status flag) is a fixed array in the library's
  * device memory, present on every GPU that loads the library until the
- * process exits.  The first call on a device resolves that array's device
- * address; make it before any stream capture.  All calls share the array
+ * process exits.  Every call looks up that array's device address on the
+ * current device (cudaGetSymbolAddress) before it launches anything; the
+ * call synchronises its stream, so it is not for use under stream capture.
+ * All calls share the array
  * and it keeps the last call's contents, so calls that overlap on the GPU
  * (different streams or threads at once) race; serialise them.
  * Limits: nbands <= 64 (ROKS_EINVAL beyond).  Synchronises the stream;

@@ -3,6 +3,7 @@
 // L, and the matrix exponential by Taylor + squaring on a tiled square GEMM.
 // Element type U is float2 (mixed path) or double2 (FP64 path); the work is
 // spread over many blocks because GB300's FP64 rate per SM is small.
+#include <algorithm>
 #include <cmath>
 
 #include "roks_impl.cuh"
@@ -293,16 +294,22 @@ void cholesky_inverse_big(int n, const double2* O, void* work, bool fp64, double
 }
 
 // ------------------------------------------------------------------ matrix exponential, large n
-// C = alpha A B (+ I when add_identity), n x n, 32 x 32 tiles, 256 threads,
-// each thread 4 outputs.
+// C = alpha A B (+ I when add_identity), n x n, 32 x 32 output tiles per
+// block of 256 threads, thread (tx, ty) owning rows ty + 16 i and columns
+// tx + 16 j (i, j < 2), K in slices of 16 staged in shared memory (two
+// shared-memory loads per complex multiply-add pair of the tile).  With
+// guard, launches past the device's squaring count copy A through.
+constexpr int SQ_K = 16;
+
 template <typename U>
 __global__ void __launch_bounds__(256) k_sq_gemm(int n, const U* __restrict__ A, const U* __restrict__ B,
                                                  U* __restrict__ C, typename Real<U>::type alpha, int add_identity,
                                                  const double* __restrict__ guard, int step) {
     using R = typename Real<U>::type;
-    __shared__ U As[BK][BK + 1];
-    __shared__ U Bs[BK][BK + 1];
+    __shared__ U As[SQ_K][BK + 1];
+    __shared__ U Bs[SQ_K][BK + 1];
     const int i0 = blockIdx.x * BK, j0 = blockIdx.y * BK;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     if (guard && step >= int(guard[0])) {
         // squaring beyond q: copy through
         for (int q = threadIdx.x; q < BK * BK; q += blockDim.x) {
@@ -311,80 +318,102 @@ __global__ void __launch_bounds__(256) k_sq_gemm(int n, const U* __restrict__ A,
         }
         return;
     }
-    R ar[4] = {0, 0, 0, 0}, ai[4] = {0, 0, 0, 0};
-    for (int k0 = 0; k0 < n; k0 += BK) {
-        for (int q = threadIdx.x; q < BK * BK; q += blockDim.x) {
+    R ar[2][2], ai[2][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) ar[a][b] = ai[a][b] = R(0);
+    for (int k0 = 0; k0 < n; k0 += SQ_K) {
+        for (int q = threadIdx.x; q < BK * SQ_K; q += blockDim.x) {
+            // A(i0 + r, k0 + c): rows contiguous; B(k0 + c, j0 + r): K contiguous
             const int r = q % BK, c = q / BK;
-            U z; z.x = 0; z.y = 0;
+            U z;
+            z.x = 0;
+            z.y = 0;
             As[c][r] = (i0 + r < n && k0 + c < n) ? A[(int64_t)(k0 + c) * n + i0 + r] : z;
-            Bs[c][r] = (k0 + r < n && j0 + c < n) ? B[(int64_t)(j0 + c) * n + k0 + r] : z;
+            const int kr = q % SQ_K, jc = q / SQ_K;
+            Bs[kr][jc] = (k0 + kr < n && j0 + jc < n) ? B[(int64_t)(j0 + jc) * n + k0 + kr] : z;
         }
         __syncthreads();
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            const int q = threadIdx.x + s * 256;
-            const int r = q % BK, c = q / BK;
-#pragma unroll 8
-            for (int kk = 0; kk < BK; ++kk) {
-                const U a = As[kk][r], b = Bs[c][kk];
-                ar[s] += a.x * b.x - a.y * b.y;
-                ai[s] += a.x * b.y + a.y * b.x;
+        for (int kk = 0; kk < SQ_K; ++kk) {
+            const U a0 = As[kk][ty], a1 = As[kk][ty + 16];
+            const U b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+            const U av[2] = {a0, a1}, bv[2] = {b0, b1};
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    ar[a][b] += av[a].x * bv[b].x - av[a].y * bv[b].y;
+                    ai[a][b] += av[a].x * bv[b].y + av[a].y * bv[b].x;
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int r = ty + 16 * a, c = tx + 16 * b;
+            if (i0 + r < n && j0 + c < n) {
+                U o;
+                o.x = alpha * ar[a][b] + ((add_identity && i0 + r == j0 + c) ? R(1) : R(0));
+                o.y = alpha * ai[a][b];
+                C[(int64_t)(j0 + c) * n + i0 + r] = o;
             }
         }
-        __syncthreads();
+}
+
+// Column sums sum_r (|Re a| + |Im a|) of A (a bound of the 1-norm with
+// fewer FP64 operations than the moduli): one warp per column.
+__global__ void k_big_colsum(int n, const double2* __restrict__ A, double* __restrict__ colsum) {
+    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= n) return;
+    double sum = 0.0;
+    for (int r = lane; r < n; r += 32) {
+        const double2 a = A[(int64_t)c * n + r];
+        sum += fabs(a.x) + fabs(a.y);
     }
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        const int q = threadIdx.x + s * 256;
-        const int r = q % BK, c = q / BK;
-        if (i0 + r < n && j0 + c < n) {
-            U o;
-            o.x = alpha * ar[s] + ((add_identity && i0 + r == j0 + c) ? R(1) : R(0));
-            o.y = alpha * ai[s];
-            C[(int64_t)(j0 + c) * n + i0 + r] = o;
-        }
-    }
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) colsum[c] = sum;
 }
 
 // X = s A / 2^q with ||s A||_1 / 2^q <= 1/4 (q on the device in info[0]);
-// P = I + X / degree.
+// P = I + X / degree.  Every block finds the largest column sum itself
+// (n values) and fills its share of the elements.
 template <typename U>
-__global__ void k_big_expm_scale(int n, const double2* __restrict__ A, const double* __restrict__ s, U* __restrict__ X,
-                                 U* __restrict__ P, double* __restrict__ info, int degree) {
-    __shared__ double colmax[256];
+__global__ void k_big_expm_scale(int n, const double2* __restrict__ A, const double* __restrict__ s,
+                                 const double* __restrict__ colsum, U* __restrict__ X, U* __restrict__ P,
+                                 double* __restrict__ info, int degree) {
+    __shared__ double red[256];
     __shared__ double fsh;
     double best = 0.0;
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        double sum = 0.0;
-        for (int r = 0; r < n; ++r) {
-            const double2 a = A[(int64_t)c * n + r];
-            sum += fabs(a.x) + fabs(a.y);        // bound of |a|, fewer FP64 operations than the modulus
-        }
-        best = fmax(best, sum);
-    }
-    colmax[threadIdx.x] = best;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) best = fmax(best, colsum[c]);
+    red[threadIdx.x] = best;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) colmax[threadIdx.x] = fmax(colmax[threadIdx.x], colmax[threadIdx.x + w]);
+        if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        double scaled = fabs(s[0]) * colmax[0];
+        double scaled = fabs(s[0]) * red[0];
         int q = 0;
         while (scaled > 0.25 && q < 40) {
             scaled *= 0.5;
             ++q;
         }
-        info[0] = double(q);
+        if (blockIdx.x == 0) info[0] = double(q);
         fsh = s[0] * ldexp(1.0, -q);
     }
     __syncthreads();
-    const double f = fsh;
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const double f = fsh, fd = fsh / degree;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * n; idx += gridDim.x * blockDim.x) {
         const double2 a = A[idx];
         X[idx] = ld_as<U>(make_double2(f * a.x, f * a.y));
         const int m = idx % n, c = idx / n;
-        P[idx] = ld_as<U>(make_double2((m == c ? 1.0 : 0.0) + f * a.x / degree, f * a.y / degree));
+        P[idx] = ld_as<U>(make_double2((m == c ? 1.0 : 0.0) + fd * a.x, fd * a.y));
     }
 }
 
@@ -398,7 +427,11 @@ template <typename U>
 void expm_big_impl(int n, const double2* A, const double* s, double2* E, U* X, U* P, U* Q, double* info, int degree,
                    int max_square, cudaStream_t st) {
     using R = typename Real<U>::type;
-    roks::count_launch(), k_big_expm_scale<U><<<1, 256, 0, st>>>(n, A, s, X, P, info, degree);
+    // the column sums go to E's storage (n doubles), overwritten at the end
+    double* colsum = reinterpret_cast<double*>(E);
+    roks::count_launch(), k_big_colsum<<<(unsigned)((32 * n + 255) / 256), 256, 0, st>>>(n, A, colsum);
+    const int fill_blocks = std::min(152, (n * n + 255) / 256);
+    roks::count_launch(), k_big_expm_scale<U><<<fill_blocks, 256, 0, st>>>(n, A, s, colsum, X, P, info, degree);
     const int nt = (n + BK - 1) / BK;
     dim3 g(nt, nt);
     for (int k = degree - 1; k >= 1; --k) {
@@ -416,7 +449,8 @@ size_t expm_big_work_bytes(int n, bool fp64) { return (fp64 ? sizeof(double2) : 
 
 void expm_big(int n, const double2* A, const double* scale_dev, double2* E, void* work, double* info, bool fp64,
               cudaStream_t st) {
-    // FP64: degree 16 (||X|| <= 1/4 gives 1e-26); FP32: degree 8 (1e-11)
+    // FP64: degree 16 (||X|| <= 1/4 gives 1e-26); FP32: degree 8 (1e-11);
+    // at most 24 squarings (the launches past the device's q copy through).
     if (fp64) {
         double2* X = static_cast<double2*>(work);
         expm_big_impl<double2>(n, A, scale_dev, E, X, X + (size_t)n * n, X + 2 * (size_t)n * n, info, 16, 24, st);

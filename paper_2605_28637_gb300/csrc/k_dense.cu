@@ -428,17 +428,17 @@ size_t gemm_cn_work(int M, int N, int K) {
 
 template <typename T>
 void gemm_cn(int M, int N, int K, const c2<T>* A, int64_t lda, const c2<T>* B, int64_t ldb, double2* C, int ldc,
-             double2* work, size_t work_elems, cudaStream_t st, bool allow_tc) {
+             double2* work, size_t work_elems, cudaStream_t st) {
     if (M <= 0 || N <= 0) return;
     const int max_chunks = (int)(work_elems / ((size_t)M * N));
     if constexpr (sizeof(T) == 4) {
-        // mixed path: tcgen05 tensor cores (split TF32) when enabled and the shape allows
-        if (!(allow_tc && tc_enabled()) &&
-            gemm_cn_stream(M, N, K, reinterpret_cast<const float2*>(A), lda, reinterpret_cast<const float2*>(B), ldb,
-                           C, ldc, work, work_elems, st))
+        // mixed path: large blocks on the tcgen05 tensor cores, the rest on
+        // the TMA-streamed SIMT kernel
+        if (gemm_cn_tcg(M, N, K, reinterpret_cast<const float2*>(A), lda, reinterpret_cast<const float2*>(B), ldb, C,
+                        ldc, work, work_elems * sizeof(double2), st))
             return;
-        if (allow_tc && gemm_cn_tc(M, N, K, reinterpret_cast<const float2*>(A), lda,
-                                   reinterpret_cast<const float2*>(B), ldb, C, ldc, work, max_chunks, st))
+        if (gemm_cn_stream(M, N, K, reinterpret_cast<const float2*>(A), lda, reinterpret_cast<const float2*>(B), ldb,
+                           C, ldc, work, work_elems, st))
             return;
     }
     run_cn<T>(cn_plan<T>(M, N, K, max_chunks), M, N, K, A, lda, B, ldb, C, ldc, work, st);
@@ -588,8 +588,15 @@ void launch_nn(int M, int N, int K, int ty, int nt, const c2<T>* A, int64_t lda,
 
 template <typename T>
 void gemm_nn(int M, int N, int K, const c2<T>* A, int64_t lda, const double2* B, int ldb, c2<T>* C, int64_t ldc,
-             double alpha, double beta, void* bwork, cudaStream_t st) {
+             double alpha, double beta, void* bwork, cudaStream_t st, size_t bwork_bytes) {
     if (M <= 0 || N <= 0) return;
+    if constexpr (sizeof(T) == 4) {
+        if (bwork_bytes > 0 &&
+            gemm_nn_tcg(M, N, K, reinterpret_cast<const float2*>(A), lda, B, ldb,
+                        beta != 0.0 ? reinterpret_cast<const float2*>(C) : nullptr, ldc, reinterpret_cast<float2*>(C),
+                        ldc, (float)alpha, (float)beta, bwork, bwork_bytes, st))
+            return;
+    }
     // column tiles of at most 64: RN = ceil(tile / 8) columns per thread, TY <= 8 warps
     const int nt = (N + 63) / 64;
     const int tn = (N + nt - 1) / nt;
@@ -621,9 +628,15 @@ void gemm_nn(int M, int N, int K, const c2<T>* A, int64_t lda, const double2* B,
 
 template <typename T>
 void gemm_nn_io(int M, int N, int K, const c2<T>* A, int64_t lda, const double2* B, int ldb, const c2<T>* Cin,
-                int64_t ldcin, c2<T>* Cout, int64_t ldc, double alpha, double beta, void* bwork, cudaStream_t st) {
+                int64_t ldcin, c2<T>* Cout, int64_t ldc, double alpha, double beta, void* bwork, cudaStream_t st,
+                size_t bwork_bytes) {
     if (M <= 0 || N <= 0) return;
     if constexpr (sizeof(T) == 4) {
+        if (bwork_bytes > 0 &&
+            gemm_nn_tcg(M, N, K, reinterpret_cast<const float2*>(A), lda, B, ldb, reinterpret_cast<const float2*>(Cin),
+                        ldcin, reinterpret_cast<float2*>(Cout), ldc, (float)alpha, (float)beta, bwork, bwork_bytes,
+                        st))
+            return;
         if (gemm_nn_stream(M, N, K, reinterpret_cast<const float2*>(A), lda, B, ldb, bwork,
                            reinterpret_cast<const float2*>(Cin), ldcin, reinterpret_cast<float2*>(Cout), ldc,
                            (float)alpha, (float)beta, st))
@@ -632,22 +645,22 @@ void gemm_nn_io(int M, int N, int K, const c2<T>* A, int64_t lda, const double2*
     if (beta != 0.0 && (Cin != Cout || ldcin != ldc))
         cudaMemcpy2DAsync(Cout, ldc * sizeof(c2<T>), Cin, ldcin * sizeof(c2<T>), M * sizeof(c2<T>), N,
                           cudaMemcpyDeviceToDevice, st);
-    gemm_nn<T>(M, N, K, A, lda, B, ldb, Cout, ldc, alpha, beta, bwork, st);
+    gemm_nn<T>(M, N, K, A, lda, B, ldb, Cout, ldc, alpha, beta, bwork, st, 0);
 }
 
 template void gemm_nn_io<float>(int, int, int, const float2*, int64_t, const double2*, int, const float2*, int64_t,
-                                float2*, int64_t, double, double, void*, cudaStream_t);
+                                float2*, int64_t, double, double, void*, cudaStream_t, size_t);
 template void gemm_nn_io<double>(int, int, int, const double2*, int64_t, const double2*, int, const double2*,
-                                 int64_t, double2*, int64_t, double, double, void*, cudaStream_t);
+                                 int64_t, double2*, int64_t, double, double, void*, cudaStream_t, size_t);
 
 template void gemm_cn<float>(int, int, int, const float2*, int64_t, const float2*, int64_t, double2*, int,
-                             double2*, size_t, cudaStream_t, bool);
+                             double2*, size_t, cudaStream_t);
 template void gemm_cn<double>(int, int, int, const double2*, int64_t, const double2*, int64_t, double2*, int,
-                              double2*, size_t, cudaStream_t, bool);
+                              double2*, size_t, cudaStream_t);
 template void gemm_nn<float>(int, int, int, const float2*, int64_t, const double2*, int, float2*, int64_t, double,
-                             double, void*, cudaStream_t);
+                             double, void*, cudaStream_t, size_t);
 template void gemm_nn<double>(int, int, int, const double2*, int64_t, const double2*, int, double2*, int64_t,
-                              double, double, void*, cudaStream_t);
+                              double, double, void*, cudaStream_t, size_t);
 
 // ------------------------------------------------------------------ small FP64 matrices
 // One warp per output element; the lanes split K and reduce with shuffles.
@@ -679,10 +692,119 @@ __global__ void k_small_gemm(int M, int N, int K, const double2* __restrict__ A,
     *c = r;
 }
 
+// ------------------------------------------------------------------ large band-space products
+// C = alpha op(A) op(B) + beta C on FP64 storage, for products too large for
+// one warp per element (hundreds of bands, thousands of projectors): 32 x 32
+// output tiles per block of 256 threads (enough blocks to fill the GPU at a
+// few hundred bands), thread (tx, ty) owning rows ty + 16 i and columns
+// tx + 16 j (i, j < 2); K in slices of 16 staged in shared memory, each load
+// coalesced along the operand's contiguous index.  Arithmetic type R (float
+// on the mixed path): every slice is summed on its own before it joins the
+// running sum, so that rounding grows with K / 16.
+constexpr int BS_T = 32, BS_K = 16, BS_R = 2;
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_bs_gemm(int M, int N, int K, const double2* __restrict__ A, int lda,
+                                                 int ca, const double2* __restrict__ B, int ldb, int cb,
+                                                 double2* __restrict__ C, int ldc, double alpha, double beta) {
+    __shared__ c2<R> As[BS_K][BS_T + 1];
+    __shared__ c2<R> Bs[BS_K][BS_T + 1];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int m0 = blockIdx.x * BS_T, n0 = blockIdx.y * BS_T;
+    c2<R> acc[BS_R][BS_R];
+#pragma unroll
+    for (int i = 0; i < BS_R; ++i)
+#pragma unroll
+        for (int j = 0; j < BS_R; ++j) acc[i][j].x = acc[i][j].y = R(0);
+    for (int k0 = 0; k0 < K; k0 += BS_K) {
+        for (int e = tid; e < BS_T * BS_K; e += 256) {
+            // op(A)[m][k]: A^H of a K x M matrix (k contiguous) or an M x K one (m contiguous)
+            const int ka = ca ? e % BS_K : e / BS_T, ma = ca ? e / BS_K : e % BS_T;
+            c2<R> v;
+            v.x = v.y = R(0);
+            if (m0 + ma < M && k0 + ka < K) {
+                const double2 d = ca ? A[(int64_t)(m0 + ma) * lda + k0 + ka] : A[(int64_t)(k0 + ka) * lda + m0 + ma];
+                v.x = (R)d.x;
+                v.y = ca ? -(R)d.y : (R)d.y;
+            }
+            As[ka][ma] = v;
+            // op(B)[k][n]: B^H of an N x K matrix (n contiguous) or a K x N one (k contiguous)
+            const int kb = cb ? e / BS_T : e % BS_K, nb = cb ? e % BS_T : e / BS_K;
+            c2<R> w;
+            w.x = w.y = R(0);
+            if (n0 + nb < N && k0 + kb < K) {
+                const double2 d = cb ? B[(int64_t)(k0 + kb) * ldb + n0 + nb] : B[(int64_t)(n0 + nb) * ldb + k0 + kb];
+                w.x = (R)d.x;
+                w.y = cb ? -(R)d.y : (R)d.y;
+            }
+            Bs[kb][nb] = w;
+        }
+        __syncthreads();
+        c2<R> t[BS_R][BS_R];
+#pragma unroll
+        for (int i = 0; i < BS_R; ++i)
+#pragma unroll
+            for (int j = 0; j < BS_R; ++j) t[i][j].x = t[i][j].y = R(0);
+#pragma unroll 4
+        for (int kk = 0; kk < BS_K; ++kk) {
+            c2<R> a[BS_R], b[BS_R];
+#pragma unroll
+            for (int i = 0; i < BS_R; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < BS_R; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < BS_R; ++i)
+#pragma unroll
+                for (int j = 0; j < BS_R; ++j) mac_nn<R>(t[i][j], a[i], b[j]);
+        }
+#pragma unroll
+        for (int i = 0; i < BS_R; ++i)
+#pragma unroll
+            for (int j = 0; j < BS_R; ++j) {
+                acc[i][j].x += t[i][j].x;
+                acc[i][j].y += t[i][j].y;
+            }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < BS_R; ++i) {
+        const int m = m0 + ty + 16 * i;
+        if (m >= M) continue;
+#pragma unroll
+        for (int j = 0; j < BS_R; ++j) {
+            const int n = n0 + tx + 16 * j;
+            if (n >= N) continue;
+            double2* c = C + (int64_t)n * ldc + m;
+            double2 r = make_double2(alpha * (double)acc[i][j].x, alpha * (double)acc[i][j].y);
+            if (beta != 0.0) {
+                r.x += beta * c->x;
+                r.y += beta * c->y;
+            }
+            *c = r;
+        }
+    }
+}
+
+// Products with at least this many outputs (and 32 or more terms each) go to
+// the tiled kernel; smaller ones keep one warp per element.
+static bool bs_tiled(int M, int N, int K) { return (long long)M * N >= 16384 && K >= 32; }
+
+template <typename R>
+static void bs_gemm(int M, int N, int K, const double2* A, int lda, bool ca, const double2* B, int ldb, bool cb,
+             double2* C, int ldc, double alpha, double beta, cudaStream_t st) {
+    const dim3 g((unsigned)((M + BS_T - 1) / BS_T), (unsigned)((N + BS_T - 1) / BS_T));
+    roks::count_launch();
+    k_bs_gemm<R><<<g, 256, 0, st>>>(M, N, K, A, lda, ca ? 1 : 0, B, ldb, cb ? 1 : 0, C, ldc, alpha, beta);
+}
+
 // op(A): A (M x K) or A^H when ca (A stored K x M); op(B) likewise.
 void small_gemm(int M, int N, int K, const double2* A, int lda, bool ca, const double2* B, int ldb, bool cb,
                 double2* C, int ldc, double alpha, double beta, cudaStream_t st) {
     if (M <= 0 || N <= 0) return;
+    if (bs_tiled(M, N, K)) {
+        bs_gemm<double>(M, N, K, A, lda, ca, B, ldb, cb, C, ldc, alpha, beta, st);
+        return;
+    }
     const long long threads = (long long)M * N * 32;
     roks::count_launch(), k_small_gemm<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(M, N, K, A, lda, ca, B, ldb, cb, C, ldc, alpha, beta);
 }
@@ -726,6 +848,10 @@ __global__ void k_small_gemm_f32(int M, int N, int K, const double2* __restrict_
 void small_gemm_f32(int M, int N, int K, const double2* A, int lda, bool ca, const double2* B, int ldb, bool cb,
                     double2* C, int ldc, double alpha, double beta, cudaStream_t st) {
     if (M <= 0 || N <= 0) return;
+    if (bs_tiled(M, N, K)) {
+        bs_gemm<float>(M, N, K, A, lda, ca, B, ldb, cb, C, ldc, alpha, beta, st);
+        return;
+    }
     const long long threads = (long long)M * N * 32;
     roks::count_launch(), k_small_gemm_f32<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
                               M, N, K, A, lda, ca, B, ldb, cb, C, ldc, alpha, beta);

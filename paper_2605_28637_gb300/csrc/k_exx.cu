@@ -10,9 +10,10 @@ namespace roks {
 
 constexpr double kPiX = 3.14159265358979323846;
 
-// v(G) / N^3 on the grid: 4 pi (1 - cos(|G| Rc)) / G^2, v(0) = 2 pi Rc^2.
+// v(G) / N^3 on the grid: 4 pi (1 - cos(|G| Rc)) / G^2, v(0) = 2 pi Rc^2
+// (spherical truncation); with bare != 0, 4 pi / G^2 and v(0) = 0.
 template <typename T>
-__global__ void k_exx_kernel(int N, double b, double Rc, T* __restrict__ vG) {
+__global__ void k_exx_kernel(int N, double b, double Rc, int bare, T* __restrict__ vG) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t N3 = (int64_t)N * N * N;
     if (p >= N3) return;
@@ -22,9 +23,9 @@ __global__ void k_exx_kernel(int N, double b, double Rc, T* __restrict__ vG) {
     double v;
     if (g2 > 0) {
         const double g = sqrt(g2);
-        v = 4.0 * kPiX * (1.0 - cos(g * Rc)) / g2;
+        v = bare ? 4.0 * kPiX / g2 : 4.0 * kPiX * (1.0 - cos(g * Rc)) / g2;
     } else {
-        v = 2.0 * kPiX * Rc * Rc;
+        v = bare ? 0.0 : 2.0 * kPiX * Rc * Rc;
     }
     vG[p] = T(v / double(N3));
 }
@@ -167,10 +168,11 @@ __global__ void k_exx_open_diag(int nb, const double* __restrict__ Kmat, ExxCoef
 
 // ------------------------------------------------------------------ host side
 template <typename T>
-void exx_setup_kernel(int N, double L, T* vG, cudaStream_t st) {
+void exx_setup_kernel(int N, double L, int bare, T* vG, cudaStream_t st) {
     const int64_t N3 = (int64_t)N * N * N;
     const double Rc = cbrt(3.0 * L * L * L / (4.0 * kPiX));
-    roks::count_launch(), k_exx_kernel<T><<<(unsigned)((N3 + 255) / 256), 256, 0, st>>>(N, 2.0 * kPiX / L, Rc, vG);
+    roks::count_launch(), k_exx_kernel<T><<<(unsigned)((N3 + 255) / 256), 256, 0, st>>>(N, 2.0 * kPiX / L, Rc, bare,
+                                                                                        vG);
 }
 
 template <typename T>
@@ -198,8 +200,8 @@ void exx_pairs(const ExxArgs<T>& a, bool want_field, cudaStream_t st) {
     roks::count_launch(), k_exx_open_diag<<<1, 32, 0, st>>>(a.nb, a.Kmat, a.cf, a.open_diag);
 }
 
-template void exx_setup_kernel<float>(int, double, float*, cudaStream_t);
-template void exx_setup_kernel<double>(int, double, double*, cudaStream_t);
+template void exx_setup_kernel<float>(int, double, int, float*, cudaStream_t);
+template void exx_setup_kernel<double>(int, double, int, double*, cudaStream_t);
 template void exx_pairs<float>(const ExxArgs<float>&, bool, cudaStream_t);
 template void exx_pairs<double>(const ExxArgs<double>&, bool, cudaStream_t);
 

@@ -115,15 +115,40 @@ __global__ void k_projectors(int npw, int nproj, double b, double omega, const i
     P[(int64_t)i * ldp + g] = mk<T>(T(re), T(im));
 }
 
+// Output i of SplitMix64 seeded with `seed` (counter based: Vigna's mixing
+// function applied to seed + (i + 1) * 0x9E3779B97F4A7C15), mapped to
+// [-1, 1) through its top 53 bits: -1 + 2 (z >> 11) 2^-53.
+__device__ __forceinline__ double splitmix64_pm1(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    const double u = (double)(z >> 11) * 0x1p-53;
+    return -1.0 + 2.0 * u;
+}
+
+// Bands band0 .. band0 + gridDim.y - 1: c_nG = (u_re + i u_im) / (1 + |G|^2),
+// the pair (u_re, u_im) read from u (numbered from band0) or, when u is
+// null, drawn as numbers 2 (n npw + g) and 2 (n npw + g) + 1 of the seed's
+// stream.
 template <typename T>
-__global__ void k_init_orbitals(int npw, int nb, const double* __restrict__ u, const double* __restrict__ g2,
-                                c2<T>* __restrict__ psi, int64_t ld) {
+__global__ void k_init_orbitals(int npw, int band0, const double* __restrict__ u, uint64_t seed,
+                                const double* __restrict__ g2, c2<T>* __restrict__ psi, int64_t ld) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = blockIdx.y;
+    const int n = band0 + blockIdx.y;
     if (g >= npw) return;
     const double d = 1.0 / (1.0 + g2[g]);
-    const double* un = u + ((int64_t)n * npw + g) * 2;
-    psi[(int64_t)n * ld + g] = mk<T>(T(un[0] * d), T(un[1] * d));
+    double ur, ui;
+    if (u) {
+        const double* un = u + ((int64_t)blockIdx.y * npw + g) * 2;
+        ur = un[0];
+        ui = un[1];
+    } else {
+        const uint64_t i = ((uint64_t)n * (uint64_t)npw + (uint64_t)g) * 2u;
+        ur = splitmix64_pm1(seed, i);
+        ui = splitmix64_pm1(seed, i + 1);
+    }
+    psi[(int64_t)n * ld + g] = mk<T>(T(ur * d), T(ui * d));
 }
 
 template <typename T>
@@ -490,9 +515,11 @@ void projectors_setup(int npw, int nproj, double L, const int* miller_dev, const
 }
 
 template <typename T>
-void init_orbitals(int npw, int nb, const double* u_dev, const double* g2, c2<T>* psi, int64_t ld, cudaStream_t st) {
-    dim3 g((npw + 255) / 256, nb);
-    roks::count_launch(), k_init_orbitals<T><<<g, 256, 0, st>>>(npw, nb, u_dev, g2, psi, ld);
+void init_orbitals(int npw, int band0, int nbands, const double* u_dev, uint64_t seed, const double* g2, c2<T>* psi,
+                   int64_t ld, cudaStream_t st) {
+    if (nbands <= 0) return;
+    dim3 g((npw + 255) / 256, nbands);
+    roks::count_launch(), k_init_orbitals<T><<<g, 256, 0, st>>>(npw, band0, u_dev, seed, g2, psi, ld);
 }
 
 template <typename T>
@@ -585,7 +612,8 @@ void axpy(int npw, int nb, const c2<T>* x, int64_t ldx, const c2<T>* y, int64_t 
 #define ROKS_INSTANTIATE_GRID(T)                                                                               \
     template void projectors_setup<T>(int, int, double, const int*, const double*, c2<T>*, int64_t,            \
                                       cudaStream_t);                                                           \
-    template void init_orbitals<T>(int, int, const double*, const double*, c2<T>*, int64_t, cudaStream_t);     \
+    template void init_orbitals<T>(int, int, int, const double*, uint64_t, const double*, c2<T>*, int64_t,     \
+                                   cudaStream_t);                                                              \
     template void to_real_type<T>(int64_t, const double*, T*, double, cudaStream_t);                           \
     template void column_sums<T>(int, int, int, const c2<T>*, int64_t, const c2<T>*, int64_t, const T*,       \
                                  double*, double*, cudaStream_t);                                              \

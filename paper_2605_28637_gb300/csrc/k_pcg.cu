@@ -83,11 +83,16 @@ void pcg_rotation(int nb, int n_closed, const double2* Theta, const double* kin_
                               Gin, A, sc);
 }
 
+// r1 = Re <A, Gin>, r2 = Re <A_prev, Gin> (sums over all n^2 elements).
+// One block (up to 64 bands), or block partials of a grid-stride sum and a
+// fixed-order final sum (larger n: the FP64 chains of one block take
+// hundreds of microseconds at a few hundred bands).
 __global__ void k_pcg_rot_dots(int nb, const double2* __restrict__ A, const double2* __restrict__ Ap,
-                               const double2* __restrict__ Gin, PcgScalars* sc) {
+                               const double2* __restrict__ Gin, double* __restrict__ part, PcgScalars* sc) {
     __shared__ double s1[256], s2[256];
     double r1 = 0, r2 = 0;
-    for (int i = threadIdx.x; i < nb * nb; i += blockDim.x) {
+    const int64_t n2 = (int64_t)nb * nb;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
         const double2 g = Gin[i], a = A[i], p = Ap[i];
         r1 += a.x * g.x + a.y * g.y;
         r2 += p.x * g.x + p.y * g.y;
@@ -103,15 +108,40 @@ __global__ void k_pcg_rot_dots(int nb, const double2* __restrict__ A, const doub
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        sc->r1 = s1[0];
-        sc->r2 = s2[0];
-        sc->rot_pg = 0.5 * s1[0];
+        if (gridDim.x == 1) {
+            sc->r1 = s1[0];
+            sc->r2 = s2[0];
+            sc->rot_pg = 0.5 * s1[0];
+        } else {
+            part[2 * blockIdx.x] = s1[0];
+            part[2 * blockIdx.x + 1] = s2[0];
+        }
     }
 }
 
-void pcg_rot_dots(int nb, const double2* A, const double2* Aprev, const double2* Gin, PcgScalars* sc,
+__global__ void k_pcg_rot_dots_final(int nblk, const double* __restrict__ part, PcgScalars* sc) {
+    if (threadIdx.x != 0) return;
+    double r1 = 0, r2 = 0;
+    for (int b = 0; b < nblk; ++b) {
+        r1 += part[2 * b];
+        r2 += part[2 * b + 1];
+    }
+    sc->r1 = r1;
+    sc->r2 = r2;
+    sc->rot_pg = 0.5 * r1;
+}
+
+void pcg_rot_dots(int nb, const double2* A, const double2* Aprev, const double2* Gin, double* part, PcgScalars* sc,
                   cudaStream_t st) {
-    roks::count_launch(), k_pcg_rot_dots<<<1, 256, 0, st>>>(nb, A, Aprev, Gin, sc);
+    if (nb <= 64) {
+        roks::count_launch(), k_pcg_rot_dots<<<1, 256, 0, st>>>(nb, A, Aprev, Gin, part, sc);
+        return;
+    }
+    // part holds at least 2 x 16 x nb doubles (the column-sum partials): 2 nblk fit
+    int nblk = (nb * nb + 2047) / 2048;
+    if (nblk > 152) nblk = 152;
+    roks::count_launch(), k_pcg_rot_dots<<<nblk, 256, 0, st>>>(nb, A, Aprev, Gin, part, sc);
+    roks::count_launch(), k_pcg_rot_dots_final<<<1, 32, 0, st>>>(nblk, part, sc);
 }
 
 // beta = pg / pg_prev; dE(beta) = 2 a1 + 2 beta a2 + r1 + beta r2.

@@ -71,8 +71,11 @@ __device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, int x,
         : "memory");
 }
 
-__device__ __forceinline__ bool wait_or_flag(uint64_t* b, uint32_t parity) {
-    if (tc::mbar_wait(b, parity, ST_WAIT)) return true;
+// A wait of the work loop gives up after `cap` polls (the context's wait
+// cap); the waits for copies already in flight before the CTA exits use
+// the default cap, so that no copy outlives its CTA.
+__device__ __forceinline__ bool wait_or_flag(uint64_t* b, uint32_t parity, uint32_t cap) {
+    if (tc::mbar_wait(b, parity, cap)) return true;
     g_stream_timeout = 1;
     return false;
 }
@@ -99,7 +102,7 @@ template <int RM, int RN, int KS>
 __global__ void __launch_bounds__(cn_maxt(RM, RN)) k_cn_stream(int M, int N, int K, int rows_per_cta, int TY, int TX,
                                                    int NS, const __grid_constant__ CUtensorMap tmA,
                                                    const __grid_constant__ CUtensorMap tmB,
-                                                   float2* __restrict__ part) {
+                                                   float2* __restrict__ part, uint32_t wcap) {
     extern __shared__ __align__(1024) unsigned char st_smem[];
     __shared__ __align__(8) uint64_t full[ST_MAXS], empty[ST_MAXS];
     unsigned char* ring = aligned_smem(st_smem);
@@ -135,7 +138,7 @@ __global__ void __launch_bounds__(cn_maxt(RM, RN)) k_cn_stream(int M, int N, int
             int issued = 0;
             for (int s = 0; s < ns; ++s) {
                 const int sg = s % NS;
-                if (s >= NS && !wait_or_flag(&empty[sg], (uint32_t)((s / NS - 1) & 1))) break;
+                if (s >= NS && !wait_or_flag(&empty[sg], (uint32_t)((s / NS - 1) & 1), wcap)) break;
                 unsigned char* st = ring + (size_t)sg * stage_bytes;
                 const int k0 = rb + s * CN_KT;
                 mb_arrive_expect(&full[sg], tx_bytes);
@@ -145,7 +148,7 @@ __global__ void __launch_bounds__(cn_maxt(RM, RN)) k_cn_stream(int M, int N, int
             }
             // copies still in flight complete before the CTA may exit
             for (int s = (issued > NS ? issued - NS : 0); s < issued; ++s)
-                wait_or_flag(&full[s % NS], (uint32_t)((s / NS) & 1));
+                wait_or_flag(&full[s % NS], (uint32_t)((s / NS) & 1), ST_WAIT);
         }
         __syncwarp();
     } else {
@@ -178,7 +181,7 @@ __global__ void __launch_bounds__(cn_maxt(RM, RN)) k_cn_stream(int M, int N, int
         };
         for (int s = 0; s < ns; ++s) {
             const int sg = s % NS;
-            if (!wait_or_flag(&full[sg], (uint32_t)((s / NS) & 1))) break;
+            if (!wait_or_flag(&full[sg], (uint32_t)((s / NS) & 1), wcap)) break;
             const int rows = min(CN_KT, re - (rb + s * CN_KT));
             const int pairs = (rows + 1) >> 1;
             if (active) {
@@ -248,7 +251,8 @@ __global__ void __launch_bounds__(768) k_nn_stream(int M, int N, int K, int KC, 
                                                    int NS, int load_c, const __grid_constant__ CUtensorMap tmA,
                                                    const __grid_constant__ CUtensorMap tmC,
                                                    const float2* __restrict__ Bf, const double2* __restrict__ Bd,
-                                                   int ldb, float2* Cout, int64_t ldc, float alpha, float beta) {
+                                                   int ldb, float2* Cout, int64_t ldc, float alpha, float beta,
+                                                   uint32_t wcap) {
     constexpr int TR = 32 * RR * WS;
     constexpr int RP = RN / 2;
     extern __shared__ __align__(1024) unsigned char st_smem[];
@@ -287,7 +291,7 @@ __global__ void __launch_bounds__(768) k_nn_stream(int M, int N, int K, int KC, 
             int issued = 0;
             for (int it = 0; it < items; ++it) {
                 const int sg = it % NS;
-                if (it >= NS && !wait_or_flag(&empty[sg], (uint32_t)((it / NS - 1) & 1))) break;
+                if (it >= NS && !wait_or_flag(&empty[sg], (uint32_t)((it / NS - 1) & 1), wcap)) break;
                 unsigned char* st = ring + (size_t)sg * stage_bytes;
                 const int kc = it % nkc;
                 const int r0 = rb + (it / nkc) * TR;
@@ -297,9 +301,9 @@ __global__ void __launch_bounds__(768) k_nn_stream(int M, int N, int K, int KC, 
                 if (last && load_c) tma_2d(st + a_span, &tmC, r0, 0, &full[sg]);
                 issued = it + 1;
             }
-            if (!Bd) wait_or_flag(&bbar, 0u);
+            if (!Bd) wait_or_flag(&bbar, 0u, ST_WAIT);
             for (int it = (issued > NS ? issued - NS : 0); it < issued; ++it)
-                wait_or_flag(&full[it % NS], (uint32_t)((it / NS) & 1));
+                wait_or_flag(&full[it % NS], (uint32_t)((it / NS) & 1), ST_WAIT);
         }
         __syncwarp();
     } else if (warp < W * WS && nt > 0) {
@@ -313,7 +317,7 @@ __global__ void __launch_bounds__(768) k_nn_stream(int M, int N, int K, int KC, 
             }
             asm volatile("bar.sync 1, %0;" ::"r"(32 * W * WS) : "memory");
         } else {
-            ok = wait_or_flag(&bbar, 0u);
+            ok = wait_or_flag(&bbar, 0u, wcap);
         }
         const int w = warp % W, hb = (warp / W) * 32 * RR;
         int ncp[RP];
@@ -322,7 +326,7 @@ __global__ void __launch_bounds__(768) k_nn_stream(int M, int N, int K, int KC, 
         float2 acc[RR][RN];
         for (int it = 0; it < items && ok; ++it) {
             const int sg = it % NS;
-            if (!wait_or_flag(&full[sg], (uint32_t)((it / NS) & 1))) break;
+            if (!wait_or_flag(&full[sg], (uint32_t)((it / NS) & 1), wcap)) break;
             const int kc = it % nkc;
             const int r0 = rb + (it / nkc) * TR;
             const int rows = min(TR, re - r0);
@@ -487,12 +491,20 @@ int st_sm_count() {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// polls of the work-loop waits of the next launches (set_wait_cap)
+uint32_t g_wait_polls = ST_WAIT;
+
 template <typename F>
 void set_smem(F* f, size_t bytes) {
     cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 }  // namespace
+
+bool tensor_map_2d(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                   int box_cols, bool swizzle128) {
+    return encode_block(map, ptr, rows, cols, ld, box_rows, box_cols, swizzle128);
+}
 
 bool stream_enabled() {
     static int on = -1;
@@ -502,6 +514,9 @@ bool stream_enabled() {
     }
     return on == 1;
 }
+
+void set_wait_cap(int cap) { g_wait_polls = cap == 0 ? ST_WAIT : (cap < 0 ? 0u : (uint32_t)cap); }
+uint32_t wait_polls() { return g_wait_polls; }
 
 int stream_timeout_take() {
     int h = 0;
@@ -593,7 +608,8 @@ bool gemm_cn_stream(int M, int N, int K, const float2* A, int64_t lda, const flo
             attr = true;                                                                                   \
         }                                                                                                  \
         roks::count_launch();                                                                              \
-        k_cn_stream<RM_, RN_, KS_><<<G, threads, smem, st>>>(M, N, K, rows, ty, tx, NS, tmA, tmB, part);    \
+        k_cn_stream<RM_, RN_, KS_><<<G, threads, smem, st>>>(M, N, K, rows, ty, tx, NS, tmA, tmB, part,      \
+                                                             g_wait_polls);                                 \
     }
 #define CNS_KS(RM_, RN_) CNS_CASE(RM_, RN_, 1) CNS_CASE(RM_, RN_, 2) CNS_CASE(RM_, RN_, 4) CNS_CASE(RM_, RN_, 8)
     CNS_KS(3, 3) CNS_KS(4, 4) CNS_KS(4, 6) CNS_KS(2, 2)
@@ -676,7 +692,7 @@ bool gemm_nn_stream(int M, int N, int K, const float2* A, int64_t lda, const dou
         roks::count_launch();                                                                               \
         k_nn_stream<RR_, RN_, WS_><<<G, threads, smem, st>>>(M, N, K, KC, nkc, rows, W, NS, load_c ? 1 : 0,  \
                                                              tmA, tmC, Bf, convert_in ? B : nullptr, ldb,   \
-                                                             Cout, ldc, alpha, beta);                       \
+                                                             Cout, ldc, alpha, beta, g_wait_polls);         \
         return true;                                                                                        \
     }
 #define NNS_RN(RR_, WS_) NNS_CASE(RR_, 2, WS_) NNS_CASE(RR_, 4, WS_) NNS_CASE(RR_, 6, WS_) NNS_CASE(RR_, 8, WS_) \

@@ -1,0 +1,562 @@
+// k_tcgemm.cu -- complex FP32 contractions of the large blocks (hundreds of
+// bands, thousands of projectors) on the 5th-generation tensor cores
+// (tcgen05, kind::tf32), mixed-precision path:
+//
+//   CN:  C (M x N, FP64 out) = A^H B,          A: K x M, B: K x N (K: plane waves)
+//   NN:  Cout (M x N) = alpha A B + beta Cin,   A: M x K tall, B: K x N small (FP64)
+//
+// Real formulation.  Complex vectors are stored as interleaved (re, im)
+// pairs, so a complex dot product is a real one over 2K numbers taken as
+// stored from one operand (a'), against a rearranged copy of the other:
+//   CN  Re = a'.(br, bi),   Im = a'.(bi, -br)      (a' = conj taken by the pairing)
+//   NN  Re = a'.(br, -bi),  Im = a'.(bi, br)
+// The MMA's N side holds 64 complex columns as 128 rows: the 64 rows that
+// give the real parts, then the 64 that give the imaginary parts; one MMA of
+// M = 128, N = 128 yields both.
+//
+// Precision (three TF32 products per FP32 product): each operand value x is
+// split as x = hi + lo, hi = tf32(x), lo = tf32(x - hi), and each product is
+// lo.hi + hi.lo + hi.hi (three MMAs, smallest first).  The tensor cores'
+// FP32 accumulation truncates instead of rounding, which biases long sums of
+// like-signed terms (norms, overlaps, diagonal-dominated rotations), so
+// every K-step (8 reals, three MMAs) goes into a fresh tensor-memory
+// accumulator and the drain warps add it into FP32 sums in registers (round
+// to nearest).  Four accumulators of 128 columns rotate, so the MMAs of the
+// next K-steps run while the previous ones drain.
+//
+// One CTA per SM (200 KB of shared memory, all 512 tensor-memory columns),
+// 14 warps:
+//   warp 0      producer: 2-D tensor copies of the raw FP32 operand slices
+//               into three raw stages; NN: bulk copies of the pre-split B;
+//   warp 1      one thread issues the MMAs;
+//   warps 2-5   split a raw stage into TF32 hi and lo, build the N-side rows,
+//               and store K-major core matrices (8 rows x 16 bytes, no
+//               swizzle) into one of two operand stages;
+//   warps 6-13  drain the accumulators (warp % 4 picks the lane quadrant,
+//               warps 6-9 the complex columns 0-31, warps 10-13 columns
+//               32-63) and write the result.
+// Every wait is bounded (the context's wait cap); a wait that gives up sets
+// a device flag and the CTA winds down: copies and MMAs in flight are waited
+// for with the default bound before the tensor memory is freed.
+#include <cuda.h>
+
+#include <cstdint>
+#include <cstdlib>
+
+#include "roks_impl.cuh"
+#include "tc_sm103.cuh"
+
+namespace roks {
+
+// 2-D tensor map of a column-major complex FP32 block (k_stream.cu)
+bool tensor_map_2d(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                   int box_cols, bool swizzle128);
+
+static __device__ int g_tcg_timeout;
+
+namespace {
+
+constexpr int GB_M = 128;      // tile rows (tensor-memory lanes)
+constexpr int GB_NC = 64;      // complex columns of a tile
+constexpr int GB_NR = 128;     // N-side rows of a tile (real parts, then imaginary parts)
+constexpr int GB_KC = 16;      // complex K per stage
+constexpr int GB_KR = 32;      // real K per stage (four MMA K-steps of 8)
+constexpr int GB_RAW = 3;      // raw stages
+constexpr int GB_CONV = 2;     // operand stages
+constexpr int GB_ACC = 4;      // tensor-memory accumulators
+constexpr int GB_THREADS = 14 * 32;
+constexpr uint32_t GB_PART = GB_M * GB_KR * 4;   // one split part (hi or lo) of a 128-row operand: 16 KB
+constexpr uint32_t GB_SLOT = 4 * GB_PART;        // A hi | A lo | B hi | B lo
+constexpr uint32_t GB_RAWA = GB_M * GB_KC * 8;   // 16 KB
+constexpr uint32_t GB_RAWB = GB_NC * GB_KC * 8;  // 8 KB (CN)
+constexpr uint32_t GB_RAWS = GB_RAWA + GB_RAWB;
+constexpr size_t GB_SMEM = (size_t)GB_CONV * GB_SLOT + (size_t)GB_RAW * GB_RAWS + 1024;
+constexpr uint32_t GB_TCOLS = GB_ACC * GB_NR;    // 512 columns
+constexpr uint32_t GB_DEFAULT_WAIT = 1u << 26;
+
+// byte offset of real element kr of row r in a K-major operand tile of
+// 32 reals per row: core matrix (r / 8, kr / 4) of 128 bytes, row r % 8 at
+// 16 (r % 8), element kr % 4 at 4 (kr % 4)
+__device__ __forceinline__ uint32_t cofs(int r, int kr) {
+    return (uint32_t)((((r >> 3) * (GB_KR / 4) + (kr >> 2)) << 7) + ((r & 7) << 4) + ((kr & 3) << 2));
+}
+
+__device__ __forceinline__ void split4(const float4 v, float4& hi, float4& lo) {
+    hi.x = tc::to_tf32(v.x);
+    hi.y = tc::to_tf32(v.y);
+    hi.z = tc::to_tf32(v.z);
+    hi.w = tc::to_tf32(v.w);
+    lo.x = tc::to_tf32(v.x - hi.x);
+    lo.y = tc::to_tf32(v.y - hi.y);
+    lo.z = tc::to_tf32(v.z - hi.z);
+    lo.w = tc::to_tf32(v.w - hi.w);
+}
+
+__device__ __forceinline__ void put_split(unsigned char* hi_base, uint32_t off, const float4 v) {
+    float4 h, l;
+    split4(v, h, l);
+    *reinterpret_cast<float4*>(hi_base + off) = h;
+    *reinterpret_cast<float4*>(hi_base + GB_PART + off) = l;
+}
+
+// Bounded wait on a phase; gives up after `cap` polls, or early once another
+// role of the CTA has given up (checked every 1024 polls).
+__device__ __forceinline__ bool gwait(uint64_t* bar, uint32_t parity, uint32_t cap, volatile int* failed) {
+    for (uint32_t i = 0; i < cap; ++i) {
+        if (tc::mbar_try(bar, parity)) return true;
+        if ((i & 1023u) == 1023u && *failed) return false;
+    }
+    return false;
+}
+
+// The same wait by every lane of a warp, with one outcome for the warp (the
+// warp-wide instructions after it need all lanes): true only if every lane
+// saw the phase complete.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, uint32_t cap, volatile int* failed) {
+    const bool ok = gwait(bar, parity, cap, failed);
+    return __all_sync(0xffffffffu, ok) != 0;
+}
+
+__device__ __forceinline__ void give_up(volatile int* failed) {
+    *failed = 1;
+    g_tcg_timeout = 1;
+}
+
+template <bool NN>
+__global__ void __launch_bounds__(GB_THREADS, 1)
+    k_tcgemm(int M, int N, int stages_per_cta, int total_stages, const __grid_constant__ CUtensorMap tmA,
+             const __grid_constant__ CUtensorMap tmB, const unsigned char* __restrict__ bsplit,
+             float2* __restrict__ part, const float2* Cin, int64_t ldcin, float2* Cout, int64_t ldc, float alpha,
+             float beta, uint32_t wcap) {
+    extern __shared__ __align__(1024) unsigned char gb_smem[];
+    __shared__ __align__(8) uint64_t raw_full[GB_RAW], raw_empty[GB_RAW], conv_full[GB_CONV], conv_empty[GB_CONV],
+        b_full[GB_CONV], acc_full[GB_ACC], acc_empty[GB_ACC], mma_done;
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int failed;
+    unsigned char* base = gb_smem + ((1024u - (tc::smem_u32(gb_smem) & 1023u)) & 1023u);
+    unsigned char* conv = base;                                // GB_CONV operand stages
+    unsigned char* raw = base + (size_t)GB_CONV * GB_SLOT;     // GB_RAW raw stages (1024-byte aligned)
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * GB_M, n0 = blockIdx.y * GB_NC;
+    const int s0 = NN ? 0 : blockIdx.z * stages_per_cta;
+    const int ns = NN ? total_stages : max(0, min(total_stages, s0 + stages_per_cta) - s0);
+
+    if (tid == 0) {
+        for (int s = 0; s < GB_RAW; ++s) {
+            tc::mbar_init(&raw_full[s], 1);
+            tc::mbar_init(&raw_empty[s], 4);
+        }
+        for (int s = 0; s < GB_CONV; ++s) {
+            tc::mbar_init(&conv_full[s], 4);
+            tc::mbar_init(&conv_empty[s], 1);
+            tc::mbar_init(&b_full[s], 1);
+        }
+        for (int s = 0; s < GB_ACC; ++s) {
+            tc::mbar_init(&acc_full[s], 1);
+            tc::mbar_init(&acc_empty[s], 8);
+        }
+        tc::mbar_init(&mma_done, 1);
+        failed = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_base, GB_TCOLS);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0) {
+        // ------------------------------------------------ producer
+        if (lane == 0) {
+            int issued = 0, bissued = 0;
+            for (int i = 0; i < ns; ++i) {
+                const int rs = i % GB_RAW;
+                if (i >= GB_RAW && !gwait(&raw_empty[rs], (uint32_t)((i / GB_RAW - 1) & 1), wcap, &failed)) {
+                    give_up(&failed);
+                    break;
+                }
+                unsigned char* ra = raw + (size_t)rs * GB_RAWS;
+                const int k0 = (s0 + i) * GB_KC;
+                if (NN) {
+                    tc::mbar_arrive_expect_tx(&raw_full[rs], GB_RAWA);
+                    tc::tma_2d(ra, &tmA, m0, k0, &raw_full[rs]);
+                } else {
+                    tc::mbar_arrive_expect_tx(&raw_full[rs], GB_RAWS);
+                    tc::tma_2d(ra, &tmA, k0, m0, &raw_full[rs]);
+                    tc::tma_2d(ra + GB_RAWA, &tmB, k0, n0, &raw_full[rs]);
+                }
+                issued = i + 1;
+                if (NN) {
+                    // the pre-split B slice goes straight into the operand stage
+                    const int cs = i % GB_CONV;
+                    if (i >= GB_CONV &&
+                        !gwait(&conv_empty[cs], (uint32_t)((i / GB_CONV - 1) & 1), wcap, &failed)) {
+                        give_up(&failed);
+                        break;
+                    }
+                    tc::mbar_arrive_expect_tx(&b_full[cs], 2 * GB_PART);
+                    tc::bulk_g2s(conv + (size_t)cs * GB_SLOT + 2 * GB_PART,
+                                 bsplit + ((size_t)blockIdx.y * total_stages + i) * (2 * GB_PART), 2 * GB_PART,
+                                 &b_full[cs]);
+                    bissued = i + 1;
+                }
+            }
+            // copies still in flight complete before the CTA may exit
+            for (int i = issued > GB_RAW ? issued - GB_RAW : 0; i < issued; ++i)
+                gwait(&raw_full[i % GB_RAW], (uint32_t)((i / GB_RAW) & 1), GB_DEFAULT_WAIT, &failed);
+            for (int i = bissued > GB_CONV ? bissued - GB_CONV : 0; i < bissued; ++i)
+                gwait(&b_full[i % GB_CONV], (uint32_t)((i / GB_CONV) & 1), GB_DEFAULT_WAIT, &failed);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issue
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_tf32(GB_M, GB_NR);
+            constexpr uint32_t LBO = 128, SBO = (GB_KR / 4) * 128;
+            bool ok = true;
+            int u = 0;
+            for (int i = 0; i < ns && ok; ++i) {
+                const int cs = i % GB_CONV;
+                const uint32_t par = (uint32_t)((i / GB_CONV) & 1);
+                if (!gwait(&conv_full[cs], par, wcap, &failed) || (NN && !gwait(&b_full[cs], par, wcap, &failed))) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t sa = tc::smem_u32(conv + (size_t)cs * GB_SLOT);
+                for (int kk = 0; kk < GB_KR / 8; ++kk, ++u) {
+                    const int b = u % GB_ACC;
+                    if (u >= GB_ACC && !gwait(&acc_empty[b], (uint32_t)((u / GB_ACC - 1) & 1), wcap, &failed)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t d = tmem + (uint32_t)(b * GB_NR);
+                    const uint32_t ko = (uint32_t)kk * 256u;   // 8 reals = two K chunks of 128 bytes
+                    const uint64_t ahi = tc::make_desc(sa + ko, LBO, SBO);
+                    const uint64_t alo = tc::make_desc(sa + GB_PART + ko, LBO, SBO);
+                    const uint64_t bhi = tc::make_desc(sa + 2 * GB_PART + ko, LBO, SBO);
+                    const uint64_t blo = tc::make_desc(sa + 3 * GB_PART + ko, LBO, SBO);
+                    tc::mma_tf32(d, alo, bhi, idesc, 0u);
+                    tc::mma_tf32(d, ahi, blo, idesc, 1u);
+                    tc::mma_tf32(d, ahi, bhi, idesc, 1u);
+                    tc::commit(&acc_full[b]);
+                }
+                if (!ok) break;
+                tc::commit(&conv_empty[cs]);   // the operand stage is free once these MMAs complete
+            }
+            if (!ok) give_up(&failed);
+            // every MMA issued completes before the tensor memory is freed
+            tc::commit(&mma_done);
+            gwait(&mma_done, 0u, GB_DEFAULT_WAIT, &failed);
+        }
+        __syncwarp();
+    } else if (warp < 6) {
+        // ------------------------------------------------ conversion: raw FP32 -> split K-major tiles
+        const int c = tid - 64;   // 0..127
+        bool ok = true;
+        for (int i = 0; i < ns; ++i) {
+            const int rs = i % GB_RAW, cs = i % GB_CONV;
+            if (!warp_wait(&raw_full[rs], (uint32_t)((i / GB_RAW) & 1), wcap, &failed) ||
+                (i >= GB_CONV && !warp_wait(&conv_empty[cs], (uint32_t)((i / GB_CONV - 1) & 1), wcap, &failed))) {
+                ok = false;
+                break;
+            }
+            const unsigned char* ra = raw + (size_t)rs * GB_RAWS;
+            unsigned char* sl = conv + (size_t)cs * GB_SLOT;
+            if (!NN) {
+                // A row c (column c of A): 16 complex = eight 16-byte chunks,
+                // stored by the copy with the 128-byte swizzle
+#pragma unroll
+                for (int ch = 0; ch < 8; ++ch) {
+                    const float4 v = *reinterpret_cast<const float4*>(ra + c * 128 + ((ch ^ (c & 7)) << 4));
+                    put_split(sl, cofs(c, 4 * ch), v);
+                }
+                // B column j: the real-part row (re, im) and the imaginary-part row (im, -re)
+                const int j = c & 63, h = c >> 6;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int ch = 4 * h + q;
+                    const float4 v =
+                        *reinterpret_cast<const float4*>(ra + GB_RAWA + j * 128 + ((ch ^ (j & 7)) << 4));
+                    put_split(sl + 2 * GB_PART, cofs(j, 4 * ch), v);
+                    put_split(sl + 2 * GB_PART, cofs(GB_NC + j, 4 * ch), make_float4(v.y, -v.x, v.w, -v.z));
+                }
+            } else {
+                // A row c (plane wave m0 + c): the raw slice is [k][m], 1 KB per k
+#pragma unroll
+                for (int ch = 0; ch < 8; ++ch) {
+                    const float2 a0 = *reinterpret_cast<const float2*>(ra + (2 * ch) * 1024 + c * 8);
+                    const float2 a1 = *reinterpret_cast<const float2*>(ra + (2 * ch + 1) * 1024 + c * 8);
+                    put_split(sl, cofs(c, 4 * ch), make_float4(a0.x, a0.y, a1.x, a1.y));
+                }
+            }
+            tc::fence_async_smem();   // generic-proxy stores become visible to the tensor cores
+            __syncwarp();
+            if (lane == 0) {
+                tc::mbar_arrive(&raw_empty[rs]);
+                tc::mbar_arrive(&conv_full[cs]);
+            }
+        }
+        if (!ok) give_up(&failed);
+    } else {
+        // ------------------------------------------------ drain and epilogue
+        const int q = warp & 3;                 // lane quadrant
+        const int h = (warp - 6) >> 2;          // complex columns 32 h .. 32 h + 31
+        const int r = 32 * q + lane;            // tile row
+        float re[32], im[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) re[j] = im[j] = 0.f;
+        const int units = ns * (GB_KR / 8);
+        bool ok = true;
+        for (int u = 0; u < units; ++u) {
+            const int b = u % GB_ACC;
+            if (!warp_wait(&acc_full[b], (uint32_t)((u / GB_ACC) & 1), wcap, &failed)) {
+                ok = false;
+                break;
+            }
+            tc::fence_after_sync();
+            const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * GB_NR + 32 * h);
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                float v[16], w[16];
+                tc::tmem_ld16_nowait(ta + 16 * half, v);
+                tc::tmem_ld16_nowait(ta + GB_NC + 16 * half, w);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    re[16 * half + j] += v[j];
+                    im[16 * half + j] += w[j];
+                }
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&acc_empty[b]);
+        }
+        if (!ok) give_up(&failed);
+        if (ok) {
+            if (NN) {
+                const int m = m0 + r;
+                if (m < M) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int n = n0 + 32 * h + j;
+                        if (n < N) {
+                            float2 o = make_float2(alpha * re[j], alpha * im[j]);
+                            if (beta != 0.f) {
+                                const float2 ci = Cin[(int64_t)n * ldcin + m];
+                                o.x = fmaf(beta, ci.x, o.x);
+                                o.y = fmaf(beta, ci.y, o.y);
+                            }
+                            Cout[(int64_t)n * ldc + m] = o;
+                        }
+                    }
+                }
+            } else {
+                const int tile = blockIdx.x + blockIdx.y * gridDim.x;
+                const int tiles = gridDim.x * gridDim.y;
+                float2* P = part + ((int64_t)blockIdx.z * tiles + tile) * GB_NC * GB_M;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) P[(int64_t)(32 * h + j) * GB_M + r] = make_float2(re[j], im[j]);
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, GB_TCOLS);
+    }
+}
+
+// B (K x N complex FP64, ldb) -> the NN kernel's N-side operand: for each
+// (64-column tile t, stage s) a block of hi (16 KB) then lo (16 KB), rows
+// j < 64 (re, -im) and 64 + j (im, re) of column 64 t + j, K-major core
+// matrices; zero beyond K and N.
+__global__ void k_tcg_bsplit(int K, int N, const double2* __restrict__ B, int ldb, int nst, int nt,
+                             unsigned char* __restrict__ out) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)nt * nst * GB_NR * 8;
+    if (idx >= total) return;
+    const int ch = (int)(idx % 8);
+    const int r = (int)((idx / 8) % GB_NR);
+    const int s = (int)((idx / (8 * GB_NR)) % nst);
+    const int t = (int)(idx / (8 * GB_NR * nst));
+    const int n = t * GB_NC + (r % GB_NC);
+    float v[4];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int k = s * GB_KC + 2 * ch + e;
+        double2 b = make_double2(0.0, 0.0);
+        if (k < K && n < N) b = B[(int64_t)n * ldb + k];
+        if (r < GB_NC) {
+            v[2 * e] = (float)b.x;
+            v[2 * e + 1] = -(float)b.y;
+        } else {
+            v[2 * e] = (float)b.y;
+            v[2 * e + 1] = (float)b.x;
+        }
+    }
+    unsigned char* blk = out + ((size_t)t * nst + s) * (2 * GB_PART);
+    const uint32_t off = (uint32_t)((((r >> 3) * (GB_KR / 4) + ch) << 7) + ((r & 7) << 4));
+    float4 hi, lo;
+    split4(make_float4(v[0], v[1], v[2], v[3]), hi, lo);
+    *reinterpret_cast<float4*>(blk + off) = hi;
+    *reinterpret_cast<float4*>(blk + GB_PART + off) = lo;
+}
+
+// C (M x N, FP64, ldc) = sum over the K splits of the CN partials, in split
+// order (FP64 sums).
+__global__ void k_tcg_reduce(int M, int N, int mt, int tiles, int ks, const float2* __restrict__ part,
+                             double2* __restrict__ C, int ldc) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)M * N) return;
+    const int m = (int)(idx % M), n = (int)(idx / M);
+    const int tile = (m / GB_M) + (n / GB_NC) * mt;
+    const int64_t off = ((int64_t)tile * GB_NC + (n % GB_NC)) * GB_M + (m % GB_M);
+    double sr = 0.0, si = 0.0;
+    for (int z = 0; z < ks; ++z) {
+        const float2 p = part[(int64_t)z * tiles * GB_NC * GB_M + off];
+        sr += (double)p.x;
+        si += (double)p.y;
+    }
+    C[(int64_t)n * ldc + m] = make_double2(sr, si);
+}
+
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = 152;
+        }
+    }
+    return n;
+}
+
+bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+template <bool NN>
+void set_attr() {
+    static bool done = false;
+    if (!done) {
+        cudaFuncSetAttribute(k_tcgemm<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GB_SMEM);
+        done = true;
+    }
+}
+
+// Waves of CTAs (one per SM) a CN product is split into, times two
+// (tcg_set_waves; 5 = 2.5 waves unless the autotuner chose otherwise)
+int g_waves_x2 = 5;
+
+// K splits of a CN product: about g_waves_x2 / 2 waves of CTAs
+int cn_splits(int tiles, int total) {
+    int ks = (g_waves_x2 * sm_count() / 2 + tiles - 1) / tiles;
+    if (ks > total) ks = total;
+    if (ks < 1) ks = 1;
+    const int per = (total + ks - 1) / ks;
+    return (total + per - 1) / per;
+}
+
+}  // namespace
+
+// The tensor-core path is the default for shapes it takes; ROKS_TENSOR_CORES=0
+// keeps every contraction on the SIMT kernels.
+bool tcg_enabled() {
+    static int on = -1;
+    if (on < 0) {
+        const char* e = std::getenv("ROKS_TENSOR_CORES");
+        on = (e && e[0] == '0') ? 0 : 1;
+    }
+    return on == 1;
+}
+
+void tcg_set_waves(int waves_x2) { g_waves_x2 = waves_x2 >= 1 ? waves_x2 : 5; }
+
+bool tcg_cn_takes(int M, int N, int K) { return tcg_enabled() && M >= 128 && N >= 64 && K >= 1024; }
+bool tcg_nn_takes(int M, int N, int K) { return tcg_enabled() && M >= 4096 && N >= 64 && K >= 64; }
+
+size_t tcg_cn_work_bytes(int M, int N, int K) {
+    const int mt = (M + GB_M - 1) / GB_M, nt = (N + GB_NC - 1) / GB_NC, total = (K + GB_KC - 1) / GB_KC;
+    return (size_t)mt * nt * cn_splits(mt * nt, total) * GB_NC * GB_M * sizeof(float2);
+}
+
+size_t tcg_nn_work_bytes(int N, int K) {
+    const int nt = (N + GB_NC - 1) / GB_NC, total = (K + GB_KC - 1) / GB_KC;
+    return (size_t)nt * total * 2 * GB_PART;
+}
+
+static long long g_tcg_launches = 0;
+long long tcg_launches_take() {
+    const long long n = g_tcg_launches;
+    g_tcg_launches = 0;
+    return n;
+}
+
+// C = A^H B on the tensor cores; false when the shape, the alignment or the
+// work buffer does not allow it (the caller then takes the SIMT kernels).
+bool gemm_cn_tcg(int M, int N, int K, const float2* A, int64_t lda, const float2* B, int64_t ldb, double2* C, int ldc,
+                 void* work, size_t work_bytes, cudaStream_t st) {
+    if (!tcg_cn_takes(M, N, K)) return false;
+    if ((lda & 1) || (ldb & 1) || !aligned(A, 16) || !aligned(B, 16) || !aligned(work, 16)) return false;
+    const int mt = (M + GB_M - 1) / GB_M, nt = (N + GB_NC - 1) / GB_NC, total = (K + GB_KC - 1) / GB_KC;
+    const int ks = cn_splits(mt * nt, total);
+    const int per = (total + ks - 1) / ks;
+    if (tcg_cn_work_bytes(M, N, K) > work_bytes) return false;
+    CUtensorMap tmA, tmB;
+    if (!tensor_map_2d(&tmA, A, K, M, lda, GB_KC, GB_M, true) || !tensor_map_2d(&tmB, B, K, N, ldb, GB_KC, GB_NC, true))
+        return false;
+    set_attr<false>();
+    float2* part = static_cast<float2*>(work);
+    roks::count_launch();
+    g_tcg_launches += 1;
+    k_tcgemm<false><<<dim3(mt, nt, ks), GB_THREADS, GB_SMEM, st>>>(M, N, per, total, tmA, tmB, nullptr, part, nullptr,
+                                                                  0, nullptr, 0, 0.f, 0.f, wait_polls());
+    const int64_t outs = (int64_t)M * N;
+    roks::count_launch();
+    k_tcg_reduce<<<(unsigned)((outs + 255) / 256), 256, 0, st>>>(M, N, mt, mt * nt, ks, part, C, ldc);
+    return true;
+}
+
+// Cout = alpha A B + beta Cin on the tensor cores (B FP64, small); false when
+// not applicable.  Cout may be Cin; it must not overlap A.
+bool gemm_nn_tcg(int M, int N, int K, const float2* A, int64_t lda, const double2* B, int ldb, const float2* Cin,
+                 int64_t ldcin, float2* Cout, int64_t ldc, float alpha, float beta, void* bwork, size_t bwork_bytes,
+                 cudaStream_t st) {
+    if (!tcg_nn_takes(M, N, K) || !bwork) return false;
+    if ((lda & 1) || !aligned(A, 16) || !aligned(bwork, 16) || !aligned(Cout, 8)) return false;
+    if (beta != 0.f && (!Cin || !aligned(Cin, 8))) return false;
+    if (static_cast<const void*>(A) == static_cast<const void*>(Cout)) return false;
+    const int nt = (N + GB_NC - 1) / GB_NC, total = (K + GB_KC - 1) / GB_KC;
+    if (tcg_nn_work_bytes(N, K) > bwork_bytes) return false;
+    CUtensorMap tmA;
+    if (!tensor_map_2d(&tmA, A, M, K, lda, GB_M, GB_KC, false)) return false;
+    unsigned char* bs = static_cast<unsigned char*>(bwork);
+    const int64_t nsplit = (int64_t)nt * total * GB_NR * 8;
+    roks::count_launch();
+    k_tcg_bsplit<<<(unsigned)((nsplit + 255) / 256), 256, 0, st>>>(K, N, B, ldb, total, nt, bs);
+    set_attr<true>();
+    roks::count_launch();
+    g_tcg_launches += 1;
+    const int mt = (M + GB_M - 1) / GB_M;
+    k_tcgemm<true><<<dim3(mt, nt, 1), GB_THREADS, GB_SMEM, st>>>(M, N, total, total, tmA, tmA, bs, nullptr, Cin,
+                                                                ldcin, Cout, ldc, alpha, beta, wait_polls());
+    return true;
+}
+
+int tcg_timeout_take() {
+    int h = 0;
+    if (cudaMemcpyFromSymbol(&h, g_tcg_timeout, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (h) {
+        const int z = 0;
+        cudaMemcpyToSymbol(g_tcg_timeout, &z, sizeof(int));
+    }
+    return h;
+}
+
+}  // namespace roks

@@ -6,6 +6,7 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -31,7 +32,13 @@ struct roks_ctx {
     cudaStream_t st = nullptr;
     int prec = ROKS_FP64;
     // model
-    double L = 0, omega = 0, ecut = 0, alpha = 0, e_tol = 1e-6;
+    double L = 0, omega = 0, ecut = 0, alpha = 0, e_tol = 1e-6, g_tol = 0;
+    int max_iter = 0, wait_cap = 0, exx_kernel = 0, autotune = 0;
+    // launch shapes (the autotuner's choices, or the defaults)
+    int dens_groups = kDensityGroups, tc_waves_x2 = 5;
+    double tune_ms[6] = {0, 0, 0, 0, 0, 0};
+    uint64_t seed = 0;
+    long long steps = 0;   // PCG and DIIS steps since the orbitals were last set
     int N = 0, npw = 0, ld_min = 0, nmax = 0, M = 0, ncol = 0, np = 0;
     int nb = 0, nc = 0, mode = 1, nproj = 0, natoms = 0, suppress_ab = 0;
     double cM = 0, cT = 0;
@@ -87,9 +94,12 @@ struct roks_ctx {
     double *d_expart = nullptr, *d_Kmat = nullptr, *d_hf2 = nullptr, *d_exopen = nullptr;
     int npairs = 0, exx_batch = 0;
     ExxCoef exc{};
-    // state
-    const void* cache_psi = nullptr;   // potentials valid for this buffer (pcg chain)
-    const void* b_psi = nullptr;       // d_B holds P^H psi for this buffer
+    // state: the density/potentials and d_B = P^H psi belong to the buffer
+    // (address and leading dimension) a step or force call last used
+    const void* cache_psi = nullptr;
+    int64_t cache_ld = 0;
+    const void* b_psi = nullptr;
+    int64_t b_ld = 0;
     // Yp holds the y-stage planes of every band of this buffer (leading
     // dimension yp_ld): the density's x stage only reads them, so the next
     // apply of the same orbitals starts at the x stage
@@ -292,7 +302,7 @@ struct Impl {
         CK(cudaMemsetAsync(ctx->d_rho3, 0, sizeof(double) * 3 * (size_t)ctx->N * ctx->N * ctx->N, st));
         {
             PROF("fft_x_density");
-            band_x_density<T>(s, ccv(ctx->d_tw), cv(ctx->d_Yp), ctx->d_rho3, ctx->d_rho_slot, kDensityGroups, 0,
+            band_x_density<T>(s, ccv(ctx->d_tw), cv(ctx->d_Yp), ctx->d_rho3, ctx->d_rho_slot, ctx->dens_groups, 0,
                               ctx->nb, ctx->nc, 1.0 / ctx->omega, st);
         }
         column_sums<T>(0, ctx->npw, ctx->nb, p, ld, nullptr, 0, static_cast<const T*>(ctx->d_g2half), ctx->d_colpart, ctx->d_kin_b, st);
@@ -303,7 +313,10 @@ struct Impl {
                        ctx->d_gemm_work, ctx->gemm_work_elems, st);
             B = ctx->d_B;
         }
-        if (B == ctx->d_B) ctx->b_psi = psi;
+        if (B == ctx->d_B) {
+            ctx->b_psi = psi;
+            ctx->b_ld = ld;
+        }
         apply_DQ(ctx->nproj, ctx->nb, B, ctx->d_blk_off, ctx->d_blk_n, ctx->d_Drow, ctx->d_Qrow, nullptr,
                  ctx->d_DB, nullptr, st);
         band_quadratic(ctx->nproj, ctx->nb, B, ctx->d_DB, ctx->d_nl_b, st);
@@ -370,12 +383,13 @@ struct Impl {
                 gemm_cn<T>(ctx->nproj, ctx->nb, ctx->npw, ccv(ctx->d_P), ctx->ld_min, p, ld, ctx->d_B, ctx->nproj,
                            ctx->d_gemm_work, ctx->gemm_work_elems, st);
                 ctx->b_psi = psi;
+                ctx->b_ld = ld;
             }
             apply_DQ(ctx->nproj, ctx->nb, ctx->d_B, ctx->d_blk_off, ctx->d_blk_n, ctx->d_Drow, ctx->d_Qrow,
                      ctx->d_wband, ctx->d_DB, ctx->d_QB, st);
             PROF("proj_PX");
             gemm_nn<T>(ctx->npw, ctx->nb, ctx->nproj, ccv(ctx->d_P), ctx->ld_min, ctx->d_DB, ctx->nproj, cv(F), ldf,
-                       1.0, 1.0, ctx->d_gemm_work, st);
+                       1.0, 1.0, ctx->d_gemm_work, st, ctx->gemm_work_elems * sizeof(double2));
         }
         if (S) {
             CK(cudaMemcpy2DAsync(S, lds * sizeof(V), psi, ld * sizeof(V), ctx->npw * sizeof(V), ctx->nb,
@@ -383,7 +397,7 @@ struct Impl {
             if (ctx->nproj > 0) {
                 PROF("proj_PX");
                 gemm_nn<T>(ctx->npw, ctx->nb, ctx->nproj, ccv(ctx->d_P), ctx->ld_min, ctx->d_QB, ctx->nproj, cv(S),
-                           lds, 1.0, 1.0, ctx->d_gemm_work, st);
+                           lds, 1.0, 1.0, ctx->d_gemm_work, st, ctx->gemm_work_elems * sizeof(double2));
             }
         }
         CK(cudaGetLastError());
@@ -397,7 +411,7 @@ struct Impl {
         {
             PROF("orth_overlap");
             gemm_cn<T>(nb, nb, ctx->npw, ccv(in), ldi, ccv(in), ldi, ctx->d_O, nb, ctx->d_gemm_work,
-                       ctx->gemm_work_elems, st, false);
+                       ctx->gemm_work_elems, st);
         }
         if (ctx->nproj > 0) {
             {
@@ -432,17 +446,18 @@ struct Impl {
             PROF("orth_apply");
             if (dev)
                 gemm_nn_io<T>(ctx->npw, nb, nb, ccv(in), ldi, ctx->d_LinvH, nb, ccv(in), ldi, cv(out), ldo, 1.0, 1.0,
-                              ctx->d_gemm_work, st);
+                              ctx->d_gemm_work, st, ctx->gemm_work_elems * sizeof(double2));
             else
                 gemm_nn<T>(ctx->npw, nb, nb, ccv(in), ldi, ctx->d_LinvH, nb, cv(out), ldo, 1.0, 0.0,
-                           ctx->d_gemm_work, st);
+                           ctx->d_gemm_work, st, ctx->gemm_work_elems * sizeof(double2));
         }
         if (Bout && ctx->nproj > 0) {
             PROF("orth_small");
             if (dev)
                 CK(cudaMemcpyAsync(Bout, ctx->d_B2, sizeof(double2) * ctx->nproj * nb, cudaMemcpyDeviceToDevice, st));
-            (dev ? small_gemm_f32 : small_gemm)(ctx->nproj, nb, nb, ctx->d_B2, ctx->nproj, false, ctx->d_LinvH, nb,
-                                                false, Bout, ctx->nproj, 1.0, dev ? 1.0 : 0.0, st);
+            (ctx->prec == ROKS_MIXED ? small_gemm_f32 : small_gemm)(ctx->nproj, nb, nb, ctx->d_B2, ctx->nproj,
+                                                                   false, ctx->d_LinvH, nb, false, Bout, ctx->nproj,
+                                                                   1.0, dev ? 1.0 : 0.0, st);
         }
         CK(cudaGetLastError());
         return ROKS_OK;
@@ -452,15 +467,18 @@ struct Impl {
         int flag = 0;
         CK(cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
         CK(cudaStreamSynchronize(ctx->st));
-        if (tc_timeout_take())
-            return fail(ctx, ROKS_ETIMEOUT, "a tensor-core completion wait ran out (bounded mbarrier wait)");
-        if (stream_timeout_take())
-            return fail(ctx, ROKS_ETIMEOUT, "a bulk-copy wait of a streamed contraction ran out (bounded mbarrier wait)");
-        if (flag) {
+        const bool tc_out = tcg_timeout_take() != 0;
+        const bool st_out = stream_timeout_take() != 0;
+        if (flag || tc_out || st_out) {
             CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->st));
+            CK(cudaStreamSynchronize(ctx->st));
+        }
+        if (tc_out) return fail(ctx, ROKS_ETIMEOUT, "a tensor-core completion wait ran out (bounded mbarrier wait)");
+        if (st_out)
+            return fail(ctx, ROKS_ETIMEOUT, "a bulk-copy wait of a streamed contraction ran out (bounded mbarrier wait)");
+        if (flag)
             return fail(ctx, ROKS_ENOTPOSDEF,
                         "overlap matrix not positive definite at band " + std::to_string(flag - 1));
-        }
         return ROKS_OK;
     }
 
@@ -473,7 +491,7 @@ struct Impl {
         gemm_cn<T>(nb, nb, ctx->npw, ccv(ctx->W_S), l, ccv(x), l, ctx->d_Msm, nb, ctx->d_gemm_work,
                    ctx->gemm_work_elems, st);
         gemm_nn_io<T>(ctx->npw, nb, nb, ccv(psi), ld, ctx->d_Msm, nb, ccv(x), l, cv(out), l, -1.0, 1.0,
-                      ctx->d_gemm_work, st);
+                      ctx->d_gemm_work, st, ctx->gemm_work_elems * sizeof(double2));
     }
 
     // dst field = sum_n Re <x_n|y_n>
@@ -495,7 +513,10 @@ struct Impl {
         }
         CK(cudaEventRecord(ctx->fork_ev, ctx->st));
         CK(cudaStreamWaitEvent(ctx->side_st, ctx->fork_ev, 0));
-        cudaStream_t ss = ctx->side_st;
+        // profiled (eager) steps time the exponential as a family of its own
+        // on the main stream; otherwise it runs beside the band-block updates
+        cudaStream_t ss = ctx->prof_on ? ctx->st : ctx->side_st;
+        PROF("expm");
         if (nb > 64) {
             expm_big(nb, ctx->d_Atot, scd + step_field, ctx->d_U, ctx->d_bigwork, ctx->d_expm_info,
                      ctx->prec == ROKS_FP64, ss);
@@ -528,7 +549,7 @@ struct Impl {
             axpy<T>(ctx->npw, nb, ccv(psi), ld, ccv(ctx->W_s), l, scd + step_field, 1.0, cv(ctx->W_Y), l, st);
             roks_status r = join_U(ctx);
             if (r != ROKS_OK) return r;
-            gemm_nn<T>(ctx->npw, nb, nb, ccv(ctx->W_Y), l, ctx->d_U, nb, cv(ctx->W_Y2), l, 1.0, 0.0, ctx->d_gemm_work, st);
+            gemm_nn<T>(ctx->npw, nb, nb, ccv(ctx->W_Y), l, ctx->d_U, nb, cv(ctx->W_Y2), l, 1.0, 0.0, ctx->d_gemm_work, st, ctx->gemm_work_elems * sizeof(double2));
         }
         roks_status r = orth(ctx, ctx->W_Y2, l, out, ldo, ctx->d_B);
         if (r != ROKS_OK) return r;
@@ -563,9 +584,9 @@ struct Impl {
         {
         PROF("gradient_precond");
         gemm_nn_io<T>(npw, nb, nb, ccv(ctx->W_S), l, ctx->d_Gam, nb, ccv(ctx->W_F), l, cv(ctx->W_G), l, -1.0, 1.0,
-                      ctx->d_gemm_work, st);
+                      ctx->d_gemm_work, st, ctx->gemm_work_elems * sizeof(double2));
         gemm_nn_io<T>(npw, nb, nb, ccv(ctx->W_S), l, ctx->d_Th, nb, ccv(ctx->W_F), l, cv(ctx->W_gI), l, -1.0, 1.0,
-                      ctx->d_gemm_work, st);
+                      ctx->d_gemm_work, st, ctx->gemm_work_elems * sizeof(double2));
         column_total<T>(3, npw, nb, ccv(ctx->W_G), l, nullptr, 0, static_cast<const T*>(ctx->d_g2half), ctx->d_colpart,
                         reinterpret_cast<double*>(ctx->d_sc) + SC_FIELD(gnorm2), 1.0, st);
         // p_I = K g_I - Psi (S Psi)^H K g_I
@@ -578,7 +599,7 @@ struct Impl {
         }
         project(ctx, psi, ld, ctx->W_K, ctx->W_K);
         dot_to(ctx, ctx->W_K, ctx->W_gI, SC_FIELD(pgI));
-        pcg_rot_dots(nb, ctx->d_A, ctx->d_Aprev, ctx->d_Gin, ctx->d_sc, st);
+        pcg_rot_dots(nb, ctx->d_A, ctx->d_Aprev, ctx->d_Gin, ctx->d_colpart, ctx->d_sc, st);
         // u = p_I (projected above; the S-projector is idempotent on
         // S-orthonormal orbitals, so projecting again changes nothing),
         // v = proj(s_prev) (s_prev was projected against the previous orbitals)
@@ -666,18 +687,19 @@ struct Impl {
     static roks_status pcg_step(roks_ctx* ctx, void* psi, int64_t ld, roks_step_info* info) {
         cudaStream_t st = ctx->st;
         roks_status r;
-        if (!(ctx->pot_valid && ctx->cache_psi == psi)) {
+        if (!(ctx->pot_valid && ctx->cache_psi == psi && ctx->cache_ld == ld)) {
             r = density(ctx, psi, ld, nullptr);
             if (r != ROKS_OK) return r;
             r = potential(ctx);
             if (r != ROKS_OK) return r;
         }
-        if (ctx->nproj > 0 && ctx->b_psi != psi) {
+        if (ctx->nproj > 0 && !(ctx->b_psi == psi && ctx->b_ld == ld)) {
             // the iteration reuses P^H psi from d_B: form it if another call replaced it
             PROF("proj_PhPsi");
             gemm_cn<T>(ctx->nproj, ctx->nb, ctx->npw, ccv(ctx->d_P), ctx->ld_min, ccv(psi), ld, ctx->d_B, ctx->nproj,
                        ctx->d_gemm_work, ctx->gemm_work_elems, st);
             ctx->b_psi = psi;
+            ctx->b_ld = ld;
         }
         // the iteration's apply starts from the planes in Yp (a captured
         // iteration leaves those of its accepted point there)
@@ -685,6 +707,7 @@ struct Impl {
         r = pcg_run(ctx, psi, ld);
         if (r != ROKS_OK) return r;
         ctx->b_psi = psi;   // d_B: projector coefficients of the accepted point, now in psi
+        ctx->b_ld = ld;
         ctx->yp_psi = psi;
         ctx->yp_ld = ld;
         // scalars and status flag in one round trip (pinned host copies)
@@ -694,20 +717,34 @@ struct Impl {
         ctx->h_flag[1] = 0;
         if (sflag) CK(cudaMemcpyAsync(ctx->h_flag + 1, sflag, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        if (tc_timeout_take())
-            return fail(ctx, ROKS_ETIMEOUT, "a tensor-core completion wait ran out (bounded mbarrier wait)");
-        if (ctx->h_flag[1]) {
-            stream_timeout_take();
-            return fail(ctx, ROKS_ETIMEOUT, "a bulk-copy wait of a streamed contraction ran out (bounded mbarrier wait)");
-        }
-        if (*ctx->h_flag) {
+        // a wait that ran out comes first (the step's numbers are then
+        // meaningless), then non-finite numbers, then a failed Cholesky
+        const bool tc_out = tcg_timeout_take() != 0;
+        const bool st_out = ctx->h_flag[1] != 0;
+        if (st_out) stream_timeout_take();
+        const PcgScalars h = *ctx->h_sc;
+        const bool finite = std::isfinite(h.E0) && std::isfinite(h.Enew) && std::isfinite(h.gnorm2);
+        if (tc_out || st_out || !finite || *ctx->h_flag) {
             const int band = *ctx->h_flag - 1;
             CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), st));
+            CK(cudaStreamSynchronize(st));
+            ctx->pot_valid = false;
+            if (tc_out)
+                return fail(ctx, ROKS_ETIMEOUT, "a tensor-core completion wait ran out (bounded mbarrier wait)");
+            if (st_out)
+                return fail(ctx, ROKS_ETIMEOUT,
+                            "a bulk-copy wait of a streamed contraction ran out (bounded mbarrier wait)");
+            if (info) {
+                info->E = h.E0;
+                info->E_new = h.Enew;
+                info->grad_norm = std::sqrt(h.gnorm2);
+            }
+            if (!finite) return fail(ctx, ROKS_EDIVERGED, "non-finite energy or gradient");
             return fail(ctx, ROKS_ENOTPOSDEF, "overlap matrix not positive definite at band " + std::to_string(band));
         }
         ctx->cache_psi = psi;
+        ctx->cache_ld = ld;
         ctx->pot_valid = true;
-        const PcgScalars h = *ctx->h_sc;
         if (info) {
             info->E = h.E0;
             info->E_new = h.Enew;
@@ -719,8 +756,6 @@ struct Impl {
             info->dE0 = h.dE0;
             info->restarted = h.restarted != 0.0;
         }
-        if (!std::isfinite(h.Enew) || !std::isfinite(h.gnorm2))
-            return fail(ctx, ROKS_EDIVERGED, "non-finite energy or gradient");
         return ROKS_OK;
     }
 
@@ -734,15 +769,16 @@ struct Impl {
         roks_status r = ROKS_OK;
         // the density and potentials of psi are current after a PCG or DIIS
         // step on it (or a previous force call); otherwise form them
-        if (!(ctx->pot_valid && ctx->cache_psi == psi)) {
+        if (!(ctx->pot_valid && ctx->cache_psi == psi && ctx->cache_ld == ld)) {
             r = density(ctx, psi, ld, nullptr);
             if (r != ROKS_OK) return r;
             r = potential(ctx);
             if (r != ROKS_OK) return r;
             ctx->cache_psi = psi;
+            ctx->cache_ld = ld;
             ctx->pot_valid = true;
         }
-        r = apply(ctx, psi, ld, ctx->W_F, l, nullptr, 0, np_ > 0 && ctx->b_psi == psi,
+        r = apply(ctx, psi, ld, ctx->W_F, l, nullptr, 0, np_ > 0 && ctx->b_psi == psi && ctx->b_ld == ld,
                   ctx->yp_psi == psi && ctx->yp_ld == ld);
         if (r != ROKS_OK) return r;
         const double b = 2.0 * M_PI / ctx->L;
@@ -772,7 +808,7 @@ struct Impl {
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(out_host, ctx->d_forces, sizeof(double) * 3 * ctx->natoms, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        if (tc_timeout_take())
+        if (tcg_timeout_take())
             return fail(ctx, ROKS_ETIMEOUT, "a tensor-core completion wait ran out (bounded mbarrier wait)");
         if (stream_timeout_take())
             return fail(ctx, ROKS_ETIMEOUT, "a bulk-copy wait of a streamed contraction ran out (bounded mbarrier wait)");
@@ -793,17 +829,18 @@ struct Impl {
         const int64_t l = ctx->ld_min;
         const int64_t blk = l * nb;
         roks_status r;
-        if (!(ctx->pot_valid && ctx->cache_psi == psi)) {
+        if (!(ctx->pot_valid && ctx->cache_psi == psi && ctx->cache_ld == ld)) {
             r = density(ctx, psi, ld, nullptr);
             if (r != ROKS_OK) return r;
             r = potential(ctx);
             if (r != ROKS_OK) return r;
         }
-        if (ctx->nproj > 0 && ctx->b_psi != psi) {
+        if (ctx->nproj > 0 && !(ctx->b_psi == psi && ctx->b_ld == ld)) {
             PROF("proj_PhPsi");
             gemm_cn<T>(ctx->nproj, nb, npw, ccv(ctx->d_P), ctx->ld_min, ccv(psi), ld, ctx->d_B, ctx->nproj,
                        ctx->d_gemm_work, ctx->gemm_work_elems, st);
             ctx->b_psi = psi;
+            ctx->b_ld = ld;
         }
         CK(cudaMemcpyAsync(&ctx->d_diis->E0, ctx->d_E + 10, sizeof(double), cudaMemcpyDeviceToDevice, st));
         r = apply(ctx, psi, ld, ctx->W_F, l, ctx->W_S, l, ctx->nproj > 0, ctx->yp_psi == psi && ctx->yp_ld == ld);
@@ -823,7 +860,7 @@ struct Impl {
                              o.lambda_ba, ctx->d_Gam, st);
             // R = F - S Lambda
             gemm_nn_io<T>(npw, nb, nb, ccv(ctx->W_S), l, ctx->d_Gam, nb, ccv(ctx->W_F), l, cv(ctx->W_G), l, -1.0,
-                          1.0, ctx->d_gemm_work, st);
+                          1.0, ctx->d_gemm_work, st, ctx->gemm_work_elems * sizeof(double2));
             // e = K R (tau enters the extrapolation; d does not depend on a common
             // scale of e); the band norms |R_n|^2 stay in d_colout[0, nb) for rnorm2
             column_sums<T>(1, npw, nb, ccv(ctx->W_G), l, nullptr, 0, static_cast<const T*>(ctx->d_g2half),
@@ -851,6 +888,7 @@ struct Impl {
         r = orth(ctx, ctx->W_Y, l, psi, ld, ctx->nproj > 0 ? ctx->d_B : nullptr);
         if (r != ROKS_OK) return r;
         ctx->b_psi = ctx->nproj > 0 ? psi : nullptr;
+        ctx->b_ld = ld;
         r = density(ctx, psi, ld, ctx->nproj > 0 ? ctx->d_B : nullptr);
         if (r != ROKS_OK) return r;
         r = potential(ctx);
@@ -863,12 +901,18 @@ struct Impl {
         if (sflag) CK(cudaMemcpyAsync(ctx->h_flag + 1, sflag, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         ctx->cache_psi = psi;
+        ctx->cache_ld = ld;
         ctx->pot_valid = true;
-        if (tc_timeout_take())
-            return fail(ctx, ROKS_ETIMEOUT, "a tensor-core completion wait ran out (bounded mbarrier wait)");
-        if (ctx->h_flag[1]) {
-            stream_timeout_take();
-            return fail(ctx, ROKS_ETIMEOUT, "a bulk-copy wait of a streamed contraction ran out (bounded mbarrier wait)");
+        const bool tc_out = tcg_timeout_take() != 0;
+        const bool st_out = ctx->h_flag[1] != 0;
+        if (st_out) stream_timeout_take();
+        if (tc_out || st_out) {
+            CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), st));
+            CK(cudaStreamSynchronize(st));
+            ctx->pot_valid = false;
+            return fail(ctx, ROKS_ETIMEOUT, tc_out ? "a tensor-core completion wait ran out (bounded mbarrier wait)"
+                                                   : "a bulk-copy wait of a streamed contraction ran out "
+                                                     "(bounded mbarrier wait)");
         }
         const DiisState& h = *ctx->h_diis;
         if (*ctx->h_flag) {
@@ -909,7 +953,79 @@ void reset_history(roks_ctx* ctx) {
     ctx->diis_small = 0;
     ctx->pcg_fresh = false;
     ctx->yp_psi = nullptr;
+    ctx->steps = 0;
     cudaStreamSynchronize(ctx->st);
+}
+
+// The context's wait cap and tensor-core split depth for the launches of
+// one entry point.
+void enter(roks_ctx* ctx) {
+    set_wait_cap(ctx->wait_cap);
+    tcg_set_waves(ctx->tc_waves_x2);
+}
+
+// Times fn(candidate) (three launches after one warm-up, CUDA events on the
+// context's stream) and returns the fastest candidate; ms[i] gets the times.
+template <typename F>
+int pick_fastest(roks_ctx* ctx, const int* cand, int nc, double* ms, F fn) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    int best = cand[0];
+    double best_ms = 1e300;
+    for (int i = 0; i < nc; ++i) {
+        fn(cand[i]);
+        cudaEventRecord(a, ctx->st);
+        for (int r = 0; r < 3; ++r) fn(cand[i]);
+        cudaEventRecord(b, ctx->st);
+        cudaEventSynchronize(b);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, a, b);
+        ms[i] = t / 3.0;
+        if (ms[i] < best_ms) {
+            best_ms = ms[i];
+            best = cand[i];
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return best;
+}
+
+// Autotuner (roks_options.autotune): the band grouping of the density's x
+// stage (grid depth against the fixed-order reduction of the group slots)
+// and, on the mixed path, the split depth of the tensor-core A^H B products,
+// each timed on the context's own buffers and sizes.
+roks_status autotune(roks_ctx* ctx) {
+    enter(ctx);
+    const Sphere s = sphere(ctx);
+    const int g_cand[3] = {2, 4, 8};
+    if (ctx->prec == ROKS_FP64)
+        ctx->dens_groups = pick_fastest(ctx, g_cand, 3, ctx->tune_ms, [&](int g) {
+            band_x_density<double>(s, static_cast<const double2*>(ctx->d_tw), static_cast<double2*>(ctx->d_Yp),
+                                   ctx->d_rho3, ctx->d_rho_slot, g, 0, ctx->nb, ctx->nc, 1.0 / ctx->omega, ctx->st);
+        });
+    else
+        ctx->dens_groups = pick_fastest(ctx, g_cand, 3, ctx->tune_ms, [&](int g) {
+            band_x_density<float>(s, static_cast<const float2*>(ctx->d_tw), static_cast<float2*>(ctx->d_Yp),
+                                  ctx->d_rho3, ctx->d_rho_slot, g, 0, ctx->nb, ctx->nc, 1.0 / ctx->omega, ctx->st);
+        });
+    // the largest A^H B product of a step that runs on the tensor cores
+    const int M = ctx->nproj >= ctx->nb ? ctx->nproj : ctx->nb;
+    const void* A = ctx->nproj >= ctx->nb ? ctx->d_P : ctx->W_Y;
+    if (ctx->prec == ROKS_MIXED && tcg_cn_takes(M, ctx->nb, ctx->npw)) {
+        const int w_cand[3] = {3, 5, 8};
+        ctx->tc_waves_x2 = pick_fastest(ctx, w_cand, 3, ctx->tune_ms + 3, [&](int w) {
+            tcg_set_waves(w);
+            gemm_cn<float>(M, ctx->nb, ctx->npw, static_cast<const float2*>(A), ctx->ld_min,
+                           static_cast<const float2*>(ctx->W_Y), ctx->ld_min, ctx->d_B2, M, ctx->d_gemm_work,
+                           ctx->gemm_work_elems, ctx->st);
+        });
+        tcg_set_waves(ctx->tc_waves_x2);
+    }
+    const cudaError_t e = cudaStreamSynchronize(ctx->st);
+    if (e != cudaSuccess) return fail(ctx, ROKS_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+    return ROKS_OK;
 }
 
 }  // namespace
@@ -927,8 +1043,13 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
         return ROKS_EINVAL;
     if (!(cell->L > 0) || !(ecut > 0) || !grid_supported(cell->grid)) return ROKS_EINVAL;
     if (occ->n_closed < 0 || occ->mode < 0 || occ->mode > 2) return ROKS_EINVAL;
+    if (occ->n_open != (occ->mode == ROKS_MODE_GS ? 0 : 2)) return ROKS_EINVAL;
     if (opt->precision != ROKS_FP64 && opt->precision != ROKS_MIXED) return ROKS_EINVAL;
     if (!(opt->alpha >= 0.0 && opt->alpha <= 1.0)) return ROKS_EINVAL;
+    if (!(opt->e_tol >= 0.0) || !(opt->g_tol >= 0.0) || opt->max_iter < 0) return ROKS_EINVAL;
+    if (opt->precond != ROKS_PRECOND_TPA && opt->precond != ROKS_PRECOND_TPA_MLP) return ROKS_EINVAL;
+    if (opt->exx_kernel != ROKS_EXX_TRUNCATED && opt->exx_kernel != ROKS_EXX_BARE) return ROKS_EINVAL;
+    if (opt->autotune != 0 && opt->autotune != 1) return ROKS_EINVAL;
     roks_ctx* ctx = new (std::nothrow) roks_ctx();
     if (!ctx) return ROKS_ENOMEM;
     ctx->st = static_cast<cudaStream_t>(cuda_stream);
@@ -944,6 +1065,13 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     ctx->ecut = ecut;
     ctx->alpha = opt->alpha;
     ctx->e_tol = opt->e_tol > 0 ? opt->e_tol : 1e-6;
+    ctx->g_tol = opt->g_tol;
+    ctx->max_iter = opt->max_iter;
+    ctx->seed = opt->seed;
+    ctx->wait_cap = opt->wait_cap;
+    ctx->exx_kernel = opt->exx_kernel;
+    ctx->autotune = opt->autotune;
+    ctx->mlp_kind = opt->precond;   // all-zero network weights until trained ones are set
     ctx->suppress_ab = opt->suppress_ab;
     ctx->mode = occ->mode;
     ctx->nc = occ->n_closed;
@@ -1081,7 +1209,7 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     AL(ctx->d_Zc, cs * (size_t)nb * ctx->ncol * N);
     AL(ctx->d_Yp, cs * (size_t)nb * ctx->np * N * N);
     AL(ctx->d_rho3, sizeof(double) * 3 * N3);
-    AL(ctx->d_rho_slot, sizeof(double) * kDensityGroups * N3);
+    AL(ctx->d_rho_slot, sizeof(double) * (opt->autotune ? kDensityGroupsMax : kDensityGroups) * N3);
     AL(ctx->d_xc3, sizeof(double) * 3 * N3);
     AL(ctx->d_grid, sizeof(double2) * N3);
     AL(ctx->d_Vk, rs * 3 * N3);
@@ -1100,7 +1228,17 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     AL(ctx->d_QB, sizeof(double2) * np_ * nb);
     AL(ctx->d_B2, sizeof(double2) * np_ * nb);
     size_t gw = gemm_cn_work(np_ > nb ? np_ : nb, nb, npw);
+    if (!f64) {
+        // partial sums of the tensor-core contractions and the split B blocks
+        // of their tall products share the buffer
+        // (sized for the deepest split the autotuner may choose)
+        tcg_set_waves(opt->autotune ? 8 : ctx->tc_waves_x2);
+        const size_t tb = std::max(std::max(tcg_cn_work_bytes(np_, nb, npw), tcg_cn_work_bytes(nb, nb, npw)),
+                                   std::max(tcg_nn_work_bytes(nb, np_), tcg_nn_work_bytes(nb, nb)));
+        gw = std::max(gw, (tb + sizeof(double2) - 1) / sizeof(double2));
+    }
     ctx->gemm_work_elems = gw;
+    tcg_set_waves(ctx->tc_waves_x2);
     AL(ctx->d_gemm_work, sizeof(double2) * gw);
     AL(ctx->d_kin_b, sizeof(double) * nb);
     AL(ctx->d_nl_b, sizeof(double) * nb);
@@ -1222,14 +1360,28 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     else projectors_setup<float>(npw, ctx->nproj, cell->L, ctx->d_miller, d_proj, static_cast<float2*>(ctx->d_P), l,
                                  ctx->st);
     if (opt->alpha != 0.0) {
-        if (f64) exx_setup_kernel<double>(N, cell->L, static_cast<double*>(ctx->d_vG), ctx->st);
-        else exx_setup_kernel<float>(N, cell->L, static_cast<float*>(ctx->d_vG), ctx->st);
+        const int bare = opt->exx_kernel == ROKS_EXX_BARE ? 1 : 0;
+        if (f64) exx_setup_kernel<double>(N, cell->L, bare, static_cast<double*>(ctx->d_vG), ctx->st);
+        else exx_setup_kernel<float>(N, cell->L, bare, static_cast<float*>(ctx->d_vG), ctx->st);
     }
     e = cudaStreamSynchronize(ctx->st);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return bail(ROKS_ECUDA, cudaGetErrorString(e));
     reset_history(ctx);
+    if (opt->autotune) {
+        const roks_status r = autotune(ctx);
+        if (r != ROKS_OK) return bail(r, ctx->err);
+        reset_history(ctx);
+    }
     *out = ctx;
+    return ROKS_OK;
+}
+
+roks_status roks_tuning_get(const roks_ctx* ctx, roks_tuning* t) {
+    if (!ctx || !t) return ROKS_EINVAL;
+    t->density_groups = ctx->dens_groups;
+    t->tc_split_waves_x2 = ctx->tc_waves_x2;
+    for (int i = 0; i < 6; ++i) t->candidate_ms[i] = ctx->tune_ms[i];
     return ROKS_OK;
 }
 
@@ -1250,32 +1402,51 @@ static roks_status check_psi(roks_ctx* ctx, const void* psi, int64_t ld) {
 
 roks_status roks_init_orbitals(roks_ctx* ctx, const double* u_host, void* psi, int64_t ld) {
     if (!ctx) return ROKS_EINVAL;
-    if (!u_host) return fail(ctx, ROKS_EINVAL, "null random numbers");
     roks_status r = check_psi(ctx, psi, ld);
     if (r != ROKS_OK) return r;
-    double* d_u = nullptr;
-    const size_t bytes = sizeof(double) * 2 * (size_t)ctx->npw * ctx->nb;
-    CK(cudaMalloc(&d_u, bytes));
-    cudaMemcpyAsync(d_u, u_host, bytes, cudaMemcpyHostToDevice, ctx->st);
+    enter(ctx);
     const int64_t l = ctx->ld_min;
-    if (ctx->prec == ROKS_FP64) {
-        init_orbitals<double>(ctx->npw, ctx->nb, d_u, ctx->d_g2, static_cast<double2*>(ctx->W_Y), l, ctx->st);
-        r = Impl<double>::orth(ctx, ctx->W_Y, l, psi, ld, nullptr);
-    } else {
-        init_orbitals<float>(ctx->npw, ctx->nb, d_u, ctx->d_g2, static_cast<float2*>(ctx->W_Y), l, ctx->st);
-        r = Impl<float>::orth(ctx, ctx->W_Y, l, psi, ld, nullptr);
+    const bool f64 = ctx->prec == ROKS_FP64;
+    // host numbers are staged, a few bands at a time, in a band block the
+    // orthonormalisation below does not use (no allocation)
+    const size_t stage_doubles = (f64 ? sizeof(double2) : sizeof(float2)) * (size_t)l * ctx->nb / sizeof(double);
+    const int per = u_host ? (int)(stage_doubles / (2 * (size_t)ctx->npw)) : ctx->nb;
+    if (per < 1) return fail(ctx, ROKS_EINVAL, "staging block too small");
+    double* stage = static_cast<double*>(ctx->W_u);
+    for (int b0 = 0; b0 < ctx->nb; b0 += per) {
+        const int nbk = std::min(per, ctx->nb - b0);
+        const double* u = nullptr;
+        if (u_host) {
+            CK(cudaMemcpyAsync(stage, u_host + 2 * (size_t)ctx->npw * b0, sizeof(double) * 2 * (size_t)ctx->npw * nbk,
+                               cudaMemcpyHostToDevice, ctx->st));
+            u = stage;
+        }
+        if (f64)
+            init_orbitals<double>(ctx->npw, b0, nbk, u, ctx->seed, ctx->d_g2, static_cast<double2*>(ctx->W_Y), l,
+                                  ctx->st);
+        else
+            init_orbitals<float>(ctx->npw, b0, nbk, u, ctx->seed, ctx->d_g2, static_cast<float2*>(ctx->W_Y), l,
+                                 ctx->st);
     }
+    CK(cudaGetLastError());
+    r = f64 ? Impl<double>::orth(ctx, ctx->W_Y, l, psi, ld, nullptr) : Impl<float>::orth(ctx, ctx->W_Y, l, psi, ld, nullptr);
     cudaStreamSynchronize(ctx->st);
-    cudaFree(d_u);
     if (r != ROKS_OK) return r;
     reset_history(ctx);
     return ctx->prec == ROKS_FP64 ? Impl<double>::check_flag(ctx) : Impl<float>::check_flag(ctx);
+}
+
+roks_status roks_invalidate(roks_ctx* ctx) {
+    if (!ctx) return ROKS_EINVAL;
+    reset_history(ctx);
+    return ROKS_OK;
 }
 
 roks_status roks_density(roks_ctx* ctx, const void* psi, int64_t ld, double* rho_out) {
     if (!ctx) return ROKS_EINVAL;
     roks_status r = check_psi(ctx, psi, ld);
     if (r != ROKS_OK) return r;
+    enter(ctx);
     ctx->pot_valid = false;
     r = ctx->prec == ROKS_FP64 ? Impl<double>::density(ctx, psi, ld, nullptr)
                                : Impl<float>::density(ctx, psi, ld, nullptr);
@@ -1321,6 +1492,7 @@ roks_status roks_apply_h(roks_ctx* ctx, const void* psi, int64_t ld, void* fpsi,
     if (!ctx) return ROKS_EINVAL;
     roks_status r = check_psi(ctx, psi, ld);
     if (r != ROKS_OK) return r;
+    enter(ctx);
     if (!fpsi) return fail(ctx, ROKS_EINVAL, "null output");
     const int64_t l = ctx->ld_min;
     const int nb = ctx->nb;
@@ -1343,10 +1515,12 @@ roks_status roks_apply_h(roks_ctx* ctx, const void* psi, int64_t ld, void* fpsi,
     CK(cudaMemcpy2DAsync(grad, ld * es, fpsi, ld * es, ctx->npw * es, nb, cudaMemcpyDeviceToDevice, ctx->st));
     if (ctx->prec == ROKS_FP64)
         gemm_nn<double>(ctx->npw, nb, nb, static_cast<const double2*>(S), lds, ctx->d_Gam, nb,
-                        static_cast<double2*>(grad), ld, -1.0, 1.0, ctx->d_gemm_work, ctx->st);
+                        static_cast<double2*>(grad), ld, -1.0, 1.0, ctx->d_gemm_work, ctx->st,
+                        ctx->gemm_work_elems * sizeof(double2));
     else
         gemm_nn<float>(ctx->npw, nb, nb, static_cast<const float2*>(S), lds, ctx->d_Gam, nb,
-                       static_cast<float2*>(grad), ld, -1.0, 1.0, ctx->d_gemm_work, ctx->st);
+                       static_cast<float2*>(grad), ld, -1.0, 1.0, ctx->d_gemm_work, ctx->st,
+                       ctx->gemm_work_elems * sizeof(double2));
     CK(cudaGetLastError());
     return ROKS_OK;
 }
@@ -1355,6 +1529,7 @@ roks_status roks_orthonormalize(roks_ctx* ctx, void* psi, int64_t ld) {
     if (!ctx) return ROKS_EINVAL;
     roks_status r = check_psi(ctx, psi, ld);
     if (r != ROKS_OK) return r;
+    enter(ctx);
     const int64_t l = ctx->ld_min;
     const size_t es = ctx->prec == ROKS_FP64 ? sizeof(double2) : sizeof(float2);
     CK(cudaMemcpy2DAsync(ctx->W_Y, l * es, psi, ld * es, ctx->npw * es, ctx->nb, cudaMemcpyDeviceToDevice, ctx->st));
@@ -1369,17 +1544,23 @@ roks_status roks_pcg_step(roks_ctx* ctx, void* psi, int64_t ld, roks_step_info* 
     if (!ctx) return ROKS_EINVAL;
     roks_status r = check_psi(ctx, psi, ld);
     if (r != ROKS_OK) return r;
+    enter(ctx);
     // after DIIS steps the direction history belongs to other orbitals
     if (ctx->pcg_fresh) reset_history(ctx);
     ctx->diis_count = 0;
     roks_step_info tmp;
     std::memset(&tmp, 0, sizeof(tmp));
     r = ctx->prec == ROKS_FP64 ? Impl<double>::pcg_step(ctx, psi, ld, &tmp) : Impl<float>::pcg_step(ctx, psi, ld, &tmp);
-    if (r != ROKS_OK && r != ROKS_EDIVERGED) return r;
-    // convergence: |E_new - E| < e_tol on two consecutive steps
+    if (r != ROKS_OK) {
+        if (info) *info = tmp;
+        return r;
+    }
+    ctx->steps += 1;
+    // convergence: |E_new - E| < e_tol on two consecutive steps, and the
+    // gradient norm below g_tol when one is set
     if (std::fabs(tmp.E_new - tmp.E) < ctx->e_tol) ctx->n_small += 1;
     else ctx->n_small = 0;
-    tmp.converged = ctx->n_small >= 2 ? 1 : 0;
+    tmp.converged = (ctx->n_small >= 2 && (ctx->g_tol <= 0 || tmp.grad_norm < ctx->g_tol)) ? 1 : 0;
     if (tmp.converged && ctx->mlp_kind == ROKS_PRECOND_TPA_MLP && !ctx->mlp_judging) {
         // TPA judges the convergence of the corrected run: switch the
         // correction off for good (a device flag the captured step reads) and
@@ -1394,7 +1575,9 @@ roks_status roks_pcg_step(roks_ctx* ctx, void* psi, int64_t ld, roks_step_info* 
         tmp.converged = 0;
     }
     if (info) *info = tmp;
-    return r;
+    if (!tmp.converged && ctx->max_iter > 0 && ctx->steps >= ctx->max_iter)
+        return fail(ctx, ROKS_ENOCONV, "no convergence within max_iter steps");
+    return ROKS_OK;
 }
 
 roks_status roks_diis_step(roks_ctx* ctx, void* psi, int64_t ld, const roks_diis_options* opt,
@@ -1402,6 +1585,7 @@ roks_status roks_diis_step(roks_ctx* ctx, void* psi, int64_t ld, const roks_diis
     if (!ctx) return ROKS_EINVAL;
     roks_status r = check_psi(ctx, psi, ld);
     if (r != ROKS_OK) return r;
+    enter(ctx);
     roks_diis_options o;
     if (opt) {
         o = *opt;
@@ -1451,18 +1635,25 @@ roks_status roks_diis_step(roks_ctx* ctx, void* psi, int64_t ld, const roks_diis
     r = ctx->prec == ROKS_FP64 ? Impl<double>::diis_step(ctx, psi, ld, o, &tmp)
                                : Impl<float>::diis_step(ctx, psi, ld, o, &tmp);
     ctx->pcg_fresh = true;
-    if (r != ROKS_OK && r != ROKS_EDIVERGED) return r;
+    if (r != ROKS_OK) {
+        if (info) *info = tmp;
+        return r;
+    }
+    ctx->steps += 1;
     if (std::fabs(tmp.E_new - tmp.E) < ctx->e_tol) ctx->diis_small += 1;
     else ctx->diis_small = 0;
-    tmp.converged = ctx->diis_small >= 2 ? 1 : 0;
+    tmp.converged = (ctx->diis_small >= 2 && (ctx->g_tol <= 0 || tmp.res_norm < ctx->g_tol)) ? 1 : 0;
     if (info) *info = tmp;
-    return r;
+    if (!tmp.converged && ctx->max_iter > 0 && ctx->steps >= ctx->max_iter)
+        return fail(ctx, ROKS_ENOCONV, "no convergence within max_iter steps");
+    return ROKS_OK;
 }
 
 roks_status roks_forces(roks_ctx* ctx, const void* psi, int64_t ld, double* forces_host) {
     if (!ctx) return ROKS_EINVAL;
     roks_status r = check_psi(ctx, psi, ld);
     if (r != ROKS_OK) return r;
+    enter(ctx);
     if (!forces_host) return fail(ctx, ROKS_EINVAL, "null force array");
     if (ctx->natoms == 0) return ROKS_OK;
     const bool f64 = ctx->prec == ROKS_FP64;
@@ -1547,6 +1738,14 @@ roks_status roks_profile_read(roks_ctx* ctx, roks_profile_entry* out, int cap, i
         std::memset(out[n].name, 0, sizeof(out[n].name));
         std::strncpy(out[n].name, "kernel_launches", sizeof(out[n].name) - 1);
         out[n].launches = (int)kernels;
+        out[n].ms = 0.0;
+    }
+    ++n;
+    const long long tensor = tcg_launches_take();
+    if (n < cap) {
+        std::memset(out[n].name, 0, sizeof(out[n].name));
+        std::strncpy(out[n].name, "tensor_core_launches", sizeof(out[n].name) - 1);
+        out[n].launches = (int)tensor;
         out[n].ms = 0.0;
     }
     ++n;

@@ -38,7 +38,7 @@ struct ExxArgs {
 };
 
 template <typename T>
-void exx_setup_kernel(int N, double L, T* vG, cudaStream_t st);
+void exx_setup_kernel(int N, double L, int bare, T* vG, cudaStream_t st);
 // K for all pairs, the energies and the open-band diagonal; the exchange
 // fields X too when want_field.
 template <typename T>

@@ -30,8 +30,11 @@ void vloc_setup(int N, double L, int natoms, const double* atoms_dev, double2* g
 template <typename T>
 void projectors_setup(int npw, int nproj, double L, const int* miller_dev, const double* proj_dev, c2<T>* P,
                       int64_t ldp, cudaStream_t st);
+// Bands band0 .. band0 + nbands - 1 of the seeded start from uniforms u_dev
+// (numbered from band0) or, when u_dev is null, from SplitMix64(seed).
 template <typename T>
-void init_orbitals(int npw, int nb, const double* u_dev, const double* g2, c2<T>* psi, int64_t ld, cudaStream_t st);
+void init_orbitals(int npw, int band0, int nbands, const double* u_dev, uint64_t seed, const double* g2, c2<T>* psi,
+                   int64_t ld, cudaStream_t st);
 template <typename T>
 void to_real_type(int64_t n, const double* in, T* out, double scale, cudaStream_t st);
 // op 0: kinetic 0.5 g2 |x|^2; 1: (|x|^2, g2 |x|^2) -> out[0..nb), out[nb..2nb), and the TPA
@@ -98,7 +101,7 @@ void pcg_rotation(int nb, int n_closed, const double2* Theta, const double* kin_
                   const double* open_vc, const double* open_x, double wc, const int* shell, int suppress_ab, int ia,
                   int ib, double2* Gam, double2* Gin, double2* A, PcgScalars* sc, cudaStream_t st);
 // sc->rot_pg = 1/2 Re sum conj(A) Gin; sc->r1, r2 as named.
-void pcg_rot_dots(int nb, const double2* A, const double2* Aprev, const double2* Gin, PcgScalars* sc,
+void pcg_rot_dots(int nb, const double2* A, const double2* Aprev, const double2* Gin, double* part, PcgScalars* sc,
                   cudaStream_t st);
 // Decide beta / restart / rotation, set dE0 and the trial step.
 void pcg_direction(PcgScalars* sc, cudaStream_t st);

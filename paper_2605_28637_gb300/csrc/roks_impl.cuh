@@ -107,6 +107,7 @@ template <> struct DensAcc<float> {
 // holds ngroups x N^3 values.  rho3 classes a, b must be zero on entry (class
 // 0 is overwritten).
 constexpr int kDensityGroups = 4;
+constexpr int kDensityGroupsMax = 8;   // the autotuner's largest candidate
 template <typename T>
 void band_x_density(const Sphere& s, const c2<T>* tw, const c2<T>* Yp, double* rho3, double* slot, int ngroups,
                     int b0, int nbb, int n_closed, double scale, cudaStream_t st);
@@ -121,22 +122,14 @@ void grid_fft3_batched(int N, const c2<T>* tw, c2<T>* data, int batch, int64_t b
 // ------------------------------------------------------------ dense complex contractions
 // Cpart[chunk] (element type T, M x N column major) = sum over the k of the
 // chunk of conj(A[k, m]) B[k, n]; then C = sum_chunks Cpart (double2, ldc)
-// in a fixed order.  work holds work_elems double2.  FP32
-// inputs go to the tensor cores when allow_tc; the tensor-core accumulation
-// rounds towards zero, so results that must not carry that bias (the
-// overlap matrix of the orthonormalisation) pass allow_tc = false.
+// in a fixed order.  work holds work_elems double2.  Large FP32 blocks go to
+// the tensor cores (gemm_cn_tcg), the others to the streamed SIMT kernel.
 template <typename T>
 void gemm_cn(int M, int N, int K, const c2<T>* A, int64_t lda, const c2<T>* B, int64_t ldb,
-             double2* C, int ldc, double2* work, size_t work_elems, cudaStream_t st, bool allow_tc = true);
+             double2* C, int ldc, double2* work, size_t work_elems, cudaStream_t st);
 size_t gemm_cn_work(int M, int N, int K);
 // C (ldc) = fixed-order sum of nchunk partials (M x N double2 each)
 void chunk_sum(int M, int N, int nchunk, const double2* part, double2* C, int ldc, cudaStream_t st);
-// tcgen05 path of the FP32 contraction (N <= 128); false when not taken.
-bool gemm_cn_tc(int M, int N, int K, const float2* A, int64_t lda, const float2* B, int64_t ldb, double2* C, int ldc,
-                double2* work, int max_chunks, cudaStream_t st);
-bool tc_enabled();
-// 1 if a tensor-core mbarrier wait gave up since the last call (then cleared)
-int tc_timeout_take();
 // FP32 partials (nchunk x M x N float2) summed like chunk_sum, with compensation.
 void chunk_sum_f32(int M, int N, int nchunk, const float2* part, double2* C, int ldc, cudaStream_t st);
 // Streamed FP32 contractions (bulk copies into a shared-memory ring, one CTA
@@ -152,6 +145,10 @@ bool gemm_nn_stream(int M, int N, int K, const float2* A, int64_t lda, const dou
 // 1 if a streamed-contraction wait gave up since the last call (then cleared);
 // the flag's device address, for asynchronous reads.
 int stream_timeout_take();
+// Polls of every bounded work-loop wait in the contraction kernels launched
+// from now on: 0 the default (2^26), < 0 none (every such wait gives up).
+void set_wait_cap(int cap);
+uint32_t wait_polls();
 int* stream_timeout_flag();
 // Same, with at most max_chunks K chunks (work holds max_chunks * M * N).
 template <typename T>
@@ -160,15 +157,40 @@ void gemm_cn_capped(int M, int N, int K, const c2<T>* A, int64_t lda, const c2<T
 // C[m, n] = alpha sum_k A[m, k] B[k, n] + beta C[m, n]; B is FP64 (small).
 // For T = float, bwork receives an FP32 copy of B (K x N float2); it may be
 // the partial-sum buffer of gemm_cn (not in use across calls).
+// bwork_bytes: size of bwork; the tensor-core path (FP32, large blocks)
+// needs tcg_nn_work_bytes(N, K) and is skipped when it is 0 or too small.
 template <typename T>
 void gemm_nn(int M, int N, int K, const c2<T>* A, int64_t lda, const double2* B, int ldb,
-             c2<T>* C, int64_t ldc, double alpha, double beta, void* bwork, cudaStream_t st);
+             c2<T>* C, int64_t ldc, double alpha, double beta, void* bwork, cudaStream_t st,
+             size_t bwork_bytes = 0);
 
 // Cout (ldc) = alpha A B + beta Cin (ldcin); Cin may differ from Cout (when
 // beta != 0 and it does, Cin is not modified).
 template <typename T>
 void gemm_nn_io(int M, int N, int K, const c2<T>* A, int64_t lda, const double2* B, int ldb, const c2<T>* Cin,
-                int64_t ldcin, c2<T>* Cout, int64_t ldc, double alpha, double beta, void* bwork, cudaStream_t st);
+                int64_t ldcin, c2<T>* Cout, int64_t ldc, double alpha, double beta, void* bwork, cudaStream_t st,
+                size_t bwork_bytes = 0);
+
+// ------------------------------------------------------------ tensor-core contractions (k_tcgemm.cu)
+// Complex FP32 contractions of large blocks on tcgen05 (three TF32 products
+// per FP32 product, every K-step drained into round-to-nearest FP32 sums).
+bool tcg_enabled();
+bool tcg_cn_takes(int M, int N, int K);
+bool tcg_nn_takes(int M, int N, int K);
+// K-split depth of the A^H B products: about waves_x2 / 2 waves of CTAs
+// (the work buffer is sized for the deepest candidate, 4 waves)
+void tcg_set_waves(int waves_x2);
+size_t tcg_cn_work_bytes(int M, int N, int K);
+size_t tcg_nn_work_bytes(int N, int K);
+bool gemm_cn_tcg(int M, int N, int K, const float2* A, int64_t lda, const float2* B, int64_t ldb, double2* C, int ldc,
+                 void* work, size_t work_bytes, cudaStream_t st);
+bool gemm_nn_tcg(int M, int N, int K, const float2* A, int64_t lda, const double2* B, int ldb, const float2* Cin,
+                 int64_t ldcin, float2* Cout, int64_t ldc, float alpha, float beta, void* bwork, size_t bwork_bytes,
+                 cudaStream_t st);
+// 1 if a tensor-core wait gave up since the last call (then cleared)
+int tcg_timeout_take();
+// tensor-core contraction launches since the last call
+long long tcg_launches_take();
 
 // ------------------------------------------------------------ small FP64 matrices (n x n, column major)
 void small_gemm(int M, int N, int K, const double2* A, int lda, bool ca, const double2* B, int ldb,

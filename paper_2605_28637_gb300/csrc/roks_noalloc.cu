@@ -9,7 +9,6 @@
 // __device__ array of fixed size, reserved when the library is loaded; every
 // GPU that loads the library holds it until the process exits.
 #include <cstddef>
-#include <mutex>
 
 #include "../../include/roks.h"
 #include "roks_impl.cuh"
@@ -27,25 +26,16 @@ constexpr size_t kNaBytes = sizeof(double2) * (kNaPart + 3 * kNaMat) + 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
-// Device address of the scratch array, resolved once per device (the host
-// name g_noalloc_scratch is only a stand-in and must never reach a kernel).
-constexpr int kMaxDevices = 64;
-unsigned char* g_scratch_addr[kMaxDevices] = {nullptr};
-std::mutex g_scratch_mu;
-
+// Device address of the scratch array on the current device (the host name
+// g_noalloc_scratch is only a stand-in and must never reach a kernel).  It
+// is resolved on every call: the lookup is cheap next to the synchronising
+// call, and a cached address would go stale if the module were reloaded
+// (after cudaDeviceReset, for instance).
 cudaError_t scratch_address(unsigned char** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = static_cast<unsigned char*>(p);
-    }
-    *out = g_scratch_addr[dev];
+    *out = static_cast<unsigned char*>(p);
     return cudaSuccess;
 }
 

@@ -17,6 +17,8 @@ import os
 
 import numpy as np
 
+from . import synthetic
+
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libroks_gb300.so")
 
@@ -46,11 +48,16 @@ class roks_species(C.Structure):
 
 
 class roks_occ(C.Structure):
-    _fields_ = [("n_closed", C.c_int), ("mode", C.c_int)]
+    _fields_ = [("n_closed", C.c_int), ("n_open", C.c_int), ("mode", C.c_int)]
 
 
 class roks_options(C.Structure):
-    _fields_ = [("precision", C.c_int), ("alpha", C.c_double), ("suppress_ab", C.c_int), ("e_tol", C.c_double)]
+    _fields_ = [("precision", C.c_int), ("alpha", C.c_double), ("suppress_ab", C.c_int), ("e_tol", C.c_double),
+                ("g_tol", C.c_double), ("max_iter", C.c_int), ("seed", C.c_uint64), ("precond", C.c_int),
+                ("autotune", C.c_int), ("exx_kernel", C.c_int), ("wait_cap", C.c_int)]
+
+
+ROKS_EXX_TRUNCATED, ROKS_EXX_BARE = 0, 1
 
 
 class roks_energies(C.Structure):
@@ -76,13 +83,17 @@ class roks_diis_info(C.Structure):
                 ("coef", C.c_double * ROKS_DIIS_MAX), ("converged", C.c_int)]
 
 
+class roks_tuning(C.Structure):
+    _fields_ = [("density_groups", C.c_int), ("tc_split_waves_x2", C.c_int), ("candidate_ms", C.c_double * 6)]
+
+
 class roks_profile_entry(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int), ("ms", C.c_double)]
 
 
-EXPORTS = ["roks_setup", "roks_basis", "roks_init_orbitals", "roks_density", "roks_potential", "roks_apply_h",
+EXPORTS = ["roks_setup", "roks_basis", "roks_init_orbitals", "roks_invalidate", "roks_density", "roks_potential", "roks_apply_h",
            "roks_orthonormalize", "roks_pcg_step", "roks_diis_step", "roks_forces", "roks_energies_get",
-           "roks_profile_enable", "roks_profile_read", "roks_orthonormalize_noalloc", "roks_mlp_forward",
+           "roks_profile_enable", "roks_profile_read", "roks_tuning_get", "roks_orthonormalize_noalloc", "roks_mlp_forward",
            "roks_mlp_grad", "roks_mlp_adam", "roks_set_preconditioner", "roks_precondition", "roks_mlp_grad_work",
            "roks_last_error", "roks_destroy"]
 
@@ -110,6 +121,7 @@ def load(path: str | None = None) -> C.CDLL:
     lib.roks_basis.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                C.POINTER(C.POINTER(C.c_int32))]
     lib.roks_init_orbitals.argtypes = [P, C.POINTER(C.c_double), P, C.c_int64]
+    lib.roks_invalidate.argtypes = [P]
     lib.roks_density.argtypes = [P, P, C.c_int64, P]
     lib.roks_potential.argtypes = [P, C.POINTER(roks_energies), P]
     lib.roks_apply_h.argtypes = [P, P, C.c_int64, P, P, P]
@@ -120,6 +132,7 @@ def load(path: str | None = None) -> C.CDLL:
     lib.roks_energies_get.argtypes = [P, C.POINTER(roks_energies)]
     lib.roks_profile_enable.argtypes = [P, C.c_int]
     lib.roks_profile_read.argtypes = [P, C.POINTER(roks_profile_entry), C.c_int, C.POINTER(C.c_int)]
+    lib.roks_tuning_get.argtypes = [P, C.POINTER(roks_tuning)]
     lib.roks_orthonormalize_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, P, C.c_int64, P]
     lib.roks_mlp_forward.argtypes = [C.c_int, P, P, C.c_int, P, P]
     lib.roks_mlp_grad.argtypes = [C.c_int, P, P, P, P, P, P, P, P]
@@ -150,7 +163,8 @@ def _ptr(t):
 
 # ---------------------------------------------------------------- C names
 def roks_setup(cfg: dict, precision: int = ROKS_FP64, stream=None, suppress_ab: bool = False,
-               e_tol: float = 1e-6):
+               e_tol: float = 1e-6, g_tol: float = 0.0, max_iter: int = 0, precond: int = 0, autotune: int = 0,
+               exx_kernel: int = ROKS_EXX_TRUNCATED, wait_cap: int = 0):
     """Marshal a workload description (see synthetic.make_config) and call roks_setup."""
     lib = load()
     cell = roks_cell(cfg["L"], cfg["grid"])
@@ -170,8 +184,9 @@ def roks_setup(cfg: dict, precision: int = ROKS_FP64, stream=None, suppress_ab: 
     at_arr = (roks_atom * max(1, len(atoms)))()
     for i, a in enumerate(atoms):
         at_arr[i] = roks_atom((C.c_double * 3)(*a["pos"]), a["species"], a["depth"], a["width"])
-    occ = roks_occ(cfg["n_closed"], cfg["mode"])
-    opt = roks_options(precision, cfg.get("alpha", 0.0), int(suppress_ab), e_tol)
+    occ = roks_occ(cfg["n_closed"], 0 if cfg["mode"] == 0 else 2, cfg["mode"])
+    opt = roks_options(precision, cfg.get("alpha", 0.0), int(suppress_ab), e_tol, g_tol, int(max_iter),
+                       synthetic.orbital_stream_seed(cfg), int(precond), int(autotune), int(exx_kernel), int(wait_cap))
     out = C.c_void_p()
     st = C.c_void_p(stream) if stream else None
     status = lib.roks_setup(C.byref(cell), cfg["ecut"], len(atoms), at_arr, len(cfg["species"]), sp_arr,
@@ -190,9 +205,18 @@ def roks_basis(ctx):
     return npw.value, nb.value, ld.value, miller
 
 
-def roks_init_orbitals(ctx, u: np.ndarray, psi, ld: int):
+def roks_init_orbitals(ctx, u, psi, ld: int):
+    """u: host uniforms (nbands, npw, 2), or None to draw them on the device
+    from the context's seed."""
+    if u is None:
+        _check(ctx, load().roks_init_orbitals(ctx, None, _ptr(psi), ld))
+        return
     u = np.ascontiguousarray(u, dtype=np.float64)
     _check(ctx, load().roks_init_orbitals(ctx, u.ctypes.data_as(C.POINTER(C.c_double)), _ptr(psi), ld))
+
+
+def roks_invalidate(ctx):
+    _check(ctx, load().roks_invalidate(ctx))
 
 
 def roks_density(ctx, psi, ld: int, rho_out=None):
@@ -254,6 +278,13 @@ def roks_profile_read(ctx, cap: int = 64) -> list:
             for i in range(min(n.value, cap))]
 
 
+def roks_tuning_get(ctx) -> dict:
+    t = roks_tuning()
+    _check(ctx, load().roks_tuning_get(ctx, C.byref(t)))
+    return {"density_groups": t.density_groups, "tc_split_waves_x2": t.tc_split_waves_x2,
+            "candidate_ms": [t.candidate_ms[i] for i in range(6)]}
+
+
 def roks_orthonormalize_noalloc(precision: int, npw: int, nbands: int, psi, ld: int, stream=None):
     """Allocation-free S = 1 orthonormalisation (see include/roks.h)."""
     st = C.c_void_p(stream) if stream else None
@@ -313,14 +344,14 @@ class Context:
     """Owns one roks_ctx on the current CUDA device and stream."""
 
     def __init__(self, cfg: dict, precision: str = "fp64", suppress_ab: bool = False, e_tol: float = 1e-6,
-                 stream=None):
+                 stream=None, **options):
         import torch
         self.torch = torch
         self.precision = ROKS_FP64 if precision == "fp64" else ROKS_MIXED
         self.cdtype = torch.complex128 if self.precision == ROKS_FP64 else torch.complex64
         self.rdtype = torch.float64 if self.precision == ROKS_FP64 else torch.float32
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        self.ctx = roks_setup(cfg, self.precision, self.stream.cuda_stream, suppress_ab, e_tol)
+        self.ctx = roks_setup(cfg, self.precision, self.stream.cuda_stream, suppress_ab, e_tol, **options)
         self.npw, self.nb, self.ld, self.miller = roks_basis(self.ctx)
         self.N = cfg["grid"]
         self.nproj = sum(len(cfg["species"][a["species"]]["l"]) for a in cfg["atoms"])
@@ -333,6 +364,9 @@ class Context:
         psi = self.new_bands() if psi is None else psi
         roks_init_orbitals(self.ctx, u, psi, self.ld)
         return psi
+
+    def invalidate(self):
+        roks_invalidate(self.ctx)
 
     def density(self, psi, want_rho=False):
         rho = (self.torch.empty((3, self.N ** 3), dtype=self.torch.float64, device="cuda")
@@ -367,6 +401,9 @@ class Context:
 
     def energies(self):
         return roks_energies_get(self.ctx)
+
+    def tuning(self):
+        return roks_tuning_get(self.ctx)
 
     def set_preconditioner(self, params=None):
         """TPA (params None) or TPA times the network (device float32 params)."""

@@ -18,6 +18,9 @@ Workloads (cubic cells, Gamma point, atomic units):
                Ecut 15 Ha, Mg 4 / O 8 projectors, 428 closed + 2 open bands
   hybrid-72    2x2x2 rocksalt (a=7.96), one O removed (63 atoms), 72^3,
                Ecut 15 Ha, exact-exchange fraction 1/3, 126 closed + 2 open
+  mgo-72       the hybrid-72 cell without exact exchange: a small system
+               with the block shapes of mgo-120 (128 bands, 376 projectors),
+               for profiling captures that must hold little device memory
 """
 from __future__ import annotations
 
@@ -149,7 +152,7 @@ def make_config(name: str, seed: int = 0) -> dict:
             else:
                 atoms.append({"pos": p, "species": 1, "depth": 1.0, "width": 1.0})
         n_closed, alpha = 40, 0.0
-    elif name in ("mgo-120", "hybrid-72"):
+    elif name in ("mgo-120", "hybrid-72", "mgo-72"):
         reps = 3 if name == "mgo-120" else 2
         L, mg, ox = _rocksalt(7.96, reps)
         N = 120 if reps == 3 else 72
@@ -158,7 +161,7 @@ def make_config(name: str, seed: int = 0) -> dict:
         atoms = [{"pos": tuple(map(float, r)), "species": 0, "depth": 1.0, "width": 1.0} for r in mg]
         atoms += [{"pos": tuple(map(float, r)), "species": 1, "depth": 3.0, "width": 1.0} for r in ox]
         n_closed = 428 if reps == 3 else 126
-        alpha = 0.0 if reps == 3 else 1.0 / 3.0
+        alpha = 1.0 / 3.0 if name == "hybrid-72" else 0.0
     else:
         raise ValueError(f"unknown workload {name!r}")
     return {
@@ -179,14 +182,20 @@ def n_bands(cfg: dict) -> int:
     return cfg["n_closed"] + (0 if cfg["mode"] == 0 else 2)
 
 
-def orbital_uniforms(cfg: dict, npw: int) -> np.ndarray:
+def orbital_stream_seed(cfg: dict) -> int:
+    """SplitMix64 seed of the stream the initial orbitals are drawn from."""
+    return (cfg["seed"] * 0x9E3779B1 + 0x0B17) & MASK64
+
+
+def orbital_uniforms(cfg: dict, npw: int, band0: int = 0, nbands: int | None = None) -> np.ndarray:
     """Uniform(-1,1) draws for the initial orbitals: shape (nbands, npw, 2).
 
     Band by band, coefficient by coefficient in basis order, real then
-    imaginary part.
+    imaginary part (number 2 (n npw + g) + part of the stream).  band0 and
+    nbands select a range of bands (default: all).
     """
-    nb = n_bands(cfg)
-    u = uniform(cfg["seed"] * 0x9E3779B1 + 0x0B17, 0, nb * npw * 2, -1.0, 1.0)
+    nb = n_bands(cfg) - band0 if nbands is None else nbands
+    u = uniform(orbital_stream_seed(cfg), 2 * band0 * npw, nb * npw * 2, -1.0, 1.0)
     return u.reshape(nb, npw, 2)
 
 

@@ -42,4 +42,10 @@ def test_degenerate_systems_fp64(name):
     assert abs(dinfo["E_new"] - dref.E_new) <= 1e-9 * max(1.0, abs(dref.E_new))
     F = ctx.forces(psi)
     assert F.shape == (len(cfg["atoms"]), 3) and np.all(np.isfinite(F))
+    # the forces of the DIIS result against the force oracle on the same orbitals
+    from oracle import forces as Fo
+    Fref = Fo.forces(s, to_np(psi, s.npw))
+    assert Fref.shape == F.shape
+    if F.size:
+        assert np.abs(F - Fref).max() <= 1e-9 * max(np.abs(Fref).max(), 1e-12), (F, Fref)
     ctx.close()

@@ -98,3 +98,38 @@ def test_organic96_diis(pair):
     check_orthonormal(s, P)
     E_ref, scale = oracle_energy(s, P)
     assert abs(info["E_new"] - E_ref) < 2e-7 * scale, (info["E_new"], E_ref, scale)
+
+
+def test_ground_state_mixed_matches_fp64_at_convergence():
+    """State-level bar of the mixed path: the organic-96 closed-shell ground
+    state (41 bands; one minimum) converged on the mixed path and on the FP64
+    path from the same seeded start, each to |dE| < 1e-6 Ha twice and
+    |g| < 2e-4 (reading R7).  The mixed path's final orbitals, re-evaluated
+    on the FP64 path, carry the FP64 leg's energy to 1e-5 Ha, and the mixed
+    path's own energy of them is within 1e-5 Ha too."""
+    import torch
+    roks = built()
+    cfg = syn.with_changes(syn.make_config("organic-96", 0), mode=0, n_closed=41)
+    out = {}
+    for prec in ("fp64", "mixed"):
+        ctx = roks.Context(cfg, prec, e_tol=1e-6, g_tol=2e-4)
+        psi = ctx.init_orbitals(syn.orbital_uniforms(cfg, ctx.npw))
+        info = None
+        for _ in range(3000):
+            info = ctx.pcg_step(psi)
+            if info["converged"]:
+                break
+        assert info["converged"], (prec, info)
+        out[prec] = (info["E_new"], psi, ctx)
+    E64, _, c64 = out["fp64"]
+    Emx, pmx, cmx = out["mixed"]
+    p64 = c64.new_bands()
+    p64[:, :c64.npw] = pmx[:, :c64.npw].to(p64.dtype)
+    torch.cuda.synchronize()
+    c64.orthonormalize(p64)
+    c64.density(p64)
+    E_eval = c64.potential()["E_total"]
+    assert abs(E_eval - E64) < 1e-5, (E_eval, E64)
+    assert abs(Emx - E64) < 1e-5, (Emx, E64)
+    c64.close()
+    cmx.close()

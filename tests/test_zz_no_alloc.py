@@ -1,5 +1,6 @@
 """The allocation-free orthonormalisation (roks_orthonormalize_noalloc) agrees
-with roks_orthonormalize on a context without projectors (S = 1).
+with roks_orthonormalize on a context without projectors (S = 1), and with
+the oracle's Cholesky orthonormalisation of the same block.
 
 It serves callers that cannot call cudaMalloc (for example code inside a
 framework that has reserved the GPU's memory for its own allocator); its
@@ -8,6 +9,7 @@ that pytest collects it last."""
 import numpy as np
 import pytest
 
+from oracle import roks as oracle_roks
 from paper_2605_28637_gb300 import synthetic as syn
 from tests.gpu_helpers import built, rel, to_dev, to_np
 
@@ -26,6 +28,7 @@ def test_noalloc_matches_orthonormalize(precision, tol):
     roks = built()
     cfg = no_projector_cfg()
     ctx = roks.Context(cfg, precision)
+    oracle_system = oracle_roks.System(cfg)
     base = to_np(ctx.init_orbitals(syn.orbital_uniforms(cfg, ctx.npw)), ctx.npw)
     prec = roks.ROKS_FP64 if precision == "fp64" else roks.ROKS_MIXED
     # two calls in a row, on different inputs, through the shared scratch
@@ -41,6 +44,9 @@ def test_noalloc_matches_orthonormalize(precision, tol):
         assert rel(G, R) < tol
         O = G.conj().T @ G
         assert np.abs(O - np.eye(ctx.nb)).max() < (1e-12 if precision == "fp64" else 2e-6)
+        # and against the oracle's Cholesky orthonormalisation of the same block
+        ref_oracle = oracle_system.orthonormalize(X)
+        assert rel(G, ref_oracle) < tol
     ctx.close()
 
 
