@@ -16,13 +16,17 @@
 //
 // Precision (three TF32 products per FP32 product): each operand value x is
 // split as x = hi + lo, hi = tf32(x), lo = tf32(x - hi), and each product is
-// lo.hi + hi.lo + hi.hi (three MMAs, smallest first).  The tensor cores'
-// FP32 accumulation truncates instead of rounding, which biases long sums of
-// like-signed terms (norms, overlaps, diagonal-dominated rotations), so
-// every K-step (8 reals, three MMAs) goes into a fresh tensor-memory
-// accumulator and the drain warps add it into FP32 sums in registers (round
-// to nearest).  Four accumulators of 128 columns rotate, so the MMAs of the
-// next K-steps run while the previous ones drain.
+// lo.hi + hi.lo + hi.hi.  The tensor cores' FP32 accumulation truncates
+// instead of rounding, which biases long sums of like-signed terms (norms,
+// overlaps, diagonal-dominated rotations).  So every stage (32 reals: four
+// K-steps of 8) goes into a fresh tensor-memory accumulator, in the order
+// of the eight small cross terms first and the four hi.hi products last:
+// only those four additions meet a large partial sum (a bias near 1e-7 of
+// the stage's sum at most), and the drain warps add the stage's result into
+// FP32 sums in registers (round to nearest).  Four accumulators of 128
+// columns rotate, so the MMAs of the next stages run while the previous
+// ones drain.  (A drain per K-step was measured a third slower on the
+// mgo-120 products.)
 //
 // One CTA per SM (200 KB of shared memory, all 512 tensor-memory columns),
 // 14 warps:
@@ -224,25 +228,30 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
                 }
                 tc::fence_after_sync();
                 const uint32_t sa = tc::smem_u32(conv + (size_t)cs * GB_SLOT);
-                for (int kk = 0; kk < GB_KR / 8; ++kk, ++u) {
-                    const int b = u % GB_ACC;
-                    if (u >= GB_ACC && !gwait(&acc_empty[b], (uint32_t)((u / GB_ACC - 1) & 1), wcap, &failed)) {
-                        ok = false;
-                        break;
-                    }
-                    tc::fence_after_sync();
-                    const uint32_t d = tmem + (uint32_t)(b * GB_NR);
-                    const uint32_t ko = (uint32_t)kk * 256u;   // 8 reals = two K chunks of 128 bytes
-                    const uint64_t ahi = tc::make_desc(sa + ko, LBO, SBO);
-                    const uint64_t alo = tc::make_desc(sa + GB_PART + ko, LBO, SBO);
-                    const uint64_t bhi = tc::make_desc(sa + 2 * GB_PART + ko, LBO, SBO);
-                    const uint64_t blo = tc::make_desc(sa + 3 * GB_PART + ko, LBO, SBO);
-                    tc::mma_tf32(d, alo, bhi, idesc, 0u);
-                    tc::mma_tf32(d, ahi, blo, idesc, 1u);
-                    tc::mma_tf32(d, ahi, bhi, idesc, 1u);
-                    tc::commit(&acc_full[b]);
+                // one accumulator per stage
+                const int b = u % GB_ACC;
+                if (u >= GB_ACC && !gwait(&acc_empty[b], (uint32_t)((u / GB_ACC - 1) & 1), wcap, &failed)) {
+                    ok = false;
+                    break;
                 }
-                if (!ok) break;
+                tc::fence_after_sync();
+                const uint32_t d = tmem + (uint32_t)(b * GB_NR);
+                // small cross terms of the four K-steps first (8 reals = two K chunks of 128 bytes) ...
+                for (int kk = 0; kk < GB_KR / 8; ++kk) {
+                    const uint32_t ko = (uint32_t)kk * 256u;
+                    tc::mma_tf32(d, tc::make_desc(sa + GB_PART + ko, LBO, SBO),
+                                 tc::make_desc(sa + 2 * GB_PART + ko, LBO, SBO), idesc, kk > 0 ? 1u : 0u);
+                    tc::mma_tf32(d, tc::make_desc(sa + ko, LBO, SBO), tc::make_desc(sa + 3 * GB_PART + ko, LBO, SBO),
+                                 idesc, 1u);
+                }
+                // ... then the hi.hi products
+                for (int kk = 0; kk < GB_KR / 8; ++kk) {
+                    const uint32_t ko = (uint32_t)kk * 256u;
+                    tc::mma_tf32(d, tc::make_desc(sa + ko, LBO, SBO), tc::make_desc(sa + 2 * GB_PART + ko, LBO, SBO),
+                                 idesc, 1u);
+                }
+                tc::commit(&acc_full[b]);
+                ++u;
                 tc::commit(&conv_empty[cs]);   // the operand stage is free once these MMAs complete
             }
             if (!ok) give_up(&failed);
@@ -307,7 +316,7 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
         float re[32], im[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) re[j] = im[j] = 0.f;
-        const int units = ns * (GB_KR / 8);
+        const int units = ns;
         bool ok = true;
         for (int u = 0; u < units; ++u) {
             const int b = u % GB_ACC;
