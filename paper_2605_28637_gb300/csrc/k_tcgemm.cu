@@ -29,16 +29,20 @@
 // mgo-120 products.)
 //
 // One CTA per SM (200 KB of shared memory, all 512 tensor-memory columns),
-// 14 warps:
+// 18 warps:
 //   warp 0      producer: 2-D tensor copies of the raw FP32 operand slices
 //               into three raw stages; NN: bulk copies of the pre-split B;
 //   warp 1      one thread issues the MMAs;
-//   warps 2-5   split a raw stage into TF32 hi and lo, build the N-side rows,
-//               and store K-major core matrices (8 rows x 16 bytes, no
-//               swizzle) into one of two operand stages;
-//   warps 6-13  drain the accumulators (warp % 4 picks the lane quadrant,
-//               warps 6-9 the complex columns 0-31, warps 10-13 columns
-//               32-63) and write the result.
+//   warps 2-17  workers.  In iteration i a worker converts its share of
+//               stage i (split into TF32 hi and lo, build the N-side rows,
+//               store K-major core matrices of 8 rows x 16 bytes, no
+//               swizzle, into one of two operand stages) and then drains its
+//               block of stage i - 2's accumulator: the lane quadrant
+//               warp % 4 and 16 complex columns.  The lag of two cannot
+//               deadlock: converting stage i waits for the MMAs of stage
+//               i - 2, which need the drain of stage i - 6 (iteration i - 4)
+//               and the conversion of stage i - 2 (iteration i - 2), and
+//               draining stage i - 2 waits for those same MMAs.
 // Every wait is bounded (the context's wait cap); a wait that gives up sets
 // a device flag and the CTA winds down: copies and MMAs in flight are waited
 // for with the default bound before the tensor memory is freed.
@@ -68,7 +72,8 @@ constexpr int GB_KR = 32;      // real K per stage (four MMA K-steps of 8)
 constexpr int GB_RAW = 3;      // raw stages
 constexpr int GB_CONV = 2;     // operand stages
 constexpr int GB_ACC = 4;      // tensor-memory accumulators
-constexpr int GB_THREADS = 14 * 32;
+constexpr int GB_WORKERS = 16;    // worker warps
+constexpr int GB_THREADS = (2 + GB_WORKERS) * 32;
 constexpr uint32_t GB_PART = GB_M * GB_KR * 4;   // one split part (hi or lo) of a 128-row operand: 16 KB
 constexpr uint32_t GB_SLOT = 4 * GB_PART;        // A hi | A lo | B hi | B lo
 constexpr uint32_t GB_RAWA = GB_M * GB_KC * 8;   // 16 KB
@@ -148,16 +153,16 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
     if (tid == 0) {
         for (int s = 0; s < GB_RAW; ++s) {
             tc::mbar_init(&raw_full[s], 1);
-            tc::mbar_init(&raw_empty[s], 4);
+            tc::mbar_init(&raw_empty[s], GB_WORKERS);
         }
         for (int s = 0; s < GB_CONV; ++s) {
-            tc::mbar_init(&conv_full[s], 4);
+            tc::mbar_init(&conv_full[s], GB_WORKERS);
             tc::mbar_init(&conv_empty[s], 1);
             tc::mbar_init(&b_full[s], 1);
         }
         for (int s = 0; s < GB_ACC; ++s) {
             tc::mbar_init(&acc_full[s], 1);
-            tc::mbar_init(&acc_empty[s], 8);
+            tc::mbar_init(&acc_empty[s], GB_WORKERS);
         }
         tc::mbar_init(&mma_done, 1);
         failed = 0;
@@ -260,87 +265,82 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
             gwait(&mma_done, 0u, GB_DEFAULT_WAIT, &failed);
         }
         __syncwarp();
-    } else if (warp < 6) {
-        // ------------------------------------------------ conversion: raw FP32 -> split K-major tiles
-        const int c = tid - 64;   // 0..127
+    } else {
+        // ------------------------------------------------ workers: conversion, then drain
+        const int wt = tid - 64;                // 0 .. 32 GB_WORKERS - 1
+        const int q = warp & 3;                 // lane quadrant
+        const int cg = (warp - 2) >> 2;         // complex columns 16 cg .. 16 cg + 15
+        const int r = 32 * q + lane;            // tile row of the drain
+        const int rr = wt & 127, c0 = wt >> 7;  // conversion of A: row rr, chunks c0 and c0 + 4
+        float re[16], im[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) re[j] = im[j] = 0.f;
         bool ok = true;
-        for (int i = 0; i < ns; ++i) {
-            const int rs = i % GB_RAW, cs = i % GB_CONV;
-            if (!warp_wait(&raw_full[rs], (uint32_t)((i / GB_RAW) & 1), wcap, &failed) ||
-                (i >= GB_CONV && !warp_wait(&conv_empty[cs], (uint32_t)((i / GB_CONV - 1) & 1), wcap, &failed))) {
-                ok = false;
-                break;
-            }
-            const unsigned char* ra = raw + (size_t)rs * GB_RAWS;
-            unsigned char* sl = conv + (size_t)cs * GB_SLOT;
-            if (!NN) {
-                // A row c (column c of A): 16 complex = eight 16-byte chunks,
-                // stored by the copy with the 128-byte swizzle
-#pragma unroll
-                for (int ch = 0; ch < 8; ++ch) {
-                    const float4 v = *reinterpret_cast<const float4*>(ra + c * 128 + ((ch ^ (c & 7)) << 4));
-                    put_split(sl, cofs(c, 4 * ch), v);
+        for (int i = 0; i < ns + 2; ++i) {
+            if (i < ns) {
+                const int rs = i % GB_RAW, cs = i % GB_CONV;
+                if (!warp_wait(&raw_full[rs], (uint32_t)((i / GB_RAW) & 1), wcap, &failed) ||
+                    (i >= GB_CONV &&
+                     !warp_wait(&conv_empty[cs], (uint32_t)((i / GB_CONV - 1) & 1), wcap, &failed))) {
+                    ok = false;
+                    break;
                 }
-                // B column j: the real-part row (re, im) and the imaginary-part row (im, -re)
-                const int j = c & 63, h = c >> 6;
+                const unsigned char* ra = raw + (size_t)rs * GB_RAWS;
+                unsigned char* sl = conv + (size_t)cs * GB_SLOT;
+                if (!NN) {
+                    // A row rr (column rr of A): 16 complex in eight 16-byte chunks,
+                    // stored by the copy with the 128-byte swizzle
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int ch = 4 * h + q;
-                    const float4 v =
-                        *reinterpret_cast<const float4*>(ra + GB_RAWA + j * 128 + ((ch ^ (j & 7)) << 4));
+                    for (int h2 = 0; h2 < 2; ++h2) {
+                        const int ch = c0 + 4 * h2;
+                        const float4 v = *reinterpret_cast<const float4*>(ra + rr * 128 + ((ch ^ (rr & 7)) << 4));
+                        put_split(sl, cofs(rr, 4 * ch), v);
+                    }
+                    // B column j, chunk ch: the real-part row (re, im) and the
+                    // imaginary-part row (im, -re)
+                    const int j = wt & 63, ch = wt >> 6;
+                    const float4 v = *reinterpret_cast<const float4*>(ra + GB_RAWA + j * 128 + ((ch ^ (j & 7)) << 4));
                     put_split(sl + 2 * GB_PART, cofs(j, 4 * ch), v);
                     put_split(sl + 2 * GB_PART, cofs(GB_NC + j, 4 * ch), make_float4(v.y, -v.x, v.w, -v.z));
+                } else {
+                    // A row rr (plane wave m0 + rr): the raw slice is [k][m], 1 KB per k
+#pragma unroll
+                    for (int h2 = 0; h2 < 2; ++h2) {
+                        const int ch = c0 + 4 * h2;
+                        const float2 a0 = *reinterpret_cast<const float2*>(ra + (2 * ch) * 1024 + rr * 8);
+                        const float2 a1 = *reinterpret_cast<const float2*>(ra + (2 * ch + 1) * 1024 + rr * 8);
+                        put_split(sl, cofs(rr, 4 * ch), make_float4(a0.x, a0.y, a1.x, a1.y));
+                    }
                 }
-            } else {
-                // A row c (plane wave m0 + c): the raw slice is [k][m], 1 KB per k
-#pragma unroll
-                for (int ch = 0; ch < 8; ++ch) {
-                    const float2 a0 = *reinterpret_cast<const float2*>(ra + (2 * ch) * 1024 + c * 8);
-                    const float2 a1 = *reinterpret_cast<const float2*>(ra + (2 * ch + 1) * 1024 + c * 8);
-                    put_split(sl, cofs(c, 4 * ch), make_float4(a0.x, a0.y, a1.x, a1.y));
+                tc::fence_async_smem();   // generic-proxy stores become visible to the tensor cores
+                __syncwarp();
+                if (lane == 0) {
+                    tc::mbar_arrive(&raw_empty[rs]);
+                    tc::mbar_arrive(&conv_full[cs]);
                 }
             }
-            tc::fence_async_smem();   // generic-proxy stores become visible to the tensor cores
-            __syncwarp();
-            if (lane == 0) {
-                tc::mbar_arrive(&raw_empty[rs]);
-                tc::mbar_arrive(&conv_full[cs]);
-            }
-        }
-        if (!ok) give_up(&failed);
-    } else {
-        // ------------------------------------------------ drain and epilogue
-        const int q = warp & 3;                 // lane quadrant
-        const int h = (warp - 6) >> 2;          // complex columns 32 h .. 32 h + 31
-        const int r = 32 * q + lane;            // tile row
-        float re[32], im[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) re[j] = im[j] = 0.f;
-        const int units = ns;
-        bool ok = true;
-        for (int u = 0; u < units; ++u) {
-            const int b = u % GB_ACC;
-            if (!warp_wait(&acc_full[b], (uint32_t)((u / GB_ACC) & 1), wcap, &failed)) {
-                ok = false;
-                break;
-            }
-            tc::fence_after_sync();
-            const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * GB_NR + 32 * h);
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
+            const int dsg = i - 2;
+            if (dsg >= 0) {
+                const int b = dsg % GB_ACC;
+                if (!warp_wait(&acc_full[b], (uint32_t)((dsg / GB_ACC) & 1), wcap, &failed)) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * GB_NR + 16 * cg);
                 float v[16], w[16];
-                tc::tmem_ld16_nowait(ta + 16 * half, v);
-                tc::tmem_ld16_nowait(ta + GB_NC + 16 * half, w);
+                tc::tmem_ld16_nowait(ta, v);
+                tc::tmem_ld16_nowait(ta + GB_NC, w);
                 tc::tmem_wait_ld();
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    re[16 * half + j] += v[j];
-                    im[16 * half + j] += w[j];
+                    re[j] += v[j];
+                    im[j] += w[j];
                 }
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&acc_empty[b]);
             }
-            tc::fence_before_sync();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&acc_empty[b]);
         }
         if (!ok) give_up(&failed);
         if (ok) {
@@ -348,8 +348,8 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
                 const int m = m0 + r;
                 if (m < M) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int n = n0 + 32 * h + j;
+                    for (int j = 0; j < 16; ++j) {
+                        const int n = n0 + 16 * cg + j;
                         if (n < N) {
                             float2 o = make_float2(alpha * re[j], alpha * im[j]);
                             if (beta != 0.f) {
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
                 const int tiles = gridDim.x * gridDim.y;
                 float2* P = part + ((int64_t)blockIdx.z * tiles + tile) * GB_NC * GB_M;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) P[(int64_t)(32 * h + j) * GB_M + r] = make_float2(re[j], im[j]);
+                for (int j = 0; j < 16; ++j) P[(int64_t)(16 * cg + j) * GB_M + r] = make_float2(re[j], im[j]);
             }
         }
     }
