@@ -270,24 +270,36 @@ def _geometry(miller):
     return {"ncol": len(ij), "np": len(i)}
 
 
-def traffic_record(family):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source."""
+def traffic_record(family, workload=None, alg_bytes=None):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (one hash over every file listed).  A
+    capture on a smaller workload (the capture size rule keeps full-size
+    multi-pass captures off the GPU) is scaled to this launch by the ratio of
+    algorithmic bytes (the stage streams its planes once per band, so its
+    traffic grows in proportion); returns (bytes, note)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
-        return None
+        return None, None
     with open(p) as f:
         rec = json.load(f)
     ent = rec.get("kernels", {}).get(family)
     if not ent:
-        return None
-    src = os.path.join(ROOT, ent["source"])
-    if not os.path.exists(src):
-        return None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if sha != ent.get("source_sha"):
-        return None
-    return float(ent["bytes_per_launch"])
+        return None, None
+    h = hashlib.sha256()
+    for rel_path in ent.get("sources", []):
+        src = os.path.join(ROOT, rel_path)
+        if not os.path.exists(src):
+            return None, None
+        with open(src, "rb") as f:
+            h.update(f.read())
+    if not ent.get("sources") or h.hexdigest()[:16] != ent.get("source_sha"):
+        return None, None
+    if workload is None or workload == ent.get("workload"):
+        return float(ent["bytes_per_launch"]), f"ncu on {ent.get('workload')}"
+    if alg_bytes and ent.get("algorithmic_bytes_per_launch"):
+        scaled = float(ent["bytes_per_launch"]) * alg_bytes / float(ent["algorithmic_bytes_per_launch"])
+        return scaled, f"ncu on {ent.get('workload')}, scaled by algorithmic bytes"
+    return None, None
 
 
 # ---------------------------------------------------------------- CPU oracle sample
@@ -612,7 +624,10 @@ def run_gpu(args):
         torch.distributed.barrier()
     from paper_2605_28637_gb300 import roks, synthetic as syn
     cfg = replica_config(args.workload, rank)
-    ctx = roks.Context(cfg, args.precision)
+    # the autotuner picks the density's band grouping and the tensor-core
+    # split depth on this context's own buffers (roks_options.autotune)
+    ctx = roks.Context(cfg, args.precision, autotune=1)
+    tuning = ctx.tuning()
     u = syn.orbital_uniforms(cfg, ctx.npw)
     psi = ctx.init_orbitals(u)
     for _ in range(args.warmup):
@@ -742,9 +757,10 @@ def run_gpu(args):
         per_launch_ms = e["ms"] / e["launches"]
         if bound == "hbm":
             achieved = amount / (per_launch_ms / 1000.0) / 1e9
+            traffic, tnote = traffic_record(e["name"], cfg["name"], amount)
             ent = {"bound": "hbm", "kernel": e["name"], "achieved": achieved, "peak": hbm, "unit": "GB/s",
                    "frac": achieved / hbm, "peak_kind": f"{peak_kind} (copy bandwidth)",
-                   "traffic": traffic_record(e["name"]), "algorithmic_bytes_per_launch": amount}
+                   "traffic": traffic, "traffic_source": tnote, "algorithmic_bytes_per_launch": amount}
         else:
             peak, pk = alu_peak(args.precision, bound)
             achieved = amount / (per_launch_ms / 1000.0) / 1e12
@@ -812,6 +828,7 @@ def run_gpu(args):
             "config": {"workload": cfg["name"], "grid": cfg["grid"], "ecut_ha": cfg["ecut"], "bands": ctx.nb,
                        "plane_waves": ctx.npw, "atoms": len(cfg["atoms"]),
                        "precision": args.precision, "parallelism": f"replicas{world}",
+                       "tuning": tuning,
                        "l2": "per-step working set above the 129 MB L2 (plane buffers, projectors, band blocks)"},
             "roofline": roofline,
             "roofline_hbm": roofline_hbm,

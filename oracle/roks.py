@@ -246,11 +246,14 @@ class System:
         return self.omega / self.N ** 3
 
     # ----------------------------------------------------------- a2, a3: densities
-    def class_densities(self, Psi: np.ndarray) -> np.ndarray:
-        """rho_k(r) = sum_{n in k} |psi_n(r)|^2 for k = closed, a, b."""
+    def class_densities(self, Psi: np.ndarray, bands=None) -> np.ndarray:
+        """rho_k(r) = sum_{n in k} |psi_n(r)|^2 for k = closed, a, b.  With
+        `bands`, the columns of Psi are those bands only (their share of the
+        sums, for callers that split the bands over processes)."""
+        bands = range(self.nb) if bands is None else bands
         rho = np.zeros((3, self.N ** 3))
-        for n in range(self.nb):
-            psi = self.to_real(Psi[:, n])
+        for col, n in enumerate(bands):
+            psi = self.to_real(Psi[:, col])
             rho[self.cls[n]] += (psi.conj() * psi).real
         return rho
 

@@ -54,12 +54,12 @@ __host__ __device__ __forceinline__ V mul_i(V a) {
 // ---------------------------------------------------------------- plans
 // Radix sequence of a transform length.  The grid sizes of the workloads get
 // two passes with register codelets up to 16 points (96 = 12 x 8,
-// 120 = 12 x 10, 72 = 9 x 8, 48 = 8 x 6, 24 = 8 x 3, 32 = 8 x 4, 16 = 4 x 4);
+// 120 = 15 x 8, 72 = 9 x 8, 48 = 8 x 6, 24 = 8 x 3, 32 = 8 x 4, 16 = 4 x 4);
 // other lengths fall back to factors of 8, 5, 4, 3, 2 in that order.
 __host__ __device__ constexpr int plan_radix(int n, int pass) {
     switch (n) {
         case 96: return pass == 0 ? 12 : (pass == 1 ? 8 : 1);
-        case 120: return pass == 0 ? 12 : (pass == 1 ? 10 : 1);
+        case 120: return pass == 0 ? 15 : (pass == 1 ? 8 : 1);
         case 72: return pass == 0 ? 9 : (pass == 1 ? 8 : 1);
         case 48: return pass == 0 ? 8 : (pass == 1 ? 6 : 1);
         case 16: return pass == 0 ? 4 : (pass == 1 ? 4 : 1);

@@ -14,8 +14,13 @@ namespace roks {
 constexpr int kGrids[] = {16, 24, 32, 48, 72, 96, 120};
 
 // Lines per shared-memory tile for a transform length.
+// Lines per transform tile.  N = 120 takes 32 lines with the 15 x 8 plan:
+// its two passes then hold 256 and 480 butterflies (one and two nearly full
+// rounds of 256 threads); 24 lines with 12 x 10 left the second round of the
+// radix-10 pass 1/8 busy.  Measured at mgo-120 (ms per launch): x-stage
+// density 1.99 -> 1.33, x-stage apply 2.99 -> 2.60, y stage 0.56 -> 0.48.
 __host__ __device__ constexpr int tile_lines(int n) {
-    return n == 16 ? 16 : (n == 32 || n == 96) ? 32 : 24;
+    return n == 16 ? 16 : (n == 32 || n == 96 || n == 120) ? 32 : 24;
 }
 constexpr int kThreads = 256;
 // Threads of the x-stage apply: for N = 96 (radix 12 then 8 over 32 lines:

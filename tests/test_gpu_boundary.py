@@ -218,3 +218,37 @@ def test_many_bands_many_projectors(precision):
             assert abs(info["E_new"] - s.energy(Pg)) <= 2e-7 * scale, (it, info["E_new"], s.energy(Pg), scale)
             assert abs(info["E_new"] - ref.E_new) <= 1e-6 * scale, (it, info["E_new"], ref.E_new, scale)
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autotune_keeps_the_results(precision):
+    """roks_options.autotune times the density's band grouping (2, 4, 8) and,
+    on the mixed path, the tensor-core split depth, then keeps the fastest:
+    the chosen shapes are valid and the energies and F|n> stay those of the
+    default shapes (only the order of some sums changes: 1e-12 relative on
+    the FP64 path, FP32 rounding on the mixed path)."""
+    cfg = syn.with_changes(syn.make_config("mgo-72", 0), grid=32, ecut=12.0)
+    roks = built()
+    ref = roks.Context(cfg, precision)
+    tuned = roks.Context(cfg, precision, autotune=1)
+    t = tuned.tuning()
+    assert t["density_groups"] in (2, 4, 8)
+    assert t["tc_split_waves_x2"] in (3, 5, 8)
+    assert all(ms > 0 for ms in t["candidate_ms"][:3])
+    if precision == "mixed":
+        assert all(ms > 0 for ms in t["candidate_ms"][3:])
+    d = roks.Context(cfg, precision).tuning()
+    assert (d["density_groups"], d["tc_split_waves_x2"]) == (4, 5)
+    u = syn.orbital_uniforms(cfg, ref.npw)
+    out = []
+    for ctx in (ref, tuned):
+        psi = ctx.init_orbitals(u)
+        ctx.density(psi)
+        e = ctx.potential()
+        f, _, _ = ctx.apply_h(psi)
+        out.append((e["E_total"], to_np(f, ctx.npw)))
+    tol_e, tol_f = (1e-12, 1e-11) if precision == "fp64" else (2e-6, 2e-5)
+    assert abs(out[0][0] - out[1][0]) <= tol_e * abs(out[0][0])
+    assert rel(out[1][1], out[0][1]) < tol_f
+    ref.close()
+    tuned.close()
