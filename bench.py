@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--force-calls", type=int, default=10,
                     help="timed roks_forces calls on the final orbitals; 0 skips them")
+    ap.add_argument("--gamma-steps", type=int, default=20,
+                    help="PCG steps of the Gamma-point leg (real orbitals, half sphere; 0: skip)")
     ap.add_argument("--diis-steps", type=int, default=50,
                     help="timed DIIS steps (roks_diis_step) after the PCG legs; 0 skips them")
     return ap.parse_args()
@@ -588,6 +590,30 @@ def hybrid_leg(args, torch):
     return out
 
 
+def gamma_leg(args, cfg, torch, complex_ms_per_step):
+    """The benchmark's workload with real orbitals at the Gamma point
+    (roks_options.gamma): half-sphere coefficients, two orbitals per complex
+    transform.  Same seeded start drawn on the half sphere, graph-replayed
+    PCG steps timed with CUDA events on the context's stream."""
+    from paper_2605_28637_gb300 import roks, synthetic as syn
+    ctx = roks.Context(cfg, args.precision, autotune=1, gamma=1)
+    psi = ctx.init_orbitals(syn.orbital_uniforms(cfg, ctx.npw))
+    for _ in range(max(3, args.warmup)):
+        ctx.pcg_step(psi)
+    ms, infos, _ = time_pcg(ctx, psi, args.gamma_steps, torch)
+    _, _, prof = time_pcg(ctx, psi, min(args.gamma_steps, 10), torch, profile=True)
+    prof = [e for e in prof if e["name"] not in ("kernel_launches", "tensor_core_launches")]
+    per = ms / args.gamma_steps
+    out = {"workload": cfg["name"], "plane_waves_half_sphere": ctx.npw, "bands": ctx.nb,
+           "steps": args.gamma_steps, "ms_per_step": per, "value": ctx.nb / (per / 1000.0), "unit": UNIT,
+           "speedup_per_step_vs_complex": complex_ms_per_step / per, "tuning": ctx.tuning(),
+           "E_last": infos[-1]["E_new"],
+           "profile": {e["name"]: {"launches": e["launches"], "ms": e["ms"]} for e in prof},
+           "launch": "one CUDA graph per PCG iteration"}
+    ctx.close()
+    return out
+
+
 def csize_of(precision):
     """Bytes of one complex coefficient on the path."""
     return 16 if precision == "fp64" else 8
@@ -813,6 +839,9 @@ def run_gpu(args):
                "mixed_diis_singlet": converge_diis(base, "mixed", args.converge_iters, torch,
                                                    min(args.converge_seconds, 20.0), args.g_tol),
                "note": "time-to-solution ratios only between converged legs in the FP64 leg's state"}
+    gamma = None
+    if args.gamma_steps > 0 and rank == 0:
+        gamma = gamma_leg(args, cfg, torch, ms_max / args.steps)
     hybrid = None
     if args.hybrid_applies > 0 and rank == 0:
         hybrid = hybrid_leg(args, torch)
@@ -843,6 +872,7 @@ def run_gpu(args):
             "diis": diis,
             "forces": forces_leg,
             "hybrid": hybrid,
+            "gamma": gamma,
             "profile": {e["name"]: {"launches": e["launches"], "ms": e["ms"]} for e in prof},
             "launch": "one CUDA graph per PCG iteration",
             "E_last": infos[-1]["E_new"] if infos else None,

@@ -147,6 +147,17 @@ typedef struct {
                           poll at all, so every such wait gives up (a test of
                           the timeout path).  Copies already in flight are
                           still waited for with the default cap.             */
+    int gamma;         /* 1: real orbitals at the Gamma point (the only
+                          k-point the paper samples, Sec. III) on the half
+                          sphere.  The basis is G = 0 and the Miller triples
+                          after it in the basis order (npw_half =
+                          (npw_full + 1) / 2); every orbital-shaped array the
+                          calls take or return holds, per band, c(0) (real)
+                          and sqrt(2) c(G) for the other half-sphere G, so
+                          that Re sum conj(a) b over the rows is the full
+                          inner product.  Two bands share one complex
+                          transform.  Requires alpha = 0 and, with an open
+                          shell, an even n_closed (ROKS_EINVAL otherwise).   */
 } roks_options;
 
 /* Energy terms (Ha).  E_kin, E_loc, E_nl carry the occupation weights;
@@ -188,7 +199,8 @@ ROKS_API roks_status roks_setup(const roks_cell* cell, double ecut, int natoms,
                        roks_ctx** out);
 
 /* Basis size, band count, the minimal leading dimension, and a host
- * pointer to the npw x 3 Miller indices (row major, owned by the context). */
+ * pointer to the npw x 3 Miller indices (row major, owned by the context).
+ * With roks_options.gamma these are the half-sphere rows. */
 ROKS_API roks_status roks_basis(roks_ctx* ctx, int* npw, int* nbands, int* ld_min,
                        const int32_t** miller);
 
@@ -200,7 +212,10 @@ ROKS_API roks_status roks_basis(roks_ctx* ctx, int* npw, int* nbands, int* ld_mi
  * -1 + 2 (z_i >> 11) 2^-53, z_i output i of SplitMix64 seeded with
  * roks_options.seed (z_i = mix(seed + (i + 1) 0x9E3779B97F4A7C15) with
  * Vigna's mixing function).  Allocates nothing (host numbers are staged in
- * the context's workspaces).  Resets the direction and DIIS histories. */
+ * the context's workspaces).  Resets the direction and DIIS histories.
+ * With roks_options.gamma, npw is the half sphere's: c(0) keeps its real
+ * part and the other rows are stored times sqrt(2) before the
+ * orthonormalisation. */
 ROKS_API roks_status roks_init_orbitals(roks_ctx* ctx, const double* u_host,
                                void* psi, int64_t ld);
 

@@ -108,10 +108,11 @@ __global__ void __launch_bounds__(kThreads) k_band_z_fwd(Sphere s, const c2<T>* 
     }
     __syncthreads();
     tile_fft<V, N, -1, TL, LS, kThreads>(buf, tws);
+    // psi null: the transform alone (the Gamma-point unpack adds the kinetic term)
     const int cls = b < n_closed ? 0 : b - n_closed + 1;
-    const T w = wk[cls];
+    const T w = psi ? wk[cls] : T(0);
     V* o = out + (int64_t)b * ldo;
-    const V* p = psi + (int64_t)b * ldp;
+    const V* p = psi ? psi + (int64_t)b * ldp : nullptr;
 #pragma unroll
     for (int r = 0; r < (TL * N + kThreads - 1) / kThreads; ++r) {
         const int idx = threadIdx.x + r * kThreads;
@@ -122,9 +123,13 @@ __global__ void __launch_bounds__(kThreads) k_band_z_fwd(Sphere s, const c2<T>* 
             if (k >= -km && k <= km) {
                 const int g = cstart[line] + k + km;
                 const V loc = buf[e * LS + line];
-                const V ps = p[g];
-                const T kin = w * g2half[g];
-                o[g] = mk<T>(loc.x + kin * ps.x, loc.y + kin * ps.y);
+                if (p) {
+                    const V ps = p[g];
+                    const T kin = w * g2half[g];
+                    o[g] = mk<T>(loc.x + kin * ps.x, loc.y + kin * ps.y);
+                } else {
+                    o[g] = loc;
+                }
             }
         }
     }
@@ -208,7 +213,7 @@ __global__ void __launch_bounds__(x_threads(N)) k_band_x_apply(Sphere s, const c
                                                                c2<T>* __restrict__ Yp,
                                                                const T* __restrict__ Vk,
                                                                const c2<T>* __restrict__ Xx, int b0,
-                                                               int n_closed, T scale) {
+                                                               int n_closed, int split_band, T scale) {
     constexpr int NT = x_threads(N);
     using V = c2<T>;
     constexpr int TL = tile_lines(N), LS = TL + 1;
@@ -222,9 +227,13 @@ __global__ void __launch_bounds__(x_threads(N)) k_band_x_apply(Sphere s, const c
     const int bb = blockIdx.z;
     const int b = b0 + bb;
     const int cls = b < n_closed ? 0 : b - n_closed + 1;
+    // split_band: a band holding two real orbitals as (re, im) with the
+    // classes a and b (the Gamma-point packing of the open pair)
+    const bool split = b == split_band;
     // offsets within one band's planes and within one N^3 grid fit in 32 bits
     V* Ypb = Yp + (int64_t)bb * s.np * N * N + y * N + z0;
-    const T* Vc = Vk + (int64_t)cls * N * N * N + y * N + z0;
+    const T* Vc = Vk + (int64_t)(split ? 1 : cls) * N * N * N + y * N + z0;
+    const T* Vc2 = Vk + (int64_t)2 * N * N * N + y * N + z0;
     const c2<T>* Xb = Xx ? Xx + (int64_t)b * N * N * N + y * N + z0 : nullptr;
     const int nmax = s.nmax;
     constexpr int NN = N * N;
@@ -240,7 +249,8 @@ __global__ void __launch_bounds__(x_threads(N)) k_band_x_apply(Sphere s, const c
             const bool in = z0 + line < N;
             const int gi = e * NN + line;
             const T w = in ? Vc[gi] * scale : T(0);
-            V o = mk<T>(v.x * w, v.y * w);
+            const T w2 = split ? (in ? Vc2[gi] * scale : T(0)) : w;
+            V o = mk<T>(v.x * w, v.y * w2);
             if (Xb && in) {
                 const V xv = Xb[gi];
                 o.x += xv.x * scale;
@@ -302,7 +312,8 @@ __global__ void __launch_bounds__(kThreads) k_band_x_density(Sphere s, const c2<
                                                              const c2<T>* __restrict__ Yp,
                                                              typename DensAcc<T>::S* __restrict__ rho3,
                                                              typename DensAcc<T>::S* __restrict__ slot,
-                                                             int b0, int nbb, int gs, int n_closed, T scale) {
+                                                             int b0, int nbb, int gs, int n_closed, T scale,
+                                                             int part_sel, int cls_override) {
     using V = c2<T>;
     using DA = DensAcc<T>;
     using DS = typename DA::S;
@@ -341,7 +352,7 @@ __global__ void __launch_bounds__(kThreads) k_band_x_density(Sphere s, const c2<
     int bb = gbeg;
     while (bb < gend) {
         const int b = b0 + bb;
-        const int cls = b < n_closed ? 0 : b - n_closed + 1;
+        const int cls = cls_override >= 0 ? cls_override : (b < n_closed ? 0 : b - n_closed + 1);
         const int seg_end = cls == 0 ? min(gend, n_closed - b0) : bb + 1;
         DS* rr = cls == 0 ? slot_g : rho3 + (int64_t)cls * N3;
         while (bb < seg_end) {
@@ -367,7 +378,11 @@ __global__ void __launch_bounds__(kThreads) k_band_x_density(Sphere s, const c2<
                         const int i = signed_freq(e, N);
                         return (i >= -nmax && i <= nmax) ? sb[(i + nmax) * TL + line] : mk<T>(T(0), T(0));
                     },
-                    [&](int, int, V v, int q, int r) { part[q][r] += v.x * v.x + v.y * v.y; });
+                    [&](int, int, V v, int q, int r) {
+                        // part_sel 1 / 2: the real / imaginary part alone (one
+                        // orbital of a Gamma-point packed pair)
+                        part[q][r] += part_sel == 0 ? v.x * v.x + v.y * v.y : (part_sel == 1 ? v.x * v.x : v.y * v.y);
+                    });
                 __syncthreads();
             }
             const bool first = cls == 0 && !slot_written;
@@ -385,7 +400,7 @@ __global__ void __launch_bounds__(kThreads) k_band_x_density(Sphere s, const c2<
             if (cls == 0) slot_written = true;
         }
     }
-    if (!slot_written) {
+    if (!slot_written && slot) {
         // a group without closed bands still owns its slot
 #pragma unroll
         for (int q = 0; q < PER; ++q)
@@ -490,10 +505,11 @@ struct BandFft {
         roks::count_launch(), k_band_y_inv<T, N><<<gy, kThreads, SM, st>>>(s, tw, Zc, Yp);
     }
     static void x_apply(const Sphere& s, const V* tw, V* Yp, const T* Vk, const V* Xx, int b0, int nbb, int nc,
-                        T scale, cudaStream_t st) {
+                        int split_band, T scale, cudaStream_t st) {
         set_smem(k_band_x_apply<T, N>, SM);
         dim3 g((N + TL - 1) / TL, N, nbb);
-        roks::count_launch(), k_band_x_apply<T, N><<<g, x_threads(N), SM, st>>>(s, tw, Yp, Vk, Xx, b0, nc, scale);
+        roks::count_launch(), k_band_x_apply<T, N><<<g, x_threads(N), SM, st>>>(s, tw, Yp, Vk, Xx, b0, nc,
+                                                                                split_band, scale);
     }
     static void x_inv_full(const Sphere& s, const V* tw, const V* Yp, V* Phi, int b0, int nbb, T scale,
                            cudaStream_t st) {
@@ -512,8 +528,11 @@ struct BandFft {
         dim3 gz((s.ncol + TL - 1) / TL, nbb);
         roks::count_launch(), k_band_z_fwd<T, N><<<gz, kThreads, SM, st>>>(s, tw, Zc, out, ldo, psi, ldp, g2half, wk, b0, nc);
     }
+    // slot null: the bands are open-shell ones (or cls_override >= 0) and go
+    // straight to rho3, no group slots are written and none are reduced
     static void x_density(const Sphere& s, const V* tw, const V* Yp, double* rho3, double* slot, int ngroups,
-                          int b0, int nbb, int nc, double scale, cudaStream_t st) {
+                          int b0, int nbb, int nc, double scale, int part_sel, int cls_override,
+                          cudaStream_t st) {
         // tile, twiddles and two staging buffers of np x TL
         const size_t sm = SM + 2 * sizeof(V) * (size_t)s.np * TL;
         set_smem(k_band_x_density<T, N>, sm);
@@ -524,7 +543,8 @@ struct BandFft {
         DS* r3 = reinterpret_cast<DS*>(rho3);
         DS* sl = reinterpret_cast<DS*>(slot);
         roks::count_launch(), k_band_x_density<T, N><<<g, kThreads, sm, st>>>(s, tw, Yp, r3, sl, b0, nbb, gs, nc,
-                                                                            T(scale));
+                                                                            T(scale), part_sel, cls_override);
+        if (!sl) return;
         const int N3 = N * N * N;
         roks::count_launch(), k_density_reduce<T><<<(unsigned)((N3 + 255) / 256), 256, 0, st>>>(N3, ng, sl, r3);
     }
@@ -564,8 +584,8 @@ void band_y_inv(const Sphere& s, const c2<T>* tw, const c2<T>* Zc, c2<T>* Yp, in
 }
 template <typename T>
 void band_x_apply(const Sphere& s, const c2<T>* tw, c2<T>* Yp, const T* Vk, const c2<T>* Xx, int b0, int nbb,
-                  int n_closed, T scale, cudaStream_t st) {
-    ROKS_GRID_DISPATCH(s.N, (BandFft<T, NN>::x_apply(s, tw, Yp, Vk, Xx, b0, nbb, n_closed, scale, st)));
+                  int n_closed, int split_band, T scale, cudaStream_t st) {
+    ROKS_GRID_DISPATCH(s.N, (BandFft<T, NN>::x_apply(s, tw, Yp, Vk, Xx, b0, nbb, n_closed, split_band, scale, st)));
 }
 template <typename T>
 void band_x_inv_full(const Sphere& s, const c2<T>* tw, const c2<T>* Yp, c2<T>* Phi, int b0, int nbb, T scale,
@@ -584,9 +604,9 @@ void band_z_fwd(const Sphere& s, const c2<T>* tw, const c2<T>* Zc, c2<T>* out, i
 }
 template <typename T>
 void band_x_density(const Sphere& s, const c2<T>* tw, const c2<T>* Yp, double* rho3, double* slot, int ngroups,
-                    int b0, int nbb, int n_closed, double scale, cudaStream_t st) {
+                    int b0, int nbb, int n_closed, double scale, cudaStream_t st, int part_sel, int cls_override) {
     ROKS_GRID_DISPATCH(s.N, (BandFft<T, NN>::x_density(s, tw, Yp, rho3, slot, ngroups, b0, nbb, n_closed, scale,
-                                                       st)));
+                                                       part_sel, cls_override, st)));
 }
 template <typename T>
 void grid_fft3(int N, const c2<T>* tw, c2<T>* data, int dir, cudaStream_t st) {
@@ -601,15 +621,15 @@ void grid_fft3_batched(int N, const c2<T>* tw, c2<T>* data, int batch, int64_t b
     template void band_z_inv<T>(const Sphere&, const c2<T>*, const c2<T>*, int64_t, int, int, c2<T>*,           \
                                 cudaStream_t);                                                                   \
     template void band_y_inv<T>(const Sphere&, const c2<T>*, const c2<T>*, c2<T>*, int, cudaStream_t);          \
-    template void band_x_apply<T>(const Sphere&, const c2<T>*, c2<T>*, const T*, const c2<T>*, int, int, int, T,  \
-                                  cudaStream_t);                                                                 \
+    template void band_x_apply<T>(const Sphere&, const c2<T>*, c2<T>*, const T*, const c2<T>*, int, int, int, int, \
+                                  T, cudaStream_t);                                                              \
     template void band_x_inv_full<T>(const Sphere&, const c2<T>*, const c2<T>*, c2<T>*, int, int, T, cudaStream_t); \
     template void grid_fft3_batched<T>(int, const c2<T>*, c2<T>*, int, int64_t, int, cudaStream_t);             \
     template void band_y_fwd<T>(const Sphere&, const c2<T>*, const c2<T>*, c2<T>*, int, cudaStream_t);          \
     template void band_z_fwd<T>(const Sphere&, const c2<T>*, const c2<T>*, c2<T>*, int64_t, const c2<T>*,        \
                                 int64_t, const T*, const T*, int, int, int, cudaStream_t);                      \
     template void band_x_density<T>(const Sphere&, const c2<T>*, const c2<T>*, double*, double*, int, int, int,  \
-                                    int, double, cudaStream_t);                                                  \
+                                    int, double, cudaStream_t, int, int);                                        \
     template void grid_fft3<T>(int, const c2<T>*, c2<T>*, int, cudaStream_t);
 
 }  // namespace roks

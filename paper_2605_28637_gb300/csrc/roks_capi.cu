@@ -41,6 +41,13 @@ struct roks_ctx {
     long long steps = 0;   // PCG and DIIS steps since the orbitals were last set
     int N = 0, npw = 0, ld_min = 0, nmax = 0, M = 0, ncol = 0, np = 0;
     int nb = 0, nc = 0, mode = 1, nproj = 0, natoms = 0, suppress_ab = 0;
+    // Gamma point (roks_options.gamma): npw counts the half sphere, the tail
+    // of the full basis from row h0; the transforms run on nbt packed bands
+    // (two real orbitals each) with n_closed nct, and band split_t (-1: none)
+    // holds the open pair a, b.  Without it nbt = nb, nct = nc, split_t = -1.
+    int gamma = 0, npw_full = 0, h0 = 0, nbt = 0, nct = 0, split_t = -1;
+    int64_t ldc_pk = 0;
+    void* d_Cpk = nullptr;   // packed full-sphere coefficients (npw_full rows, ldc_pk, nbt bands)
     double cM = 0, cT = 0;
     PotCoef cf{};
     std::vector<int32_t> miller;
@@ -258,6 +265,33 @@ struct Impl {
     static V* cv(void* p) { return static_cast<V*>(p); }
     static const V* ccv(const void* p) { return static_cast<const V*>(p); }
 
+    // C = A^H B over the basis rows; at the Gamma point its real part (the
+    // full-sphere product of real orbitals in the stored half-sphere form)
+    static void cn(roks_ctx* ctx, int M, int N, int K, const V* A, int64_t lda, const V* B, int64_t ldb, double2* C,
+                   int ldc, cudaStream_t st) {
+        gemm_cn<T>(M, N, K, A, lda, B, ldb, C, ldc, ctx->d_gemm_work, ctx->gemm_work_elems, st);
+        if (ctx->gamma) gamma_real_part(M, N, C, ldc, st);
+    }
+
+    // Yp <- y-stage planes of the transform bands of psi (at the Gamma point
+    // two real orbitals per band, expanded to the full sphere first)
+    static void inv_planes(roks_ctx* ctx, const void* psi, int64_t ld) {
+        const Sphere s = sphere(ctx);
+        cudaStream_t st = ctx->st;
+        const V* src = ccv(psi);
+        int64_t lds = ld;
+        if (ctx->gamma) {
+            PROF("fft_z_inv");
+            gamma_expand<T>(ctx->npw, ctx->h0, ctx->nb, src, ld, cv(ctx->d_Cpk), ctx->ldc_pk, st);
+            src = ccv(ctx->d_Cpk);
+            lds = ctx->ldc_pk;
+        }
+        { PROF("fft_z_inv"); band_z_inv<T>(s, ccv(ctx->d_tw), src, lds, 0, ctx->nbt, cv(ctx->d_Zc), st); }
+        { PROF("fft_y_inv"); band_y_inv<T>(s, ccv(ctx->d_tw), cv(ctx->d_Zc), cv(ctx->d_Yp), ctx->nbt, st); }
+        ctx->yp_psi = psi;
+        ctx->yp_ld = ld;
+    }
+
     // Exact exchange of the bands whose plane data sit in Yp: real-space
     // orbitals, pair integrals, energies and (want_field) the exchange fields.
     static void exchange(roks_ctx* ctx, bool want_field) {
@@ -291,10 +325,7 @@ struct Impl {
         const Sphere s = sphere(ctx);
         cudaStream_t st = ctx->st;
         const V* p = ccv(psi);
-        { PROF("fft_z_inv"); band_z_inv<T>(s, ccv(ctx->d_tw), p, ld, 0, ctx->nb, cv(ctx->d_Zc), st); }
-        { PROF("fft_y_inv"); band_y_inv<T>(s, ccv(ctx->d_tw), cv(ctx->d_Zc), cv(ctx->d_Yp), ctx->nb, st); }
-        ctx->yp_psi = psi;
-        ctx->yp_ld = ld;
+        inv_planes(ctx, psi, ld);
         if (ctx->alpha != 0.0) {
             PROF("exchange");
             exchange(ctx, false);
@@ -302,15 +333,27 @@ struct Impl {
         CK(cudaMemsetAsync(ctx->d_rho3, 0, sizeof(double) * 3 * (size_t)ctx->N * ctx->N * ctx->N, st));
         {
             PROF("fft_x_density");
-            band_x_density<T>(s, ccv(ctx->d_tw), cv(ctx->d_Yp), ctx->d_rho3, ctx->d_rho_slot, ctx->dens_groups, 0,
-                              ctx->nb, ctx->nc, 1.0 / ctx->omega, st);
+            if (ctx->split_t < 0) {
+                band_x_density<T>(s, ccv(ctx->d_tw), cv(ctx->d_Yp), ctx->d_rho3, ctx->d_rho_slot, ctx->dens_groups,
+                                  0, ctx->nbt, ctx->nct, 1.0 / ctx->omega, st);
+            } else {
+                // Gamma point: the closed pairs, then the packed open pair's
+                // real part (a) and imaginary part (b) into their own classes
+                if (ctx->nct > 0)
+                    band_x_density<T>(s, ccv(ctx->d_tw), cv(ctx->d_Yp), ctx->d_rho3, ctx->d_rho_slot,
+                                      ctx->dens_groups, 0, ctx->nct, ctx->nct, 1.0 / ctx->omega, st);
+                // (the kernel indexes the plane buffer from the launch's first band)
+                const V* yo = ccv(ctx->d_Yp) + (int64_t)ctx->split_t * ctx->np * ctx->N * ctx->N;
+                for (int part = 1; part <= 2; ++part)
+                    band_x_density<T>(s, ccv(ctx->d_tw), yo, ctx->d_rho3, nullptr, 1, ctx->split_t, 1, ctx->nct,
+                                      1.0 / ctx->omega, st, part, part);
+            }
         }
         column_sums<T>(0, ctx->npw, ctx->nb, p, ld, nullptr, 0, static_cast<const T*>(ctx->d_g2half), ctx->d_colpart, ctx->d_kin_b, st);
         const double2* B = Bgiven;
         if (!B) {
             PROF("proj_PhPsi");
-            gemm_cn<T>(ctx->nproj, ctx->nb, ctx->npw, ccv(ctx->d_P), ctx->ld_min, p, ld, ctx->d_B, ctx->nproj,
-                       ctx->d_gemm_work, ctx->gemm_work_elems, st);
+            cn(ctx, ctx->nproj, ctx->nb, ctx->npw, ccv(ctx->d_P), ctx->ld_min, p, ld, ctx->d_B, ctx->nproj, st);
             B = ctx->d_B;
         }
         if (B == ctx->d_B) {
@@ -342,14 +385,7 @@ struct Impl {
     // reuse_B: d_B already holds P^H psi (the PCG chain keeps it from the
     // orthonormalisation of the accepted point)
     // Yp <- y-stage planes of psi
-    static void planes(roks_ctx* ctx, const void* psi, int64_t ld) {
-        const Sphere s = sphere(ctx);
-        cudaStream_t st = ctx->st;
-        { PROF("fft_z_inv"); band_z_inv<T>(s, ccv(ctx->d_tw), ccv(psi), ld, 0, ctx->nb, cv(ctx->d_Zc), st); }
-        { PROF("fft_y_inv"); band_y_inv<T>(s, ccv(ctx->d_tw), cv(ctx->d_Zc), cv(ctx->d_Yp), ctx->nb, st); }
-        ctx->yp_psi = psi;
-        ctx->yp_ld = ld;
-    }
+    static void planes(roks_ctx* ctx, const void* psi, int64_t ld) { inv_planes(ctx, psi, ld); }
 
     // planes_ready: Yp already holds the planes of psi (yp_psi), so the
     // transform starts at the x stage
@@ -367,21 +403,32 @@ struct Impl {
         {
             PROF("fft_x_apply");
             band_x_apply<T>(s, ccv(ctx->d_tw), cv(ctx->d_Yp), static_cast<const T*>(ctx->d_Vk),
-                            ctx->alpha != 0.0 ? ccv(ctx->d_Xx) : nullptr, 0, ctx->nb, ctx->nc,
+                            ctx->alpha != 0.0 ? ccv(ctx->d_Xx) : nullptr, 0, ctx->nbt, ctx->nct, ctx->split_t,
                             T(1.0 / (double(N) * N * N)), st);
         }
         ctx->yp_psi = nullptr;   // the x stage works in place
-        { PROF("fft_y_fwd"); band_y_fwd<T>(s, ccv(ctx->d_tw), cv(ctx->d_Yp), cv(ctx->d_Zc), ctx->nb, st); }
+        { PROF("fft_y_fwd"); band_y_fwd<T>(s, ccv(ctx->d_tw), cv(ctx->d_Yp), cv(ctx->d_Zc), ctx->nbt, st); }
         {
             PROF("fft_z_fwd");
-            band_z_fwd<T>(s, ccv(ctx->d_tw), cv(ctx->d_Zc), cv(F), ldf, p, ld, static_cast<const T*>(ctx->d_g2half),
-                          static_cast<const T*>(ctx->d_wk), 0, ctx->nb, ctx->nc, st);
+            if (ctx->gamma) {
+                // packed transforms on the full sphere, then each real
+                // orbital's half with its kinetic term
+                band_z_fwd<T>(s, ccv(ctx->d_tw), cv(ctx->d_Zc), cv(ctx->d_Cpk), ctx->ldc_pk, nullptr, 0,
+                              static_cast<const T*>(ctx->d_g2half), static_cast<const T*>(ctx->d_wk), 0, ctx->nbt,
+                              ctx->nct, st);
+                gamma_unpack<T>(ctx->npw, ctx->h0, ctx->nb, ctx->nc, ccv(ctx->d_Cpk), ctx->ldc_pk, p, ld,
+                                static_cast<const T*>(ctx->d_g2half), static_cast<const T*>(ctx->d_wk), cv(F), ldf,
+                                st);
+            } else {
+                band_z_fwd<T>(s, ccv(ctx->d_tw), cv(ctx->d_Zc), cv(F), ldf, p, ld,
+                              static_cast<const T*>(ctx->d_g2half), static_cast<const T*>(ctx->d_wk), 0, ctx->nb,
+                              ctx->nc, st);
+            }
         }
         if (ctx->nproj > 0) {
             if (!reuse_B) {
                 PROF("proj_PhPsi");
-                gemm_cn<T>(ctx->nproj, ctx->nb, ctx->npw, ccv(ctx->d_P), ctx->ld_min, p, ld, ctx->d_B, ctx->nproj,
-                           ctx->d_gemm_work, ctx->gemm_work_elems, st);
+                cn(ctx, ctx->nproj, ctx->nb, ctx->npw, ccv(ctx->d_P), ctx->ld_min, p, ld, ctx->d_B, ctx->nproj, st);
                 ctx->b_psi = psi;
                 ctx->b_ld = ld;
             }
@@ -410,14 +457,12 @@ struct Impl {
         const int nb = ctx->nb;
         {
             PROF("orth_overlap");
-            gemm_cn<T>(nb, nb, ctx->npw, ccv(in), ldi, ccv(in), ldi, ctx->d_O, nb, ctx->d_gemm_work,
-                       ctx->gemm_work_elems, st);
+            cn(ctx, nb, nb, ctx->npw, ccv(in), ldi, ccv(in), ldi, ctx->d_O, nb, st);
         }
         if (ctx->nproj > 0) {
             {
                 PROF("proj_PhPsi");
-                gemm_cn<T>(ctx->nproj, nb, ctx->npw, ccv(ctx->d_P), ctx->ld_min, ccv(in), ldi, ctx->d_B2, ctx->nproj,
-                           ctx->d_gemm_work, ctx->gemm_work_elems, st);
+                cn(ctx, ctx->nproj, nb, ctx->npw, ccv(ctx->d_P), ctx->ld_min, ccv(in), ldi, ctx->d_B2, ctx->nproj, st);
             }
             PROF("orth_small");
             apply_DQ(ctx->nproj, nb, ctx->d_B2, ctx->d_blk_off, ctx->d_blk_n, ctx->d_Drow, ctx->d_Qrow, nullptr,
@@ -488,8 +533,7 @@ struct Impl {
         const int nb = ctx->nb;
         const int64_t l = ctx->ld_min;
         PROF("subspace_project");
-        gemm_cn<T>(nb, nb, ctx->npw, ccv(ctx->W_S), l, ccv(x), l, ctx->d_Msm, nb, ctx->d_gemm_work,
-                   ctx->gemm_work_elems, st);
+        cn(ctx, nb, nb, ctx->npw, ccv(ctx->W_S), l, ccv(x), l, ctx->d_Msm, nb, st);
         gemm_nn_io<T>(ctx->npw, nb, nb, ccv(psi), ld, ctx->d_Msm, nb, ccv(x), l, cv(out), l, -1.0, 1.0,
                       ctx->d_gemm_work, st, ctx->gemm_work_elems * sizeof(double2));
     }
@@ -571,8 +615,7 @@ struct Impl {
         if (r != ROKS_OK) return r;
         {
             PROF("subspace_theta");
-            gemm_cn<T>(nb, nb, npw, ccv(psi), ld, ccv(ctx->W_F), l, ctx->d_Th, nb, ctx->d_gemm_work,
-                       ctx->gemm_work_elems, st);
+            cn(ctx, nb, nb, npw, ccv(psi), ld, ccv(ctx->W_F), l, ctx->d_Th, nb, st);
         }
         const int ia = (ctx->mode == ROKS_MODE_SINGLET) ? ctx->nc : -1;
         const int ib = (ctx->mode == ROKS_MODE_SINGLET) ? ctx->nc + 1 : -1;
@@ -696,8 +739,7 @@ struct Impl {
         if (ctx->nproj > 0 && !(ctx->b_psi == psi && ctx->b_ld == ld)) {
             // the iteration reuses P^H psi from d_B: form it if another call replaced it
             PROF("proj_PhPsi");
-            gemm_cn<T>(ctx->nproj, ctx->nb, ctx->npw, ccv(ctx->d_P), ctx->ld_min, ccv(psi), ld, ctx->d_B, ctx->nproj,
-                       ctx->d_gemm_work, ctx->gemm_work_elems, st);
+            cn(ctx, ctx->nproj, ctx->nb, ctx->npw, ccv(ctx->d_P), ctx->ld_min, ccv(psi), ld, ctx->d_B, ctx->nproj, st);
             ctx->b_psi = psi;
             ctx->b_ld = ld;
         }
@@ -784,14 +826,13 @@ struct Impl {
         const double b = 2.0 * M_PI / ctx->L;
         {
             PROF("force");
-            gemm_cn<T>(nb, nb, npw, ccv(psi), ld, ccv(ctx->W_F), l, ctx->d_Th, nb, ctx->d_gemm_work,
-                       ctx->gemm_work_elems, st);
+            cn(ctx, nb, nb, npw, ccv(psi), ld, ccv(ctx->W_F), l, ctx->d_Th, nb, st);
             diis_multipliers(nb, ctx->d_Th, -1, -1, 0.5, 0.5, ctx->d_Gam, st);   // Gam = (theta + theta^H)/2
             if (np_ > 0) {
                 for (int nu = 0; nu < 3; ++nu) {
                     force_dP<T>(npw, np_, ccv(ctx->d_P), l, ctx->d_miller, b, nu, cv(ctx->d_fdP), st);
-                    gemm_cn<T>(np_, nb, npw, ccv(ctx->d_fdP), l, ccv(psi), ld, ctx->d_fdB + (int64_t)nu * np_ * nb,
-                               np_, ctx->d_gemm_work, ctx->gemm_work_elems, st);
+                    cn(ctx, np_, nb, npw, ccv(ctx->d_fdP), l, ccv(psi), ld, ctx->d_fdB + (int64_t)nu * np_ * nb, np_,
+                       st);
                 }
                 apply_DQ(np_, nb, ctx->d_B, ctx->d_blk_off, ctx->d_blk_n, ctx->d_Drow, ctx->d_Qrow, ctx->d_wband,
                          ctx->d_DB, ctx->d_QB, st);
@@ -837,8 +878,7 @@ struct Impl {
         }
         if (ctx->nproj > 0 && !(ctx->b_psi == psi && ctx->b_ld == ld)) {
             PROF("proj_PhPsi");
-            gemm_cn<T>(ctx->nproj, nb, npw, ccv(ctx->d_P), ctx->ld_min, ccv(psi), ld, ctx->d_B, ctx->nproj,
-                       ctx->d_gemm_work, ctx->gemm_work_elems, st);
+            cn(ctx, ctx->nproj, nb, npw, ccv(ctx->d_P), ctx->ld_min, ccv(psi), ld, ctx->d_B, ctx->nproj, st);
             ctx->b_psi = psi;
             ctx->b_ld = ld;
         }
@@ -847,8 +887,7 @@ struct Impl {
         if (r != ROKS_OK) return r;
         {
             PROF("subspace_theta");
-            gemm_cn<T>(nb, nb, npw, ccv(psi), ld, ccv(ctx->W_F), l, ctx->d_Th, nb, ctx->d_gemm_work,
-                       ctx->gemm_work_elems, st);
+            cn(ctx, nb, nb, npw, ccv(psi), ld, ccv(ctx->W_F), l, ctx->d_Th, nb, st);
         }
         const int slot = int(ctx->diis_count % o.history);
         V* Pj = cv(ctx->diis_ring) + slot * blk;
@@ -1003,12 +1042,12 @@ roks_status autotune(roks_ctx* ctx) {
     if (ctx->prec == ROKS_FP64)
         ctx->dens_groups = pick_fastest(ctx, g_cand, 3, ctx->tune_ms, [&](int g) {
             band_x_density<double>(s, static_cast<const double2*>(ctx->d_tw), static_cast<double2*>(ctx->d_Yp),
-                                   ctx->d_rho3, ctx->d_rho_slot, g, 0, ctx->nb, ctx->nc, 1.0 / ctx->omega, ctx->st);
+                                   ctx->d_rho3, ctx->d_rho_slot, g, 0, ctx->nbt, ctx->nct, 1.0 / ctx->omega, ctx->st);
         });
     else
         ctx->dens_groups = pick_fastest(ctx, g_cand, 3, ctx->tune_ms, [&](int g) {
             band_x_density<float>(s, static_cast<const float2*>(ctx->d_tw), static_cast<float2*>(ctx->d_Yp),
-                                  ctx->d_rho3, ctx->d_rho_slot, g, 0, ctx->nb, ctx->nc, 1.0 / ctx->omega, ctx->st);
+                                  ctx->d_rho3, ctx->d_rho_slot, g, 0, ctx->nbt, ctx->nct, 1.0 / ctx->omega, ctx->st);
         });
     // the largest A^H B product of a step that runs on the tensor cores
     const int M = ctx->nproj >= ctx->nb ? ctx->nproj : ctx->nb;
@@ -1050,6 +1089,10 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     if (opt->precond != ROKS_PRECOND_TPA && opt->precond != ROKS_PRECOND_TPA_MLP) return ROKS_EINVAL;
     if (opt->exx_kernel != ROKS_EXX_TRUNCATED && opt->exx_kernel != ROKS_EXX_BARE) return ROKS_EINVAL;
     if (opt->autotune != 0 && opt->autotune != 1) return ROKS_EINVAL;
+    if (opt->gamma != 0 && opt->gamma != 1) return ROKS_EINVAL;
+    // the Gamma-point packing pairs bands (2k, 2k + 1): an open pair must be
+    // one packed band, and exact exchange runs on the complex path only
+    if (opt->gamma && (opt->alpha != 0.0 || (occ->mode != ROKS_MODE_GS && (occ->n_closed & 1)))) return ROKS_EINVAL;
     roks_ctx* ctx = new (std::nothrow) roks_ctx();
     if (!ctx) return ROKS_ENOMEM;
     ctx->st = static_cast<cudaStream_t>(cuda_stream);
@@ -1071,6 +1114,7 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     ctx->wait_cap = opt->wait_cap;
     ctx->exx_kernel = opt->exx_kernel;
     ctx->autotune = opt->autotune;
+    ctx->gamma = opt->gamma;
     ctx->mlp_kind = opt->precond;   // all-zero network weights until trained ones are set
     ctx->suppress_ab = opt->suppress_ab;
     ctx->mode = occ->mode;
@@ -1108,10 +1152,30 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
         }
     }
     ctx->npw = (int)(ctx->miller.size() / 3);
+    ctx->npw_full = ctx->npw;
+    if (ctx->gamma) {
+        // the half sphere: G = 0 (row h0, the middle of the symmetric,
+        // lexicographically sorted basis) and every row after it
+        ctx->h0 = (ctx->npw - 1) / 2;
+        const int32_t* g0 = &ctx->miller[3 * (size_t)ctx->h0];
+        if (g0[0] != 0 || g0[1] != 0 || g0[2] != 0) return bail(ROKS_EINVAL, "basis without G = 0 at its middle");
+        ctx->miller.erase(ctx->miller.begin(), ctx->miller.begin() + 3 * (size_t)ctx->h0);
+        ctx->npw = ctx->npw_full - ctx->h0;
+    }
     ctx->ld_min = (ctx->npw + 31) / 32 * 32;
     ctx->ncol = (int)col_kmax.size();
     ctx->np = 2 * n + 1;
     if (ctx->nb > ctx->npw) return bail(ROKS_EINVAL, "more bands than plane waves");
+    if (ctx->gamma) {
+        ctx->nbt = (ctx->nb + 1) / 2;
+        ctx->nct = ctx->mode == ROKS_MODE_GS ? ctx->nbt : ctx->nc / 2;
+        ctx->split_t = ctx->mode == ROKS_MODE_GS ? -1 : ctx->nc / 2;
+        ctx->ldc_pk = ((int64_t)ctx->npw_full + 31) / 32 * 32;
+    } else {
+        ctx->nbt = ctx->nb;
+        ctx->nct = ctx->nc;
+        ctx->split_t = -1;
+    }
     // -------- occupations (Eqs. 7, 13): f table and c_L
     const double ftab[3][4] = {{1, 1, 1, 1}, {1, 0, 1, 0}, {0, 1, 1, 0}};
     ctx->cM = occ->mode == 0 ? 1.0 : (occ->mode == 1 ? 2.0 : 0.0);
@@ -1206,8 +1270,9 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     AL(ctx->d_Qrow, sizeof(double) * (Qrow.size() + 1));
     AL(ctx->d_tw, cs * N);
     AL(ctx->d_tw64, sizeof(double2) * N);
-    AL(ctx->d_Zc, cs * (size_t)nb * ctx->ncol * N);
-    AL(ctx->d_Yp, cs * (size_t)nb * ctx->np * N * N);
+    AL(ctx->d_Zc, cs * (size_t)ctx->nbt * ctx->ncol * N);
+    AL(ctx->d_Yp, cs * (size_t)ctx->nbt * ctx->np * N * N);
+    if (ctx->gamma) AL(ctx->d_Cpk, cs * (size_t)ctx->ldc_pk * ctx->nbt);
     AL(ctx->d_rho3, sizeof(double) * 3 * N3);
     AL(ctx->d_rho_slot, sizeof(double) * (opt->autotune ? kDensityGroupsMax : kDensityGroups) * N3);
     AL(ctx->d_xc3, sizeof(double) * 3 * N3);
@@ -1359,6 +1424,11 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
                                       static_cast<double2*>(ctx->d_P), l, ctx->st);
     else projectors_setup<float>(npw, ctx->nproj, cell->L, ctx->d_miller, d_proj, static_cast<float2*>(ctx->d_P), l,
                                  ctx->st);
+    if (ctx->gamma && ctx->nproj > 0) {
+        // real-space-real projectors in the stored half-sphere form
+        if (f64) gamma_scale_rows<double>(npw, ctx->nproj, static_cast<double2*>(ctx->d_P), l, ctx->st);
+        else gamma_scale_rows<float>(npw, ctx->nproj, static_cast<float2*>(ctx->d_P), l, ctx->st);
+    }
     if (opt->alpha != 0.0) {
         const int bare = opt->exx_kernel == ROKS_EXX_BARE ? 1 : 0;
         if (f64) exx_setup_kernel<double>(N, cell->L, bare, static_cast<double*>(ctx->d_vG), ctx->st);
@@ -1427,6 +1497,11 @@ roks_status roks_init_orbitals(roks_ctx* ctx, const double* u_host, void* psi, i
         else
             init_orbitals<float>(ctx->npw, b0, nbk, u, ctx->seed, ctx->d_g2, static_cast<float2*>(ctx->W_Y), l,
                                  ctx->st);
+    }
+    if (ctx->gamma) {
+        // real orbitals: c(0) real, the other half-sphere rows in the stored form
+        if (f64) gamma_scale_rows<double>(ctx->npw, ctx->nb, static_cast<double2*>(ctx->W_Y), l, ctx->st);
+        else gamma_scale_rows<float>(ctx->npw, ctx->nb, static_cast<float2*>(ctx->W_Y), l, ctx->st);
     }
     CK(cudaGetLastError());
     r = f64 ? Impl<double>::orth(ctx, ctx->W_Y, l, psi, ld, nullptr) : Impl<float>::orth(ctx, ctx->W_Y, l, psi, ld, nullptr);
@@ -1509,6 +1584,7 @@ roks_status roks_apply_h(roks_ctx* ctx, const void* psi, int64_t ld, void* fpsi,
         gemm_cn<float>(nb, nb, ctx->npw, static_cast<const float2*>(psi), ld, static_cast<const float2*>(fpsi), ld,
                        ctx->d_Th, nb, ctx->d_gemm_work, ctx->gemm_work_elems, ctx->st);
     }
+    if (ctx->gamma) gamma_real_part(nb, nb, ctx->d_Th, nb, ctx->st);
     CK(cudaMemcpyAsync(ctx->d_Gam, ctx->d_Th, sizeof(double2) * nb * nb, cudaMemcpyDeviceToDevice, ctx->st));
     hermitize(nb, ctx->d_Gam, ctx->st);
     const size_t es = ctx->prec == ROKS_FP64 ? sizeof(double2) : sizeof(float2);

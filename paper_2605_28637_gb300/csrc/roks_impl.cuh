@@ -63,10 +63,11 @@ void band_z_inv(const Sphere& s, const c2<T>* tw, const c2<T>* psi, int64_t ld, 
 template <typename T>
 void band_y_inv(const Sphere& s, const c2<T>* tw, const c2<T>* Zc, c2<T>* Yp, int nbb, cudaStream_t st);
 // x stage, in place on Yp: inverse transform, multiply by V^{class(b)} * scale,
-// forward transform, keep the planes of the sphere
+// forward transform, keep the planes of the sphere.  Band split_band (-1:
+// none) holds two real orbitals as (re, im): re is multiplied by V^a, im by V^b.
 template <typename T>
 void band_x_apply(const Sphere& s, const c2<T>* tw, c2<T>* Yp, const T* Vk, const c2<T>* Xx, int b0, int nbb,
-                  int n_closed, T scale, cudaStream_t st);
+                  int n_closed, int split_band, T scale, cudaStream_t st);
 // x stage, inverse, full real-space lines: Phi[b0 + b] = scale * psi~ (N^3 each)
 template <typename T>
 void band_x_inv_full(const Sphere& s, const c2<T>* tw, const c2<T>* Yp, c2<T>* Phi, int b0, int nbb, T scale,
@@ -75,6 +76,7 @@ void band_x_inv_full(const Sphere& s, const c2<T>* tw, const c2<T>* Yp, c2<T>* P
 template <typename T>
 void band_y_fwd(const Sphere& s, const c2<T>* tw, const c2<T>* Yp, c2<T>* Zc, int nbb, cudaStream_t st);
 // z stage, forward: Zc -> out[b] = gathered coefficients + wk[class] g2half psi[b]
+// (psi null: the gathered coefficients alone)
 template <typename T>
 void band_z_fwd(const Sphere& s, const c2<T>* tw, const c2<T>* Zc, c2<T>* out, int64_t ldo, const c2<T>* psi,
                 int64_t ldp, const T* g2half, const T* wk, int b0, int nbb, int n_closed, cudaStream_t st);
@@ -110,12 +112,42 @@ template <> struct DensAcc<float> {
 // x stage, inverse: rho3 (3 x N^3 DensAcc<T>::S, in a buffer of doubles) =
 // sum |psi|^2 * scale per class, bands split into up to ngroups groups; slot
 // holds ngroups x N^3 values.  rho3 classes a, b must be zero on entry (class
-// 0 is overwritten).
+// 0 is overwritten).  part_sel 1 / 2 sums (Re psi)^2 / (Im psi)^2 instead of
+// |psi|^2, and cls_override >= 0 sends every band to that class of rho3
+// (with slot null: no group slots; the Gamma-point open pair).
 constexpr int kDensityGroups = 4;
 constexpr int kDensityGroupsMax = 8;   // the autotuner's largest candidate
 template <typename T>
 void band_x_density(const Sphere& s, const c2<T>* tw, const c2<T>* Yp, double* rho3, double* slot, int ngroups,
-                    int b0, int nbb, int n_closed, double scale, cudaStream_t st);
+                    int b0, int nbb, int n_closed, double scale, cudaStream_t st, int part_sel = 0,
+                    int cls_override = -1);
+
+// ------------------------------------------------------------ Gamma point (k_gamma.cu)
+// Real orbitals are stored on the half sphere (G = 0 and the Miller triples
+// after it in the basis order, the contiguous tail of the full basis from
+// row h0 = (npw_full - 1) / 2), with every coefficient of G != 0 scaled by
+// sqrt 2.  With that scaling the real part of a half-sphere sum of
+// conj(a) b equals the full-sphere inner product of the real orbitals, so
+// the contractions, norms and dot products of the complex path carry over.
+// The partner -G of full row h0 + h is row h0 - h.
+//
+// Cpk[k] (full sphere, ldc) = a + i b for the bands a = 2k, b = 2k + 1 (b
+// absent: 0), unscaled and expanded with c(-G) = conj(c(G)).
+template <typename T>
+void gamma_expand(int nh, int h0, int nb, const c2<T>* psi, int64_t ld, c2<T>* Cpk, int64_t ldc, cudaStream_t st);
+// F[n] (half sphere, scaled) = the transform of real orbital n taken out of
+// the packed transform Fpk[n / 2] (A = (X + conj X~) / 2 for the real part,
+// (X - conj X~) / 2i for the imaginary one, X~ the -G entry), plus the
+// kinetic term wk[class(n)] g2half psi[n].
+template <typename T>
+void gamma_unpack(int nh, int h0, int nb, int n_closed, const c2<T>* Fpk, int64_t ldc, const c2<T>* psi,
+                  int64_t ldp, const T* g2half, const T* wk, c2<T>* F, int64_t ldf, cudaStream_t st);
+// rows 1 .. nh-1 of ncols columns times sqrt 2; row 0 (G = 0) keeps its real
+// part only (the half-sphere form of a real-space-real set)
+template <typename T>
+void gamma_scale_rows(int nh, int ncols, c2<T>* X, int64_t ld, cudaStream_t st);
+// C (M x N, ldc) <- Re C: the band-space products of real orbitals
+void gamma_real_part(int M, int N, double2* C, int ldc, cudaStream_t st);
 
 // ------------------------------------------------------------ full-grid 3D FFT (in place)
 template <typename T>
