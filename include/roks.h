@@ -249,6 +249,15 @@ ROKS_API roks_status roks_potential(roks_ctx* ctx, roks_energies* e, void* vclas
 ROKS_API roks_status roks_apply_h(roks_ctx* ctx, const void* psi, int64_t ld,
                          void* fpsi, void* spsi, void* grad);
 
+/* roks_apply_h with both gradients of the step (Eqs. 7, 11, 12), from
+ * theta = Psi^H F Psi: grad = F|n> - sum_m S|m> gamma_nm (gamma = (theta +
+ * theta^H) / 2) and grad_I = F|n> - sum_m S|m> theta_mn, the part the
+ * preconditioner of Eq. 16 takes.  spsi, grad and grad_I may each be NULL;
+ * fpsi may not.  Device arrays with the same ld as psi; the call also leaves
+ * theta for roks_precondition's band energies. */
+ROKS_API roks_status roks_gradient_parts(roks_ctx* ctx, const void* psi, int64_t ld, void* fpsi, void* spsi,
+                                void* grad, void* grad_I);
+
 /* In place S-orthonormalisation: O = Psi^H S Psi = L L^H (Cholesky: FP64
  * on the FP64 path; on the mixed path FP32 in deviation form up to 64 bands
  * and blocked FP32 beyond), Psi <- Psi L^{-H}; band order closed, a, b.

@@ -34,13 +34,19 @@ __global__ void k_big_load(int n, const double2* __restrict__ O, U* __restrict__
     A[idx] = ld_as<U>(make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y)));
 }
 
-// Factor the diagonal block kb (one block): L_kk and D = L_kk^{-1} (BK x BK).
+// Factor the diagonal block kb (one block): L_kk, and D = L_kk^{-1} by a
+// column sweep in the same loop (solve L D = I for all right-hand sides at
+// once: row j of D is scaled by 1/L_jj as soon as column j of L is final,
+// then subtracted from the rows below).  Every thread forms the pivot
+// itself, so a step needs two barriers.  D goes to Dinv and to X = L^{-1}
+// (block kb, kb).
 template <typename U>
-__global__ void __launch_bounds__(256) k_big_diag(int n, int kb, U* __restrict__ A, U* __restrict__ Dinv, int* flag) {
+__global__ void __launch_bounds__(256) k_big_diag(int n, int kb, U* __restrict__ A, U* __restrict__ Dinv,
+                                                  U* __restrict__ Xm, int* flag) {
     using R = typename Real<U>::type;
-    __shared__ U L[BK][BK + 1];
-    __shared__ U X[BK][BK + 1];
-    __shared__ R piv_inv[BK];
+    __shared__ U L[BK][BK + 1];   // L[col][row]
+    __shared__ U X[BK][BK + 1];   // X[col][row]
+    __shared__ R piv[BK];
     const int k0 = kb * BK;
     const int m = min(BK, n - k0);
     for (int t = threadIdx.x; t < BK * BK; t += blockDim.x) {
@@ -48,194 +54,200 @@ __global__ void __launch_bounds__(256) k_big_diag(int n, int kb, U* __restrict__
         U v;
         v.x = 0; v.y = 0;
         if (i < m && j < m) v = A[(int64_t)(k0 + j) * n + k0 + i];
-        L[j][i] = v;                 // L[col][row]
+        L[j][i] = v;
         U z; z.x = (i == j) ? R(1) : R(0); z.y = 0;
         X[j][i] = z;
     }
     __syncthreads();
     for (int j = 0; j < m; ++j) {
-        if (threadIdx.x == 0) {
-            R d = L[j][j].x;
-            if (!(d > R(0))) {
-                if (flag) atomicCAS(flag, 0, k0 + j + 1);
-                d = R(1);
-            }
-            const R p = sqrt(d);
-            L[j][j].x = p;
-            L[j][j].y = 0;
-            piv_inv[j] = R(1) / p;
+        R d = L[j][j].x;
+        if (!(d > R(0))) {
+            if (threadIdx.x == 0 && flag) atomicCAS(flag, 0, k0 + j + 1);
+            d = R(1);
         }
-        __syncthreads();
-        const R inv = piv_inv[j];
-        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
-            L[j][i].x *= inv;
-            L[j][i].y *= inv;
-        }
-        __syncthreads();
+        const R p = sqrt(d);
+        const R inv = R(1) / p;
+        if (threadIdx.x == 0) piv[j] = p;
+        // column j of L below the diagonal, row j of D (columns c <= j)
         const int r = m - j - 1;
-        for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
-            const int i = j + 1 + t % r, k = j + 1 + t / r;
-            if (k > i) continue;
-            const U a = L[j][i], b = L[j][k];
-            L[k][i].x -= a.x * b.x + a.y * b.y;
-            L[k][i].y -= a.y * b.x - a.x * b.y;
+        for (int t = threadIdx.x; t < r + j + 1; t += blockDim.x) {
+            if (t < r) {
+                L[j][j + 1 + t].x *= inv;
+                L[j][j + 1 + t].y *= inv;
+            } else {
+                const int c = t - r;
+                X[c][j].x *= inv;
+                X[c][j].y *= inv;
+            }
+        }
+        __syncthreads();
+        // trailing L (j < k <= i) and the rows i > j of D (columns c <= j)
+        for (int t = threadIdx.x; t < r * r + r * (j + 1); t += blockDim.x) {
+            if (t < r * r) {
+                const int i = j + 1 + t % r, k = j + 1 + t / r;
+                if (k > i) continue;
+                const U a = L[j][i], b = L[j][k];
+                L[k][i].x -= a.x * b.x + a.y * b.y;
+                L[k][i].y -= a.y * b.x - a.x * b.y;
+            } else {
+                const int q = t - r * r;
+                const int i = j + 1 + q % r, c = q / r;
+                const U a = L[j][i], x = X[c][j];
+                X[c][i].x -= a.x * x.x - a.y * x.y;
+                X[c][i].y -= a.x * x.y + a.y * x.x;
+            }
         }
         __syncthreads();
     }
-    // X = L^{-1}: column c by one thread (BK <= 32 columns)
-    if (threadIdx.x < m) {
-        const int c = threadIdx.x;
-        for (int i = c; i < m; ++i) {
-            R sr = (i == c) ? R(1) : R(0), si = 0;
-            for (int k = c; k < i; ++k) {
-                const U l = L[k][i], x = X[c][k];
-                sr -= l.x * x.x - l.y * x.y;
-                si -= l.x * x.y + l.y * x.x;
-            }
-            X[c][i].x = sr * piv_inv[i];
-            X[c][i].y = si * piv_inv[i];
-        }
-    }
-    __syncthreads();
     for (int t = threadIdx.x; t < BK * BK; t += blockDim.x) {
         const int i = t % BK, j = t / BK;
-        if (i < m && j < m) A[(int64_t)(k0 + j) * n + k0 + i] = L[j][i];
+        if (i < m && j < m) {
+            U l = L[j][i];
+            if (i == j) {
+                l.x = piv[j];
+                l.y = 0;
+            }
+            A[(int64_t)(k0 + j) * n + k0 + i] = l;
+            Xm[(int64_t)(k0 + j) * n + k0 + i] = X[j][i];
+        }
         U z; z.x = 0; z.y = 0;
         Dinv[(int64_t)kb * BK * BK + j * BK + i] = (i < m && j < m) ? X[j][i] : z;
     }
 }
 
-// Panel: L_ik = A_ik D^H for the row blocks i > kb (one block per row block).
+// Blocks 0 .. nt-1, panel: L_ik = A_ik D^H for the row blocks i > kb.
+// Blocks nt .. nt+kb-1, row kb of X = L^{-1}: X_kj = D_kb W_kj for j < kb,
+// in place (W_kj, accumulated in Xm by the updates of the earlier steps,
+// holds -sum_{m<kb} L_km X_mj).
 template <typename U>
-__global__ void __launch_bounds__(256) k_big_panel(int n, int kb, U* __restrict__ A, const U* __restrict__ Dinv) {
+__global__ void __launch_bounds__(256) k_big_panel(int n, int kb, int nt, U* __restrict__ A,
+                                                   const U* __restrict__ Dinv, U* __restrict__ Xm) {
     using R = typename Real<U>::type;
     __shared__ U S[BK][BK + 1];
     __shared__ U Dm[BK][BK + 1];
     const int k0 = kb * BK;
-    const int i0 = (kb + 1 + blockIdx.x) * BK;
-    const int rows = min(BK, n - i0), cols = min(BK, n - k0);
     for (int t = threadIdx.x; t < BK * BK; t += blockDim.x) {
         const int r = t % BK, c = t / BK;
-        U v; v.x = 0; v.y = 0;
-        if (r < rows && c < cols) v = A[(int64_t)(k0 + c) * n + i0 + r];
-        S[c][r] = v;
         Dm[c][r] = Dinv[(int64_t)kb * BK * BK + c * BK + r];
     }
-    __syncthreads();
-    for (int t = threadIdx.x; t < BK * BK; t += blockDim.x) {
-        const int r = t % BK, c = t / BK;
-        if (r >= rows || c >= cols) continue;
-        // (A D^H)_rc = sum_m A_rm conj(D_cm), D lower: m <= c
-        R sr = 0, si = 0;
-        for (int mm = 0; mm <= c; ++mm) {
-            const U a = S[mm][r], d = Dm[mm][c];
-            sr += a.x * d.x + a.y * d.y;
-            si += a.y * d.x - a.x * d.y;
+    if ((int)blockIdx.x < nt) {
+        const int i0 = (kb + 1 + blockIdx.x) * BK;
+        const int rows = min(BK, n - i0), cols = min(BK, n - k0);
+        for (int t = threadIdx.x; t < BK * BK; t += blockDim.x) {
+            const int r = t % BK, c = t / BK;
+            U v; v.x = 0; v.y = 0;
+            if (r < rows && c < cols) v = A[(int64_t)(k0 + c) * n + i0 + r];
+            S[c][r] = v;
         }
-        U o; o.x = sr; o.y = si;
-        A[(int64_t)(k0 + c) * n + i0 + r] = o;
+        __syncthreads();
+        for (int t = threadIdx.x; t < BK * BK; t += blockDim.x) {
+            const int r = t % BK, c = t / BK;
+            if (r >= rows || c >= cols) continue;
+            // (A D^H)_rc = sum_m A_rm conj(D_cm), D lower: m <= c
+            R sr = 0, si = 0;
+            for (int mm = 0; mm <= c; ++mm) {
+                const U a = S[mm][r], d = Dm[mm][c];
+                sr += a.x * d.x + a.y * d.y;
+                si += a.y * d.x - a.x * d.y;
+            }
+            U o; o.x = sr; o.y = si;
+            A[(int64_t)(k0 + c) * n + i0 + r] = o;
+        }
+    } else {
+        const int j0 = (blockIdx.x - nt) * BK;
+        const int rows = min(BK, n - k0);   // j0 + BK <= k0: full columns
+        for (int t = threadIdx.x; t < BK * BK; t += blockDim.x) {
+            const int r = t % BK, c = t / BK;
+            U v; v.x = 0; v.y = 0;
+            if (r < rows) v = Xm[(int64_t)(j0 + c) * n + k0 + r];
+            S[c][r] = v;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < BK * BK; t += blockDim.x) {
+            const int r = t % BK, c = t / BK;
+            if (r >= rows) continue;
+            // (D W)_rc = sum_{m <= r} D_rm W_mc
+            R sr = 0, si = 0;
+            for (int mm = 0; mm <= r; ++mm) {
+                const U d = Dm[mm][r], w = S[c][mm];
+                sr += d.x * w.x - d.y * w.y;
+                si += d.x * w.y + d.y * w.x;
+            }
+            U o; o.x = sr; o.y = si;
+            Xm[(int64_t)(j0 + c) * n + k0 + r] = o;
+        }
     }
 }
 
-// Trailing update: A_ij -= L_ik L_jk^H for block pairs kb < jb <= ib.
+// Blocks 0 .. ntri-1, trailing update: A_ij -= L_ik L_jk^H for the block
+// pairs kb < jb <= ib.  Blocks ntri .. ntri + nt (kb+1) - 1, the inverse's
+// right-looking update: W_ij -= L_ik X_kj for the row blocks i > kb and the
+// column blocks j <= kb (X_kj final after the panel of this step).
 template <typename U>
-__global__ void __launch_bounds__(256) k_big_update(int n, int kb, U* __restrict__ A) {
+__global__ void __launch_bounds__(256) k_big_update(int n, int kb, int nt, U* __restrict__ A, U* __restrict__ Xm) {
     using R = typename Real<U>::type;
     __shared__ U Li[BK][BK + 1];
     __shared__ U Lj[BK][BK + 1];
-    // blockIdx.x enumerates the lower-triangle block pairs of the trailing matrix
-    int t = blockIdx.x, ib = 0;
-    while ((ib + 1) * (ib + 2) / 2 <= t) ++ib;
-    const int jb = t - ib * (ib + 1) / 2;
+    const int ntri = nt * (nt + 1) / 2;
     const int k0 = kb * BK;
-    const int i0 = (kb + 1 + ib) * BK, j0 = (kb + 1 + jb) * BK;
-    const int ri = min(BK, n - i0), rj = min(BK, n - j0), cc = min(BK, n - k0);
-    for (int q = threadIdx.x; q < BK * BK; q += blockDim.x) {
-        const int r = q % BK, c = q / BK;
-        U z; z.x = 0; z.y = 0;
-        Li[c][r] = (r < ri && c < cc) ? A[(int64_t)(k0 + c) * n + i0 + r] : z;
-        Lj[c][r] = (r < rj && c < cc) ? A[(int64_t)(k0 + c) * n + j0 + r] : z;
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < BK * BK; q += blockDim.x) {
-        const int r = q % BK, c = q / BK;
-        if (r >= ri || c >= rj) continue;
-        if (ib == jb && c > r) continue;
-        R sr = 0, si = 0;
-        for (int mm = 0; mm < cc; ++mm) {
-            const U a = Li[mm][r], b = Lj[mm][c];
-            sr += a.x * b.x + a.y * b.y;
-            si += a.y * b.x - a.x * b.y;
-        }
-        U* dst = A + (int64_t)(j0 + c) * n + i0 + r;
-        U o = *dst;
-        o.x -= sr;
-        o.y -= si;
-        *dst = o;
-    }
-}
-
-// Inverse, block row ib: X_ij = -D_i sum_{m=j}^{i-1} L_im X_mj for jb < ib
-// (X_ii = D_i); X lives in the upper... separate buffer Xm (n x n).
-template <typename U>
-__global__ void __launch_bounds__(256) k_big_inv_row(int n, int ib, const U* __restrict__ A,
-                                                     const U* __restrict__ Dinv, U* __restrict__ Xm) {
-    using R = typename Real<U>::type;
-    __shared__ U Sacc[BK][BK + 1];
-    __shared__ U Lt[BK][BK + 1];
-    __shared__ U Xt[BK][BK + 1];
-    const int jb = blockIdx.x;          // 0 .. ib
-    const int i0 = ib * BK, j0 = jb * BK;
-    const int ri = min(BK, n - i0), cj = min(BK, n - j0);
-    if (jb == ib) {
-        for (int q = threadIdx.x; q < BK * BK; q += blockDim.x) {
-            const int r = q % BK, c = q / BK;
-            if (r < ri && c < cj) Xm[(int64_t)(j0 + c) * n + i0 + r] = Dinv[(int64_t)ib * BK * BK + c * BK + r];
-        }
-        return;
-    }
-    R accr[4] = {0, 0, 0, 0}, acci[4] = {0, 0, 0, 0};
-    for (int mb = jb; mb < ib; ++mb) {
-        const int m0 = mb * BK, cm = min(BK, n - m0);
+    const int cc = min(BK, n - k0);
+    if ((int)blockIdx.x < ntri) {
+        // blockIdx.x enumerates the lower-triangle block pairs of the trailing matrix
+        int t = blockIdx.x, ib = 0;
+        while ((ib + 1) * (ib + 2) / 2 <= t) ++ib;
+        const int jb = t - ib * (ib + 1) / 2;
+        const int i0 = (kb + 1 + ib) * BK, j0 = (kb + 1 + jb) * BK;
+        const int ri = min(BK, n - i0), rj = min(BK, n - j0);
         for (int q = threadIdx.x; q < BK * BK; q += blockDim.x) {
             const int r = q % BK, c = q / BK;
             U z; z.x = 0; z.y = 0;
-            Lt[c][r] = (r < ri && c < cm) ? A[(int64_t)(m0 + c) * n + i0 + r] : z;        // L_im (r, c)
-            Xt[c][r] = (r < cm && c < cj) ? Xm[(int64_t)(j0 + c) * n + m0 + r] : z;       // X_mj (r, c)
+            Li[c][r] = (r < ri && c < cc) ? A[(int64_t)(k0 + c) * n + i0 + r] : z;
+            Lj[c][r] = (r < rj && c < cc) ? A[(int64_t)(k0 + c) * n + j0 + r] : z;
         }
         __syncthreads();
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            const int q = threadIdx.x + s * 256;
+        for (int q = threadIdx.x; q < BK * BK; q += blockDim.x) {
             const int r = q % BK, c = q / BK;
-            for (int mm = 0; mm < BK; ++mm) {
-                const U a = Lt[mm][r], b = Xt[c][mm];
-                accr[s] += a.x * b.x - a.y * b.y;
-                acci[s] += a.x * b.y + a.y * b.x;
+            if (r >= ri || c >= rj) continue;
+            if (ib == jb && c > r) continue;
+            R sr = 0, si = 0;
+            for (int mm = 0; mm < cc; ++mm) {
+                const U a = Li[mm][r], b = Lj[mm][c];
+                sr += a.x * b.x + a.y * b.y;
+                si += a.y * b.x - a.x * b.y;
             }
+            U* dst = A + (int64_t)(j0 + c) * n + i0 + r;
+            U o = *dst;
+            o.x -= sr;
+            o.y -= si;
+            *dst = o;
+        }
+    } else {
+        const int q0 = blockIdx.x - ntri;
+        const int i0 = (kb + 1 + q0 % nt) * BK, j0 = (q0 / nt) * BK;
+        const int ri = min(BK, n - i0);
+        // Li: L_ik (r, m); Lj: X_kj stored as [col][row] = X(m, c)
+        for (int q = threadIdx.x; q < BK * BK; q += blockDim.x) {
+            const int r = q % BK, c = q / BK;
+            U z; z.x = 0; z.y = 0;
+            Li[c][r] = (r < ri && c < cc) ? A[(int64_t)(k0 + c) * n + i0 + r] : z;
+            Lj[c][r] = (r < cc) ? Xm[(int64_t)(j0 + c) * n + k0 + r] : z;
         }
         __syncthreads();
-    }
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        const int q = threadIdx.x + s * 256;
-        const int r = q % BK, c = q / BK;
-        U v; v.x = accr[s]; v.y = acci[s];
-        Sacc[c][r] = v;
-    }
-    __syncthreads();
-    const U* D = Dinv + (int64_t)ib * BK * BK;
-    for (int q = threadIdx.x; q < BK * BK; q += blockDim.x) {
-        const int r = q % BK, c = q / BK;
-        if (r >= ri || c >= cj) continue;
-        R sr = 0, si = 0;
-        for (int mm = 0; mm <= r; ++mm) {
-            const U d = D[mm * BK + r], b = Sacc[c][mm];
-            sr += d.x * b.x - d.y * b.y;
-            si += d.x * b.y + d.y * b.x;
+        for (int q = threadIdx.x; q < BK * BK; q += blockDim.x) {
+            const int r = q % BK, c = q / BK;
+            if (r >= ri) continue;
+            R sr = 0, si = 0;
+            for (int mm = 0; mm < cc; ++mm) {
+                const U a = Li[mm][r], x = Lj[c][mm];
+                sr += a.x * x.x - a.y * x.y;
+                si += a.x * x.y + a.y * x.x;
+            }
+            U* dst = Xm + (int64_t)(j0 + c) * n + i0 + r;
+            U o = *dst;
+            o.x -= sr;
+            o.y -= si;
+            *dst = o;
         }
-        U o; o.x = -sr; o.y = -si;
-        Xm[(int64_t)(j0 + c) * n + i0 + r] = o;
     }
 }
 
@@ -253,20 +265,24 @@ __global__ void k_big_store_inverse(int n, const U* __restrict__ Xm, double2* __
     LinvH[idx] = make_double2((double)x.x, -(double)x.y);
 }
 
+// Right-looking blocked Cholesky with the inverse X = L^{-1} formed along
+// the way: step kb factors the diagonal block (and its inverse D_kb), forms
+// the panel below it and row kb of X (X_kj = D_kb W_kj), then updates the
+// trailing matrix and the accumulated rows W_ij -= L_ik X_kj of X below.
+// Three launches per block step, each spread over the blocks it touches.
 template <typename U>
 void cholesky_big_impl(int n, const double2* O, U* A, U* Dinv, U* Xm, double2* LinvH, int* flag, cudaStream_t st) {
     const int nbk = (n + BK - 1) / BK;
     const int blocks = (n * n + 255) / 256;
+    cudaMemsetAsync(Xm, 0, sizeof(U) * (size_t)n * n, st);
     roks::count_launch(), k_big_load<U><<<blocks, 256, 0, st>>>(n, O, A);
     for (int kb = 0; kb < nbk; ++kb) {
-        roks::count_launch(), k_big_diag<U><<<1, 256, 0, st>>>(n, kb, A, Dinv, flag);
+        roks::count_launch(), k_big_diag<U><<<1, 256, 0, st>>>(n, kb, A, Dinv, Xm, flag);
         const int nt = nbk - kb - 1;
-        if (nt > 0) {
-            roks::count_launch(), k_big_panel<U><<<nt, 256, 0, st>>>(n, kb, A, Dinv);
-            roks::count_launch(), k_big_update<U><<<nt * (nt + 1) / 2, 256, 0, st>>>(n, kb, A);
-        }
+        if (nt + kb > 0) roks::count_launch(), k_big_panel<U><<<nt + kb, 256, 0, st>>>(n, kb, nt, A, Dinv, Xm);
+        if (nt > 0)
+            roks::count_launch(), k_big_update<U><<<nt * (nt + 1) / 2 + nt * (kb + 1), 256, 0, st>>>(n, kb, nt, A, Xm);
     }
-    for (int ib = 0; ib < nbk; ++ib) roks::count_launch(), k_big_inv_row<U><<<ib + 1, 256, 0, st>>>(n, ib, A, Dinv, Xm);
     roks::count_launch(), k_big_store_inverse<U><<<blocks, 256, 0, st>>>(n, Xm, LinvH);
 }
 
@@ -294,52 +310,58 @@ void cholesky_inverse_big(int n, const double2* O, void* work, bool fp64, double
 }
 
 // ------------------------------------------------------------------ matrix exponential, large n
-// C = alpha A B (+ I when add_identity), n x n, 32 x 32 output tiles per
-// block of 256 threads, thread (tx, ty) owning rows ty + 16 i and columns
-// tx + 16 j (i, j < 2), K in slices of 16 staged in shared memory (two
-// shared-memory loads per complex multiply-add pair of the tile).  With
-// guard, launches past the device's squaring count copy A through.
-constexpr int SQ_K = 16;
+// C = alpha A B (+ D when D is given) (+ I when add_identity), n x n.  A
+// block owns a 16 x 16 output tile and splits K over four groups of 64
+// threads (contiguous K ranges, 16-deep slices staged in shared memory);
+// each thread keeps a 2 x 2 complex tile, and the four partial tiles are
+// added in group order at the end (deterministic).  At n = 430 this is 729
+// blocks, enough to keep every SM busy, where 32 x 32 tiles over all of K
+// gave 196 blocks with one slice in flight each.  With guard, launches past
+// the device's squaring count (guard[0]) return at once: the result then
+// stays in the buffer the last real squaring wrote (k_big_to_double picks it).
+constexpr int SQ_T = 16;   // output tile
+constexpr int SQ_K = 16;   // K slice
+constexpr int SQ_G = 4;    // K groups per block
 
 template <typename U>
 __global__ void __launch_bounds__(256) k_sq_gemm(int n, const U* __restrict__ A, const U* __restrict__ B,
-                                                 U* __restrict__ C, typename Real<U>::type alpha, int add_identity,
+                                                 U* __restrict__ C, typename Real<U>::type alpha,
+                                                 const U* __restrict__ D, int add_identity,
                                                  const double* __restrict__ guard, int step) {
     using R = typename Real<U>::type;
-    __shared__ U As[SQ_K][BK + 1];
-    __shared__ U Bs[SQ_K][BK + 1];
-    const int i0 = blockIdx.x * BK, j0 = blockIdx.y * BK;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    if (guard && step >= int(guard[0])) {
-        // squaring beyond q: copy through
-        for (int q = threadIdx.x; q < BK * BK; q += blockDim.x) {
-            const int r = q % BK, c = q / BK;
-            if (i0 + r < n && j0 + c < n) C[(int64_t)(j0 + c) * n + i0 + r] = A[(int64_t)(j0 + c) * n + i0 + r];
-        }
-        return;
-    }
+    __shared__ U As[SQ_G][SQ_K][SQ_T + 1];
+    __shared__ U Bs[SQ_G][SQ_K][SQ_T + 1];
+    if (guard && step >= int(guard[0])) return;
+    const int i0 = blockIdx.x * SQ_T, j0 = blockIdx.y * SQ_T;
+    const int g = threadIdx.x >> 6, t = threadIdx.x & 63;
+    const int tx = t & 7, ty = t >> 3;
+    // K range of group g: [kb, ke), the same slice count for every group
+    const int kr = ((n + SQ_G - 1) / SQ_G + SQ_K - 1) / SQ_K * SQ_K;
+    const int kb = g * kr, ke = min(n, kb + kr);
     R ar[2][2], ai[2][2];
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < 2; ++b) ar[a][b] = ai[a][b] = R(0);
-    for (int k0 = 0; k0 < n; k0 += SQ_K) {
-        for (int q = threadIdx.x; q < BK * SQ_K; q += blockDim.x) {
-            // A(i0 + r, k0 + c): rows contiguous; B(k0 + c, j0 + r): K contiguous
-            const int r = q % BK, c = q / BK;
+    for (int k0 = 0; k0 < kr; k0 += SQ_K) {
+#pragma unroll
+        for (int q = t; q < SQ_T * SQ_K; q += 64) {
+            // A(i0 + r, kb + k0 + c): rows contiguous; B(kb + k0 + kk, j0 + c): K contiguous
+            const int r = q % SQ_T, c = q / SQ_T;
+            const int ka = kb + k0 + c;
             U z;
             z.x = 0;
             z.y = 0;
-            As[c][r] = (i0 + r < n && k0 + c < n) ? A[(int64_t)(k0 + c) * n + i0 + r] : z;
-            const int kr = q % SQ_K, jc = q / SQ_K;
-            Bs[kr][jc] = (k0 + kr < n && j0 + jc < n) ? B[(int64_t)(j0 + jc) * n + k0 + kr] : z;
+            As[g][c][r] = (i0 + r < n && ka < ke) ? A[(int64_t)ka * n + i0 + r] : z;
+            const int kk = q % SQ_K, jc = q / SQ_K;
+            const int kbb = kb + k0 + kk;
+            Bs[g][kk][jc] = (kbb < ke && j0 + jc < n) ? B[(int64_t)(j0 + jc) * n + kbb] : z;
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < SQ_K; ++kk) {
-            const U a0 = As[kk][ty], a1 = As[kk][ty + 16];
-            const U b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
-            const U av[2] = {a0, a1}, bv[2] = {b0, b1};
+            const U av[2] = {As[g][kk][ty], As[g][kk][ty + 8]};
+            const U bv[2] = {Bs[g][kk][tx], Bs[g][kk][tx + 8]};
 #pragma unroll
             for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -350,18 +372,57 @@ __global__ void __launch_bounds__(256) k_sq_gemm(int n, const U* __restrict__ A,
         }
         __syncthreads();
     }
+    // partial tiles of the groups, added in group order by group 0
+    U* part = &As[0][0][0];   // SQ_G x SQ_T x SQ_T fits in As (SQ_K >= SQ_T)
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-            const int r = ty + 16 * a, c = tx + 16 * b;
-            if (i0 + r < n && j0 + c < n) {
-                U o;
-                o.x = alpha * ar[a][b] + ((add_identity && i0 + r == j0 + c) ? R(1) : R(0));
-                o.y = alpha * ai[a][b];
-                C[(int64_t)(j0 + c) * n + i0 + r] = o;
-            }
+            U v;
+            v.x = ar[a][b];
+            v.y = ai[a][b];
+            part[(g * SQ_T + ty + 8 * a) * SQ_T + tx + 8 * b] = v;
         }
+    __syncthreads();
+    if (g != 0) return;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int r = ty + 8 * a, c = tx + 8 * b;
+            if (i0 + r >= n || j0 + c >= n) continue;
+            R sr = 0, si = 0;
+            for (int gg = 0; gg < SQ_G; ++gg) {
+                const U v = part[(gg * SQ_T + r) * SQ_T + c];
+                sr += v.x;
+                si += v.y;
+            }
+            const int64_t idx = (int64_t)(j0 + c) * n + i0 + r;
+            U o;
+            o.x = alpha * sr + ((add_identity && i0 + r == j0 + c) ? R(1) : R(0));
+            o.y = alpha * si;
+            if (D) {
+                o.x += D[idx].x;
+                o.y += D[idx].y;
+            }
+            C[idx] = o;
+        }
+}
+
+// Paterson-Stockmeyer blocks of the Taylor polynomial: B = c0 I + c1 X +
+// c2 X^2 + c3 X^3 + c4 X^4 (elementwise over the four powers).
+template <typename U>
+__global__ void k_big_ps_block(int n, const U* __restrict__ X1, const U* __restrict__ X2, const U* __restrict__ X3,
+                               const U* __restrict__ X4, typename Real<U>::type c0, typename Real<U>::type c1,
+                               typename Real<U>::type c2, typename Real<U>::type c3, typename Real<U>::type c4,
+                               U* __restrict__ Bo) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * n) return;
+    const int r = idx % n, c = idx / n;
+    U o;
+    o.x = c1 * X1[idx].x + c2 * X2[idx].x + c3 * X3[idx].x + c4 * X4[idx].x + (r == c ? c0 : 0);
+    o.y = c1 * X1[idx].y + c2 * X2[idx].y + c3 * X3[idx].y + c4 * X4[idx].y;
+    Bo[idx] = o;
 }
 
 // Column sums sum_r (|Re a| + |Im a|) of A (a bound of the 1-norm with
@@ -380,13 +441,12 @@ __global__ void k_big_colsum(int n, const double2* __restrict__ A, double* __res
     if (lane == 0) colsum[c] = sum;
 }
 
-// X = s A / 2^q with ||s A||_1 / 2^q <= 1/4 (q on the device in info[0]);
-// P = I + X / degree.  Every block finds the largest column sum itself
-// (n values) and fills its share of the elements.
+// X = s A / 2^q with ||s A||_1 / 2^q <= 1/4 (q on the device in info[0]).
+// Every block finds the largest column sum itself (n values) and fills its
+// share of the elements.
 template <typename U>
 __global__ void k_big_expm_scale(int n, const double2* __restrict__ A, const double* __restrict__ s,
-                                 const double* __restrict__ colsum, U* __restrict__ X, U* __restrict__ P,
-                                 double* __restrict__ info, int degree) {
+                                 const double* __restrict__ colsum, U* __restrict__ X, double* __restrict__ info) {
     __shared__ double red[256];
     __shared__ double fsh;
     double best = 0.0;
@@ -408,56 +468,87 @@ __global__ void k_big_expm_scale(int n, const double2* __restrict__ A, const dou
         fsh = s[0] * ldexp(1.0, -q);
     }
     __syncthreads();
-    const double f = fsh, fd = fsh / degree;
+    const double f = fsh;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * n; idx += gridDim.x * blockDim.x) {
         const double2 a = A[idx];
         X[idx] = ld_as<U>(make_double2(f * a.x, f * a.y));
-        const int m = idx % n, c = idx / n;
-        P[idx] = ld_as<U>(make_double2((m == c ? 1.0 : 0.0) + fd * a.x, fd * a.y));
     }
 }
 
+// E = the squared polynomial: buffer P0 after an even number of squarings
+// (min(q, max_square), q = info[0]), P1 after an odd one.
 template <typename U>
-__global__ void k_big_to_double(int n, const U* __restrict__ P, double2* __restrict__ E) {
+__global__ void k_big_to_double(int n, const U* __restrict__ P0, const U* __restrict__ P1,
+                                const double* __restrict__ info, int max_square, double2* __restrict__ E) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx < n * n) E[idx] = make_double2((double)P[idx].x, (double)P[idx].y);
+    if (idx >= n * n) return;
+    const int q = min(int(info[0]), max_square);
+    const U v = (q & 1) ? P1[idx] : P0[idx];
+    E[idx] = make_double2((double)v.x, (double)v.y);
 }
 
+// exp(s A) = (p(X))^(2^q), X = s A / 2^q, p the Taylor polynomial of degree
+// 4 r (FP32: r = 2, degree 8; FP64: r = 4, degree 16) evaluated by
+// Paterson-Stockmeyer: X^2, X^3, X^4 (three products), blocks B_j =
+// sum_{i<4} c_{4j+i} X^i (the last one with c_{4r} X^4), then
+// p = B_0 + X^4 (B_1 + X^4 (B_2 + ...)) (r - 1 products), instead of the
+// 4 r - 1 products of Horner's rule.  Work: seven n x n buffers.
 template <typename U>
-void expm_big_impl(int n, const double2* A, const double* s, double2* E, U* X, U* P, U* Q, double* info, int degree,
-                   int max_square, cudaStream_t st) {
+void expm_big_impl(int n, const double2* A, const double* s, double2* E, U* W, double* info, int r, int max_square,
+                   cudaStream_t st) {
     using R = typename Real<U>::type;
+    const size_t nn = (size_t)n * n;
+    U* X1 = W;
+    U* X2 = W + nn;
+    U* X3 = W + 2 * nn;
+    U* X4 = W + 3 * nn;
+    U* Bj = W + 4 * nn;
+    U* P = W + 5 * nn;
+    U* Q = W + 6 * nn;
     // the column sums go to E's storage (n doubles), overwritten at the end
     double* colsum = reinterpret_cast<double*>(E);
     roks::count_launch(), k_big_colsum<<<(unsigned)((32 * n + 255) / 256), 256, 0, st>>>(n, A, colsum);
     const int fill_blocks = std::min(152, (n * n + 255) / 256);
-    roks::count_launch(), k_big_expm_scale<U><<<fill_blocks, 256, 0, st>>>(n, A, s, colsum, X, P, info, degree);
-    const int nt = (n + BK - 1) / BK;
+    roks::count_launch(), k_big_expm_scale<U><<<fill_blocks, 256, 0, st>>>(n, A, s, colsum, X1, info);
+    const int nt = (n + SQ_T - 1) / SQ_T;
     dim3 g(nt, nt);
-    for (int k = degree - 1; k >= 1; --k) {
-        roks::count_launch(), k_sq_gemm<U><<<g, 256, 0, st>>>(n, X, P, Q, R(1) / R(k), 1, nullptr, 0);
+    const int eb = (n * n + 255) / 256;
+    roks::count_launch(), k_sq_gemm<U><<<g, 256, 0, st>>>(n, X1, X1, X2, R(1), nullptr, 0, nullptr, 0);
+    roks::count_launch(), k_sq_gemm<U><<<g, 256, 0, st>>>(n, X2, X1, X3, R(1), nullptr, 0, nullptr, 0);
+    roks::count_launch(), k_sq_gemm<U><<<g, 256, 0, st>>>(n, X2, X2, X4, R(1), nullptr, 0, nullptr, 0);
+    // Taylor coefficients 1/k!
+    double cf[17];
+    cf[0] = 1.0;
+    for (int k = 1; k <= 16; ++k) cf[k] = cf[k - 1] / k;
+    const int d = 4 * r;
+    // innermost block (with the top coefficient on X^4), then Horner in X^4
+    int j = r - 1;
+    roks::count_launch(), k_big_ps_block<U><<<eb, 256, 0, st>>>(n, X1, X2, X3, X4, R(cf[4 * j]), R(cf[4 * j + 1]),
+                                                                  R(cf[4 * j + 2]), R(cf[4 * j + 3]), R(cf[d]), P);
+    for (j = r - 2; j >= 0; --j) {
+        roks::count_launch(), k_big_ps_block<U><<<eb, 256, 0, st>>>(n, X1, X2, X3, X4, R(cf[4 * j]),
+                                                                      R(cf[4 * j + 1]), R(cf[4 * j + 2]),
+                                                                      R(cf[4 * j + 3]), R(0), Bj);
+        roks::count_launch(), k_sq_gemm<U><<<g, 256, 0, st>>>(n, X4, P, Q, R(1), Bj, 0, nullptr, 0);
         U* t = P; P = Q; Q = t;
     }
-    for (int r = 0; r < max_square; ++r) {
-        roks::count_launch(), k_sq_gemm<U><<<g, 256, 0, st>>>(n, P, P, Q, R(1), 0, info, r);
-        U* t = P; P = Q; Q = t;
+    // squarings: the device's q of them, the rest return at once
+    for (int k = 0; k < max_square; ++k) {
+        U* src = (k & 1) ? Q : P;
+        U* dst = (k & 1) ? P : Q;
+        roks::count_launch(), k_sq_gemm<U><<<g, 256, 0, st>>>(n, src, src, dst, R(1), nullptr, 0, info, k);
     }
-    roks::count_launch(), k_big_to_double<U><<<(n * n + 255) / 256, 256, 0, st>>>(n, P, E);
+    roks::count_launch(), k_big_to_double<U><<<eb, 256, 0, st>>>(n, P, Q, info, max_square, E);
 }
 
-size_t expm_big_work_bytes(int n, bool fp64) { return (fp64 ? sizeof(double2) : sizeof(float2)) * 3 * (size_t)n * n; }
+size_t expm_big_work_bytes(int n, bool fp64) { return (fp64 ? sizeof(double2) : sizeof(float2)) * 7 * (size_t)n * n; }
 
 void expm_big(int n, const double2* A, const double* scale_dev, double2* E, void* work, double* info, bool fp64,
               cudaStream_t st) {
     // FP64: degree 16 (||X|| <= 1/4 gives 1e-26); FP32: degree 8 (1e-11);
-    // at most 24 squarings (the launches past the device's q copy through).
-    if (fp64) {
-        double2* X = static_cast<double2*>(work);
-        expm_big_impl<double2>(n, A, scale_dev, E, X, X + (size_t)n * n, X + 2 * (size_t)n * n, info, 16, 24, st);
-    } else {
-        float2* X = static_cast<float2*>(work);
-        expm_big_impl<float2>(n, A, scale_dev, E, X, X + (size_t)n * n, X + 2 * (size_t)n * n, info, 8, 24, st);
-    }
+    // at most 24 squarings (the launches past the device's q return at once).
+    if (fp64) expm_big_impl<double2>(n, A, scale_dev, E, static_cast<double2*>(work), info, 4, 24, st);
+    else expm_big_impl<float2>(n, A, scale_dev, E, static_cast<float2*>(work), info, 2, 24, st);
 }
 
 }  // namespace roks

@@ -208,12 +208,15 @@ __device__ __forceinline__ void load_x_lines(const Sphere& s, c2<T>* buf, const 
     }
 }
 
-template <typename T, int N>
+// SPLIT: every band of the launch holds two real orbitals as (re, im) with
+// the classes a and b (the Gamma-point packing of the open pair): re is
+// multiplied by V^a, im by V^b.
+template <typename T, int N, bool SPLIT>
 __global__ void __launch_bounds__(x_threads(N)) k_band_x_apply(Sphere s, const c2<T>* __restrict__ tw,
                                                                c2<T>* __restrict__ Yp,
                                                                const T* __restrict__ Vk,
                                                                const c2<T>* __restrict__ Xx, int b0,
-                                                               int n_closed, int split_band, T scale) {
+                                                               int n_closed, T scale) {
     constexpr int NT = x_threads(N);
     using V = c2<T>;
     constexpr int TL = tile_lines(N), LS = TL + 1;
@@ -226,13 +229,10 @@ __global__ void __launch_bounds__(x_threads(N)) k_band_x_apply(Sphere s, const c
     const int y = blockIdx.y;
     const int bb = blockIdx.z;
     const int b = b0 + bb;
-    const int cls = b < n_closed ? 0 : b - n_closed + 1;
-    // split_band: a band holding two real orbitals as (re, im) with the
-    // classes a and b (the Gamma-point packing of the open pair)
-    const bool split = b == split_band;
+    const int cls = SPLIT ? 1 : (b < n_closed ? 0 : b - n_closed + 1);
     // offsets within one band's planes and within one N^3 grid fit in 32 bits
     V* Ypb = Yp + (int64_t)bb * s.np * N * N + y * N + z0;
-    const T* Vc = Vk + (int64_t)(split ? 1 : cls) * N * N * N + y * N + z0;
+    const T* Vc = Vk + (int64_t)cls * N * N * N + y * N + z0;
     const T* Vc2 = Vk + (int64_t)2 * N * N * N + y * N + z0;
     const c2<T>* Xb = Xx ? Xx + (int64_t)b * N * N * N + y * N + z0 : nullptr;
     const int nmax = s.nmax;
@@ -249,7 +249,8 @@ __global__ void __launch_bounds__(x_threads(N)) k_band_x_apply(Sphere s, const c
             const bool in = z0 + line < N;
             const int gi = e * NN + line;
             const T w = in ? Vc[gi] * scale : T(0);
-            const T w2 = split ? (in ? Vc2[gi] * scale : T(0)) : w;
+            T w2 = w;
+            if constexpr (SPLIT) w2 = in ? Vc2[gi] * scale : T(0);
             V o = mk<T>(v.x * w, v.y * w2);
             if (Xb && in) {
                 const V xv = Xb[gi];
@@ -504,12 +505,30 @@ struct BandFft {
         dim3 gy((N + TL - 1) / TL, s.np, nbb);
         roks::count_launch(), k_band_y_inv<T, N><<<gy, kThreads, SM, st>>>(s, tw, Zc, Yp);
     }
+    // split_band (if within the launch) takes the SPLIT instance, alone
     static void x_apply(const Sphere& s, const V* tw, V* Yp, const T* Vk, const V* Xx, int b0, int nbb, int nc,
                         int split_band, T scale, cudaStream_t st) {
-        set_smem(k_band_x_apply<T, N>, SM);
-        dim3 g((N + TL - 1) / TL, N, nbb);
-        roks::count_launch(), k_band_x_apply<T, N><<<g, x_threads(N), SM, st>>>(s, tw, Yp, Vk, Xx, b0, nc,
-                                                                                split_band, scale);
+        set_smem(k_band_x_apply<T, N, false>, SM);
+        set_smem(k_band_x_apply<T, N, true>, SM);
+        auto run = [&](bool split, int first, int count) {
+            if (count <= 0) return;
+            // the kernel indexes the planes from the launch's first band
+            V* Y = Yp + (int64_t)(first - b0) * s.np * N * N;
+            dim3 g((N + TL - 1) / TL, N, count);
+            if (split)
+                roks::count_launch(),
+                    k_band_x_apply<T, N, true><<<g, x_threads(N), SM, st>>>(s, tw, Y, Vk, Xx, first, nc, scale);
+            else
+                roks::count_launch(),
+                    k_band_x_apply<T, N, false><<<g, x_threads(N), SM, st>>>(s, tw, Y, Vk, Xx, first, nc, scale);
+        };
+        if (split_band < b0 || split_band >= b0 + nbb) {
+            run(false, b0, nbb);
+        } else {
+            run(false, b0, split_band - b0);
+            run(true, split_band, 1);
+            run(false, split_band + 1, b0 + nbb - split_band - 1);
+        }
     }
     static void x_inv_full(const Sphere& s, const V* tw, const V* Yp, V* Phi, int b0, int nbb, T scale,
                            cudaStream_t st) {

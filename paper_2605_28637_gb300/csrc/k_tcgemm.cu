@@ -79,7 +79,6 @@ constexpr uint32_t GB_SLOT = 4 * GB_PART;        // A hi | A lo | B hi | B lo
 constexpr uint32_t GB_RAWA = GB_M * GB_KC * 8;   // 16 KB
 constexpr uint32_t GB_RAWB = GB_NC * GB_KC * 8;  // 8 KB (CN)
 constexpr uint32_t GB_RAWS = GB_RAWA + GB_RAWB;
-constexpr size_t GB_SMEM = (size_t)GB_CONV * GB_SLOT + (size_t)GB_RAW * GB_RAWS + 1024;
 constexpr uint32_t GB_TCOLS = GB_ACC * GB_NR;    // 512 columns
 constexpr uint32_t GB_DEFAULT_WAIT = 1u << 26;
 
@@ -131,20 +130,43 @@ __device__ __forceinline__ void give_up(volatile int* failed) {
     g_tcg_timeout = 1;
 }
 
-template <bool NN>
+// Shared-memory plan of a variant: operand slots (A hi | A lo | B hi | B lo)
+// and raw stages.  APRE: A arrives pre-split (k_tcg_asplit), copied by the
+// producer straight into the slot, so the slots can be three deep; the tall
+// product P Y takes it (B is pre-split as well: no raw stage, no conversion,
+// the worker warps only drain).  The plan also covers A^H B with a pre-split
+// A (raw stages of B alone), which gemm_cn_tcg does not launch: it measured
+// slower than converting both operands in the kernel.
+template <bool NN, bool APRE>
+struct GbPlan {
+    static constexpr int SLOTS = APRE ? 3 : GB_CONV;
+    static constexpr uint32_t RAWA = APRE ? 0u : GB_RAWA;       // raw A bytes per stage
+    static constexpr uint32_t RAWB = NN ? 0u : GB_RAWB;         // raw B bytes per stage
+    static constexpr uint32_t RAWS = (NN && !APRE) ? GB_RAWS : RAWA + RAWB;
+    static constexpr bool RAW = RAWA + RAWB > 0;                // a TMA raw stage per K stage
+    static constexpr bool CONVERT = RAW;                        // workers convert raw operands
+    static constexpr bool BULK = NN || APRE;                    // bulk copies into the slot
+    static constexpr uint32_t BULK_BYTES = (NN ? 2 * GB_PART : 0u) + (APRE ? 2 * GB_PART : 0u);
+    static constexpr size_t SMEM = (size_t)SLOTS * GB_SLOT + (RAW ? (size_t)GB_RAW * RAWS : 0) + 1024;
+    static constexpr int LAG = CONVERT ? 2 : 0;                 // drain of stage i - LAG in iteration i
+};
+
+template <bool NN, bool APRE>
 __global__ void __launch_bounds__(GB_THREADS, 1)
     k_tcgemm(int M, int N, int stages_per_cta, int total_stages, const __grid_constant__ CUtensorMap tmA,
              const __grid_constant__ CUtensorMap tmB, const unsigned char* __restrict__ bsplit,
-             float2* __restrict__ part, const float2* Cin, int64_t ldcin, float2* Cout, int64_t ldc, float alpha,
-             float beta, uint32_t wcap) {
+             const unsigned char* __restrict__ asplit, float2* __restrict__ part, const float2* Cin, int64_t ldcin,
+             float2* Cout, int64_t ldc, float alpha, float beta, uint32_t wcap) {
+    using PL = GbPlan<NN, APRE>;
+    constexpr int SL = PL::SLOTS;
     extern __shared__ __align__(1024) unsigned char gb_smem[];
-    __shared__ __align__(8) uint64_t raw_full[GB_RAW], raw_empty[GB_RAW], conv_full[GB_CONV], conv_empty[GB_CONV],
-        b_full[GB_CONV], acc_full[GB_ACC], acc_empty[GB_ACC], mma_done;
+    __shared__ __align__(8) uint64_t raw_full[GB_RAW], raw_empty[GB_RAW], conv_full[SL], conv_empty[SL], b_full[SL],
+        acc_full[GB_ACC], acc_empty[GB_ACC], mma_done;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int failed;
     unsigned char* base = gb_smem + ((1024u - (tc::smem_u32(gb_smem) & 1023u)) & 1023u);
-    unsigned char* conv = base;                                // GB_CONV operand stages
-    unsigned char* raw = base + (size_t)GB_CONV * GB_SLOT;     // GB_RAW raw stages (1024-byte aligned)
+    unsigned char* conv = base;                                // SL operand slots
+    unsigned char* raw = base + (size_t)SL * GB_SLOT;          // GB_RAW raw stages (1024-byte aligned)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * GB_M, n0 = blockIdx.y * GB_NC;
     const int s0 = NN ? 0 : blockIdx.z * stages_per_cta;
@@ -155,7 +177,7 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
             tc::mbar_init(&raw_full[s], 1);
             tc::mbar_init(&raw_empty[s], GB_WORKERS);
         }
-        for (int s = 0; s < GB_CONV; ++s) {
+        for (int s = 0; s < SL; ++s) {
             tc::mbar_init(&conv_full[s], GB_WORKERS);
             tc::mbar_init(&conv_empty[s], 1);
             tc::mbar_init(&b_full[s], 1);
@@ -179,42 +201,48 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
         if (lane == 0) {
             int issued = 0, bissued = 0;
             for (int i = 0; i < ns; ++i) {
-                const int rs = i % GB_RAW;
-                if (i >= GB_RAW && !gwait(&raw_empty[rs], (uint32_t)((i / GB_RAW - 1) & 1), wcap, &failed)) {
-                    give_up(&failed);
-                    break;
-                }
-                unsigned char* ra = raw + (size_t)rs * GB_RAWS;
-                const int k0 = (s0 + i) * GB_KC;
-                if (NN) {
-                    tc::mbar_arrive_expect_tx(&raw_full[rs], GB_RAWA);
-                    tc::tma_2d(ra, &tmA, m0, k0, &raw_full[rs]);
-                } else {
-                    tc::mbar_arrive_expect_tx(&raw_full[rs], GB_RAWS);
-                    tc::tma_2d(ra, &tmA, k0, m0, &raw_full[rs]);
-                    tc::tma_2d(ra + GB_RAWA, &tmB, k0, n0, &raw_full[rs]);
-                }
-                issued = i + 1;
-                if (NN) {
-                    // the pre-split B slice goes straight into the operand stage
-                    const int cs = i % GB_CONV;
-                    if (i >= GB_CONV &&
-                        !gwait(&conv_empty[cs], (uint32_t)((i / GB_CONV - 1) & 1), wcap, &failed)) {
+                if (PL::RAW) {
+                    const int rs = i % GB_RAW;
+                    if (i >= GB_RAW && !gwait(&raw_empty[rs], (uint32_t)((i / GB_RAW - 1) & 1), wcap, &failed)) {
                         give_up(&failed);
                         break;
                     }
-                    tc::mbar_arrive_expect_tx(&b_full[cs], 2 * GB_PART);
-                    tc::bulk_g2s(conv + (size_t)cs * GB_SLOT + 2 * GB_PART,
-                                 bsplit + ((size_t)blockIdx.y * total_stages + i) * (2 * GB_PART), 2 * GB_PART,
-                                 &b_full[cs]);
+                    unsigned char* ra = raw + (size_t)rs * PL::RAWS;
+                    const int k0 = (s0 + i) * GB_KC;
+                    if (NN) {
+                        tc::mbar_arrive_expect_tx(&raw_full[rs], GB_RAWA);
+                        tc::tma_2d(ra, &tmA, m0, k0, &raw_full[rs]);
+                    } else {
+                        tc::mbar_arrive_expect_tx(&raw_full[rs], PL::RAWA + PL::RAWB);
+                        if (!APRE) tc::tma_2d(ra, &tmA, k0, m0, &raw_full[rs]);
+                        tc::tma_2d(ra + PL::RAWA, &tmB, k0, n0, &raw_full[rs]);
+                    }
+                    issued = i + 1;
+                }
+                if (PL::BULK) {
+                    // pre-split operands go straight into the operand slot
+                    const int cs = i % SL;
+                    if (i >= SL && !gwait(&conv_empty[cs], (uint32_t)((i / SL - 1) & 1), wcap, &failed)) {
+                        give_up(&failed);
+                        break;
+                    }
+                    unsigned char* sl = conv + (size_t)cs * GB_SLOT;
+                    tc::mbar_arrive_expect_tx(&b_full[cs], PL::BULK_BYTES);
+                    if (APRE)
+                        tc::bulk_g2s(sl, asplit + ((size_t)blockIdx.x * total_stages + s0 + i) * (2 * GB_PART),
+                                     2 * GB_PART, &b_full[cs]);
+                    if (NN)
+                        tc::bulk_g2s(sl + 2 * GB_PART,
+                                     bsplit + ((size_t)blockIdx.y * total_stages + i) * (2 * GB_PART), 2 * GB_PART,
+                                     &b_full[cs]);
                     bissued = i + 1;
                 }
             }
             // copies still in flight complete before the CTA may exit
             for (int i = issued > GB_RAW ? issued - GB_RAW : 0; i < issued; ++i)
                 gwait(&raw_full[i % GB_RAW], (uint32_t)((i / GB_RAW) & 1), GB_DEFAULT_WAIT, &failed);
-            for (int i = bissued > GB_CONV ? bissued - GB_CONV : 0; i < bissued; ++i)
-                gwait(&b_full[i % GB_CONV], (uint32_t)((i / GB_CONV) & 1), GB_DEFAULT_WAIT, &failed);
+            for (int i = bissued > SL ? bissued - SL : 0; i < bissued; ++i)
+                gwait(&b_full[i % SL], (uint32_t)((i / SL) & 1), GB_DEFAULT_WAIT, &failed);
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -225,9 +253,10 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
             bool ok = true;
             int u = 0;
             for (int i = 0; i < ns && ok; ++i) {
-                const int cs = i % GB_CONV;
-                const uint32_t par = (uint32_t)((i / GB_CONV) & 1);
-                if (!gwait(&conv_full[cs], par, wcap, &failed) || (NN && !gwait(&b_full[cs], par, wcap, &failed))) {
+                const int cs = i % SL;
+                const uint32_t par = (uint32_t)((i / SL) & 1);
+                if ((PL::CONVERT && !gwait(&conv_full[cs], par, wcap, &failed)) ||
+                    (PL::BULK && !gwait(&b_full[cs], par, wcap, &failed))) {
                     ok = false;
                     break;
                 }
@@ -257,7 +286,7 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
                 }
                 tc::commit(&acc_full[b]);
                 ++u;
-                tc::commit(&conv_empty[cs]);   // the operand stage is free once these MMAs complete
+                tc::commit(&conv_empty[cs]);   // the operand slot is free once these MMAs complete
             }
             if (!ok) give_up(&failed);
             // every MMA issued completes before the tensor memory is freed
@@ -276,30 +305,33 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
 #pragma unroll
         for (int j = 0; j < 16; ++j) re[j] = im[j] = 0.f;
         bool ok = true;
-        for (int i = 0; i < ns + 2; ++i) {
-            if (i < ns) {
-                const int rs = i % GB_RAW, cs = i % GB_CONV;
+        for (int i = 0; i < ns + PL::LAG; ++i) {
+            if (PL::CONVERT && i < ns) {
+                const int rs = i % GB_RAW, cs = i % SL;
                 if (!warp_wait(&raw_full[rs], (uint32_t)((i / GB_RAW) & 1), wcap, &failed) ||
-                    (i >= GB_CONV &&
-                     !warp_wait(&conv_empty[cs], (uint32_t)((i / GB_CONV - 1) & 1), wcap, &failed))) {
+                    (i >= SL && !warp_wait(&conv_empty[cs], (uint32_t)((i / SL - 1) & 1), wcap, &failed))) {
                     ok = false;
                     break;
                 }
-                const unsigned char* ra = raw + (size_t)rs * GB_RAWS;
+                const unsigned char* ra = raw + (size_t)rs * PL::RAWS;
                 unsigned char* sl = conv + (size_t)cs * GB_SLOT;
                 if (!NN) {
-                    // A row rr (column rr of A): 16 complex in eight 16-byte chunks,
-                    // stored by the copy with the 128-byte swizzle
+                    if (!APRE) {
+                        // A row rr (column rr of A): 16 complex in eight 16-byte chunks,
+                        // stored by the copy with the 128-byte swizzle
 #pragma unroll
-                    for (int h2 = 0; h2 < 2; ++h2) {
-                        const int ch = c0 + 4 * h2;
-                        const float4 v = *reinterpret_cast<const float4*>(ra + rr * 128 + ((ch ^ (rr & 7)) << 4));
-                        put_split(sl, cofs(rr, 4 * ch), v);
+                        for (int h2 = 0; h2 < 2; ++h2) {
+                            const int ch = c0 + 4 * h2;
+                            const float4 v =
+                                *reinterpret_cast<const float4*>(ra + rr * 128 + ((ch ^ (rr & 7)) << 4));
+                            put_split(sl, cofs(rr, 4 * ch), v);
+                        }
                     }
                     // B column j, chunk ch: the real-part row (re, im) and the
                     // imaginary-part row (im, -re)
                     const int j = wt & 63, ch = wt >> 6;
-                    const float4 v = *reinterpret_cast<const float4*>(ra + GB_RAWA + j * 128 + ((ch ^ (j & 7)) << 4));
+                    const float4 v =
+                        *reinterpret_cast<const float4*>(ra + PL::RAWA + j * 128 + ((ch ^ (j & 7)) << 4));
                     put_split(sl + 2 * GB_PART, cofs(j, 4 * ch), v);
                     put_split(sl + 2 * GB_PART, cofs(GB_NC + j, 4 * ch), make_float4(v.y, -v.x, v.w, -v.z));
                 } else {
@@ -319,7 +351,7 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
                     tc::mbar_arrive(&conv_full[cs]);
                 }
             }
-            const int dsg = i - 2;
+            const int dsg = i - PL::LAG;
             if (dsg >= 0) {
                 const int b = dsg % GB_ACC;
                 if (!warp_wait(&acc_full[b], (uint32_t)((dsg / GB_ACC) & 1), wcap, &failed)) {
@@ -376,6 +408,37 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem, GB_TCOLS);
     }
+}
+
+// A pre-split for the tall product A B, once per operand that does not
+// change (the projector matrix): for each (128-row tile t, stage s of 16
+// complex K) a block of hi (16 KB) then lo (16 KB) in the operand-slot
+// layout, element (r, kr) = real part kr & 1 of A(128 t + r, 16 s + kr / 2)
+// (A is M x K, column major).  Zero beyond M and K.
+__global__ void k_tcg_asplit(int M, int K, const float2* __restrict__ A, int64_t lda, int nst, int mt,
+                             unsigned char* __restrict__ out) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)mt * nst * GB_M * 8;
+    if (idx >= total) return;
+    const int ch = (int)(idx % 8);
+    const int rr = (int)((idx / 8) % GB_M);
+    const int s = (int)((idx / (8 * GB_M)) % nst);
+    const int t = (int)(idx / (8 * GB_M * nst));
+    const int m = t * GB_M + rr;
+    float v[4];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int k = s * GB_KC + 2 * ch + e;
+        float2 a = make_float2(0.f, 0.f);
+        if (k < K && m < M) a = A[(int64_t)k * lda + m];
+        v[2 * e] = a.x;
+        v[2 * e + 1] = a.y;
+    }
+    unsigned char* blk = out + ((size_t)t * nst + s) * (2 * GB_PART);
+    float4 hi, lo;
+    split4(make_float4(v[0], v[1], v[2], v[3]), hi, lo);
+    *reinterpret_cast<float4*>(blk + cofs(rr, 4 * ch)) = hi;
+    *reinterpret_cast<float4*>(blk + GB_PART + cofs(rr, 4 * ch)) = lo;
 }
 
 // B (K x N complex FP64, ldb) -> the NN kernel's N-side operand: for each
@@ -447,13 +510,41 @@ int sm_count() {
 
 bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 
-template <bool NN>
+template <bool NN, bool APRE>
 void set_attr() {
     static bool done = false;
     if (!done) {
-        cudaFuncSetAttribute(k_tcgemm<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GB_SMEM);
+        cudaFuncSetAttribute(k_tcgemm<NN, APRE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)GbPlan<NN, APRE>::SMEM);
         done = true;
     }
+}
+
+// Operands split once (tcg_presplit): looked up by address, leading
+// dimension and shape, so that a call on another matrix never takes them.
+struct PreSplit {
+    const void* A;
+    int64_t lda;
+    int M, K;
+    const unsigned char* split;
+};
+constexpr int kMaxPreSplit = 32;
+PreSplit g_pre[kMaxPreSplit];
+int g_npre = 0;
+
+const unsigned char* find_presplit(const void* A, int64_t lda, int M, int K) {
+    static int on = -1;
+    if (on < 0) {
+        // ROKS_TC_PRESPLIT=0 converts every operand in the kernel (for comparisons)
+        const char* e = std::getenv("ROKS_TC_PRESPLIT");
+        on = (e && e[0] == '0') ? 0 : 1;
+    }
+    if (!on) return nullptr;
+    for (int i = 0; i < g_npre; ++i) {
+        const PreSplit& p = g_pre[i];
+        if (p.A == A && p.lda == lda && p.M == M && p.K == K) return p.split;
+    }
+    return nullptr;
 }
 
 // Waves of CTAs (one per SM) a CN product is split into, times two
@@ -497,6 +588,30 @@ size_t tcg_nn_work_bytes(int N, int K) {
     return (size_t)nt * total * 2 * GB_PART;
 }
 
+size_t tcg_presplit_bytes(int M, int K) {
+    const size_t mt = (M + GB_M - 1) / GB_M, nst = (K + GB_KC - 1) / GB_KC;
+    return mt * nst * 2 * GB_PART;
+}
+
+bool tcg_presplit(int M, int K, const float2* A, int64_t lda, void* out, cudaStream_t st) {
+    if (g_npre >= kMaxPreSplit || !aligned(out, 16)) return false;
+    const int mt = (M + GB_M - 1) / GB_M, nst = (K + GB_KC - 1) / GB_KC;
+    const int64_t n = (int64_t)mt * nst * GB_M * 8;
+    unsigned char* o = static_cast<unsigned char*>(out);
+    roks::count_launch();
+    k_tcg_asplit<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(M, K, A, lda, nst, mt, o);
+    if (cudaGetLastError() != cudaSuccess) return false;
+    g_pre[g_npre++] = PreSplit{A, lda, M, K, o};
+    return true;
+}
+
+void tcg_presplit_forget(const void* split) {
+    int w = 0;
+    for (int i = 0; i < g_npre; ++i)
+        if (g_pre[i].split != split) g_pre[w++] = g_pre[i];
+    g_npre = w;
+}
+
 static long long g_tcg_launches = 0;
 long long tcg_launches_take() {
     const long long n = g_tcg_launches;
@@ -514,15 +629,18 @@ bool gemm_cn_tcg(int M, int N, int K, const float2* A, int64_t lda, const float2
     const int ks = cn_splits(mt * nt, total);
     const int per = (total + ks - 1) / ks;
     if (tcg_cn_work_bytes(M, N, K) > work_bytes) return false;
+    // (A^H B converts both operands in the kernel: a pre-split A, copied as
+    // 32 KB hi/lo blocks while the workers still convert B, measured slower
+    // on P^H Psi at mgo-120, 1.45 -> 1.49 ms)
     CUtensorMap tmA, tmB;
     if (!tensor_map_2d(&tmA, A, K, M, lda, GB_KC, GB_M, true) || !tensor_map_2d(&tmB, B, K, N, ldb, GB_KC, GB_NC, true))
         return false;
-    set_attr<false>();
     float2* part = static_cast<float2*>(work);
     roks::count_launch();
     g_tcg_launches += 1;
-    k_tcgemm<false><<<dim3(mt, nt, ks), GB_THREADS, GB_SMEM, st>>>(M, N, per, total, tmA, tmB, nullptr, part, nullptr,
-                                                                  0, nullptr, 0, 0.f, 0.f, wait_polls());
+    set_attr<false, false>();
+    k_tcgemm<false, false><<<dim3(mt, nt, ks), GB_THREADS, GbPlan<false, false>::SMEM, st>>>(
+        M, N, per, total, tmA, tmB, nullptr, nullptr, part, nullptr, 0, nullptr, 0, 0.f, 0.f, wait_polls());
     const int64_t outs = (int64_t)M * N;
     roks::count_launch();
     k_tcg_reduce<<<(unsigned)((outs + 255) / 256), 256, 0, st>>>(M, N, mt, mt * nt, ks, part, C, ldc);
@@ -540,18 +658,26 @@ bool gemm_nn_tcg(int M, int N, int K, const float2* A, int64_t lda, const double
     if (static_cast<const void*>(A) == static_cast<const void*>(Cout)) return false;
     const int nt = (N + GB_NC - 1) / GB_NC, total = (K + GB_KC - 1) / GB_KC;
     if (tcg_nn_work_bytes(N, K) > bwork_bytes) return false;
-    CUtensorMap tmA;
-    if (!tensor_map_2d(&tmA, A, M, K, lda, GB_M, GB_KC, false)) return false;
+    const unsigned char* as = find_presplit(A, lda, M, K);
+    CUtensorMap tmA{};
+    if (!as && !tensor_map_2d(&tmA, A, M, K, lda, GB_M, GB_KC, false)) return false;
     unsigned char* bs = static_cast<unsigned char*>(bwork);
     const int64_t nsplit = (int64_t)nt * total * GB_NR * 8;
     roks::count_launch();
     k_tcg_bsplit<<<(unsigned)((nsplit + 255) / 256), 256, 0, st>>>(K, N, B, ldb, total, nt, bs);
-    set_attr<true>();
     roks::count_launch();
     g_tcg_launches += 1;
     const int mt = (M + GB_M - 1) / GB_M;
-    k_tcgemm<true><<<dim3(mt, nt, 1), GB_THREADS, GB_SMEM, st>>>(M, N, total, total, tmA, tmA, bs, nullptr, Cin,
-                                                                ldcin, Cout, ldc, alpha, beta, wait_polls());
+    const dim3 grid(mt, nt, 1);
+    if (as) {
+        set_attr<true, true>();
+        k_tcgemm<true, true><<<grid, GB_THREADS, GbPlan<true, true>::SMEM, st>>>(
+            M, N, total, total, tmA, tmA, bs, as, nullptr, Cin, ldcin, Cout, ldc, alpha, beta, wait_polls());
+    } else {
+        set_attr<true, false>();
+        k_tcgemm<true, false><<<grid, GB_THREADS, GbPlan<true, false>::SMEM, st>>>(
+            M, N, total, total, tmA, tmA, bs, nullptr, nullptr, Cin, ldcin, Cout, ldc, alpha, beta, wait_polls());
+    }
     return true;
 }
 

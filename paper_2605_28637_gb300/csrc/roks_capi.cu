@@ -48,6 +48,9 @@ struct roks_ctx {
     int gamma = 0, npw_full = 0, h0 = 0, nbt = 0, nct = 0, split_t = -1;
     int64_t ldc_pk = 0;
     void* d_Cpk = nullptr;   // packed full-sphere coefficients (npw_full rows, ldc_pk, nbt bands)
+    // the projector matrix split once into TF32 hi/lo operand blocks for the
+    // tensor-core tall products P Y, where they take it
+    void* d_Psplit_nn = nullptr;
     double cM = 0, cT = 0;
     PotCoef cf{};
     std::vector<int32_t> miller;
@@ -1348,6 +1351,8 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
         AL(ctx->d_hf2, sizeof(double) * 2);
         AL(ctx->d_exopen, sizeof(double) * 2);
     }
+    if (!f64 && ctx->nproj > 0 && tcg_nn_takes(npw, nb, ctx->nproj))
+        AL(ctx->d_Psplit_nn, tcg_presplit_bytes(npw, ctx->nproj));
     double* d_atoms = nullptr;
     double* d_proj = nullptr;
     AL(d_atoms, sizeof(double) * (atomtab.size() + 1));
@@ -1429,6 +1434,9 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
         if (f64) gamma_scale_rows<double>(npw, ctx->nproj, static_cast<double2*>(ctx->d_P), l, ctx->st);
         else gamma_scale_rows<float>(npw, ctx->nproj, static_cast<float2*>(ctx->d_P), l, ctx->st);
     }
+    if (ctx->d_Psplit_nn &&
+        !tcg_presplit(npw, ctx->nproj, static_cast<const float2*>(ctx->d_P), l, ctx->d_Psplit_nn, ctx->st))
+        return bail(ROKS_ECUDA, "projector split");
     if (opt->alpha != 0.0) {
         const int bare = opt->exx_kernel == ROKS_EXX_BARE ? 1 : 0;
         if (f64) exx_setup_kernel<double>(N, cell->L, bare, static_cast<double*>(ctx->d_vG), ctx->st);
@@ -1564,6 +1572,11 @@ roks_status roks_potential(roks_ctx* ctx, roks_energies* e, void* vclass_out) {
 }
 
 roks_status roks_apply_h(roks_ctx* ctx, const void* psi, int64_t ld, void* fpsi, void* spsi, void* grad) {
+    return roks_gradient_parts(ctx, psi, ld, fpsi, spsi, grad, nullptr);
+}
+
+roks_status roks_gradient_parts(roks_ctx* ctx, const void* psi, int64_t ld, void* fpsi, void* spsi, void* grad,
+                                void* grad_I) {
     if (!ctx) return ROKS_EINVAL;
     roks_status r = check_psi(ctx, psi, ld);
     if (r != ROKS_OK) return r;
@@ -1571,12 +1584,12 @@ roks_status roks_apply_h(roks_ctx* ctx, const void* psi, int64_t ld, void* fpsi,
     if (!fpsi) return fail(ctx, ROKS_EINVAL, "null output");
     const int64_t l = ctx->ld_min;
     const int nb = ctx->nb;
-    void* S = spsi ? spsi : (grad ? ctx->W_S : nullptr);
+    void* S = spsi ? spsi : ((grad || grad_I) ? ctx->W_S : nullptr);
     const int64_t lds = spsi ? ld : l;
     if (ctx->prec == ROKS_FP64) r = Impl<double>::apply(ctx, psi, ld, fpsi, ld, S, lds);
     else r = Impl<float>::apply(ctx, psi, ld, fpsi, ld, S, lds);
-    if (r != ROKS_OK || !grad) return r;
-    // g = F - S Gam, Gam_mn = (theta_mn + conj theta_nm) / 2
+    if (r != ROKS_OK || !(grad || grad_I)) return r;
+    // theta = Psi^H F Psi; g = F - S Gam, Gam_mn = (theta_mn + conj theta_nm) / 2; g_I = F - S theta
     if (ctx->prec == ROKS_FP64) {
         gemm_cn<double>(nb, nb, ctx->npw, static_cast<const double2*>(psi), ld, static_cast<const double2*>(fpsi), ld,
                         ctx->d_Th, nb, ctx->d_gemm_work, ctx->gemm_work_elems, ctx->st);
@@ -1585,18 +1598,24 @@ roks_status roks_apply_h(roks_ctx* ctx, const void* psi, int64_t ld, void* fpsi,
                        ctx->d_Th, nb, ctx->d_gemm_work, ctx->gemm_work_elems, ctx->st);
     }
     if (ctx->gamma) gamma_real_part(nb, nb, ctx->d_Th, nb, ctx->st);
-    CK(cudaMemcpyAsync(ctx->d_Gam, ctx->d_Th, sizeof(double2) * nb * nb, cudaMemcpyDeviceToDevice, ctx->st));
-    hermitize(nb, ctx->d_Gam, ctx->st);
     const size_t es = ctx->prec == ROKS_FP64 ? sizeof(double2) : sizeof(float2);
-    CK(cudaMemcpy2DAsync(grad, ld * es, fpsi, ld * es, ctx->npw * es, nb, cudaMemcpyDeviceToDevice, ctx->st));
-    if (ctx->prec == ROKS_FP64)
-        gemm_nn<double>(ctx->npw, nb, nb, static_cast<const double2*>(S), lds, ctx->d_Gam, nb,
-                        static_cast<double2*>(grad), ld, -1.0, 1.0, ctx->d_gemm_work, ctx->st,
-                        ctx->gemm_work_elems * sizeof(double2));
-    else
-        gemm_nn<float>(ctx->npw, nb, nb, static_cast<const float2*>(S), lds, ctx->d_Gam, nb,
-                       static_cast<float2*>(grad), ld, -1.0, 1.0, ctx->d_gemm_work, ctx->st,
-                       ctx->gemm_work_elems * sizeof(double2));
+    for (int part = 0; part < 2; ++part) {
+        void* out = part == 0 ? grad : grad_I;
+        if (!out) continue;
+        const double2* M = ctx->d_Th;
+        if (part == 0) {
+            CK(cudaMemcpyAsync(ctx->d_Gam, ctx->d_Th, sizeof(double2) * nb * nb, cudaMemcpyDeviceToDevice, ctx->st));
+            hermitize(nb, ctx->d_Gam, ctx->st);
+            M = ctx->d_Gam;
+        }
+        CK(cudaMemcpy2DAsync(out, ld * es, fpsi, ld * es, ctx->npw * es, nb, cudaMemcpyDeviceToDevice, ctx->st));
+        if (ctx->prec == ROKS_FP64)
+            gemm_nn<double>(ctx->npw, nb, nb, static_cast<const double2*>(S), lds, M, nb, static_cast<double2*>(out),
+                            ld, -1.0, 1.0, ctx->d_gemm_work, ctx->st, ctx->gemm_work_elems * sizeof(double2));
+        else
+            gemm_nn<float>(ctx->npw, nb, nb, static_cast<const float2*>(S), lds, M, nb, static_cast<float2*>(out), ld,
+                           -1.0, 1.0, ctx->d_gemm_work, ctx->st, ctx->gemm_work_elems * sizeof(double2));
+    }
     CK(cudaGetLastError());
     return ROKS_OK;
 }
@@ -1914,6 +1933,7 @@ void roks_destroy(roks_ctx* ctx) {
     if (ctx->st) cudaStreamSynchronize(ctx->st);
     else cudaDeviceSynchronize();
     if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
+    if (ctx->d_Psplit_nn) tcg_presplit_forget(ctx->d_Psplit_nn);
     if (ctx->h_sc) cudaFreeHost(ctx->h_sc);
     if (ctx->h_diis) cudaFreeHost(ctx->h_diis);
     if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);

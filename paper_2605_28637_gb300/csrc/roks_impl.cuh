@@ -224,6 +224,14 @@ bool gemm_cn_tcg(int M, int N, int K, const float2* A, int64_t lda, const float2
 bool gemm_nn_tcg(int M, int N, int K, const float2* A, int64_t lda, const double2* B, int ldb, const float2* Cin,
                  int64_t ldcin, float2* Cout, int64_t ldc, float alpha, float beta, void* bwork, size_t bwork_bytes,
                  cudaStream_t st);
+// An operand that does not change (the projector matrix) split once into
+// TF32 hi/lo blocks in the kernels' operand layout: the tall products A B
+// whose A is that matrix (same address, leading dimension and shape) then
+// copy it instead of converting it.  out holds tcg_presplit_bytes(M, K);
+// false when not registered.
+size_t tcg_presplit_bytes(int M, int K);
+bool tcg_presplit(int M, int K, const float2* A, int64_t lda, void* out, cudaStream_t st);
+void tcg_presplit_forget(const void* split);
 // 1 if a tensor-core wait gave up since the last call (then cleared)
 int tcg_timeout_take();
 // tensor-core contraction launches since the last call

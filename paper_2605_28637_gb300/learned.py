@@ -59,16 +59,11 @@ def make_pairs(cfg: dict, precision: str = "fp64", iters=(1, 2, 3, 4, 6, 8, 12, 
     U_all, t_all, w_all = [], [], []
     for it in range(max(iters) + 1):
         if it in iters:
-            f, s, _ = ctx.apply_h(psi, want_s=True, want_grad=True)   # sets Theta for the features
+            # F, S, g_I = F - S theta on the device (theta kept for the features' band energies)
+            f, s, _, gI_dev = ctx.gradient_parts(psi)
             P = _host(psi, npw)
-            F = _host(f, npw)
             SP = _host(s, npw)
-            Theta = P.conj().T @ F
-            gI = F - SP @ Theta
-            gI_dev = ctx.new_bands()
-            h = np.zeros((nb, ctx.ld), dtype=np.complex128)
-            h[:, :npw] = gI.T
-            gI_dev.copy_(ctx.torch.from_numpy(h).to(gI_dev.dtype))
+            gI = _host(gI_dev, npw)
             kg_dev, feats = ctx.precondition(gI_dev, want_feats=True)
             Kg = _host(kg_dev, npw)
             U = feats.cpu().numpy().reshape(nb, npw, 3)

@@ -92,7 +92,7 @@ class roks_profile_entry(C.Structure):
 
 
 EXPORTS = ["roks_setup", "roks_basis", "roks_init_orbitals", "roks_invalidate", "roks_density", "roks_potential", "roks_apply_h",
-           "roks_orthonormalize", "roks_pcg_step", "roks_diis_step", "roks_forces", "roks_energies_get",
+           "roks_gradient_parts", "roks_orthonormalize", "roks_pcg_step", "roks_diis_step", "roks_forces", "roks_energies_get",
            "roks_profile_enable", "roks_profile_read", "roks_tuning_get", "roks_orthonormalize_noalloc", "roks_mlp_forward",
            "roks_mlp_grad", "roks_mlp_adam", "roks_set_preconditioner", "roks_precondition", "roks_mlp_grad_work",
            "roks_last_error", "roks_destroy"]
@@ -125,6 +125,7 @@ def load(path: str | None = None) -> C.CDLL:
     lib.roks_density.argtypes = [P, P, C.c_int64, P]
     lib.roks_potential.argtypes = [P, C.POINTER(roks_energies), P]
     lib.roks_apply_h.argtypes = [P, P, C.c_int64, P, P, P]
+    lib.roks_gradient_parts.argtypes = [P, P, C.c_int64, P, P, P, P]
     lib.roks_orthonormalize.argtypes = [P, P, C.c_int64]
     lib.roks_pcg_step.argtypes = [P, P, C.c_int64, C.POINTER(roks_step_info)]
     lib.roks_diis_step.argtypes = [P, P, C.c_int64, C.POINTER(roks_diis_options), C.POINTER(roks_diis_info)]
@@ -232,6 +233,10 @@ def roks_potential(ctx, vclass_out=None) -> dict:
 
 def roks_apply_h(ctx, psi, ld: int, fpsi, spsi=None, grad=None):
     _check(ctx, load().roks_apply_h(ctx, _ptr(psi), ld, _ptr(fpsi), _ptr(spsi), _ptr(grad)))
+
+
+def roks_gradient_parts(ctx, psi, ld: int, fpsi, spsi=None, grad=None, grad_I=None):
+    _check(ctx, load().roks_gradient_parts(ctx, _ptr(psi), ld, _ptr(fpsi), _ptr(spsi), _ptr(grad), _ptr(grad_I)))
 
 
 def roks_orthonormalize(ctx, psi, ld: int):
@@ -386,6 +391,12 @@ class Context:
         g = self.new_bands() if want_grad else None
         roks_apply_h(self.ctx, psi, self.ld, f, s, g)
         return f, s, g
+
+    def gradient_parts(self, psi):
+        """F|n>, S|n>, g and g_I (the gradient with gamma and with theta)."""
+        f, s, g, gi = (self.new_bands() for _ in range(4))
+        roks_gradient_parts(self.ctx, psi, self.ld, f, s, g, gi)
+        return f, s, g, gi
 
     def orthonormalize(self, psi):
         roks_orthonormalize(self.ctx, psi, self.ld)

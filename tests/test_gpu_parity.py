@@ -345,3 +345,56 @@ def test_many_bands_blocked_paths_mixed():
         info = ctx.pcg_step(psi)
         P, ref = pcg.step(P)
         assert abs(info["E_new"] - ref.E_new) < 5e-5, (it, info["E_new"], ref.E_new)
+
+
+def test_many_bands_ragged_orthonormalize_and_steps():
+    """200 bands (six full 32-column blocks and a ragged one of 8): the
+    blocked Cholesky with its inverse formed along the way, against the
+    oracle's orthonormalisation (FP64, 1e-10) and two PCG steps (the
+    Paterson-Stockmeyer exponential with the device's squarings); the mixed
+    path's orthonormality at 200 bands."""
+    cfg = cfg_of(grid=32, L=16.0, ecut=16.0, n_closed=198)
+    roks = built()
+    ctx = roks.Context(cfg, "fp64")
+    s = R.System(cfg)
+    assert s.nb == 200 and s.npw > 400
+    X = s.initial_orbitals(syn.orbital_uniforms(cfg, s.npw)) + 0.3 * syn.random_vectors(4, s.npw, s.nb)
+    psi = to_dev(ctx, X)
+    ctx.orthonormalize(psi)
+    assert rel(to_np(psi, s.npw), s.orthonormalize(X)) < TOL64
+    u = syn.orbital_uniforms(cfg, ctx.npw)
+    psi = ctx.init_orbitals(u)
+    P = s.initial_orbitals(u)
+    pcg = R.PCG(s)
+    for it in range(2):
+        info = ctx.pcg_step(psi)
+        P, ref = pcg.step(P)
+        assert abs(info["E_new"] - ref.E_new) <= TOL64 * max(1, abs(ref.E_new)), (it, info["E_new"], ref.E_new)
+    ctx.close()
+    ctx = roks.Context(cfg, "mixed")
+    psi = to_dev(ctx, X)
+    ctx.orthonormalize(psi)
+    Y = to_np(psi, s.npw)
+    assert np.abs(s.overlap(Y) - np.eye(s.nb)).max() < 5e-6
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_gradient_parts(precision):
+    """roks_gradient_parts: F, S, g = F - S gamma and g_I = F - S theta (Eqs. 7,
+    11, 12) against the oracle on the GPU's own orbitals (FP64 1e-9, mixed
+    2e-5 of the largest entry)."""
+    cfg = cfg_of()
+    roks, ctx, s = setup_pair(cfg, precision)
+    psi = ctx.init_orbitals(syn.orbital_uniforms(cfg, ctx.npw))
+    P = to_np(psi, s.npw)
+    ctx.density(psi)
+    ctx.potential()
+    f, sp, g, gi = ctx.gradient_parts(psi)
+    F_ref, S_ref = s.apply(P, s.potentials(s.class_densities(P)))
+    _, G_ref, gI_ref, _ = R.gradient_parts(P, F_ref, S_ref)
+    bar = 1e-9 if precision == "fp64" else 2e-5
+    assert rel(to_np(f, s.npw), F_ref) < bar
+    assert rel(to_np(g, s.npw), G_ref) < bar
+    assert rel(to_np(gi, s.npw), gI_ref) < bar
+    ctx.close()

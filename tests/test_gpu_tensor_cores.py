@@ -104,3 +104,29 @@ def test_tensor_cores_match_simt_kernels(tmp_path):
     assert rel(to_np(f, ctx.npw), d["f"]) < 2e-5
     assert rel(to_np(sp, ctx.npw), d["sp"]) < 2e-6
     ctx.close()
+
+
+def test_presplit_projectors_are_bit_identical(tmp_path):
+    """The projector matrix split once at setup (the products P^H X and P Y
+    copy its TF32 hi/lo blocks instead of converting them) gives the same
+    bits as the in-kernel conversion (ROKS_TC_PRESPLIT=0 in a child process)."""
+    roks = built()
+    cfg = big_cfg()
+    ctx = roks.Context(cfg, "mixed")
+    psi = ctx.init_orbitals(syn.orbital_uniforms(cfg, ctx.npw))
+    P = to_np(psi, ctx.npw)
+    np.save(tmp_path / "p.npy", P)
+    psi = to_dev(ctx, P)
+    ctx.density(psi)
+    ctx.potential()
+    f, sp, _ = ctx.apply_h(psi)
+    env = dict(os.environ, ROKS_TC_PRESPLIT="0")
+    out = tmp_path / "conv.npz"
+    r = subprocess.run([sys.executable, "-c", CHILD, ROOT, str(tmp_path / "p.npy"), str(out)], env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-3000:]
+    d = np.load(out)
+    assert int(d["tc"]) > 0
+    assert np.array_equal(to_np(f, ctx.npw), d["f"])
+    assert np.array_equal(to_np(sp, ctx.npw), d["sp"])
+    ctx.close()
