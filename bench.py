@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--force-calls", type=int, default=10,
                     help="timed roks_forces calls on the final orbitals; 0 skips them")
+    ap.add_argument("--n-closed", type=int, default=0,
+                    help="override the workload's closed-shell band count (profiler captures of a "
+                         "smaller context with the same block shapes); 0: the workload's own")
     ap.add_argument("--gamma-steps", type=int, default=20,
                     help="PCG steps of the Gamma-point leg (real orbitals, half sphere; 0: skip)")
     ap.add_argument("--diis-steps", type=int, default=50,
@@ -650,6 +653,8 @@ def run_gpu(args):
         torch.distributed.barrier()
     from paper_2605_28637_gb300 import roks, synthetic as syn
     cfg = replica_config(args.workload, rank)
+    if args.n_closed > 0:
+        cfg = syn_with(cfg, n_closed=args.n_closed)
     # the autotuner picks the density's band grouping and the tensor-core
     # split depth on this context's own buffers (roks_options.autotune)
     ctx = roks.Context(cfg, args.precision, autotune=1)

@@ -34,84 +34,115 @@ __global__ void k_big_load(int n, const double2* __restrict__ O, U* __restrict__
     A[idx] = ld_as<U>(make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y)));
 }
 
-// Factor the diagonal block kb (one block): L_kk, and D = L_kk^{-1} by a
-// column sweep in the same loop (solve L D = I for all right-hand sides at
-// once: row j of D is scaled by 1/L_jj as soon as column j of L is final,
-// then subtracted from the rows below).  Every thread forms the pivot
-// itself, so a step needs two barriers.  D goes to Dinv and to X = L^{-1}
-// (block kb, kb).
+// Factor the diagonal block kb (one block of 256 threads): L_kk, and
+// D = L_kk^{-1} by a column sweep in the same loop (solve L D = I for all
+// right-hand sides at once: row j of D is scaled by 1/L_jj as soon as
+// column j of L is final, then subtracted from the rows below).
+// Thread (lane i, warp w) keeps the elements (row i, column w + 8 q), q < 4,
+// of L and of D in registers.  Step j: the warp owning column j forms the
+// pivot (a shuffle from lane j), scales the column and publishes it with
+// 1/L_jj; after one barrier every thread updates its own elements, and the
+// lane owning row j + 1 of D publishes that row for the next step.  The
+// published column and row are double-buffered by the parity of j, so one
+// barrier per step suffices.  D goes to Dinv and to X = L^{-1} (block kb, kb).
 template <typename U>
 __global__ void __launch_bounds__(256) k_big_diag(int n, int kb, U* __restrict__ A, U* __restrict__ Dinv,
                                                   U* __restrict__ Xm, int* flag) {
     using R = typename Real<U>::type;
-    __shared__ U L[BK][BK + 1];   // L[col][row]
-    __shared__ U X[BK][BK + 1];   // X[col][row]
-    __shared__ R piv[BK];
+    __shared__ U colbuf[2][BK];    // column j of L (scaled), by row
+    __shared__ U xrow[2][BK];      // row j of D before its scaling, by column
+    __shared__ R invbuf[2];
     const int k0 = kb * BK;
     const int m = min(BK, n - k0);
-    for (int t = threadIdx.x; t < BK * BK; t += blockDim.x) {
-        const int i = t % BK, j = t / BK;
+    const int i = threadIdx.x & 31, w = threadIdx.x >> 5;
+    U Lr[4], Xr[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int k = w + 8 * q;
         U v;
-        v.x = 0; v.y = 0;
-        if (i < m && j < m) v = A[(int64_t)(k0 + j) * n + k0 + i];
-        L[j][i] = v;
-        U z; z.x = (i == j) ? R(1) : R(0); z.y = 0;
-        X[j][i] = z;
+        v.x = 0;
+        v.y = 0;
+        if (i < m && k < m) v = A[(int64_t)(k0 + k) * n + k0 + i];
+        Lr[q] = v;
+        Xr[q].x = (i == k) ? R(1) : R(0);
+        Xr[q].y = 0;
     }
-    __syncthreads();
+    // row 0 of D (D[0][0] = 1 before scaling) for step 0
+    if (w == 0 && i == 0) xrow[0][0] = Xr[0];
     for (int j = 0; j < m; ++j) {
-        R d = L[j][j].x;
-        if (!(d > R(0))) {
-            if (threadIdx.x == 0 && flag) atomicCAS(flag, 0, k0 + j + 1);
-            d = R(1);
-        }
-        const R p = sqrt(d);
-        const R inv = R(1) / p;
-        if (threadIdx.x == 0) piv[j] = p;
-        // column j of L below the diagonal, row j of D (columns c <= j)
-        const int r = m - j - 1;
-        for (int t = threadIdx.x; t < r + j + 1; t += blockDim.x) {
-            if (t < r) {
-                L[j][j + 1 + t].x *= inv;
-                L[j][j + 1 + t].y *= inv;
-            } else {
-                const int c = t - r;
-                X[c][j].x *= inv;
-                X[c][j].y *= inv;
+        const int b = j & 1;
+        const int wj = j & 7, qj = j >> 3;
+        if (w == wj) {
+            // this warp owns column j: pivot from lane j
+            U lj = Lr[0];
+#pragma unroll
+            for (int q = 1; q < 4; ++q)
+                if (q == qj) lj = Lr[q];
+            R d = __shfl_sync(0xffffffffu, lj.x, j);
+            if (!(d > R(0))) {
+                if (i == 0 && flag) atomicCAS(flag, 0, k0 + j + 1);
+                d = R(1);
             }
+            const R p = sqrt(d);
+            const R inv = R(1) / p;
+            if (i > j) {
+                lj.x *= inv;
+                lj.y *= inv;
+            } else if (i == j) {
+                lj.x = p;
+                lj.y = 0;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (q == qj) Lr[q] = lj;
+            colbuf[b][i] = lj;
+            if (i == 0) invbuf[b] = inv;
         }
         __syncthreads();
-        // trailing L (j < k <= i) and the rows i > j of D (columns c <= j)
-        for (int t = threadIdx.x; t < r * r + r * (j + 1); t += blockDim.x) {
-            if (t < r * r) {
-                const int i = j + 1 + t % r, k = j + 1 + t / r;
-                if (k > i) continue;
-                const U a = L[j][i], b = L[j][k];
-                L[k][i].x -= a.x * b.x + a.y * b.y;
-                L[k][i].y -= a.y * b.x - a.x * b.y;
-            } else {
-                const int q = t - r * r;
-                const int i = j + 1 + q % r, c = q / r;
-                const U a = L[j][i], x = X[c][j];
-                X[c][i].x -= a.x * x.x - a.y * x.y;
-                X[c][i].y -= a.x * x.y + a.y * x.x;
+        const R inv = invbuf[b];
+        const U a = colbuf[b][i];   // L(i, j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = w + 8 * q;
+            if (k > j && i >= k) {
+                // trailing L(i, k) -= L(i, j) conj(L(k, j))
+                const U c = colbuf[b][k];
+                Lr[q].x -= a.x * c.x + a.y * c.y;
+                Lr[q].y -= a.y * c.x - a.x * c.y;
+            } else if (k <= j) {
+                if (i == j) {
+                    // row j of D, final: scaled by 1 / L_jj
+                    Xr[q].x *= inv;
+                    Xr[q].y *= inv;
+                } else if (i > j) {
+                    // D(i, k) -= L(i, j) D(j, k), D(j, k) = xrow * inv
+                    const U xv = xrow[b][k];
+                    const R xr = xv.x * inv, xi = xv.y * inv;
+                    Xr[q].x -= a.x * xr - a.y * xi;
+                    Xr[q].y -= a.x * xi + a.y * xr;
+                }
             }
         }
-        __syncthreads();
+        // row j + 1 of D (columns k <= j + 1) for the next step
+        if (i == j + 1) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = w + 8 * q;
+                if (k <= j + 1) xrow[b ^ 1][k] = Xr[q];
+            }
+        }
     }
-    for (int t = threadIdx.x; t < BK * BK; t += blockDim.x) {
-        const int i = t % BK, j = t / BK;
-        if (i < m && j < m) {
-            U l = L[j][i];
-            if (i == j) {
-                l.x = piv[j];
-                l.y = 0;
-            }
-            A[(int64_t)(k0 + j) * n + k0 + i] = l;
-            Xm[(int64_t)(k0 + j) * n + k0 + i] = X[j][i];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int k = w + 8 * q;
+        if (i < m && k < m) {
+            A[(int64_t)(k0 + k) * n + k0 + i] = Lr[q];
+            Xm[(int64_t)(k0 + k) * n + k0 + i] = Xr[q];
         }
-        U z; z.x = 0; z.y = 0;
-        Dinv[(int64_t)kb * BK * BK + j * BK + i] = (i < m && j < m) ? X[j][i] : z;
+        U z;
+        z.x = 0;
+        z.y = 0;
+        Dinv[(int64_t)kb * BK * BK + k * BK + i] = (i < m && k < m) ? Xr[q] : z;
     }
 }
 
