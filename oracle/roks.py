@@ -305,12 +305,13 @@ class System:
             v[~nz] = 2.0 * np.pi * Rc * Rc
         return v
 
-    def exchange(self, Occ: np.ndarray, X: np.ndarray | None = None, classes=None):
+    def exchange(self, Occ: np.ndarray, X: np.ndarray | None = None, classes=None, pair_integrals: bool = True):
         """Pair terms W_jn(r) = sum_G v(G) rho_jn(G) e^{iGr}, rho_jn = psi_j^* x_n,
         psi_j the occupied orbitals Occ.  Returns the operator part
         -alpha sum_j wx(k,k_j) psi_j W_jn for each column x_n of X (default Occ),
         as plane-wave coefficients, and the pair integrals of the occupied set
-        K_ij = Omega sum_G v(G) |rho_ij(G)|^2."""
+        K_ij = Omega sum_G v(G) |rho_ij(G)|^2 (None when pair_integrals is
+        False: the operator alone)."""
         if X is None:
             X = Occ
         if classes is None:
@@ -327,6 +328,8 @@ class System:
                 W = self.grid_synth(v * rG)
                 X += self.WX[classes[n], self.cls[j]] * psis[j] * W
             out[:, n] = -self.alpha * self.to_pw(X)
+        if not pair_integrals:
+            return out, None
         K = np.zeros((self.nb, self.nb))
         for i in range(self.nb):
             for j in range(self.nb):
@@ -356,7 +359,7 @@ class System:
             F[:, n] = kin + loc + nl
             S[:, n] = Psi[:, n] + self.P @ (self.Q @ B[:, n])
         if self.alpha != 0.0:
-            X, _ = self.exchange(occ, Psi, classes)
+            X, _ = self.exchange(occ, Psi, classes, pair_integrals=False)
             F += X
         return F, S
 
