@@ -116,6 +116,37 @@ def aggregate_value(nb: int, steps: int, world: int, ms_max: float) -> float:
 # FP32 peak is provided): 152 SMs x 128 lanes x 2 flops x 2.07 GHz
 FP32_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_TFLOPS_NOMINAL = 1.25
+# FP32 (SIMT) and FP64 throughput measured on this GPU by measure_alu_peaks
+# (cuBLAS SGEMM with TF32 off, DGEMM), when the bench has run it
+MEASURED_ALU = {}
+
+
+def measure_alu_peaks(torch):
+    """Dense GEMM throughput of the library cuBLAS in FP32 (TF32 disabled)
+    and FP64, timed with CUDA events after a warm-up: the denominators of the
+    SIMT-FP32 and FP64 rooflines (MEASURED_PEAKS.json holds the HBM copy and
+    BF16 rates only)."""
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        for name, dt, n, reps in (("fp32", torch.float32, 8192, 5), ("fp64", torch.float64, 4096, 3)):
+            a = torch.randn(n, n, dtype=dt, device="cuda")
+            b = torch.randn(n, n, dtype=dt, device="cuda")
+            c = a @ b
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                c = a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            out[name] = 2.0 * n ** 3 * reps / (e0.elapsed_time(e1) / 1000.0) / 1e12
+            del a, b, c
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    MEASURED_ALU.update(out)
+    return out
 
 
 def peaks():
@@ -265,7 +296,11 @@ def alu_peak(precision: str, bound: str = "alu"):
         b, kind = bf16_peak()
         return b * (1.1 / 2.25) / 3.0, (f"{kind} bf16 peak x 1.1/2.25 (TF32) / 3 TF32 products per FP32 product")
     if precision == "fp64":
+        if "fp64" in MEASURED_ALU:
+            return MEASURED_ALU["fp64"], "measured FP64 (cuBLAS DGEMM on this GPU)"
         return FP64_TFLOPS_NOMINAL, "nominal FP64: 1.25 TFLOP/s (GB300 dense FP64)"
+    if "fp32" in MEASURED_ALU:
+        return MEASURED_ALU["fp32"], "measured FP32 SIMT (cuBLAS SGEMM, TF32 off, on this GPU)"
     return FP32_TFLOPS_NOMINAL, "nominal FP32: 152 SMs x 128 lanes x 2 flops x 2.07 GHz"
 
 
@@ -411,9 +446,51 @@ def oracle_parallel(name: str, seed: int, mode: str, amount: float, warmup: int 
             "npw": res[0][2], "nproj": res[0][3], "host_cores": cores}
 
 
+def cpp_oracle_rate(name: str, seed: int, mode: str, amount: float, warmup: int = 0):
+    """The C++ FP64 oracle's band applies on all host cores (OpenMP, one band
+    per thread): F^n|n> of `cores` bands of the seeded start at the potential
+    of its first two bands, repeated `amount` times (mode "steps", after
+    `warmup` untimed rounds) or for `amount` seconds."""
+    from oracle import cpp_oracle as CO
+    from paper_2605_28637_gb300 import synthetic as syn
+    cfg = syn.make_config(name, seed)
+    cores = host_cores()
+    c = CO.CppSystem(cfg, threads=cores)
+    g2 = (np.asarray(c.miller, dtype=np.float64) ** 2).sum(axis=1) * (2.0 * np.pi / cfg["L"]) ** 2
+
+    def coeffs(b0, nb):
+        u = syn.orbital_uniforms(cfg, c.npw, b0, nb)
+        return (u[..., 0] + 1j * u[..., 1]).T / (1.0 + g2)[:, None]
+
+    Vk, _ = c.potentials(c.class_densities(coeffs(0, min(2, c.nb))))
+    nb = min(cores, c.nb)
+    X = coeffs(0, nb)
+    cls = c.cls[:nb]
+    for _ in range(warmup):
+        c.apply(X, Vk, classes=cls)
+    t0 = time.perf_counter()
+    rounds = 0
+    while (mode == "steps" and rounds < amount) or (mode == "seconds" and (rounds == 0 or
+                                                                            time.perf_counter() - t0 < amount)):
+        c.apply(X, Vk, classes=cls)
+        rounds += 1
+    dt = time.perf_counter() - t0
+    out = {"value": rounds * nb / dt, "cores": cores, "seconds": dt, "applies": rounds * nb, "npw": c.npw,
+           "nproj": c.nproj, "host_cores": cores, "kind": "C++ oracle (OpenMP)"}
+    c.close()
+    return out
+
+
 def cpu_baseline_leg(name: str, seconds: float):
-    r = oracle_parallel(name, 0, "seconds", seconds)
-    desc = (f"F^n|n> (kinetic + local + non-local, FP64 numpy oracle) of one band per core of {name} "
+    """The FP64 C++ oracle on all host cores; the NumPy oracle (one process
+    per core) if the C++ one cannot be built on this host."""
+    try:
+        r = cpp_oracle_rate(name, 0, "seconds", seconds)
+        impl = "FP64 C++ oracle, OpenMP"
+    except Exception:
+        r = oracle_parallel(name, 0, "seconds", seconds)
+        impl = "FP64 numpy oracle, one process per core"
+    desc = (f"F^n|n> (kinetic + local + non-local, {impl}) of one band per core of {name} "
             f"({r['npw']} plane waves, {r['nproj']} projectors) at the potential of the seeded start's first two "
             f"bands, repeated for about {seconds:.0f} s on {r['cores']} host cores at once "
             f"({r['applies']} band applies); scaled to band-applies/s")
@@ -429,10 +506,15 @@ def run_reference(args):
     from paper_2605_28637_gb300 import synthetic as syn
     cfg = syn.make_config(args.workload, 0)
     # each step: every host core applies F to one band of the workload
-    r = oracle_parallel(args.workload, 0, "steps", args.steps, warmup=args.warmup)
+    try:
+        r = cpp_oracle_rate(args.workload, 0, "steps", args.steps, warmup=args.warmup)
+        impl = "FP64 C++ oracle (OpenMP)"
+    except Exception:
+        r = oracle_parallel(args.workload, 0, "steps", args.steps, warmup=args.warmup)
+        impl = "FP64 numpy oracle (one process per core)"
     value = r["value"]
     sample = (f"each step: F^n|n> (kinetic + local + non-local) of one band per host core of {cfg['name']} "
-              f"({cfg['grid']}^3, {r['npw']} plane waves, {r['nproj']} projectors), FP64 numpy oracle, "
+              f"({cfg['grid']}^3, {r['npw']} plane waves, {r['nproj']} projectors), {impl}, "
               f"{r['cores']} cores at once, fixed potential")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * r["seconds"] / args.steps, "higher_is_better": True,
@@ -617,6 +699,44 @@ def gamma_leg(args, cfg, torch, complex_ms_per_step):
     return out
 
 
+def fp64_leg(cfg, torch, steps=5):
+    """The plain FP64 path on the convergence workload: seconds per PCG step
+    (graph replays) and the rooflines of its kernel families from a profiled
+    eager pass, against the measured FP64 rate (contractions) and the HBM
+    copy bandwidth (transform stages)."""
+    from paper_2605_28637_gb300 import roks, synthetic as syn
+    ctx = roks.Context(cfg, "fp64")
+    psi = ctx.init_orbitals(syn.orbital_uniforms(cfg, ctx.npw))
+    for _ in range(3):
+        ctx.pcg_step(psi)
+    ms, _, _ = time_pcg(ctx, psi, steps, torch)
+    _, _, prof = time_pcg(ctx, psi, steps, torch, profile=True)
+    prof = [e for e in prof if e["name"] not in ("kernel_launches", "tensor_core_launches")]
+    total = sum(e["ms"] for e in prof) or 1.0
+    hbm, peak_kind = peaks()
+    rows = []
+    for e in sorted(prof, key=lambda e: -e["ms"]):
+        work = family_work(ctx, cfg, e["name"], 16, 8, "fp64")
+        if work is None:
+            continue
+        bound, amount = work
+        per = e["ms"] / e["launches"]
+        if bound == "hbm":
+            ach = amount / (per / 1000.0) / 1e9
+            rows.append({"bound": "hbm", "kernel": e["name"], "achieved": ach, "peak": hbm, "unit": "GB/s",
+                         "frac": ach / hbm, "peak_kind": f"{peak_kind} (copy bandwidth)", "ms_per_launch": per,
+                         "share_of_step": e["ms"] / total})
+        else:
+            pk, kind = alu_peak("fp64", bound)
+            ach = amount / (per / 1000.0) / 1e12
+            rows.append({"bound": "alu", "kernel": e["name"], "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                         "frac": ach / pk, "peak_kind": kind, "ms_per_launch": per, "share_of_step": e["ms"] / total})
+    out = {"workload": cfg["name"], "ms_per_step": ms / steps, "rooflines": rows,
+           "profile": {e["name"]: {"launches": e["launches"], "ms": e["ms"]} for e in prof}}
+    ctx.close()
+    return out
+
+
 def csize_of(precision):
     """Bytes of one complex coefficient on the path."""
     return 16 if precision == "fp64" else 8
@@ -770,6 +890,8 @@ def run_gpu(args):
                       "launches_per_call": f_launch[0]["launches"] / args.force_calls if f_launch else None,
                       "max_abs_force_ha_per_bohr": float(abs(Fa).max()),
                       "launch": "eager, one host read per call"}
+    # ---- measured FP32 (SIMT) and FP64 rates for the ALU rooflines
+    alu_measured = measure_alu_peaks(torch)
     # ---- rooflines of the kernel families with known algorithmic work; the
     # family with the most device time is the line's "roofline"
     csize = 16 if args.precision == "fp64" else 8
@@ -843,7 +965,8 @@ def run_gpu(args):
                "speedup_s_per_iter_mixed_vs_fp64": g64["s_per_iter"] / gl["mixed_tpa"]["s_per_iter"],
                "mixed_diis_singlet": converge_diis(base, "mixed", args.converge_iters, torch,
                                                    min(args.converge_seconds, 20.0), args.g_tol),
-               "note": "time-to-solution ratios only between converged legs in the FP64 leg's state"}
+               "note": "time-to-solution ratios only between converged legs in the FP64 leg's state",
+               "fp64_path": fp64_leg(ground, torch)}
     gamma = None
     if args.gamma_steps > 0 and rank == 0:
         gamma = gamma_leg(args, cfg, torch, ms_max / args.steps)
@@ -874,6 +997,7 @@ def run_gpu(args):
             "clocks": ck,
             "apply_only": {"value": ctx.nb / (apply_ms / 1000.0), "unit": UNIT, "ms_per_apply_all_bands": apply_ms},
             "pcg": pcg,
+            "alu_peaks_measured_tflops": alu_measured,
             "diis": diis,
             "forces": forces_leg,
             "hybrid": hybrid,
