@@ -700,12 +700,15 @@ __global__ void k_small_gemm(int M, int N, int K, const double2* __restrict__ A,
 // tx + 16 j (i, j < 2); K in slices of 16 staged in shared memory, each load
 // coalesced along the operand's contiguous index.  Arithmetic type R (float
 // on the mixed path): every slice is summed on its own before it joins the
-// running sum, so that rounding grows with K / 16.
+// running sum, so that rounding grows with K / 16.  TI: the stored operand
+// type (double2, or float2 packed once by k_pack_f32 on the mixed path, so
+// that the FP64 -> FP32 conversions, which run on the narrow FP64 pipe, are
+// made once per element instead of once per output tile).
 constexpr int BS_T = 32, BS_K = 16, BS_R = 2;
 
-template <typename R>
-__global__ void __launch_bounds__(256) k_bs_gemm(int M, int N, int K, const double2* __restrict__ A, int lda,
-                                                 int ca, const double2* __restrict__ B, int ldb, int cb,
+template <typename R, typename TI>
+__global__ void __launch_bounds__(256) k_bs_gemm(int M, int N, int K, const TI* __restrict__ A, int lda,
+                                                 int ca, const TI* __restrict__ B, int ldb, int cb,
                                                  double2* __restrict__ C, int ldc, double alpha, double beta) {
     __shared__ c2<R> As[BS_K][BS_T + 1];
     __shared__ c2<R> Bs[BS_K][BS_T + 1];
@@ -723,7 +726,7 @@ __global__ void __launch_bounds__(256) k_bs_gemm(int M, int N, int K, const doub
             c2<R> v;
             v.x = v.y = R(0);
             if (m0 + ma < M && k0 + ka < K) {
-                const double2 d = ca ? A[(int64_t)(m0 + ma) * lda + k0 + ka] : A[(int64_t)(k0 + ka) * lda + m0 + ma];
+                const TI d = ca ? A[(int64_t)(m0 + ma) * lda + k0 + ka] : A[(int64_t)(k0 + ka) * lda + m0 + ma];
                 v.x = (R)d.x;
                 v.y = ca ? -(R)d.y : (R)d.y;
             }
@@ -733,7 +736,7 @@ __global__ void __launch_bounds__(256) k_bs_gemm(int M, int N, int K, const doub
             c2<R> w;
             w.x = w.y = R(0);
             if (n0 + nb < N && k0 + kb < K) {
-                const double2 d = cb ? B[(int64_t)(k0 + kb) * ldb + n0 + nb] : B[(int64_t)(n0 + nb) * ldb + k0 + kb];
+                const TI d = cb ? B[(int64_t)(k0 + kb) * ldb + n0 + nb] : B[(int64_t)(n0 + nb) * ldb + k0 + kb];
                 w.x = (R)d.x;
                 w.y = cb ? -(R)d.y : (R)d.y;
             }
@@ -794,7 +797,16 @@ static void bs_gemm(int M, int N, int K, const double2* A, int lda, bool ca, con
              double2* C, int ldc, double alpha, double beta, cudaStream_t st) {
     const dim3 g((unsigned)((M + BS_T - 1) / BS_T), (unsigned)((N + BS_T - 1) / BS_T));
     roks::count_launch();
-    k_bs_gemm<R><<<g, 256, 0, st>>>(M, N, K, A, lda, ca ? 1 : 0, B, ldb, cb ? 1 : 0, C, ldc, alpha, beta);
+    k_bs_gemm<R, double2><<<g, 256, 0, st>>>(M, N, K, A, lda, ca ? 1 : 0, B, ldb, cb ? 1 : 0, C, ldc, alpha, beta);
+}
+
+// dst (rows x cols, leading dimension rows) = src (FP64, leading dimension ld) in FP32
+__global__ void k_pack_f32(int rows, int cols, const double2* __restrict__ src, int ld, float2* __restrict__ dst) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)rows * cols) return;
+    const int r = (int)(i % rows), c = (int)(i / rows);
+    const double2 v = src[(int64_t)c * ld + r];
+    dst[i] = make_float2((float)v.x, (float)v.y);
 }
 
 // op(A): A (M x K) or A^H when ca (A stored K x M); op(B) likewise.
@@ -846,10 +858,25 @@ __global__ void k_small_gemm_f32(int M, int N, int K, const double2* __restrict_
 }
 
 void small_gemm_f32(int M, int N, int K, const double2* A, int lda, bool ca, const double2* B, int ldb, bool cb,
-                    double2* C, int ldc, double alpha, double beta, cudaStream_t st) {
+                    double2* C, int ldc, double alpha, double beta, cudaStream_t st, void* work, size_t work_bytes) {
     if (M <= 0 || N <= 0) return;
     if (bs_tiled(M, N, K)) {
-        bs_gemm<float>(M, N, K, A, lda, ca, B, ldb, cb, C, ldc, alpha, beta, st);
+        // the stored shapes of A (K x M for A^H, else M x K) and B (N x K for B^H, else K x N)
+        const int ra = ca ? K : M, na = ca ? M : K, rb = cb ? N : K, nbc = cb ? K : N;
+        const size_t need = sizeof(float2) * ((size_t)ra * na + (size_t)rb * nbc);
+        if (work && need <= work_bytes) {
+            float2* Ap = static_cast<float2*>(work);
+            float2* Bp = Ap + (size_t)ra * na;
+            const int64_t ta = (int64_t)ra * na, tb = (int64_t)rb * nbc;
+            roks::count_launch(), k_pack_f32<<<(unsigned)((ta + 255) / 256), 256, 0, st>>>(ra, na, A, lda, Ap);
+            roks::count_launch(), k_pack_f32<<<(unsigned)((tb + 255) / 256), 256, 0, st>>>(rb, nbc, B, ldb, Bp);
+            const dim3 g((unsigned)((M + BS_T - 1) / BS_T), (unsigned)((N + BS_T - 1) / BS_T));
+            roks::count_launch();
+            k_bs_gemm<float, float2><<<g, 256, 0, st>>>(M, N, K, Ap, ra, ca ? 1 : 0, Bp, rb, cb ? 1 : 0, C, ldc, alpha,
+                                                        beta);
+        } else {
+            bs_gemm<float>(M, N, K, A, lda, ca, B, ldb, cb, C, ldc, alpha, beta, st);
+        }
         return;
     }
     const long long threads = (long long)M * N * 32;

@@ -470,9 +470,12 @@ struct Impl {
             PROF("orth_small");
             apply_DQ(ctx->nproj, nb, ctx->d_B2, ctx->d_blk_off, ctx->d_blk_n, ctx->d_Drow, ctx->d_Qrow, nullptr,
                      nullptr, ctx->d_QB, st);
-            (ctx->prec == ROKS_MIXED ? small_gemm_f32 : small_gemm)(nb, nb, ctx->nproj, ctx->d_B2, ctx->nproj, true,
-                                                                   ctx->d_QB, ctx->nproj, false, ctx->d_O, nb, 1.0,
-                                                                   1.0, st);
+            if (ctx->prec == ROKS_MIXED)
+                small_gemm_f32(nb, nb, ctx->nproj, ctx->d_B2, ctx->nproj, true, ctx->d_QB, ctx->nproj, false, ctx->d_O,
+                               nb, 1.0, 1.0, st, ctx->d_gemm_work, ctx->gemm_work_elems * sizeof(double2));
+            else
+                small_gemm(nb, nb, ctx->nproj, ctx->d_B2, ctx->nproj, true, ctx->d_QB, ctx->nproj, false, ctx->d_O, nb,
+                           1.0, 1.0, st);
         }
         // mixed path, small n: L^{-H} = I + Xi^H in deviation form (FP32 errors
         // relative to |O - I|); out = in + in Xi^H keeps the identity exact
@@ -503,9 +506,13 @@ struct Impl {
             PROF("orth_small");
             if (dev)
                 CK(cudaMemcpyAsync(Bout, ctx->d_B2, sizeof(double2) * ctx->nproj * nb, cudaMemcpyDeviceToDevice, st));
-            (ctx->prec == ROKS_MIXED ? small_gemm_f32 : small_gemm)(ctx->nproj, nb, nb, ctx->d_B2, ctx->nproj,
-                                                                   false, ctx->d_LinvH, nb, false, Bout, ctx->nproj,
-                                                                   1.0, dev ? 1.0 : 0.0, st);
+            if (ctx->prec == ROKS_MIXED)
+                small_gemm_f32(ctx->nproj, nb, nb, ctx->d_B2, ctx->nproj, false, ctx->d_LinvH, nb, false, Bout,
+                               ctx->nproj, 1.0, dev ? 1.0 : 0.0, st, ctx->d_gemm_work,
+                               ctx->gemm_work_elems * sizeof(double2));
+            else
+                small_gemm(ctx->nproj, nb, nb, ctx->d_B2, ctx->nproj, false, ctx->d_LinvH, nb, false, Bout, ctx->nproj,
+                           1.0, dev ? 1.0 : 0.0, st);
         }
         CK(cudaGetLastError());
         return ROKS_OK;

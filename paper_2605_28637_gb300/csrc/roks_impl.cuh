@@ -241,8 +241,11 @@ long long tcg_launches_take();
 void small_gemm(int M, int N, int K, const double2* A, int lda, bool ca, const double2* B, int ldb,
                 bool cb, double2* C, int ldc, double alpha, double beta, cudaStream_t st);
 // Same with FP32 arithmetic (FP64 storage, alpha and beta applied in FP64).
+// work (optional, work_bytes): the large products pack both operands into
+// FP32 there first.
 void small_gemm_f32(int M, int N, int K, const double2* A, int lda, bool ca, const double2* B, int ldb, bool cb,
-                    double2* C, int ldc, double alpha, double beta, cudaStream_t st);
+                    double2* C, int ldc, double alpha, double beta, cudaStream_t st, void* work = nullptr,
+                    size_t work_bytes = 0);
 // O (Hermitian) -> LinvH = L^{-H}, L L^H = O.  flag[0] set to 1 + column on failure.
 void cholesky_inverse(int n, const double2* O, double2* Lw, double2* LinvH, int* flag, cudaStream_t st);
 // n within the single-block factorisations
