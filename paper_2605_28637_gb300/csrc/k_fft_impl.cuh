@@ -308,7 +308,11 @@ __global__ void __launch_bounds__(kThreads) k_band_x_inv_full(Sphere s, const c2
 // to the group's own slot (slot[g], N^3 doubles, written in full so no
 // clearing is needed); the open bands a and b, one band each, go straight to
 // rho3.  k_density_reduce adds the slots in group order.
-template <typename T, int N>
+// The staging buffers hold full x lines, element e of line l at e * TL + l:
+// the rows of the planes outside the sphere (and the lines past N of the
+// last z tile) are zeroed once, so the first pass loads without tests.
+// SEL: (Re psi)^2 (part_sel 1) or (Im psi)^2 (part_sel 2) instead of |psi|^2.
+template <typename T, int N, bool SEL>
 __global__ void __launch_bounds__(kThreads) k_band_x_density(Sphere s, const c2<T>* __restrict__ tw,
                                                              const c2<T>* __restrict__ Yp,
                                                              typename DensAcc<T>::S* __restrict__ rho3,
@@ -324,7 +328,7 @@ __global__ void __launch_bounds__(kThreads) k_band_x_density(Sphere s, const c2<
     extern __shared__ __align__(16) unsigned char smem[];
     V* buf = reinterpret_cast<V*>(smem);
     V* tws = buf + N * LS;
-    V* stg = tws + N;   // two staging buffers of np x TL (planes x lines) for the next band
+    V* stg = tws + N;   // two staging buffers of N x TL (x lines) for the next band
     load_twiddles<V, N>(tws, tw);
     const int z0 = blockIdx.x * TL;
     const int y = blockIdx.y;
@@ -333,21 +337,27 @@ __global__ void __launch_bounds__(kThreads) k_band_x_density(Sphere s, const c2<
     const int nmax = s.nmax, np = s.np;
     const int gbeg = g * gs, gend = min(nbb, gbeg + gs);
     // rows of TL lines are 16-byte aligned in both memories (N even, TL a
-    // multiple of 16): copy them with 16-byte cp.async
+    // multiple of 16): copy them with 16-byte cp.async, only the chunks of
+    // lines z < N (the last tile may overhang the row)
     constexpr int CH = TL * (int)sizeof(V) / 16;   // 16-byte chunks per row
+    const int chv = min(CH, (N - z0) * (int)sizeof(V) / 16);
+    for (int t = threadIdx.x; t < 2 * N * TL; t += blockDim.x) stg[t] = mk<T>(T(0), T(0));
+    __syncthreads();
     auto stage = [&](int band, int which) {
         const char* src = reinterpret_cast<const char*>(Yp + (int64_t)band * np * N * N + y * N + z0);
-        char* dst = reinterpret_cast<char*>(stg + which * np * TL);
+        char* dst = reinterpret_cast<char*>(stg + which * N * TL);
         for (int c = threadIdx.x; c < np * CH; c += blockDim.x) {
             const int row = c / CH, k = c - row * CH;
-            const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst + row * TL * sizeof(V) + 16 * k));
+            if (k >= chv) continue;
+            // plane row (i + nmax) -> x index e = i mod N
+            const int e = row >= nmax ? row - nmax : N + row - nmax;
+            const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst + e * TL * sizeof(V) + 16 * k));
             const char* sp = src + (int64_t)row * N * N * sizeof(V) + 16 * k;
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(sp) : "memory");
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
     if (gbeg < gend) stage(gbeg, 0);
-    __syncthreads();
     DS* slot_g = slot + (int64_t)g * N3;
     bool slot_written = false;
     int bb = gbeg;
@@ -372,17 +382,14 @@ __global__ void __launch_bounds__(kThreads) k_band_x_density(Sphere s, const c2<
                     asm volatile("cp.async.wait_group 0;" ::: "memory");
                 }
                 __syncthreads();
-                const V* sb = stg + ((bb - gbeg) & 1) * np * TL;
+                const V* sb = stg + ((bb - gbeg) & 1) * N * TL;
                 fft_io<V, N, +1, TL, LS, kThreads, false, false>(
-                    buf, tws,
-                    [&](int line, int e) {
-                        const int i = signed_freq(e, N);
-                        return (i >= -nmax && i <= nmax) ? sb[(i + nmax) * TL + line] : mk<T>(T(0), T(0));
-                    },
+                    buf, tws, [&](int line, int e) { return sb[e * TL + line]; },
                     [&](int, int, V v, int q, int r) {
-                        // part_sel 1 / 2: the real / imaginary part alone (one
-                        // orbital of a Gamma-point packed pair)
-                        part[q][r] += part_sel == 0 ? v.x * v.x + v.y * v.y : (part_sel == 1 ? v.x * v.x : v.y * v.y);
+                        if constexpr (SEL)
+                            part[q][r] += part_sel == 1 ? v.x * v.x : v.y * v.y;
+                        else
+                            part[q][r] += v.x * v.x + v.y * v.y;
                     });
                 __syncthreads();
             }
@@ -552,17 +559,22 @@ struct BandFft {
     static void x_density(const Sphere& s, const V* tw, const V* Yp, double* rho3, double* slot, int ngroups,
                           int b0, int nbb, int nc, double scale, int part_sel, int cls_override,
                           cudaStream_t st) {
-        // tile, twiddles and two staging buffers of np x TL
-        const size_t sm = SM + 2 * sizeof(V) * (size_t)s.np * TL;
-        set_smem(k_band_x_density<T, N>, sm);
+        // tile, twiddles and two staging buffers of N x TL
+        const size_t sm = SM + 2 * sizeof(V) * (size_t)N * TL;
+        set_smem(k_band_x_density<T, N, false>, sm);
+        set_smem(k_band_x_density<T, N, true>, sm);
         const int gs = (nbb + ngroups - 1) / ngroups;
         const int ng = (nbb + gs - 1) / gs;
         dim3 g((N + TL - 1) / TL, N, ng);
         using DS = typename DensAcc<T>::S;
         DS* r3 = reinterpret_cast<DS*>(rho3);
         DS* sl = reinterpret_cast<DS*>(slot);
-        roks::count_launch(), k_band_x_density<T, N><<<g, kThreads, sm, st>>>(s, tw, Yp, r3, sl, b0, nbb, gs, nc,
-                                                                            T(scale), part_sel, cls_override);
+        if (part_sel == 0)
+            roks::count_launch(), k_band_x_density<T, N, false><<<g, kThreads, sm, st>>>(
+                                      s, tw, Yp, r3, sl, b0, nbb, gs, nc, T(scale), part_sel, cls_override);
+        else
+            roks::count_launch(), k_band_x_density<T, N, true><<<g, kThreads, sm, st>>>(
+                                      s, tw, Yp, r3, sl, b0, nbb, gs, nc, T(scale), part_sel, cls_override);
         if (!sl) return;
         const int N3 = N * N * N;
         roks::count_launch(), k_density_reduce<T><<<(unsigned)((N3 + 255) / 256), 256, 0, st>>>(N3, ng, sl, r3);
