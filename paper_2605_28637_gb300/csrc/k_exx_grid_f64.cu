@@ -1,0 +1,5 @@
+// Double-precision instantiation of the exact exchange's fused grid passes.
+#include "k_exx_grid.cuh"
+namespace roks {
+template void exx_batch_grid<double>(const ExxArgs<double>&, int, int, bool, cudaStream_t);
+}

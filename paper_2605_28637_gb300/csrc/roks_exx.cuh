@@ -43,5 +43,11 @@ void exx_setup_kernel(int N, double L, int bare, T* vG, cudaStream_t st);
 // fields X too when want_field.
 template <typename T>
 void exx_pairs(const ExxArgs<T>& a, bool want_field, cudaStream_t st);
+// The grid work of one batch of pairs p0 .. p0 + np - 1 (k_exx_grid.cuh):
+// pair densities, transforms, v(G) and the block partials of the pair
+// integrals in a.part (np x kExxBlocks), and with want_field the fields
+// added to a.X.
+template <typename T>
+void exx_batch_grid(const ExxArgs<T>& a, int p0, int np, bool want_field, cudaStream_t st);
 
 }  // namespace roks
