@@ -74,7 +74,9 @@ __global__ void __launch_bounds__(kThreads) k_band_z_inv(Sphere s, const c2<T>* 
     }
 }
 
-template <typename T, int N>
+// KIN: add the kinetic term w_k |G|^2/2 psi(G) while scattering out; without
+// it the transform alone (the Gamma-point unpack adds the kinetic term)
+template <typename T, int N, bool KIN>
 __global__ void __launch_bounds__(kThreads) k_band_z_fwd(Sphere s, const c2<T>* __restrict__ tw,
                                                          const c2<T>* __restrict__ Zc,
                                                          c2<T>* __restrict__ out, int64_t ldo,
@@ -108,11 +110,10 @@ __global__ void __launch_bounds__(kThreads) k_band_z_fwd(Sphere s, const c2<T>* 
     }
     __syncthreads();
     tile_fft<V, N, -1, TL, LS, kThreads>(buf, tws);
-    // psi null: the transform alone (the Gamma-point unpack adds the kinetic term)
     const int cls = b < n_closed ? 0 : b - n_closed + 1;
-    const T w = psi ? wk[cls] : T(0);
+    const T w = KIN ? wk[cls] : T(0);
     V* o = out + (int64_t)b * ldo;
-    const V* p = psi ? psi + (int64_t)b * ldp : nullptr;
+    const V* p = KIN ? psi + (int64_t)b * ldp : nullptr;
 #pragma unroll
     for (int r = 0; r < (TL * N + kThreads - 1) / kThreads; ++r) {
         const int idx = threadIdx.x + r * kThreads;
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(kThreads) k_band_z_fwd(Sphere s, const c2<T>* 
             if (k >= -km && k <= km) {
                 const int g = cstart[line] + k + km;
                 const V loc = buf[e * LS + line];
-                if (p) {
+                if constexpr (KIN) {
                     const V ps = p[g];
                     const T kin = w * g2half[g];
                     o[g] = mk<T>(loc.x + kin * ps.x, loc.y + kin * ps.y);
@@ -550,9 +551,16 @@ struct BandFft {
     }
     static void z_fwd(const Sphere& s, const V* tw, const V* Zc, V* out, int64_t ldo, const V* psi, int64_t ldp,
                       const T* g2half, const T* wk, int b0, int nbb, int nc, cudaStream_t st) {
-        set_smem(k_band_z_fwd<T, N>, SM);
         dim3 gz((s.ncol + TL - 1) / TL, nbb);
-        roks::count_launch(), k_band_z_fwd<T, N><<<gz, kThreads, SM, st>>>(s, tw, Zc, out, ldo, psi, ldp, g2half, wk, b0, nc);
+        if (psi) {
+            set_smem(k_band_z_fwd<T, N, true>, SM);
+            roks::count_launch(), k_band_z_fwd<T, N, true><<<gz, kThreads, SM, st>>>(s, tw, Zc, out, ldo, psi, ldp,
+                                                                                     g2half, wk, b0, nc);
+        } else {
+            set_smem(k_band_z_fwd<T, N, false>, SM);
+            roks::count_launch(), k_band_z_fwd<T, N, false><<<gz, kThreads, SM, st>>>(s, tw, Zc, out, ldo, psi, ldp,
+                                                                                      g2half, wk, b0, nc);
+        }
     }
     // slot null: the bands are open-shell ones (or cls_override >= 0) and go
     // straight to rho3, no group slots are written and none are reduced

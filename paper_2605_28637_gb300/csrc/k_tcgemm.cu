@@ -142,7 +142,7 @@ struct GbPlan {
     static constexpr int SLOTS = APRE ? 3 : GB_CONV;
     static constexpr uint32_t RAWA = APRE ? 0u : GB_RAWA;       // raw A bytes per stage
     static constexpr uint32_t RAWB = NN ? 0u : GB_RAWB;         // raw B bytes per stage
-    static constexpr uint32_t RAWS = (NN && !APRE) ? GB_RAWS : RAWA + RAWB;
+    static constexpr uint32_t RAWS = RAWA + RAWB;                // bytes of one raw stage
     static constexpr bool RAW = RAWA + RAWB > 0;                // a TMA raw stage per K stage
     static constexpr bool CONVERT = RAW;                        // workers convert raw operands
     static constexpr bool BULK = NN || APRE;                    // bulk copies into the slot
@@ -168,7 +168,11 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
     unsigned char* conv = base;                                // SL operand slots
     unsigned char* raw = base + (size_t)SL * GB_SLOT;          // GB_RAW raw stages (1024-byte aligned)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.x * GB_M, n0 = blockIdx.y * GB_NC;
+    // CN: grid (M tiles, N tiles, K splits).  NN: grid (N tiles, M tiles),
+    // so that the CTAs sharing one tile of the tall A run side by side and A
+    // comes from DRAM about once (M fastest re-read it once per N tile)
+    const int mi = NN ? blockIdx.y : blockIdx.x, ni = NN ? blockIdx.x : blockIdx.y;
+    const int m0 = mi * GB_M, n0 = ni * GB_NC;
     const int s0 = NN ? 0 : blockIdx.z * stages_per_cta;
     const int ns = NN ? total_stages : max(0, min(total_stages, s0 + stages_per_cta) - s0);
 
@@ -229,11 +233,11 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
                     unsigned char* sl = conv + (size_t)cs * GB_SLOT;
                     tc::mbar_arrive_expect_tx(&b_full[cs], PL::BULK_BYTES);
                     if (APRE)
-                        tc::bulk_g2s(sl, asplit + ((size_t)blockIdx.x * total_stages + s0 + i) * (2 * GB_PART),
+                        tc::bulk_g2s(sl, asplit + ((size_t)mi * total_stages + s0 + i) * (2 * GB_PART),
                                      2 * GB_PART, &b_full[cs]);
                     if (NN)
                         tc::bulk_g2s(sl + 2 * GB_PART,
-                                     bsplit + ((size_t)blockIdx.y * total_stages + i) * (2 * GB_PART), 2 * GB_PART,
+                                     bsplit + ((size_t)ni * total_stages + i) * (2 * GB_PART), 2 * GB_PART,
                                      &b_full[cs]);
                     bissued = i + 1;
                 }
@@ -668,7 +672,7 @@ bool gemm_nn_tcg(int M, int N, int K, const float2* A, int64_t lda, const double
     roks::count_launch();
     g_tcg_launches += 1;
     const int mt = (M + GB_M - 1) / GB_M;
-    const dim3 grid(mt, nt, 1);
+    const dim3 grid(nt, mt, 1);
     if (as) {
         set_attr<true, true>();
         k_tcgemm<true, true><<<grid, GB_THREADS, GbPlan<true, true>::SMEM, st>>>(
