@@ -133,6 +133,8 @@ class DIIS:
     def __init__(self, sys_: R.System, history: int = HISTORY, tau: float = TAU,
                  lambda_ab: float = 0.5, lambda_ba: float = 0.5, e_tol: float = 1e-6, tol: float = COND_TOL,
                  g_tol: float = 0.0):
+        if sys_.n_empty:
+            raise ValueError("the DIIS solver takes occupied bands only (no empty shell)")
         self.sys = sys_
         self.tau = tau
         self.tol = tol

@@ -71,12 +71,14 @@ def well_fourier(sys_: R.System, a: int) -> np.ndarray:
 
 def energy_gradient(sys_: R.System, Psi, gamma=None) -> np.ndarray:
     """dE/dR_Inu (natoms x 3) by the Hellmann-Feynman expression above; gamma
-    defaults to that of Psi."""
+    defaults to that of Psi.  Only the occupied bands enter (empty bands, the
+    columns after them, carry no occupation)."""
+    Psi = Psi[:, :sys_.n_occ]
     pot = sys_.potentials(sys_.class_densities(Psi))
     if gamma is None:
         FPsi, _ = sys_.apply(Psi, pot)
         gamma = gamma_matrix(Psi, FPsi)
-    wn = sys_.w[sys_.cls]
+    wn = sys_.w[sys_.cls[:sys_.n_occ]]
     rho_w = (sys_.w[:, None] * pot.rho_k).sum(axis=0)
     rG = sys_.grid_fourier(rho_w)
     N = sys_.N
@@ -104,7 +106,7 @@ def energy_gradient(sys_: R.System, Psi, gamma=None) -> np.ndarray:
             Qa = sys_.Q[np.ix_(cols, cols)]
             # <n|dV_nl|n> = <n|dP D P^H + P D dP^H|n>
             nl = sum(wn[n] * (np.vdot(dBa[:, n], Da @ Ba[:, n]) + np.vdot(Ba[:, n], Da @ dBa[:, n]))
-                     for n in range(sys_.nb))
+                     for n in range(sys_.n_occ))
             # C_mn = <m|dP Q P^H + P Q dP^H|n>
             C = dBa.conj().T @ Qa @ Ba + Ba.conj().T @ Qa @ dBa
             ov = np.sum(gamma * C)

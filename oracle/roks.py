@@ -39,11 +39,26 @@ CUDA path, which implements them independently):
       the step is capped at 3 dt.  The same step scales the rotation (Eq. 24).
   R6  the search direction is projected S-orthogonal to the current orbitals
       before the step; orbitals are S-orthonormalised by Cholesky in the
-      order closed, a, b after each step.
+      order closed, a, b, empty after each step.
   R7  convergence: |E_i+1 - E_i| < e_tol on two consecutive iterations and,
       when a gradient tolerance g_tol > 0 is given, |g| < g_tol at the start
       of the last step (the stationarity the energy criterion stands for,
       Eq. 15 and SI S1, made explicit).
+  R8  the empty shell (Eq. 20, fourth row and column): n_empty unoccupied
+      bands follow a, b.  They carry no occupation in any configuration, so
+      F^e = 0 in the energy and its gradient: theta_mn = <m|F^e|n> = 0 for an
+      empty n in gamma, the full gradient g and the in-subspace gradient, and
+      R_mn = <m|F^s|n> between an occupied shell s and the empty shell.  The
+      empty-empty block of R is F^c, and an empty band's own out-of-subspace
+      direction is the preconditioned F^c residual (1 - S Psi Psi^H) F^c|e>,
+      so the empty bands relax to the lowest eigenvectors of F^c outside the
+      occupied space; that direction takes the line search's common step but
+      adds nothing to its slope E'(0).  The Fletcher-Reeves ratio (R4) sums
+      over all bands.  The rotation of an occupied-empty pair turns the
+      occupied band to the lower eigenvector of their 2 x 2 block (angle
+      (1/2) atan2(2|R|, d_e - d_o), the Jacobi angle of Eq. 22 when d_o <
+      d_e; past pi/4 it exchanges the pair, so the occupied bands take the
+      lowest states).  Not combined with exact exchange.
 
 What pins each part (tests/test_oracle_*.py; none compares the oracle with
 itself): the transforms against the DFT sum and brute force; the basis
@@ -113,7 +128,11 @@ class System:
         self.mode = int(cfg["mode"])
         self.n_closed = int(cfg["n_closed"])
         self.n_open = 0 if self.mode == 0 else 2
-        self.nb = self.n_closed + self.n_open
+        self.n_empty = int(cfg.get("n_empty", 0))
+        self.n_occ = self.n_closed + self.n_open
+        self.nb = self.n_occ + self.n_empty
+        if self.n_empty and self.alpha != 0.0:
+            raise ValueError("empty bands are not modelled with exact exchange")
         self.hartree = hartree
         self.xc = xc
         self._occupations()
@@ -130,7 +149,10 @@ class System:
         self.C = F_TABLE * c_ch[None, :]              # c_L f_k^{sigma L}
         self.w = self.C.sum(axis=1)                   # weight of T, V_ext, V_H in F^k
         self.WX = (F_TABLE * c_ch) @ F_TABLE.T        # sum c_L f_k f_k' (exchange pairs)
-        self.cls = np.array([0] * self.n_closed + list(range(1, self.n_open + 1)))
+        # class of the operator applied to each band: closed 0, open a 1 and
+        # b 2; an empty band takes F^c (R8) but no occupation
+        self.cls = np.array([0] * self.n_closed + list(range(1, self.n_open + 1)) + [0] * self.n_empty)
+        self.empty = np.arange(self.nb) >= self.n_occ
 
     # ----------------------------------------------------------- plane-wave basis
     def _basis(self):
@@ -247,10 +269,11 @@ class System:
 
     # ----------------------------------------------------------- a2, a3: densities
     def class_densities(self, Psi: np.ndarray, bands=None) -> np.ndarray:
-        """rho_k(r) = sum_{n in k} |psi_n(r)|^2 for k = closed, a, b.  With
-        `bands`, the columns of Psi are those bands only (their share of the
-        sums, for callers that split the bands over processes)."""
-        bands = range(self.nb) if bands is None else bands
+        """rho_k(r) = sum_{n in k} |psi_n(r)|^2 for k = closed, a, b (the
+        occupied bands; empty ones carry no density).  With `bands`, the
+        columns of Psi are those bands only (their share of the sums, for
+        callers that split the bands over processes)."""
+        bands = range(self.n_occ) if bands is None else [n for n in bands if n < self.n_occ]
         rho = np.zeros((3, self.N ** 3))
         for col, n in enumerate(bands):
             psi = self.to_real(Psi[:, col])
@@ -372,17 +395,18 @@ class System:
         E = sum_L c_L E_L, which is E_S = 2 E_M - E_T for the singlet (Eq. 1)."""
         if pot is None:
             pot = self.potentials(self.class_densities(Psi))
-        wn = self.w[self.cls]
+        Psi = Psi[:, :self.n_occ]               # empty bands carry no energy
+        wn = self.w[self.cls[:self.n_occ]]
         kin = float((wn[None, :] * 0.5 * self.g2[:, None] * np.abs(Psi) ** 2).sum())
         B = self.P.conj().T @ Psi
-        nl = float(sum(wn[n] * (B[:, n].conj() @ self.D @ B[:, n]).real for n in range(self.nb)))
+        nl = float(sum(wn[n] * (B[:, n].conj() @ self.D @ B[:, n]).real for n in range(self.n_occ)))
         E = dict(pot.E)
         E["kin"] = kin
         E["nl"] = nl
         if self.alpha != 0.0:
             _, K = self.exchange(Psi)
-            fM = F_TABLE[self.cls][:, 0:2]
-            fT = F_TABLE[self.cls][:, 2:4]
+            fM = F_TABLE[self.cls[:self.n_occ]][:, 0:2]
+            fT = F_TABLE[self.cls[:self.n_occ]][:, 2:4]
             E["hf_M"] = -0.5 * float(((fM @ fM.T) * K).sum())
             E["hf_T"] = -0.5 * float(((fT @ fT.T) * K).sum())
         else:
@@ -417,16 +441,27 @@ class System:
 
 
 # =========================================================== a12-a16: PCG pieces
-def gradient_parts(Psi, FPsi, SPsi):
+def gradient_parts(Psi, FPsi, SPsi, empty=None):
     """theta_mn = <m|F^n|n>; gamma (Eq. 11) as Gam_mn = gamma_nm =
     (theta_mn + theta_nm^*)/2; full gradient g = F Psi - S Psi Gam (Eq. 7);
     out-of-subspace part g_I = F Psi - S Psi theta and in-subspace matrix
-    Gin_mn = theta_mn - theta_nm^* = 2 <m|g_n> (Eq. 12)."""
+    Gin_mn = theta_mn - theta_nm^* = 2 <m|g_n> (Eq. 12).
+
+    empty (bool per band, R8): those columns of F Psi hold F^c|e>; the
+    energy's operator there is F^e = 0, so gamma, g and Gin take theta and
+    F Psi with those columns zero, while g_I keeps the F^c residual (the
+    empty bands' own direction).  theta is returned as computed."""
     Theta = Psi.conj().T @ FPsi
-    Gam = 0.5 * (Theta + Theta.conj().T)
-    G = FPsi - SPsi @ Gam
     gI = FPsi - SPsi @ Theta
-    Gin = Theta - Theta.conj().T
+    ThE, FE = Theta, FPsi
+    if empty is not None and np.any(empty):
+        ThE = Theta.copy()
+        ThE[:, empty] = 0.0
+        FE = FPsi.copy()
+        FE[:, empty] = 0.0
+    Gam = 0.5 * (ThE + ThE.conj().T)
+    G = FE - SPsi @ Gam
+    Gin = ThE - ThE.conj().T
     return Theta, G, gI, Gin
 
 
@@ -455,28 +490,37 @@ def precondition(sys_: System, Psi, SPsi, gI):
     return pI, X
 
 
-def shell_of(cls: np.ndarray, mode: int) -> np.ndarray:
-    """Shell index per band: closed = 0; singlet: a = 1, b = 2; triplet: a, b share shell 1."""
-    if mode == 2:
-        return np.minimum(cls, 1)
-    return cls.copy()
+def shell_of(cls: np.ndarray, mode: int, empty=None) -> np.ndarray:
+    """Shell index per band: closed = 0; singlet: a = 1, b = 2; triplet: a, b
+    share shell 1 (one open shell, Eq. 20 for high-spin states); empty = 3."""
+    sh = np.minimum(cls, 1) if mode == 2 else cls.copy()
+    if empty is not None:
+        sh = np.where(empty, 3, sh)
+    return sh
 
 
-def r_matrix(Theta, cls, mode, suppress_ab=False):
+def r_matrix(Theta, cls, mode, suppress_ab=False, empty=None):
     """Off-diagonal R_mn of Eq. 20 from theta: same shell <m|F^s|n> = theta_mn;
     shells s < t: <m|F^s - F^t|n> = theta_nm^* - theta_mn; s > t the conjugate
-    relation.  The a-b element is zeroed when the coupling is suppressed."""
-    sh = shell_of(cls, mode)
+    relation.  The a-b element is zeroed when the coupling is suppressed.
+    With empty bands (R8) theta_mn = <m|F^c|n> in their columns: F^e = 0
+    between shells (so R_mn = <m|F^s|n> there) and F^c within the empty
+    shell, as in the fourth row and column of Eq. 20."""
+    sh = shell_of(cls, mode, empty)
     nb = len(cls)
+    ThE = Theta
+    if empty is not None and np.any(empty):
+        ThE = Theta.copy()
+        ThE[:, empty] = 0.0
     R = np.zeros_like(Theta)
     for m in range(nb):
         for n in range(nb):
             if sh[m] == sh[n]:
                 R[m, n] = Theta[m, n]
             elif sh[m] < sh[n]:
-                R[m, n] = np.conj(Theta[n, m]) - Theta[m, n]
+                R[m, n] = np.conj(ThE[n, m]) - ThE[m, n]
             else:
-                R[m, n] = Theta[m, n] - np.conj(Theta[n, m])
+                R[m, n] = ThE[m, n] - np.conj(ThE[n, m])
     if suppress_ab and mode == 1:
         ia = np.where(cls == 1)[0]
         ib = np.where(cls == 2)[0]
@@ -487,9 +531,18 @@ def r_matrix(Theta, cls, mode, suppress_ab=False):
     return R
 
 
-def rotation_generator(R, d):
+def rotation_generator(R, d, empty=None, dk=None, cls=None, Theta=None):
     """A_mn = -(1/2) atan(2|x|) x/|x|, x = R_mn/(d_m - d_n) (Eqs. 22-23 with R2, R3);
-    computed for m < n and completed anti-Hermitian."""
+    computed for m < n and completed anti-Hermitian.
+
+    An occupied band m of class k and an empty band n (R8, the empty bands
+    come last): A_mn = (1/2) atan2(2|R_mn|, <n|F^k|n> - <m|F^k|m>) R_mn/|R_mn|
+    (R_mn = <m|F^k|n>, dk[k, n] = <n|F^k|n>, Theta_mm = <m|F^k|m>), the
+    rotation that takes m to the lower eigenvector of the 2 x 2 block of its
+    own operator F^k.  Where m lies lower this is a Jacobi angle; where the
+    empty band does, the angle exceeds pi/4 and exchanges the two, so the
+    occupied bands end on the lowest states (aufbau), which a Jacobi step,
+    never past pi/4, cannot reach."""
     nb = R.shape[0]
     A = np.zeros_like(R)
     for m in range(nb):
@@ -498,9 +551,14 @@ def rotation_generator(R, d):
             if r < 1e-14:
                 continue
             dd = d[m] - d[n]
-            sg = 1.0 if dd >= 0.0 else -1.0
-            phi = 0.5 * np.arctan2(2.0 * r, abs(dd))
-            A[m, n] = -phi * sg * R[m, n] / r
+            if empty is not None and empty[n] and not empty[m]:
+                k = cls[m]
+                gap = dk[k, n] - Theta[m, m].real
+                A[m, n] = 0.5 * np.arctan2(2.0 * r, gap) * R[m, n] / r
+            else:
+                sg = 1.0 if dd >= 0.0 else -1.0
+                phi = 0.5 * np.arctan2(2.0 * r, abs(dd))
+                A[m, n] = -phi * sg * R[m, n] / r
             A[n, m] = -np.conj(A[m, n])
     return A
 
@@ -551,12 +609,22 @@ class PCG:
         pot = sy.potentials(sy.class_densities(Psi))
         E0 = sy.energies(Psi, pot)["total"]
         FPsi, SPsi = sy.apply(Psi, pot)
-        Theta, G, gI, Gin = gradient_parts(Psi, FPsi, SPsi)
+        empty = sy.empty if sy.n_empty else None
+        Theta, G, gI, Gin = gradient_parts(Psi, FPsi, SPsi, empty)
         pI, _ = precondition(sy, Psi, SPsi, gI)
         d = closed_shell_diagonal(sy, Psi, pot)
-        R = r_matrix(Theta, sy.cls, sy.mode, self.suppress_ab)
-        A = rotation_generator(R, d)
-        pg = float(np.real(np.vdot(pI, gI))) + 0.5 * float(np.real(np.vdot(A, Gin)))
+        R = r_matrix(Theta, sy.cls, sy.mode, self.suppress_ab, empty)
+        dk = None
+        if sy.n_empty:
+            # <e|F^k|e> of the empty bands for the three classes (R8)
+            Pe = Psi[:, sy.empty]
+            dk = np.zeros((3, sy.nb))
+            for k in range(3):
+                Fe, _ = sy.apply(Pe, pot, classes=np.full(Pe.shape[1], k, dtype=int), occ=Psi[:, :sy.n_occ])
+                dk[k, sy.empty] = np.real(np.einsum("gm,gm->m", Pe.conj(), Fe))
+        A = rotation_generator(R, d, empty, dk, sy.cls, Theta)
+        no = sy.n_occ       # R8: the ratio of the energy's gradient (occupied bands)
+        pg = float(np.real(np.vdot(pI[:, :no], gI[:, :no]))) + 0.5 * float(np.real(np.vdot(A, Gin)))
         beta = 0.0 if self.pg_prev is None else pg / self.pg_prev
         restarted = False
 
@@ -576,7 +644,14 @@ class PCG:
             dE0 = 2.0 * float(np.real(np.vdot(s, G)))
             restarted = True
         dt = self.dt
-        Et = sy.energy(self.trial(Psi, s, At, dt))
+        # the trial point moves the occupied bands only: the empty bands'
+        # direction does not change the energy to first order, and its second
+        # order (through the rotation) would distort the parabola (R8)
+        s_t = s
+        if sy.n_empty:
+            s_t = s.copy()
+            s_t[:, sy.empty] = 0.0
+        Et = sy.energy(self.trial(Psi, s_t, At, dt))
         c = (Et - E0 - dE0 * dt) / (dt * dt)
         step = -dE0 / (2.0 * c) if c > 0.0 else dt
         step = min(step, 3.0 * dt)

@@ -179,7 +179,8 @@ def with_changes(cfg: dict, **kw) -> dict:
 
 
 def n_bands(cfg: dict) -> int:
-    return cfg["n_closed"] + (0 if cfg["mode"] == 0 else 2)
+    """closed, open (a, b unless the ground state) and empty bands"""
+    return cfg["n_closed"] + (0 if cfg["mode"] == 0 else 2) + int(cfg.get("n_empty", 0))
 
 
 def orbital_stream_seed(cfg: dict) -> int:
