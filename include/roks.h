@@ -98,11 +98,26 @@ typedef struct {
 
 /* n_closed doubly occupied bands; modes 1 and 2 add the two singly
  * occupied bands a, b (Fig. 1A).  n_open states the open-shell size and must
- * be 0 for ROKS_MODE_GS and 2 for the other modes (ROKS_EINVAL otherwise). */
+ * be 0 for ROKS_MODE_GS and 2 for the other modes (ROKS_EINVAL otherwise).
+ *
+ * n_empty unoccupied bands (the empty shell of Eq. 20) follow: bands are
+ * ordered closed, a, b, empty.  They carry no occupation in any
+ * configuration, so the densities, energies and forces are those of the
+ * occupied bands.  In a PCG step they enter the R matrix (F^s between an
+ * occupied shell s and the empty shell, F^c within it), an occupied-empty
+ * pair rotates the occupied band to the lower eigenvector of the pair's
+ * 2 x 2 block of its own operator, and each empty band moves along its
+ * preconditioned F^c residual, so the empty bands relax to the lowest
+ * eigenvectors of F^c outside the occupied space.  roks_apply_h applies F^c
+ * to them; the gradient roks_gradient_parts writes is the energy's
+ * (F^e = 0) and its g_I the F^c residual.  Not with exact exchange
+ * (alpha != 0) or the Gamma-point form (ROKS_EINVAL); roks_diis_step
+ * returns ROKS_EINVAL on a context with empty bands. */
 typedef struct {
     int n_closed;
     int n_open;
     int mode;
+    int n_empty;
 } roks_occ;
 
 /* Exact-exchange kernels v(G) of the pair potentials (Sec. III hybrid). */

@@ -16,11 +16,12 @@ namespace roks {
 // A_nm = -conj A_mn (|R| < 1e-14 -> 0).
 // d_m = <m|F^c|m>.  Closed bands: Re theta_mm.  Open bands:
 // w_c (<m|T|m> + <m|V_nl|m>) + <m|V^c|m> with the local part from rho_m.
-__device__ __forceinline__ double band_diag(int m, int nb, int n_closed, const double2* __restrict__ Th,
+__device__ __forceinline__ double band_diag(int m, int nb, int n_closed, int n_occ, const double2* __restrict__ Th,
                                             const double* __restrict__ kin_b, const double* __restrict__ nl_b,
                                             const double* __restrict__ open_vc, const double* __restrict__ open_x,
                                             double wc) {
-    if (m < n_closed) return Th[(int64_t)m * nb + m].x;
+    // closed and empty bands: F^c was applied to them
+    if (m < n_closed || m >= n_occ) return Th[(int64_t)m * nb + m].x;
     double v = wc * (kin_b[m] + nl_b[m]) + open_vc[m - n_closed];
     if (open_x) v += open_x[m - n_closed];
     return v;
@@ -32,7 +33,7 @@ __global__ void k_pcg_rotation(int nb, int n_closed, const double2* __restrict__
                                const double* __restrict__ nl_b, const double* __restrict__ open_vc,
                                const double* __restrict__ open_x, double wc, const int* __restrict__ shell,
                                int suppress_ab, int ia, int ib, double2* __restrict__ Gam, double2* __restrict__ Gin,
-                               double2* __restrict__ A, PcgScalars* sc) {
+                               double2* __restrict__ A, PcgScalars* sc, int n_occ, const double* __restrict__ dk) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx == 0) {
         if (ia < 0) {
@@ -47,28 +48,39 @@ __global__ void k_pcg_rotation(int nb, int n_closed, const double2* __restrict__
     }
     if (idx >= nb * nb) return;
     const int m = idx % nb, n = idx / nb;
-    const double2 tmn = Th[(int64_t)n * nb + m];
-    const double2 tnm = Th[(int64_t)m * nb + n];
+    const double2 z2 = make_double2(0.0, 0.0);
+    // theta of the energy: <m|F^e|n> = 0 in the empty columns
+    const double2 tmn = n < n_occ ? Th[(int64_t)n * nb + m] : z2;
+    const double2 tnm = m < n_occ ? Th[(int64_t)m * nb + n] : z2;
     Gam[idx] = make_double2(0.5 * (tmn.x + tnm.x), 0.5 * (tmn.y - tnm.y));
     Gin[idx] = make_double2(tmn.x - tnm.x, tmn.y + tnm.y);
-    double2 a = make_double2(0.0, 0.0);
+    double2 a = z2;
     if (m != n) {
         // the element of the upper triangle that defines this pair
         const int p = m < n ? m : n, q = m < n ? n : m;
-        const double2 tpq = Th[(int64_t)q * nb + p];
-        const double2 tqp = Th[(int64_t)p * nb + q];
+        const double2 tpq = q < n_occ ? Th[(int64_t)q * nb + p] : z2;
+        const double2 tqp = p < n_occ ? Th[(int64_t)p * nb + q] : z2;
         double2 r;
-        if (shell[p] == shell[q]) r = tpq;
+        if (shell[p] == shell[q]) r = Th[(int64_t)q * nb + p];   // same shell (the empty one: F^c)
         else if (shell[p] < shell[q]) r = make_double2(tqp.x - tpq.x, -tqp.y - tpq.y);
         else r = make_double2(tpq.x - tqp.x, tpq.y + tqp.y);
         if (suppress_ab && ((p == ia && q == ib) || (p == ib && q == ia))) r = make_double2(0.0, 0.0);
         const double ar = sqrt(r.x * r.x + r.y * r.y);
         if (ar >= 1e-14) {
-            const double dd = band_diag(p, nb, n_closed, Th, kin_b, nl_b, open_vc, open_x, wc) -
-                              band_diag(q, nb, n_closed, Th, kin_b, nl_b, open_vc, open_x, wc);
-            const double sg = dd >= 0.0 ? 1.0 : -1.0;
-            const double phi = 0.5 * atan2(2.0 * ar, fabs(dd));
-            const double2 apq = make_double2(-phi * sg * r.x / ar, -phi * sg * r.y / ar);
+            double2 apq;
+            if (p < n_occ && q >= n_occ) {
+                // occupied p of class k, empty q: p to the lower state of F^k
+                const int k = p < n_closed ? 0 : p - n_closed + 1;
+                const double gap = dk[k * (nb - n_occ) + (q - n_occ)] - Th[(int64_t)p * nb + p].x;
+                const double phi = 0.5 * atan2(2.0 * ar, gap);
+                apq = make_double2(phi * r.x / ar, phi * r.y / ar);
+            } else {
+                const double dd = band_diag(p, nb, n_closed, n_occ, Th, kin_b, nl_b, open_vc, open_x, wc) -
+                                  band_diag(q, nb, n_closed, n_occ, Th, kin_b, nl_b, open_vc, open_x, wc);
+                const double sg = dd >= 0.0 ? 1.0 : -1.0;
+                const double phi = 0.5 * atan2(2.0 * ar, fabs(dd));
+                apq = make_double2(-phi * sg * r.x / ar, -phi * sg * r.y / ar);
+            }
             a = (m == p) ? apq : make_double2(-apq.x, apq.y);
         }
     }
@@ -77,11 +89,66 @@ __global__ void k_pcg_rotation(int nb, int n_closed, const double2* __restrict__
 
 void pcg_rotation(int nb, int n_closed, const double2* Theta, const double* kin_b, const double* nl_b,
                   const double* open_vc, const double* open_x, double wc, const int* shell, int suppress_ab, int ia,
-                  int ib, double2* Gam, double2* Gin, double2* A, PcgScalars* sc, cudaStream_t st) {
+                  int ib, double2* Gam, double2* Gin, double2* A, PcgScalars* sc, cudaStream_t st, int n_occ,
+                  const double* dk) {
     roks::count_launch(), k_pcg_rotation<<<(nb * nb + 127) / 128, 128, 0, st>>>(
                               nb, n_closed, Theta, kin_b, nl_b, open_vc, open_x, wc, shell, suppress_ab, ia, ib, Gam,
-                              Gin, A, sc);
+                              Gin, A, sc, n_occ, dk);
 }
+
+// Empty bands: block partial sums of dvol V^k rho_e (grid-stride, one block
+// row per (band, class)), then the fixed-order total plus the
+// kinetic/non-local part.
+template <typename T>
+__global__ void k_empty_vexp(int64_t N3, int n_empty, const typename DensAcc<T>::S* __restrict__ rho_e,
+                             const T* __restrict__ Vk, double* __restrict__ part) {
+    using DA = DensAcc<T>;
+    __shared__ double red[256];
+    const int i = blockIdx.y % n_empty, k = blockIdx.y / n_empty;
+    const typename DA::S* r = rho_e + (int64_t)(i + 1) * N3;
+    const T* v = Vk + (int64_t)k * N3;
+    double acc = 0.0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N3; p += (int64_t)gridDim.x * blockDim.x)
+        acc += double(v[p]) * double(DA::value(r[p]));
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+}
+
+__global__ void k_empty_diag_final(int nblk, int n_empty, int n_occ, const double* __restrict__ part, double dvol,
+                                   const double* __restrict__ kin_b, const double* __restrict__ nl_b, double w0,
+                                   double w1, double w2, double* __restrict__ dk) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= 3 * n_empty) return;
+    const int i = j % n_empty, k = j / n_empty;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(int64_t)j * nblk + b];
+    const int e = n_occ + i;
+    const double w = k == 0 ? w0 : (k == 1 ? w1 : w2);
+    dk[j] = w * (kin_b[e] + nl_b[e]) + dvol * s;
+}
+
+template <typename T>
+void empty_band_diagonal(int64_t N3, int n_empty, int n_occ, const double* rho_e, const T* Vk, double dvol,
+                         const double* kin_b, const double* nl_b, double w0, double w1, double w2, double* part,
+                         double* dk, cudaStream_t st) {
+    if (n_empty <= 0) return;
+    constexpr int kBlk = 64;
+    using DS = typename DensAcc<T>::S;
+    roks::count_launch(), k_empty_vexp<T><<<dim3(kBlk, 3 * n_empty), 256, 0, st>>>(
+                              N3, n_empty, reinterpret_cast<const DS*>(rho_e), Vk, part);
+    roks::count_launch(), k_empty_diag_final<<<(3 * n_empty + 127) / 128, 128, 0, st>>>(kBlk, n_empty, n_occ, part,
+                                                                                        dvol, kin_b, nl_b, w0, w1, w2,
+                                                                                        dk);
+}
+template void empty_band_diagonal<float>(int64_t, int, int, const double*, const float*, double, const double*,
+                                         const double*, double, double, double, double*, double*, cudaStream_t);
+template void empty_band_diagonal<double>(int64_t, int, int, const double*, const double*, double, const double*,
+                                          const double*, double, double, double, double*, double*, cudaStream_t);
 
 // r1 = Re <A, Gin>, r2 = Re <A_prev, Gin> (sums over all n^2 elements).
 // One block (up to 64 bands), or block partials of a grid-stride sum and a

@@ -41,6 +41,10 @@ struct roks_ctx {
     long long steps = 0;   // PCG and DIIS steps since the orbitals were last set
     int N = 0, npw = 0, ld_min = 0, nmax = 0, M = 0, ncol = 0, np = 0;
     int nb = 0, nc = 0, mode = 1, nproj = 0, natoms = 0, suppress_ab = 0;
+    // empty shell (Eq. 20): bands nocc .. nb - 1 carry no occupation; ne of them
+    int nocc = 0, ne = 0;
+    double* d_rho_e = nullptr;   // their densities, band i at (i + 1) N^3 (density storage)
+    double* d_dk = nullptr;      // <e|F^k|e>, 3 x ne
     // Gamma point (roks_options.gamma): npw counts the half sphere, the tail
     // of the full basis from row h0; the transforms run on nbt packed bands
     // (two real orbitals each) with n_closed nct, and band split_t (-1: none)
@@ -337,8 +341,22 @@ struct Impl {
         {
             PROF("fft_x_density");
             if (ctx->split_t < 0) {
+                // the occupied bands (the empty ones carry no density)
                 band_x_density<T>(s, ccv(ctx->d_tw), cv(ctx->d_Yp), ctx->d_rho3, ctx->d_rho_slot, ctx->dens_groups,
-                                  0, ctx->nbt, ctx->nct, 1.0 / ctx->omega, st);
+                                  0, ctx->nbt - ctx->ne, ctx->nct, 1.0 / ctx->omega, st);
+                if (ctx->ne > 0) {
+                    // each empty band's own density, for its <e|V^k|e> (the
+                    // kernel indexes the planes from the launch's first band
+                    // and adds class 1 of the rho3 it is given)
+                    const int64_t N3 = (int64_t)ctx->N * ctx->N * ctx->N;
+                    CK(cudaMemsetAsync(ctx->d_rho_e + N3, 0, sizeof(double) * ctx->ne * N3, st));
+                    for (int i = 0; i < ctx->ne; ++i) {
+                        const int e = ctx->nocc + i;
+                        const V* yo = ccv(ctx->d_Yp) + (int64_t)e * ctx->np * ctx->N * ctx->N;
+                        band_x_density<T>(s, ccv(ctx->d_tw), yo, ctx->d_rho_e + i * N3, nullptr, 1, e, 1, ctx->nc,
+                                          1.0 / ctx->omega, st, 0, 1);
+                    }
+                }
             } else {
                 // Gamma point: the closed pairs, then the packed open pair's
                 // real part (a) and imaginary part (b) into their own classes
@@ -378,7 +396,7 @@ struct Impl {
         potentials<T>(ctx->N, ctx->L, ctx->d_rho3, static_cast<const T*>(ctx->d_vloc_t), ctx->cf,
                       reinterpret_cast<V*>(ctx->d_grid), reinterpret_cast<T*>(ctx->d_xc3), ccv(ctx->d_tw),
                       static_cast<T*>(ctx->d_Vk), nullptr, ctx->d_part, ctx->d_out6, st, energies_only);
-        energy_combine(ctx->d_kin_b, ctx->d_nl_b, ctx->nb, ctx->d_wband, ctx->d_out6, ctx->cM, ctx->cT,
+        energy_combine(ctx->d_kin_b, ctx->d_nl_b, ctx->nocc, ctx->d_wband, ctx->d_out6, ctx->cM, ctx->cT,
                        ctx->alpha, ctx->alpha != 0.0 ? ctx->d_hf2 : nullptr, ctx->d_E, st);
         CK(cudaGetLastError());
         return ROKS_OK;
@@ -405,9 +423,15 @@ struct Impl {
         }
         {
             PROF("fft_x_apply");
+            const int nx = ctx->nbt - ctx->ne;
             band_x_apply<T>(s, ccv(ctx->d_tw), cv(ctx->d_Yp), static_cast<const T*>(ctx->d_Vk),
-                            ctx->alpha != 0.0 ? ccv(ctx->d_Xx) : nullptr, 0, ctx->nbt, ctx->nct, ctx->split_t,
+                            ctx->alpha != 0.0 ? ccv(ctx->d_Xx) : nullptr, 0, nx, ctx->nct, ctx->split_t,
                             T(1.0 / (double(N) * N * N)), st);
+            // empty bands: F^c (a closed count past the last band gives class 0)
+            if (ctx->ne > 0)
+                band_x_apply<T>(s, ccv(ctx->d_tw), cv(ctx->d_Yp) + (int64_t)nx * ctx->np * N * N,
+                                static_cast<const T*>(ctx->d_Vk), nullptr, nx, ctx->ne, ctx->nb, -1,
+                                T(1.0 / (double(N) * N * N)), st);
         }
         ctx->yp_psi = nullptr;   // the x stage works in place
         { PROF("fft_y_fwd"); band_y_fwd<T>(s, ccv(ctx->d_tw), cv(ctx->d_Yp), cv(ctx->d_Zc), ctx->nbt, st); }
@@ -424,8 +448,12 @@ struct Impl {
                                 st);
             } else {
                 band_z_fwd<T>(s, ccv(ctx->d_tw), cv(ctx->d_Zc), cv(F), ldf, p, ld,
-                              static_cast<const T*>(ctx->d_g2half), static_cast<const T*>(ctx->d_wk), 0, ctx->nb,
+                              static_cast<const T*>(ctx->d_g2half), static_cast<const T*>(ctx->d_wk), 0, ctx->nocc,
                               ctx->nc, st);
+                if (ctx->ne > 0)
+                    band_z_fwd<T>(s, ccv(ctx->d_tw), cv(ctx->d_Zc) + (int64_t)ctx->nocc * ctx->ncol * N, cv(F), ldf,
+                                  p, ld, static_cast<const T*>(ctx->d_g2half), static_cast<const T*>(ctx->d_wk),
+                                  ctx->nocc, ctx->ne, ctx->nb, st);
             }
         }
         if (ctx->nproj > 0) {
@@ -549,9 +577,9 @@ struct Impl {
     }
 
     // dst field = sum_n Re <x_n|y_n>
-    static void dot_to(roks_ctx* ctx, const void* x, const void* y, int field) {
+    static void dot_to(roks_ctx* ctx, const void* x, const void* y, int field, int ncols = -1) {
         const int64_t l = ctx->ld_min;
-        column_total<T>(2, ctx->npw, ctx->nb, ccv(x), l, ccv(y), l, static_cast<const T*>(ctx->d_g2half),
+        column_total<T>(2, ctx->npw, ncols < 0 ? ctx->nb : ncols, ccv(x), l, ccv(y), l, static_cast<const T*>(ctx->d_g2half),
                         ctx->d_colpart, reinterpret_cast<double*>(ctx->d_sc) + field, 1.0, ctx->st);
     }
 
@@ -600,7 +628,15 @@ struct Impl {
         double* scd = reinterpret_cast<double*>(ctx->d_sc);
         {
             PROF("rotate");
-            axpy<T>(ctx->npw, nb, ccv(psi), ld, ccv(ctx->W_s), l, scd + step_field, 1.0, cv(ctx->W_Y), l, st);
+            // the trial point (energies only) moves the occupied bands alone:
+            // the empty bands' directions do not change the energy to first
+            // order, and their second order would distort the parabola
+            const int nmv = (energies_only && ctx->ne > 0) ? ctx->nocc : nb;
+            axpy<T>(ctx->npw, nmv, ccv(psi), ld, ccv(ctx->W_s), l, scd + step_field, 1.0, cv(ctx->W_Y), l, st);
+            if (nmv < nb)
+                CK(cudaMemcpy2DAsync(static_cast<V*>(ctx->W_Y) + (int64_t)nmv * l, l * sizeof(V),
+                                     static_cast<const V*>(psi) + (int64_t)nmv * ld, ld * sizeof(V),
+                                     ctx->npw * sizeof(V), nb - nmv, cudaMemcpyDeviceToDevice, st));
             roks_status r = join_U(ctx);
             if (r != ROKS_OK) return r;
             gemm_nn<T>(ctx->npw, nb, nb, ccv(ctx->W_Y), l, ctx->d_U, nb, cv(ctx->W_Y2), l, 1.0, 0.0, ctx->d_gemm_work, st, ctx->gemm_work_elems * sizeof(double2));
@@ -629,16 +665,24 @@ struct Impl {
         }
         const int ia = (ctx->mode == ROKS_MODE_SINGLET) ? ctx->nc : -1;
         const int ib = (ctx->mode == ROKS_MODE_SINGLET) ? ctx->nc + 1 : -1;
+        if (ctx->ne > 0)
+            empty_band_diagonal<T>((int64_t)ctx->N * ctx->N * ctx->N, ctx->ne, ctx->nocc, ctx->d_rho_e,
+                                   static_cast<const T*>(ctx->d_Vk), ctx->omega / (double(ctx->N) * ctx->N * ctx->N),
+                                   ctx->d_kin_b, ctx->d_nl_b, ctx->cf.w[0], ctx->cf.w[1], ctx->cf.w[2],
+                                   ctx->d_dk + 3 * ctx->ne, ctx->d_dk, st);
         pcg_rotation(nb, ctx->nc, ctx->d_Th, ctx->d_kin_b, ctx->d_nl_b, ctx->d_out6 + 4,
                      ctx->alpha != 0.0 ? ctx->d_exopen : nullptr, ctx->cf.w[0], ctx->d_shell,
                      ctx->suppress_ab && ctx->mode == ROKS_MODE_SINGLET, ia, ib, ctx->d_Gam, ctx->d_Gin, ctx->d_A,
-                     ctx->d_sc, st);
-        // G = F - S Gam ; gI = F - S theta
+                     ctx->d_sc, st, ctx->nocc, ctx->d_dk);
+        // gI = F - S theta ; G = F - S Gam, with F^e = 0 in the empty columns
+        // (their g_I is the F^c residual, the empty bands' own direction)
         {
         PROF("gradient_precond");
-        gemm_nn_io<T>(npw, nb, nb, ccv(ctx->W_S), l, ctx->d_Gam, nb, ccv(ctx->W_F), l, cv(ctx->W_G), l, -1.0, 1.0,
-                      ctx->d_gemm_work, st, ctx->gemm_work_elems * sizeof(double2));
         gemm_nn_io<T>(npw, nb, nb, ccv(ctx->W_S), l, ctx->d_Th, nb, ccv(ctx->W_F), l, cv(ctx->W_gI), l, -1.0, 1.0,
+                      ctx->d_gemm_work, st, ctx->gemm_work_elems * sizeof(double2));
+        if (ctx->ne > 0) CK(cudaMemsetAsync(static_cast<V*>(ctx->W_F) + (int64_t)ctx->nocc * l, 0,
+                                            sizeof(V) * l * ctx->ne, st));
+        gemm_nn_io<T>(npw, nb, nb, ccv(ctx->W_S), l, ctx->d_Gam, nb, ccv(ctx->W_F), l, cv(ctx->W_G), l, -1.0, 1.0,
                       ctx->d_gemm_work, st, ctx->gemm_work_elems * sizeof(double2));
         column_total<T>(3, npw, nb, ccv(ctx->W_G), l, nullptr, 0, static_cast<const T*>(ctx->d_g2half), ctx->d_colpart,
                         reinterpret_cast<double*>(ctx->d_sc) + SC_FIELD(gnorm2), 1.0, st);
@@ -651,7 +695,8 @@ struct Impl {
             precondition<T>(npw, nb, ccv(ctx->W_gI), l, static_cast<const T*>(ctx->d_g2half), ctx->d_colout, cv(ctx->W_K), l, st);
         }
         project(ctx, psi, ld, ctx->W_K, ctx->W_K);
-        dot_to(ctx, ctx->W_K, ctx->W_gI, SC_FIELD(pgI));
+        // the Fletcher-Reeves ratio of the energy's gradient: occupied bands
+        dot_to(ctx, ctx->W_K, ctx->W_gI, SC_FIELD(pgI), ctx->nocc);
         pcg_rot_dots(nb, ctx->d_A, ctx->d_Aprev, ctx->d_Gin, ctx->d_colpart, ctx->d_sc, st);
         // u = p_I (projected above; the S-projector is idempotent on
         // S-orthonormal orbitals, so projecting again changes nothing),
@@ -816,7 +861,8 @@ struct Impl {
     // projector and the local term per atom (k_force.cu), summed per atom.
     static roks_status forces(roks_ctx* ctx, const void* psi, int64_t ld, double* out_host) {
         cudaStream_t st = ctx->st;
-        const int nb = ctx->nb, npw = ctx->npw, np_ = ctx->nproj;
+        // the occupied bands (the first nocc) alone carry the energy
+        const int nb = ctx->nocc, npw = ctx->npw, np_ = ctx->nproj;
         const int64_t l = ctx->ld_min;
         roks_status r = ROKS_OK;
         // the density and potentials of psi are current after a PCG or DIIS
@@ -1052,12 +1098,12 @@ roks_status autotune(roks_ctx* ctx) {
     if (ctx->prec == ROKS_FP64)
         ctx->dens_groups = pick_fastest(ctx, g_cand, 3, ctx->tune_ms, [&](int g) {
             band_x_density<double>(s, static_cast<const double2*>(ctx->d_tw), static_cast<double2*>(ctx->d_Yp),
-                                   ctx->d_rho3, ctx->d_rho_slot, g, 0, ctx->nbt, ctx->nct, 1.0 / ctx->omega, ctx->st);
+                                   ctx->d_rho3, ctx->d_rho_slot, g, 0, ctx->nbt - ctx->ne, ctx->nct, 1.0 / ctx->omega, ctx->st);
         });
     else
         ctx->dens_groups = pick_fastest(ctx, g_cand, 3, ctx->tune_ms, [&](int g) {
             band_x_density<float>(s, static_cast<const float2*>(ctx->d_tw), static_cast<float2*>(ctx->d_Yp),
-                                  ctx->d_rho3, ctx->d_rho_slot, g, 0, ctx->nbt, ctx->nct, 1.0 / ctx->omega, ctx->st);
+                                  ctx->d_rho3, ctx->d_rho_slot, g, 0, ctx->nbt - ctx->ne, ctx->nct, 1.0 / ctx->omega, ctx->st);
         });
     // the largest A^H B product of a step that runs on the tensor cores
     const int M = ctx->nproj >= ctx->nb ? ctx->nproj : ctx->nb;
@@ -1103,6 +1149,8 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     // the Gamma-point packing pairs bands (2k, 2k + 1): an open pair must be
     // one packed band, and exact exchange runs on the complex path only
     if (opt->gamma && (opt->alpha != 0.0 || (occ->mode != ROKS_MODE_GS && (occ->n_closed & 1)))) return ROKS_EINVAL;
+    // empty bands: the complex path without exact exchange
+    if (occ->n_empty < 0 || (occ->n_empty > 0 && (opt->gamma || opt->alpha != 0.0))) return ROKS_EINVAL;
     roks_ctx* ctx = new (std::nothrow) roks_ctx();
     if (!ctx) return ROKS_ENOMEM;
     ctx->st = static_cast<cudaStream_t>(cuda_stream);
@@ -1129,7 +1177,9 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     ctx->suppress_ab = opt->suppress_ab;
     ctx->mode = occ->mode;
     ctx->nc = occ->n_closed;
-    ctx->nb = occ->n_closed + (occ->mode == ROKS_MODE_GS ? 0 : 2);
+    ctx->nocc = occ->n_closed + (occ->mode == ROKS_MODE_GS ? 0 : 2);
+    ctx->ne = occ->n_empty;
+    ctx->nb = ctx->nocc + ctx->ne;
     ctx->natoms = natoms;
     auto bail = [&](roks_status s, const std::string& m) {
         roks_destroy(ctx);
@@ -1285,6 +1335,10 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     if (ctx->gamma) AL(ctx->d_Cpk, cs * (size_t)ctx->ldc_pk * ctx->nbt);
     AL(ctx->d_rho3, sizeof(double) * 3 * N3);
     AL(ctx->d_rho_slot, sizeof(double) * (opt->autotune ? kDensityGroupsMax : kDensityGroups) * N3);
+    if (ctx->ne > 0) {
+        AL(ctx->d_rho_e, sizeof(double) * (size_t)(ctx->ne + 1) * N3);
+        AL(ctx->d_dk, sizeof(double) * 3 * ctx->ne * (1 + 64));   // values, then block partials
+    }
     AL(ctx->d_xc3, sizeof(double) * 3 * N3);
     AL(ctx->d_grid, sizeof(double2) * N3);
     AL(ctx->d_Vk, rs * 3 * N3);
@@ -1367,10 +1421,13 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     ctx->d_atoms = d_atoms;
 #undef AL
     // -------- uploads
+    // shells of Eq. 20: closed 0, open a 1 and b 2 (the triplet's a, b: one
+    // open shell 1), empty 3; the operator applied to an empty band is F^c
     std::vector<int> shell(nb), dummy;
+    auto band_class = [&](int b) { return (b < ctx->nc || b >= ctx->nocc) ? 0 : b - ctx->nc + 1; };
     for (int b = 0; b < nb; ++b) {
-        const int cls = b < ctx->nc ? 0 : b - ctx->nc + 1;
-        shell[b] = (ctx->mode == ROKS_MODE_TRIPLET && cls > 0) ? 1 : cls;
+        const int cls = band_class(b);
+        shell[b] = b >= ctx->nocc ? 3 : ((ctx->mode == ROKS_MODE_TRIPLET && cls > 0) ? 1 : cls);
     }
     std::vector<double> g2(npw), wband(nb);
     const double bq = 2.0 * M_PI / cell->L;
@@ -1378,7 +1435,7 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
         const double gx = bq * ctx->miller[3 * g], gy = bq * ctx->miller[3 * g + 1], gz = bq * ctx->miller[3 * g + 2];
         g2[g] = gx * gx + gy * gy + gz * gz;
     }
-    for (int b = 0; b < nb; ++b) wband[b] = ctx->cf.w[b < ctx->nc ? 0 : b - ctx->nc + 1];
+    for (int b = 0; b < nb; ++b) wband[b] = ctx->cf.w[band_class(b)];
     std::vector<double2> tw64(N);
     for (int t = 0; t < N; ++t) tw64[t] = make_double2(std::cos(-2.0 * M_PI * t / N), std::sin(-2.0 * M_PI * t / N));
     auto up = [&](void* dst, const void* src, size_t bytes) {
@@ -1612,10 +1669,16 @@ roks_status roks_gradient_parts(roks_ctx* ctx, const void* psi, int64_t ld, void
         const double2* M = ctx->d_Th;
         if (part == 0) {
             CK(cudaMemcpyAsync(ctx->d_Gam, ctx->d_Th, sizeof(double2) * nb * nb, cudaMemcpyDeviceToDevice, ctx->st));
+            // the energy's operator of an empty band is F^e = 0
+            if (ctx->ne > 0)
+                CK(cudaMemsetAsync(ctx->d_Gam + (int64_t)ctx->nocc * nb, 0, sizeof(double2) * nb * ctx->ne, ctx->st));
             hermitize(nb, ctx->d_Gam, ctx->st);
             M = ctx->d_Gam;
         }
         CK(cudaMemcpy2DAsync(out, ld * es, fpsi, ld * es, ctx->npw * es, nb, cudaMemcpyDeviceToDevice, ctx->st));
+        if (part == 0 && ctx->ne > 0)
+            CK(cudaMemset2DAsync(static_cast<char*>(out) + (size_t)ctx->nocc * ld * es, ld * es, 0, ctx->npw * es,
+                                 ctx->ne, ctx->st));
         if (ctx->prec == ROKS_FP64)
             gemm_nn<double>(ctx->npw, nb, nb, static_cast<const double2*>(S), lds, M, nb, static_cast<double2*>(out),
                             ld, -1.0, 1.0, ctx->d_gemm_work, ctx->st, ctx->gemm_work_elems * sizeof(double2));
@@ -1688,6 +1751,7 @@ roks_status roks_diis_step(roks_ctx* ctx, void* psi, int64_t ld, const roks_diis
     roks_status r = check_psi(ctx, psi, ld);
     if (r != ROKS_OK) return r;
     enter(ctx);
+    if (ctx->ne > 0) return fail(ctx, ROKS_EINVAL, "the DIIS solver takes occupied bands only (no empty shell)");
     roks_diis_options o;
     if (opt) {
         o = *opt;

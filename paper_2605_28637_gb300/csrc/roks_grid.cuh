@@ -97,9 +97,27 @@ struct PcgScalars {
 // diagonal d_m = <m|F^c|m> is Re theta_mm for closed bands and is formed from
 // expectation values for open ones (w_c (<m|T|m> + <m|V_nl|m>) + <m|V^c|m>,
 // plus the exchange term when open_x is given).
+//
+// Empty bands (n_occ <= n < nb, the empty shell of Eq. 20): their columns of
+// theta hold <m|F^c|n>.  The energy's operator there is F^e = 0, so Gam, Gin
+// and the inter-shell R take theta with those columns zero; R within the
+// empty shell is F^c.  An occupied band m of class k and an empty band n
+// rotate by A_mn = (1/2) atan2(2|R|, <n|F^k|n> - <m|F^k|m>) R/|R|, which
+// takes m to the lower eigenvector of the pair's 2 x 2 block of F^k;
+// dk[k * n_empty + (n - n_occ)] = <n|F^k|n>.  n_occ = nb: no empty bands.
 void pcg_rotation(int nb, int n_closed, const double2* Theta, const double* kin_b, const double* nl_b,
                   const double* open_vc, const double* open_x, double wc, const int* shell, int suppress_ab, int ia,
-                  int ib, double2* Gam, double2* Gin, double2* A, PcgScalars* sc, cudaStream_t st);
+                  int ib, double2* Gam, double2* Gin, double2* A, PcgScalars* sc, cudaStream_t st, int n_occ,
+                  const double* dk);
+// <e|F^k|e> = w_k (<e|T|e> + <e|V_nl|e>) + dvol sum_r V^k(r) rho_e(r) of the
+// n_empty empty bands e = n_occ + i, k = 0, 1, 2 (w_k = w0, w1, w2; class potentials Vk, 3 x N3
+// in the element type; rho_e: the band densities in the element type's
+// density storage, band i at rho_e + (i + 1) N3) -> dk[k * n_empty + i].
+// part: at least 3 n_empty x 64 doubles.
+template <typename T>
+void empty_band_diagonal(int64_t N3, int n_empty, int n_occ, const double* rho_e, const T* Vk, double dvol,
+                         const double* kin_b, const double* nl_b, double w0, double w1, double w2, double* part,
+                         double* dk, cudaStream_t st);
 // sc->rot_pg = 1/2 Re sum conj(A) Gin; sc->r1, r2 as named.
 void pcg_rot_dots(int nb, const double2* A, const double2* Aprev, const double2* Gin, double* part, PcgScalars* sc,
                   cudaStream_t st);

@@ -48,7 +48,7 @@ class roks_species(C.Structure):
 
 
 class roks_occ(C.Structure):
-    _fields_ = [("n_closed", C.c_int), ("n_open", C.c_int), ("mode", C.c_int)]
+    _fields_ = [("n_closed", C.c_int), ("n_open", C.c_int), ("mode", C.c_int), ("n_empty", C.c_int)]
 
 
 class roks_options(C.Structure):
@@ -185,7 +185,7 @@ def roks_setup(cfg: dict, precision: int = ROKS_FP64, stream=None, suppress_ab: 
     at_arr = (roks_atom * max(1, len(atoms)))()
     for i, a in enumerate(atoms):
         at_arr[i] = roks_atom((C.c_double * 3)(*a["pos"]), a["species"], a["depth"], a["width"])
-    occ = roks_occ(cfg["n_closed"], 0 if cfg["mode"] == 0 else 2, cfg["mode"])
+    occ = roks_occ(cfg["n_closed"], 0 if cfg["mode"] == 0 else 2, cfg["mode"], int(cfg.get("n_empty", 0)))
     opt = roks_options(precision, cfg.get("alpha", 0.0), int(suppress_ab), e_tol, g_tol, int(max_iter),
                        synthetic.orbital_stream_seed(cfg), int(precond), int(autotune), int(exx_kernel), int(wait_cap),
                        int(gamma))
