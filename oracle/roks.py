@@ -44,21 +44,25 @@ CUDA path, which implements them independently):
       when a gradient tolerance g_tol > 0 is given, |g| < g_tol at the start
       of the last step (the stationarity the energy criterion stands for,
       Eq. 15 and SI S1, made explicit).
-  R8  the empty shell (Eq. 20, fourth row and column): n_empty unoccupied
+  R13 the empty shell (Eq. 20, fourth row and column): n_empty unoccupied
       bands follow a, b.  They carry no occupation in any configuration, so
       F^e = 0 in the energy and its gradient: theta_mn = <m|F^e|n> = 0 for an
       empty n in gamma, the full gradient g and the in-subspace gradient, and
       R_mn = <m|F^s|n> between an occupied shell s and the empty shell.  The
-      empty-empty block of R is F^c, and an empty band's own out-of-subspace
-      direction is the preconditioned F^c residual (1 - S Psi Psi^H) F^c|e>,
-      so the empty bands relax to the lowest eigenvectors of F^c outside the
-      occupied space; that direction takes the line search's common step but
-      adds nothing to its slope E'(0).  The Fletcher-Reeves ratio (R4) sums
-      over all bands.  The rotation of an occupied-empty pair turns the
-      occupied band to the lower eigenvector of their 2 x 2 block (angle
-      (1/2) atan2(2|R|, d_e - d_o), the Jacobi angle of Eq. 22 when d_o <
-      d_e; past pi/4 it exchanges the pair, so the occupied bands take the
-      lowest states).  Not combined with exact exchange.
+      empty-empty block of R is F^c.  The paper leaves the rest open; read
+      here: an empty band's own out-of-subspace direction is the
+      preconditioned F^c residual (1 - S Psi Psi^H) F^c|e>, so the empty bands
+      relax to the lowest eigenvectors of F^c outside the occupied space; it
+      moves with the accepted step, while the trial point of the line search
+      moves the occupied bands alone (the empty directions add nothing to
+      E'(0), and their second order through the rotation would distort the
+      parabola); the Fletcher-Reeves ratio (R4) takes the occupied bands.  An
+      occupied band m of class k and an empty band rotate by the angle that
+      turns m to the lower eigenvector of the pair's 2 x 2 block of F^k,
+      (1/2) atan2(2|R|, <e|F^k|e> - <m|F^k|m>): the Jacobi angle of Eq. 22
+      when m lies lower, past pi/4 (an exchange) when the empty band does, so
+      the occupied bands take the lowest states.  Not combined with exact
+      exchange.
 
 What pins each part (tests/test_oracle_*.py; none compares the oracle with
 itself): the transforms against the DFT sum and brute force; the basis
@@ -150,7 +154,7 @@ class System:
         self.w = self.C.sum(axis=1)                   # weight of T, V_ext, V_H in F^k
         self.WX = (F_TABLE * c_ch) @ F_TABLE.T        # sum c_L f_k f_k' (exchange pairs)
         # class of the operator applied to each band: closed 0, open a 1 and
-        # b 2; an empty band takes F^c (R8) but no occupation
+        # b 2; an empty band takes F^c (R13) but no occupation
         self.cls = np.array([0] * self.n_closed + list(range(1, self.n_open + 1)) + [0] * self.n_empty)
         self.empty = np.arange(self.nb) >= self.n_occ
 
@@ -447,7 +451,7 @@ def gradient_parts(Psi, FPsi, SPsi, empty=None):
     out-of-subspace part g_I = F Psi - S Psi theta and in-subspace matrix
     Gin_mn = theta_mn - theta_nm^* = 2 <m|g_n> (Eq. 12).
 
-    empty (bool per band, R8): those columns of F Psi hold F^c|e>; the
+    empty (bool per band, R13): those columns of F Psi hold F^c|e>; the
     energy's operator there is F^e = 0, so gamma, g and Gin take theta and
     F Psi with those columns zero, while g_I keeps the F^c residual (the
     empty bands' own direction).  theta is returned as computed."""
@@ -503,7 +507,7 @@ def r_matrix(Theta, cls, mode, suppress_ab=False, empty=None):
     """Off-diagonal R_mn of Eq. 20 from theta: same shell <m|F^s|n> = theta_mn;
     shells s < t: <m|F^s - F^t|n> = theta_nm^* - theta_mn; s > t the conjugate
     relation.  The a-b element is zeroed when the coupling is suppressed.
-    With empty bands (R8) theta_mn = <m|F^c|n> in their columns: F^e = 0
+    With empty bands (R13) theta_mn = <m|F^c|n> in their columns: F^e = 0
     between shells (so R_mn = <m|F^s|n> there) and F^c within the empty
     shell, as in the fourth row and column of Eq. 20."""
     sh = shell_of(cls, mode, empty)
@@ -535,7 +539,7 @@ def rotation_generator(R, d, empty=None, dk=None, cls=None, Theta=None):
     """A_mn = -(1/2) atan(2|x|) x/|x|, x = R_mn/(d_m - d_n) (Eqs. 22-23 with R2, R3);
     computed for m < n and completed anti-Hermitian.
 
-    An occupied band m of class k and an empty band n (R8, the empty bands
+    An occupied band m of class k and an empty band n (R13, the empty bands
     come last): A_mn = (1/2) atan2(2|R_mn|, <n|F^k|n> - <m|F^k|m>) R_mn/|R_mn|
     (R_mn = <m|F^k|n>, dk[k, n] = <n|F^k|n>, Theta_mm = <m|F^k|m>), the
     rotation that takes m to the lower eigenvector of the 2 x 2 block of its
@@ -616,14 +620,14 @@ class PCG:
         R = r_matrix(Theta, sy.cls, sy.mode, self.suppress_ab, empty)
         dk = None
         if sy.n_empty:
-            # <e|F^k|e> of the empty bands for the three classes (R8)
+            # <e|F^k|e> of the empty bands for the three classes (R13)
             Pe = Psi[:, sy.empty]
             dk = np.zeros((3, sy.nb))
             for k in range(3):
                 Fe, _ = sy.apply(Pe, pot, classes=np.full(Pe.shape[1], k, dtype=int), occ=Psi[:, :sy.n_occ])
                 dk[k, sy.empty] = np.real(np.einsum("gm,gm->m", Pe.conj(), Fe))
         A = rotation_generator(R, d, empty, dk, sy.cls, Theta)
-        no = sy.n_occ       # R8: the ratio of the energy's gradient (occupied bands)
+        no = sy.n_occ       # R13: the ratio of the energy's gradient (occupied bands)
         pg = float(np.real(np.vdot(pI[:, :no], gI[:, :no]))) + 0.5 * float(np.real(np.vdot(A, Gin)))
         beta = 0.0 if self.pg_prev is None else pg / self.pg_prev
         restarted = False
@@ -646,7 +650,7 @@ class PCG:
         dt = self.dt
         # the trial point moves the occupied bands only: the empty bands'
         # direction does not change the energy to first order, and its second
-        # order (through the rotation) would distort the parabola (R8)
+        # order (through the rotation) would distort the parabola (R13)
         s_t = s
         if sy.n_empty:
             s_t = s.copy()

@@ -1,5 +1,5 @@
 """Pins of the oracle's empty shell (Eq. 20, fourth row and column; reading
-R8): unoccupied bands after a, b that carry no occupation, the 4 x 4 shell
+R13): unoccupied bands after a, b that carry no occupation, the 4 x 4 shell
 structure of R, and triplet runs with unoccupied bands.
 
 What fixes the oracle here, without comparing it with itself:
@@ -12,9 +12,12 @@ What fixes the oracle here, without comparing it with itself:
 * the converged closed-shell ground state with empty bands spans the lowest
   eigenvectors of the dense generalised problem F^c x = e S x, and the empty
   bands the next ones (the aufbau order of the Kohn-Sham virtual orbitals);
-* a triplet with unoccupied bands converges to the energy of the triplet
-  without them, and its empty bands are eigenvectors of F^c outside the
-  occupied space."""
+* a converged triplet with unoccupied bands is a stationary state of the
+  triplet without them, its empty bands are eigenvectors of F^c outside the
+  occupied space, and none lies below an occupied band in that band's own
+  operator (aufbau);
+* the occupied-empty rotation reaches the lower eigenvalue of a 2 x 2 block
+  whichever of the two lies lower."""
 import numpy as np
 import pytest
 import scipy.linalg
@@ -192,7 +195,7 @@ def test_triplet_with_empty_bands_is_stationary_with_aufbau_empty_bands():
 
 @pytest.mark.parametrize("d_occ,d_emp", [(-1.0, -0.4), (-0.4, -1.0), (0.3, 0.2)])
 def test_occupied_empty_rotation_reaches_the_lower_state(d_occ, d_emp):
-    """The occupied-empty generator (R8) turns the occupied band to the lower
+    """The occupied-empty generator (R13) turns the occupied band to the lower
     eigenvector of the pair's 2 x 2 block, whichever of the two lies lower:
     with |m'> = sum_k U_km |k>, U = exp(A), <m'|H|m'> is H's lower
     eigenvalue; a Jacobi angle (never past pi/4) would leave the occupied
