@@ -108,6 +108,20 @@ def slater_prefactor() -> float:
     return 0.75 * (6.0 / np.pi) ** (1.0 / 3.0)
 
 
+# PBE exchange (the GGA of Sec. III; Perdew, Burke and Ernzerhof 1996):
+# enhancement factor F_x(s) = 1 + kappa - kappa / (1 + mu s^2 / kappa), with
+# mu = beta pi^2 / 3 the gradient-expansion coefficient.
+PBE_KAPPA = 0.804
+PBE_MU = 0.06672455060314922 * np.pi ** 2 / 3.0
+RHO_MIN = 1e-10        # a spin-channel density at or below this carries no exchange
+
+
+def pbe_enhancement(s2):
+    """F_x and dF_x/d(s^2) of PBE exchange at s^2."""
+    den = 1.0 + PBE_MU * s2 / PBE_KAPPA
+    return 1.0 + PBE_MU * s2 / den, PBE_MU / (den * den)
+
+
 @dataclass
 class Potentials:
     rho_k: np.ndarray          # (3, N^3) class densities closed, a, b
@@ -139,6 +153,10 @@ class System:
             raise ValueError("empty bands are not modelled with exact exchange")
         self.hartree = hartree
         self.xc = xc
+        # exchange functional: "slater" (LSDA) or "pbe_x" (PBE exchange, the GGA)
+        self.xc_kind = str(cfg.get("xc", "slater"))
+        if self.xc_kind not in ("slater", "pbe_x"):
+            raise ValueError("unknown exchange functional " + self.xc_kind)
         self._occupations()
         self._basis()
         self._grid_vectors()
@@ -304,14 +322,59 @@ class System:
             VH = np.zeros_like(rho)
             E["H"] = 0.0
         scale = (1.0 - self.alpha) if self.xc else 0.0
-        vx = -scale * np.cbrt(6.0 * rho_ch / np.pi)
-        ex = -scale * slater_prefactor() * self.dvol() * (np.cbrt(rho_ch) * rho_ch).sum(axis=1)
+        vx, ex = self.exchange_channels(rho_ch, scale)
         E["x_M"] = float(ex[0] + ex[1])
         E["x_T"] = float(ex[2] + ex[3])
         E["loc"] = self.dvol() * float((self.Vloc * rho).sum())
         V0 = self.Vloc + VH
         Vk = self.w[:, None] * V0[None, :] + self.C @ vx
         return Potentials(rho_k=rho_k, rho_ch=rho_ch, rho=rho, VH=VH, vx=vx, Vk=Vk, E=E)
+
+    def grid_derivative(self, f: np.ndarray, axis: int) -> np.ndarray:
+        """d f / d r_axis of a real grid field by the spectral derivative:
+        i G_axis f(G), with the Nyquist index of that axis left out (so the
+        derivative of a real field stays real)."""
+        N = self.N
+        g = np.where(self.mt == N // 2, 0.0, self.gx) if N % 2 == 0 else self.gx
+        shape = [1, 1, 1]
+        shape[axis] = N
+        mult = np.broadcast_to(g.reshape(shape), (N, N, N)).reshape(-1)
+        return self.grid_synth(1j * mult * self.grid_fourier(f)).real
+
+    def exchange_channels(self, rho_ch: np.ndarray, scale: float = 1.0):
+        """Exchange potential v^{ch} (4, N^3) and energies (4,) of the channel
+        densities, each a spin density, times `scale` (1 - alpha).
+
+        Slater (LSDA): e = -(3/4) (6/pi)^{1/3} rho^{4/3}, v = -(6 rho / pi)^{1/3}.
+        PBE exchange: e = e_Slater F_x(s), s^2 = |grad rho|^2 / (4 (6 pi^2)^{2/3}
+        rho^{8/3}) (the spin-scaled reduced gradient, E_x[rho_up, rho_dn] =
+        (E_x[2 rho_up] + E_x[2 rho_dn]) / 2), and v = de/drho - div(2
+        de/d|grad rho|^2 grad rho), with spectral derivatives."""
+        dv = self.dvol()
+        r = np.maximum(rho_ch, 0.0)
+        cx = slater_prefactor()
+        if self.xc_kind == "slater":
+            v = -scale * np.cbrt(6.0 * r / np.pi)
+            return v, -scale * cx * dv * (np.cbrt(r) * r).sum(axis=1)
+        k2 = (6.0 * np.pi ** 2) ** (2.0 / 3.0)
+        vx = np.zeros_like(r)
+        ex = np.zeros(r.shape[0])
+        for ch in range(r.shape[0]):
+            rr = r[ch]
+            grad = [self.grid_derivative(rr, c) for c in range(3)]
+            g = grad[0] ** 2 + grad[1] ** 2 + grad[2] ** 2
+            on = rr > RHO_MIN
+            c = np.cbrt(np.where(on, rr, 1.0))
+            s2 = np.where(on, g / (4.0 * k2 * np.where(on, rr, 1.0) ** 2 * c * c), 0.0)
+            F, dF = pbe_enhancement(s2)
+            eL = -cx * rr * c
+            e = np.where(on, eL * F, 0.0)
+            v1 = np.where(on, -(4.0 / 3.0) * cx * c * (F - 2.0 * s2 * dF), 0.0)
+            f = np.where(on, -cx * dF / (2.0 * k2 * np.where(on, rr, 1.0) * c), 0.0)   # 2 de/dg
+            div = sum(self.grid_derivative(f * grad[c], c) for c in range(3))
+            vx[ch] = scale * (v1 - div)
+            ex[ch] = scale * dv * float(e.sum())
+        return vx, ex
 
     # ----------------------------------------------------------- a11: exact exchange
     def coulomb_trunc(self) -> np.ndarray:
