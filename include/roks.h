@@ -127,6 +127,22 @@ enum {
     ROKS_EXX_BARE = 1         /* bare Coulomb 4 pi / G^2 without the G = 0 term  */
 };
 
+/* Exchange functional of the spin channels (Eq. 8's v_x^{sigma L}), scaled
+ * by (1 - alpha).  Per channel density rho (a spin density):
+ *   SLATER: e = -(3/4) (6/pi)^{1/3} rho^{4/3}, v = -(6 rho/pi)^{1/3} (LSDA);
+ *   PBE_X:  the GGA exchange of Perdew, Burke and Ernzerhof (the paper's
+ *           molecules use PBE, Sec. III): e = e_Slater F_x(s), F_x = 1 +
+ *           mu s^2 / (1 + mu s^2/kappa), kappa = 0.804, mu = beta pi^2/3,
+ *           s^2 = |grad rho|^2 / (4 (6 pi^2)^{2/3} rho^{8/3}), and v =
+ *           de/drho - div(2 de/d|grad rho|^2 grad rho), the derivatives
+ *           spectral on the grid (i G, the Nyquist index of each axis left
+ *           out); a channel at or below 1e-10 Bohr^-3 carries no exchange.
+ *           Without correlation, like the Slater model. */
+enum {
+    ROKS_XC_SLATER = 0,
+    ROKS_XC_PBE_X = 1
+};
+
 /* Options.  Every field after e_tol takes its default when zero. */
 typedef struct {
     int precision;     /* ROKS_FP64, or ROKS_MIXED: FP32 transforms and
@@ -173,6 +189,9 @@ typedef struct {
                           inner product.  Two bands share one complex
                           transform.  Requires alpha = 0 and, with an open
                           shell, an even n_closed (ROKS_EINVAL otherwise).   */
+    int xc;            /* ROKS_XC_SLATER (default) or ROKS_XC_PBE_X.  PBE
+                          exchange holds 8 complex and 4 real grids of work
+                          space and adds 16 grid transforms to a potential. */
 } roks_options;
 
 /* Energy terms (Ha).  E_kin, E_loc, E_nl carry the occupation weights;

@@ -381,6 +381,165 @@ __global__ void __launch_bounds__(RB) k_pot_xc(int N3, const typename DensAcc<T>
     }
 }
 
+// ------------------------------------------------------------------ PBE exchange
+// Channel densities (clamped at 0) packed in pairs, gg = (up M + i down M,
+// up T + i down T); the total density for the Hartree solve; V_loc rho.
+template <typename T>
+__global__ void __launch_bounds__(RB) k_gga_pack(int N3, const typename DensAcc<T>::S* __restrict__ rho3,
+                                                 const T* __restrict__ vloc, PotCoefT<T> cf,
+                                                 c2<T>* __restrict__ rho_grid, c2<T>* __restrict__ gg,
+                                                 double* __restrict__ part) {
+    __shared__ double sh[RB];
+    T eloc = 0;
+    for (int p = blockIdx.x * RB + threadIdx.x; p < N3; p += gridDim.x * RB) {
+        using DA = DensAcc<T>;
+        const T rk[3] = {T(DA::value(rho3[p])), T(DA::value(rho3[N3 + p])), T(DA::value(rho3[2 * N3 + p]))};
+        T r[4];
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+            T v = 0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) v += cf.f[k][ch] * rk[k];
+            r[ch] = v > T(0) ? v : T(0);
+        }
+        gg[p] = mk<T>(r[0], r[1]);
+        gg[N3 + p] = mk<T>(r[2], r[3]);
+        const T rt = r[0] + r[1];
+        rho_grid[p] = mk<T>(rt, T(0));
+        eloc += vloc[p] * rt;
+    }
+    const double d = block_sum_t<T>(eloc, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x * 4 + 2] = d;
+        part[blockIdx.x * 4 + 3] = 0.0;
+    }
+}
+
+// grid index p = (x N + y) N + z; the spectral derivative along axis c
+// multiplies by i G_c, with G_c = b f_c and the Nyquist index left out
+template <typename T>
+__device__ __forceinline__ void gga_gvec(int p, int N, T b, T g[3]) {
+    const int z = p % N, y = (p / N) % N, x = p / (N * N);
+    const int idx[3] = {x, y, z};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) g[c] = (2 * idx[c] == N) ? T(0) : b * T(signed_freq(idx[c], N));
+}
+
+// dd[3 P + c] = i G_c gg[P] / N^3 (after the forward transform of gg)
+template <typename T>
+__global__ void __launch_bounds__(RB) k_gga_grad(int N, T b, T inv, const c2<T>* __restrict__ gg,
+                                                 c2<T>* __restrict__ dd) {
+    const int N3 = N * N * N;
+    for (int p = blockIdx.x * RB + threadIdx.x; p < N3; p += gridDim.x * RB) {
+        T g[3];
+        gga_gvec<T>(p, N, b, g);
+#pragma unroll
+        for (int P = 0; P < 2; ++P) {
+            const c2<T> s = gg[(int64_t)P * N3 + p];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                dd[(int64_t)(3 * P + c) * N3 + p] = mk<T>(-g[c] * s.y * inv, g[c] * s.x * inv);
+        }
+    }
+}
+
+// Per point and channel (the gradients in dd after the inverse transform):
+// e, v1 = de/drho (-> v4) and the flux f grad rho, f = 2 de/d|grad rho|^2
+// (-> dd, in place), all times xscale; partial sums of E_x^M, E_x^T.
+template <typename T>
+__global__ void __launch_bounds__(RB) k_gga_point(int N3, const typename DensAcc<T>::S* __restrict__ rho3,
+                                                  PotCoefT<T> cf, T cx, T k2, T mu, T kappa, T rho_min,
+                                                  c2<T>* __restrict__ dd, T* __restrict__ v4,
+                                                  double* __restrict__ part) {
+    __shared__ double sh[RB];
+    T exM = 0, exT = 0;
+    const T xs = cf.xscale;
+    for (int p = blockIdx.x * RB + threadIdx.x; p < N3; p += gridDim.x * RB) {
+        using DA = DensAcc<T>;
+        const T rk[3] = {T(DA::value(rho3[p])), T(DA::value(rho3[N3 + p])), T(DA::value(rho3[2 * N3 + p]))};
+#pragma unroll
+        for (int P = 0; P < 2; ++P) {
+            c2<T> gr[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) gr[c] = dd[(int64_t)(3 * P + c) * N3 + p];
+            T fl[2][3];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int ch = 2 * P + h;
+                T r = 0;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) r += cf.f[k][ch] * rk[k];
+                r = r > T(0) ? r : T(0);
+                const T gx = h ? gr[0].y : gr[0].x, gy = h ? gr[1].y : gr[1].x, gz = h ? gr[2].y : gr[2].x;
+                T e = 0, v1 = 0, f = 0;
+                if (r > rho_min) {
+                    const T c = cbrt(r);
+                    const T s2 = (gx * gx + gy * gy + gz * gz) / (T(4) * k2 * r * r * c * c);
+                    const T den = T(1) + mu * s2 / kappa;
+                    const T F = T(1) + mu * s2 / den;
+                    const T dF = mu / (den * den);
+                    e = -xs * cx * r * c * F;
+                    v1 = -(T(4) / T(3)) * xs * cx * c * (F - T(2) * s2 * dF);
+                    f = -xs * cx * dF / (T(2) * k2 * r * c);
+                }
+                v4[(int64_t)ch * N3 + p] = v1;
+                fl[h][0] = f * gx;
+                fl[h][1] = f * gy;
+                fl[h][2] = f * gz;
+                if (P == 0) exM += e;
+                else exT += e;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dd[(int64_t)(3 * P + c) * N3 + p] = mk<T>(fl[0][c], fl[1][c]);
+        }
+    }
+    const double dM = block_sum_t<T>(exM, sh);
+    const double dT = block_sum_t<T>(exT, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x * 4 + 0] = dM;
+        part[blockIdx.x * 4 + 1] = dT;
+    }
+}
+
+// gg[P] = sum_c i G_c dd[3 P + c] / N^3 (after the forward transform of dd)
+template <typename T>
+__global__ void __launch_bounds__(RB) k_gga_div(int N, T b, T inv, const c2<T>* __restrict__ dd,
+                                                c2<T>* __restrict__ gg) {
+    const int N3 = N * N * N;
+    for (int p = blockIdx.x * RB + threadIdx.x; p < N3; p += gridDim.x * RB) {
+        T g[3];
+        gga_gvec<T>(p, N, b, g);
+#pragma unroll
+        for (int P = 0; P < 2; ++P) {
+            T re = 0, im = 0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const c2<T> s = dd[(int64_t)(3 * P + c) * N3 + p];
+                re -= g[c] * s.y;
+                im += g[c] * s.x;
+            }
+            gg[(int64_t)P * N3 + p] = mk<T>(re * inv, im * inv);
+        }
+    }
+}
+
+// v^{ch} = v1 - div (gg after the inverse transform); xc3[k] = sum_ch C[k][ch] v^{ch}
+template <typename T>
+__global__ void __launch_bounds__(RB) k_gga_combine(int N3, PotCoefT<T> cf, const T* __restrict__ v4,
+                                                    const c2<T>* __restrict__ gg, T* __restrict__ xc3) {
+    for (int p = blockIdx.x * RB + threadIdx.x; p < N3; p += gridDim.x * RB) {
+        const c2<T> d0 = gg[p], d1 = gg[N3 + p];
+        const T v[4] = {v4[p] - d0.x, v4[N3 + p] - d0.y, v4[2 * N3 + p] - d1.x, v4[3 * N3 + p] - d1.y};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            T s = 0;
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch) s += cf.C[k][ch] * v[ch];
+            xc3[(int64_t)k * N3 + p] = s;
+        }
+    }
+}
+
 // After the forward transform: rho(G) = grid / N^3; E_H partial
 // sum 4 pi |rho(G)|^2 / G^2; grid <- V_H(G) = 4 pi rho(G) / G^2 (G = 0 -> 0).
 template <typename T>
@@ -564,7 +723,7 @@ constexpr int kPotBlocks = 512;
 template <typename T>
 void potentials(int N, double L, const double* rho3, const T* vloc, const PotCoef& cf, c2<T>* grid,
                 T* xc3, const c2<T>* tw, T* Vk, double* Vk64, double* part, double* out6,
-                cudaStream_t st, bool energies_only) {
+                cudaStream_t st, bool energies_only, const GgaWork* gga) {
     // out6: [E_x^M, E_x^T, E_loc, E_H, <a|V^c|a>, <b|V^c|b>]; energies_only
     // stops after E_H (out6[4..5] and Vk are left as they were)
     const int N3 = N * N * N;
@@ -580,14 +739,39 @@ void potentials(int N, double L, const double* rho3, const T* vloc, const PotCoe
             ct.C[k][ch] = T(cf.C[k][ch]);
         }
     ct.xscale = T(cf.xscale);
-    roks::count_launch(), k_pot_xc<T><<<kPotBlocks, RB, 0, st>>>(N3, r3, vloc, ct, T(c6), T(0.75 * c6), grid, xc3,
-                                                                  part);
+    c2<T>* gg = gga ? static_cast<c2<T>*>(gga->gg) : nullptr;
+    c2<T>* dd = gga ? static_cast<c2<T>*>(gga->dd) : nullptr;
+    if (!gga) {
+        roks::count_launch(), k_pot_xc<T><<<kPotBlocks, RB, 0, st>>>(N3, r3, vloc, ct, T(c6), T(0.75 * c6), grid,
+                                                                      xc3, part);
+    } else {
+        // PBE exchange: the channels' gradients by two forward and six
+        // inverse grid transforms, then the pointwise energy, de/drho and flux
+        const T inv = T(1.0 / double(N3));
+        roks::count_launch(), k_gga_pack<T><<<kPotBlocks, RB, 0, st>>>(N3, r3, vloc, ct, grid, gg, part);
+        grid_fft3_batched<T>(N, tw, gg, 2, (int64_t)N3, -1, st);
+        roks::count_launch(), k_gga_grad<T><<<kPotBlocks, RB, 0, st>>>(N, T(b), inv, gg, dd);
+        grid_fft3_batched<T>(N, tw, dd, 6, (int64_t)N3, +1, st);
+        roks::count_launch(), k_gga_point<T><<<kPotBlocks, RB, 0, st>>>(
+                                  N3, r3, ct, T(0.75 * c6), T(std::pow(6.0 * kPi * kPi, 2.0 / 3.0)), T(gga->mu),
+                                  T(gga->kappa), T(gga->rho_min), dd, static_cast<T*>(gga->v4), part);
+    }
     roks::count_launch(), k_partials_final<<<4, RB, 0, st>>>(kPotBlocks, 4, part, out6, dvol, dvol, dvol, 0.0);
     grid_fft3<T>(N, tw, grid, -1, st);
     roks::count_launch(), k_hartree_G<T><<<kPotBlocks, RB, 0, st>>>(N, T(1.0 / double(N3)), T(4.0 * kPi / (b * b)),
                                                                      grid, part);
     roks::count_launch(), k_partials_final<<<1, RB, 0, st>>>(kPotBlocks, 1, part, out6 + 3, 0.5 * L * L * L, 0, 0, 0);
     if (energies_only) return;
+    if (gga) {
+        // the divergence of the fluxes: six forward transforms, i G . flux,
+        // two inverse transforms
+        const T inv = T(1.0 / double(N3));
+        grid_fft3_batched<T>(N, tw, dd, 6, (int64_t)N3, -1, st);
+        roks::count_launch(), k_gga_div<T><<<kPotBlocks, RB, 0, st>>>(N, T(b), inv, dd, gg);
+        grid_fft3_batched<T>(N, tw, gg, 2, (int64_t)N3, +1, st);
+        roks::count_launch(), k_gga_combine<T><<<kPotBlocks, RB, 0, st>>>(N3, ct, static_cast<const T*>(gga->v4),
+                                                                           gg, xc3);
+    }
     grid_fft3<T>(N, tw, grid, +1, st);
     roks::count_launch(), k_pot_class<T><<<kPotBlocks, RB, 0, st>>>(N3, vloc, grid, xc3, r3, cf, Vk, Vk64, part);
     roks::count_launch(), k_partials_final<<<2, RB, 0, st>>>(kPotBlocks, 2, part, out6 + 4, dvol, dvol, 0, 0);
@@ -620,7 +804,8 @@ void axpy(int npw, int nb, const c2<T>* x, int64_t ldx, const c2<T>* y, int64_t 
     template void column_total<T>(int, int, int, const c2<T>*, int64_t, const c2<T>*, int64_t, const T*,      \
                                   double*, double*, double, cudaStream_t);                                     \
     template void potentials<T>(int, double, const double*, const T*, const PotCoef&, c2<T>*, T*,             \
-                                const c2<T>*, T*, double*, double*, double*, cudaStream_t, bool);             \
+                                const c2<T>*, T*, double*, double*, double*, cudaStream_t, bool,              \
+                                const GgaWork*);                                                               \
     template void precondition<T>(int, int, const c2<T>*, int64_t, const T*, const double*, c2<T>*,           \
                                   int64_t, cudaStream_t);                                                      \
     template void axpy<T>(int, int, const c2<T>*, int64_t, const c2<T>*, int64_t, const double*, double,      \

@@ -44,6 +44,9 @@ struct roks_ctx {
     // empty shell (Eq. 20): bands nocc .. nb - 1 carry no occupation; ne of them
     int nocc = 0, ne = 0;
     double* d_rho_e = nullptr;   // their densities, band i at (i + 1) N^3 (density storage)
+    // exchange functional (roks_options.xc) and PBE exchange's work grids
+    int xc = ROKS_XC_SLATER;
+    GgaWork gga{};
     double* d_dk = nullptr;      // <e|F^k|e>, 3 x ne
     // Gamma point (roks_options.gamma): npw counts the half sphere, the tail
     // of the full basis from row h0; the transforms run on nbt packed bands
@@ -395,7 +398,8 @@ struct Impl {
         PROF("potential");
         potentials<T>(ctx->N, ctx->L, ctx->d_rho3, static_cast<const T*>(ctx->d_vloc_t), ctx->cf,
                       reinterpret_cast<V*>(ctx->d_grid), reinterpret_cast<T*>(ctx->d_xc3), ccv(ctx->d_tw),
-                      static_cast<T*>(ctx->d_Vk), nullptr, ctx->d_part, ctx->d_out6, st, energies_only);
+                      static_cast<T*>(ctx->d_Vk), nullptr, ctx->d_part, ctx->d_out6, st, energies_only,
+                      ctx->xc == ROKS_XC_PBE_X ? &ctx->gga : nullptr);
         energy_combine(ctx->d_kin_b, ctx->d_nl_b, ctx->nocc, ctx->d_wband, ctx->d_out6, ctx->cM, ctx->cT,
                        ctx->alpha, ctx->alpha != 0.0 ? ctx->d_hf2 : nullptr, ctx->d_E, st);
         CK(cudaGetLastError());
@@ -1146,6 +1150,7 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     if (opt->exx_kernel != ROKS_EXX_TRUNCATED && opt->exx_kernel != ROKS_EXX_BARE) return ROKS_EINVAL;
     if (opt->autotune != 0 && opt->autotune != 1) return ROKS_EINVAL;
     if (opt->gamma != 0 && opt->gamma != 1) return ROKS_EINVAL;
+    if (opt->xc != ROKS_XC_SLATER && opt->xc != ROKS_XC_PBE_X) return ROKS_EINVAL;
     // the Gamma-point packing pairs bands (2k, 2k + 1): an open pair must be
     // one packed band, and exact exchange runs on the complex path only
     if (opt->gamma && (opt->alpha != 0.0 || (occ->mode != ROKS_MODE_GS && (occ->n_closed & 1)))) return ROKS_EINVAL;
@@ -1173,6 +1178,7 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     ctx->exx_kernel = opt->exx_kernel;
     ctx->autotune = opt->autotune;
     ctx->gamma = opt->gamma;
+    ctx->xc = opt->xc;
     ctx->mlp_kind = opt->precond;   // all-zero network weights until trained ones are set
     ctx->suppress_ab = opt->suppress_ab;
     ctx->mode = occ->mode;
@@ -1335,6 +1341,15 @@ roks_status roks_setup(const roks_cell* cell, double ecut, int natoms, const rok
     if (ctx->gamma) AL(ctx->d_Cpk, cs * (size_t)ctx->ldc_pk * ctx->nbt);
     AL(ctx->d_rho3, sizeof(double) * 3 * N3);
     AL(ctx->d_rho_slot, sizeof(double) * (opt->autotune ? kDensityGroupsMax : kDensityGroups) * N3);
+    if (ctx->xc == ROKS_XC_PBE_X) {
+        AL(ctx->gga.gg, 2 * rs * 2 * N3);
+        AL(ctx->gga.dd, 2 * rs * 6 * N3);
+        AL(ctx->gga.v4, rs * 4 * N3);
+        // PBE's kappa and mu = beta pi^2 / 3 (beta of the gradient expansion)
+        ctx->gga.kappa = 0.804;
+        ctx->gga.mu = 0.06672455060314922 * M_PI * M_PI / 3.0;
+        ctx->gga.rho_min = 1e-10;
+    }
     if (ctx->ne > 0) {
         AL(ctx->d_rho_e, sizeof(double) * (size_t)(ctx->ne + 1) * N3);
         AL(ctx->d_dk, sizeof(double) * 3 * ctx->ne * (1 + 64));   // values, then block partials

@@ -58,10 +58,23 @@ void density_to_f64(int64_t n, const double* rho3, double* out, cudaStream_t st)
 // in FP64.  rho3 in DensAcc<T> storage; vloc and the exchange-correlation
 // fields xc3 (3 x N^3) in the element type T.  energies_only: out6[0..3]
 // alone (no inverse transform, no class potentials Vk).
+//
+// gga: work grids of PBE exchange (the GGA); null keeps the Slater exchange.
+// Per spin channel e = e_Slater F_x(s), F_x = 1 + mu s^2 / (1 + mu s^2 /
+// kappa), s^2 = |grad rho|^2 / (4 (6 pi^2)^{2/3} rho^{8/3}), and v = de/drho -
+// div(2 de/d|grad rho|^2 grad rho), with spectral derivatives (i G_c, the
+// Nyquist index of axis c left out); a channel at or below rho_min carries
+// no exchange.
+struct GgaWork {
+    void* gg = nullptr;   // 2 N^3 complex T: the channel pairs (up M + i down M, up T + i down T)
+    void* dd = nullptr;   // 6 N^3 complex T: their three derivatives, then the fluxes
+    void* v4 = nullptr;   // 4 N^3 T: de/drho per channel
+    double mu = 0, kappa = 0, rho_min = 0;
+};
 template <typename T>
 void potentials(int N, double L, const double* rho3, const T* vloc, const PotCoef& cf, c2<T>* grid,
                 T* xc3, const c2<T>* tw, T* Vk, double* Vk64, double* part, double* out6,
-                cudaStream_t st, bool energies_only = false);
+                cudaStream_t st, bool energies_only = false, const GgaWork* gga = nullptr);
 size_t potentials_part_elems();
 template <typename T>
 void precondition(int npw, int nb, const c2<T>* gI, int64_t ld, const T* g2h, const double* sums, c2<T>* out,

@@ -34,6 +34,10 @@ class RoksError(RuntimeError):
         self.status = status
 
 
+# exchange functionals (roks_options.xc) by the workload's name for them
+XC_KINDS = {"slater": 0, "pbe_x": 1}
+
+
 class roks_cell(C.Structure):
     _fields_ = [("L", C.c_double), ("grid", C.c_int)]
 
@@ -54,7 +58,8 @@ class roks_occ(C.Structure):
 class roks_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("alpha", C.c_double), ("suppress_ab", C.c_int), ("e_tol", C.c_double),
                 ("g_tol", C.c_double), ("max_iter", C.c_int), ("seed", C.c_uint64), ("precond", C.c_int),
-                ("autotune", C.c_int), ("exx_kernel", C.c_int), ("wait_cap", C.c_int), ("gamma", C.c_int)]
+                ("autotune", C.c_int), ("exx_kernel", C.c_int), ("wait_cap", C.c_int), ("gamma", C.c_int),
+                ("xc", C.c_int)]
 
 
 ROKS_EXX_TRUNCATED, ROKS_EXX_BARE = 0, 1
@@ -165,7 +170,7 @@ def _ptr(t):
 # ---------------------------------------------------------------- C names
 def roks_setup(cfg: dict, precision: int = ROKS_FP64, stream=None, suppress_ab: bool = False,
                e_tol: float = 1e-6, g_tol: float = 0.0, max_iter: int = 0, precond: int = 0, autotune: int = 0,
-               exx_kernel: int = ROKS_EXX_TRUNCATED, wait_cap: int = 0, gamma: int = 0):
+               exx_kernel: int = ROKS_EXX_TRUNCATED, wait_cap: int = 0, gamma: int = 0, xc=None):
     """Marshal a workload description (see synthetic.make_config) and call roks_setup."""
     lib = load()
     cell = roks_cell(cfg["L"], cfg["grid"])
@@ -188,7 +193,7 @@ def roks_setup(cfg: dict, precision: int = ROKS_FP64, stream=None, suppress_ab: 
     occ = roks_occ(cfg["n_closed"], 0 if cfg["mode"] == 0 else 2, cfg["mode"], int(cfg.get("n_empty", 0)))
     opt = roks_options(precision, cfg.get("alpha", 0.0), int(suppress_ab), e_tol, g_tol, int(max_iter),
                        synthetic.orbital_stream_seed(cfg), int(precond), int(autotune), int(exx_kernel), int(wait_cap),
-                       int(gamma))
+                       int(gamma), XC_KINDS[cfg.get("xc", "slater") if xc is None else xc])
     out = C.c_void_p()
     st = C.c_void_p(stream) if stream else None
     status = lib.roks_setup(C.byref(cell), cfg["ecut"], len(atoms), at_arr, len(cfg["species"]), sp_arr,
