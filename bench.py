@@ -71,6 +71,8 @@ def parse():
                          "smaller context with the same block shapes); 0: the workload's own")
     ap.add_argument("--gamma-steps", type=int, default=20,
                     help="PCG steps of the Gamma-point leg (real orbitals, half sphere; 0: skip)")
+    ap.add_argument("--gga-steps", type=int, default=10,
+                    help="PCG steps of the PBE-exchange leg (roks_options.xc = ROKS_XC_PBE_X; 0: skip)")
     ap.add_argument("--diis-steps", type=int, default=50,
                     help="timed DIIS steps (roks_diis_step) after the PCG legs; 0 skips them")
     return ap.parse_args()
@@ -699,6 +701,29 @@ def gamma_leg(args, cfg, torch, complex_ms_per_step):
     return out
 
 
+def gga_leg(args, cfg, torch, slater_ms_per_step):
+    """The benchmark's workload with PBE exchange (the GGA) in place of the
+    Slater exchange: graph-replayed PCG steps timed with CUDA events, and the
+    potential family's time per call from a profiled eager pass (its grid
+    gradient and divergence transforms)."""
+    from paper_2605_28637_gb300 import roks, synthetic as syn
+    c = syn.with_changes(cfg, xc="pbe_x")
+    ctx = roks.Context(c, args.precision, autotune=1)
+    psi = ctx.init_orbitals(syn.orbital_uniforms(c, ctx.npw))
+    for _ in range(max(3, args.warmup)):
+        ctx.pcg_step(psi)
+    ms, infos, _ = time_pcg(ctx, psi, args.gga_steps, torch)
+    _, _, prof = time_pcg(ctx, psi, min(args.gga_steps, 5), torch, profile=True)
+    pot = [e for e in prof if e["name"] == "potential"]
+    per = ms / args.gga_steps
+    out = {"workload": cfg["name"], "xc": "pbe_x", "steps": args.gga_steps, "ms_per_step": per,
+           "value": ctx.nb / (per / 1000.0), "unit": UNIT, "ms_per_step_slater": slater_ms_per_step,
+           "potential_ms_per_call": pot[0]["ms"] / pot[0]["launches"] if pot else None,
+           "E_last": infos[-1]["E_new"], "launch": "one CUDA graph per PCG iteration"}
+    ctx.close()
+    return out
+
+
 def fp64_leg(cfg, torch, steps=5):
     """The plain FP64 path on the convergence workload: seconds per PCG step
     (graph replays) and the rooflines of its kernel families from a profiled
@@ -970,6 +995,9 @@ def run_gpu(args):
     gamma = None
     if args.gamma_steps > 0 and rank == 0:
         gamma = gamma_leg(args, cfg, torch, ms_max / args.steps)
+    gga = None
+    if args.gga_steps > 0 and rank == 0:
+        gga = gga_leg(args, cfg, torch, ms_max / args.steps)
     hybrid = None
     if args.hybrid_applies > 0 and rank == 0:
         hybrid = hybrid_leg(args, torch)
@@ -1002,6 +1030,7 @@ def run_gpu(args):
             "forces": forces_leg,
             "hybrid": hybrid,
             "gamma": gamma,
+            "gga": gga,
             "profile": {e["name"]: {"launches": e["launches"], "ms": e["ms"]} for e in prof},
             "launch": "one CUDA graph per PCG iteration",
             "E_last": infos[-1]["E_new"] if infos else None,
