@@ -71,6 +71,9 @@ def parse():
                          "smaller context with the same block shapes); 0: the workload's own")
     ap.add_argument("--gamma-steps", type=int, default=20,
                     help="PCG steps of the Gamma-point leg (real orbitals, half sphere; 0: skip)")
+    ap.add_argument("--autotune", type=int, default=1, choices=(0, 1),
+                    help="1: the library times its launch shapes on each context's buffers at setup; "
+                         "0: the default shapes (for profiler runs, whose timing the autotuner should not read)")
     ap.add_argument("--gga-steps", type=int, default=10,
                     help="PCG steps of the PBE-exchange leg (roks_options.xc = ROKS_XC_PBE_X; 0: skip)")
     ap.add_argument("--diis-steps", type=int, default=50,
@@ -683,7 +686,7 @@ def gamma_leg(args, cfg, torch, complex_ms_per_step):
     transform.  Same seeded start drawn on the half sphere, graph-replayed
     PCG steps timed with CUDA events on the context's stream."""
     from paper_2605_28637_gb300 import roks, synthetic as syn
-    ctx = roks.Context(cfg, args.precision, autotune=1, gamma=1)
+    ctx = roks.Context(cfg, args.precision, autotune=args.autotune, gamma=1)
     psi = ctx.init_orbitals(syn.orbital_uniforms(cfg, ctx.npw))
     for _ in range(max(3, args.warmup)):
         ctx.pcg_step(psi)
@@ -708,7 +711,7 @@ def gga_leg(args, cfg, torch, slater_ms_per_step):
     gradient and divergence transforms)."""
     from paper_2605_28637_gb300 import roks, synthetic as syn
     c = syn.with_changes(cfg, xc="pbe_x")
-    ctx = roks.Context(c, args.precision, autotune=1)
+    ctx = roks.Context(c, args.precision, autotune=args.autotune)
     psi = ctx.init_orbitals(syn.orbital_uniforms(c, ctx.npw))
     for _ in range(max(3, args.warmup)):
         ctx.pcg_step(psi)
@@ -801,8 +804,8 @@ def run_gpu(args):
     if args.n_closed > 0:
         cfg = syn_with(cfg, n_closed=args.n_closed)
     # the autotuner picks the density's band grouping and the tensor-core
-    # split depth on this context's own buffers (roks_options.autotune)
-    ctx = roks.Context(cfg, args.precision, autotune=1)
+    # schedule on this context's own buffers (roks_options.autotune)
+    ctx = roks.Context(cfg, args.precision, autotune=args.autotune)
     tuning = ctx.tuning()
     u = syn.orbital_uniforms(cfg, ctx.npw)
     psi = ctx.init_orbitals(u)

@@ -392,10 +392,13 @@ ROKS_API roks_status roks_forces(roks_ctx* ctx, const void* psi, int64_t ld, dou
 
 /* Launch shapes in use (the autotuner's choices when roks_options.autotune
  * was set, else the defaults): the number of band groups of the density's
- * x-stage transform (2, 4 or 8; default 4) and the K-split depth of the
- * tensor-core A^H B products in waves of one CTA per SM, times two (3, 5 or
- * 8; default 5).  candidate_ms: the timed candidates in that order (ms per
- * launch; 0 when not timed).  Host struct, filled before the call returns. */
+ * x-stage transform (2, 4 or 8; default 4) and the schedule of the
+ * tensor-core A^H B products: 2 is a stream-K schedule over one wave of
+ * one CTA per SM (each CTA an equal run of the (tile, K stage) units, the
+ * tiles' partial sums added in K order; the default), 5 and 8 split K over
+ * 2.5 or 4 waves.  candidate_ms: the timed candidates in that order (ms
+ * per launch; 0 when not timed).  Host struct, filled before the call
+ * returns. */
 typedef struct {
     int density_groups;
     int tc_split_waves_x2;

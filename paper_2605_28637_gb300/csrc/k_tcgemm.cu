@@ -48,6 +48,7 @@
 // for with the default bound before the tensor memory is freed.
 #include <cuda.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdlib>
 
@@ -151,9 +152,19 @@ struct GbPlan {
     static constexpr int LAG = CONVERT ? 2 : 0;                 // drain of stage i - LAG in iteration i
 };
 
-template <bool NN, bool APRE>
+// Stream-K schedule of A^H B (ctas > 0): one CTA per SM, CTA c takes units
+// units * c / ctas .. units * (c + 1) / ctas - 1 of the (tile, stage)
+// sequence, stage fastest (tile t: M tile t % mt, N tile t / mt), and writes
+// the partial sums of each tile it touches to its segment slot c * maxseg +
+// (t - its first tile).  ctas = 0: split K over the grid's z.
+struct SkPlan {
+    int64_t units = 0;
+    int ctas = 0, maxseg = 0, mt = 0;
+};
+
+template <bool NN, bool APRE, bool SK = false>
 __global__ void __launch_bounds__(GB_THREADS, 1)
-    k_tcgemm(int M, int N, int stages_per_cta, int total_stages, const __grid_constant__ CUtensorMap tmA,
+    k_tcgemm(int M, int N, int stages_per_cta, int total_stages, SkPlan sk, const __grid_constant__ CUtensorMap tmA,
              const __grid_constant__ CUtensorMap tmB, const unsigned char* __restrict__ bsplit,
              const unsigned char* __restrict__ asplit, float2* __restrict__ part, const float2* Cin, int64_t ldcin,
              float2* Cout, int64_t ldc, float alpha, float beta, uint32_t wcap) {
@@ -174,7 +185,14 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
     const int mi = NN ? blockIdx.y : blockIdx.x, ni = NN ? blockIdx.x : blockIdx.y;
     const int m0 = mi * GB_M, n0 = ni * GB_NC;
     const int s0 = NN ? 0 : blockIdx.z * stages_per_cta;
-    const int ns = NN ? total_stages : max(0, min(total_stages, s0 + stages_per_cta) - s0);
+    static_assert(!(SK && NN), "stream-K takes A^H B only");
+    const int64_t u0 = SK ? sk.units * blockIdx.x / sk.ctas : 0;
+    // stream-K: the first unit's tile and stage (the loops then step them)
+    const int t_first = SK ? (int)(u0 / total_stages) : 0;
+    const int s_first = SK ? (int)(u0 - (int64_t)t_first * total_stages) : 0;
+    const int ns = NN ? total_stages
+                      : (SK ? (int)(sk.units * (blockIdx.x + 1) / sk.ctas - u0)
+                            : max(0, min(total_stages, s0 + stages_per_cta) - s0));
 
     if (tid == 0) {
         for (int s = 0; s < GB_RAW; ++s) {
@@ -204,6 +222,7 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
         // ------------------------------------------------ producer
         if (lane == 0) {
             int issued = 0, bissued = 0;
+            int t_cur = t_first, s_cur = s_first;
             for (int i = 0; i < ns; ++i) {
                 if (PL::RAW) {
                     const int rs = i % GB_RAW;
@@ -212,14 +231,23 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
                         break;
                     }
                     unsigned char* ra = raw + (size_t)rs * PL::RAWS;
-                    const int k0 = (s0 + i) * GB_KC;
+                    int k0 = (s0 + i) * GB_KC, am = m0, bn = n0;
+                    if (SK) {
+                        k0 = s_cur * GB_KC;
+                        am = (t_cur % sk.mt) * GB_M;
+                        bn = (t_cur / sk.mt) * GB_NC;
+                        if (++s_cur == total_stages) {
+                            s_cur = 0;
+                            ++t_cur;
+                        }
+                    }
                     if (NN) {
                         tc::mbar_arrive_expect_tx(&raw_full[rs], GB_RAWA);
                         tc::tma_2d(ra, &tmA, m0, k0, &raw_full[rs]);
                     } else {
                         tc::mbar_arrive_expect_tx(&raw_full[rs], PL::RAWA + PL::RAWB);
-                        if (!APRE) tc::tma_2d(ra, &tmA, k0, m0, &raw_full[rs]);
-                        tc::tma_2d(ra + PL::RAWA, &tmB, k0, n0, &raw_full[rs]);
+                        if (!APRE) tc::tma_2d(ra, &tmA, k0, am, &raw_full[rs]);
+                        tc::tma_2d(ra + PL::RAWA, &tmB, k0, bn, &raw_full[rs]);
                     }
                     issued = i + 1;
                 }
@@ -309,6 +337,8 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
 #pragma unroll
         for (int j = 0; j < 16; ++j) re[j] = im[j] = 0.f;
         bool ok = true;
+        // stream-K: stages left in the current tile's segment, its index
+        int left = total_stages - s_first, seg = 0;
         for (int i = 0; i < ns + PL::LAG; ++i) {
             if (PL::CONVERT && i < ns) {
                 const int rs = i % GB_RAW, cs = i % SL;
@@ -376,6 +406,20 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
                 tc::fence_before_sync();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&acc_empty[b]);
+                if (SK) {
+                    // the last stage of a tile in this CTA's run: its partial
+                    // sums go to the segment slot, and the sums restart
+                    if (--left == 0 || dsg == ns - 1) {
+                        float2* Pp = part + ((int64_t)blockIdx.x * sk.maxseg + seg) * GB_NC * GB_M;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            Pp[(int64_t)(16 * cg + j) * GB_M + r] = make_float2(re[j], im[j]);
+                            re[j] = im[j] = 0.f;
+                        }
+                        ++seg;
+                        left = total_stages;
+                    }
+                }
             }
         }
         if (!ok) give_up(&failed);
@@ -397,7 +441,7 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
                         }
                     }
                 }
-            } else {
+            } else if (!SK) {
                 const int tile = blockIdx.x + blockIdx.y * gridDim.x;
                 const int tiles = gridDim.x * gridDim.y;
                 float2* P = part + ((int64_t)blockIdx.z * tiles + tile) * GB_NC * GB_M;
@@ -499,6 +543,31 @@ __global__ void k_tcg_reduce(int M, int N, int mt, int tiles, int ks, const floa
     C[(int64_t)n * ldc + m] = make_double2(sr, si);
 }
 
+// The stream-K partials of tile t: the CTAs whose unit runs meet the tile's
+// units t T .. (t + 1) T - 1, in CTA (that is K) order, summed in FP64.
+__global__ void k_tcg_reduce_sk(int M, int N, int mt, int T, SkPlan sk, const float2* __restrict__ part,
+                                double2* __restrict__ C, int ldc) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)M * N) return;
+    const int m = (int)(idx % M), n = (int)(idx / M);
+    const int t = (m / GB_M) + (n / GB_NC) * mt;
+    const int64_t off = (int64_t)(n % GB_NC) * GB_M + (m % GB_M);
+    const int64_t ta = (int64_t)t * T, tb = ta + T;
+    int c = (int)(ta * sk.ctas / sk.units) - 1;
+    if (c < 0) c = 0;
+    double sr = 0.0, si = 0.0;
+    for (; c < sk.ctas; ++c) {
+        const int64_t a = sk.units * c / sk.ctas, b = sk.units * (c + 1) / sk.ctas;
+        if (a >= tb) break;
+        if (b <= ta || a == b) continue;   // no unit of the tile (or none at all)
+        const int seg = t - (int)(a / T);
+        const float2 p = part[((int64_t)c * sk.maxseg + seg) * GB_NC * GB_M + off];
+        sr += (double)p.x;
+        si += (double)p.y;
+    }
+    C[(int64_t)n * ldc + m] = make_double2(sr, si);
+}
+
 int sm_count() {
     static int n = 0;
     if (n == 0) {
@@ -514,11 +583,11 @@ int sm_count() {
 
 bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 
-template <bool NN, bool APRE>
+template <bool NN, bool APRE, bool SK = false>
 void set_attr() {
     static bool done = false;
     if (!done) {
-        cudaFuncSetAttribute(k_tcgemm<NN, APRE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_tcgemm<NN, APRE, SK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)GbPlan<NN, APRE>::SMEM);
         done = true;
     }
@@ -551,11 +620,25 @@ const unsigned char* find_presplit(const void* A, int64_t lda, int M, int K) {
     return nullptr;
 }
 
-// Waves of CTAs (one per SM) a CN product is split into, times two
-// (tcg_set_waves; 5 = 2.5 waves unless the autotuner chose otherwise)
-int g_waves_x2 = 5;
+// Schedule of A^H B (tcg_set_waves): 2 (the default) is the stream-K
+// schedule over one wave of one CTA per SM; 5 and 8 split K into 2.5 or 4
+// waves.  Stream-K removes the partial last wave of the split (P^H Psi at
+// mgo-120: 385 CTAs ran as 3 waves of 148): 1.45 -> 1.23 ms.
+int g_waves_x2 = 2;
 
 // K splits of a CN product: about g_waves_x2 / 2 waves of CTAs
+// waves_x2 = 2: the stream-K schedule over one wave (one CTA per SM)
+SkPlan cn_stream_k(int mt, int nt, int total) {
+    SkPlan p;
+    if (g_waves_x2 != 2) return p;
+    p.ctas = sm_count();
+    p.mt = mt;
+    p.units = (int64_t)mt * nt * total;
+    const int64_t len = (p.units + p.ctas - 1) / p.ctas;
+    p.maxseg = (int)((len + total - 1) / total) + 1;
+    return p;
+}
+
 int cn_splits(int tiles, int total) {
     int ks = (g_waves_x2 * sm_count() / 2 + tiles - 1) / tiles;
     if (ks > total) ks = total;
@@ -577,14 +660,26 @@ bool tcg_enabled() {
     return on == 1;
 }
 
-void tcg_set_waves(int waves_x2) { g_waves_x2 = waves_x2 >= 1 ? waves_x2 : 5; }
+void tcg_set_waves(int waves_x2) { g_waves_x2 = waves_x2 >= 1 ? waves_x2 : 2; }
 
 bool tcg_cn_takes(int M, int N, int K) { return tcg_enabled() && M >= 128 && N >= 64 && K >= 1024; }
 bool tcg_nn_takes(int M, int N, int K) { return tcg_enabled() && M >= 4096 && N >= 64 && K >= 64; }
 
 size_t tcg_cn_work_bytes(int M, int N, int K) {
+    // the larger of the split-K and the stream-K partials (the autotuner
+    // may take either after the buffer is sized)
     const int mt = (M + GB_M - 1) / GB_M, nt = (N + GB_NC - 1) / GB_NC, total = (K + GB_KC - 1) / GB_KC;
-    return (size_t)mt * nt * cn_splits(mt * nt, total) * GB_NC * GB_M * sizeof(float2);
+    size_t split = 0;
+    for (int w : {3, 5, 8}) {
+        const int keep = g_waves_x2;
+        g_waves_x2 = w;
+        split = std::max(split, (size_t)mt * nt * cn_splits(mt * nt, total));
+        g_waves_x2 = keep;
+    }
+    const int ctas = sm_count();
+    const int64_t len = ((int64_t)mt * nt * total + ctas - 1) / ctas;
+    const size_t sk = (size_t)ctas * (size_t)((len + total - 1) / total + 1);
+    return std::max(split, sk) * GB_NC * GB_M * sizeof(float2);
 }
 
 size_t tcg_nn_work_bytes(int N, int K) {
@@ -630,7 +725,8 @@ bool gemm_cn_tcg(int M, int N, int K, const float2* A, int64_t lda, const float2
     if (!tcg_cn_takes(M, N, K)) return false;
     if ((lda & 1) || (ldb & 1) || !aligned(A, 16) || !aligned(B, 16) || !aligned(work, 16)) return false;
     const int mt = (M + GB_M - 1) / GB_M, nt = (N + GB_NC - 1) / GB_NC, total = (K + GB_KC - 1) / GB_KC;
-    const int ks = cn_splits(mt * nt, total);
+    const SkPlan sk = cn_stream_k(mt, nt, total);
+    const int ks = sk.ctas > 0 ? 1 : cn_splits(mt * nt, total);
     const int per = (total + ks - 1) / ks;
     if (tcg_cn_work_bytes(M, N, K) > work_bytes) return false;
     // (A^H B converts both operands in the kernel: a pre-split A, copied as
@@ -642,12 +738,21 @@ bool gemm_cn_tcg(int M, int N, int K, const float2* A, int64_t lda, const float2
     float2* part = static_cast<float2*>(work);
     roks::count_launch();
     g_tcg_launches += 1;
-    set_attr<false, false>();
-    k_tcgemm<false, false><<<dim3(mt, nt, ks), GB_THREADS, GbPlan<false, false>::SMEM, st>>>(
-        M, N, per, total, tmA, tmB, nullptr, nullptr, part, nullptr, 0, nullptr, 0, 0.f, 0.f, wait_polls());
+    if (sk.ctas > 0) {
+        set_attr<false, false, true>();
+        k_tcgemm<false, false, true><<<dim3(sk.ctas, 1, 1), GB_THREADS, GbPlan<false, false>::SMEM, st>>>(
+            M, N, per, total, sk, tmA, tmB, nullptr, nullptr, part, nullptr, 0, nullptr, 0, 0.f, 0.f, wait_polls());
+    } else {
+        set_attr<false, false>();
+        k_tcgemm<false, false><<<dim3(mt, nt, ks), GB_THREADS, GbPlan<false, false>::SMEM, st>>>(
+            M, N, per, total, sk, tmA, tmB, nullptr, nullptr, part, nullptr, 0, nullptr, 0, 0.f, 0.f, wait_polls());
+    }
     const int64_t outs = (int64_t)M * N;
     roks::count_launch();
-    k_tcg_reduce<<<(unsigned)((outs + 255) / 256), 256, 0, st>>>(M, N, mt, mt * nt, ks, part, C, ldc);
+    if (sk.ctas > 0)
+        k_tcg_reduce_sk<<<(unsigned)((outs + 255) / 256), 256, 0, st>>>(M, N, mt, total, sk, part, C, ldc);
+    else
+        k_tcg_reduce<<<(unsigned)((outs + 255) / 256), 256, 0, st>>>(M, N, mt, mt * nt, ks, part, C, ldc);
     return true;
 }
 
@@ -676,11 +781,13 @@ bool gemm_nn_tcg(int M, int N, int K, const float2* A, int64_t lda, const double
     if (as) {
         set_attr<true, true>();
         k_tcgemm<true, true><<<grid, GB_THREADS, GbPlan<true, true>::SMEM, st>>>(
-            M, N, total, total, tmA, tmA, bs, as, nullptr, Cin, ldcin, Cout, ldc, alpha, beta, wait_polls());
+            M, N, total, total, SkPlan{}, tmA, tmA, bs, as, nullptr, Cin, ldcin, Cout, ldc, alpha, beta,
+            wait_polls());
     } else {
         set_attr<true, false>();
         k_tcgemm<true, false><<<grid, GB_THREADS, GbPlan<true, false>::SMEM, st>>>(
-            M, N, total, total, tmA, tmA, bs, nullptr, nullptr, Cin, ldcin, Cout, ldc, alpha, beta, wait_polls());
+            M, N, total, total, SkPlan{}, tmA, tmA, bs, nullptr, nullptr, Cin, ldcin, Cout, ldc, alpha, beta,
+            wait_polls());
     }
     return true;
 }

@@ -35,7 +35,7 @@ struct roks_ctx {
     double L = 0, omega = 0, ecut = 0, alpha = 0, e_tol = 1e-6, g_tol = 0;
     int max_iter = 0, wait_cap = 0, exx_kernel = 0, autotune = 0;
     // launch shapes (the autotuner's choices, or the defaults)
-    int dens_groups = kDensityGroups, tc_waves_x2 = 5;
+    int dens_groups = kDensityGroups, tc_waves_x2 = 2;   // 2: stream-K A^H B
     double tune_ms[6] = {0, 0, 0, 0, 0, 0};
     uint64_t seed = 0;
     long long steps = 0;   // PCG and DIIS steps since the orbitals were last set
@@ -1113,7 +1113,8 @@ roks_status autotune(roks_ctx* ctx) {
     const int M = ctx->nproj >= ctx->nb ? ctx->nproj : ctx->nb;
     const void* A = ctx->nproj >= ctx->nb ? ctx->d_P : ctx->W_Y;
     if (ctx->prec == ROKS_MIXED && tcg_cn_takes(M, ctx->nb, ctx->npw)) {
-        const int w_cand[3] = {3, 5, 8};
+        // 2: stream-K over one wave; 5, 8: K split into 2.5 or 4 waves
+        const int w_cand[3] = {2, 5, 8};
         ctx->tc_waves_x2 = pick_fastest(ctx, w_cand, 3, ctx->tune_ms + 3, [&](int w) {
             tcg_set_waves(w);
             gemm_cn<float>(M, ctx->nb, ctx->npw, static_cast<const float2*>(A), ctx->ld_min,
