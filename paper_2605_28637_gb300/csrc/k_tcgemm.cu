@@ -79,7 +79,6 @@ constexpr uint32_t GB_PART = GB_M * GB_KR * 4;   // one split part (hi or lo) of
 constexpr uint32_t GB_SLOT = 4 * GB_PART;        // A hi | A lo | B hi | B lo
 constexpr uint32_t GB_RAWA = GB_M * GB_KC * 8;   // 16 KB
 constexpr uint32_t GB_RAWB = GB_NC * GB_KC * 8;  // 8 KB (CN)
-constexpr uint32_t GB_RAWS = GB_RAWA + GB_RAWB;
 constexpr uint32_t GB_TCOLS = GB_ACC * GB_NR;    // 512 columns
 constexpr uint32_t GB_DEFAULT_WAIT = 1u << 26;
 
@@ -152,14 +151,18 @@ struct GbPlan {
     static constexpr int LAG = CONVERT ? 2 : 0;                 // drain of stage i - LAG in iteration i
 };
 
-// Stream-K schedule of A^H B (ctas > 0): one CTA per SM, CTA c takes units
-// units * c / ctas .. units * (c + 1) / ctas - 1 of the (tile, stage)
-// sequence, stage fastest (tile t: M tile t % mt, N tile t / mt), and writes
-// the partial sums of each tile it touches to its segment slot c * maxseg +
-// (t - its first tile).  ctas = 0: split K over the grid's z.
+// CTA-loop schedules (the kernel's SK instance), one CTA per SM:
+// * A^H B, stream-K: CTA c takes units units * c / ctas .. units * (c + 1) /
+//   ctas - 1 of the (tile, stage) sequence, stage fastest (tile t: M tile
+//   t % fast, N tile t / fast), and writes the partial sums of each tile it
+//   touches to its segment slot c * maxseg + (t - its first tile);
+// * A B, persistent: units = tiles, CTA c takes the whole tiles c, c + ctas,
+//   ... (tile t: N tile t % fast, M tile t / fast), its pipeline running on
+//   across them, and writes each tile's result as it completes.
+// ctas = 0: one tile (and one K range) per CTA of a 3-D grid.
 struct SkPlan {
     int64_t units = 0;
-    int ctas = 0, maxseg = 0, mt = 0;
+    int ctas = 0, maxseg = 0, fast = 0;
 };
 
 template <bool NN, bool APRE, bool SK = false>
@@ -185,12 +188,13 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
     const int mi = NN ? blockIdx.y : blockIdx.x, ni = NN ? blockIdx.x : blockIdx.y;
     const int m0 = mi * GB_M, n0 = ni * GB_NC;
     const int s0 = NN ? 0 : blockIdx.z * stages_per_cta;
-    static_assert(!(SK && NN), "stream-K takes A^H B only");
-    const int64_t u0 = SK ? sk.units * blockIdx.x / sk.ctas : 0;
-    // stream-K: the first unit's tile and stage (the loops then step them)
-    const int t_first = SK ? (int)(u0 / total_stages) : 0;
-    const int s_first = SK ? (int)(u0 - (int64_t)t_first * total_stages) : 0;
-    const int ns = NN ? total_stages
+    const int64_t u0 = (SK && !NN) ? sk.units * blockIdx.x / sk.ctas : 0;
+    // CTA loop: the first tile and stage (the loops then step them); after a
+    // tile's last stage the next tile is t + tstep
+    const int t_first = SK ? (NN ? (int)blockIdx.x : (int)(u0 / total_stages)) : 0;
+    const int s_first = (SK && !NN) ? (int)(u0 - (int64_t)t_first * total_stages) : 0;
+    const int tstep = (SK && NN) ? sk.ctas : 1;
+    const int ns = NN ? (SK ? (int)((sk.units - blockIdx.x + sk.ctas - 1) / sk.ctas) * total_stages : total_stages)
                       : (SK ? (int)(sk.units * (blockIdx.x + 1) / sk.ctas - u0)
                             : max(0, min(total_stages, s0 + stages_per_cta) - s0));
 
@@ -224,6 +228,17 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
             int issued = 0, bissued = 0;
             int t_cur = t_first, s_cur = s_first;
             for (int i = 0; i < ns; ++i) {
+                // this stage's tile (M tile ma, N tile nb_) and K stage ks_
+                int ma = mi, nb_ = ni, ks_ = s0 + i;
+                if (SK) {
+                    ma = NN ? t_cur / sk.fast : t_cur % sk.fast;
+                    nb_ = NN ? t_cur % sk.fast : t_cur / sk.fast;
+                    ks_ = s_cur;
+                    if (++s_cur == total_stages) {
+                        s_cur = 0;
+                        t_cur += tstep;
+                    }
+                }
                 if (PL::RAW) {
                     const int rs = i % GB_RAW;
                     if (i >= GB_RAW && !gwait(&raw_empty[rs], (uint32_t)((i / GB_RAW - 1) & 1), wcap, &failed)) {
@@ -231,19 +246,10 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
                         break;
                     }
                     unsigned char* ra = raw + (size_t)rs * PL::RAWS;
-                    int k0 = (s0 + i) * GB_KC, am = m0, bn = n0;
-                    if (SK) {
-                        k0 = s_cur * GB_KC;
-                        am = (t_cur % sk.mt) * GB_M;
-                        bn = (t_cur / sk.mt) * GB_NC;
-                        if (++s_cur == total_stages) {
-                            s_cur = 0;
-                            ++t_cur;
-                        }
-                    }
+                    const int k0 = ks_ * GB_KC, am = ma * GB_M, bn = nb_ * GB_NC;
                     if (NN) {
                         tc::mbar_arrive_expect_tx(&raw_full[rs], GB_RAWA);
-                        tc::tma_2d(ra, &tmA, m0, k0, &raw_full[rs]);
+                        tc::tma_2d(ra, &tmA, am, k0, &raw_full[rs]);
                     } else {
                         tc::mbar_arrive_expect_tx(&raw_full[rs], PL::RAWA + PL::RAWB);
                         if (!APRE) tc::tma_2d(ra, &tmA, k0, am, &raw_full[rs]);
@@ -261,11 +267,11 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
                     unsigned char* sl = conv + (size_t)cs * GB_SLOT;
                     tc::mbar_arrive_expect_tx(&b_full[cs], PL::BULK_BYTES);
                     if (APRE)
-                        tc::bulk_g2s(sl, asplit + ((size_t)mi * total_stages + s0 + i) * (2 * GB_PART),
+                        tc::bulk_g2s(sl, asplit + ((size_t)ma * total_stages + ks_) * (2 * GB_PART),
                                      2 * GB_PART, &b_full[cs]);
                     if (NN)
                         tc::bulk_g2s(sl + 2 * GB_PART,
-                                     bsplit + ((size_t)ni * total_stages + i) * (2 * GB_PART), 2 * GB_PART,
+                                     bsplit + ((size_t)nb_ * total_stages + ks_) * (2 * GB_PART), 2 * GB_PART,
                                      &b_full[cs]);
                     bissued = i + 1;
                 }
@@ -337,8 +343,28 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
 #pragma unroll
         for (int j = 0; j < 16; ++j) re[j] = im[j] = 0.f;
         bool ok = true;
-        // stream-K: stages left in the current tile's segment, its index
-        int left = total_stages - s_first, seg = 0;
+        // CTA loop: stages left in the current tile's segment, its index,
+        // and its tile
+        int left = total_stages - s_first, seg = 0, t_drain = t_first;
+        // A B: this thread's row and 16 columns of the tile at (mo, no),
+        // times alpha, plus beta Cin
+        auto write_nn = [&](int mo, int no) {
+            const int m = mo + r;
+            if (m >= M) return;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int n = no + 16 * cg + j;
+                if (n < N) {
+                    float2 o = make_float2(alpha * re[j], alpha * im[j]);
+                    if (beta != 0.f) {
+                        const float2 ci = Cin[(int64_t)n * ldcin + m];
+                        o.x = fmaf(beta, ci.x, o.x);
+                        o.y = fmaf(beta, ci.y, o.y);
+                    }
+                    Cout[(int64_t)n * ldc + m] = o;
+                }
+            }
+        };
         for (int i = 0; i < ns + PL::LAG; ++i) {
             if (PL::CONVERT && i < ns) {
                 const int rs = i % GB_RAW, cs = i % SL;
@@ -407,41 +433,31 @@ __global__ void __launch_bounds__(GB_THREADS, 1)
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&acc_empty[b]);
                 if (SK) {
-                    // the last stage of a tile in this CTA's run: its partial
-                    // sums go to the segment slot, and the sums restart
+                    // the last stage of a tile in this CTA's run: its sums
+                    // go out (A B: the result; A^H B: the partial sums to
+                    // the segment slot), and the sums restart
                     if (--left == 0 || dsg == ns - 1) {
-                        float2* Pp = part + ((int64_t)blockIdx.x * sk.maxseg + seg) * GB_NC * GB_M;
+                        if (NN) {
+                            write_nn((t_drain / sk.fast) * GB_M, (t_drain % sk.fast) * GB_NC);
+                        } else {
+                            float2* Pp = part + ((int64_t)blockIdx.x * sk.maxseg + seg) * GB_NC * GB_M;
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            Pp[(int64_t)(16 * cg + j) * GB_M + r] = make_float2(re[j], im[j]);
-                            re[j] = im[j] = 0.f;
+                            for (int j = 0; j < 16; ++j) Pp[(int64_t)(16 * cg + j) * GB_M + r] = make_float2(re[j], im[j]);
                         }
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) re[j] = im[j] = 0.f;
                         ++seg;
+                        t_drain += tstep;
                         left = total_stages;
                     }
                 }
             }
         }
         if (!ok) give_up(&failed);
-        if (ok) {
+        if (ok && !SK) {
             if (NN) {
-                const int m = m0 + r;
-                if (m < M) {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int n = n0 + 16 * cg + j;
-                        if (n < N) {
-                            float2 o = make_float2(alpha * re[j], alpha * im[j]);
-                            if (beta != 0.f) {
-                                const float2 ci = Cin[(int64_t)n * ldcin + m];
-                                o.x = fmaf(beta, ci.x, o.x);
-                                o.y = fmaf(beta, ci.y, o.y);
-                            }
-                            Cout[(int64_t)n * ldc + m] = o;
-                        }
-                    }
-                }
-            } else if (!SK) {
+                write_nn(m0, n0);
+            } else {
                 const int tile = blockIdx.x + blockIdx.y * gridDim.x;
                 const int tiles = gridDim.x * gridDim.y;
                 float2* P = part + ((int64_t)blockIdx.z * tiles + tile) * GB_NC * GB_M;
@@ -632,7 +648,7 @@ SkPlan cn_stream_k(int mt, int nt, int total) {
     SkPlan p;
     if (g_waves_x2 != 2) return p;
     p.ctas = sm_count();
-    p.mt = mt;
+    p.fast = mt;
     p.units = (int64_t)mt * nt * total;
     const int64_t len = (p.units + p.ctas - 1) / p.ctas;
     p.maxseg = (int)((len + total - 1) / total) + 1;
@@ -778,6 +794,30 @@ bool gemm_nn_tcg(int M, int N, int K, const float2* A, int64_t lda, const double
     g_tcg_launches += 1;
     const int mt = (M + GB_M - 1) / GB_M;
     const dim3 grid(nt, mt, 1);
+    // more tiles than SMs: persistent CTAs, one per SM, each looping over
+    // whole tiles (tile t: N tile t % nt, M tile t / nt) with its pipeline
+    // running on across them
+    SkPlan pp;
+    if ((int64_t)mt * nt > sm_count()) {
+        pp.ctas = sm_count();
+        pp.units = (int64_t)mt * nt;
+        pp.fast = nt;
+    }
+    if (pp.ctas > 0) {
+        const dim3 g1(pp.ctas, 1, 1);
+        if (as) {
+            set_attr<true, true, true>();
+            k_tcgemm<true, true, true><<<g1, GB_THREADS, GbPlan<true, true>::SMEM, st>>>(
+                M, N, total, total, pp, tmA, tmA, bs, as, nullptr, Cin, ldcin, Cout, ldc, alpha, beta,
+                wait_polls());
+        } else {
+            set_attr<true, false, true>();
+            k_tcgemm<true, false, true><<<g1, GB_THREADS, GbPlan<true, false>::SMEM, st>>>(
+                M, N, total, total, pp, tmA, tmA, bs, nullptr, nullptr, Cin, ldcin, Cout, ldc, alpha, beta,
+                wait_polls());
+        }
+        return true;
+    }
     if (as) {
         set_attr<true, true>();
         k_tcgemm<true, true><<<grid, GB_THREADS, GbPlan<true, true>::SMEM, st>>>(
