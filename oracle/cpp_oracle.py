@@ -72,6 +72,10 @@ class CppSystem:
     """One model system in the C++ oracle (see oracle.roks.System for the model)."""
 
     def __init__(self, cfg: dict, threads: int = 0):
+        # the C++ oracle restates the Slater-exchange model without empty
+        # bands (the baseline's workloads); the rest stays in oracle.roks
+        if int(cfg.get("n_empty", 0)) or cfg.get("xc", "slater") != "slater":
+            raise ValueError("the C++ oracle takes occupied bands and Slater exchange only")
         lib = load()
         self.cfg = cfg
         self.N = int(cfg["grid"])

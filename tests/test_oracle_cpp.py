@@ -60,3 +60,10 @@ def test_cpp_oracle_rejects_a_small_grid():
     cfg = syn.with_changes(syn.make_config("tiny-16", 0), ecut=40.0)
     with pytest.raises(ValueError):
         CO.CppSystem(cfg)
+
+
+@pytest.mark.parametrize("change", [dict(n_empty=2), dict(xc="pbe_x")])
+def test_cpp_oracle_refuses_what_it_does_not_model(change):
+    cfg = syn.with_changes(syn.make_config("tiny-16", 0), **change)
+    with pytest.raises(ValueError):
+        CO.CppSystem(cfg)
