@@ -130,7 +130,7 @@ def _rocksalt(a: float, reps: int):
 
 
 def make_config(name: str, seed: int = 0) -> dict:
-    """One of the four model workloads, with seeded random parts."""
+    """One of the model workloads, with seeded random parts."""
     st = _Stream(seed * 0x100000001 + 0x5EED)
     if name == "tiny-16":
         L, N, ecut = 10.0, 16, 8.0
@@ -152,15 +152,17 @@ def make_config(name: str, seed: int = 0) -> dict:
             else:
                 atoms.append({"pos": p, "species": 1, "depth": 1.0, "width": 1.0})
         n_closed, alpha = 40, 0.0
-    elif name in ("mgo-120", "hybrid-72", "mgo-72"):
-        reps = 3 if name == "mgo-120" else 2
+    elif name in ("mgo-120", "hybrid-72", "mgo-72", "mgo-32"):
+        # the rocksalt cell with an O vacancy; mgo-32 is its single cell (7
+        # atoms), the small system of the same shape for training and tests
+        reps = {"mgo-120": 3, "mgo-32": 1}.get(name, 2)
         L, mg, ox = _rocksalt(7.96, reps)
-        N = 120 if reps == 3 else 72
+        N = {3: 120, 2: 72, 1: 32}[reps]
         ecut = 15.0
         sp = [_species(st, [0.8], [0.8]), _species(st, [0.8, 1.2], [0.8, 1.2])]
         atoms = [{"pos": tuple(map(float, r)), "species": 0, "depth": 1.0, "width": 1.0} for r in mg]
         atoms += [{"pos": tuple(map(float, r)), "species": 1, "depth": 3.0, "width": 1.0} for r in ox]
-        n_closed = 428 if reps == 3 else 126
+        n_closed = {3: 428, 2: 126, 1: 14}[reps]
         alpha = 1.0 / 3.0 if name == "hybrid-72" else 0.0
     else:
         raise ValueError(f"unknown workload {name!r}")
