@@ -97,6 +97,21 @@ __host__ __device__ constexpr bool plan_ok(int n) {
     return m == 1;
 }
 
+// Sphere pruning of the first pass.  When only the frequencies |i| <= nb of
+// a line are nonzero, input r of every butterfly of the first pass (element
+// j + r S of the line, S = N / R0 for the pass's radix R0, j < S) is zero for
+// nb / S < r <= (N - nb) / S - 1.  The kernels prune for
+// nb = sphere_prune_nmax(N) = (N - 1) / 4, which covers every sphere whose
+// density fits the grid without aliasing (N >= 4 nmax + 1); a larger sphere
+// takes the full first pass.
+__host__ __device__ constexpr int sphere_prune_nmax(int n) { return (n - 1) / 4; }
+__host__ __device__ constexpr unsigned sphere_zero_mask(int n) {
+    const int r0 = plan_radix(n, 0), S = n / r0, nb = sphere_prune_nmax(n);
+    unsigned m = 0;
+    for (int r = nb / S + 1; r <= (n - nb) / S - 1 && r < r0; ++r) m |= 1u << r;
+    return m;
+}
+
 // ---------------------------------------------------------------- compile-time trigonometry
 // cos and sin of 2 pi m / R from their Taylor series (argument reduced to
 // [-pi, pi]; 30 terms give full double precision there).  Used only to fold
@@ -258,24 +273,212 @@ template <int DIR, typename V> struct Dft<12, DIR, V> : DftAB<4, 3, DIR, V> {};
 template <int DIR, typename V> struct Dft<15, DIR, V> : DftAB<5, 3, DIR, V> {};
 template <int DIR, typename V> struct Dft<16, DIR, V> : DftAB<4, 4, DIR, V> {};
 
+// ---------------------------------------------------------------- pruned codelets
+// The same DFTs when some inputs are known at compile time to be zero (bit n
+// of Z: input n is zero and holds 0).  Additions with a known zero are left
+// out; Z = 0 is the plain codelet.  The first pass of an inverse x transform
+// uses them: x planes outside the sphere are zero for every butterfly.
+template <bool ZA, bool ZB, typename V>
+__host__ __device__ __forceinline__ V zadd(V a, V b) {
+    if constexpr (ZB) return a;          // also a = b = 0
+    else if constexpr (ZA) return b;
+    else return cadd(a, b);
+}
+template <bool ZA, bool ZB, typename V>
+__host__ __device__ __forceinline__ V zsub(V a, V b) {
+    if constexpr (ZB) return a;
+    else if constexpr (ZA) { V r; r.x = -b.x; r.y = -b.y; return r; }
+    else return csub(a, b);
+}
+
+template <int R, int DIR, typename V, unsigned Z> struct DftZ {
+    static_assert(Z == 0, "no pruned codelet for this radix");
+    __host__ __device__ static __forceinline__ void run(V* v) { Dft<R, DIR, V>::run(v); }
+};
+
+template <int DIR, typename V, unsigned Z> struct DftZ<2, DIR, V, Z> {
+    __host__ __device__ static __forceinline__ void run(V* v) {
+        constexpr bool z0 = Z & 1u, z1 = Z & 2u;
+        V a = zadd<z0, z1>(v[0], v[1]), b = zsub<z0, z1>(v[0], v[1]);
+        v[0] = a; v[1] = b;
+    }
+};
+
+template <int DIR, typename V, unsigned Z> struct DftZ<3, DIR, V, Z> {
+    __host__ __device__ static __forceinline__ void run(V* v) {
+        if constexpr (Z == 0) {
+            Dft<3, DIR, V>::run(v);
+        } else {
+            static_assert(!(Z & 1u), "input 0 of a pruned 3-point codelet is not zero");
+            using T = decltype(v[0].x);
+            constexpr bool z1 = Z & 2u, z2 = Z & 4u;
+            if constexpr (z1 && z2) {
+                v[1] = v[0]; v[2] = v[0];
+            } else {
+                const T h = T(0.86602540378443864676);
+                V t = zadd<z1, z2>(v[1], v[2]);
+                V u = mul_i<DIR>(cscale(zsub<z1, z2>(v[1], v[2]), h));
+                V m = csub(v[0], cscale(t, T(0.5)));
+                v[0] = cadd(v[0], t);
+                v[1] = cadd(m, u);
+                v[2] = csub(m, u);
+            }
+        }
+    }
+};
+
+template <int DIR, typename V, unsigned Z> struct DftZ<4, DIR, V, Z> {
+    __host__ __device__ static __forceinline__ void run(V* v) {
+        if constexpr (Z == 0) {
+            Dft<4, DIR, V>::run(v);
+        } else {
+            constexpr bool z0 = Z & 1u, z1 = Z & 2u, z2 = Z & 4u, z3 = Z & 8u;
+            constexpr bool ze = z0 && z2, zo = z1 && z3;
+            V t0 = zadd<z0, z2>(v[0], v[2]), t1 = zsub<z0, z2>(v[0], v[2]);
+            V t2 = zadd<z1, z3>(v[1], v[3]), t3 = mul_i<DIR>(zsub<z1, z3>(v[1], v[3]));
+            v[0] = zadd<ze, zo>(t0, t2); v[2] = zsub<ze, zo>(t0, t2);
+            v[1] = zadd<ze, zo>(t1, t3); v[3] = zsub<ze, zo>(t1, t3);
+        }
+    }
+};
+
+template <int DIR, typename V, unsigned Z> struct DftZ<5, DIR, V, Z> {
+    __host__ __device__ static __forceinline__ void run(V* v) {
+        if constexpr (Z == 0) {
+            Dft<5, DIR, V>::run(v);
+        } else {
+            static_assert(!(Z & 1u), "input 0 of a pruned 5-point codelet is not zero");
+            using T = decltype(v[0].x);
+            const T c1 = T(0.30901699437494742410);   // cos(2 pi / 5)
+            const T c2 = T(-0.80901699437494742410);  // cos(4 pi / 5)
+            const T s1 = T(0.95105651629515357212);   // sin(2 pi / 5)
+            const T s2 = T(0.58778525229247312917);   // sin(4 pi / 5)
+            constexpr bool z1 = Z & 2u, z2 = Z & 4u, z3 = Z & 8u, z4 = Z & 16u;
+            constexpr bool p1 = !(z1 && z4), p2 = !(z2 && z3);   // pair (1, 4) and pair (2, 3) present
+            V t1 = zadd<z1, z4>(v[1], v[4]), t2 = zadd<z2, z3>(v[2], v[3]);
+            V u1 = zsub<z1, z4>(v[1], v[4]), u2 = zsub<z2, z3>(v[2], v[3]);
+            if constexpr (!p1 && !p2) {
+                v[1] = v[0]; v[2] = v[0]; v[3] = v[0]; v[4] = v[0];
+            } else {
+                V a1, a2, b1, b2, s0;
+                if constexpr (p1 && p2) {
+                    a1 = cadd(v[0], cadd(cscale(t1, c1), cscale(t2, c2)));
+                    a2 = cadd(v[0], cadd(cscale(t1, c2), cscale(t2, c1)));
+                    b1 = cadd(cscale(u1, s1), cscale(u2, s2));
+                    b2 = csub(cscale(u1, s2), cscale(u2, s1));
+                    s0 = cadd(v[0], cadd(t1, t2));
+                } else if constexpr (p1) {
+                    a1 = cadd(v[0], cscale(t1, c1));
+                    a2 = cadd(v[0], cscale(t1, c2));
+                    b1 = cscale(u1, s1);
+                    b2 = cscale(u1, s2);
+                    s0 = cadd(v[0], t1);
+                } else {
+                    a1 = cadd(v[0], cscale(t2, c2));
+                    a2 = cadd(v[0], cscale(t2, c1));
+                    b1 = cscale(u2, s2);
+                    b2 = cscale(u2, -s1);
+                    s0 = cadd(v[0], t2);
+                }
+                b1 = mul_i<DIR>(b1);
+                b2 = mul_i<DIR>(b2);
+                v[0] = s0;
+                v[1] = cadd(a1, b1); v[4] = csub(a1, b1);
+                v[2] = cadd(a2, b2); v[3] = csub(a2, b2);
+            }
+        }
+    }
+};
+
+template <int DIR, typename V, unsigned Z> struct DftZ<8, DIR, V, Z> {
+    __host__ __device__ static __forceinline__ void run(V* v) {
+        if constexpr (Z == 0) {
+            Dft<8, DIR, V>::run(v);
+        } else {
+            using T = decltype(v[0].x);
+            const T r2 = T(0.70710678118654752440);
+            // even inputs 0, 2, 4, 6 and odd inputs 1, 3, 5, 7
+            constexpr unsigned ZE = (Z & 1u) | ((Z >> 1) & 2u) | ((Z >> 2) & 4u) | ((Z >> 3) & 8u);
+            constexpr unsigned ZO = ((Z >> 1) & 1u) | ((Z >> 2) & 2u) | ((Z >> 3) & 4u) | ((Z >> 4) & 8u);
+            static_assert(ZE != 15u && ZO != 15u, "a pruned 8-point codelet keeps even and odd inputs");
+            V e[4] = {v[0], v[2], v[4], v[6]};
+            V o[4] = {v[1], v[3], v[5], v[7]};
+            DftZ<4, DIR, V, ZE>::run(e);
+            DftZ<4, DIR, V, ZO>::run(o);
+            V w1 = cscale(cadd(o[1], mul_i<DIR>(o[1])), r2);
+            V w2 = mul_i<DIR>(o[2]);
+            V w3 = cscale(csub(mul_i<DIR>(o[3]), o[3]), r2);
+            v[0] = cadd(e[0], o[0]); v[4] = csub(e[0], o[0]);
+            v[1] = cadd(e[1], w1);   v[5] = csub(e[1], w1);
+            v[2] = cadd(e[2], w2);   v[6] = csub(e[2], w2);
+            v[3] = cadd(e[3], w3);   v[7] = csub(e[3], w3);
+        }
+    }
+};
+
+// Composite A * B with known-zero inputs: each A-point DFT over n1 (inputs
+// B n1 + n2) drops the zeros of its own group.  No group may be all zero.
+template <int A, int B, int DIR, typename V, unsigned Z>
+struct DftABZ {
+    template <int N2>
+    __host__ __device__ static constexpr unsigned group_mask() {
+        unsigned m = 0;
+        for (int n1 = 0; n1 < A; ++n1)
+            if (Z & (1u << (B * n1 + N2))) m |= 1u << n1;
+        return m;
+    }
+    __host__ __device__ static __forceinline__ void run(V* v) {
+        constexpr int R = A * B;
+        V y[B][A];
+        sfor<B>([&](auto n2c) {
+            constexpr int n2 = decltype(n2c)::value;
+            constexpr unsigned G = group_mask<n2>();
+            static_assert(G != (1u << A) - 1u, "a pruned composite codelet keeps every input group");
+            V t[A];
+            sfor<A>([&](auto n1c) { t[decltype(n1c)::value] = v[B * decltype(n1c)::value + n2]; });
+            DftZ<A, DIR, V, G>::run(t);
+            sfor<A>([&](auto k1c) {
+                constexpr int k1 = decltype(k1c)::value;
+                y[n2][k1] = twiddle_const<R, n2 * k1, DIR>(t[k1]);
+            });
+        });
+        sfor<A>([&](auto k1c) {
+            constexpr int k1 = decltype(k1c)::value;
+            V t[B];
+            sfor<B>([&](auto n2c) { t[decltype(n2c)::value] = y[decltype(n2c)::value][k1]; });
+            Dft<B, DIR, V>::run(t);
+            sfor<B>([&](auto k2c) { v[k1 + A * decltype(k2c)::value] = t[decltype(k2c)::value]; });
+        });
+    }
+};
+
+template <int DIR, typename V, unsigned Z> struct DftZ<6, DIR, V, Z> : DftABZ<3, 2, DIR, V, Z> {};
+template <int DIR, typename V, unsigned Z> struct DftZ<9, DIR, V, Z> : DftABZ<3, 3, DIR, V, Z> {};
+template <int DIR, typename V, unsigned Z> struct DftZ<10, DIR, V, Z> : DftABZ<5, 2, DIR, V, Z> {};
+template <int DIR, typename V, unsigned Z> struct DftZ<12, DIR, V, Z> : DftABZ<4, 3, DIR, V, Z> {};
+template <int DIR, typename V, unsigned Z> struct DftZ<15, DIR, V, Z> : DftABZ<5, 3, DIR, V, Z> {};
+template <int DIR, typename V, unsigned Z> struct DftZ<16, DIR, V, Z> : DftABZ<4, 4, DIR, V, Z> {};
+
 // ---------------------------------------------------------------- Stockham
 // One pass of radix R with Ns = NS over all TL lines of a tile, in place.
 // tw[t] = exp(-2 pi i t / N); the inverse (DIR = +1) uses its conjugate.
 // Butterfly b of a line reads elements b + r N/R and writes
 // (b / NS) NS R + (b mod NS) + r NS.
-template <typename V, int N, int R, int NS, int DIR>
+// Z: inputs known to be zero (pruned codelet; their twiddles are skipped).
+template <typename V, int N, int R, int NS, int DIR, unsigned Z = 0>
 __host__ __device__ __forceinline__ void twiddle_dft(V* v, const V* tw, int j) {
     const int k = j % NS;
     if (NS > 1) {
 #pragma unroll
         for (int r = 1; r < R; ++r) {
+            if ((Z >> r) & 1u) continue;
             const int t = r * k * (N / (NS * R));
             V w = tw[t];
             if (DIR > 0) w.y = -w.y;
             v[r] = cmul(v[r], w);
         }
     }
-    Dft<R, DIR, V>::run(v);
+    DftZ<R, DIR, V, Z>::run(v);
 }
 
 #ifdef __CUDACC__
@@ -331,7 +534,9 @@ __device__ __forceinline__ void tile_fft(V* buf, const V* tw) {
 // identify the register slot, the same for every call with the same tile
 // shape).  SYNC waits between the reads and the writes (needed when both go
 // to the same shared tile).
-template <typename V, int N, int P, int DIR, int TL, int NT, bool SYNC, class Ld, class St>
+// Z: inputs of the pass's codelet known to be zero for every butterfly; they
+// are neither loaded nor added.
+template <typename V, int N, int P, int DIR, int TL, int NT, bool SYNC, unsigned Z = 0, class Ld, class St>
 __device__ __forceinline__ void pass_io(const V* tw, Ld&& ld, St&& st) {
     constexpr int R = plan_radix(N, P);
     constexpr int NS = plan_ns(N, P);
@@ -346,7 +551,14 @@ __device__ __forceinline__ void pass_io(const V* tw, Ld&& ld, St&& st) {
         if (beta < TOT) {
             const int line = beta % TL, j = beta / TL;
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[q][r] = ld(line, j + r * NBF);
+            for (int r = 0; r < R; ++r) {
+                if ((Z >> r) & 1u) {
+                    v[q][r].x = 0;
+                    v[q][r].y = 0;
+                } else {
+                    v[q][r] = ld(line, j + r * NBF);
+                }
+            }
         }
     }
     if constexpr (SYNC) __syncthreads();
@@ -355,7 +567,7 @@ __device__ __forceinline__ void pass_io(const V* tw, Ld&& ld, St&& st) {
         const int beta = tid + q * NT;
         if (beta < TOT) {
             const int line = beta % TL, j = beta / TL;
-            twiddle_dft<V, N, R, NS, DIR>(v[q], tw, j);
+            twiddle_dft<V, N, R, NS, DIR, Z>(v[q], tw, j);
             const int base = (j / NS) * NS * R + (j % NS);
 #pragma unroll
             for (int r = 0; r < R; ++r) st(line, base + r * NS, v[q][r], q, r);
@@ -375,17 +587,19 @@ __device__ __forceinline__ void middle_passes(V* buf, const V* tw, Sl& sl, Ss& s
 // Full transform of TL lines whose first pass reads through ld and whose last
 // pass writes through st; the passes in between use the shared tile buf.
 // FIRST_SMEM: ld reads buf (the caller has synchronised).  LAST_SMEM: st
-// writes buf (the caller synchronises before reading it).
-template <typename V, int N, int DIR, int TL, int LS, int NT, bool FIRST_SMEM, bool LAST_SMEM, class Ld, class St>
+// writes buf (the caller synchronises before reading it).  Z0: inputs of the
+// first pass's codelet that are zero for every butterfly (sphere_zero_mask).
+template <typename V, int N, int DIR, int TL, int LS, int NT, bool FIRST_SMEM, bool LAST_SMEM, unsigned Z0 = 0,
+          class Ld, class St>
 __device__ __forceinline__ void fft_io(V* buf, const V* tw, Ld&& ld, St&& st) {
     static_assert(plan_ok(N), "unsupported transform length");
     constexpr int NP = plan_passes(N);
     auto sl = [&](int line, int e) { return buf[e * LS + line]; };
     auto ss = [&](int line, int e, V v, int, int) { buf[e * LS + line] = v; };
     if constexpr (NP == 1) {
-        pass_io<V, N, 0, DIR, TL, NT, FIRST_SMEM || LAST_SMEM>(tw, ld, st);
+        pass_io<V, N, 0, DIR, TL, NT, FIRST_SMEM || LAST_SMEM, Z0>(tw, ld, st);
     } else {
-        pass_io<V, N, 0, DIR, TL, NT, FIRST_SMEM>(tw, ld, ss);
+        pass_io<V, N, 0, DIR, TL, NT, FIRST_SMEM, Z0>(tw, ld, ss);
         __syncthreads();
         middle_passes<V, N, DIR, TL, LS, NT, 1>(buf, tw, sl, ss);
         pass_io<V, N, NP - 1, DIR, TL, NT, LAST_SMEM>(tw, sl, st);
@@ -413,22 +627,28 @@ struct LastPassSlots {
 
 // The same pass sequence on one line, on the host: tests/cpp/fft_passes.cu
 // runs it for every compiled length against the DFT sum.
-template <typename V, int N, int DIR, int P>
+// Z0: the first pass's known-zero inputs (sphere_zero_mask), not read.
+template <typename V, int N, int DIR, int P, unsigned Z0 = 0>
 __host__ void host_passes(V* line, const V* tw) {
     if constexpr (P < plan_passes(N)) {
         constexpr int R = plan_radix(N, P);
         constexpr int NS = plan_ns(N, P);
         constexpr int NBF = N / R;
+        constexpr unsigned Z = P == 0 ? Z0 : 0u;
         V out[N];
         for (int j = 0; j < NBF; ++j) {
             V v[R];
-            for (int r = 0; r < R; ++r) v[r] = line[j + r * NBF];
-            twiddle_dft<V, N, R, NS, DIR>(v, tw, j);
+            for (int r = 0; r < R; ++r) {
+                v[r].x = 0;
+                v[r].y = 0;
+                if (!((Z >> r) & 1u)) v[r] = line[j + r * NBF];
+            }
+            twiddle_dft<V, N, R, NS, DIR, Z>(v, tw, j);
             const int base = (j / NS) * NS * R + (j % NS);
             for (int r = 0; r < R; ++r) out[base + r * NS] = v[r];
         }
         for (int e = 0; e < N; ++e) line[e] = out[e];
-        host_passes<V, N, DIR, P + 1>(line, tw);
+        host_passes<V, N, DIR, P + 1, Z0>(line, tw);
     }
 }
 

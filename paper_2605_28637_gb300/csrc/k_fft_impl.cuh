@@ -142,7 +142,10 @@ __global__ void __launch_bounds__(kThreads) k_band_z_fwd(Sphere s, const c2<T>* 
 }
 
 // ------------------------------------------------------------------ y stage
-template <typename T, int N>
+// PRUNE (y_inv and the inverse x stages): the sphere's frequencies lie within
+// |i|, |j| <= sphere_prune_nmax(N), so the first pass leaves out the inputs
+// that are zero for every butterfly (sphere_zero_mask).
+template <typename T, int N, bool PRUNE>
 __global__ void __launch_bounds__(kThreads) k_band_y_inv(Sphere s, const c2<T>* __restrict__ tw,
                                                          const c2<T>* __restrict__ Zc,
                                                          c2<T>* __restrict__ Yp) {
@@ -159,7 +162,7 @@ __global__ void __launch_bounds__(kThreads) k_band_y_inv(Sphere s, const c2<T>* 
     const int jm = s.plane_jmax[p];
     const V* in = Zc + ((int64_t)bb * s.ncol + s.plane_col0[p] + jm) * N;
     V* out = Yp + ((int64_t)bb * s.np + p) * N * N;
-    fft_io<V, N, +1, TL, LS, kThreads, false, false>(
+    fft_io<V, N, +1, TL, LS, kThreads, false, false, PRUNE ? sphere_zero_mask(N) : 0u>(
         buf, tws,
         [&](int line, int e) {
             const int z = z0 + line, j = signed_freq(e, N);
@@ -217,7 +220,7 @@ __device__ __forceinline__ void load_x_lines(const Sphere& s, c2<T>* buf, const 
 // SPLIT: every band of the launch holds two real orbitals as (re, im) with
 // the classes a and b (the Gamma-point packing of the open pair): re is
 // multiplied by V^a, im by V^b.
-template <typename T, int N, bool SPLIT>
+template <typename T, int N, bool SPLIT, bool PRUNE>
 __global__ void __launch_bounds__(x_threads(N)) k_band_x_apply(Sphere s, const c2<T>* __restrict__ tw,
                                                                c2<T>* __restrict__ Yp,
                                                                const T* __restrict__ Vk,
@@ -245,7 +248,7 @@ __global__ void __launch_bounds__(x_threads(N)) k_band_x_apply(Sphere s, const c
     constexpr int NN = N * N;
     // inverse x transform; the last pass forms (V psi + X) * scale in the tile,
     // X being the exchange field of the band (absent without exact exchange)
-    fft_io<V, N, +1, TL, LS, NT, false, true>(
+    fft_io<V, N, +1, TL, LS, NT, false, true, PRUNE ? sphere_zero_mask(N) : 0u>(
         buf, tws,
         [&](int line, int e) {
             const int i = signed_freq(e, N);
@@ -277,7 +280,7 @@ __global__ void __launch_bounds__(x_threads(N)) k_band_x_apply(Sphere s, const c
 
 // Real-space orbitals on the full grid: Phi[b] = scale * inverse x transform
 // of the plane data (used by the exact-exchange pair densities).
-template <typename T, int N>
+template <typename T, int N, bool PRUNE>
 __global__ void __launch_bounds__(kThreads) k_band_x_inv_full(Sphere s, const c2<T>* __restrict__ tw,
                                                               const c2<T>* __restrict__ Yp,
                                                               c2<T>* __restrict__ Phi, int b0, T scale) {
@@ -294,7 +297,7 @@ __global__ void __launch_bounds__(kThreads) k_band_x_inv_full(Sphere s, const c2
     const V* Ypb = Yp + (int64_t)bb * s.np * N * N;
     V* out = Phi + (int64_t)(b0 + bb) * N * N * N;
     const int nmax = s.nmax;
-    fft_io<V, N, +1, TL, LS, kThreads, false, false>(
+    fft_io<V, N, +1, TL, LS, kThreads, false, false, PRUNE ? sphere_zero_mask(N) : 0u>(
         buf, tws,
         [&](int line, int e) {
             const int z = z0 + line, i = signed_freq(e, N);
@@ -318,7 +321,7 @@ __global__ void __launch_bounds__(kThreads) k_band_x_inv_full(Sphere s, const c2
 // the rows of the planes outside the sphere (and the lines past N of the
 // last z tile) are zeroed once, so the first pass loads without tests.
 // SEL: (Re psi)^2 (part_sel 1) or (Im psi)^2 (part_sel 2) instead of |psi|^2.
-template <typename T, int N, bool SEL>
+template <typename T, int N, bool SEL, bool PRUNE>
 __global__ void __launch_bounds__(kThreads) k_band_x_density(Sphere s, const c2<T>* __restrict__ tw,
                                                              const c2<T>* __restrict__ Yp,
                                                              typename DensAcc<T>::S* __restrict__ rho3,
@@ -389,7 +392,7 @@ __global__ void __launch_bounds__(kThreads) k_band_x_density(Sphere s, const c2<
                 }
                 __syncthreads();
                 const V* sb = stg + ((bb - gbeg) & 1) * N * TL;
-                fft_io<V, N, +1, TL, LS, kThreads, false, false>(
+                fft_io<V, N, +1, TL, LS, kThreads, false, false, PRUNE ? sphere_zero_mask(N) : 0u>(
                     buf, tws, [&](int line, int e) { return sb[e * TL + line]; },
                     [&](int, int, V v, int q, int r) {
                         if constexpr (SEL)
@@ -515,27 +518,35 @@ struct BandFft {
         dim3 gz((s.ncol + TLZ - 1) / TLZ, nbb);
         roks::count_launch(), k_band_z_inv<T, N><<<gz, kThreads, SMZ, st>>>(s, tw, psi, ld, b0, Zc);
     }
+    // the sphere fits the pruned first passes
+    static bool prune(const Sphere& s) { return s.nmax <= sphere_prune_nmax(N); }
     static void y_inv(const Sphere& s, const V* tw, const V* Zc, V* Yp, int nbb, cudaStream_t st) {
-        set_smem(k_band_y_inv<T, N>, SM);
         dim3 gy((N + TL - 1) / TL, s.np, nbb);
-        roks::count_launch(), k_band_y_inv<T, N><<<gy, kThreads, SM, st>>>(s, tw, Zc, Yp);
+        if (prune(s)) {
+            set_smem(k_band_y_inv<T, N, true>, SM);
+            roks::count_launch(), k_band_y_inv<T, N, true><<<gy, kThreads, SM, st>>>(s, tw, Zc, Yp);
+        } else {
+            set_smem(k_band_y_inv<T, N, false>, SM);
+            roks::count_launch(), k_band_y_inv<T, N, false><<<gy, kThreads, SM, st>>>(s, tw, Zc, Yp);
+        }
     }
     // split_band (if within the launch) takes the SPLIT instance, alone
     static void x_apply(const Sphere& s, const V* tw, V* Yp, const T* Vk, const V* Xx, int b0, int nbb, int nc,
                         int split_band, T scale, cudaStream_t st) {
-        set_smem(k_band_x_apply<T, N, false>, SM);
-        set_smem(k_band_x_apply<T, N, true>, SM);
+        const bool pr = prune(s);
         auto run = [&](bool split, int first, int count) {
             if (count <= 0) return;
             // the kernel indexes the planes from the launch's first band
             V* Y = Yp + (int64_t)(first - b0) * s.np * N * N;
             dim3 g((N + TL - 1) / TL, N, count);
+            auto go = [&](auto kernel) {
+                set_smem(kernel, SM);
+                roks::count_launch(), kernel<<<g, x_threads(N), SM, st>>>(s, tw, Y, Vk, Xx, first, nc, scale);
+            };
             if (split)
-                roks::count_launch(),
-                    k_band_x_apply<T, N, true><<<g, x_threads(N), SM, st>>>(s, tw, Y, Vk, Xx, first, nc, scale);
+                pr ? go(k_band_x_apply<T, N, true, true>) : go(k_band_x_apply<T, N, true, false>);
             else
-                roks::count_launch(),
-                    k_band_x_apply<T, N, false><<<g, x_threads(N), SM, st>>>(s, tw, Y, Vk, Xx, first, nc, scale);
+                pr ? go(k_band_x_apply<T, N, false, true>) : go(k_band_x_apply<T, N, false, false>);
         };
         if (split_band < b0 || split_band >= b0 + nbb) {
             run(false, b0, nbb);
@@ -547,9 +558,14 @@ struct BandFft {
     }
     static void x_inv_full(const Sphere& s, const V* tw, const V* Yp, V* Phi, int b0, int nbb, T scale,
                            cudaStream_t st) {
-        set_smem(k_band_x_inv_full<T, N>, SM);
         dim3 g((N + TL - 1) / TL, N, nbb);
-        roks::count_launch(), k_band_x_inv_full<T, N><<<g, kThreads, SM, st>>>(s, tw, Yp, Phi, b0, scale);
+        if (prune(s)) {
+            set_smem(k_band_x_inv_full<T, N, true>, SM);
+            roks::count_launch(), k_band_x_inv_full<T, N, true><<<g, kThreads, SM, st>>>(s, tw, Yp, Phi, b0, scale);
+        } else {
+            set_smem(k_band_x_inv_full<T, N, false>, SM);
+            roks::count_launch(), k_band_x_inv_full<T, N, false><<<g, kThreads, SM, st>>>(s, tw, Yp, Phi, b0, scale);
+        }
     }
     static void y_fwd(const Sphere& s, const V* tw, const V* Yp, V* Zc, int nbb, cudaStream_t st) {
         set_smem(k_band_y_fwd<T, N>, SM);
@@ -576,20 +592,22 @@ struct BandFft {
                           cudaStream_t st) {
         // tile, twiddles and two staging buffers of N x TL
         const size_t sm = SM + 2 * sizeof(V) * (size_t)N * TL;
-        set_smem(k_band_x_density<T, N, false>, sm);
-        set_smem(k_band_x_density<T, N, true>, sm);
         const int gs = (nbb + ngroups - 1) / ngroups;
         const int ng = (nbb + gs - 1) / gs;
         dim3 g((N + TL - 1) / TL, N, ng);
         using DS = typename DensAcc<T>::S;
         DS* r3 = reinterpret_cast<DS*>(rho3);
         DS* sl = reinterpret_cast<DS*>(slot);
+        auto go = [&](auto kernel) {
+            set_smem(kernel, sm);
+            roks::count_launch(),
+                kernel<<<g, kThreads, sm, st>>>(s, tw, Yp, r3, sl, b0, nbb, gs, nc, T(scale), part_sel, cls_override);
+        };
+        const bool pr = prune(s);
         if (part_sel == 0)
-            roks::count_launch(), k_band_x_density<T, N, false><<<g, kThreads, sm, st>>>(
-                                      s, tw, Yp, r3, sl, b0, nbb, gs, nc, T(scale), part_sel, cls_override);
+            pr ? go(k_band_x_density<T, N, false, true>) : go(k_band_x_density<T, N, false, false>);
         else
-            roks::count_launch(), k_band_x_density<T, N, true><<<g, kThreads, sm, st>>>(
-                                      s, tw, Yp, r3, sl, b0, nbb, gs, nc, T(scale), part_sel, cls_override);
+            pr ? go(k_band_x_density<T, N, true, true>) : go(k_band_x_density<T, N, true, false>);
         if (!sl) return;
         const int N3 = N * N * N;
         roks::count_launch(), k_density_reduce<T><<<(unsigned)((N3 + 255) / 256), 256, 0, st>>>(N3, ng, sl, r3);

@@ -3,7 +3,15 @@ compiles the pass sequence of fft_core.cuh (radix plan, register codelets,
 twiddles, Stockham index map) as host code and compares every compiled grid
 length (16, 24, 32, 48, 72, 96, 120), in both directions, with the DFT sum
 written out in extended precision.  FP64 bar: 1e-14 relative to the largest
-output (the measured errors are near 3e-16)."""
+output (the measured errors are near 3e-16).
+
+The sphere-pruned first pass (inputs known to be zero left out, for the
+frequencies |i| <= (N - 1) / 4) against the same sums at the same bar, with
+every dropped input checked to lie outside that range and the number of
+dropped inputs of the 120-, 96- and 72-point plans fixed (7 of 15, 6 of 12,
+3 of 9).  Every pruned codelet (radix 2, 3, 4, 5, 8) for every mask it
+accepts equals the plain codelet on inputs with zeros at the mask, exactly:
+it only leaves out additions of zeros."""
 import os
 import shutil
 import subprocess
@@ -23,9 +31,24 @@ def test_pass_arithmetic_all_grid_lengths(tmp_path):
     subprocess.run([nvcc, "-std=c++17", "-O2", "-gencode", "arch=compute_103a,code=sm_103a", "-I", inc, src,
                     "-o", str(exe)], check=True, capture_output=True, timeout=600)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True, timeout=300).stdout
-    seen = set()
+    seen, pruned, codelets = set(), {}, {}
     for line in out.strip().splitlines():
-        n, d, err = line.split()
-        seen.add((int(n), int(d)))
-        assert float(err) < 1e-14, line
-    assert seen == {(n, d) for n in (16, 24, 32, 48, 72, 96, 120) for d in (-1, 1)}
+        f = line.split()
+        if f[0] == "prune":
+            n, d, err, nz, ok = int(f[1]), int(f[2]), float(f[3]), int(f[4]), int(f[5])
+            assert err < 1e-14 and ok == 1, line
+            pruned[(n, d)] = nz
+        elif f[0] == "codelet":
+            r, d, err, count = int(f[1]), int(f[2]), float(f[3]), int(f[4])
+            assert err == 0.0, line
+            codelets[(r, d)] = count
+        else:
+            n, d, err = f
+            seen.add((int(n), int(d)))
+            assert float(err) < 1e-14, line
+    lengths = (16, 24, 32, 48, 72, 96, 120)
+    assert seen == {(n, d) for n in lengths for d in (-1, 1)}
+    assert set(pruned) == seen
+    assert all(pruned[(n, d)] > 0 for n, d in pruned)
+    assert (pruned[(120, 1)], pruned[(96, 1)], pruned[(72, 1)]) == (7, 6, 3)
+    assert codelets == {(r, d): c for r, c in ((2, 4), (3, 4), (4, 16), (5, 16), (8, 225)) for d in (-1, 1)}
