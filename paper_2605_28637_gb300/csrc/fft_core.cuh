@@ -50,6 +50,34 @@ __host__ __device__ __forceinline__ V mul_i(V a) {
     if (DIR > 0) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
     return r;
 }
+// a * s + c with s real
+template <typename V, typename S>
+__host__ __device__ __forceinline__ V cfma(V a, S s, V c) {
+    V r; r.x = a.x * s + c.x; r.y = a.y * s + c.y; return r;
+}
+// a + dir i b and a - dir i b, without forming i b (its components swap
+// places, which paired instructions cannot do)
+template <int DIR, typename V>
+__host__ __device__ __forceinline__ V cadd_i(V a, V b) {
+    V r;
+    if (DIR > 0) { r.x = a.x - b.y; r.y = a.y + b.x; } else { r.x = a.x + b.y; r.y = a.y - b.x; }
+    return r;
+}
+template <int DIR, typename V>
+__host__ __device__ __forceinline__ V csub_i(V a, V b) { return cadd_i<-DIR, V>(a, b); }
+
+// Paired FP32 arithmetic (sm_100 and later): the complex float2 add,
+// subtract, real scale and real multiply-add are each one instruction on
+// both components, rounded to nearest like the scalar forms.  These
+// overloads take precedence over the templates above in device code; the
+// codelets below are written so that every swap of components (the factor i)
+// stays in cadd_i / csub_i.
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
+__device__ __forceinline__ float2 cfma(float2 a, float s, float2 c) { return __ffma2_rn(a, make_float2(s, s), c); }
+#endif
 
 // ---------------------------------------------------------------- plans
 // Radix sequence of a transform length.  The grid sizes of the workloads get
@@ -160,20 +188,20 @@ template <int DIR, typename V> struct Dft<3, DIR, V> {
         using T = decltype(v[0].x);
         const T h = T(0.86602540378443864676);         // sin(2 pi / 3)
         V t = cadd(v[1], v[2]);
-        V u = mul_i<DIR>(cscale(csub(v[1], v[2]), h));
-        V m = csub(v[0], cscale(t, T(0.5)));
+        V d = cscale(csub(v[1], v[2]), h);
+        V m = cfma(t, T(-0.5), v[0]);
         v[0] = cadd(v[0], t);
-        v[1] = cadd(m, u);
-        v[2] = csub(m, u);
+        v[1] = cadd_i<DIR>(m, d);
+        v[2] = csub_i<DIR>(m, d);
     }
 };
 
 template <int DIR, typename V> struct Dft<4, DIR, V> {
     __host__ __device__ static __forceinline__ void run(V* v) {
         V t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-        V t2 = cadd(v[1], v[3]), t3 = mul_i<DIR>(csub(v[1], v[3]));
+        V t2 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
         v[0] = cadd(t0, t2); v[2] = csub(t0, t2);
-        v[1] = cadd(t1, t3); v[3] = csub(t1, t3);
+        v[1] = cadd_i<DIR>(t1, d); v[3] = csub_i<DIR>(t1, d);
     }
 };
 
@@ -186,32 +214,39 @@ template <int DIR, typename V> struct Dft<5, DIR, V> {
         const T s2 = T(0.58778525229247312917);   // sin(4 pi / 5)
         V t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
         V u1 = csub(v[1], v[4]), u2 = csub(v[2], v[3]);
-        V a1 = cadd(v[0], cadd(cscale(t1, c1), cscale(t2, c2)));
-        V a2 = cadd(v[0], cadd(cscale(t1, c2), cscale(t2, c1)));
-        V b1 = mul_i<DIR>(cadd(cscale(u1, s1), cscale(u2, s2)));
-        V b2 = mul_i<DIR>(csub(cscale(u1, s2), cscale(u2, s1)));
+        V a1 = cfma(t2, c2, cfma(t1, c1, v[0]));
+        V a2 = cfma(t2, c1, cfma(t1, c2, v[0]));
+        V b1 = cfma(u2, s2, cscale(u1, s1));
+        V b2 = cfma(u2, -s1, cscale(u1, s2));
         v[0] = cadd(v[0], cadd(t1, t2));
-        v[1] = cadd(a1, b1); v[4] = csub(a1, b1);
-        v[2] = cadd(a2, b2); v[3] = csub(a2, b2);
+        v[1] = cadd_i<DIR>(a1, b1); v[4] = csub_i<DIR>(a1, b1);
+        v[2] = cadd_i<DIR>(a2, b2); v[3] = csub_i<DIR>(a2, b2);
+    }
+};
+
+// The last butterflies of the 8-point DFT from the 4-point DFTs of the even
+// (e) and odd (o) inputs, with the twiddles exp(DIR i pi k / 4), k = 1, 2, 3:
+// (1 + DIR i) / sqrt 2, DIR i, (DIR i - 1) / sqrt 2.
+template <int DIR, typename V> struct Dft8Combine {
+    __host__ __device__ static __forceinline__ void run(V* v, const V* e, const V* o) {
+        using T = decltype(v[0].x);
+        const T r2 = T(0.70710678118654752440);    // cos(pi / 4)
+        V w1 = cscale(cadd_i<DIR>(o[1], o[1]), r2);
+        V w3 = cscale(csub_i<DIR>(o[3], o[3]), -r2);
+        v[0] = cadd(e[0], o[0]);         v[4] = csub(e[0], o[0]);
+        v[1] = cadd(e[1], w1);           v[5] = csub(e[1], w1);
+        v[2] = cadd_i<DIR>(e[2], o[2]);  v[6] = csub_i<DIR>(e[2], o[2]);
+        v[3] = cadd(e[3], w3);           v[7] = csub(e[3], w3);
     }
 };
 
 template <int DIR, typename V> struct Dft<8, DIR, V> {
     __host__ __device__ static __forceinline__ void run(V* v) {
-        using T = decltype(v[0].x);
-        const T r2 = T(0.70710678118654752440);    // cos(pi / 4)
         V e[4] = {v[0], v[2], v[4], v[6]};
         V o[4] = {v[1], v[3], v[5], v[7]};
         Dft<4, DIR, V>::run(e);
         Dft<4, DIR, V>::run(o);
-        // twiddles exp(DIR i pi k / 4), k = 1, 2, 3
-        V w1 = cscale(cadd(o[1], mul_i<DIR>(o[1])), r2);
-        V w2 = mul_i<DIR>(o[2]);
-        V w3 = cscale(csub(mul_i<DIR>(o[3]), o[3]), r2);
-        v[0] = cadd(e[0], o[0]); v[4] = csub(e[0], o[0]);
-        v[1] = cadd(e[1], w1);   v[5] = csub(e[1], w1);
-        v[2] = cadd(e[2], w2);   v[6] = csub(e[2], w2);
-        v[3] = cadd(e[3], w3);   v[7] = csub(e[3], w3);
+        Dft8Combine<DIR, V>::run(v, e, o);
     }
 };
 
@@ -276,19 +311,18 @@ template <int DIR, typename V> struct Dft<16, DIR, V> : DftAB<4, 4, DIR, V> {};
 // ---------------------------------------------------------------- pruned codelets
 // The same DFTs when some inputs are known at compile time to be zero (bit n
 // of Z: input n is zero and holds 0).  Additions with a known zero are left
-// out; Z = 0 is the plain codelet.  The first pass of an inverse x transform
-// uses them: x planes outside the sphere are zero for every butterfly.
+// out, a difference with a zero first operand carries its sign into the next
+// constant or into the choice of cadd_i / csub_i, and the remaining operations
+// are those of the plain codelet in the same order, so a pruned codelet gives
+// the plain codelet's result exactly.  Z = 0 is the plain codelet.  Input 0
+// is never pruned (the first pass's butterflies all read a frequency near 0
+// there).  The first pass of an inverse x or y transform uses them: x and y
+// planes outside the sphere are zero for every butterfly.
 template <bool ZA, bool ZB, typename V>
 __host__ __device__ __forceinline__ V zadd(V a, V b) {
     if constexpr (ZB) return a;          // also a = b = 0
     else if constexpr (ZA) return b;
     else return cadd(a, b);
-}
-template <bool ZA, bool ZB, typename V>
-__host__ __device__ __forceinline__ V zsub(V a, V b) {
-    if constexpr (ZB) return a;
-    else if constexpr (ZA) { V r; r.x = -b.x; r.y = -b.y; return r; }
-    else return csub(a, b);
 }
 
 template <int R, int DIR, typename V, unsigned Z> struct DftZ {
@@ -297,94 +331,114 @@ template <int R, int DIR, typename V, unsigned Z> struct DftZ {
 };
 
 template <int DIR, typename V, unsigned Z> struct DftZ<2, DIR, V, Z> {
+    static_assert(!(Z & 1u), "input 0 of a pruned codelet is not zero");
     __host__ __device__ static __forceinline__ void run(V* v) {
-        constexpr bool z0 = Z & 1u, z1 = Z & 2u;
-        V a = zadd<z0, z1>(v[0], v[1]), b = zsub<z0, z1>(v[0], v[1]);
-        v[0] = a; v[1] = b;
+        if constexpr (Z & 2u) v[1] = v[0];
+        else Dft<2, DIR, V>::run(v);
     }
 };
 
 template <int DIR, typename V, unsigned Z> struct DftZ<3, DIR, V, Z> {
+    static_assert(!(Z & 1u), "input 0 of a pruned codelet is not zero");
     __host__ __device__ static __forceinline__ void run(V* v) {
+        using T = decltype(v[0].x);
+        constexpr bool z1 = Z & 2u, z2 = Z & 4u;
         if constexpr (Z == 0) {
             Dft<3, DIR, V>::run(v);
+        } else if constexpr (z1 && z2) {
+            v[1] = v[0]; v[2] = v[0];
         } else {
-            static_assert(!(Z & 1u), "input 0 of a pruned 3-point codelet is not zero");
-            using T = decltype(v[0].x);
-            constexpr bool z1 = Z & 2u, z2 = Z & 4u;
-            if constexpr (z1 && z2) {
-                v[1] = v[0]; v[2] = v[0];
-            } else {
-                const T h = T(0.86602540378443864676);
-                V t = zadd<z1, z2>(v[1], v[2]);
-                V u = mul_i<DIR>(cscale(zsub<z1, z2>(v[1], v[2]), h));
-                V m = csub(v[0], cscale(t, T(0.5)));
-                v[0] = cadd(v[0], t);
-                v[1] = cadd(m, u);
-                v[2] = csub(m, u);
-            }
+            const T h = T(0.86602540378443864676);
+            V t = zadd<z1, z2>(v[1], v[2]);
+            V d;
+            if constexpr (z1) d = cscale(v[2], -h);
+            else d = cscale(v[1], h);
+            V m = cfma(t, T(-0.5), v[0]);
+            v[0] = cadd(v[0], t);
+            v[1] = cadd_i<DIR>(m, d);
+            v[2] = csub_i<DIR>(m, d);
         }
     }
 };
 
 template <int DIR, typename V, unsigned Z> struct DftZ<4, DIR, V, Z> {
+    static_assert(!(Z & 1u), "input 0 of a pruned codelet is not zero");
     __host__ __device__ static __forceinline__ void run(V* v) {
+        constexpr bool z1 = Z & 2u, z2 = Z & 4u, z3 = Z & 8u;
         if constexpr (Z == 0) {
             Dft<4, DIR, V>::run(v);
         } else {
-            constexpr bool z0 = Z & 1u, z1 = Z & 2u, z2 = Z & 4u, z3 = Z & 8u;
-            constexpr bool ze = z0 && z2, zo = z1 && z3;
-            V t0 = zadd<z0, z2>(v[0], v[2]), t1 = zsub<z0, z2>(v[0], v[2]);
-            V t2 = zadd<z1, z3>(v[1], v[3]), t3 = mul_i<DIR>(zsub<z1, z3>(v[1], v[3]));
-            v[0] = zadd<ze, zo>(t0, t2); v[2] = zsub<ze, zo>(t0, t2);
-            v[1] = zadd<ze, zo>(t1, t3); v[3] = zsub<ze, zo>(t1, t3);
+            V t0, t1;
+            if constexpr (z2) { t0 = v[0]; t1 = v[0]; }
+            else { t0 = cadd(v[0], v[2]); t1 = csub(v[0], v[2]); }
+            if constexpr (z1 && z3) {
+                v[0] = t0; v[1] = t1; v[2] = t0; v[3] = t1;
+            } else {
+                V t2, o1, o3;
+                if constexpr (z1) {            // d = -v3
+                    t2 = v[3];
+                    o1 = csub_i<DIR>(t1, v[3]); o3 = cadd_i<DIR>(t1, v[3]);
+                } else if constexpr (z3) {     // d = v1
+                    t2 = v[1];
+                    o1 = cadd_i<DIR>(t1, v[1]); o3 = csub_i<DIR>(t1, v[1]);
+                } else {
+                    t2 = cadd(v[1], v[3]);
+                    V d = csub(v[1], v[3]);
+                    o1 = cadd_i<DIR>(t1, d); o3 = csub_i<DIR>(t1, d);
+                }
+                v[0] = cadd(t0, t2); v[2] = csub(t0, t2);
+                v[1] = o1; v[3] = o3;
+            }
         }
     }
 };
 
 template <int DIR, typename V, unsigned Z> struct DftZ<5, DIR, V, Z> {
+    static_assert(!(Z & 1u), "input 0 of a pruned codelet is not zero");
     __host__ __device__ static __forceinline__ void run(V* v) {
         if constexpr (Z == 0) {
             Dft<5, DIR, V>::run(v);
         } else {
-            static_assert(!(Z & 1u), "input 0 of a pruned 5-point codelet is not zero");
             using T = decltype(v[0].x);
             const T c1 = T(0.30901699437494742410);   // cos(2 pi / 5)
             const T c2 = T(-0.80901699437494742410);  // cos(4 pi / 5)
             const T s1 = T(0.95105651629515357212);   // sin(2 pi / 5)
             const T s2 = T(0.58778525229247312917);   // sin(4 pi / 5)
             constexpr bool z1 = Z & 2u, z2 = Z & 4u, z3 = Z & 8u, z4 = Z & 16u;
-            constexpr bool p1 = !(z1 && z4), p2 = !(z2 && z3);   // pair (1, 4) and pair (2, 3) present
+            constexpr bool p1 = !(z1 && z4), p2 = !(z2 && z3);   // pair (1, 4), pair (2, 3) present
+            // sums t and differences u = g * w of the pairs, g = -1 when the
+            // pair's first member is zero (then w is the second member)
+            constexpr T g1 = z1 ? T(-1) : T(1), g2 = z2 ? T(-1) : T(1);
             V t1 = zadd<z1, z4>(v[1], v[4]), t2 = zadd<z2, z3>(v[2], v[3]);
-            V u1 = zsub<z1, z4>(v[1], v[4]), u2 = zsub<z2, z3>(v[2], v[3]);
+            V w1, w2;
+            if constexpr (z1 || z4) w1 = t1; else w1 = csub(v[1], v[4]);
+            if constexpr (z2 || z3) w2 = t2; else w2 = csub(v[2], v[3]);
             if constexpr (!p1 && !p2) {
                 v[1] = v[0]; v[2] = v[0]; v[3] = v[0]; v[4] = v[0];
             } else {
                 V a1, a2, b1, b2, s0;
                 if constexpr (p1 && p2) {
-                    a1 = cadd(v[0], cadd(cscale(t1, c1), cscale(t2, c2)));
-                    a2 = cadd(v[0], cadd(cscale(t1, c2), cscale(t2, c1)));
-                    b1 = cadd(cscale(u1, s1), cscale(u2, s2));
-                    b2 = csub(cscale(u1, s2), cscale(u2, s1));
+                    a1 = cfma(t2, c2, cfma(t1, c1, v[0]));
+                    a2 = cfma(t2, c1, cfma(t1, c2, v[0]));
+                    b1 = cfma(w2, g2 * s2, cscale(w1, g1 * s1));
+                    b2 = cfma(w2, -g2 * s1, cscale(w1, g1 * s2));
                     s0 = cadd(v[0], cadd(t1, t2));
                 } else if constexpr (p1) {
-                    a1 = cadd(v[0], cscale(t1, c1));
-                    a2 = cadd(v[0], cscale(t1, c2));
-                    b1 = cscale(u1, s1);
-                    b2 = cscale(u1, s2);
+                    a1 = cfma(t1, c1, v[0]);
+                    a2 = cfma(t1, c2, v[0]);
+                    b1 = cscale(w1, g1 * s1);
+                    b2 = cscale(w1, g1 * s2);
                     s0 = cadd(v[0], t1);
                 } else {
-                    a1 = cadd(v[0], cscale(t2, c2));
-                    a2 = cadd(v[0], cscale(t2, c1));
-                    b1 = cscale(u2, s2);
-                    b2 = cscale(u2, -s1);
+                    a1 = cfma(t2, c2, v[0]);
+                    a2 = cfma(t2, c1, v[0]);
+                    b1 = cscale(w2, g2 * s2);
+                    b2 = cscale(w2, -g2 * s1);
                     s0 = cadd(v[0], t2);
                 }
-                b1 = mul_i<DIR>(b1);
-                b2 = mul_i<DIR>(b2);
                 v[0] = s0;
-                v[1] = cadd(a1, b1); v[4] = csub(a1, b1);
-                v[2] = cadd(a2, b2); v[3] = csub(a2, b2);
+                v[1] = cadd_i<DIR>(a1, b1); v[4] = csub_i<DIR>(a1, b1);
+                v[2] = cadd_i<DIR>(a2, b2); v[3] = csub_i<DIR>(a2, b2);
             }
         }
     }
@@ -395,23 +449,14 @@ template <int DIR, typename V, unsigned Z> struct DftZ<8, DIR, V, Z> {
         if constexpr (Z == 0) {
             Dft<8, DIR, V>::run(v);
         } else {
-            using T = decltype(v[0].x);
-            const T r2 = T(0.70710678118654752440);
             // even inputs 0, 2, 4, 6 and odd inputs 1, 3, 5, 7
             constexpr unsigned ZE = (Z & 1u) | ((Z >> 1) & 2u) | ((Z >> 2) & 4u) | ((Z >> 3) & 8u);
             constexpr unsigned ZO = ((Z >> 1) & 1u) | ((Z >> 2) & 2u) | ((Z >> 3) & 4u) | ((Z >> 4) & 8u);
-            static_assert(ZE != 15u && ZO != 15u, "a pruned 8-point codelet keeps even and odd inputs");
             V e[4] = {v[0], v[2], v[4], v[6]};
             V o[4] = {v[1], v[3], v[5], v[7]};
             DftZ<4, DIR, V, ZE>::run(e);
             DftZ<4, DIR, V, ZO>::run(o);
-            V w1 = cscale(cadd(o[1], mul_i<DIR>(o[1])), r2);
-            V w2 = mul_i<DIR>(o[2]);
-            V w3 = cscale(csub(mul_i<DIR>(o[3]), o[3]), r2);
-            v[0] = cadd(e[0], o[0]); v[4] = csub(e[0], o[0]);
-            v[1] = cadd(e[1], w1);   v[5] = csub(e[1], w1);
-            v[2] = cadd(e[2], w2);   v[6] = csub(e[2], w2);
-            v[3] = cadd(e[3], w3);   v[7] = csub(e[3], w3);
+            Dft8Combine<DIR, V>::run(v, e, o);
         }
     }
 };

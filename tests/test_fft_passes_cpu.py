@@ -51,4 +51,4 @@ def test_pass_arithmetic_all_grid_lengths(tmp_path):
     assert set(pruned) == seen
     assert all(pruned[(n, d)] > 0 for n, d in pruned)
     assert (pruned[(120, 1)], pruned[(96, 1)], pruned[(72, 1)]) == (7, 6, 3)
-    assert codelets == {(r, d): c for r, c in ((2, 4), (3, 4), (4, 16), (5, 16), (8, 225)) for d in (-1, 1)}
+    assert codelets == {(r, d): c for r, c in ((2, 2), (3, 4), (4, 8), (5, 16), (8, 64)) for d in (-1, 1)}
