@@ -52,3 +52,23 @@ def test_pass_arithmetic_all_grid_lengths(tmp_path):
     assert all(pruned[(n, d)] > 0 for n, d in pruned)
     assert (pruned[(120, 1)], pruned[(96, 1)], pruned[(72, 1)]) == (7, 6, 3)
     assert codelets == {(r, d): c for r, c in ((2, 2), (3, 4), (4, 8), (5, 16), (8, 64)) for d in (-1, 1)}
+
+
+def test_full_size_workloads_take_the_pruned_first_pass():
+    """The pruned first pass applies to spheres with nmax <= (N - 1) / 4 (the
+    density fits the grid without aliasing).  The full-size workloads are such
+    spheres, so the benchmark runs the pruned instances; tiny-16 (nmax 6 on a
+    16-point grid) is not, and its parity cases run the full first pass."""
+    import math
+
+    from paper_2605_28637_gb300 import synthetic as syn
+
+    def nmax(cfg):
+        m = math.floor(2.0 * cfg["ecut"] * (cfg["L"] / (2.0 * math.pi)) ** 2)
+        return math.isqrt(m)
+
+    for name in ("organic-96", "mgo-120", "hybrid-72", "mgo-72", "mgo-32"):
+        cfg = syn.make_config(name, 0)
+        assert nmax(cfg) <= (cfg["grid"] - 1) // 4, name
+    tiny = syn.make_config("tiny-16", 0)
+    assert nmax(tiny) > (tiny["grid"] - 1) // 4
