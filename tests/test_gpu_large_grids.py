@@ -1,14 +1,16 @@
-"""GPU parity on the 72^3 and 120^3 grids (the transform lengths of the
-hybrid-72 and mgo-120 workloads) at small band counts, against the FP64
+"""GPU parity on the 72^3, 96^3 and 120^3 grids (the transform lengths of
+the hybrid-72, organic-96 and mgo-120 workloads) at small band counts,
+against the FP64
 oracle: densities, potentials, energies, F|n> and S|n> on the FP64 path
 (1e-10 relative) and on the mixed path (the bars of test_gpu_parity.py:
 densities 2e-6, F|n> 2e-5, S|n> 2e-6 relative, energies 2e-5 Ha), and, on
 the 72^3 grid, one FP64 PCG step.
 
-The first two spheres (nmax 7 and 8) take the inverse transforms whose first
-pass leaves out the x and y planes that are zero for every butterfly
-(nmax <= (N - 1) / 4); the "wide" ones (nmax 19 on 72^3, 30 on 120^3) are
-too large for that and take the full first passes."""
+The small spheres (nmax 7 on 72^3, 8 on 96^3 and 120^3) take the inverse
+transforms whose first pass leaves out the x and y planes that are zero for
+every butterfly (nmax <= (N - 1) / 4); the "wide" ones (nmax 19 on 72^3, 25
+on 96^3, 30 on 120^3) are too large for that and take the full first
+passes."""
 import pytest
 
 from oracle import roks as R
@@ -20,10 +22,13 @@ pytestmark = pytest.mark.gpu
 GRIDS = {
     "grid72": dict(grid=72, L=14.0, ecut=6.0, n_closed=2),
     "grid120": dict(grid=120, L=16.0, ecut=6.0, n_closed=2),
+    "grid96": dict(grid=96, L=16.0, ecut=6.0, n_closed=2),
     "grid72-wide": dict(grid=72, L=14.0, ecut=38.0, n_closed=2),
+    "grid96-wide": dict(grid=96, L=16.0, ecut=50.0, n_closed=2),
     "grid120-wide": dict(grid=120, L=16.0, ecut=70.0, n_closed=2),
 }
-PRUNED = {"grid72": True, "grid120": True, "grid72-wide": False, "grid120-wide": False}
+PRUNED = {"grid72": True, "grid120": True, "grid96": True, "grid72-wide": False, "grid96-wide": False,
+          "grid120-wide": False}
 
 
 @pytest.mark.parametrize("name", list(GRIDS))
