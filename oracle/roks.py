@@ -73,8 +73,10 @@ E_T term by term; gamma, the gradient split, p_I and the R-matrix rotation
 against their defining identities; the line-search slope against finite
 differences along the path taken; the converged result against the dense
 generalised eigenproblem (closed shell) and the stationarity conditions
-(singlet).  Parity unpinned: the exact sequence of step lengths (R5) and of
-Fletcher-Reeves ratios (R4) beyond monotone descent and the fixed point.
+(singlet); the Fletcher-Reeves numerator (R4) against central differences
+of the energy along a fresh steepest-descent path, and each accepted step
+(R5) against the energy along its own path (a local minimum on +-25%, or
+still descending where the 3 dt cap applies).
 """
 from __future__ import annotations
 

@@ -193,3 +193,64 @@ def test_line_search_slope_matches_finite_difference():
         assert abs(fd - info.dE0) < 1e-6 * max(1.0, abs(info.dE0)), (it, fd, info.dE0)
         checked += info.beta != 0.0
     assert checked >= 1          # at least one step used the Fletcher-Reeves history
+
+
+@pytest.mark.parametrize("mode_kw", [dict(), dict(mode=0, n_closed=5), dict(mode=2)],
+                         ids=["singlet", "ground-state", "triplet"])
+def test_line_search_step_and_fr_numerator_against_the_energy_curve(mode_kw):
+    """The step lengths (R5) and the Fletcher-Reeves ratios (R4), each
+    against the energy along a path rather than against the formulas.
+
+    * Fletcher-Reeves numerator: the ratio of step i is pg_i / pg_{i-1}, with
+      pg = Re<p_I|g_I> + 1/2 Re<A|G_in> at the step's start.  A fresh solver
+      at that start takes the preconditioned steepest-descent direction, and
+      central differences of the energy along its path give the slope.  The
+      slope equals 2 pg, so both factors of every ratio are fixed by energies.
+      A dropped 1/2 on the in-subspace term, a sign, or the full gradient in
+      place of g_I would break it.
+    * Step: the accepted step minimises the energy along the accepted path
+      to within the quadratic model's error.  The energy at 0.75 and 1.25
+      times the step lies above the energy at the step.  A step off by a
+      factor of two from the parabola's vertex fails this.  The first step
+      is capped at 3 dt (R5), and there the energy still falls past the
+      step."""
+    s, Psi = start(tiny(**mode_kw))
+    pcg = R.PCG(s)
+    seen = []
+    trial = pcg.trial
+
+    def spy(P, d, A, h):
+        seen.append((P, d, A))
+        return trial(P, d, A, h)
+
+    pcg.trial = spy
+    h = 1e-4
+    for it in range(6):
+        fresh = R.PCG(s)
+        fresh_calls = []
+
+        def fresh_spy(P, d, A, t, calls=fresh_calls):
+            calls.append((P, d, A))
+            return trial(P, d, A, t)
+
+        fresh.trial = fresh_spy
+        _, finfo = fresh.step(Psi)
+        assert finfo.beta == 0.0 and not finfo.restarted
+        P0, d0, A0 = fresh_calls[0]
+        slope = (s.energy(trial(P0, d0, A0, h)) - s.energy(trial(P0, d0, A0, -h))) / (2 * h)
+
+        dt = pcg.dt
+        start_psi = Psi
+        Psi, info = pcg.step(Psi)
+        assert abs(slope - 2.0 * pcg.pg_prev) < 1e-7 * abs(slope), (it, slope, pcg.pg_prev)
+
+        Pa, da, Aa = [x for x in seen if x[0] is start_psi][-1]
+        st = info.step
+        e_at = s.energy(trial(Pa, da, Aa, st))
+        e_lo = s.energy(trial(Pa, da, Aa, 0.75 * st))
+        e_hi = s.energy(trial(Pa, da, Aa, 1.25 * st))
+        assert e_at == pytest.approx(info.E_new, abs=1e-12)
+        if abs(st - 3.0 * dt) < 1e-15:
+            assert e_hi < e_at < e_lo, (it, e_lo, e_at, e_hi)      # capped: still descending
+        else:
+            assert e_at < e_lo and e_at < e_hi, (it, e_lo, e_at, e_hi)
